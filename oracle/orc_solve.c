@@ -1,0 +1,298 @@
+/*
+ * orc_solve.c -- Dirichlet data projection, right-hand side (1/2 M_h + K_h) g,
+ * block-Toeplitz matrix-vector product and block forward substitution for
+ * V_h w = (1/2 M_h + K_h) g, plus the L2(Sigma_h) error of w_h
+ * (TEST INFRASTRUCTURE ONLY; see orc.h).
+ *
+ * Sec. 3.4 (systems of linear equations), Sec. 6.1 (exterior heat source
+ * data and the relative L2(Sigma_h) error).  With piecewise constant trial
+ * functions for g the mass matrix is M_h = h blockdiag(diag(Delta_l)).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include "orc.h"
+
+static void chi_plain(const double *P0, const double *P1, const double *P2,
+                      double s1, double s2, double *x)
+{
+    for (int c = 0; c < 3; ++c)
+        x[c] = P0[c] + s1 * (P1[c] - P0[c]) + s2 * (P2[c] - P1[c]);
+}
+
+/* g_r(x, t) = sum_s weight_s G_alpha(x - y_s, t - t0_s) */
+static double dirichlet_datum(const double *src, int32_t n_src, double alpha,
+                              const double *x, double t)
+{
+    double g = 0.0;
+    for (int s = 0; s < n_src; ++s) {
+        const double *S = src + 5 * s;
+        double d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
+        g += S[4] * orc_heat_kernel(sqrt(d0 * d0 + d1 * d1 + d2 * d2), t - S[3], alpha);
+    }
+    return g;
+}
+
+/* w_r(x, t) = alpha du/dn_x = sum_s weight_s alpha grad_x G . n_x
+ *          = -sum_s weight_s G_alpha(x - y_s, t - t0_s) ((x - y_s) . n_x) / (2 (t - t0_s)) */
+static double neumann_datum(const double *src, int32_t n_src, double alpha,
+                            const double *x, const double *n, double t)
+{
+    double w = 0.0;
+    for (int s = 0; s < n_src; ++s) {
+        const double *S = src + 5 * s;
+        double tau = t - S[3];
+        if (tau <= 0.0)
+            continue;
+        double d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
+        double rho = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        double dn = d0 * n[0] + d1 * n[1] + d2 * n[2];
+        w -= S[4] * orc_heat_kernel(rho, tau, alpha) * dn / (2.0 * tau);
+    }
+    return w;
+}
+
+/* L2 projection into piecewise constants: the element mean
+ * g_{r,k,j} = (h Delta_j)^{-1} int_{t_k}^{t_{k+1}} int_{gamma_j} g_r,
+ * by the conical rule of order q_space in space and n_time Gauss-Legendre
+ * points per step (the paper only asks for rules of sufficiently high order). */
+int orc_project_dirichlet(const double *nodes, int64_t n_nodes,
+                          const int32_t *tris, int64_t E, double alpha,
+                          double T, int32_t n_steps, const double *sources,
+                          int32_t n_src, int32_t nrhs, int32_t q_space,
+                          int32_t n_time, double *g)
+{
+    if (E < 1 || n_steps < 1 || nrhs < 1 || n_src < 1 || q_space < 1 ||
+        q_space > 32 || n_time < 1 || n_time > 64)
+        return -1;
+    int nq = q_space * q_space;
+    double *s1 = malloc(sizeof(double) * nq), *s2 = malloc(sizeof(double) * nq);
+    double *sw = malloc(sizeof(double) * nq), tx[64], tw[64];
+    int rc = -1;
+    if (orc_triangle_rule(q_space, s1, s2, sw) || orc_gauss_legendre01(n_time, tx, tw))
+        goto done;
+    double h = T / n_steps;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k)
+            for (int64_t j = 0; j < E; ++j) {
+                const int32_t *t3 = tris + 3 * j;
+                double acc = 0.0;
+                for (int a = 0; a < nq; ++a) {
+                    double x[3];
+                    chi_plain(nodes + 3 * t3[0], nodes + 3 * t3[1], nodes + 3 * t3[2],
+                              s1[a], s2[a], x);
+                    for (int b = 0; b < n_time; ++b)
+                        acc += sw[a] * tw[b] *
+                               dirichlet_datum(sources + (int64_t)r * n_src * 5, n_src,
+                                               alpha, x, (k + tx[b]) * h);
+                }
+                /* (h Delta)^{-1} * (2 Delta) * h * acc */
+                g[((int64_t)r * n_steps + k) * E + j] = 2.0 * acc;
+            }
+    rc = 0;
+done:
+    free(s1);
+    free(s2);
+    free(sw);
+    return rc;
+}
+
+/* Element means of the exact Neumann datum w_r = alpha du/dn_x (the L2
+ * projection into piecewise constants, whose error is the best-approximation
+ * reference of Table dirconv's "projected" column), same rule as above. */
+int orc_project_neumann(const double *nodes, int64_t n_nodes,
+                        const int32_t *tris, int64_t E, double alpha, double T,
+                        int32_t n_steps, const double *sources, int32_t n_src,
+                        int32_t nrhs, int32_t q_space, int32_t n_time,
+                        double *wproj)
+{
+    if (E < 1 || n_steps < 1 || nrhs < 1 || n_src < 1 || q_space < 1 ||
+        q_space > 32 || n_time < 1 || n_time > 64)
+        return -1;
+    int nq = q_space * q_space;
+    double *s1 = malloc(sizeof(double) * nq), *s2 = malloc(sizeof(double) * nq);
+    double *sw = malloc(sizeof(double) * nq), tx[64], tw[64];
+    double *area = malloc(sizeof(double) * E), *normal = malloc(sizeof(double) * 3 * E);
+    int rc = -1;
+    if (orc_triangle_rule(q_space, s1, s2, sw) || orc_gauss_legendre01(n_time, tx, tw) ||
+        orc_triangle_geometry(nodes, n_nodes, tris, E, area, normal))
+        goto done;
+    double h = T / n_steps;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k)
+            for (int64_t j = 0; j < E; ++j) {
+                const int32_t *t3 = tris + 3 * j;
+                double acc = 0.0;
+                for (int a = 0; a < nq; ++a) {
+                    double x[3];
+                    chi_plain(nodes + 3 * t3[0], nodes + 3 * t3[1], nodes + 3 * t3[2],
+                              s1[a], s2[a], x);
+                    for (int b = 0; b < n_time; ++b)
+                        acc += sw[a] * tw[b] *
+                               neumann_datum(sources + (int64_t)r * n_src * 5, n_src, alpha,
+                                             x, normal + 3 * j, (k + tx[b]) * h);
+                }
+                wproj[((int64_t)r * n_steps + k) * E + j] = 2.0 * acc;
+            }
+    rc = 0;
+done:
+    free(s1);
+    free(s2);
+    free(sw);
+    free(area);
+    free(normal);
+    return rc;
+}
+
+/* y_r^k = sum_{d=0}^{k} A^d x_r^{k-d}  (eq. V_mat layout), A: [n_steps][E][E]. */
+int orc_toeplitz_matvec(const double *A, int64_t E, int32_t n_steps,
+                        int32_t nrhs, const double *x, double *y)
+{
+    if (E < 1 || n_steps < 1 || nrhs < 1)
+        return -1;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k)
+            for (int64_t l = 0; l < E; ++l) {
+                double acc = 0.0;
+                for (int d = 0; d <= k; ++d) {
+                    const double *Arow = A + ((int64_t)d * E + l) * E;
+                    const double *xv = x + ((int64_t)r * n_steps + (k - d)) * E;
+                    for (int64_t j = 0; j < E; ++j)
+                        acc += Arow[j] * xv[j];
+                }
+                y[((int64_t)r * n_steps + k) * E + l] = acc;
+            }
+    return 0;
+}
+
+/* f = (1/2 M_h + K_h) g with M_h = h diag(Delta) per time step. */
+int orc_dirichlet_rhs(const double *area, const double *K, int64_t E,
+                      double T, int32_t n_steps, int32_t nrhs,
+                      const double *g, double *f)
+{
+    if (orc_toeplitz_matvec(K, E, n_steps, nrhs, g, f))
+        return -1;
+    double h = T / n_steps;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k)
+            for (int64_t l = 0; l < E; ++l) {
+                int64_t i = ((int64_t)r * n_steps + k) * E + l;
+                f[i] += 0.5 * h * area[l] * g[i];
+            }
+    return 0;
+}
+
+/* Block forward substitution (marching in time) for the lower-triangular
+ * block-Toeplitz system of eq. V_mat:
+ *   V^0 w^k = f^k - sum_{d=1}^{k} V^d w^{k-d},
+ * with a plain dense Cholesky factorisation V^0 = L L^T.  Returns -5 if V^0
+ * is not numerically positive definite. */
+int orc_dirichlet_solve(const double *V, int64_t E, int32_t n_steps,
+                        int32_t nrhs, const double *f, double *w)
+{
+    if (E < 1 || n_steps < 1 || nrhs < 1)
+        return -1;
+    double *L = malloc(sizeof(double) * E * E);
+    double *rhs = malloc(sizeof(double) * E);
+    int rc = 0;
+    memcpy(L, V, sizeof(double) * E * E);
+    for (int64_t c = 0; c < E && rc == 0; ++c) {
+        double s = L[c * E + c];
+        for (int64_t k = 0; k < c; ++k)
+            s -= L[c * E + k] * L[c * E + k];
+        if (!(s > 0.0)) {
+            rc = -5;
+            break;
+        }
+        double lcc = sqrt(s);
+        L[c * E + c] = lcc;
+        for (int64_t i = c + 1; i < E; ++i) {
+            double t = L[i * E + c];
+            for (int64_t k = 0; k < c; ++k)
+                t -= L[i * E + k] * L[c * E + k];
+            L[i * E + c] = t / lcc;
+        }
+    }
+    for (int r = 0; r < nrhs && rc == 0; ++r)
+        for (int k = 0; k < n_steps; ++k) {
+            const double *fk = f + ((int64_t)r * n_steps + k) * E;
+            double *wk = w + ((int64_t)r * n_steps + k) * E;
+            for (int64_t l = 0; l < E; ++l) {
+                double acc = fk[l];
+                for (int d = 1; d <= k; ++d) {
+                    const double *Vrow = V + ((int64_t)d * E + l) * E;
+                    const double *wv = w + ((int64_t)r * n_steps + (k - d)) * E;
+                    for (int64_t j = 0; j < E; ++j)
+                        acc -= Vrow[j] * wv[j];
+                }
+                rhs[l] = acc;
+            }
+            for (int64_t i = 0; i < E; ++i) { /* L z = rhs */
+                double t = rhs[i];
+                for (int64_t k2 = 0; k2 < i; ++k2)
+                    t -= L[i * E + k2] * rhs[k2];
+                rhs[i] = t / L[i * E + i];
+            }
+            for (int64_t i = E - 1; i >= 0; --i) { /* L^T w = z */
+                double t = rhs[i];
+                for (int64_t k2 = i + 1; k2 < E; ++k2)
+                    t -= L[k2 * E + i] * wk[k2];
+                wk[i] = t / L[i * E + i];
+            }
+        }
+    free(L);
+    free(rhs);
+    return rc;
+}
+
+/* err2 = sum_r || w_r - w_{h,r} ||^2_{L2(Sigma_h)}, ref2 = sum_r || w_r ||^2,
+ * both by the same product rule as the projection (Sec. 6.1, error norm). */
+int orc_neumann_error(const double *nodes, int64_t n_nodes,
+                      const int32_t *tris, int64_t E, double alpha, double T,
+                      int32_t n_steps, const double *sources, int32_t n_src,
+                      int32_t nrhs, const double *w, int32_t q_space,
+                      int32_t n_time, double *err2, double *ref2)
+{
+    if (E < 1 || n_steps < 1 || nrhs < 1 || q_space < 1 || q_space > 32 ||
+        n_time < 1 || n_time > 64)
+        return -1;
+    int nq = q_space * q_space;
+    double *s1 = malloc(sizeof(double) * nq), *s2 = malloc(sizeof(double) * nq);
+    double *sw = malloc(sizeof(double) * nq), tx[64], tw[64];
+    double *area = malloc(sizeof(double) * E), *normal = malloc(sizeof(double) * 3 * E);
+    int rc = -1;
+    if (orc_triangle_rule(q_space, s1, s2, sw) || orc_gauss_legendre01(n_time, tx, tw) ||
+        orc_triangle_geometry(nodes, n_nodes, tris, E, area, normal))
+        goto done;
+    double h = T / n_steps, e2 = 0.0, r2 = 0.0;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k)
+            for (int64_t j = 0; j < E; ++j) {
+                const int32_t *t3 = tris + 3 * j;
+                double wh = w[((int64_t)r * n_steps + k) * E + j];
+                double ae = 0.0, ar = 0.0;
+                for (int a = 0; a < nq; ++a) {
+                    double x[3];
+                    chi_plain(nodes + 3 * t3[0], nodes + 3 * t3[1], nodes + 3 * t3[2],
+                              s1[a], s2[a], x);
+                    for (int b = 0; b < n_time; ++b) {
+                        double we = neumann_datum(sources + (int64_t)r * n_src * 5, n_src,
+                                                  alpha, x, normal + 3 * j, (k + tx[b]) * h);
+                        ae += sw[a] * tw[b] * (we - wh) * (we - wh);
+                        ar += sw[a] * tw[b] * we * we;
+                    }
+                }
+                e2 += 2.0 * area[j] * h * ae;
+                r2 += 2.0 * area[j] * h * ar;
+            }
+    *err2 = e2;
+    *ref2 = r2;
+    rc = 0;
+done:
+    free(s1);
+    free(s2);
+    free(sw);
+    free(area);
+    free(normal);
+    return rc;
+}
