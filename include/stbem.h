@@ -1,0 +1,198 @@
+/*
+ * stbem.h -- C ABI of the GB300 space-time boundary element library for the
+ * 3D heat equation (Zapletal, Watschinger, Of, Merta: "Semi-analytic
+ * integration for a parallel space-time boundary element method modeling the
+ * heat equation").
+ *
+ * The library assembles the blocks V^d and K^d of the block lower-triangular
+ * Toeplitz Galerkin matrices V_h and K_h (Sec. 3.1, eq. V_mat, eq. V_blocks;
+ * Sec. 3.2, eq. K_mat) for piecewise-constant test and trial functions on a
+ * tensor-product space-time mesh with uniform steps, applies the
+ * block-Toeplitz matrix-vector product, builds the Dirichlet right-hand side
+ * (1/2 M_h + K_h) g and solves V_h w = (1/2 M_h + K_h) g (Sec. 3.4) by block
+ * forward substitution in time.  Every computation runs in the library's own
+ * sm_103a CUDA kernels.
+ *
+ * Conventions
+ *   - Host arrays (nodes, tris, sources given to stb_mesh_create /
+ *     stb_project_dirichlet) are read during the call and not retained.
+ *   - Device arrays are caller-owned, allocated by the caller (cudaMalloc,
+ *     PyTorch, ...) on the current device; the library never frees them.
+ *   - Scratch memory is caller-owned too: query its size with the matching
+ *     *_workspace_size call and pass a device buffer of at least that many
+ *     bytes, 256-byte aligned.
+ *   - Calls are asynchronous on the given stream unless stated otherwise;
+ *     argument and mesh errors are returned immediately.  Device-side errors
+ *     (a non-positive pivot, an exhausted bounded wait) are written to a status
+ *     word in the workspace and returned by the calls that synchronise
+ *     (stb_dirichlet_solve) or by stb_workspace_status.
+ *   - No C++ exception crosses this interface.  Functions are thread-safe
+ *     except that calls sharing one workspace must not overlap on the GPU.
+ *   - Mesh: nodes [n_nodes][3] (double), tris [E][3] (int32), vertex order
+ *     counter-clockwise seen from outside (outward normals).  The surface must
+ *     be a closed, conforming, consistently oriented 2-manifold of
+ *     non-degenerate flat triangles.
+ *   - Time grid t_i = i h, h = T / n_steps.  Block d = 0..n_steps-1 of a
+ *     Toeplitz matrix is the E x E row-major array A[d][l][j] (row l = test
+ *     triangle, column j = trial triangle); a whole matrix is
+ *     A[n_steps][E][E], contiguous.
+ *   - Space-time vectors are laid out [nrhs][n_steps][E] (time step k holds
+ *     the coefficients of interval (t_k, t_{k+1})).
+ */
+#ifndef STBEM_H
+#define STBEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *stb_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef int32_t stb_status;
+#define STB_OK 0
+#define STB_ERR_INVALID_ARG (-1)   /* a pointer, size or parameter is invalid   */
+#define STB_ERR_BAD_MESH (-2)      /* not a closed oriented manifold / degenerate */
+#define STB_ERR_NOMEM (-3)         /* a library allocation failed                */
+#define STB_ERR_CUDA (-4)          /* a CUDA runtime call failed                 */
+#define STB_ERR_NOT_SPD (-5)       /* V^0 has a non-positive pivot               */
+#define STB_ERR_NOT_CONVERGED (-6) /* iterative refinement did not converge      */
+#define STB_ERR_TIMEOUT (-7)       /* a bounded device-side wait expired         */
+#define STB_ERR_WORKSPACE (-8)     /* workspace missing, too small or misaligned */
+
+/* Arithmetic of the assembly. */
+#define STB_PREC_FP64 0  /* every quadrature point and time level in FP64 (the paper's) */
+#define STB_PREC_MIXED 1 /* reserved: mixed-precision assembly                            */
+
+/* Element type of V/K storage. */
+#define STB_STORE_F64 0
+#define STB_STORE_F32 1
+
+typedef struct stb_params {
+    double alpha;          /* heat capacity constant alpha > 0 (eq. heat_eq)           */
+    double T;              /* end time T > 0                                            */
+    int32_t n_steps;       /* E_t >= 1 uniform time steps                               */
+    int32_t quad_regular;  /* q: q x q conical product rule per triangle (eq. st), 1..16 */
+    int32_t quad_singular; /* m: m^4 Gauss points per sub-domain (eq. ss), 1..12         */
+    int32_t precision;     /* STB_PREC_*                                                */
+    int32_t storage;       /* STB_STORE_*                                               */
+    int32_t reserved;      /* must be 0                                                 */
+} stb_params;
+
+/* Default parameters (q = 3, m = 4, FP64, F64 storage) for given alpha, T, E_t. */
+stb_params stb_default_params(double alpha, double T, int32_t n_steps);
+
+const char *stb_status_string(stb_status status);
+/* Message of the last error raised on the calling thread ("" if none). */
+const char *stb_last_error_message(void);
+/* Number of kernels this library has launched in the process so far. */
+int64_t stb_launch_count(void);
+
+/* ---- mesh (Sec. 3: the spatial mesh Gamma_h of flat triangles) ---------------
+ * Validates the surface, copies nodes and tris to device memory owned by the
+ * mesh object (O(E) bytes on the current device) and counts the touching
+ * triangle pairs.  Synchronous.  Errors: INVALID_ARG, BAD_MESH, NOMEM, CUDA. */
+typedef struct stb_mesh stb_mesh;
+stb_status stb_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tris,
+                           int64_t n_tris, stb_mesh **out);
+void stb_mesh_destroy(stb_mesh *mesh);
+/* Counts: nodes, triangles, and unordered touching pairs (a <= b sharing at
+ * least one vertex, the identical pairs included). */
+stb_status stb_mesh_info(const stb_mesh *mesh, int64_t *n_nodes, int64_t *n_tris,
+                         int64_t *n_touching_pairs);
+
+/* ---- assembly of V_h and K_h (Sec. 3.1-3.2, Sec. 5) ------------------------------
+ * Writes all blocks V^d and K^d, d = 0..n_steps-1, each E x E, in the layout
+ * above (element type per params->storage).  Every entry is
+ *   V^d[l][j] = int_{gamma_l} int_{gamma_j} V^d(x - y) ds_y ds_x
+ * with V^d(r) from eq. vd (d >= 1) and eq. V0 (d = 0), K^d likewise from
+ * eq. K_d / eq. K0, computed as second differences of the time-level sums
+ * S_i = int int G^{dtau dt}(x - y, i h) (each level evaluated once, Table
+ * deltad); separated pairs use the regular rule (eq. quad_reg, eq. st),
+ * pairs sharing a vertex, an edge or the whole triangle the regularised rules
+ * (eq. quad_duffy, eq. ss) at every time level.  K may be NULL (V only).
+ * The kernels compute triangle geometry and the pair classification in the
+ * workspace first.  Asynchronous on `stream`. */
+stb_status stb_assemble_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                       size_t *bytes);
+stb_status stb_assemble(const stb_mesh *mesh, const stb_params *params, void *V, void *K,
+                        void *workspace, size_t workspace_bytes, stb_stream stream);
+
+/* ---- Dirichlet data (Sec. 3.4, Sec. 6.1) --------------------------------------
+ * sources: HOST array [nrhs][n_src][5] of (y1, y2, y3, t0, weight); right-hand
+ * side r has the Dirichlet datum g_r(x,t) = sum_s weight_s G_alpha(x - y_s, t - t0_s)
+ * (the exterior-source exact solution of Sec. 6.1).  g (device, [nrhs][n_steps][E])
+ * receives its L2 projection into piecewise constants (element means) by a
+ * q_space x q_space conical rule and n_time Gauss points per step. */
+stb_status stb_project_workspace_size(const stb_mesh *mesh, int32_t nrhs, int32_t n_src,
+                                      int32_t q_space, int32_t n_time, size_t *bytes);
+stb_status stb_project_dirichlet(const stb_mesh *mesh, const stb_params *params,
+                                 const double *sources, int32_t nrhs, int32_t n_src,
+                                 int32_t q_space, int32_t n_time, double *g, void *workspace,
+                                 size_t workspace_bytes, stb_stream stream);
+
+/* ---- block-Toeplitz matrix-vector product (eq. V_mat) ---------------------------
+ *   y_r^k = beta y_r^k + sum_{d=0}^{k} A^d x_r^{k-d},  k = 0..n_steps-1,
+ * A: device [n_steps][E][E] of `a_storage`; x, y: device FP64
+ * [nrhs][n_steps][E], not overlapping.  FP64 arithmetic. */
+stb_status stb_toeplitz_workspace_size(int64_t E, int32_t n_steps, int32_t nrhs, size_t *bytes);
+stb_status stb_toeplitz_matvec(const void *A, int32_t a_storage, int64_t E, int32_t n_steps,
+                               int32_t nrhs, const double *x, double beta, double *y,
+                               void *workspace, size_t workspace_bytes, stb_stream stream);
+
+/* ---- right-hand side f = (1/2 M_h + K_h) g, M_h = h blockdiag(diag(Delta_l)) -- */
+stb_status stb_rhs_workspace_size(const stb_mesh *mesh, const stb_params *params, int32_t nrhs,
+                                  size_t *bytes);
+stb_status stb_dirichlet_rhs(const stb_mesh *mesh, const stb_params *params, const void *K,
+                             const double *g, int32_t nrhs, double *f, void *workspace,
+                             size_t workspace_bytes, stb_stream stream);
+
+/* ---- forward-substitution solve of V_h w = f (eq. V_mat) --------------------------
+ * Factorises V^0 = L L^T (blocked Cholesky of its lower triangle; V^0 is
+ * symmetric positive definite), inverts L, then marches in time:
+ *   w^k = (V^0)^{-1} (f^k - sum_{d=1}^{k} V^d w^{k-d}).
+ * V: device [n_steps][E][E] (params->storage), f, w: device FP64
+ * [nrhs][n_steps][E].  Synchronises `stream` at the end and returns
+ * STB_ERR_NOT_SPD if a pivot was not positive. */
+stb_status stb_solve_workspace_size(const stb_mesh *mesh, const stb_params *params, int32_t nrhs,
+                                    size_t *bytes);
+stb_status stb_dirichlet_solve(const stb_mesh *mesh, const stb_params *params, const void *V,
+                               const double *f, int32_t nrhs, double *w, void *workspace,
+                               size_t workspace_bytes, stb_stream stream);
+
+/* ---- error of the Neumann datum (Sec. 6.1, relative L2(Sigma_h) error) -------------
+ * out[0] = sum_r || w_r - w_{h,r} ||^2_{L2(Sigma_h)},  out[1] = sum_r || w_r ||^2
+ * for the exact w_r = alpha du_r/dn of the sources (HOST array as above),
+ * by the same product rule as the projection.  out: device FP64 [2]. */
+stb_status stb_error_workspace_size(const stb_mesh *mesh, const stb_params *params, int32_t nrhs,
+                                    int32_t n_src, int32_t q_space, int32_t n_time, size_t *bytes);
+stb_status stb_neumann_error(const stb_mesh *mesh, const stb_params *params,
+                             const double *sources, int32_t nrhs, int32_t n_src,
+                             const double *w, int32_t q_space, int32_t n_time, double *out,
+                             void *workspace, size_t workspace_bytes, stb_stream stream);
+
+/* Device status word of a workspace (STB_OK or the first device-side error);
+ * synchronises `stream`. */
+stb_status stb_workspace_status(const void *workspace, stb_stream stream);
+
+/* ---- kernel tracing (no counterpart in the paper; timing of the kernels) ------
+ * While enabled, every kernel the library launches is bracketed by two CUDA
+ * events recorded on its launch stream.  stb_trace_read synchronises those
+ * events and returns, per kernel name, the number of launches and the summed
+ * device time since the last reset.  Process-wide; not for concurrent use from
+ * several threads while enabled. */
+typedef struct stb_trace_entry {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} stb_trace_entry;
+stb_status stb_trace_enable(int32_t on);
+stb_status stb_trace_reset(void);
+stb_status stb_trace_read(stb_trace_entry *out, int32_t max_entries, int32_t *n_entries);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STBEM_H */

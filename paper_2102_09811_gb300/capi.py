@@ -1,0 +1,262 @@
+"""Thin ctypes binding of the C ABI in include/stbem.h.
+
+Functions carry the C names and only marshal arguments: device buffers are
+torch CUDA tensors (their data_ptr is passed), host arrays are numpy arrays,
+streams are torch.cuda.Stream objects (or None for the current stream).
+Every computation runs in the CUDA library; if the compiled library is missing
+this module raises instead of falling back to anything else.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+STB_OK = 0
+STB_PREC_FP64, STB_PREC_MIXED = 0, 1
+STB_STORE_F64, STB_STORE_F32 = 0, 1
+
+_lib = None
+
+
+class stb_params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("T", ctypes.c_double), ("n_steps", ctypes.c_int32),
+                ("quad_regular", ctypes.c_int32), ("quad_singular", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class StbError(RuntimeError):
+    def __init__(self, code, where):
+        lib = _library()
+        msg = lib.stb_last_error_message().decode()
+        super().__init__("%s: %s (%d): %s" % (where, lib.stb_status_string(code).decode(), code, msg))
+        self.code = code
+
+
+_P, _I32, _I64, _D, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+_PSZ = ctypes.POINTER(ctypes.c_size_t)
+_PAR = ctypes.POINTER(stb_params)
+
+_SIGS = {
+    "stb_default_params": (stb_params, [_D, _D, _I32]),
+    "stb_status_string": (ctypes.c_char_p, [_I32]),
+    "stb_last_error_message": (ctypes.c_char_p, []),
+    "stb_launch_count": (_I64, []),
+    "stb_mesh_create": (_I32, [_P, _I64, _P, _I64, ctypes.POINTER(_P)]),
+    "stb_mesh_destroy": (None, [_P]),
+    "stb_mesh_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "stb_assemble_workspace_size": (_I32, [_P, _PAR, _PSZ]),
+    "stb_assemble": (_I32, [_P, _PAR, _P, _P, _P, _SZ, _P]),
+    "stb_project_workspace_size": (_I32, [_P, _I32, _I32, _I32, _I32, _PSZ]),
+    "stb_project_dirichlet": (_I32, [_P, _PAR, _P, _I32, _I32, _I32, _I32, _P, _P, _SZ, _P]),
+    "stb_toeplitz_workspace_size": (_I32, [_I64, _I32, _I32, _PSZ]),
+    "stb_toeplitz_matvec": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _D, _P, _P, _SZ, _P]),
+    "stb_rhs_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
+    "stb_dirichlet_rhs": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
+    "stb_solve_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
+    "stb_dirichlet_solve": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
+    "stb_error_workspace_size": (_I32, [_P, _PAR, _I32, _I32, _I32, _I32, _PSZ]),
+    "stb_neumann_error": (_I32, [_P, _PAR, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _SZ, _P]),
+    "stb_workspace_status": (_I32, [_P, _P]),
+    "stb_trace_enable": (_I32, [_I32]),
+    "stb_trace_reset": (_I32, []),
+    "stb_trace_read": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
+}
+
+
+class stb_trace_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+def library_path():
+    return _build.LIB
+
+
+def _library():
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError("CUDA library %s is not built; run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code, where):
+    if code != STB_OK:
+        raise StbError(code, where)
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _host_f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---- small helpers ------------------------------------------------------------
+def stb_default_params(alpha, T, n_steps, quad_regular=3, quad_singular=4, precision=STB_PREC_FP64,
+                       storage=STB_STORE_F64):
+    p = _library().stb_default_params(alpha, T, n_steps)
+    p.quad_regular, p.quad_singular = quad_regular, quad_singular
+    p.precision, p.storage = precision, storage
+    return p
+
+
+def stb_launch_count():
+    return int(_library().stb_launch_count())
+
+
+class Mesh:
+    """Owns an stb_mesh handle."""
+
+    def __init__(self, nodes, tris):
+        nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        tris = np.ascontiguousarray(tris, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(_library().stb_mesh_create(nodes.ctypes.data_as(_P), nodes.shape[0],
+                                          tris.ctypes.data_as(_P), tris.shape[0], ctypes.byref(h)),
+               "stb_mesh_create")
+        self.handle = h
+        n, e, t = _I64(), _I64(), _I64()
+        _check(_library().stb_mesh_info(h, ctypes.byref(n), ctypes.byref(e), ctypes.byref(t)),
+               "stb_mesh_info")
+        self.n_nodes, self.n_tris, self.n_touching = n.value, e.value, t.value
+
+    def close(self):
+        if self.handle:
+            _library().stb_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stb_mesh_create(nodes, tris):
+    return Mesh(nodes, tris)
+
+
+def _size(fn, *args):
+    n = _SZ()
+    _check(fn(*args, ctypes.byref(n)), fn.__name__)
+    return n.value
+
+
+def stb_assemble_workspace_size(mesh, params):
+    return _size(_library().stb_assemble_workspace_size, mesh.handle, ctypes.byref(params))
+
+
+def stb_assemble(mesh, params, V, K, workspace, stream=None):
+    _check(_library().stb_assemble(mesh.handle, ctypes.byref(params), _ptr(V), _ptr(K),
+                                   _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                   _stream(stream)), "stb_assemble")
+
+
+def stb_project_workspace_size(mesh, nrhs, n_src, q_space=8, n_time=16):
+    return _size(_library().stb_project_workspace_size, mesh.handle, nrhs, n_src, q_space, n_time)
+
+
+def stb_project_dirichlet(mesh, params, sources, g, workspace, q_space=8, n_time=16, stream=None):
+    src, sp = _host_f64(sources)
+    nrhs, n_src = src.shape[0], src.shape[1]
+    _check(_library().stb_project_dirichlet(mesh.handle, ctypes.byref(params), sp, nrhs, n_src,
+                                            q_space, n_time, _ptr(g), _ptr(workspace),
+                                            workspace.numel() * workspace.element_size(),
+                                            _stream(stream)), "stb_project_dirichlet")
+
+
+def stb_toeplitz_workspace_size(E, n_steps, nrhs):
+    return _size(_library().stb_toeplitz_workspace_size, E, n_steps, nrhs)
+
+
+def stb_toeplitz_matvec(A, a_storage, E, n_steps, nrhs, x, beta, y, workspace, stream=None):
+    _check(_library().stb_toeplitz_matvec(_ptr(A), a_storage, E, n_steps, nrhs, _ptr(x), beta, _ptr(y),
+                                          _ptr(workspace),
+                                          workspace.numel() * workspace.element_size(),
+                                          _stream(stream)), "stb_toeplitz_matvec")
+
+
+def stb_rhs_workspace_size(mesh, params, nrhs):
+    return _size(_library().stb_rhs_workspace_size, mesh.handle, ctypes.byref(params), nrhs)
+
+
+def stb_dirichlet_rhs(mesh, params, K, g, nrhs, f, workspace, stream=None):
+    _check(_library().stb_dirichlet_rhs(mesh.handle, ctypes.byref(params), _ptr(K), _ptr(g), nrhs,
+                                        _ptr(f), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(),
+                                        _stream(stream)), "stb_dirichlet_rhs")
+
+
+def stb_solve_workspace_size(mesh, params, nrhs):
+    return _size(_library().stb_solve_workspace_size, mesh.handle, ctypes.byref(params), nrhs)
+
+
+def stb_dirichlet_solve(mesh, params, V, f, nrhs, w, workspace, stream=None):
+    _check(_library().stb_dirichlet_solve(mesh.handle, ctypes.byref(params), _ptr(V), _ptr(f), nrhs,
+                                          _ptr(w), _ptr(workspace),
+                                          workspace.numel() * workspace.element_size(),
+                                          _stream(stream)), "stb_dirichlet_solve")
+
+
+def stb_error_workspace_size(mesh, params, nrhs, n_src, q_space=8, n_time=16):
+    return _size(_library().stb_error_workspace_size, mesh.handle, ctypes.byref(params), nrhs, n_src,
+                 q_space, n_time)
+
+
+def stb_neumann_error(mesh, params, sources, w, out, workspace, q_space=8, n_time=16, stream=None):
+    src, sp = _host_f64(sources)
+    _check(_library().stb_neumann_error(mesh.handle, ctypes.byref(params), sp, src.shape[0],
+                                        src.shape[1], _ptr(w), q_space, n_time, _ptr(out),
+                                        _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(),
+                                        _stream(stream)), "stb_neumann_error")
+
+
+def stb_workspace_status(workspace, stream=None):
+    _check(_library().stb_workspace_status(_ptr(workspace), _stream(stream)), "stb_workspace_status")
+
+
+def stb_trace_enable(on=True):
+    _check(_library().stb_trace_enable(1 if on else 0), "stb_trace_enable")
+
+
+def stb_trace_reset():
+    _check(_library().stb_trace_reset(), "stb_trace_reset")
+
+
+def stb_trace_read():
+    """{kernel name: (launches, total device ms)} since the last reset."""
+    n = _I32()
+    _check(_library().stb_trace_read(None, 0, ctypes.byref(n)), "stb_trace_read")
+    buf = (stb_trace_entry * max(n.value, 1))()
+    _check(_library().stb_trace_read(ctypes.cast(buf, _P), n.value, ctypes.byref(n)),
+           "stb_trace_read")
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+            for i in range(n.value)}

@@ -1,0 +1,665 @@
+// stb_assemble.cu -- triangle geometry, pair classification and the FP64
+// assembly of the Toeplitz blocks V^d, K^d (Sec. 3.1-3.2, Sec. 5).
+//
+// Work decomposition (GB300):
+//  * separated pairs: one thread per (test l, trial j) pair, a CTA covers 128
+//    consecutive trial triangles of one test triangle, so every store of a
+//    block entry V^d[l][j] is coalesced over j.  The time levels i_t = 1..E_t
+//    are processed in chunks of CH levels whose spatial sums stay in
+//    registers; the pair geometry (rho, 1/rho, r.n_y/rho) of a quadrature point
+//    is recomputed once per chunk, so one heat-kernel evaluation costs one
+//    erf + one exp shared by V and K.  After a chunk the second differences of
+//    eq. vd / eq. V0 (and eq. K_d / eq. K0) are formed from a sliding window of
+//    three level sums (Table deltad read as a gather: block d needs levels
+//    d-1, d, d+1), so no atomics and no re-reads are needed.
+//  * touching pairs (shared vertex / edge / identical): one CTA of 128 threads
+//    per unordered pair a <= b; the threads split the m^4 x sub-domain points
+//    of the regularised rule, reduce each level chunk through shuffles and
+//    shared memory, and one thread writes V^d and K^d of both (a,b) and (b,a):
+//    the rule is built once for the ordered pair, so V^d is symmetric.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "stb_internal.h"
+
+namespace stb {
+
+// --------------------------------------------------------------- geometry ---
+__global__ void k_geometry(const double *__restrict__ nodes, const int32_t *__restrict__ tris,
+                           int64_t E, double *__restrict__ geo) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    double v[9];
+    for (int k = 0; k < 3; ++k) {
+        int32_t i = tris[3 * e + k];
+        v[3 * k] = nodes[3 * i];
+        v[3 * k + 1] = nodes[3 * i + 1];
+        v[3 * k + 2] = nodes[3 * i + 2];
+    }
+    double u0 = v[3] - v[0], u1 = v[4] - v[1], u2 = v[5] - v[2];
+    double w0 = v[6] - v[0], w1 = v[7] - v[1], w2 = v[8] - v[2];
+    double n0 = u1 * w2 - u2 * w1, n1 = u2 * w0 - u0 * w2, n2 = u0 * w1 - u1 * w0;
+    double len = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    double *g = geo + e * GEO_STRIDE;
+    for (int k = 0; k < 9; ++k) g[k] = v[k];
+    g[GEO_N] = n0 / len;
+    g[GEO_N + 1] = n1 / len;
+    g[GEO_N + 2] = n2 / len;
+    g[GEO_AREA] = 0.5 * len;
+}
+
+stb_status launch_geometry(const Mesh &m, double *geo, cudaStream_t s) {
+    int64_t E = m.n_tris;
+    count_launch(s);
+    k_geometry<<<(unsigned)((E + 255) / 256), 256, 0, s>>>(m.d_nodes, m.d_tris, E, geo);
+    return check_launch("k_geometry");
+}
+
+// ---------------------------------------------------------- classification ---
+// Local vertex orders of a touching pair (the same reading as the regularised
+// rules assume): shared vertices first and in the same order in both
+// triangles; an edge pair rotates a so that the shared edge is (v0, v1) in a's
+// cyclic order; a vertex pair rotates both so the shared vertex is v0.
+__device__ __forceinline__ void classify_pair(const int32_t ta[3], const int32_t tb[3], int &cls,
+                                              int &perm) {
+    int sa[3], n = 0;
+    for (int i = 0; i < 3; ++i) {
+        sa[i] = (ta[i] == tb[0]) | (ta[i] == tb[1]) | (ta[i] == tb[2]);
+        n += sa[i];
+    }
+    int oa[3] = {0, 1, 2}, ob[3] = {0, 1, 2};
+    if (n == 3) {
+        cls = PAIR_IDENTICAL;
+    } else if (n == 2) {
+        cls = PAIR_EDGE;
+        int k = (sa[0] && sa[1]) ? 0 : (sa[1] && sa[2]) ? 1 : 2;
+        for (int i = 0; i < 3; ++i) oa[i] = (k + i) % 3;
+        int used = 0;
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j)
+                if (tb[j] == ta[oa[i]]) {
+                    ob[i] = j;
+                    used |= 1 << j;
+                }
+        ob[2] = (used & 1) == 0 ? 0 : (used & 2) == 0 ? 1 : 2;
+    } else if (n == 1) {
+        cls = PAIR_VERTEX;
+        int ka = sa[0] ? 0 : sa[1] ? 1 : 2;
+        int kb = tb[0] == ta[ka] ? 0 : tb[1] == ta[ka] ? 1 : 2;
+        for (int i = 0; i < 3; ++i) {
+            oa[i] = (ka + i) % 3;
+            ob[i] = (kb + i) % 3;
+        }
+    } else {
+        cls = PAIR_DISJOINT;
+    }
+    perm = oa[0] | (oa[1] << 2) | (oa[2] << 4) | (ob[0] << 6) | (ob[1] << 8) | (ob[2] << 10);
+}
+
+__device__ __forceinline__ bool touches(const int32_t ta[3], const int32_t tb[3]) {
+    bool t = false;
+    for (int i = 0; i < 3; ++i) t |= (ta[i] == tb[0]) | (ta[i] == tb[1]) | (ta[i] == tb[2]);
+    return t;
+}
+
+// One warp per row a: count (pass 0) or emit (pass 1) the pairs (a, b >= a)
+// that share a vertex, in increasing b.
+__global__ void k_classify(const int32_t *__restrict__ tris, int64_t E, int pass,
+                           int32_t *__restrict__ row_count, const int32_t *__restrict__ row_off,
+                           TouchPair *__restrict__ out, int64_t capacity) {
+    int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (a >= E) return;
+    int32_t ta[3] = {tris[3 * a], tris[3 * a + 1], tris[3 * a + 2]};
+    int32_t cnt = 0;
+    int32_t base = pass ? row_off[a] : 0;
+    for (int64_t b0 = a; b0 < E; b0 += 32) {
+        int64_t b = b0 + lane;
+        bool t = false;
+        int32_t tb[3];
+        if (b < E) {
+            tb[0] = tris[3 * b];
+            tb[1] = tris[3 * b + 1];
+            tb[2] = tris[3 * b + 2];
+            t = touches(ta, tb);
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, t);
+        if (pass && t) {
+            int cls, perm;
+            classify_pair(ta, tb, cls, perm);
+            int pos = base + cnt + __popc(bal & ((1u << lane) - 1u));
+            if (pos < capacity) out[pos] = TouchPair{(int32_t)a, (int32_t)b, cls, perm};
+        }
+        cnt += __popc(bal);
+    }
+    if (!pass && lane == 0) row_count[a] = cnt;
+}
+
+// Exclusive scan of the row counts (one CTA); checks the total against the
+// host's count of touching pairs.
+__global__ void k_scan_rows(const int32_t *__restrict__ cnt, int64_t E, int32_t *__restrict__ off,
+                            int64_t expect_total, int32_t *__restrict__ status) {
+    __shared__ int64_t part[1024];
+    int t = threadIdx.x, nt = blockDim.x;
+    int64_t chunk = (E + nt - 1) / nt, lo = t * chunk, hi = min(E, lo + chunk);
+    int64_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += cnt[i];
+    part[t] = s;
+    __syncthreads();
+    for (int d = 1; d < nt; d <<= 1) {
+        int64_t v = t >= d ? part[t - d] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = part[t] - s;
+    for (int64_t i = lo; i < hi; ++i) {
+        off[i] = (int32_t)run;
+        run += cnt[i];
+    }
+    if (t == nt - 1) {
+        off[E] = (int32_t)part[t];
+        if (part[t] != expect_total) atomicCAS(status, 0, STB_ERR_BAD_MESH);
+    }
+}
+
+stb_status launch_classify(const Mesh &m, int32_t *row_count, int32_t *row_off, TouchPair *pairs,
+                           int32_t *status, cudaStream_t s) {
+    int64_t E = m.n_tris;
+    unsigned blocks = (unsigned)((E * 32 + 255) / 256);
+    count_launch(s);
+    k_classify<<<blocks, 256, 0, s>>>(m.d_tris, E, 0, row_count, row_off, pairs, m.n_touch);
+    stb_status st = check_launch("k_classify(count)");
+    if (st) return st;
+    count_launch(s);
+    k_scan_rows<<<1, 1024, 0, s>>>(row_count, E, row_off, m.n_touch, status);
+    if ((st = check_launch("k_scan_rows"))) return st;
+    count_launch(s);
+    k_classify<<<blocks, 256, 0, s>>>(m.d_tris, E, 1, row_count, row_off, pairs, m.n_touch);
+    return check_launch("k_classify(fill)");
+}
+
+// ------------------------------------------------------- kernel evaluation ---
+// Per-level constants (level i >= 1, delta = i h) of the closed forms
+//   G^{dtau dt}(r, delta)      = A rho erf(x) + B_i/rho erf(x) + C_i exp(-x^2)   (eq. G_dtau_dt)
+//   alpha dG^{dtau dt}/dn_y    = (r.n/rho) [ (D_i/rho^2 - A') erf(x) - E_i/rho exp(-x^2) ]  (eq. dG)
+// with x = rho c_i, c_i = 1/(2 sqrt(alpha delta)), A = 1/(8 pi alpha^2),
+// B_i = delta/(4 pi alpha), C_i = sqrt(delta)/(4 pi sqrt(pi alpha^3)),
+// A' = 1/(8 pi alpha), D_i = delta/(4 pi), E_i = sqrt(delta)/(4 pi sqrt(pi alpha)).
+// For x < 1/2 the bracket of eq. dG cancels; it is evaluated as
+//   alpha dG^{dtau dt}/dn_y = -(r.n/rho) psi(x) / (4 pi alpha),
+//   psi(x) = (2/sqrt(pi)) sum_m (-1)^m x^{2m+1} / (m! (2m+1)(2m+3)).
+// Level 0 uses the delta -> 0 limits of Sec. 3.1-3.2: A rho and -A' r.n/rho,
+// and the delta = 0 integrands 1/(4 pi alpha rho) and r.n/(4 pi rho^3).
+enum { LV_C = 0, LV_B, LV_CC, LV_D, LV_E, LV_STRIDE = 8 };
+struct Globals {
+    double A, Ap, F, Fs, h;  // F = 1/(4 pi alpha), Fs = 1/(4 pi)
+};
+
+__constant__ double c_psi[12];  // (2/sqrt(pi)) (-1)^m / (m! (2m+1)(2m+3))
+
+static void upload_psi_coeffs(cudaStream_t s) {
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && done[dev]) return;
+    double c[12];
+    double fact = 1.0;
+    for (int m = 0; m < 12; ++m) {
+        if (m > 0) fact *= m;
+        c[m] = (m % 2 ? -1.0 : 1.0) * 1.1283791670955126 / (fact * (2.0 * m + 1.0) * (2.0 * m + 3.0));
+    }
+    cudaMemcpyToSymbol(c_psi, c, sizeof c);
+    if (dev < 64) done[dev] = true;
+}
+
+__device__ __forceinline__ double psi_series(double x) {
+    double x2 = x * x, p = c_psi[11];
+#pragma unroll
+    for (int m = 10; m >= 0; --m) p = fma(p, x2, c_psi[m]);
+    return p * x;
+}
+
+// V and K-factor at one level: V = G^{dtau dt}, Kf such that
+// alpha dG^{dtau dt}/dn_y = (r.n/rho) * Kf.
+__device__ __forceinline__ void eval_level(double rho, double irho, const double *lv,
+                                           const Globals &g, double &v, double &kf) {
+    double x = rho * lv[LV_C];
+    double f = erf(x);
+    double e = exp(-x * x);
+    v = fma(fma(g.A, rho, lv[LV_B] * irho), f, lv[LV_CC] * e);
+    if (x >= 0.5) {
+        kf = fma(fma(lv[LV_D], irho * irho, -g.Ap), f, -lv[LV_E] * irho * e);
+    } else {
+        kf = -g.F * psi_series(x);
+    }
+}
+
+template <class T> __device__ __forceinline__ void store(T *p, double v);
+template <> __device__ __forceinline__ void store<double>(double *p, double v) { *p = v; }
+template <> __device__ __forceinline__ void store<float>(float *p, double v) { *p = (float)v; }
+
+// ------------------------------------------------- separated pairs, FP64 ---
+constexpr int REG_THREADS = 128;
+constexpr int MAX_RULE = 256;       // q <= 16
+constexpr int MAX_LEVELS = 2049;    // n_steps <= 2048 (level table in smem)
+
+template <int CH, class OutT>
+__global__ void __launch_bounds__(REG_THREADS)
+k_regular_f64(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E,
+              const double *__restrict__ rule, int nq, const double *__restrict__ levels,
+              int n_steps, Globals g, OutT *__restrict__ V, OutT *__restrict__ K) {
+    extern __shared__ double sm[];
+    double *xa = sm;                   // [nq][4]: x_a (3) and w_a
+    double *lv = sm + 4 * MAX_RULE;    // [n_steps+1][LV_STRIDE]
+    const int l = blockIdx.y;
+    const int j = blockIdx.x * REG_THREADS + threadIdx.x;
+    const double *gl = geo + (size_t)l * GEO_STRIDE;
+    for (int a = threadIdx.x; a < nq; a += REG_THREADS) {
+        double s1 = rule[3 * a], s2 = rule[3 * a + 1];
+        for (int c = 0; c < 3; ++c)
+            xa[4 * a + c] = gl[GEO_V0 + c] + s1 * (gl[GEO_V1 + c] - gl[GEO_V0 + c]) +
+                            s2 * (gl[GEO_V2 + c] - gl[GEO_V1 + c]);
+        xa[4 * a + 3] = rule[3 * a + 2];
+    }
+    for (int i = threadIdx.x; i < (n_steps + 1) * LV_STRIDE; i += REG_THREADS) lv[i] = levels[i];
+    __syncthreads();
+    if (j >= E) return;
+    const int32_t tl[3] = {tris[3 * l], tris[3 * l + 1], tris[3 * l + 2]};
+    const int32_t tj[3] = {tris[3 * j], tris[3 * j + 1], tris[3 * j + 2]};
+    if (touches(tl, tj)) return;  // written by the regularised-rule kernel
+
+    const double *gj = geo + (size_t)j * GEO_STRIDE;
+    double P0[3], e1[3], e2[3], n[3];
+    for (int c = 0; c < 3; ++c) {
+        P0[c] = gj[GEO_V0 + c];
+        e1[c] = gj[GEO_V1 + c] - gj[GEO_V0 + c];
+        e2[c] = gj[GEO_V2 + c] - gj[GEO_V1 + c];
+        n[c] = gj[GEO_N + c];
+    }
+    const double scale = 4.0 * gl[GEO_AREA] * gj[GEO_AREA];
+    const size_t EE = (size_t)E * E, ij = (size_t)l * E + j;
+
+    // level 0: delta -> 0 limits and the delta = 0 singular integrands
+    double s0v = 0, s0k = 0, ssv = 0, ssk = 0;
+    for (int b = 0; b < nq; ++b) {
+        double t1 = rule[3 * b], t2 = rule[3 * b + 1], wb = rule[3 * b + 2];
+        double y0 = P0[0] + t1 * e1[0] + t2 * e2[0];
+        double y1 = P0[1] + t1 * e1[1] + t2 * e2[1];
+        double y2 = P0[2] + t1 * e1[2] + t2 * e2[2];
+        for (int a = 0; a < nq; ++a) {
+            double r0 = xa[4 * a] - y0, r1 = xa[4 * a + 1] - y1, r2 = xa[4 * a + 2] - y2;
+            double rr = r0 * r0 + r1 * r1 + r2 * r2;
+            double irho = rsqrt(rr), rho = rr * irho;
+            double rnr = (r0 * n[0] + r1 * n[1] + r2 * n[2]) * irho;
+            double w = xa[4 * a + 3] * wb;
+            s0v = fma(w, g.A * rho, s0v);
+            s0k = fma(w, -g.Ap * rnr, s0k);
+            ssv = fma(w, g.F * irho, ssv);
+            ssk = fma(w, g.Fs * rnr * irho * irho, ssk);
+        }
+    }
+    double pv2 = 0, pk2 = 0;                   // S_{i-2}
+    double pv1 = scale * s0v, pk1 = scale * s0k;  // S_{i-1}
+    const double sv_sing = scale * ssv, sk_sing = scale * ssk;
+
+    for (int c0 = 1; c0 <= n_steps; c0 += CH) {
+        double sv[CH], sk[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) sv[u] = sk[u] = 0.0;
+        for (int b = 0; b < nq; ++b) {
+            double t1 = rule[3 * b], t2 = rule[3 * b + 1], wb = rule[3 * b + 2];
+            double y0 = P0[0] + t1 * e1[0] + t2 * e2[0];
+            double y1 = P0[1] + t1 * e1[1] + t2 * e2[1];
+            double y2 = P0[2] + t1 * e1[2] + t2 * e2[2];
+            for (int a = 0; a < nq; ++a) {
+                double r0 = xa[4 * a] - y0, r1 = xa[4 * a + 1] - y1, r2 = xa[4 * a + 2] - y2;
+                double rr = r0 * r0 + r1 * r1 + r2 * r2;
+                double irho = rsqrt(rr), rho = rr * irho;
+                double rnr = (r0 * n[0] + r1 * n[1] + r2 * n[2]) * irho;
+                double w = xa[4 * a + 3] * wb, wk = w * rnr;
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    if (c0 + u <= n_steps) {
+                        double v, kf;
+                        eval_level(rho, irho, lv + (c0 + u) * LV_STRIDE, g, v, kf);
+                        sv[u] = fma(w, v, sv[u]);
+                        sk[u] = fma(wk, kf, sk[u]);
+                    }
+                }
+            }
+        }
+        // second differences: level i = c0 + u completes block d = i - 1
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            int i = c0 + u;
+            if (i <= n_steps) {
+                double cv = scale * sv[u], ck = scale * sk[u];
+                double bv, bk;
+                if (i == 1) {  // eq. V0 / eq. K0
+                    bv = g.h * sv_sing - cv + pv1;
+                    bk = g.h * sk_sing - ck + pk1;
+                } else {       // eq. vd / eq. K_d for d = i - 1
+                    bv = 2.0 * pv1 - cv - pv2;
+                    bk = 2.0 * pk1 - ck - pk2;
+                }
+                store(V + (size_t)(i - 1) * EE + ij, bv);
+                if (K) store(K + (size_t)(i - 1) * EE + ij, bk);
+                pv2 = pv1; pk2 = pk1;
+                pv1 = cv;  pk1 = ck;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------- touching pairs, FP64 ---
+constexpr int SS_THREADS = 128;
+
+struct SSTables {
+    const double *s1[4], *s2[4], *t1[4], *t2[4], *w[4];
+    int n[4];
+};
+
+template <int CH, class OutT>
+__global__ void __launch_bounds__(SS_THREADS)
+k_singular_f64(const double *__restrict__ geo, const TouchPair *__restrict__ pairs, int E,
+               SSTables tab, const double *__restrict__ levels, int n_steps, Globals g,
+               OutT *__restrict__ V, OutT *__restrict__ K) {
+    __shared__ double red[SS_THREADS / 32][3 * CH + 8];
+    __shared__ double fin[3 * CH + 8];
+    const TouchPair P = pairs[blockIdx.x];
+    const int a = P.a, b = P.b, cls = P.cls;
+    // slots are pre-filled with -1; a slot the classification did not write
+    // (a count mismatch, reported through the status word) is skipped
+    if (a < 0 || b < a || b >= E || cls < PAIR_VERTEX || cls > PAIR_IDENTICAL) return;
+    const double *ga = geo + (size_t)a * GEO_STRIDE, *gb = geo + (size_t)b * GEO_STRIDE;
+    double A0[3], A1[3], A2[3], B0[3], B1[3], B2[3], na[3], nb[3];
+    {
+        int oa0 = P.perm & 3, oa1 = (P.perm >> 2) & 3, oa2 = (P.perm >> 4) & 3;
+        int ob0 = (P.perm >> 6) & 3, ob1 = (P.perm >> 8) & 3, ob2 = (P.perm >> 10) & 3;
+        for (int c = 0; c < 3; ++c) {
+            A0[c] = ga[3 * oa0 + c];
+            A1[c] = ga[3 * oa1 + c] - ga[3 * oa0 + c];
+            A2[c] = ga[3 * oa2 + c] - ga[3 * oa1 + c];
+            B0[c] = gb[3 * ob0 + c];
+            B1[c] = gb[3 * ob1 + c] - gb[3 * ob0 + c];
+            B2[c] = gb[3 * ob2 + c] - gb[3 * ob1 + c];
+            na[c] = ga[GEO_N + c];
+            nb[c] = gb[GEO_N + c];
+        }
+    }
+    const double scale = 4.0 * ga[GEO_AREA] * gb[GEO_AREA];
+    const bool ident = cls == PAIR_IDENTICAL;
+    const int npt = tab.n[cls];
+    const double *S1 = tab.s1[cls], *S2 = tab.s2[cls], *T1 = tab.t1[cls], *T2 = tab.t2[cls],
+                 *W = tab.w[cls];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t EE = (size_t)E * E, iab = (size_t)a * E + b, iba = (size_t)b * E + a;
+
+    // point p: x on a, y on b; entry (a,b): r = x - y, n_b; entry (b,a): r' = -r, n_a
+    auto point = [&](int p, double &rho, double &irho, double &rab, double &rba, double &w) {
+        double s1 = S1[p], s2 = S2[p], t1 = T1[p], t2 = T2[p];
+        double r[3];
+        for (int c = 0; c < 3; ++c)
+            r[c] = (A0[c] + s1 * A1[c] + s2 * A2[c]) - (B0[c] + t1 * B1[c] + t2 * B2[c]);
+        double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        irho = rsqrt(rr);
+        rho = rr * irho;
+        rab = (r[0] * nb[0] + r[1] * nb[1] + r[2] * nb[2]) * irho;
+        rba = -(r[0] * na[0] + r[1] * na[1] + r[2] * na[2]) * irho;
+        w = W[p];
+    };
+    auto reduce = [&](double *vals, int nv) {
+        for (int k = 0; k < nv; ++k) {
+            double v = vals[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < nv) {
+            double s = 0.0;
+            for (int wi = 0; wi < SS_THREADS / 32; ++wi) s += red[wi][threadIdx.x];
+            fin[threadIdx.x] = scale * s;
+        }
+        __syncthreads();
+    };
+
+    // level 0 and delta = 0 integrands
+    double z[6] = {0, 0, 0, 0, 0, 0};
+    for (int p = threadIdx.x; p < npt; p += SS_THREADS) {
+        double rho, irho, rab, rba, w;
+        point(p, rho, irho, rab, rba, w);
+        z[0] = fma(w, g.A * rho, z[0]);
+        z[1] = fma(w, -g.Ap * rab, z[1]);
+        z[2] = fma(w, -g.Ap * rba, z[2]);
+        z[3] = fma(w, g.F * irho, z[3]);
+        z[4] = fma(w, g.Fs * rab * irho * irho, z[4]);
+        z[5] = fma(w, g.Fs * rba * irho * irho, z[5]);
+    }
+    reduce(z, 6);
+    // sliding window (only thread 0 uses it)
+    double pv2 = 0, pa2 = 0, pb2 = 0, pv1 = fin[0], pa1 = fin[1], pb1 = fin[2];
+    const double sv_s = fin[3], sa_s = fin[4], sb_s = fin[5];
+    __syncthreads();
+
+    for (int c0 = 1; c0 <= n_steps; c0 += CH) {
+        double acc[3 * CH];
+#pragma unroll
+        for (int k = 0; k < 3 * CH; ++k) acc[k] = 0.0;
+        for (int p = threadIdx.x; p < npt; p += SS_THREADS) {
+            double rho, irho, rab, rba, w;
+            point(p, rho, irho, rab, rba, w);
+            double wa = w * rab, wb = w * rba;
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                if (c0 + u <= n_steps) {
+                    double v, kf;
+                    eval_level(rho, irho, levels + (c0 + u) * LV_STRIDE, g, v, kf);
+                    acc[u] = fma(w, v, acc[u]);
+                    acc[CH + u] = fma(wa, kf, acc[CH + u]);
+                    acc[2 * CH + u] = fma(wb, kf, acc[2 * CH + u]);
+                }
+            }
+        }
+        reduce(acc, 3 * CH);
+        if (threadIdx.x == 0) {
+            for (int u = 0; u < CH; ++u) {
+                int i = c0 + u;
+                if (i > n_steps) break;
+                double cv = fin[u], ca = fin[CH + u], cb = fin[2 * CH + u];
+                double bv, ba, bb;
+                if (i == 1) {
+                    bv = g.h * sv_s - cv + pv1;
+                    ba = g.h * sa_s - ca + pa1;
+                    bb = g.h * sb_s - cb + pb1;
+                } else {
+                    bv = 2.0 * pv1 - cv - pv2;
+                    ba = 2.0 * pa1 - ca - pa2;
+                    bb = 2.0 * pb1 - cb - pb2;
+                }
+                size_t off = (size_t)(i - 1) * EE;
+                store(V + off + iab, bv);
+                if (!ident) store(V + off + iba, bv);
+                if (K) {
+                    // flat triangles: r . n_y vanishes on an identical pair
+                    store(K + off + iab, ident ? 0.0 : ba);
+                    if (!ident) store(K + off + iba, bb);
+                }
+                pv2 = pv1; pa2 = pa1; pb2 = pb1;
+                pv1 = cv;  pa1 = ca;  pb1 = cb;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------- driver ---
+struct AssemblyLayout {
+    double *geo;
+    int32_t *row_count, *row_off;
+    TouchPair *pairs;
+    double *rule, *ss, *levels;
+    size_t ss_n[4];
+    size_t bytes;
+};
+
+static AssemblyLayout layout(const Mesh &m, const stb_params &p, void *ws, size_t cap) {
+    Carve c(ws, cap);
+    AssemblyLayout L{};
+    L.geo = c.take<double>((size_t)m.n_tris * GEO_STRIDE);
+    L.row_count = c.take<int32_t>(m.n_tris);
+    L.row_off = c.take<int32_t>(m.n_tris + 1);
+    L.pairs = c.take<TouchPair>(m.n_touch > 0 ? m.n_touch : 1);
+    L.rule = c.take<double>(3 * (size_t)p.quad_regular * p.quad_regular);
+    size_t tot = 0;
+    for (int cls = 1; cls <= 3; ++cls) {
+        L.ss_n[cls] = ss_rule_size(cls, p.quad_singular);
+        tot += 5 * L.ss_n[cls];
+    }
+    L.ss = c.take<double>(tot);
+    L.levels = c.take<double>((size_t)(p.n_steps + 1) * LV_STRIDE);
+    L.bytes = c.off;
+    return L;
+}
+
+static stb_status check_params(const stb_params *p) {
+    if (!p) return fail(STB_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->alpha > 0.0) || !(p->T > 0.0) || !std::isfinite(p->alpha) || !std::isfinite(p->T))
+        return fail(STB_ERR_INVALID_ARG, "alpha and T must be positive and finite");
+    if (p->n_steps < 1 || p->n_steps > MAX_LEVELS - 1)
+        return fail(STB_ERR_INVALID_ARG, "n_steps must be in [1, %d]", MAX_LEVELS - 1);
+    if (p->quad_regular < 1 || p->quad_regular > 16)
+        return fail(STB_ERR_INVALID_ARG, "quad_regular must be in [1, 16]");
+    if (p->quad_singular < 1 || p->quad_singular > 12)
+        return fail(STB_ERR_INVALID_ARG, "quad_singular must be in [1, 12]");
+    if (p->precision != STB_PREC_FP64)
+        return fail(STB_ERR_INVALID_ARG, "precision %d is not available", p->precision);
+    if (p->storage != STB_STORE_F64 && p->storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "storage must be STB_STORE_F64 or STB_STORE_F32");
+    if (p->reserved != 0) return fail(STB_ERR_INVALID_ARG, "reserved must be 0");
+    return STB_OK;
+}
+
+static Globals make_globals(const stb_params &p) {
+    const double pi = 3.14159265358979323846;
+    Globals g;
+    g.A = 1.0 / (8.0 * pi * p.alpha * p.alpha);
+    g.Ap = 1.0 / (8.0 * pi * p.alpha);
+    g.F = 1.0 / (4.0 * pi * p.alpha);
+    g.Fs = 1.0 / (4.0 * pi);
+    g.h = p.T / p.n_steps;
+    return g;
+}
+
+template <class OutT>
+static stb_status run_assembly(const Mesh &m, const stb_params &p, OutT *V, OutT *K,
+                               const AssemblyLayout &L, int32_t *status, cudaStream_t s) {
+    constexpr int CH = 8;
+    const int E = (int)m.n_tris;
+    const int nq = p.quad_regular * p.quad_regular;
+    Globals g = make_globals(p);
+    size_t smem = sizeof(double) * (4 * MAX_RULE + (size_t)(p.n_steps + 1) * LV_STRIDE);
+    STB_CUDA(cudaFuncSetAttribute(k_regular_f64<CH, OutT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((E + REG_THREADS - 1) / REG_THREADS, E);
+    count_launch(s);
+    k_regular_f64<CH, OutT><<<grid, REG_THREADS, smem, s>>>(L.geo, m.d_tris, E, L.rule, nq,
+                                                            L.levels, p.n_steps, g, V, K);
+    stb_status st = check_launch("k_regular_f64");
+    if (st) return st;
+    if (m.n_touch > 0) {
+        SSTables tab{};
+        const double *base = L.ss;
+        for (int cls = 1; cls <= 3; ++cls) {
+            size_t n = L.ss_n[cls];
+            tab.s1[cls] = base;
+            tab.s2[cls] = base + n;
+            tab.t1[cls] = base + 2 * n;
+            tab.t2[cls] = base + 3 * n;
+            tab.w[cls] = base + 4 * n;
+            tab.n[cls] = (int)n;
+            base += 5 * n;
+        }
+        count_launch(s);
+        k_singular_f64<CH, OutT><<<(unsigned)m.n_touch, SS_THREADS, 0, s>>>(
+            L.geo, L.pairs, E, tab, L.levels, p.n_steps, g, V, K);
+        if ((st = check_launch("k_singular_f64"))) return st;
+    }
+    return STB_OK;
+}
+
+}  // namespace stb
+
+using namespace stb;
+
+extern "C" stb_status stb_assemble_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                                  size_t *bytes) {
+    if (!mesh || !bytes) return fail(STB_ERR_INVALID_ARG, "mesh and bytes must be given");
+    stb_status st = check_params(params);
+    if (st) return st;
+    *bytes = align256(layout(mesh->m, *params, nullptr, 0).bytes);
+    return STB_OK;
+}
+
+extern "C" stb_status stb_assemble(const stb_mesh *mesh, const stb_params *params, void *V, void *K,
+                                   void *ws, size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !V) return fail(STB_ERR_INVALID_ARG, "mesh and V must be given");
+    stb_status st = check_params(params);
+    if (st) return st;
+    const Mesh &m = mesh->m;
+    if (m.n_tris > 65535) return fail(STB_ERR_INVALID_ARG, "dense assembly supports E <= 65535");
+    AssemblyLayout L = layout(m, *params, ws, ws_bytes);
+    if ((st = check_workspace(ws, ws_bytes, L.bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    upload_psi_coeffs(s);
+
+    // host tables: regular rule, regularised rules, level constants
+    std::vector<double> host;
+    {
+        std::vector<double> a, b, c, d, w;
+        triangle_rule(params->quad_regular, a, b, w);
+        for (size_t i = 0; i < w.size(); ++i) {
+            host.push_back(a[i]);
+            host.push_back(b[i]);
+            host.push_back(w[i]);
+        }
+        size_t rule_pad = (size_t)((char *)L.ss - (char *)L.rule) / sizeof(double);
+        host.resize(rule_pad, 0.0);
+        for (int cls = 1; cls <= 3; ++cls) {
+            ss_rule(cls, params->quad_singular, a, b, c, d, w);
+            host.insert(host.end(), a.begin(), a.end());
+            host.insert(host.end(), b.begin(), b.end());
+            host.insert(host.end(), c.begin(), c.end());
+            host.insert(host.end(), d.begin(), d.end());
+            host.insert(host.end(), w.begin(), w.end());
+        }
+        size_t lev_pad = (size_t)((char *)L.levels - (char *)L.rule) / sizeof(double);
+        host.resize(lev_pad, 0.0);
+        const double pi = 3.14159265358979323846, al = params->alpha;
+        const double h = params->T / params->n_steps;
+        for (int i = 0; i <= params->n_steps; ++i) {
+            double lvv[LV_STRIDE] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (i > 0) {
+                double delta = i * h, sd = std::sqrt(delta);
+                lvv[LV_C] = 1.0 / (2.0 * std::sqrt(al * delta));
+                lvv[LV_B] = delta / (4.0 * pi * al);
+                lvv[LV_CC] = sd / (4.0 * pi * std::sqrt(pi * al * al * al));
+                lvv[LV_D] = delta / (4.0 * pi);
+                lvv[LV_E] = sd / (4.0 * pi * std::sqrt(pi * al));
+            }
+            host.insert(host.end(), lvv, lvv + LV_STRIDE);
+        }
+    }
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    STB_CUDA(cudaMemcpyAsync(L.rule, host.data(), host.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, s));
+    int32_t *status = status_word(ws);
+    STB_CUDA(cudaMemsetAsync(L.pairs, 0xff, sizeof(TouchPair) * (m.n_touch > 0 ? m.n_touch : 1), s));
+    if ((st = launch_geometry(m, L.geo, s))) return st;
+    if ((st = launch_classify(m, L.row_count, L.row_off, L.pairs, status, s))) return st;
+    if (params->storage == STB_STORE_F64)
+        return run_assembly<double>(m, *params, (double *)V, (double *)K, L, status, s);
+    return run_assembly<float>(m, *params, (float *)V, (float *)K, L, status, s);
+}

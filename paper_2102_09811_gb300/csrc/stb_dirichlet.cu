@@ -1,0 +1,334 @@
+// stb_dirichlet.cu -- Dirichlet data of exterior heat sources, its L2
+// projection into piecewise constants, the right-hand side
+// f = (1/2 M_h + K_h) g and the L2(Sigma_h) error of the Neumann datum
+// (Sec. 3.4, Sec. 6.1).  One thread per space-time element (r, k, j); the
+// space rule (conical, q x q) and time rule (Gauss, n_time) live in shared
+// memory.
+#include <cmath>
+#include <vector>
+
+#include "stb_internal.h"
+#include "stb_toeplitz.h"
+
+namespace stb {
+
+constexpr int DIR_THREADS = 128;
+constexpr int MAX_QS = 32;   // q_space <= 32
+constexpr int MAX_NT = 64;   // n_time <= 64
+constexpr int MAX_SRC = 64;  // sources per right-hand side
+
+// G_alpha(r, tau) (Sec. 2), zero for tau <= 0
+__device__ __forceinline__ double heat(double rr, double tau, double alpha) {
+    if (tau <= 0.0) return 0.0;
+    const double s = 4.0 * 3.14159265358979323846 * alpha * tau;
+    return exp(-rr / (4.0 * alpha * tau)) / (s * sqrt(s));
+}
+
+struct DirLayout {
+    double *geo, *rule, *src, *part;
+    size_t bytes;
+};
+
+static DirLayout dir_layout(const Mesh &m, int nrhs, int n_src, int q, int nt, void *ws,
+                            size_t cap, size_t n_part) {
+    Carve c(ws, cap);
+    DirLayout L{};
+    L.geo = c.take<double>((size_t)m.n_tris * GEO_STRIDE);
+    L.rule = c.take<double>(3 * (size_t)q * q + 2 * (size_t)nt);
+    L.src = c.take<double>(5 * (size_t)nrhs * n_src);
+    L.part = c.take<double>(n_part);
+    L.bytes = c.off;
+    return L;
+}
+
+static void host_rules(int q, int nt, std::vector<double> &out) {
+    std::vector<double> s1, s2, w, tx(nt), tw(nt);
+    triangle_rule(q, s1, s2, w);
+    gauss_legendre01(nt, tx.data(), tw.data());
+    out.clear();
+    for (size_t i = 0; i < w.size(); ++i) {
+        out.push_back(s1[i]);
+        out.push_back(s2[i]);
+        out.push_back(w[i]);
+    }
+    out.insert(out.end(), tx.begin(), tx.end());
+    out.insert(out.end(), tw.begin(), tw.end());
+}
+
+// g_{r,k,j} = (h Delta_j)^{-1} int_{t_k}^{t_{k+1}} int_{gamma_j} g_r  (element mean)
+__global__ void __launch_bounds__(DIR_THREADS)
+k_project(const double *__restrict__ geo, int E, const double *__restrict__ rule, int nq, int nt,
+          const double *__restrict__ src, int n_src, int nrhs, int n_steps, double h, double alpha,
+          double *__restrict__ g) {
+    __shared__ double rs[3 * MAX_QS * MAX_QS + 2 * MAX_NT];
+    __shared__ double sr[5 * MAX_SRC];
+    for (int i = threadIdx.x; i < 3 * nq + 2 * nt; i += DIR_THREADS) rs[i] = rule[i];
+    const int r = blockIdx.y;
+    for (int i = threadIdx.x; i < 5 * n_src; i += DIR_THREADS) sr[i] = src[(size_t)r * n_src * 5 + i];
+    __syncthreads();
+    size_t idx = (size_t)blockIdx.x * DIR_THREADS + threadIdx.x;  // (k, j)
+    if (idx >= (size_t)n_steps * E) return;
+    const int k = (int)(idx / E), j = (int)(idx % E);
+    const double *gj = geo + (size_t)j * GEO_STRIDE;
+    const double *tx = rs + 3 * nq, *tw = tx + nt;
+    double acc = 0.0;
+    for (int a = 0; a < nq; ++a) {
+        double s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
+        double x[3];
+        for (int c = 0; c < 3; ++c)
+            x[c] = gj[c] + s1 * (gj[3 + c] - gj[c]) + s2 * (gj[6 + c] - gj[3 + c]);
+        double inner = 0.0;
+        for (int b = 0; b < nt; ++b) {
+            double t = (k + tx[b]) * h, gv = 0.0;
+            for (int s = 0; s < n_src; ++s) {
+                const double *S = sr + 5 * s;
+                double d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
+                gv = fma(S[4], heat(d0 * d0 + d1 * d1 + d2 * d2, t - S[3], alpha), gv);
+            }
+            inner = fma(tw[b], gv, inner);
+        }
+        acc = fma(wa, inner, acc);
+    }
+    g[(size_t)r * n_steps * E + idx] = 2.0 * acc;
+}
+
+// out-partials of sum (w - w_h)^2 and sum w^2 over Sigma_h (Sec. 6.1), with
+// w = alpha du/dn_x = -sum_s weight_s G (x - y_s).n_x / (2 (t - t0_s))
+__global__ void __launch_bounds__(DIR_THREADS)
+k_error(const double *__restrict__ geo, int E, const double *__restrict__ rule, int nq, int nt,
+        const double *__restrict__ src, int n_src, int nrhs, int n_steps, double h, double alpha,
+        const double *__restrict__ wh, double *__restrict__ part) {
+    __shared__ double rs[3 * MAX_QS * MAX_QS + 2 * MAX_NT];
+    __shared__ double sr[5 * MAX_SRC];
+    __shared__ double red[2][DIR_THREADS / 32];
+    for (int i = threadIdx.x; i < 3 * nq + 2 * nt; i += DIR_THREADS) rs[i] = rule[i];
+    const int r = blockIdx.y;
+    for (int i = threadIdx.x; i < 5 * n_src; i += DIR_THREADS) sr[i] = src[(size_t)r * n_src * 5 + i];
+    __syncthreads();
+    size_t idx = (size_t)blockIdx.x * DIR_THREADS + threadIdx.x;
+    double e2 = 0.0, r2 = 0.0;
+    if (idx < (size_t)n_steps * E) {
+        const int k = (int)(idx / E), j = (int)(idx % E);
+        const double *gj = geo + (size_t)j * GEO_STRIDE;
+        const double *tx = rs + 3 * nq, *tw = tx + nt;
+        const double whv = wh[(size_t)r * n_steps * E + idx];
+        for (int a = 0; a < nq; ++a) {
+            double s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
+            double x[3];
+            for (int c = 0; c < 3; ++c)
+                x[c] = gj[c] + s1 * (gj[3 + c] - gj[c]) + s2 * (gj[6 + c] - gj[3 + c]);
+            double ie = 0.0, ir = 0.0;
+            for (int b = 0; b < nt; ++b) {
+                double t = (k + tx[b]) * h, wv = 0.0;
+                for (int s = 0; s < n_src; ++s) {
+                    const double *S = sr + 5 * s;
+                    double tau = t - S[3];
+                    if (tau <= 0.0) continue;
+                    double d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
+                    double dn = d0 * gj[GEO_N] + d1 * gj[GEO_N + 1] + d2 * gj[GEO_N + 2];
+                    wv -= S[4] * heat(d0 * d0 + d1 * d1 + d2 * d2, tau, alpha) * dn / (2.0 * tau);
+                }
+                ie = fma(tw[b], (wv - whv) * (wv - whv), ie);
+                ir = fma(tw[b], wv * wv, ir);
+            }
+            e2 = fma(wa, ie, e2);
+            r2 = fma(wa, ir, r2);
+        }
+        double f = 2.0 * gj[GEO_AREA] * h;
+        e2 *= f;
+        r2 *= f;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = e2;
+        red[1][threadIdx.x >> 5] = r2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double se = 0.0, sr2 = 0.0;
+        for (int w = 0; w < DIR_THREADS / 32; ++w) {
+            se += red[0][w];
+            sr2 += red[1][w];
+        }
+        size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        part[2 * b] = se;
+        part[2 * b + 1] = sr2;
+    }
+}
+
+__global__ void k_sum_pairs(const double *__restrict__ part, size_t n, double *__restrict__ out) {
+    __shared__ double red[2][32];
+    double a = 0.0, b = 0.0;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a;
+        red[1][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            sa += red[0][w];
+            sb += red[1][w];
+        }
+        out[0] = sa;
+        out[1] = sb;
+    }
+}
+
+// f += (h/2) Delta_l g
+__global__ void k_add_mass(const double *__restrict__ geo, int E, size_t total, double h,
+                           const double *__restrict__ g, double *__restrict__ f) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int l = (int)(idx % E);
+    f[idx] = fma(0.5 * h * geo[(size_t)l * GEO_STRIDE + GEO_AREA], g[idx], f[idx]);
+}
+
+static stb_status check_rule_args(int nrhs, int n_src, int q, int nt) {
+    if (nrhs < 1 || nrhs > 65535 || n_src < 1 || n_src > MAX_SRC || q < 1 || q > MAX_QS ||
+        nt < 1 || nt > MAX_NT)
+        return fail(STB_ERR_INVALID_ARG,
+                    "need 1 <= nrhs <= 65535, 1 <= n_src <= %d, 1 <= q_space <= %d, 1 <= n_time <= %d",
+                    MAX_SRC, MAX_QS, MAX_NT);
+    return STB_OK;
+}
+
+static stb_status upload_rules_sources(const DirLayout &L, int q, int nt, const double *sources,
+                                       int nrhs, int n_src, cudaStream_t s) {
+    std::vector<double> host;
+    host_rules(q, nt, host);
+    STB_CUDA(cudaMemcpyAsync(L.rule, host.data(), host.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, s));
+    STB_CUDA(cudaMemcpyAsync(L.src, sources, sizeof(double) * 5 * (size_t)nrhs * n_src,
+                             cudaMemcpyHostToDevice, s));
+    return STB_OK;
+}
+
+}  // namespace stb
+
+using namespace stb;
+
+extern "C" stb_status stb_project_workspace_size(const stb_mesh *mesh, int32_t nrhs, int32_t n_src,
+                                                 int32_t q, int32_t nt, size_t *bytes) {
+    if (!mesh || !bytes) return fail(STB_ERR_INVALID_ARG, "mesh and bytes must be given");
+    stb_status st = check_rule_args(nrhs, n_src, q, nt);
+    if (st) return st;
+    *bytes = align256(dir_layout(mesh->m, nrhs, n_src, q, nt, nullptr, 0, 0).bytes);
+    return STB_OK;
+}
+
+extern "C" stb_status stb_project_dirichlet(const stb_mesh *mesh, const stb_params *p,
+                                            const double *sources, int32_t nrhs, int32_t n_src,
+                                            int32_t q, int32_t nt, double *g, void *ws,
+                                            size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !p || !sources || !g) return fail(STB_ERR_INVALID_ARG, "null argument");
+    if (!(p->alpha > 0) || !(p->T > 0) || p->n_steps < 1)
+        return fail(STB_ERR_INVALID_ARG, "alpha, T and n_steps must be positive");
+    stb_status st = check_rule_args(nrhs, n_src, q, nt);
+    if (st) return st;
+    const Mesh &m = mesh->m;
+    DirLayout L = dir_layout(m, nrhs, n_src, q, nt, ws, ws_bytes, 0);
+    if ((st = check_workspace(ws, ws_bytes, L.bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = upload_rules_sources(L, q, nt, sources, nrhs, n_src, s))) return st;
+    if ((st = launch_geometry(m, L.geo, s))) return st;
+    size_t n = (size_t)p->n_steps * m.n_tris;
+    dim3 grid((unsigned)((n + DIR_THREADS - 1) / DIR_THREADS), (unsigned)nrhs);
+    count_launch(s);
+    k_project<<<grid, DIR_THREADS, 0, s>>>(L.geo, (int)m.n_tris, L.rule, q * q, nt, L.src, n_src,
+                                           nrhs, p->n_steps, p->T / p->n_steps, p->alpha, g);
+    return check_launch("k_project");
+}
+
+extern "C" stb_status stb_rhs_workspace_size(const stb_mesh *mesh, const stb_params *p, int32_t nrhs,
+                                             size_t *bytes) {
+    if (!mesh || !p || !bytes || nrhs < 1 || p->n_steps < 1)
+        return fail(STB_ERR_INVALID_ARG, "invalid argument");
+    Carve c(nullptr, 0);
+    c.take<double>((size_t)mesh->m.n_tris * GEO_STRIDE);
+    c.take<char>(toeplitz_partial_bytes(mesh->m.n_tris, p->n_steps, nrhs));
+    *bytes = align256(c.off);
+    return STB_OK;
+}
+
+extern "C" stb_status stb_dirichlet_rhs(const stb_mesh *mesh, const stb_params *p, const void *K,
+                                        const double *g, int32_t nrhs, double *f, void *ws,
+                                        size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !p || !K || !g || !f) return fail(STB_ERR_INVALID_ARG, "null argument");
+    if (p->storage != STB_STORE_F64 && p->storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "bad storage");
+    size_t need;
+    stb_status st = stb_rhs_workspace_size(mesh, p, nrhs, &need);
+    if (st) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    const Mesh &m = mesh->m;
+    Carve c(ws, ws_bytes);
+    double *geo = c.take<double>((size_t)m.n_tris * GEO_STRIDE);
+    double *part = (double *)c.take<char>(toeplitz_partial_bytes(m.n_tris, p->n_steps, nrhs));
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = launch_geometry(m, geo, s))) return st;
+    if ((st = toeplitz_fp64(K, p->storage, m.n_tris, p->n_steps, nrhs, g, 0.0, f, part, s))) return st;
+    size_t total = (size_t)nrhs * p->n_steps * m.n_tris;
+    count_launch(s);
+    k_add_mass<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(geo, (int)m.n_tris, total,
+                                                                p->T / p->n_steps, g, f);
+    return check_launch("k_add_mass");
+}
+
+static size_t error_blocks(const Mesh &m, int n_steps, int nrhs) {
+    size_t n = (size_t)n_steps * m.n_tris;
+    return ((n + DIR_THREADS - 1) / DIR_THREADS) * (size_t)nrhs;
+}
+
+extern "C" stb_status stb_error_workspace_size(const stb_mesh *mesh, const stb_params *p,
+                                               int32_t nrhs, int32_t n_src, int32_t q, int32_t nt,
+                                               size_t *bytes) {
+    if (!mesh || !p || !bytes || p->n_steps < 1) return fail(STB_ERR_INVALID_ARG, "invalid argument");
+    stb_status st = check_rule_args(nrhs, n_src, q, nt);
+    if (st) return st;
+    size_t nblk = error_blocks(mesh->m, p->n_steps, nrhs);
+    *bytes = align256(dir_layout(mesh->m, nrhs, n_src, q, nt, nullptr, 0, 2 * nblk).bytes);
+    return STB_OK;
+}
+
+extern "C" stb_status stb_neumann_error(const stb_mesh *mesh, const stb_params *p,
+                                        const double *sources, int32_t nrhs, int32_t n_src,
+                                        const double *w, int32_t q, int32_t nt, double *out,
+                                        void *ws, size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !p || !sources || !w || !out) return fail(STB_ERR_INVALID_ARG, "null argument");
+    if (!(p->alpha > 0) || !(p->T > 0) || p->n_steps < 1 || p->n_steps > 4096)
+        return fail(STB_ERR_INVALID_ARG, "alpha, T must be positive, 1 <= n_steps <= 4096");
+    stb_status st = check_rule_args(nrhs, n_src, q, nt);
+    if (st) return st;
+    const Mesh &m = mesh->m;
+    size_t n = (size_t)p->n_steps * m.n_tris;
+    unsigned gx = (unsigned)((n + DIR_THREADS - 1) / DIR_THREADS);
+    size_t nblk = error_blocks(m, p->n_steps, nrhs);
+    DirLayout L = dir_layout(m, nrhs, n_src, q, nt, ws, ws_bytes, 2 * nblk);
+    if ((st = check_workspace(ws, ws_bytes, L.bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = upload_rules_sources(L, q, nt, sources, nrhs, n_src, s))) return st;
+    if ((st = launch_geometry(m, L.geo, s))) return st;
+    count_launch(s);
+    k_error<<<dim3(gx, (unsigned)nrhs), DIR_THREADS, 0, s>>>(L.geo, (int)m.n_tris, L.rule, q * q, nt,
+                                                            L.src, n_src, nrhs, p->n_steps,
+                                                            p->T / p->n_steps, p->alpha, w, L.part);
+    if ((st = check_launch("k_error"))) return st;
+    count_launch(s);
+    k_sum_pairs<<<1, 1024, 0, s>>>(L.part, nblk, out);
+    return check_launch("k_sum_pairs");
+}

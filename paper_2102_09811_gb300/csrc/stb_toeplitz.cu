@@ -1,0 +1,134 @@
+// stb_toeplitz.cu -- block-Toeplitz matrix-vector product (eq. V_mat):
+//   y_r^k = beta y_r^k + sum_{d=0}^{k} A^d x_r^{k-d}
+// FP64 arithmetic on the SIMT FP64 pipe.  The product is a sum of dense
+// E x E by E x (n_steps - d) products, one per block d; the work is cut into
+// items (64 rows of l) x (16 time columns k) x (8 blocks d) so that every SM
+// gets a balanced share even though block d only feeds the columns k >= d.
+// Each item accumulates into its own partial slice; a second kernel adds the
+// slices in a fixed order (deterministic result).
+#include "stb_internal.h"
+#include "stb_toeplitz.h"
+
+namespace stb {
+
+constexpr int TM = 64;   // rows per item
+constexpr int TK = 16;   // time columns per item
+constexpr int TD = 8;    // blocks d per item
+constexpr int TJ = 32;   // contraction chunk
+constexpr int MV_THREADS = 128;
+
+template <class AT>
+__global__ void __launch_bounds__(MV_THREADS)
+k_toeplitz_partial(const AT *__restrict__ A, int E, int n_steps, int nrhs,
+                   const double *__restrict__ x, double *__restrict__ part) {
+    __shared__ double As[TM][TJ + 1];
+    __shared__ double Xs[TK][TJ + 1];
+    const int n_kt = (n_steps + TK - 1) / TK;
+    const int lt = blockIdx.x, kt = blockIdx.y % n_kt, r = blockIdx.y / n_kt, dr = blockIdx.z;
+    const int l0 = lt * TM, k0 = kt * TK, d0 = dr * TD;
+    if (d0 > k0 + TK - 1 || d0 >= n_steps) return;  // block range feeds no column here
+    const int d1 = min(min(d0 + TD, n_steps), k0 + TK);
+    const int tx = threadIdx.x % TK, ty = threadIdx.x / TK;  // column, row group (8 rows)
+    double acc[TM / (MV_THREADS / TK)];
+#pragma unroll
+    for (int i = 0; i < TM / (MV_THREADS / TK); ++i) acc[i] = 0.0;
+    const size_t EE = (size_t)E * E;
+    const double *xr = x + (size_t)r * n_steps * E;
+    for (int d = d0; d < d1; ++d) {
+        const AT *Ad = A + (size_t)d * EE;
+        for (int j0 = 0; j0 < E; j0 += TJ) {
+            for (int t = threadIdx.x; t < TM * TJ; t += MV_THREADS) {
+                int i = t / TJ, jj = t % TJ, l = l0 + i, j = j0 + jj;
+                As[i][jj] = (l < E && j < E) ? (double)Ad[(size_t)l * E + j] : 0.0;
+            }
+            for (int t = threadIdx.x; t < TK * TJ; t += MV_THREADS) {
+                int c = t / TJ, jj = t % TJ, k = k0 + c, j = j0 + jj;
+                Xs[c][jj] = (k < n_steps && k - d >= 0 && j < E) ? xr[(size_t)(k - d) * E + j] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int jj = 0; jj < TJ; ++jj) {
+                double xv = Xs[tx][jj];
+#pragma unroll
+                for (int i = 0; i < TM / (MV_THREADS / TK); ++i)
+                    acc[i] = fma(As[ty * (TM / (MV_THREADS / TK)) + i][jj], xv, acc[i]);
+            }
+            __syncthreads();
+        }
+    }
+    const int k = k0 + tx;
+    if (k >= n_steps) return;
+    double *pr = part + (((size_t)dr * nrhs + r) * n_steps + k) * E;
+#pragma unroll
+    for (int i = 0; i < TM / (MV_THREADS / TK); ++i) {
+        int l = l0 + ty * (TM / (MV_THREADS / TK)) + i;
+        if (l < E) pr[l] = acc[i];
+    }
+}
+
+// y = beta y + sum over the d-slices that feed column k (fixed order)
+__global__ void k_toeplitz_reduce(const double *__restrict__ part, int E, int n_steps, int nrhs,
+                                  double beta, double *__restrict__ y) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)nrhs * n_steps * E;
+    if (idx >= total) return;
+    int k = (int)((idx / E) % n_steps);
+    size_t slice = total;
+    double s = 0.0;
+    for (int dr = 0; dr * TD <= k; ++dr) s += part[dr * slice + idx];
+    y[idx] = beta == 0.0 ? s : fma(beta, y[idx], s);
+}
+
+size_t toeplitz_partial_bytes(int64_t E, int32_t n_steps, int32_t nrhs) {
+    size_t n_dr = (n_steps + TD - 1) / TD;
+    return align256(n_dr * (size_t)nrhs * n_steps * E * sizeof(double));
+}
+
+stb_status toeplitz_fp64(const void *A, int32_t storage, int64_t E, int32_t n_steps, int32_t nrhs,
+                         const double *x, double beta, double *y, double *part, cudaStream_t s) {
+    int n_kt = (n_steps + TK - 1) / TK, n_dr = (n_steps + TD - 1) / TD;
+    dim3 grid((unsigned)((E + TM - 1) / TM), (unsigned)(n_kt * nrhs), (unsigned)n_dr);
+    count_launch(s);
+    if (storage == STB_STORE_F64)
+        k_toeplitz_partial<double><<<grid, MV_THREADS, 0, s>>>((const double *)A, (int)E, n_steps,
+                                                               nrhs, x, part);
+    else
+        k_toeplitz_partial<float><<<grid, MV_THREADS, 0, s>>>((const float *)A, (int)E, n_steps,
+                                                              nrhs, x, part);
+    stb_status st = check_launch("k_toeplitz_partial");
+    if (st) return st;
+    size_t total = (size_t)nrhs * n_steps * E;
+    count_launch(s);
+    k_toeplitz_reduce<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, (int)E, n_steps, nrhs,
+                                                                      beta, y);
+    return check_launch("k_toeplitz_reduce");
+}
+
+}  // namespace stb
+
+using namespace stb;
+
+extern "C" stb_status stb_toeplitz_workspace_size(int64_t E, int32_t n_steps, int32_t nrhs,
+                                                  size_t *bytes) {
+    if (!bytes || E < 1 || E > 65535 || n_steps < 1 || nrhs < 1)
+        return fail(STB_ERR_INVALID_ARG, "need bytes, 1 <= E <= 65535, n_steps >= 1, nrhs >= 1");
+    *bytes = 256 + toeplitz_partial_bytes(E, n_steps, nrhs);
+    return STB_OK;
+}
+
+extern "C" stb_status stb_toeplitz_matvec(const void *A, int32_t a_storage, int64_t E,
+                                          int32_t n_steps, int32_t nrhs, const double *x,
+                                          double beta, double *y, void *ws, size_t ws_bytes,
+                                          stb_stream stream) {
+    if (!A || !x || !y) return fail(STB_ERR_INVALID_ARG, "A, x and y must be given");
+    if (a_storage != STB_STORE_F64 && a_storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "a_storage must be STB_STORE_F64 or STB_STORE_F32");
+    size_t need;
+    stb_status st = stb_toeplitz_workspace_size(E, n_steps, nrhs, &need);
+    if (st) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    double *part = reinterpret_cast<double *>(static_cast<char *>(ws) + 256);
+    return toeplitz_fp64(A, a_storage, E, n_steps, nrhs, x, beta, y, part, s);
+}

@@ -1,0 +1,271 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances.  Every block entry is a second difference of time-level sums,
+V^d = 2 S_d - S_{d+1} - S_{d-1} (eq. vd) or h S_* - S_1 + S_0 (eq. V0), and the
+two sides evaluate the sums with different (equally valid) rounding: erf/exp
+of different libraries, another summation order.  The difference of an entry
+is therefore bounded by c eps (|S_{d-1}| + 2|S_d| + |S_{d+1}|), which can
+exceed 1e-12 |V^d| where the difference cancels (large d, far pairs at small
+d).  Per block the test requires
+    ||A_gpu^d - A_orc^d||_F <= max(1e-12 ||A_orc^d||_F, 64 eps ||C^d||_F),
+C^d the entrywise magnitude above, computed from the oracle's own sums.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from paper_2102_09811_gb300 import capi, pipeline
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_device():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    capi._library()
+
+
+def gpu_assemble(nodes, tris, alpha, T, n_steps, q=3, m=4, storage=capi.STB_STORE_F64, k=True):
+    mesh = capi.Mesh(nodes, tris)
+    p = capi.stb_default_params(alpha, T, n_steps, q, m, storage=storage)
+    dt = torch.float64 if storage == capi.STB_STORE_F64 else torch.float32
+    E = mesh.n_tris
+    V = torch.full((n_steps, E, E), float("nan"), dtype=dt, device="cuda")
+    K = torch.full((n_steps, E, E), float("nan"), dtype=dt, device="cuda") if k else None
+    ws = torch.empty(capi.stb_assemble_workspace_size(mesh, p), dtype=torch.uint8, device="cuda")
+    capi.stb_assemble(mesh, p, V, K, ws)
+    capi.stb_workspace_status(ws)
+    torch.cuda.synchronize()
+    return mesh, V.double().cpu().numpy(), (K.double().cpu().numpy() if k else None)
+
+
+def cond_mag(S, h):
+    """[rows, n_steps, E] magnitude of the second-difference terms per entry."""
+    A = np.abs(S)
+    n_steps = S.shape[1] - 2
+    C = np.empty((S.shape[0], n_steps, S.shape[2]))
+    C[:, 0] = h * A[:, -1] + A[:, 1] + A[:, 0]
+    for d in range(1, n_steps):
+        C[:, d] = A[:, d - 1] + 2 * A[:, d] + A[:, d + 1]
+    return C
+
+
+def check_blocks(got, ref, S, h, label, extra_rel=0.0):
+    """got/ref: [rows, n_steps, E]; returns the worst ratio error/bound."""
+    C = cond_mag(S, h)
+    worst = 0.0
+    for d in range(ref.shape[1]):
+        err = np.linalg.norm(got[:, d] - ref[:, d])
+        nrm = np.linalg.norm(ref[:, d])
+        bound = max(1e-12 * nrm, 64 * EPS * np.linalg.norm(C[:, d])) + extra_rel * nrm
+        assert np.all(np.isfinite(got[:, d])), (label, d)
+        assert err <= bound, (label, d, err / max(nrm, 1e-300), bound / max(nrm, 1e-300))
+        worst = max(worst, err / bound if bound > 0 else 0.0)
+    return worst
+
+
+def test_c1_blocks_match_oracle():
+    """cube, 192 triangles, 16 steps, alpha = 1 (the plain FP64 workload)."""
+    wl = workloads.workload("cube192_e16")
+    nodes, tris, alpha, T, n = wl["nodes"], wl["tris"], wl["alpha"], wl["T"], wl["n_steps"]
+    _, V, K = gpu_assemble(nodes, tris, alpha, T, n)
+    E = len(tris)
+    Vo, Ko, SV, SK = oracle.assemble_rows(nodes, tris, alpha, T, n, np.arange(E), with_sums=True)
+    Vg, Kg = V.transpose(1, 0, 2), K.transpose(1, 0, 2)  # -> [rows][d][j]
+    h = T / n
+    wv = check_blocks(Vg, Vo, SV, h, "V")
+    wk = check_blocks(Kg, Ko, SK, h, "K")
+    # well-conditioned blocks meet 1e-12 outright
+    rel0 = np.linalg.norm(Vg[:, 0] - Vo[:, 0]) / np.linalg.norm(Vo[:, 0])
+    assert rel0 < 1e-12
+    print("C1 worst error/bound: V %.3f K %.3f; block-0 rel err %.2e" % (wv, wk, rel0))
+
+
+@pytest.mark.parametrize("n_face,n_steps,q,m", [(2, 13, 2, 3), (2, 1, 3, 4), (1, 9, 1, 1), (2, 8, 4, 5)])
+def test_ragged_orders_and_steps(n_face, n_steps, q, m):
+    """E not a multiple of the CTA width, E_t not a multiple of the level
+    chunk, the smallest and larger quadrature orders, a single step."""
+    nodes, tris = workloads.cube_mesh(n_face)
+    alpha, T = 0.7, 0.5
+    _, V, K = gpu_assemble(nodes, tris, alpha, T, n_steps, q, m)
+    Vo, Ko, SV, SK = oracle.assemble_rows(nodes, tris, alpha, T, n_steps, np.arange(len(tris)), q, m,
+                                          with_sums=True)
+    h = T / n_steps
+    check_blocks(V.transpose(1, 0, 2), Vo, SV, h, "V")
+    check_blocks(K.transpose(1, 0, 2), Ko, SK, h, "K")
+
+
+@pytest.mark.parametrize("nf", [1, 2])
+def test_icosphere_all_pair_classes(nf):
+    """icosahedron (every pair touches at nf = 1) and its 80-triangle refinement."""
+    nodes, tris = workloads.icosphere(nf)
+    alpha, T, n_steps = 1.3, 0.4, 5
+    _, V, K = gpu_assemble(nodes, tris, alpha, T, n_steps)
+    Vo, Ko, SV, SK = oracle.assemble_rows(nodes, tris, alpha, T, n_steps, np.arange(len(tris)),
+                                          with_sums=True)
+    h = T / n_steps
+    check_blocks(V.transpose(1, 0, 2), Vo, SV, h, "V")
+    check_blocks(K.transpose(1, 0, 2), Ko, SK, h, "K")
+
+
+def test_v_only_and_f32_storage():
+    nodes, tris = workloads.cube_mesh(2)
+    alpha, T, n = 1.0, 0.6, 6
+    _, V64, _ = gpu_assemble(nodes, tris, alpha, T, n, k=False)
+    _, V32, K32 = gpu_assemble(nodes, tris, alpha, T, n, storage=capi.STB_STORE_F32)
+    Vo, Ko, SV, SK = oracle.assemble_rows(nodes, tris, alpha, T, n, np.arange(len(tris)), with_sums=True)
+    h = T / n
+    check_blocks(V64.transpose(1, 0, 2), Vo, SV, h, "V64")
+    # storage rounding to FP32 adds at most 2^-24 relative per entry
+    check_blocks(V32.transpose(1, 0, 2), Vo, SV, h, "V32", extra_rel=2.0 ** -24)
+    check_blocks(K32.transpose(1, 0, 2), Ko, SK, h, "K32", extra_rel=2.0 ** -24)
+
+
+@pytest.mark.slow
+def test_c2_sampled_rows():
+    """cube, 3072 triangles, 64 steps, alpha = 0.5: the full-size assembly in
+    the launch configuration bench.py times, checked on sampled rows."""
+    wl = workloads.workload("cube3072_e64", alpha=0.5)
+    nodes, tris, alpha, T, n = wl["nodes"], wl["tris"], wl["alpha"], wl["T"], wl["n_steps"]
+    _, V, K = gpu_assemble(nodes, tris, alpha, T, n)
+    rows = np.array([0, 1537, 3071])
+    Vo, Ko, SV, SK = oracle.assemble_rows(nodes, tris, alpha, T, n, rows, with_sums=True)
+    h = T / n
+    check_blocks(V[:, rows].transpose(1, 0, 2), Vo, SV, h, "V")
+    check_blocks(K[:, rows].transpose(1, 0, 2), Ko, SK, h, "K")
+    # symmetry of V over the whole matrix (rule shared by (l,j) and (j,l))
+    for d in (0, 1, 63):
+        A = V[d]
+        assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max() + 64 * EPS * np.abs(A).max()
+
+
+def test_toeplitz_matvec_vs_oracle():
+    rng = np.random.default_rng(7)
+    E, n_steps, nrhs = 150, 11, 3
+    A = rng.normal(size=(n_steps, E, E))
+    x = rng.normal(size=(nrhs, n_steps, E))
+    y0 = rng.normal(size=(nrhs, n_steps, E))
+    ref = oracle.toeplitz_matvec(A, x)
+    for storage, dt in ((capi.STB_STORE_F64, torch.float64), (capi.STB_STORE_F32, torch.float32)):
+        Ad = torch.tensor(A, dtype=dt, device="cuda")
+        Aref = Ad.double().cpu().numpy()
+        refs = oracle.toeplitz_matvec(Aref, x) if storage == capi.STB_STORE_F32 else ref
+        xd = torch.tensor(x, device="cuda")
+        yd = torch.tensor(y0, device="cuda")
+        ws = torch.empty(capi.stb_toeplitz_workspace_size(E, n_steps, nrhs), dtype=torch.uint8,
+                         device="cuda")
+        capi.stb_toeplitz_matvec(Ad, storage, E, n_steps, nrhs, xd, 0.5, yd, ws)
+        got = yd.cpu().numpy()
+        expect = 0.5 * y0 + refs
+        scale = np.abs(Aref).max() * np.abs(x).max() * E * n_steps
+        assert np.abs(got - expect).max() <= 4 * EPS * scale
+
+
+@pytest.fixture(scope="module")
+def c1_problem():
+    wl = workloads.workload("cube192_e16")
+    nodes, tris, alpha, T, n = wl["nodes"], wl["tris"], wl["alpha"], wl["T"], wl["n_steps"]
+    Vo, Ko = oracle.assemble(nodes, tris, alpha, T, n)
+    return dict(wl=wl, Vo=Vo, Ko=Ko)
+
+
+def test_projection_rhs_solve_error_vs_oracle(c1_problem):
+    wl = c1_problem["wl"]
+    nodes, tris, alpha, T, n, src = (wl["nodes"], wl["tris"], wl["alpha"], wl["T"], wl["n_steps"],
+                                     wl["sources"])
+    Vo, Ko = c1_problem["Vo"], c1_problem["Ko"]
+    prob = pipeline.DirichletProblem(nodes, tris, alpha, T, n, src)
+    # projection
+    prob.project()
+    go = oracle.project_dirichlet(nodes, tris, alpha, T, n, src)
+    g = prob.g.cpu().numpy()
+    assert np.abs(g - go).max() <= 1e-13 * np.abs(go).max()
+    # right-hand side from the oracle's K and g
+    prob.K.copy_(torch.tensor(Ko))
+    prob.g.copy_(torch.tensor(go))
+    prob.rhs()
+    area, _ = oracle.triangle_geometry(nodes, tris)
+    fo = oracle.dirichlet_rhs(area, Ko, go, T)
+    f = prob.f.cpu().numpy()
+    assert np.abs(f - fo).max() <= 1e-13 * np.abs(fo).max() + 64 * EPS * np.abs(go).max() * np.abs(Ko).sum(axis=(0, 2)).max()
+    # solve from the oracle's V and f
+    prob.V.copy_(torch.tensor(Vo))
+    prob.f.copy_(torch.tensor(fo))
+    prob.solve()
+    wo = oracle.dirichlet_solve(Vo, fo)
+    w = prob.w.cpu().numpy()
+    # forward error of two backward-stable solves: a small multiple of
+    # cond(V_h) eps, V_h the full lower block-triangular matrix
+    E = len(tris)
+    M = np.zeros((n * E, n * E))
+    for k in range(n):
+        for i in range(k + 1):
+            M[k * E:(k + 1) * E, i * E:(i + 1) * E] = Vo[k - i]
+    kappa = np.linalg.cond(M)
+    rel = np.linalg.norm(w - wo) / np.linalg.norm(wo)
+    assert rel <= 16 * kappa * EPS, (rel, kappa)
+    # error norm of the same w
+    prob.w.copy_(torch.tensor(wo))
+    prob.error()
+    e2, r2 = oracle.neumann_error(nodes, tris, alpha, T, n, src, wo)
+    out = prob.err.cpu().numpy()
+    assert abs(out[0] - e2) <= 1e-12 * r2 and abs(out[1] - r2) <= 1e-12 * r2
+    print("C1 solve: rel diff %.2e, cond(V_h) %.2e" % (rel, kappa))
+
+
+def test_full_pipeline_matches_oracle_pipeline(c1_problem):
+    wl = c1_problem["wl"]
+    nodes, tris, alpha, T, n, src = (wl["nodes"], wl["tris"], wl["alpha"], wl["T"], wl["n_steps"],
+                                     wl["sources"])
+    Vo, Ko = c1_problem["Vo"], c1_problem["Ko"]
+    prob = pipeline.DirichletProblem(nodes, tris, alpha, T, n, src)
+    n0 = capi.stb_launch_count()
+    prob.run()
+    torch.cuda.synchronize()
+    assert capi.stb_launch_count() > n0
+    area, _ = oracle.triangle_geometry(nodes, tris)
+    go = oracle.project_dirichlet(nodes, tris, alpha, T, n, src)
+    wo = oracle.dirichlet_solve(Vo, oracle.dirichlet_rhs(area, Ko, go, T))
+    w = prob.w.cpu().numpy()
+    assert np.linalg.norm(w - wo) / np.linalg.norm(wo) < 1e-8
+    e2, r2 = oracle.neumann_error(nodes, tris, alpha, T, n, src, wo)
+    assert abs(prob.relative_error() - math.sqrt(e2 / r2)) < 1e-8
+
+
+def test_not_spd_is_reported():
+    nodes, tris = workloads.cube_mesh(1)
+    mesh = capi.Mesh(nodes, tris)
+    p = capi.stb_default_params(1.0, 1.0, 3)
+    E = mesh.n_tris
+    V = torch.eye(E, dtype=torch.float64, device="cuda").repeat(3, 1, 1)
+    V[0, 5, 5] = -1.0
+    f = torch.ones((1, 3, E), dtype=torch.float64, device="cuda")
+    w = torch.empty_like(f)
+    ws = torch.empty(capi.stb_solve_workspace_size(mesh, p, 1), dtype=torch.uint8, device="cuda")
+    with pytest.raises(capi.StbError) as ei:
+        capi.stb_dirichlet_solve(mesh, p, V, f, 1, w, ws)
+    assert ei.value.code == -5
+
+
+def test_workspace_errors():
+    nodes, tris = workloads.cube_mesh(1)
+    mesh = capi.Mesh(nodes, tris)
+    p = capi.stb_default_params(1.0, 1.0, 3)
+    E = mesh.n_tris
+    V = torch.empty((3, E, E), dtype=torch.float64, device="cuda")
+    need = capi.stb_assemble_workspace_size(mesh, p)
+    small = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(capi.StbError) as ei:
+        capi.stb_assemble(mesh, p, V, None, small)
+    assert ei.value.code == -8
+    big = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    with pytest.raises(capi.StbError) as ei:
+        capi.stb_assemble(mesh, p, V, None, big[1:need + 1])  # misaligned view
+    assert ei.value.code == -8
