@@ -41,7 +41,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 flops (DADD + DMUL + 2 DFMA, from ncu's SASS op counters) per
 # separated-pair quadrature-point evaluation at one time level i_t >= 1 of
 # k_regular_f64, see profiles/.
-FP64_FLOPS_PER_EVAL = None
+FP64_FLOPS_PER_EVAL = 137.34
+# MUFU (XU) pipe: 16 ex2 per SM per clock.
+MUFU_PEAK_TEX2 = 152 * 16 * 2.07e9 / 1e12
 
 
 def parse():
@@ -55,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
 
 
@@ -159,6 +163,36 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _roofline(name, trace_entry, ms_step, n_reg_pairs, nq, n_steps):
+    """Roofline of the step's dominant kernel from the live trace."""
+    cnt, tot = trace_entry
+    launch_ms = tot / cnt
+    roof = {"kernel": name, "launch_ms": launch_ms, "share_of_step": tot / ms_step, "traffic": None}
+    if name == "k_regular_f64":
+        evals = float(n_reg_pairs) * nq * nq * n_steps  # levels 1..E_t
+        roof.update({"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                     "peak_source": "FP64 FMA pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz "
+                                    "(measured 1.255 TFLOP/s, nominal 1.25)",
+                     "units_per_launch": evals, "unit_name": "separated-pair point-level evaluations"})
+        if FP64_FLOPS_PER_EVAL:
+            ach = FP64_FLOPS_PER_EVAL * evals / (launch_ms / 1e3) / 1e12
+            roof.update({"achieved": ach, "frac": ach / FP64_PEAK_TFLOPS})
+    elif name == "k_regular_mixed":
+        # exp2 evaluations: 6 on interval k = 1 and MIX_NG = 4 on every interval
+        # k = 2..E_t-1, each interval evaluated by the two chunks that share it
+        chunks = max(0, (n_steps - 2 + 15) // 16)
+        nodes = 6 + 4 * max(0, n_steps - 2) + 4 * max(0, chunks - 1)
+        ex2 = float(n_reg_pairs) * nq * nq * nodes
+        roof.update({"bound": "alu", "unit": "Tex2/s", "peak": MUFU_PEAK_TEX2,
+                     "peak_source": "MUFU pipe: 152 SM x 16 ex2/clk x 2.07 GHz",
+                     "units_per_launch": ex2, "unit_name": "MUFU.EX2 time-node evaluations"})
+        ach = ex2 / (launch_ms / 1e3) / 1e12
+        roof.update({"achieved": ach, "frac": ach / MUFU_PEAK_TEX2})
+    else:
+        roof.update({"bound": None, "achieved": None, "peak": None, "frac": None})
+    return roof
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -173,8 +207,12 @@ def run_gpu(args):
     alphas = [float(a) for a in args.alphas.split(",")]
     E, n = len(wl["tris"]), wl["n_steps"]
     nodes, tris, src = wl["nodes"], wl["tris"], wl["sources"]
+    mixed = args.precision == "mixed"
+    prec = capi.STB_PREC_MIXED if mixed else capi.STB_PREC_FP64
+    storage = capi.STB_STORE_F32 if mixed else capi.STB_STORE_F64
     mesh = capi.Mesh(nodes, tris)
-    probs = [pipeline.DirichletProblem(nodes, tris, a, wl["T"], n, src, mesh=mesh) for a in alphas]
+    probs = [pipeline.DirichletProblem(nodes, tris, a, wl["T"], n, src, mesh=mesh, precision=prec,
+                                       storage=storage) for a in alphas]
     stream = torch.cuda.current_stream()
 
     def step():
@@ -211,33 +249,62 @@ def run_gpu(args):
     entries = 2.0 * n * E * E * len(alphas)
     value = world * entries * args.steps / (ms / 1e3)
     rel_err = [p.relative_error() for p in probs]
+    n_reg_pairs = E * E - 2 * mesh.n_touching + E  # ordered separated pairs
+    name = max(trace.items(), key=lambda kv: kv[1][1])[0]
+    roof = _roofline(name, trace[name], ms / 1.0, n_reg_pairs, 3, n)
 
-    # block-Toeplitz matvec (FP64) on the assembled V of the first problem
+    # block-Toeplitz matvec (FP64 arithmetic) on the assembled V of the first problem
     p0 = probs[0]
     ws = torch.empty(capi.stb_toeplitz_workspace_size(E, n, p0.nrhs), dtype=torch.uint8, device="cuda")
     y = torch.empty_like(p0.w)
-    capi.stb_toeplitz_matvec(p0.V, capi.STB_STORE_F64, E, n, p0.nrhs, p0.w, 0.0, y, ws)
+    capi.stb_toeplitz_matvec(p0.V, storage, E, n, p0.nrhs, p0.w, 0.0, y, ws)
     torch.cuda.synchronize()
     a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 5
     a_.record(stream)
     for _ in range(reps):
-        capi.stb_toeplitz_matvec(p0.V, capi.STB_STORE_F64, E, n, p0.nrhs, p0.w, 0.0, y, ws)
+        capi.stb_toeplitz_matvec(p0.V, storage, E, n, p0.nrhs, p0.w, 0.0, y, ws)
     b_.record(stream)
     torch.cuda.synchronize()
     mv_ms = a_.elapsed_time(b_) / reps
     mv_tflops = float(E) * E * n * (n + 1) * p0.nrhs / (mv_ms / 1e3) / 1e12
+
+    # the other precision: FP64 assembly of one problem for "mixed vs FP64"
+    cmp = None
+    if mixed and not args.no_fp64_compare:
+        pf = pipeline.DirichletProblem(nodes, tris, alphas[0], wl["T"], n, src, mesh=mesh)
+        pf.assemble(stream)
+        torch.cuda.synchronize()
+        a_.record(stream)
+        pf.assemble(stream)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        f_ms = a_.elapsed_time(b_)
+        # error of the mixed blocks against these FP64 blocks (per block, relative Frobenius)
+        errs_v = [float(torch.linalg.norm(probs[0].V[d].double() - pf.V[d]) / torch.linalg.norm(pf.V[d]))
+                  for d in range(n)]
+        errs_k = [float(torch.linalg.norm(probs[0].K[d].double() - pf.K[d]) / torch.linalg.norm(pf.K[d]))
+                  for d in range(n)]
+        mixed_ms = trace.get("k_regular_mixed", (1, 0.0))[1] + trace.get("k_singular_mixed", (1, 0.0))[1]
+        mixed_ms /= max(1, trace.get("k_regular_mixed", (1, 0))[0])
+        cmp = {"fp64_assembly_ms": f_ms, "fp64_assembly_entries_per_s": 2.0 * n * E * E / (f_ms / 1e3),
+               "mixed_assembly_ms": mixed_ms,
+               "mixed_assembly_entries_per_s": 2.0 * n * E * E / (mixed_ms / 1e3) if mixed_ms else None,
+               "alpha": alphas[0], "mixed_vs_fp64_max_block_rel_err": {"V": max(errs_v), "K": max(errs_k)}}
+        del pf
 
     # end to end through the public API from host buffers (mesh, sources in;
     # solution and error norms out)
     e2e = None
     if not args.no_e2e:
         h2d = d2h = 0
+        n_e2e = max(1, min(args.steps, 2))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(max(1, min(args.steps, 2))):
+        for _ in range(n_e2e):
             for a in alphas:
-                pr = pipeline.DirichletProblem(nodes, tris, a, wl["T"], n, src)
+                pr = pipeline.DirichletProblem(nodes, tris, a, wl["T"], n, src, precision=prec,
+                                               storage=storage)
                 pr.run(stream)
                 w_host = pr.w.cpu()
                 err_host = pr.err.cpu()
@@ -246,35 +313,22 @@ def run_gpu(args):
                 del pr
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        n_e2e = max(1, min(args.steps, 2))
         e2e = {"value": world * entries * n_e2e / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": h2d // n_e2e, "d2h_bytes_per_step": d2h // n_e2e}
 
-    # roofline of the dominant kernel from the live trace
-    name, (cnt, tot) = max(trace.items(), key=lambda kv: kv[1][1])
-    n_reg_pairs = E * E - mesh.n_touching * 2 + E  # ordered separated pairs
-    q2 = 3 * 3
-    evals = float(n_reg_pairs) * q2 * q2 * n  # levels 1..E_t per launch
-    roof = {"kernel": name, "bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
-            "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (nominal FP64 1.25 TFLOP/s)",
-            "launch_ms": tot / cnt, "share_of_step": tot / ms, "evaluations_per_launch": evals,
-            "traffic": None}
-    if name == "k_regular_f64" and FP64_FLOPS_PER_EVAL:
-        achieved = FP64_FLOPS_PER_EVAL * evals / (tot / cnt / 1e3) / 1e12
-        roof.update({"achieved": achieved, "frac": achieved / FP64_PEAK_TFLOPS})
-    else:
-        roof.update({"achieved": None, "frac": None,
-                     "evals_per_s": evals / (tot / cnt / 1e3)})
-
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if mixed else "f64",
+            "data": "synthetic",
             "config": {"workload": args.workload, "E": E, "n_steps": n, "alphas": alphas,
-                       "quad_regular": 3, "quad_singular": 4, "precision": "fp64",
+                       "quad_regular": 3, "quad_singular": 4,
+                       "precision": "mixed (FP32 points, stated block error <= 2e-6; FP64 solve)"
+                       if mixed else "fp64",
+                       "storage": "f32" if mixed else "f64",
                        "l2": "no flush: every step writes %.1f GB of V/K blocks (>> 129 MB L2)"
-                             % (2 * 8 * n * E * E * len(alphas) / 1e9),
+                             % (2 * (4 if mixed else 8) * n * E * E * len(alphas) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "matvec_tflops": mv_tflops, "matvec_ms": mv_ms,
+            "mixed_vs_fp64": cmp, "matvec_tflops": mv_tflops, "matvec_ms": mv_ms,
             "rel_l2_error_w": rel_err, "gpu_launches": launches,
             "kernels_ms": {k: v[1] for k, v in trace.items()}, "roofline": roof, "e2e": e2e}
     if rank == 0:

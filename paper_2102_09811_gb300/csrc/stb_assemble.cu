@@ -22,7 +22,7 @@
 #include <cstring>
 #include <vector>
 
-#include "stb_internal.h"
+#include "stb_assemble.h"
 
 namespace stb {
 
@@ -496,15 +496,6 @@ k_singular_f64(const double *__restrict__ geo, const TouchPair *__restrict__ pai
 }
 
 // ----------------------------------------------------------------- driver ---
-struct AssemblyLayout {
-    double *geo;
-    int32_t *row_count, *row_off;
-    TouchPair *pairs;
-    double *rule, *ss, *levels;
-    size_t ss_n[4];
-    size_t bytes;
-};
-
 static AssemblyLayout layout(const Mesh &m, const stb_params &p, void *ws, size_t cap) {
     Carve c(ws, cap);
     AssemblyLayout L{};
@@ -512,14 +503,21 @@ static AssemblyLayout layout(const Mesh &m, const stb_params &p, void *ws, size_
     L.row_count = c.take<int32_t>(m.n_tris);
     L.row_off = c.take<int32_t>(m.n_tris + 1);
     L.pairs = c.take<TouchPair>(m.n_touch > 0 ? m.n_touch : 1);
-    L.rule = c.take<double>(3 * (size_t)p.quad_regular * p.quad_regular);
     size_t tot = 0;
     for (int cls = 1; cls <= 3; ++cls) {
         L.ss_n[cls] = ss_rule_size(cls, p.quad_singular);
         tot += 5 * L.ss_n[cls];
     }
-    L.ss = c.take<double>(tot);
-    L.levels = c.take<double>((size_t)(p.n_steps + 1) * LV_STRIDE);
+    // one contiguous table region (uploaded with one copy)
+    if (p.precision == STB_PREC_FP64) {
+        L.rule = c.take<double>(3 * (size_t)p.quad_regular * p.quad_regular);
+        L.ss = c.take<double>(tot);
+        L.levels = c.take<double>((size_t)(p.n_steps + 1) * LV_STRIDE);
+    } else {
+        L.mrule = c.take<float>(4 * (size_t)p.quad_regular * p.quad_regular);
+        L.mss = c.take<float>(tot);
+        L.mnodes = c.take<float>(mixed_node_floats(p.n_steps));
+    }
     L.bytes = c.off;
     return L;
 }
@@ -534,8 +532,10 @@ static stb_status check_params(const stb_params *p) {
         return fail(STB_ERR_INVALID_ARG, "quad_regular must be in [1, 16]");
     if (p->quad_singular < 1 || p->quad_singular > 12)
         return fail(STB_ERR_INVALID_ARG, "quad_singular must be in [1, 12]");
-    if (p->precision != STB_PREC_FP64)
-        return fail(STB_ERR_INVALID_ARG, "precision %d is not available", p->precision);
+    if (p->precision != STB_PREC_FP64 && p->precision != STB_PREC_MIXED)
+        return fail(STB_ERR_INVALID_ARG, "precision must be STB_PREC_FP64 or STB_PREC_MIXED");
+    if (p->precision == STB_PREC_MIXED && p->n_steps > 1024)
+        return fail(STB_ERR_INVALID_ARG, "mixed precision supports n_steps <= 1024");
     if (p->storage != STB_STORE_F64 && p->storage != STB_STORE_F32)
         return fail(STB_ERR_INVALID_ARG, "storage must be STB_STORE_F64 or STB_STORE_F32");
     if (p->reserved != 0) return fail(STB_ERR_INVALID_ARG, "reserved must be 0");
@@ -615,7 +615,24 @@ extern "C" stb_status stb_assemble(const stb_mesh *mesh, const stb_params *param
     cudaStream_t s = (cudaStream_t)stream;
     upload_psi_coeffs(s);
 
-    // host tables: regular rule, regularised rules, level constants
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    int32_t *status = status_word(ws);
+    if (params->precision == STB_PREC_MIXED) {
+        std::vector<float> rule, ss, nodes, host;
+        mixed_tables(*params, rule, ss, nodes);
+        host = rule;
+        host.resize((size_t)(L.mss - L.mrule), 0.f);
+        host.insert(host.end(), ss.begin(), ss.end());
+        host.resize((size_t)(L.mnodes - L.mrule), 0.f);
+        host.insert(host.end(), nodes.begin(), nodes.end());
+        STB_CUDA(cudaMemcpyAsync(L.mrule, host.data(), host.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, s));
+        STB_CUDA(cudaMemsetAsync(L.pairs, 0xff, sizeof(TouchPair) * (m.n_touch > 0 ? m.n_touch : 1), s));
+        if ((st = launch_geometry(m, L.geo, s))) return st;
+        if ((st = launch_classify(m, L.row_count, L.row_off, L.pairs, status, s))) return st;
+        return run_assembly_mixed(m, *params, V, K, L, s);
+    }
+    // FP64 host tables: regular rule, regularised rules, level constants
     std::vector<double> host;
     {
         std::vector<double> a, b, c, d, w;
@@ -652,10 +669,8 @@ extern "C" stb_status stb_assemble(const stb_mesh *mesh, const stb_params *param
             host.insert(host.end(), lvv, lvv + LV_STRIDE);
         }
     }
-    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
     STB_CUDA(cudaMemcpyAsync(L.rule, host.data(), host.size() * sizeof(double),
                              cudaMemcpyHostToDevice, s));
-    int32_t *status = status_word(ws);
     STB_CUDA(cudaMemsetAsync(L.pairs, 0xff, sizeof(TouchPair) * (m.n_touch > 0 ? m.n_touch : 1), s));
     if ((st = launch_geometry(m, L.geo, s))) return st;
     if ((st = launch_classify(m, L.row_count, L.row_off, L.pairs, status, s))) return st;

@@ -1,0 +1,499 @@
+// stb_assemble_mixed.cu -- mixed-precision assembly of V^d and K^d: every
+// quadrature point in FP32, no FP64 arithmetic in the hot loops.
+//
+// The FP64 path differences the closed-form antiderivatives (eq. vd), which
+// cancels: V^d is about h^2 G while the three terms are about G^{dtau dt},
+// and for far pairs at small d the true value is exponentially small.  In
+// FP32 that loses every digit, so this path evaluates the same integrals in
+// cancellation-free forms:
+//  * d = 0, 1 from the closed forms with the part that is linear in delta
+//    (exactly annihilated by the second difference) removed analytically:
+//      V^0 = H(h),  V^1 = H(2h) - 2 H(h),
+//      H(delta) = sqrt(delta)/(4 pi alpha^{3/2}) [ (x + 1/(2x)) erfc(x) - exp(-x^2)/sqrt(pi) ],
+//    written for x(2h) < 1 with H - delta/(4 pi alpha rho) =
+//      sqrt(delta)/(4 pi alpha^{3/2}) [ x erfc(x) - erf(x)/(2x) - exp(-x^2)/sqrt(pi) ],
+//    and K^0, K^1 from eq. K0 / eq. K_d in the same way (see k_d01);
+//  * d >= 2 from the definition eq. V_d reduced to one time variable,
+//      V^d(r) = int_{-h}^{h} (h - |s|) G(r, dh + s) ds,   K^d: G -> (r.n_y)/(2 delta) G,
+//    by Gauss-Legendre on every interval [kh, (k+1)h] (6 nodes for k = 1,
+//    4 for k >= 2); one exp2 per node feeds two blocks (d = k, k + 1).
+// The regularised rules of touching pairs are stored in difference form so
+// that x - y keeps its relative accuracy as it shrinks.
+#include <cmath>
+#include <vector>
+
+#include "stb_assemble.h"
+
+namespace stb {
+
+struct MixConsts {
+    float c1, c2;    // 1/(2 sqrt(alpha h)), 1/(2 sqrt(2 alpha h))
+    float pV1, pV2;  // sqrt(h)/(4 pi alpha^{3/2}), sqrt(2h)/(4 pi alpha^{3/2})
+    float pK;        // 1/(4 pi alpha)
+};
+
+constexpr float ISQRTPI = 0.5641895835477563f;  // 1/sqrt(pi)
+
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// psi(x) = erf(x)/2 - erf(x)/(4x^2) + exp(-x^2)/(2 sqrt(pi) x) (bracket of eq. dG)
+__device__ __forceinline__ float psi32(float x, float erfx, float ex) {
+    if (x < 0.5f) {
+        // (2/sqrt(pi)) sum_m (-1)^m x^{2m+1} / (m! (2m+1)(2m+3)), m <= 6
+        float x2 = x * x;
+        float p = -1.0f / (720.0f * 13.0f * 15.0f);
+        p = fmaf(p, x2, 1.0f / (120.0f * 11.0f * 13.0f));
+        p = fmaf(p, x2, -1.0f / (24.0f * 9.0f * 11.0f));
+        p = fmaf(p, x2, 1.0f / (6.0f * 7.0f * 9.0f));
+        p = fmaf(p, x2, -1.0f / (2.0f * 5.0f * 7.0f));
+        p = fmaf(p, x2, 1.0f / (3.0f * 5.0f));
+        p = fmaf(p, x2, 1.0f / 3.0f);
+        return 2.0f * ISQRTPI * x * p;
+    }
+    return 0.5f * erfx - erfx / (4.0f * x * x) + 0.5f * ISQRTPI * ex / x;
+}
+
+// Blocks d = 0 and d = 1 of one quadrature point, without the factor of the
+// quadrature weight: V^0, V^1 and K^0 / (r.n), K^1 / (r.n).
+__device__ __forceinline__ void k_d01(float rho, float irho, const MixConsts &g, float &v0,
+                                      float &v1, float &k0, float &k1) {
+    const float x1 = rho * g.c1, x2 = rho * g.c2;
+    const float ix1 = irho / g.c1, ix2 = irho / g.c2;
+    const float ec1 = erfcf(x1), ec2 = erfcf(x2);
+    const float ee1 = expf(-x1 * x1), ee2 = expf(-x2 * x2);
+    const float H1 = g.pV1 * ((x1 + 0.5f * ix1) * ec1 - ee1 * ISQRTPI);
+    v0 = H1;
+    const float kf = g.pK * irho;  // K = r.n / (4 pi alpha rho) * bracket
+    k0 = kf * (ec1 * (0.25f * ix1 * ix1 - 0.5f) + 0.5f * ISQRTPI * ee1 * ix1);
+    if (x2 < 1.0f) {
+        const float ef1 = erff(x1), ef2 = erff(x2);
+        const float Hh1 = g.pV1 * (x1 * ec1 - 0.5f * ef1 * ix1 - ee1 * ISQRTPI);
+        const float Hh2 = g.pV2 * (x2 * ec2 - 0.5f * ef2 * ix2 - ee2 * ISQRTPI);
+        v1 = Hh2 - 2.0f * Hh1;
+        k1 = -kf * (2.0f * psi32(x1, ef1, ee1) - psi32(x2, ef2, ee2) - 0.5f);
+    } else {
+        const float H2 = g.pV2 * ((x2 + 0.5f * ix2) * ec2 - ee2 * ISQRTPI);
+        v1 = H2 - 2.0f * H1;
+        // 1/2 - psi(x) minus its part linear in delta: erfc(x)(1/2 - 1/(4x^2)) - exp(-x^2)/(2 sqrt(pi) x)
+        const float c1h = ec1 * (0.5f - 0.25f * ix1 * ix1) - 0.5f * ISQRTPI * ee1 * ix1;
+        const float c2h = ec2 * (0.5f - 0.25f * ix2 * ix2) - 0.5f * ISQRTPI * ee2 * ix2;
+        k1 = -kf * (-2.0f * c1h + c2h);
+    }
+}
+
+template <class T> __device__ __forceinline__ void store_m(T *p, float v);
+template <> __device__ __forceinline__ void store_m<double>(double *p, float v) { *p = (double)v; }
+template <> __device__ __forceinline__ void store_m<float>(float *p, float v) { *p = v; }
+
+constexpr int MREG_THREADS = 128;
+constexpr int MAX_RULE_M = 256;
+
+// ------------------------------------------------------ separated pairs ---
+template <int CH, class OutT>
+__global__ void __launch_bounds__(MREG_THREADS)
+k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E,
+                const float *__restrict__ rule, int nq, const float *__restrict__ nodes,
+                int n_nodes_f, int n_steps, MixConsts g, OutT *__restrict__ V,
+                OutT *__restrict__ K) {
+    extern __shared__ float smf[];
+    float4 *xa = reinterpret_cast<float4 *>(smf);  // x_a - P0_l and w_a
+    float *nd = smf + 4 * MAX_RULE_M;             // time nodes
+    const int l = blockIdx.y;
+    const int j = blockIdx.x * MREG_THREADS + threadIdx.x;
+    const double *gl = geo + (size_t)l * GEO_STRIDE;
+    for (int a = threadIdx.x; a < nq; a += MREG_THREADS) {
+        double s1 = rule[4 * a], s2 = rule[4 * a + 1];
+        double p[3];
+        for (int c = 0; c < 3; ++c)
+            p[c] = s1 * (gl[GEO_V1 + c] - gl[GEO_V0 + c]) + s2 * (gl[GEO_V2 + c] - gl[GEO_V1 + c]);
+        xa[a] = make_float4((float)p[0], (float)p[1], (float)p[2], rule[4 * a + 2]);
+    }
+    for (int i = threadIdx.x; i < n_nodes_f; i += MREG_THREADS) nd[i] = nodes[i];
+    __syncthreads();
+    if (j >= E) return;
+    const int32_t tl[3] = {tris[3 * l], tris[3 * l + 1], tris[3 * l + 2]};
+    const int32_t tj[3] = {tris[3 * j], tris[3 * j + 1], tris[3 * j + 2]};
+    {
+        bool t = false;
+        for (int i = 0; i < 3; ++i) t |= (tl[i] == tj[0]) | (tl[i] == tj[1]) | (tl[i] == tj[2]);
+        if (t) return;
+    }
+    const double *gj = geo + (size_t)j * GEO_STRIDE;
+    float D[3], B1[3], B2[3], n[3];
+    for (int c = 0; c < 3; ++c) {
+        D[c] = (float)(gl[GEO_V0 + c] - gj[GEO_V0 + c]);
+        B1[c] = (float)(gj[GEO_V1 + c] - gj[GEO_V0 + c]);
+        B2[c] = (float)(gj[GEO_V2 + c] - gj[GEO_V1 + c]);
+        n[c] = (float)gj[GEO_N + c];
+    }
+    const float scale = (float)(4.0 * gl[GEO_AREA] * gj[GEO_AREA]);
+    const size_t EE = (size_t)E * E, ij = (size_t)l * E + j;
+
+    // pass 1: blocks 0 and 1 (closed forms) and the k = 1 interval of block 2
+    float v0 = 0.f, v1 = 0.f, k0 = 0.f, k1 = 0.f, v2 = 0.f, k2 = 0.f;
+    for (int b = 0; b < nq; ++b) {
+        const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
+        const float r0b = D[0] - (t1 * B1[0] + t2 * B2[0]);
+        const float r1b = D[1] - (t1 * B1[1] + t2 * B2[1]);
+        const float r2b = D[2] - (t1 * B1[2] + t2 * B2[2]);
+        for (int a = 0; a < nq; ++a) {
+            const float4 xq = xa[a];
+            const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
+            const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+            const float irho = rsqrtf(rr), rho = rr * irho;
+            const float rn = r0 * n[0] + r1 * n[1] + r2 * n[2];
+            const float w = xq.w * wb, wrn = w * rn;
+            float a0, a1, c0, c1;
+            k_d01(rho, irho, g, a0, a1, c0, c1);
+            v0 = fmaf(w, a0, v0);
+            v1 = fmaf(w, a1, v1);
+            k0 = fmaf(wrn, c0, k0);
+            k1 = fmaf(wrn, c1, k1);
+            if (n_steps > 2) {
+#pragma unroll
+                for (int q = 0; q < MIX_NG1; ++q) {
+                    const float *c = nd + q * MIX_NODE;
+                    const float e = ex2(rr * c[0]);
+                    v2 = fmaf(w * c[2], e, v2);
+                    k2 = fmaf(wrn * c[4], e, k2);
+                }
+            }
+        }
+    }
+    store_m(V + ij, scale * v0);
+    if (K) store_m(K + ij, scale * k0);
+    if (n_steps > 1) {
+        store_m(V + EE + ij, scale * v1);
+        if (K) store_m(K + EE + ij, scale * k1);
+    }
+
+    // blocks d >= 2 in chunks [d0, d0 + CH): intervals k = d0 - 1 .. d0 + CH - 1
+    for (int d0 = 2; d0 < n_steps; d0 += CH) {
+        float sv[CH], sk[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) sv[u] = sk[u] = 0.f;
+        if (d0 == 2) {
+            sv[0] = v2;
+            sk[0] = k2;
+        }
+        for (int b = 0; b < nq; ++b) {
+            const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
+            const float r0b = D[0] - (t1 * B1[0] + t2 * B2[0]);
+            const float r1b = D[1] - (t1 * B1[1] + t2 * B2[1]);
+            const float r2b = D[2] - (t1 * B1[2] + t2 * B2[2]);
+            for (int a = 0; a < nq; ++a) {
+                const float4 xq = xa[a];
+                const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
+                const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+                const float rn = r0 * n[0] + r1 * n[1] + r2 * n[2];
+                const float w = xq.w * wb, wrn = w * rn;
+#pragma unroll
+                for (int u = 0; u <= CH; ++u) {
+                    const int k = d0 - 1 + u;
+                    if (k < 2 || k > n_steps - 1) continue;
+                    const float *c = nd + (MIX_NG1 + (k - 2) * MIX_NG) * MIX_NODE;
+                    float tv_f = 0.f, tv_r = 0.f, tk_f = 0.f, tk_r = 0.f;
+#pragma unroll
+                    for (int q = 0; q < MIX_NG; ++q) {
+                        const float4 cq = *reinterpret_cast<const float4 *>(c + q * MIX_NODE);
+                        const float ckr = c[q * MIX_NODE + 4];
+                        const float e = ex2(rr * cq.x);
+                        tv_f = fmaf(cq.y, e, tv_f);
+                        tv_r = fmaf(cq.z, e, tv_r);
+                        tk_f = fmaf(cq.w, e, tk_f);
+                        tk_r = fmaf(ckr, e, tk_r);
+                    }
+                    if (u >= 1) {  // falling side: block d = k
+                        sv[u - 1] = fmaf(w, tv_f, sv[u - 1]);
+                        sk[u - 1] = fmaf(wrn, tk_f, sk[u - 1]);
+                    }
+                    if (u < CH && k + 1 < n_steps) {  // rising side: block d = k + 1
+                        sv[u] = fmaf(w, tv_r, sv[u]);
+                        sk[u] = fmaf(wrn, tk_r, sk[u]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int d = d0 + u;
+            if (d < n_steps) {
+                store_m(V + (size_t)d * EE + ij, scale * sv[u]);
+                if (K) store_m(K + (size_t)d * EE + ij, scale * sk[u]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------- touching pairs ---
+constexpr int MSS_THREADS = 128;
+
+struct MixSS {
+    const float *p0[4], *p1[4], *p2[4], *p3[4], *w[4];
+    int n[4];
+};
+
+template <int CH, class OutT>
+__global__ void __launch_bounds__(MSS_THREADS)
+k_singular_mixed(const double *__restrict__ geo, const TouchPair *__restrict__ pairs, int E,
+                 MixSS tab, const float *__restrict__ nodes, int n_steps, MixConsts g,
+                 OutT *__restrict__ V, OutT *__restrict__ K) {
+    __shared__ float red[MSS_THREADS / 32][3 * CH + 9];
+    __shared__ float fin[3 * CH + 9];
+    const TouchPair P = pairs[blockIdx.x];
+    const int a = P.a, b = P.b, cls = P.cls;
+    if (a < 0 || b < a || b >= E || cls < PAIR_VERTEX || cls > PAIR_IDENTICAL) return;
+    const double *ga = geo + (size_t)a * GEO_STRIDE, *gb = geo + (size_t)b * GEO_STRIDE;
+    // x - y = p0 X0 + p1 X1 + p2 X2 + p3 X3 (difference form of the rule)
+    float X[4][3], na[3], nb[3];
+    {
+        const int oa0 = P.perm & 3, oa1 = (P.perm >> 2) & 3, oa2 = (P.perm >> 4) & 3;
+        const int ob0 = (P.perm >> 6) & 3, ob1 = (P.perm >> 8) & 3, ob2 = (P.perm >> 10) & 3;
+        for (int c = 0; c < 3; ++c) {
+            const double A1 = ga[3 * oa1 + c] - ga[3 * oa0 + c], A2 = ga[3 * oa2 + c] - ga[3 * oa1 + c];
+            const double Bv1 = gb[3 * ob1 + c] - gb[3 * ob0 + c], Bv2 = gb[3 * ob2 + c] - gb[3 * ob1 + c];
+            if (cls == PAIR_IDENTICAL) {
+                X[0][c] = (float)-A1; X[1][c] = (float)-A2; X[2][c] = 0.f; X[3][c] = 0.f;
+            } else if (cls == PAIR_EDGE) {
+                X[0][c] = (float)-A1; X[1][c] = (float)A2; X[2][c] = (float)-Bv2; X[3][c] = 0.f;
+            } else {
+                X[0][c] = (float)A1; X[1][c] = (float)A2; X[2][c] = (float)-Bv1; X[3][c] = (float)-Bv2;
+            }
+            na[c] = (float)ga[GEO_N + c];
+            nb[c] = (float)gb[GEO_N + c];
+        }
+    }
+    const float scale = (float)(4.0 * ga[GEO_AREA] * gb[GEO_AREA]);
+    const bool ident = cls == PAIR_IDENTICAL;
+    const int npt = tab.n[cls];
+    const float *R0 = tab.p0[cls], *R1 = tab.p1[cls], *R2 = tab.p2[cls], *R3 = tab.p3[cls],
+                *W = tab.w[cls];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t EE = (size_t)E * E, iab = (size_t)a * E + b, iba = (size_t)b * E + a;
+
+    // entry (a,b): r = x - y, n_b; entry (b,a): r' = -r, n_a
+    auto point = [&](int p, float &rr, float &rab, float &rba, float &w) {
+        const float q0 = R0[p], q1 = R1[p], q2 = R2[p], q3 = R3[p];
+        float r[3];
+        for (int c = 0; c < 3; ++c) r[c] = q0 * X[0][c] + q1 * X[1][c] + q2 * X[2][c] + q3 * X[3][c];
+        rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        rab = r[0] * nb[0] + r[1] * nb[1] + r[2] * nb[2];
+        rba = -(r[0] * na[0] + r[1] * na[1] + r[2] * na[2]);
+        w = W[p];
+    };
+    auto reduce = [&](float *vals, int nv) {
+        for (int k = 0; k < nv; ++k) {
+            float v = vals[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < nv) {
+            float s = 0.f;
+            for (int wi = 0; wi < MSS_THREADS / 32; ++wi) s += red[wi][threadIdx.x];
+            fin[threadIdx.x] = scale * s;
+        }
+        __syncthreads();
+    };
+
+    // pass 1: blocks 0, 1 and the k = 1 interval of block 2
+    float z[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) z[i] = 0.f;
+    for (int p = threadIdx.x; p < npt; p += MSS_THREADS) {
+        float rr, rab, rba, w;
+        point(p, rr, rab, rba, w);
+        const float irho = rsqrtf(rr), rho = rr * irho;
+        float a0, a1, c0, c1;
+        k_d01(rho, irho, g, a0, a1, c0, c1);
+        z[0] = fmaf(w, a0, z[0]);
+        z[1] = fmaf(w, a1, z[1]);
+        z[2] = fmaf(w * rab, c0, z[2]);
+        z[3] = fmaf(w * rab, c1, z[3]);
+        z[4] = fmaf(w * rba, c0, z[4]);
+        z[5] = fmaf(w * rba, c1, z[5]);
+        if (n_steps > 2) {
+#pragma unroll
+            for (int q = 0; q < MIX_NG1; ++q) {
+                const float *c = nodes + q * MIX_NODE;
+                const float e = ex2(rr * c[0]);
+                z[6] = fmaf(w * c[2], e, z[6]);
+                z[7] = fmaf(w * rab * c[4], e, z[7]);
+                z[8] = fmaf(w * rba * c[4], e, z[8]);
+            }
+        }
+    }
+    reduce(z, 9);
+    if (threadIdx.x == 0) {
+        store_m(V + iab, fin[0]);
+        if (!ident) store_m(V + iba, fin[0]);
+        if (K) {
+            store_m(K + iab, ident ? 0.f : fin[2]);
+            if (!ident) store_m(K + iba, fin[4]);
+        }
+        if (n_steps > 1) {
+            store_m(V + EE + iab, fin[1]);
+            if (!ident) store_m(V + EE + iba, fin[1]);
+            if (K) {
+                store_m(K + EE + iab, ident ? 0.f : fin[3]);
+                if (!ident) store_m(K + EE + iba, fin[5]);
+            }
+        }
+    }
+    const float v2 = fin[6], ka2 = fin[7], kb2 = fin[8];  // already scaled
+    __syncthreads();
+
+    for (int d0 = 2; d0 < n_steps; d0 += CH) {
+        float acc[3 * CH];
+#pragma unroll
+        for (int i = 0; i < 3 * CH; ++i) acc[i] = 0.f;
+        for (int p = threadIdx.x; p < npt; p += MSS_THREADS) {
+            float rr, rab, rba, w;
+            point(p, rr, rab, rba, w);
+            const float wa = w * rab, wb = w * rba;
+#pragma unroll
+            for (int u = 0; u <= CH; ++u) {
+                const int k = d0 - 1 + u;
+                if (k < 2 || k > n_steps - 1) continue;
+                const float *c = nodes + (MIX_NG1 + (k - 2) * MIX_NG) * MIX_NODE;
+                float tv_f = 0.f, tv_r = 0.f, tk_f = 0.f, tk_r = 0.f;
+#pragma unroll
+                for (int q = 0; q < MIX_NG; ++q) {
+                    const float4 cq = *reinterpret_cast<const float4 *>(c + q * MIX_NODE);
+                    const float ckr = c[q * MIX_NODE + 4];
+                    const float e = ex2(rr * cq.x);
+                    tv_f = fmaf(cq.y, e, tv_f);
+                    tv_r = fmaf(cq.z, e, tv_r);
+                    tk_f = fmaf(cq.w, e, tk_f);
+                    tk_r = fmaf(ckr, e, tk_r);
+                }
+                if (u >= 1) {
+                    acc[u - 1] = fmaf(w, tv_f, acc[u - 1]);
+                    acc[CH + u - 1] = fmaf(wa, tk_f, acc[CH + u - 1]);
+                    acc[2 * CH + u - 1] = fmaf(wb, tk_f, acc[2 * CH + u - 1]);
+                }
+                if (u < CH && k + 1 < n_steps) {
+                    acc[u] = fmaf(w, tv_r, acc[u]);
+                    acc[CH + u] = fmaf(wa, tk_r, acc[CH + u]);
+                    acc[2 * CH + u] = fmaf(wb, tk_r, acc[2 * CH + u]);
+                }
+            }
+        }
+        reduce(acc, 3 * CH);
+        if (threadIdx.x == 0) {
+            for (int u = 0; u < CH; ++u) {
+                const int d = d0 + u;
+                if (d >= n_steps) break;
+                float bv = fin[u], ba = fin[CH + u], bb = fin[2 * CH + u];
+                if (d == 2) {
+                    bv += v2;
+                    ba += ka2;
+                    bb += kb2;
+                }
+                const size_t off = (size_t)d * EE;
+                store_m(V + off + iab, bv);
+                if (!ident) store_m(V + off + iba, bv);
+                if (K) {
+                    store_m(K + off + iab, ident ? 0.f : ba);
+                    if (!ident) store_m(K + off + iba, bb);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ host side ---
+void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<float> &ss,
+                  std::vector<float> &nodes) {
+    const double pi = 3.14159265358979323846, al = p.alpha, h = p.T / p.n_steps;
+    std::vector<double> a, b, c, d, w;
+    triangle_rule(p.quad_regular, a, b, w);
+    rule.clear();
+    for (size_t i = 0; i < w.size(); ++i) {
+        rule.push_back((float)a[i]);
+        rule.push_back((float)b[i]);
+        rule.push_back((float)w[i]);
+        rule.push_back(0.f);
+    }
+    ss.clear();
+    for (int cls = 1; cls <= 3; ++cls) {
+        ss_rule_diff(cls, p.quad_singular, a, b, c, d, w);
+        for (auto *v : {&a, &b, &c, &d, &w})
+            for (double x : *v) ss.push_back((float)x);
+    }
+    nodes.assign(mixed_node_floats(p.n_steps), 0.f);
+    auto put = [&](size_t slot, int k, double ug, double wg) {
+        const double delta = (k + ug) * h, a_ = std::pow(4.0 * pi * al * delta, -1.5);
+        const double wf = h * wg * h * (1.0 - ug) * a_, wr = h * wg * h * ug * a_;
+        float *q = nodes.data() + slot * MIX_NODE;
+        q[0] = (float)(-1.0 / (4.0 * al * delta) * 1.4426950408889634);  // log2(e)
+        q[1] = (float)wf;
+        q[2] = (float)wr;
+        q[3] = (float)(wf / (2.0 * delta));
+        q[4] = (float)(wr / (2.0 * delta));
+    };
+    std::vector<double> u1(MIX_NG1), w1(MIX_NG1), u(MIX_NG), wq(MIX_NG);
+    gauss_legendre01(MIX_NG1, u1.data(), w1.data());
+    gauss_legendre01(MIX_NG, u.data(), wq.data());
+    for (int q = 0; q < MIX_NG1; ++q) put(q, 1, u1[q], w1[q]);
+    for (int k = 2; k <= p.n_steps - 1; ++k)
+        for (int q = 0; q < MIX_NG; ++q) put(MIX_NG1 + (size_t)(k - 2) * MIX_NG + q, k, u[q], wq[q]);
+}
+
+template <class OutT>
+static stb_status run_mixed_t(const Mesh &m, const stb_params &p, OutT *V, OutT *K,
+                              const AssemblyLayout &L, cudaStream_t s) {
+    constexpr int CH = 16;
+    const int E = (int)m.n_tris;
+    const int nq = p.quad_regular * p.quad_regular;
+    const double pi = 3.14159265358979323846, al = p.alpha, h = p.T / p.n_steps;
+    MixConsts g;
+    g.c1 = (float)(1.0 / (2.0 * std::sqrt(al * h)));
+    g.c2 = (float)(1.0 / (2.0 * std::sqrt(2.0 * al * h)));
+    g.pV1 = (float)(std::sqrt(h) / (4.0 * pi * std::pow(al, 1.5)));
+    g.pV2 = (float)(std::sqrt(2.0 * h) / (4.0 * pi * std::pow(al, 1.5)));
+    g.pK = (float)(1.0 / (4.0 * pi * al));
+    const int nf = (int)mixed_node_floats(p.n_steps);
+    const size_t smem = sizeof(float) * (4 * MAX_RULE_M + (size_t)nf);
+    STB_CUDA(cudaFuncSetAttribute(k_regular_mixed<CH, OutT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((E + MREG_THREADS - 1) / MREG_THREADS, E);
+    count_launch(s);
+    k_regular_mixed<CH, OutT><<<grid, MREG_THREADS, smem, s>>>(L.geo, m.d_tris, E, L.mrule, nq,
+                                                               L.mnodes, nf, p.n_steps, g, V, K);
+    stb_status st = check_launch("k_regular_mixed");
+    if (st) return st;
+    if (m.n_touch > 0) {
+        MixSS tab{};
+        const float *base = L.mss;
+        for (int cls = 1; cls <= 3; ++cls) {
+            const size_t n = L.ss_n[cls];
+            tab.p0[cls] = base;
+            tab.p1[cls] = base + n;
+            tab.p2[cls] = base + 2 * n;
+            tab.p3[cls] = base + 3 * n;
+            tab.w[cls] = base + 4 * n;
+            tab.n[cls] = (int)n;
+            base += 5 * n;
+        }
+        count_launch(s);
+        k_singular_mixed<CH, OutT><<<(unsigned)m.n_touch, MSS_THREADS, 0, s>>>(
+            L.geo, L.pairs, E, tab, L.mnodes, p.n_steps, g, V, K);
+        if ((st = check_launch("k_singular_mixed"))) return st;
+    }
+    return STB_OK;
+}
+
+stb_status run_assembly_mixed(const Mesh &m, const stb_params &p, void *V, void *K,
+                              const AssemblyLayout &L, cudaStream_t s) {
+    if (p.storage == STB_STORE_F64)
+        return run_mixed_t<double>(m, p, (double *)V, (double *)K, L, s);
+    return run_mixed_t<float>(m, p, (float *)V, (float *)K, L, s);
+}
+
+}  // namespace stb

@@ -228,7 +228,8 @@ int ss_rule_size(int cls, int m) {
 //      jac = zeta^2 (1 - zeta) [* a]
 //  vertex (2 orderings of the Duffy radii, shared vertex s = t = 0):
 //      jac = zeta^3 a
-static void ss_point(int cls, int sub, const double u[4], double st[4], double &jac) {
+static void ss_point(int cls, int sub, const double u[4], double st[4], double &jac,
+                     double *diff = nullptr) {
     const double zt = u[0], L = 1.0 - zt;
     if (cls == PAIR_IDENTICAL) {
         const double v = u[1], p1 = u[2], p2 = u[3];
@@ -246,6 +247,11 @@ static void ss_point(int cls, int sub, const double u[4], double st[4], double &
         st[2] = st[0] + z1;
         st[3] = st[1] + z2;
         jac = zt * L * L * p1;
+        if (diff) {
+            diff[0] = z1;
+            diff[1] = z2;
+            diff[2] = diff[3] = 0.0;
+        }
     } else if (cls == PAIR_EDGE) {
         const double a = u[1], b = u[2], sg = u[3];
         double s1, s2, t2, du;  // du = t1 - s1
@@ -259,6 +265,12 @@ static void ss_point(int cls, int sub, const double u[4], double st[4], double &
         st[1] = s2;
         st[2] = s1 + du;
         st[3] = t2;
+        if (diff) {
+            diff[0] = du;
+            diff[1] = s2;
+            diff[2] = t2;
+            diff[3] = 0.0;
+        }
     } else {  // vertex
         const double a = u[1], p2 = u[2], q2 = u[3];
         const double S = sub == 0 ? zt : zt * a, R = sub == 0 ? zt * a : zt;
@@ -267,7 +279,30 @@ static void ss_point(int cls, int sub, const double u[4], double st[4], double &
         st[2] = R;
         st[3] = R * q2;
         jac = zt * zt * zt * a;
+        if (diff)
+            for (int i = 0; i < 4; ++i) diff[i] = st[i];
     }
+}
+
+void ss_rule_diff(int cls, int m, std::vector<double> &p0, std::vector<double> &p1,
+                  std::vector<double> &p2, std::vector<double> &p3, std::vector<double> &w) {
+    std::vector<double> g(m), gw(m);
+    gauss_legendre01(m, g.data(), gw.data());
+    int nsub = cls == PAIR_IDENTICAL ? 6 : cls == PAIR_EDGE ? 4 : 2;
+    p0.clear(); p1.clear(); p2.clear(); p3.clear(); w.clear();
+    for (int sub = 0; sub < nsub; ++sub)
+        for (int i0 = 0; i0 < m; ++i0)
+            for (int i1 = 0; i1 < m; ++i1)
+                for (int i2 = 0; i2 < m; ++i2)
+                    for (int i3 = 0; i3 < m; ++i3) {
+                        double u[4] = {g[i0], g[i1], g[i2], g[i3]}, st[4], jac, df[4];
+                        ss_point(cls, sub, u, st, jac, df);
+                        p0.push_back(df[0]);
+                        p1.push_back(df[1]);
+                        p2.push_back(df[2]);
+                        p3.push_back(df[3]);
+                        w.push_back(gw[i0] * gw[i1] * gw[i2] * gw[i3] * jac);
+                    }
 }
 
 void ss_rule(int cls, int m, std::vector<double> &s1, std::vector<double> &s2,

@@ -84,6 +84,14 @@ void triangle_rule(int q, std::vector<double> &s1, std::vector<double> &s2,
 int ss_rule_size(int cls, int m);
 void ss_rule(int cls, int m, std::vector<double> &s1, std::vector<double> &s2,
              std::vector<double> &t1, std::vector<double> &t2, std::vector<double> &w);
+// The same rule in difference form, so that x - y keeps its relative accuracy
+// as it shrinks (shared vertices first in both triangles, P_i, Q_i their
+// vertices, A_i = P_i - P_{i-1}, B_i = Q_i - Q_{i-1}):
+//   identical: (z1, z2, -, -),   x - y = -(z1 A1 + z2 A2),      z = t - s
+//   edge     : (u, s2, t2, -),   x - y = -u A1 + s2 A2 - t2 B2,  u = t1 - s1
+//   vertex   : (s1, s2, t1, t2), x - y = s1 A1 + s2 A2 - t1 B1 - t2 B2
+void ss_rule_diff(int cls, int m, std::vector<double> &p0, std::vector<double> &p1,
+                  std::vector<double> &p2, std::vector<double> &p3, std::vector<double> &w);
 
 // ------------------------------------------------------- kernel launchers --
 stb_status launch_geometry(const Mesh &m, double *geo, cudaStream_t s);

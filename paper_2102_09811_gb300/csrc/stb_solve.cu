@@ -278,10 +278,24 @@ k_history(const AT *__restrict__ V, int E, int n_steps, int r0, int nr, int k,
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) acc[r] = 0.0;
     const size_t EE = (size_t)E * E, SE = (size_t)n_steps * E;
+    constexpr int U = 8;  // independent loads in flight per lane
     for (int d = 1; d <= k; ++d) {
         const AT *row = V + d * EE + (size_t)l * E;
         const double *wk = w + (size_t)(k - d) * E;
-        for (int j = lane; j < E; j += 32) {
+        int j0 = 0;
+        for (; j0 + 32 * U <= E; j0 += 32 * U) {
+            double v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = (double)row[j0 + 32 * u + lane];
+#pragma unroll
+            for (int r = 0; r < MAXR; ++r)
+                if (r < nr) {
+                    const double *wr = wk + (size_t)(r0 + r) * SE + j0 + lane;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) acc[r] = fma(v[u], wr[32 * u], acc[r]);
+                }
+        }
+        for (int j = j0 + lane; j < E; j += 32) {
             double v = (double)row[j];
 #pragma unroll
             for (int r = 0; r < MAXR; ++r)
@@ -309,7 +323,21 @@ k_trmv(const double *__restrict__ M, int E, int nrhs, int lower, const double *_
         double acc[MAXR];
 #pragma unroll
         for (int r = 0; r < MAXR; ++r) acc[r] = 0.0;
-        for (int j = jlo + lane; j < jhi; j += 32) {
+        constexpr int U = 8;
+        int j0 = jlo;
+        for (; j0 + 32 * U <= jhi; j0 += 32 * U) {
+            double v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = row[j0 + 32 * u + lane];
+#pragma unroll
+            for (int r = 0; r < MAXR; ++r)
+                if (r0 + r < nrhs) {
+                    const double *ir = in + (size_t)(r0 + r) * in_stride + j0 + lane;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) acc[r] = fma(v[u], ir[32 * u], acc[r]);
+                }
+        }
+        for (int j = j0 + lane; j < jhi; j += 32) {
             double v = row[j];
 #pragma unroll
             for (int r = 0; r < MAXR; ++r)

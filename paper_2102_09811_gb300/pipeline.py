@@ -23,10 +23,11 @@ class DirichletProblem:
     """
 
     def __init__(self, nodes, tris, alpha, T, n_steps, sources, quad_regular=3, quad_singular=4,
-                 storage=capi.STB_STORE_F64, q_space=8, n_time=16, device="cuda", mesh=None):
+                 storage=capi.STB_STORE_F64, q_space=8, n_time=16, device="cuda", mesh=None,
+                 precision=capi.STB_PREC_FP64):
         self.mesh = mesh if mesh is not None else capi.Mesh(nodes, tris)
         self.params = capi.stb_default_params(alpha, T, n_steps, quad_regular, quad_singular,
-                                              storage=storage)
+                                              precision=precision, storage=storage)
         self.sources = sources
         self.nrhs, self.n_src = sources.shape[0], sources.shape[1]
         self.q_space, self.n_time = q_space, n_time
