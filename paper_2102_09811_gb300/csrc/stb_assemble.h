@@ -22,9 +22,16 @@ struct AssemblyLayout {
 // Gauss-Legendre per interval [kh, (k+1)h]: MIX_NG1 nodes on k = 1, MIX_NG on k >= 2.
 constexpr int MIX_NG1 = 6;
 constexpr int MIX_NG = 4;
-constexpr int MIX_NODE = 8;  // floats per node: b, cVf, cVr, cKf, cKr, pad
+// Node table: interval k = 1 as MIX_NG1 float4 (b, cVr, cKr, 0) (only its
+// rising side, block 2, is needed); every interval k >= 2 as MIX_IV floats:
+// float4 (b_0..b_3), then per node float4 (cVf, cKf, cVr, cKr).  b is the
+// exp2 scale -log2(e)/(4 alpha delta); c* fold the Gauss weight, the hat
+// weight (falling side: block k, rising side: block k+1) and (4 pi alpha
+// delta)^{-3/2} (K: times 1/(2 delta)).
+constexpr int MIX_K1 = 4 * MIX_NG1;
+constexpr int MIX_IV = 4 + 4 * MIX_NG;
 inline size_t mixed_node_floats(int n_steps) {
-    return (size_t)MIX_NODE * (MIX_NG1 + MIX_NG * (size_t)(n_steps > 2 ? n_steps - 2 : 0));
+    return (size_t)MIX_K1 + (size_t)MIX_IV * (size_t)(n_steps > 2 ? n_steps - 2 : 0);
 }
 void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<float> &ss,
                   std::vector<float> &nodes);

@@ -45,13 +45,13 @@ __device__ __forceinline__ float psi32(float x, float erfx, float ex) {
     if (x < 0.5f) {
         // (2/sqrt(pi)) sum_m (-1)^m x^{2m+1} / (m! (2m+1)(2m+3)), m <= 6
         float x2 = x * x;
-        float p = -1.0f / (720.0f * 13.0f * 15.0f);
-        p = fmaf(p, x2, 1.0f / (120.0f * 11.0f * 13.0f));
-        p = fmaf(p, x2, -1.0f / (24.0f * 9.0f * 11.0f));
-        p = fmaf(p, x2, 1.0f / (6.0f * 7.0f * 9.0f));
-        p = fmaf(p, x2, -1.0f / (2.0f * 5.0f * 7.0f));
-        p = fmaf(p, x2, 1.0f / (3.0f * 5.0f));
-        p = fmaf(p, x2, 1.0f / 3.0f);
+        float p = 1.0f / (720.0f * 13.0f * 15.0f);          // m = 6
+        p = fmaf(p, x2, -1.0f / (120.0f * 11.0f * 13.0f));  // m = 5
+        p = fmaf(p, x2, 1.0f / (24.0f * 9.0f * 11.0f));     // m = 4
+        p = fmaf(p, x2, -1.0f / (6.0f * 7.0f * 9.0f));      // m = 3
+        p = fmaf(p, x2, 1.0f / (2.0f * 5.0f * 7.0f));       // m = 2
+        p = fmaf(p, x2, -1.0f / (3.0f * 5.0f));             // m = 1
+        p = fmaf(p, x2, 1.0f / 3.0f);                       // m = 0
         return 2.0f * ISQRTPI * x * p;
     }
     return 0.5f * erfx - erfx / (4.0f * x * x) + 0.5f * ISQRTPI * ex / x;
@@ -82,6 +82,27 @@ __device__ __forceinline__ void k_d01(float rho, float irho, const MixConsts &g,
         const float c1h = ec1 * (0.5f - 0.25f * ix1 * ix1) - 0.5f * ISQRTPI * ee1 * ix1;
         const float c2h = ec2 * (0.5f - 0.25f * ix2 * ix2) - 0.5f * ISQRTPI * ee2 * ix2;
         k1 = -kf * (-2.0f * c1h + c2h);
+    }
+}
+
+// Node sums of interval k >= 2 (table `iv`, see stb_assemble.h) for one point
+// with squared distance rr: fall = (sum cVf e, sum cKf e) feeds block k,
+// rise = (sum cVr e, sum cKr e) feeds block k + 1, e = exp2(rr b).
+__device__ __forceinline__ void interval_sums(const float *iv, float rr, float2 &fall,
+                                              float2 &rise) {
+    const float4 b = *reinterpret_cast<const float4 *>(iv);
+    const float2 rr2 = make_float2(rr, rr);
+    const float2 t01 = __fmul2_rn(rr2, make_float2(b.x, b.y));
+    const float2 t23 = __fmul2_rn(rr2, make_float2(b.z, b.w));
+    const float e[MIX_NG] = {ex2(t01.x), ex2(t01.y), ex2(t23.x), ex2(t23.y)};
+    fall = make_float2(0.f, 0.f);
+    rise = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < MIX_NG; ++q) {
+        const float4 c = *reinterpret_cast<const float4 *>(iv + 4 + 4 * q);
+        const float2 ee = make_float2(e[q], e[q]);
+        fall = __ffma2_rn(make_float2(c.x, c.y), ee, fall);
+        rise = __ffma2_rn(make_float2(c.z, c.w), ee, rise);
     }
 }
 
@@ -156,10 +177,10 @@ k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris
             if (n_steps > 2) {
 #pragma unroll
                 for (int q = 0; q < MIX_NG1; ++q) {
-                    const float *c = nd + q * MIX_NODE;
-                    const float e = ex2(rr * c[0]);
-                    v2 = fmaf(w * c[2], e, v2);
-                    k2 = fmaf(wrn * c[4], e, k2);
+                    const float4 c = reinterpret_cast<const float4 *>(nd)[q];
+                    const float e = ex2(rr * c.x);
+                    v2 = fmaf(w * c.y, e, v2);
+                    k2 = fmaf(wrn * c.z, e, k2);
                 }
             }
         }
@@ -173,13 +194,10 @@ k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris
 
     // blocks d >= 2 in chunks [d0, d0 + CH): intervals k = d0 - 1 .. d0 + CH - 1
     for (int d0 = 2; d0 < n_steps; d0 += CH) {
-        float sv[CH], sk[CH];
+        float2 acc[CH];  // (V, K) of blocks d0 .. d0 + CH - 1
 #pragma unroll
-        for (int u = 0; u < CH; ++u) sv[u] = sk[u] = 0.f;
-        if (d0 == 2) {
-            sv[0] = v2;
-            sk[0] = k2;
-        }
+        for (int u = 0; u < CH; ++u) acc[u] = make_float2(0.f, 0.f);
+        if (d0 == 2) acc[0] = make_float2(v2, k2);
         for (int b = 0; b < nq; ++b) {
             const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
             const float r0b = D[0] - (t1 * B1[0] + t2 * B2[0]);
@@ -190,31 +208,16 @@ k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris
                 const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
                 const float rr = r0 * r0 + r1 * r1 + r2 * r2;
                 const float rn = r0 * n[0] + r1 * n[1] + r2 * n[2];
-                const float w = xq.w * wb, wrn = w * rn;
+                const float w = xq.w * wb;
+                const float2 wp = make_float2(w, w * rn);
 #pragma unroll
                 for (int u = 0; u <= CH; ++u) {
                     const int k = d0 - 1 + u;
                     if (k < 2 || k > n_steps - 1) continue;
-                    const float *c = nd + (MIX_NG1 + (k - 2) * MIX_NG) * MIX_NODE;
-                    float tv_f = 0.f, tv_r = 0.f, tk_f = 0.f, tk_r = 0.f;
-#pragma unroll
-                    for (int q = 0; q < MIX_NG; ++q) {
-                        const float4 cq = *reinterpret_cast<const float4 *>(c + q * MIX_NODE);
-                        const float ckr = c[q * MIX_NODE + 4];
-                        const float e = ex2(rr * cq.x);
-                        tv_f = fmaf(cq.y, e, tv_f);
-                        tv_r = fmaf(cq.z, e, tv_r);
-                        tk_f = fmaf(cq.w, e, tk_f);
-                        tk_r = fmaf(ckr, e, tk_r);
-                    }
-                    if (u >= 1) {  // falling side: block d = k
-                        sv[u - 1] = fmaf(w, tv_f, sv[u - 1]);
-                        sk[u - 1] = fmaf(wrn, tk_f, sk[u - 1]);
-                    }
-                    if (u < CH && k + 1 < n_steps) {  // rising side: block d = k + 1
-                        sv[u] = fmaf(w, tv_r, sv[u]);
-                        sk[u] = fmaf(wrn, tk_r, sk[u]);
-                    }
+                    float2 fall, rise;
+                    interval_sums(nd + MIX_K1 + (k - 2) * MIX_IV, rr, fall, rise);
+                    if (u >= 1) acc[u - 1] = __ffma2_rn(wp, fall, acc[u - 1]);      // block k
+                    if (u < CH && k + 1 < n_steps) acc[u] = __ffma2_rn(wp, rise, acc[u]);  // block k+1
                 }
             }
         }
@@ -222,8 +225,8 @@ k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris
         for (int u = 0; u < CH; ++u) {
             const int d = d0 + u;
             if (d < n_steps) {
-                store_m(V + (size_t)d * EE + ij, scale * sv[u]);
-                if (K) store_m(K + (size_t)d * EE + ij, scale * sk[u]);
+                store_m(V + (size_t)d * EE + ij, scale * acc[u].x);
+                if (K) store_m(K + (size_t)d * EE + ij, scale * acc[u].y);
             }
         }
     }
@@ -319,11 +322,11 @@ k_singular_mixed(const double *__restrict__ geo, const TouchPair *__restrict__ p
         if (n_steps > 2) {
 #pragma unroll
             for (int q = 0; q < MIX_NG1; ++q) {
-                const float *c = nodes + q * MIX_NODE;
-                const float e = ex2(rr * c[0]);
-                z[6] = fmaf(w * c[2], e, z[6]);
-                z[7] = fmaf(w * rab * c[4], e, z[7]);
-                z[8] = fmaf(w * rba * c[4], e, z[8]);
+                const float4 c = reinterpret_cast<const float4 *>(nodes)[q];
+                const float e = ex2(rr * c.x);
+                z[6] = fmaf(w * c.y, e, z[6]);
+                z[7] = fmaf(w * rab * c.z, e, z[7]);
+                z[8] = fmaf(w * rba * c.z, e, z[8]);
             }
         }
     }
@@ -359,27 +362,17 @@ k_singular_mixed(const double *__restrict__ geo, const TouchPair *__restrict__ p
             for (int u = 0; u <= CH; ++u) {
                 const int k = d0 - 1 + u;
                 if (k < 2 || k > n_steps - 1) continue;
-                const float *c = nodes + (MIX_NG1 + (k - 2) * MIX_NG) * MIX_NODE;
-                float tv_f = 0.f, tv_r = 0.f, tk_f = 0.f, tk_r = 0.f;
-#pragma unroll
-                for (int q = 0; q < MIX_NG; ++q) {
-                    const float4 cq = *reinterpret_cast<const float4 *>(c + q * MIX_NODE);
-                    const float ckr = c[q * MIX_NODE + 4];
-                    const float e = ex2(rr * cq.x);
-                    tv_f = fmaf(cq.y, e, tv_f);
-                    tv_r = fmaf(cq.z, e, tv_r);
-                    tk_f = fmaf(cq.w, e, tk_f);
-                    tk_r = fmaf(ckr, e, tk_r);
-                }
+                float2 fall, rise;
+                interval_sums(nodes + MIX_K1 + (k - 2) * MIX_IV, rr, fall, rise);
                 if (u >= 1) {
-                    acc[u - 1] = fmaf(w, tv_f, acc[u - 1]);
-                    acc[CH + u - 1] = fmaf(wa, tk_f, acc[CH + u - 1]);
-                    acc[2 * CH + u - 1] = fmaf(wb, tk_f, acc[2 * CH + u - 1]);
+                    acc[u - 1] = fmaf(w, fall.x, acc[u - 1]);
+                    acc[CH + u - 1] = fmaf(wa, fall.y, acc[CH + u - 1]);
+                    acc[2 * CH + u - 1] = fmaf(wb, fall.y, acc[2 * CH + u - 1]);
                 }
                 if (u < CH && k + 1 < n_steps) {
-                    acc[u] = fmaf(w, tv_r, acc[u]);
-                    acc[CH + u] = fmaf(wa, tk_r, acc[CH + u]);
-                    acc[2 * CH + u] = fmaf(wb, tk_r, acc[2 * CH + u]);
+                    acc[u] = fmaf(w, rise.x, acc[u]);
+                    acc[CH + u] = fmaf(wa, rise.y, acc[CH + u]);
+                    acc[2 * CH + u] = fmaf(wb, rise.y, acc[2 * CH + u]);
                 }
             }
         }
@@ -427,22 +420,37 @@ void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<flo
             for (double x : *v) ss.push_back((float)x);
     }
     nodes.assign(mixed_node_floats(p.n_steps), 0.f);
-    auto put = [&](size_t slot, int k, double ug, double wg) {
-        const double delta = (k + ug) * h, a_ = std::pow(4.0 * pi * al * delta, -1.5);
-        const double wf = h * wg * h * (1.0 - ug) * a_, wr = h * wg * h * ug * a_;
-        float *q = nodes.data() + slot * MIX_NODE;
-        q[0] = (float)(-1.0 / (4.0 * al * delta) * 1.4426950408889634);  // log2(e)
-        q[1] = (float)wf;
-        q[2] = (float)wr;
-        q[3] = (float)(wf / (2.0 * delta));
-        q[4] = (float)(wr / (2.0 * delta));
+    // b = exp2 scale, wf / wr = falling / rising weights of block k / k+1
+    auto node = [&](int k, double ug, double wg, double &b, double &wf, double &wr, double &delta) {
+        delta = (k + ug) * h;
+        const double a_ = std::pow(4.0 * pi * al * delta, -1.5);
+        b = -1.0 / (4.0 * al * delta) * 1.4426950408889634;  // log2(e)
+        wf = h * wg * h * (1.0 - ug) * a_;
+        wr = h * wg * h * ug * a_;
     };
     std::vector<double> u1(MIX_NG1), w1(MIX_NG1), u(MIX_NG), wq(MIX_NG);
     gauss_legendre01(MIX_NG1, u1.data(), w1.data());
     gauss_legendre01(MIX_NG, u.data(), wq.data());
-    for (int q = 0; q < MIX_NG1; ++q) put(q, 1, u1[q], w1[q]);
-    for (int k = 2; k <= p.n_steps - 1; ++k)
-        for (int q = 0; q < MIX_NG; ++q) put(MIX_NG1 + (size_t)(k - 2) * MIX_NG + q, k, u[q], wq[q]);
+    for (int q = 0; q < MIX_NG1; ++q) {
+        double b, wf, wr, delta;
+        node(1, u1[q], w1[q], b, wf, wr, delta);
+        float *o = nodes.data() + 4 * q;
+        o[0] = (float)b;
+        o[1] = (float)wr;
+        o[2] = (float)(wr / (2.0 * delta));
+    }
+    for (int k = 2; k <= p.n_steps - 1; ++k) {
+        float *o = nodes.data() + MIX_K1 + (size_t)(k - 2) * MIX_IV;
+        for (int q = 0; q < MIX_NG; ++q) {
+            double b, wf, wr, delta;
+            node(k, u[q], wq[q], b, wf, wr, delta);
+            o[q] = (float)b;
+            o[4 + 4 * q + 0] = (float)wf;
+            o[4 + 4 * q + 1] = (float)(wf / (2.0 * delta));
+            o[4 + 4 * q + 2] = (float)wr;
+            o[4 + 4 * q + 3] = (float)(wr / (2.0 * delta));
+        }
+    }
 }
 
 template <class OutT>

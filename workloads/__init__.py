@@ -150,10 +150,13 @@ def workload(name, alpha=None):
         nodes, tris = cube_mesh(4)
         return dict(name=name, nodes=nodes, tris=tris, alpha=1.0 if alpha is None else alpha,
                     T=1.0, n_steps=16, sources=point_source((1.5, 1.5, 1.5), t0=-0.1))
-    if name == "cube3072_e64":
+    if name.startswith("cube3072_e"):
+        # cube3072_e64 is the full-size workload; cube3072_e8 / _e16 are the
+        # same mesh with fewer steps (profiling captures of one launch)
+        n_steps = int(name[len("cube3072_e"):])
         nodes, tris = cube_mesh(16)
         return dict(name=name, nodes=nodes, tris=tris, alpha=1.0 if alpha is None else alpha,
-                    T=1.0, n_steps=64, sources=point_source((1.5, 1.5, 1.5), t0=0.0))
+                    T=1.0, n_steps=n_steps, sources=point_source((1.5, 1.5, 1.5), t0=0.0))
     if name == "sphere5120_e128":
         nodes, tris = icosphere(16)
         return dict(name=name, nodes=nodes, tris=tris, alpha=1.0 if alpha is None else alpha,
