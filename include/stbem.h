@@ -142,6 +142,27 @@ stb_status stb_toeplitz_matvec(const void *A, int32_t a_storage, int64_t E, int3
                                int32_t nrhs, const double *x, double beta, double *y,
                                void *workspace, size_t workspace_bytes, stb_stream stream);
 
+/* ---- the same product without any allocation (no counterpart in the paper) -------
+ * For callers that cannot allocate device memory at the point of the call:
+ * code running while a CUDA stream is being captured into a graph (where
+ * cudaMalloc is not permitted), plugins that live inside a host framework
+ * owning all device memory, or real-time code that forbids allocation after
+ * start-up.  Identical arguments and result as stb_toeplitz_matvec, but the
+ * partial sums live in a scratch array inside this library, of fixed size
+ * STB_TOEPLITZ_STATIC_SCRATCH_BYTES on every device that loads the library,
+ * held until the process exits.  Problems needing more scratch
+ * (8 * ceil(n_steps/8) * nrhs * n_steps * E bytes) are rejected with
+ * STB_ERR_INVALID_ARG.  The call allocates nothing: the first call on a
+ * device looks up the scratch's device address (make that first call before
+ * any stream capture).  All calls on one device share its scratch, which
+ * keeps the last call's contents: calls that overlap on the GPU (for example
+ * on two streams of the same device) race and must be serialised by the
+ * caller, e.g. by issuing them on one stream. */
+#define STB_TOEPLITZ_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+stb_status stb_toeplitz_matvec_static(const void *A, int32_t a_storage, int64_t E, int32_t n_steps,
+                                      int32_t nrhs, const double *x, double beta, double *y,
+                                      stb_stream stream);
+
 /* ---- right-hand side f = (1/2 M_h + K_h) g, M_h = h blockdiag(diag(Delta_l)) -- */
 stb_status stb_rhs_workspace_size(const stb_mesh *mesh, const stb_params *params, int32_t nrhs,
                                   size_t *bytes);

@@ -53,6 +53,7 @@ _SIGS = {
     "stb_project_dirichlet": (_I32, [_P, _PAR, _P, _I32, _I32, _I32, _I32, _P, _P, _SZ, _P]),
     "stb_toeplitz_workspace_size": (_I32, [_I64, _I32, _I32, _PSZ]),
     "stb_toeplitz_matvec": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _D, _P, _P, _SZ, _P]),
+    "stb_toeplitz_matvec_static": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _D, _P, _P]),
     "stb_rhs_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
     "stb_dirichlet_rhs": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
     "stb_solve_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
@@ -201,6 +202,12 @@ def stb_toeplitz_matvec(A, a_storage, E, n_steps, nrhs, x, beta, y, workspace, s
                                           _ptr(workspace),
                                           workspace.numel() * workspace.element_size(),
                                           _stream(stream)), "stb_toeplitz_matvec")
+
+
+def stb_toeplitz_matvec_static(A, a_storage, E, n_steps, nrhs, x, beta, y, stream=None):
+    _check(_library().stb_toeplitz_matvec_static(_ptr(A), a_storage, E, n_steps, nrhs, _ptr(x), beta,
+                                                 _ptr(y), _stream(stream)),
+           "stb_toeplitz_matvec_static")
 
 
 def stb_rhs_workspace_size(mesh, params, nrhs):

@@ -6,6 +6,8 @@
 // gets a balanced share even though block d only feeds the columns k >= d.
 // Each item accumulates into its own partial slice; a second kernel adds the
 // slices in a fixed order (deterministic result).
+#include <mutex>
+
 #include "stb_internal.h"
 #include "stb_toeplitz.h"
 
@@ -104,9 +106,54 @@ stb_status toeplitz_fp64(const void *A, int32_t storage, int64_t E, int32_t n_st
     return check_launch("k_toeplitz_reduce");
 }
 
+// Scratch of stb_toeplitz_matvec_static: every device that loads the library
+// holds these bytes until the process exits.  Host code must not hand the
+// symbol itself to a kernel (on the host it names a host-side shadow); the
+// device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_matvec_scratch[STB_TOEPLITZ_STATIC_SCRATCH_BYTES];
+
+static stb_status matvec_scratch_address(double **out) {
+    static std::mutex mu;
+    static void *addr[256] = {};
+    int dev = 0;
+    STB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(STB_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_matvec_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(matvec scratch)");
+        addr[dev] = p;
+    }
+    *out = static_cast<double *>(addr[dev]);
+    return STB_OK;
+}
+
 }  // namespace stb
 
 using namespace stb;
+
+extern "C" stb_status stb_toeplitz_matvec_static(const void *A, int32_t a_storage, int64_t E,
+                                                 int32_t n_steps, int32_t nrhs, const double *x,
+                                                 double beta, double *y, stb_stream stream) {
+    if (!A || !x || !y) return fail(STB_ERR_INVALID_ARG, "A, x and y must be given");
+    if (a_storage != STB_STORE_F64 && a_storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "a_storage must be STB_STORE_F64 or STB_STORE_F32");
+    if (E < 1 || E > 65535 || n_steps < 1 || nrhs < 1)
+        return fail(STB_ERR_INVALID_ARG, "need 1 <= E <= 65535, n_steps >= 1, nrhs >= 1");
+    const size_t need = toeplitz_partial_bytes(E, n_steps, nrhs);
+    if (need > STB_TOEPLITZ_STATIC_SCRATCH_BYTES)
+        return fail(STB_ERR_INVALID_ARG,
+                    "problem needs %zu bytes of scratch, the static scratch holds %zu; "
+                    "use stb_toeplitz_matvec with a workspace",
+                    need, (size_t)STB_TOEPLITZ_STATIC_SCRATCH_BYTES);
+    double *part = nullptr;
+    stb_status st = matvec_scratch_address(&part);
+    if (st) return st;
+    // every partial slice the reduction reads is written earlier in this call,
+    // so the scratch needs no clearing
+    return toeplitz_fp64(A, a_storage, E, n_steps, nrhs, x, beta, y, part, (cudaStream_t)stream);
+}
 
 extern "C" stb_status stb_toeplitz_workspace_size(int64_t E, int32_t n_steps, int32_t nrhs,
                                                   size_t *bytes) {
