@@ -42,8 +42,21 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # separated-pair quadrature-point evaluation at one time level i_t >= 1 of
 # k_regular_f64, see profiles/.
 FP64_FLOPS_PER_EVAL = 137.34
-# MUFU (XU) pipe: 16 ex2 per SM per clock.
-MUFU_PEAK_TEX2 = 152 * 16 * 2.07e9 / 1e12
+# MUFU (XU) pipe: 32 ex2.approx.f32 per SM per clock (a throughput
+# microbenchmark of eight independent ex2 chains per thread measured 9.995e12
+# per second = 31.8 per SM per clock at 2.07 GHz on GB300).
+MUFU_PEAK_TEX2 = 152 * 32 * 2.07e9 / 1e12
+
+
+def _measured_hbm_gbs():
+    try:
+        with open(MEASURED_PEAKS) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # fallback figure for a GB300 copy
+
+
+HBM_PEAK_GBS = _measured_hbm_gbs()
 
 
 def parse():
@@ -163,13 +176,15 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _roofline(name, trace_entry, ms_step, n_reg_pairs, nq, n_steps):
-    """Roofline of the step's dominant kernel from the live trace."""
+def _roofline(name, trace_entry, ms_step, n_reg_pairs, q, n_steps):
+    """Roofline of the step's dominant kernel from the live trace (q: points
+    per direction of the conical rule, so (q*q)^2 points per pair)."""
     cnt, tot = trace_entry
     launch_ms = tot / cnt
+    pts = float(q * q) ** 2
     roof = {"kernel": name, "launch_ms": launch_ms, "share_of_step": tot / ms_step, "traffic": None}
     if name == "k_regular_f64":
-        evals = float(n_reg_pairs) * nq * nq * n_steps  # levels 1..E_t
+        evals = float(n_reg_pairs) * pts * n_steps  # levels 1..E_t
         roof.update({"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
                      "peak_source": "FP64 FMA pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz "
                                     "(measured 1.255 TFLOP/s, nominal 1.25)",
@@ -182,9 +197,9 @@ def _roofline(name, trace_entry, ms_step, n_reg_pairs, nq, n_steps):
         # k = 2..E_t-1, each interval evaluated by the two chunks that share it
         chunks = max(0, (n_steps - 2 + 15) // 16)
         nodes = 6 + 4 * max(0, n_steps - 2) + 4 * max(0, chunks - 1)
-        ex2 = float(n_reg_pairs) * nq * nq * nodes
+        ex2 = float(n_reg_pairs) * pts * nodes
         roof.update({"bound": "alu", "unit": "Tex2/s", "peak": MUFU_PEAK_TEX2,
-                     "peak_source": "MUFU pipe: 152 SM x 16 ex2/clk x 2.07 GHz",
+                     "peak_source": "MUFU pipe: 152 SM x 32 ex2/clk x 2.07 GHz (measured 9.995 Tex2/s)",
                      "units_per_launch": ex2, "unit_name": "MUFU.EX2 time-node evaluations"})
         ach = ex2 / (launch_ms / 1e3) / 1e12
         roof.update({"achieved": ach, "frac": ach / MUFU_PEAK_TEX2})
@@ -253,21 +268,39 @@ def run_gpu(args):
     name = max(trace.items(), key=lambda kv: kv[1][1])[0]
     roof = _roofline(name, trace[name], ms / 1.0, n_reg_pairs, 3, n)
 
-    # block-Toeplitz matvec (FP64 arithmetic) on the assembled V of the first problem
+    # block-Toeplitz matvec on the assembled V of the first problem, in each
+    # arithmetic the stored blocks allow; errors relative to the FP64 product
     p0 = probs[0]
-    ws = torch.empty(capi.stb_toeplitz_workspace_size(E, n, p0.nrhs), dtype=torch.uint8, device="cuda")
     y = torch.empty_like(p0.w)
-    capi.stb_toeplitz_matvec(p0.V, storage, E, n, p0.nrhs, p0.w, 0.0, y, ws)
-    torch.cuda.synchronize()
+    ariths = [("fp64", capi.STB_ARITH_FP64)]
+    if storage == capi.STB_STORE_F32:
+        ariths += [("df", capi.STB_ARITH_DF), ("tf32", capi.STB_ARITH_TF32)]
     a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 5
-    a_.record(stream)
-    for _ in range(reps):
-        capi.stb_toeplitz_matvec(p0.V, storage, E, n, p0.nrhs, p0.w, 0.0, y, ws)
-    b_.record(stream)
-    torch.cuda.synchronize()
-    mv_ms = a_.elapsed_time(b_) / reps
-    mv_tflops = float(E) * E * n * (n + 1) * p0.nrhs / (mv_ms / 1e3) / 1e12
+    flops = float(E) * E * n * (n + 1) * p0.nrhs
+    a_bytes = float(n) * E * E * (4 if storage == capi.STB_STORE_F32 else 8)
+    matvec, y_ref = {}, None
+    for label, ar in ariths:
+        ws = torch.empty(capi.stb_toeplitz_ex_workspace_size(E, n, p0.nrhs, ar), dtype=torch.uint8,
+                         device="cuda")
+        capi.stb_toeplitz_matvec_ex(p0.V, storage, E, n, p0.nrhs, p0.w, 0.0, y, ar, ws)
+        capi.stb_workspace_status(ws)
+        if y_ref is None:
+            y_ref = y.clone()
+        rel = float(torch.linalg.norm(y - y_ref) / torch.linalg.norm(y_ref))
+        reps = 5 if label == "fp64" else 20
+        a_.record(stream)
+        for _ in range(reps):
+            capi.stb_toeplitz_matvec_ex(p0.V, storage, E, n, p0.nrhs, p0.w, 0.0, y, ar, ws)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        mv_ms = a_.elapsed_time(b_) / reps
+        matvec[label] = {"ms": mv_ms, "tflops": flops / (mv_ms / 1e3) / 1e12,
+                         "block_gbs": a_bytes / (mv_ms / 1e3) / 1e9, "rel_err_vs_fp64": rel}
+        del ws
+    best = "tf32" if "tf32" in matvec else "fp64"
+    mv_tflops, mv_ms = matvec[best]["tflops"], matvec[best]["ms"]
+    matvec["blocks_read_gb"] = a_bytes / 1e9
+    matvec["hbm_peak_gbs"] = HBM_PEAK_GBS
 
     # the other precision: FP64 assembly of one problem for "mixed vs FP64"
     cmp = None
@@ -328,7 +361,7 @@ def run_gpu(args):
                        "l2": "no flush: every step writes %.1f GB of V/K blocks (>> 129 MB L2)"
                              % (2 * (4 if mixed else 8) * n * E * E * len(alphas) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "mixed_vs_fp64": cmp, "matvec_tflops": mv_tflops, "matvec_ms": mv_ms,
+            "mixed_vs_fp64": cmp, "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
             "rel_l2_error_w": rel_err, "gpu_launches": launches,
             "kernels_ms": {k: v[1] for k, v in trace.items()}, "roofline": roof, "e2e": e2e}
     if rank == 0:

@@ -125,7 +125,8 @@ stb_status stb_assemble(const stb_mesh *mesh, const stb_params *params, void *V,
  * side r has the Dirichlet datum g_r(x,t) = sum_s weight_s G_alpha(x - y_s, t - t0_s)
  * (the exterior-source exact solution of Sec. 6.1).  g (device, [nrhs][n_steps][E])
  * receives its L2 projection into piecewise constants (element means) by a
- * q_space x q_space conical rule and n_time Gauss points per step. */
+ * q_space x q_space conical rule and n_time Gauss points per step, in FP64
+ * (STB_PREC_FP64) or FP32 arithmetic (STB_PREC_MIXED). */
 stb_status stb_project_workspace_size(const stb_mesh *mesh, int32_t nrhs, int32_t n_src,
                                       int32_t q_space, int32_t n_time, size_t *bytes);
 stb_status stb_project_dirichlet(const stb_mesh *mesh, const stb_params *params,
@@ -141,6 +142,30 @@ stb_status stb_toeplitz_workspace_size(int64_t E, int32_t n_steps, int32_t nrhs,
 stb_status stb_toeplitz_matvec(const void *A, int32_t a_storage, int64_t E, int32_t n_steps,
                                int32_t nrhs, const double *x, double beta, double *y,
                                void *workspace, size_t workspace_bytes, stb_stream stream);
+
+/* ---- the same product in a chosen arithmetic (eq. V_mat) --------------------------
+ * Same y, A, x, beta as stb_toeplitz_matvec; `arith` selects how it is formed:
+ *   STB_ARITH_FP64  FP64 FMA, blocks of either storage (= stb_toeplitz_matvec);
+ *   STB_ARITH_DF    STB_STORE_F32 blocks, exact FP32 products with a two-float
+ *                   split of x summed in FP32 pairs (about 44 significant bits);
+ *   STB_ARITH_TF32  STB_STORE_F32 blocks on the tensor cores: blocks read as
+ *                   TF32 (10 stored mantissa bits), x rounded to TF32, FP32
+ *                   accumulation over slices of blocks, slices added in FP64.
+ *                   Needs E % 4 == 0 and A 16-byte aligned.  Error per entry
+ *                   <= (2^-10 + 2^-11) sum_d |A^d| |x^{k-d}| plus the FP32
+ *                   accumulation error.
+ * Workspace from stb_toeplitz_ex_workspace_size (same arith).  STB_ARITH_TF32
+ * bounds every device wait (2 s); an expired wait leaves STB_ERR_TIMEOUT in the
+ * workspace status word (stb_workspace_status). */
+#define STB_ARITH_FP64 0
+#define STB_ARITH_DF 1
+#define STB_ARITH_TF32 2
+stb_status stb_toeplitz_ex_workspace_size(int64_t E, int32_t n_steps, int32_t nrhs, int32_t arith,
+                                          size_t *bytes);
+stb_status stb_toeplitz_matvec_ex(const void *A, int32_t a_storage, int64_t E, int32_t n_steps,
+                                  int32_t nrhs, const double *x, double beta, double *y,
+                                  int32_t arith, void *workspace, size_t workspace_bytes,
+                                  stb_stream stream);
 
 /* ---- the same product without any allocation (no counterpart in the paper) -------
  * For callers that cannot allocate device memory at the point of the call:
@@ -175,13 +200,21 @@ stb_status stb_dirichlet_rhs(const stb_mesh *mesh, const stb_params *params, con
  * symmetric positive definite), inverts L, then marches in time:
  *   w^k = (V^0)^{-1} (f^k - sum_{d=1}^{k} V^d w^{k-d}).
  * V: device [n_steps][E][E] (params->storage), f, w: device FP64
- * [nrhs][n_steps][E].  Synchronises `stream` at the end and returns
- * STB_ERR_NOT_SPD if a pivot was not positive. */
+ * [nrhs][n_steps][E].  STB_PREC_FP64: every step in FP64.  STB_PREC_MIXED
+ * (needs STB_STORE_F32 blocks): FP32 factorisation and march inside
+ * iterative refinement w <- w + march(f - V_h w) with the residual formed in
+ * FP32-pair (double-float) arithmetic, until ||f - V_h w|| <= 1e-10 ||f||
+ * (at most 8 refinements, else STB_ERR_NOT_CONVERGED).  Synchronises `stream`
+ * at the end and returns STB_ERR_NOT_SPD if a pivot was not positive. */
 stb_status stb_solve_workspace_size(const stb_mesh *mesh, const stb_params *params, int32_t nrhs,
                                     size_t *bytes);
 stb_status stb_dirichlet_solve(const stb_mesh *mesh, const stb_params *params, const void *V,
                                const double *f, int32_t nrhs, double *w, void *workspace,
                                size_t workspace_bytes, stb_stream stream);
+/* Refinement count and final ||f - V_h w|| / ||f|| of the last solve that used
+ * this workspace (0 and 0.0 after an FP64 solve).  Synchronises `stream`. */
+stb_status stb_solve_report(const void *workspace, stb_stream stream, int32_t *refinements,
+                            double *rel_residual);
 
 /* ---- error of the Neumann datum (Sec. 6.1, relative L2(Sigma_h) error) -------------
  * out[0] = sum_r || w_r - w_{h,r} ||^2_{L2(Sigma_h)},  out[1] = sum_r || w_r ||^2

@@ -16,6 +16,7 @@ from . import _build
 STB_OK = 0
 STB_PREC_FP64, STB_PREC_MIXED = 0, 1
 STB_STORE_F64, STB_STORE_F32 = 0, 1
+STB_ARITH_FP64, STB_ARITH_DF, STB_ARITH_TF32 = 0, 1, 2
 
 _lib = None
 
@@ -54,10 +55,13 @@ _SIGS = {
     "stb_toeplitz_workspace_size": (_I32, [_I64, _I32, _I32, _PSZ]),
     "stb_toeplitz_matvec": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _D, _P, _P, _SZ, _P]),
     "stb_toeplitz_matvec_static": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _D, _P, _P]),
+    "stb_toeplitz_ex_workspace_size": (_I32, [_I64, _I32, _I32, _I32, _PSZ]),
+    "stb_toeplitz_matvec_ex": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _D, _P, _I32, _P, _SZ, _P]),
     "stb_rhs_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
     "stb_dirichlet_rhs": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
     "stb_solve_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
     "stb_dirichlet_solve": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
+    "stb_solve_report": (_I32, [_P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
     "stb_error_workspace_size": (_I32, [_P, _PAR, _I32, _I32, _I32, _I32, _PSZ]),
     "stb_neumann_error": (_I32, [_P, _PAR, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _SZ, _P]),
     "stb_workspace_status": (_I32, [_P, _P]),
@@ -204,6 +208,17 @@ def stb_toeplitz_matvec(A, a_storage, E, n_steps, nrhs, x, beta, y, workspace, s
                                           _stream(stream)), "stb_toeplitz_matvec")
 
 
+def stb_toeplitz_ex_workspace_size(E, n_steps, nrhs, arith):
+    return _size(_library().stb_toeplitz_ex_workspace_size, E, n_steps, nrhs, arith)
+
+
+def stb_toeplitz_matvec_ex(A, a_storage, E, n_steps, nrhs, x, beta, y, arith, workspace, stream=None):
+    _check(_library().stb_toeplitz_matvec_ex(_ptr(A), a_storage, E, n_steps, nrhs, _ptr(x), beta,
+                                             _ptr(y), arith, _ptr(workspace),
+                                             workspace.numel() * workspace.element_size(),
+                                             _stream(stream)), "stb_toeplitz_matvec_ex")
+
+
 def stb_toeplitz_matvec_static(A, a_storage, E, n_steps, nrhs, x, beta, y, stream=None):
     _check(_library().stb_toeplitz_matvec_static(_ptr(A), a_storage, E, n_steps, nrhs, _ptr(x), beta,
                                                  _ptr(y), _stream(stream)),
@@ -230,6 +245,14 @@ def stb_dirichlet_solve(mesh, params, V, f, nrhs, w, workspace, stream=None):
                                           _ptr(w), _ptr(workspace),
                                           workspace.numel() * workspace.element_size(),
                                           _stream(stream)), "stb_dirichlet_solve")
+
+
+def stb_solve_report(workspace, stream=None):
+    """(refinements, relative residual) of the last solve with this workspace."""
+    it, res = _I32(), _D()
+    _check(_library().stb_solve_report(_ptr(workspace), _stream(stream), ctypes.byref(it),
+                                       ctypes.byref(res)), "stb_solve_report")
+    return int(it.value), float(res.value)
 
 
 def stb_error_workspace_size(mesh, params, nrhs, n_src, q_space=8, n_time=16):

@@ -17,11 +17,20 @@ constexpr int MAX_QS = 32;   // q_space <= 32
 constexpr int MAX_NT = 64;   // n_time <= 64
 constexpr int MAX_SRC = 64;  // sources per right-hand side
 
-// G_alpha(r, tau) (Sec. 2), zero for tau <= 0
-__device__ __forceinline__ double heat(double rr, double tau, double alpha) {
+// G_alpha(r, tau) (Sec. 2), zero for tau <= 0; rr = |r|^2.  FP64, or FP32
+// (mixed precision: exp2 on the MUFU pipe and a reciprocal square root).
+template <class R> __device__ __forceinline__ R heat(R rr, R tau, R alpha);
+template <> __device__ __forceinline__ double heat<double>(double rr, double tau, double alpha) {
     if (tau <= 0.0) return 0.0;
     const double s = 4.0 * 3.14159265358979323846 * alpha * tau;
     return exp(-rr / (4.0 * alpha * tau)) / (s * sqrt(s));
+}
+template <> __device__ __forceinline__ float heat<float>(float rr, float tau, float alpha) {
+    if (tau <= 0.0f) return 0.0f;
+    const float s = 4.0f * 3.14159265f * alpha * tau;
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-rr / (4.0f * alpha * tau) * 1.44269504f));
+    return e * rsqrtf(s * s * s);
 }
 
 struct DirLayout {
@@ -56,12 +65,14 @@ static void host_rules(int q, int nt, std::vector<double> &out) {
 }
 
 // g_{r,k,j} = (h Delta_j)^{-1} int_{t_k}^{t_{k+1}} int_{gamma_j} g_r  (element mean)
+template <class R>
 __global__ void __launch_bounds__(DIR_THREADS)
 k_project(const double *__restrict__ geo, int E, const double *__restrict__ rule, int nq, int nt,
-          const double *__restrict__ src, int n_src, int nrhs, int n_steps, double h, double alpha,
+          const double *__restrict__ src, int n_src, int nrhs, int n_steps, double h_, double alpha_,
           double *__restrict__ g) {
-    __shared__ double rs[3 * MAX_QS * MAX_QS + 2 * MAX_NT];
-    __shared__ double sr[5 * MAX_SRC];
+    __shared__ R rs[3 * MAX_QS * MAX_QS + 2 * MAX_NT];
+    __shared__ R sr[5 * MAX_SRC];
+    const R h = (R)h_, alpha = (R)alpha_;
     for (int i = threadIdx.x; i < 3 * nq + 2 * nt; i += DIR_THREADS) rs[i] = rule[i];
     const int r = blockIdx.y;
     for (int i = threadIdx.x; i < 5 * n_src; i += DIR_THREADS) sr[i] = src[(size_t)r * n_src * 5 + i];
@@ -70,36 +81,38 @@ k_project(const double *__restrict__ geo, int E, const double *__restrict__ rule
     if (idx >= (size_t)n_steps * E) return;
     const int k = (int)(idx / E), j = (int)(idx % E);
     const double *gj = geo + (size_t)j * GEO_STRIDE;
-    const double *tx = rs + 3 * nq, *tw = tx + nt;
-    double acc = 0.0;
+    const R *tx = rs + 3 * nq, *tw = tx + nt;
+    R acc = 0;
     for (int a = 0; a < nq; ++a) {
-        double s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
-        double x[3];
+        R s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
+        R x[3];
         for (int c = 0; c < 3; ++c)
-            x[c] = gj[c] + s1 * (gj[3 + c] - gj[c]) + s2 * (gj[6 + c] - gj[3 + c]);
-        double inner = 0.0;
+            x[c] = (R)(gj[c] + (double)s1 * (gj[3 + c] - gj[c]) + (double)s2 * (gj[6 + c] - gj[3 + c]));
+        R inner = 0;
         for (int b = 0; b < nt; ++b) {
-            double t = (k + tx[b]) * h, gv = 0.0;
+            R t = (k + tx[b]) * h, gv = 0;
             for (int s = 0; s < n_src; ++s) {
-                const double *S = sr + 5 * s;
-                double d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
-                gv = fma(S[4], heat(d0 * d0 + d1 * d1 + d2 * d2, t - S[3], alpha), gv);
+                const R *S = sr + 5 * s;
+                R d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
+                gv = fma(S[4], heat<R>(d0 * d0 + d1 * d1 + d2 * d2, t - S[3], alpha), gv);
             }
             inner = fma(tw[b], gv, inner);
         }
         acc = fma(wa, inner, acc);
     }
-    g[(size_t)r * n_steps * E + idx] = 2.0 * acc;
+    g[(size_t)r * n_steps * E + idx] = 2.0 * (double)acc;
 }
 
 // out-partials of sum (w - w_h)^2 and sum w^2 over Sigma_h (Sec. 6.1), with
 // w = alpha du/dn_x = -sum_s weight_s G (x - y_s).n_x / (2 (t - t0_s))
+template <class R>
 __global__ void __launch_bounds__(DIR_THREADS)
 k_error(const double *__restrict__ geo, int E, const double *__restrict__ rule, int nq, int nt,
-        const double *__restrict__ src, int n_src, int nrhs, int n_steps, double h, double alpha,
+        const double *__restrict__ src, int n_src, int nrhs, int n_steps, double h_, double alpha_,
         const double *__restrict__ wh, double *__restrict__ part) {
-    __shared__ double rs[3 * MAX_QS * MAX_QS + 2 * MAX_NT];
-    __shared__ double sr[5 * MAX_SRC];
+    __shared__ R rs[3 * MAX_QS * MAX_QS + 2 * MAX_NT];
+    __shared__ R sr[5 * MAX_SRC];
+    const R h = (R)h_, alpha = (R)alpha_;
     __shared__ double red[2][DIR_THREADS / 32];
     for (int i = threadIdx.x; i < 3 * nq + 2 * nt; i += DIR_THREADS) rs[i] = rule[i];
     const int r = blockIdx.y;
@@ -110,33 +123,35 @@ k_error(const double *__restrict__ geo, int E, const double *__restrict__ rule, 
     if (idx < (size_t)n_steps * E) {
         const int k = (int)(idx / E), j = (int)(idx % E);
         const double *gj = geo + (size_t)j * GEO_STRIDE;
-        const double *tx = rs + 3 * nq, *tw = tx + nt;
-        const double whv = wh[(size_t)r * n_steps * E + idx];
+        const R *tx = rs + 3 * nq, *tw = tx + nt;
+        const R whv = (R)wh[(size_t)r * n_steps * E + idx];
+        const R nx = (R)gj[GEO_N], ny = (R)gj[GEO_N + 1], nz = (R)gj[GEO_N + 2];
+        R e2r = 0, r2r = 0;
         for (int a = 0; a < nq; ++a) {
-            double s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
-            double x[3];
+            R s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
+            R x[3];
             for (int c = 0; c < 3; ++c)
-                x[c] = gj[c] + s1 * (gj[3 + c] - gj[c]) + s2 * (gj[6 + c] - gj[3 + c]);
-            double ie = 0.0, ir = 0.0;
+                x[c] = (R)(gj[c] + (double)s1 * (gj[3 + c] - gj[c]) + (double)s2 * (gj[6 + c] - gj[3 + c]));
+            R ie = 0, ir = 0;
             for (int b = 0; b < nt; ++b) {
-                double t = (k + tx[b]) * h, wv = 0.0;
+                R t = (k + tx[b]) * h, wv = 0;
                 for (int s = 0; s < n_src; ++s) {
-                    const double *S = sr + 5 * s;
-                    double tau = t - S[3];
-                    if (tau <= 0.0) continue;
-                    double d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
-                    double dn = d0 * gj[GEO_N] + d1 * gj[GEO_N + 1] + d2 * gj[GEO_N + 2];
-                    wv -= S[4] * heat(d0 * d0 + d1 * d1 + d2 * d2, tau, alpha) * dn / (2.0 * tau);
+                    const R *S = sr + 5 * s;
+                    R tau = t - S[3];
+                    if (tau <= (R)0) continue;
+                    R d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
+                    R dn = d0 * nx + d1 * ny + d2 * nz;
+                    wv -= S[4] * heat<R>(d0 * d0 + d1 * d1 + d2 * d2, tau, alpha) * dn / ((R)2 * tau);
                 }
                 ie = fma(tw[b], (wv - whv) * (wv - whv), ie);
                 ir = fma(tw[b], wv * wv, ir);
             }
-            e2 = fma(wa, ie, e2);
-            r2 = fma(wa, ir, r2);
+            e2r = fma(wa, ie, e2r);
+            r2r = fma(wa, ir, r2r);
         }
-        double f = 2.0 * gj[GEO_AREA] * h;
-        e2 *= f;
-        r2 *= f;
+        double f = 2.0 * gj[GEO_AREA] * h_;
+        e2 = (double)e2r * f;
+        r2 = (double)r2r * f;
     }
     for (int o = 16; o > 0; o >>= 1) {
         e2 += __shfl_xor_sync(0xffffffffu, e2, o);
@@ -247,8 +262,14 @@ extern "C" stb_status stb_project_dirichlet(const stb_mesh *mesh, const stb_para
     size_t n = (size_t)p->n_steps * m.n_tris;
     dim3 grid((unsigned)((n + DIR_THREADS - 1) / DIR_THREADS), (unsigned)nrhs);
     count_launch(s);
-    k_project<<<grid, DIR_THREADS, 0, s>>>(L.geo, (int)m.n_tris, L.rule, q * q, nt, L.src, n_src,
-                                           nrhs, p->n_steps, p->T / p->n_steps, p->alpha, g);
+    if (p->precision == STB_PREC_MIXED)
+        k_project<float><<<grid, DIR_THREADS, 0, s>>>(L.geo, (int)m.n_tris, L.rule, q * q, nt, L.src,
+                                                      n_src, nrhs, p->n_steps, p->T / p->n_steps,
+                                                      p->alpha, g);
+    else
+        k_project<double><<<grid, DIR_THREADS, 0, s>>>(L.geo, (int)m.n_tris, L.rule, q * q, nt, L.src,
+                                                       n_src, nrhs, p->n_steps, p->T / p->n_steps,
+                                                       p->alpha, g);
     return check_launch("k_project");
 }
 
@@ -258,7 +279,9 @@ extern "C" stb_status stb_rhs_workspace_size(const stb_mesh *mesh, const stb_par
         return fail(STB_ERR_INVALID_ARG, "invalid argument");
     Carve c(nullptr, 0);
     c.take<double>((size_t)mesh->m.n_tris * GEO_STRIDE);
-    c.take<char>(toeplitz_partial_bytes(mesh->m.n_tris, p->n_steps, nrhs));
+    c.take<char>(p->precision == STB_PREC_MIXED
+                     ? toeplitz_df_bytes(mesh->m.n_tris, p->n_steps, nrhs)
+                     : toeplitz_partial_bytes(mesh->m.n_tris, p->n_steps, nrhs));
     *bytes = align256(c.off);
     return STB_OK;
 }
@@ -274,13 +297,22 @@ extern "C" stb_status stb_dirichlet_rhs(const stb_mesh *mesh, const stb_params *
     if (st) return st;
     if ((st = check_workspace(ws, ws_bytes, need))) return st;
     const Mesh &m = mesh->m;
+    const bool mixed = p->precision == STB_PREC_MIXED;
+    if (mixed && p->storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "mixed precision needs STB_STORE_F32 blocks");
     Carve c(ws, ws_bytes);
     double *geo = c.take<double>((size_t)m.n_tris * GEO_STRIDE);
-    double *part = (double *)c.take<char>(toeplitz_partial_bytes(m.n_tris, p->n_steps, nrhs));
+    void *part = c.take<char>(mixed ? toeplitz_df_bytes(m.n_tris, p->n_steps, nrhs)
+                                    : toeplitz_partial_bytes(m.n_tris, p->n_steps, nrhs));
     cudaStream_t s = (cudaStream_t)stream;
     STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
     if ((st = launch_geometry(m, geo, s))) return st;
-    if ((st = toeplitz_fp64(K, p->storage, m.n_tris, p->n_steps, nrhs, g, 0.0, f, part, s))) return st;
+    if (mixed)
+        st = toeplitz_df((const float *)K, m.n_tris, p->n_steps, nrhs, g, DF_AXPBY, nullptr, 0.0, f,
+                         part, s);
+    else
+        st = toeplitz_fp64(K, p->storage, m.n_tris, p->n_steps, nrhs, g, 0.0, f, (double *)part, s);
+    if (st) return st;
     size_t total = (size_t)nrhs * p->n_steps * m.n_tris;
     count_launch(s);
     k_add_mass<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(geo, (int)m.n_tris, total,
@@ -324,9 +356,14 @@ extern "C" stb_status stb_neumann_error(const stb_mesh *mesh, const stb_params *
     if ((st = upload_rules_sources(L, q, nt, sources, nrhs, n_src, s))) return st;
     if ((st = launch_geometry(m, L.geo, s))) return st;
     count_launch(s);
-    k_error<<<dim3(gx, (unsigned)nrhs), DIR_THREADS, 0, s>>>(L.geo, (int)m.n_tris, L.rule, q * q, nt,
-                                                            L.src, n_src, nrhs, p->n_steps,
-                                                            p->T / p->n_steps, p->alpha, w, L.part);
+    if (p->precision == STB_PREC_MIXED)
+        k_error<float><<<dim3(gx, (unsigned)nrhs), DIR_THREADS, 0, s>>>(
+            L.geo, (int)m.n_tris, L.rule, q * q, nt, L.src, n_src, nrhs, p->n_steps, p->T / p->n_steps,
+            p->alpha, w, L.part);
+    else
+        k_error<double><<<dim3(gx, (unsigned)nrhs), DIR_THREADS, 0, s>>>(
+            L.geo, (int)m.n_tris, L.rule, q * q, nt, L.src, n_src, nrhs, p->n_steps, p->T / p->n_steps,
+            p->alpha, w, L.part);
     if ((st = check_launch("k_error"))) return st;
     count_launch(s);
     k_sum_pairs<<<1, 1024, 0, s>>>(L.part, nblk, out);

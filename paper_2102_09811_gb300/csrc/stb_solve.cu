@@ -6,72 +6,84 @@
 // a right-looking blocked Cholesky (64 x 64 tiles), L is inverted blockwise,
 // and every time step is then three matrix-vector kernels: the history sum
 // (reads V^1..V^k once, all right-hand sides together), z = L^{-1} r and
-// w^k = L^{-T} z.  All FP64.
+// w^k = L^{-T} z.
+//
+// FP64 precision: everything in FP64.
+// Mixed precision: the factorisation and the march run in FP32 and are wrapped
+// in iterative refinement,  w <- w + march(f - V_h w),  whose residual is
+// formed with FP32-pair ("double-float") products and sums (exact FP32
+// products of the stored FP32 blocks with a two-float split of w, error-free
+// two-sums), so that no O(E^2 E_t^2) work runs on the scarce FP64 pipe.  The
+// refinement stops at ||f - V_h w|| <= 1e-10 ||f||.
 #include <cmath>
+#include <vector>
 
 #include "stb_internal.h"
+#include "stb_toeplitz.h"
 
 namespace stb {
 
 constexpr int NB = 64;
 
-template <class AT>
-__global__ void k_copy_to_f64(const AT *__restrict__ src, size_t n, double *__restrict__ dst) {
+template <class S, class T>
+__global__ void k_copy_convert(const S *__restrict__ src, size_t n, T *__restrict__ dst) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = (double)src[i];
+    if (i < n) dst[i] = (T)src[i];
 }
 
 // Cholesky of diagonal tile kb (updates from the left already applied).
-__global__ void __launch_bounds__(256) k_potrf_diag(double *__restrict__ L, int E, int kb,
+template <class T>
+__global__ void __launch_bounds__(256) k_potrf_diag(T *__restrict__ L, int E, int kb,
                                                     int32_t *__restrict__ status) {
-    __shared__ double T[NB][NB + 1];
+    __shared__ T Tt[NB][NB + 1];
     const int b0 = kb * NB, n = min(NB, E - b0);
     for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
         int i = t / NB, j = t % NB;
-        T[i][j] = (i < n && j < n && j <= i) ? L[(size_t)(b0 + i) * E + b0 + j] : 0.0;
+        Tt[i][j] = (i < n && j < n && j <= i) ? L[(size_t)(b0 + i) * E + b0 + j] : (T)0;
     }
     __syncthreads();
     for (int c = 0; c < n; ++c) {
         if (threadIdx.x == 0) {
-            double p = T[c][c];
-            if (!(p > 0.0)) {
+            T p = Tt[c][c];
+            if (!(p > (T)0)) {
                 atomicCAS(status, 0, STB_ERR_NOT_SPD);
-                p = 1.0;
+                p = (T)1;
             }
-            T[c][c] = sqrt(p);
+            Tt[c][c] = sqrt(p);
         }
         __syncthreads();
-        const double inv = 1.0 / T[c][c];
-        for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) T[i][c] *= inv;
+        const T inv = (T)1 / Tt[c][c];
+        for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) Tt[i][c] *= inv;
         __syncthreads();
         const int m = n - c - 1;  // trailing size
         for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
             int i = c + 1 + t / m, j = c + 1 + t % m;
-            if (j <= i) T[i][j] = fma(-T[i][c], T[j][c], T[i][j]);
+            if (j <= i) Tt[i][j] = fma(-Tt[i][c], Tt[j][c], Tt[i][j]);
         }
         __syncthreads();
     }
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
         int i = t / n, j = t % n;
-        L[(size_t)(b0 + i) * E + b0 + j] = j <= i ? T[i][j] : 0.0;
+        L[(size_t)(b0 + i) * E + b0 + j] = j <= i ? Tt[i][j] : (T)0;
     }
 }
 
 // Panel: L_ik = A_ik L_kk^{-T} for the tile rows i > kb.
-__global__ void __launch_bounds__(128) k_trsm_panel(double *__restrict__ L, int E, int kb) {
-    __shared__ double Lk[NB][NB + 1];
-    __shared__ double A[NB][NB + 1];
+template <class T>
+__global__ void __launch_bounds__(128) k_trsm_panel(T *__restrict__ L, int E, int kb) {
+    __shared__ T Lk[NB][NB + 1];
+    __shared__ T A[NB][NB + 1];
     const int b0 = kb * NB, n = min(NB, E - b0);
     const int i0 = (kb + 1 + blockIdx.x) * NB, mrows = min(NB, E - i0);
     for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
         int i = t / NB, j = t % NB;
-        Lk[i][j] = (i < n && j < n) ? L[(size_t)(b0 + i) * E + b0 + j] : 0.0;
-        A[i][j] = (i < mrows && j < n) ? L[(size_t)(i0 + i) * E + b0 + j] : 0.0;
+        Lk[i][j] = (i < n && j < n) ? L[(size_t)(b0 + i) * E + b0 + j] : (T)0;
+        A[i][j] = (i < mrows && j < n) ? L[(size_t)(i0 + i) * E + b0 + j] : (T)0;
     }
     __syncthreads();
     for (int row = threadIdx.x; row < mrows; row += blockDim.x) {
         for (int c = 0; c < n; ++c) {
-            double x = A[row][c];
+            T x = A[row][c];
             for (int cc = 0; cc < c; ++cc) x = fma(-A[row][cc], Lk[c][cc], x);
             A[row][c] = x / Lk[c][c];
         }
@@ -83,29 +95,29 @@ __global__ void __launch_bounds__(128) k_trsm_panel(double *__restrict__ L, int 
     }
 }
 
-// 64x64 FP64 tile product helper: acc (4x4 per thread, 256 threads) +=
-// P (rows of tile) * Q^T, both read from global in 32-wide chunks.
-struct TileAcc {
-    double v[4][4];
+// 64x64 tile product helper: acc (4x4 per thread, 256 threads) +=
+// P (rows of the tile) * Q^T, both read from global in 32-wide chunks.
+template <class T> struct TileAcc {
+    T v[4][4];
 };
 
-__device__ __forceinline__ void tile_mma_abt(TileAcc &acc, const double *P, size_t ldp, int prow,
-                                             int pcol, const double *Q, size_t ldq, int qrow,
-                                             int qcol, int E, int kn, double (*Ps)[33],
-                                             double (*Qs)[33]) {
+template <class T>
+__device__ __forceinline__ void tile_mma_abt(TileAcc<T> &acc, const T *P, size_t ldp, int prow,
+                                             int pcol, const T *Q, size_t ldq, int qrow, int qcol,
+                                             int E, int kn, T (*Ps)[33], T (*Qs)[33]) {
     // acc[i][j] += sum_k P[prow+i][pcol+k] * Q[qrow+j][qcol+k], k < kn
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     for (int k0 = 0; k0 < kn; k0 += 32) {
         for (int t = threadIdx.x; t < NB * 32; t += blockDim.x) {
             int r = t / 32, kk = t % 32;
             int pr = prow + r, qr = qrow + r, pc = pcol + k0 + kk, qc = qcol + k0 + kk;
-            Ps[r][kk] = (pr < E && k0 + kk < kn) ? P[(size_t)pr * ldp + pc] : 0.0;
-            Qs[r][kk] = (qr < E && k0 + kk < kn) ? Q[(size_t)qr * ldq + qc] : 0.0;
+            Ps[r][kk] = (pr < E && k0 + kk < kn) ? P[(size_t)pr * ldp + pc] : (T)0;
+            Qs[r][kk] = (qr < E && k0 + kk < kn) ? Q[(size_t)qr * ldq + qc] : (T)0;
         }
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < 32; ++kk) {
-            double a[4], b[4];
+            T a[4], b[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 a[u] = Ps[4 * ty + u][kk];
@@ -121,8 +133,9 @@ __device__ __forceinline__ void tile_mma_abt(TileAcc &acc, const double *P, size
 }
 
 // Trailing update A_ij -= L_ik L_jk^T for kb < j <= i.
-__global__ void __launch_bounds__(256) k_syrk_update(double *__restrict__ L, int E, int kb, int nb) {
-    __shared__ double Ps[NB][33], Qs[NB][33];
+template <class T>
+__global__ void __launch_bounds__(256) k_syrk_update(T *__restrict__ L, int E, int kb) {
+    __shared__ T Ps[NB][33], Qs[NB][33];
     const int t = blockIdx.x;
     int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
     while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
@@ -130,39 +143,39 @@ __global__ void __launch_bounds__(256) k_syrk_update(double *__restrict__ L, int
     const int jj = t - ii * (ii + 1) / 2;
     const int i0 = (kb + 1 + ii) * NB, j0 = (kb + 1 + jj) * NB, b0 = kb * NB;
     const int kn = min(NB, E - b0);
-    TileAcc acc;
+    TileAcc<T> acc;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc.v[u][v] = 0.0;
-    tile_mma_abt(acc, L, E, i0, b0, L, E, j0, b0, E, kn, Ps, Qs);
+        for (int v = 0; v < 4; ++v) acc.v[u][v] = (T)0;
+    tile_mma_abt<T>(acc, L, E, i0, b0, L, E, j0, b0, E, kn, Ps, Qs);
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     for (int u = 0; u < 4; ++u)
         for (int v = 0; v < 4; ++v) {
             int r = i0 + 4 * ty + u, c = j0 + 4 * tx + v;
             if (r < E && c < E) L[(size_t)r * E + c] -= acc.v[u][v];
         }
-    (void)nb;
 }
 
 // Inverse of every diagonal tile of L (lower triangular), in parallel.
-__global__ void __launch_bounds__(64) k_trtri_diag(const double *__restrict__ L,
-                                                   double *__restrict__ Li, int E) {
-    __shared__ double T[NB][NB + 1];
-    __shared__ double X[NB][NB + 1];
+template <class T>
+__global__ void __launch_bounds__(64) k_trtri_diag(const T *__restrict__ L, T *__restrict__ Li,
+                                                   int E) {
+    __shared__ T Tt[NB][NB + 1];
+    __shared__ T X[NB][NB + 1];
     const int b0 = blockIdx.x * NB, n = min(NB, E - b0);
     for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
         int i = t / NB, j = t % NB;
-        T[i][j] = (i < n && j < n) ? L[(size_t)(b0 + i) * E + b0 + j] : 0.0;
-        X[i][j] = 0.0;
+        Tt[i][j] = (i < n && j < n) ? L[(size_t)(b0 + i) * E + b0 + j] : (T)0;
+        X[i][j] = (T)0;
     }
     __syncthreads();
     const int c = threadIdx.x;  // column of the inverse
     if (c < n) {
         for (int i = c; i < n; ++i) {
-            double x = (i == c) ? 1.0 : 0.0;
-            for (int m = c; m < i; ++m) x = fma(-T[i][m], X[m][c], x);
-            X[i][c] = x / T[i][i];
+            T x = (i == c) ? (T)1 : (T)0;
+            for (int m = c; m < i; ++m) x = fma(-Tt[i][m], X[m][c], x);
+            X[i][c] = x / Tt[i][i];
         }
     }
     __syncthreads();
@@ -173,33 +186,33 @@ __global__ void __launch_bounds__(64) k_trtri_diag(const double *__restrict__ L,
 }
 
 // Tile row i of L^{-1}: Li_ij = -Li_ii sum_{m=j}^{i-1} L_im Li_mj, j < i.
-// Li tiles are read transposed through a staging copy (Q^T form).
-__global__ void __launch_bounds__(256) k_trtri_row(const double *__restrict__ L,
-                                                   double *__restrict__ Li, int E, int i) {
-    __shared__ double Ps[NB][33], Qs[NB][33];
-    __shared__ double Tt[NB][NB + 1];  // T^T, T = sum L_im Li_mj
+template <class T>
+__global__ void __launch_bounds__(256) k_trtri_row(const T *__restrict__ L, T *__restrict__ Li,
+                                                   int E, int i) {
+    __shared__ T Ps[NB][33], Qs[NB][33];
+    __shared__ T Tt[NB][NB + 1];  // T^T, T = sum L_im Li_mj
     const int j = blockIdx.x;
     const int i0 = i * NB, j0 = j * NB;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    TileAcc acc;
+    TileAcc<T> acc;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc.v[u][v] = 0.0;
+        for (int v = 0; v < 4; ++v) acc.v[u][v] = (T)0;
     for (int m = j; m < i; ++m) {
         const int m0 = m * NB;
-        // acc[r][c] += sum_k L[i0+r][m0+k] * Li[m0+k][j0+c]  (Q = Li^T: Q[c][k] = Li[m0+k][j0+c])
+        // acc[r][c] += sum_k L[i0+r][m0+k] * Li[m0+k][j0+c]  (Q[c][k] = Li[m0+k][j0+c])
         for (int k0 = 0; k0 < NB; k0 += 32) {
             for (int t = threadIdx.x; t < NB * 32; t += blockDim.x) {
                 int r = t / 32, kk = t % 32;
                 int gr = i0 + r, gk = m0 + k0 + kk, gc = j0 + r;
-                Ps[r][kk] = (gr < E && gk < E) ? L[(size_t)gr * E + gk] : 0.0;
-                Qs[r][kk] = (gk < E && gc < E) ? Li[(size_t)gk * E + gc] : 0.0;
+                Ps[r][kk] = (gr < E && gk < E) ? L[(size_t)gr * E + gk] : (T)0;
+                Qs[r][kk] = (gk < E && gc < E) ? Li[(size_t)gk * E + gc] : (T)0;
             }
             __syncthreads();
 #pragma unroll 4
             for (int kk = 0; kk < 32; ++kk) {
-                double a[4], b[4];
+                T a[4], b[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     a[u] = Ps[4 * ty + u][kk];
@@ -213,26 +226,25 @@ __global__ void __launch_bounds__(256) k_trtri_row(const double *__restrict__ L,
             __syncthreads();
         }
     }
-    // store T^T so that the second product reads it as Q[c][k] = T[k][c]
     for (int u = 0; u < 4; ++u)
         for (int v = 0; v < 4; ++v) Tt[4 * tx + v][4 * ty + u] = acc.v[u][v];
     __syncthreads();
-    TileAcc out;
+    TileAcc<T> out;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) out.v[u][v] = 0.0;
+        for (int v = 0; v < 4; ++v) out.v[u][v] = (T)0;
     for (int k0 = 0; k0 < NB; k0 += 32) {
         for (int t = threadIdx.x; t < NB * 32; t += blockDim.x) {
             int r = t / 32, kk = t % 32;
             int gr = i0 + r, gk = i0 + k0 + kk;
-            Ps[r][kk] = (gr < E && gk < E) ? Li[(size_t)gr * E + gk] : 0.0;
+            Ps[r][kk] = (gr < E && gk < E) ? Li[(size_t)gr * E + gk] : (T)0;
             Qs[r][kk] = Tt[r][k0 + kk];
         }
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < 32; ++kk) {
-            double a[4], b[4];
+            T a[4], b[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 a[u] = Ps[4 * ty + u][kk];
@@ -252,8 +264,9 @@ __global__ void __launch_bounds__(256) k_trtri_row(const double *__restrict__ L,
         }
 }
 
-__global__ void k_transpose(const double *__restrict__ A, double *__restrict__ B, int E) {
-    __shared__ double t[32][33];
+template <class T>
+__global__ void k_transpose(const T *__restrict__ A, T *__restrict__ B, int E) {
+    __shared__ T t[32][33];
     int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 32 + threadIdx.y;
     for (int k = 0; k < 32; k += 8)
         if (x < E && y + k < E) t[threadIdx.y + k][threadIdx.x] = A[(size_t)(y + k) * E + x];
@@ -266,37 +279,39 @@ __global__ void k_transpose(const double *__restrict__ A, double *__restrict__ B
 
 constexpr int MAXR = 8;  // right-hand sides per pass of the march kernels
 
-// r_r = f_r^k - sum_{d=1}^{k} V^d w_r^{k-d}: one warp per row l, all rhs of
-// the group [r0, r0 + nr) together so that each V^d row is read once.
-template <class AT>
+// rv_r[l] = base_r[l] - sum_{d=1}^{dmax} V^d[l,:] x_r^{k-d}: one warp per row
+// l, all right-hand sides of the group [r0, r0 + nr) together so that each
+// V^d row is read once.  AT: storage of V; T: arithmetic of the march.
+template <class AT, class T>
 __global__ void __launch_bounds__(256)
-k_history(const AT *__restrict__ V, int E, int n_steps, int r0, int nr, int k,
-          const double *__restrict__ f, const double *__restrict__ w, double *__restrict__ rv) {
+k_history(const AT *__restrict__ V, int E, int n_steps, int r0, int nr, int k, int dmax,
+          const double *__restrict__ base, size_t base_rstride, size_t base_off,
+          const T *__restrict__ x, T *__restrict__ rv) {
     const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (l >= E) return;
-    double acc[MAXR];
+    T acc[MAXR];
 #pragma unroll
-    for (int r = 0; r < MAXR; ++r) acc[r] = 0.0;
+    for (int r = 0; r < MAXR; ++r) acc[r] = (T)0;
     const size_t EE = (size_t)E * E, SE = (size_t)n_steps * E;
     constexpr int U = 8;  // independent loads in flight per lane
-    for (int d = 1; d <= k; ++d) {
+    for (int d = 1; d <= dmax; ++d) {
         const AT *row = V + d * EE + (size_t)l * E;
-        const double *wk = w + (size_t)(k - d) * E;
+        const T *wk = x + (size_t)(k - d) * E;
         int j0 = 0;
         for (; j0 + 32 * U <= E; j0 += 32 * U) {
-            double v[U];
+            T v[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = (double)row[j0 + 32 * u + lane];
+            for (int u = 0; u < U; ++u) v[u] = (T)row[j0 + 32 * u + lane];
 #pragma unroll
             for (int r = 0; r < MAXR; ++r)
                 if (r < nr) {
-                    const double *wr = wk + (size_t)(r0 + r) * SE + j0 + lane;
+                    const T *wr = wk + (size_t)(r0 + r) * SE + j0 + lane;
 #pragma unroll
                     for (int u = 0; u < U; ++u) acc[r] = fma(v[u], wr[32 * u], acc[r]);
                 }
         }
         for (int j = j0 + lane; j < E; j += 32) {
-            double v = (double)row[j];
+            T v = (T)row[j];
 #pragma unroll
             for (int r = 0; r < MAXR; ++r)
                 if (r < nr) acc[r] = fma(v, wk[(size_t)(r0 + r) * SE + j], acc[r]);
@@ -305,40 +320,144 @@ k_history(const AT *__restrict__ V, int E, int n_steps, int r0, int nr, int k,
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) {
         if (r >= nr) break;
-        double a = acc[r];
+        T a = acc[r];
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) rv[(size_t)(r0 + r) * E + l] = f[(size_t)(r0 + r) * SE + (size_t)k * E + l] - a;
+        if (lane == 0)
+            rv[(size_t)(r0 + r) * E + l] =
+                (T)(base[(size_t)(r0 + r) * base_rstride + base_off + l] - (double)a);
     }
 }
 
+// Far history of a panel of PB steps k = kp + c (c < nb): all contributions
+// of the steps before the panel,
+//   sum_{d : 0 <= k-d < kp} V^d[l,:] x_r^{k-d},
+// a skinny product (PB columns per right-hand side) over the blocks
+// d = 1..kp+nb-1.  Register tiling: a warp owns R rows, a lane four
+// consecutive columns j, so one vector load of V feeds 4 x PB FMAs per row and
+// one load of x feeds R x 4.  The block range is cut into gridDim.y slices of
+// dz blocks whose partial sums k_far_reduce adds up.
+constexpr int PB = 8;
+constexpr int FAR_NZ = 16;  // at most this many slices
+template <class T, int PR>
+constexpr int far_rows_per_warp() { return (sizeof(T) == 4 ? 4 : 2) / PR; }
+
+// four consecutive elements p[0..3] as T; VEC: p is 16-byte aligned and all
+// four are in range, else only the first `left` of them are
+template <class S, class T, bool VEC>
+__device__ __forceinline__ void load4(const S *__restrict__ p, int left, T v[4]) {
+    if constexpr (VEC && sizeof(S) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = (T)q.x, v[1] = (T)q.y, v[2] = (T)q.z, v[3] = (T)q.w;
+    } else if constexpr (VEC) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0];
+        const double2 b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = (T)a.x, v[1] = (T)a.y, v[2] = (T)b.x, v[3] = (T)b.y;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = u < left ? (T)p[u] : (T)0;
+    }
+}
+
+// part[z][r][c][l] = slice z's share of the far history (T)
+template <class AT, class T, int PR, bool VEC>
+__global__ void __launch_bounds__(256, 2)
+k_history_far(const AT *__restrict__ V, int E, int n_steps, int nrhs, int kp, int nb, int dz,
+              const T *__restrict__ x, T *__restrict__ part) {
+    constexpr int FAR_R = far_rows_per_warp<T, PR>();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int l0 = (blockIdx.x * 8 + warp) * FAR_R;
+    const int dlo = 1 + (int)blockIdx.y * dz, dhi = min(dlo + dz, kp + nb);
+    const size_t EE = (size_t)E * E, SE = (size_t)n_steps * E;
+    for (int r0 = 0; r0 < nrhs; r0 += PR) {
+        T acc[PR][FAR_R][PB];
+#pragma unroll
+        for (int r = 0; r < PR; ++r)
+#pragma unroll
+            for (int i = 0; i < FAR_R; ++i)
+#pragma unroll
+                for (int c = 0; c < PB; ++c) acc[r][i][c] = (T)0;
+        for (int d = dlo; d < dhi; ++d) {
+            // columns c with 0 <= kp + c - d < kp (non-empty for 1 <= d < kp + nb, kp >= 1)
+            const int cl = max(kp, d) - kp, ch = min(kp + nb - 1, kp - 1 + d) - kp;
+            const AT *Vd = V + (size_t)d * EE;
+#pragma unroll 1
+            for (int j = 4 * lane; j < E; j += 128) {
+                T v[FAR_R][4];
+#pragma unroll
+                for (int i = 0; i < FAR_R; ++i)  // rows past E re-read row E-1, never stored
+                    load4<AT, T, VEC>(Vd + (size_t)min(l0 + i, E - 1) * E + j, E - j, v[i]);
+#pragma unroll
+                for (int c = 0; c < PB; ++c) {
+                    if (c < cl || c > ch) continue;
+#pragma unroll
+                    for (int r = 0; r < PR; ++r) {
+                        if (r0 + r >= nrhs) continue;
+                        T xv[4];
+                        load4<T, T, VEC>(x + (size_t)(r0 + r) * SE + (size_t)(kp + c - d) * E + j,
+                                         E - j, xv);
+#pragma unroll
+                        for (int i = 0; i < FAR_R; ++i)
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) acc[r][i][c] = fma(v[i][u], xv[u], acc[r][i][c]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < PR; ++r)
+#pragma unroll
+            for (int i = 0; i < FAR_R; ++i)
+#pragma unroll
+                for (int c = 0; c < PB; ++c) {
+                    T a = acc[r][i][c];
+                    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                    if (lane == 0 && r0 + r < nrhs && c < nb && l0 + i < E)
+                        part[(((size_t)blockIdx.y * nrhs + r0 + r) * PB + c) * E + l0 + i] = a;
+                }
+    }
+}
+
+// hv_r[c][l] = f_r^{kp+c}[l] - sum_z part[z][r][c][l]  (c < nb)
+template <class T>
+__global__ void k_far_reduce(const T *__restrict__ part, int nz, int E, int n_steps, int nrhs, int kp,
+                             int nb, const double *__restrict__ f, double *__restrict__ hv) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)nrhs * nb * E) return;
+    const int l = (int)(i % E), c = (int)((i / E) % nb), r = (int)(i / ((size_t)E * nb));
+    double s = 0.0;
+    for (int z = 0; z < nz; ++z) s += (double)part[(((size_t)z * nrhs + r) * PB + c) * E + l];
+    hv[((size_t)r * PB + c) * E + l] = f[(size_t)r * n_steps * E + (size_t)(kp + c) * E + l] - s;
+}
+
 // out_r[l] = sum_{j in tri(l)} M[l][j] in_r[j]; lower: j <= l, else j >= l.
+template <class T>
 __global__ void __launch_bounds__(256)
-k_trmv(const double *__restrict__ M, int E, int nrhs, int lower, const double *__restrict__ in,
-       size_t in_stride, double *__restrict__ out, size_t out_stride) {
+k_trmv(const T *__restrict__ M, int E, int nrhs, int lower, const T *__restrict__ in,
+       size_t in_stride, T *__restrict__ out, size_t out_stride) {
     const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (l >= E) return;
-    const double *row = M + (size_t)l * E;
+    const T *row = M + (size_t)l * E;
     const int jlo = lower ? 0 : l, jhi = lower ? l + 1 : E;
     for (int r0 = 0; r0 < nrhs; r0 += MAXR) {
-        double acc[MAXR];
+        T acc[MAXR];
 #pragma unroll
-        for (int r = 0; r < MAXR; ++r) acc[r] = 0.0;
+        for (int r = 0; r < MAXR; ++r) acc[r] = (T)0;
         constexpr int U = 8;
         int j0 = jlo;
         for (; j0 + 32 * U <= jhi; j0 += 32 * U) {
-            double v[U];
+            T v[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) v[u] = row[j0 + 32 * u + lane];
 #pragma unroll
             for (int r = 0; r < MAXR; ++r)
                 if (r0 + r < nrhs) {
-                    const double *ir = in + (size_t)(r0 + r) * in_stride + j0 + lane;
+                    const T *ir = in + (size_t)(r0 + r) * in_stride + j0 + lane;
 #pragma unroll
                     for (int u = 0; u < U; ++u) acc[r] = fma(v[u], ir[32 * u], acc[r]);
                 }
         }
         for (int j = j0 + lane; j < jhi; j += 32) {
-            double v = row[j];
+            T v = row[j];
 #pragma unroll
             for (int r = 0; r < MAXR; ++r)
                 if (r0 + r < nrhs) acc[r] = fma(v, in[(size_t)(r0 + r) * in_stride + j], acc[r]);
@@ -346,80 +465,222 @@ k_trmv(const double *__restrict__ M, int E, int nrhs, int lower, const double *_
 #pragma unroll
         for (int r = 0; r < MAXR; ++r) {
             if (r0 + r >= nrhs) break;
-            double a = acc[r];
+            T a = acc[r];
             for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
             if (lane == 0) out[(size_t)(r0 + r) * out_stride + l] = a;
         }
     }
 }
 
+// ---------------------------------------------------- refinement kernels ---
+// w += delta (FP64 += FP32)
+__global__ void k_update(double *__restrict__ w, const float *__restrict__ delta, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] += (double)delta[i];
+}
+
+// out[0] = ||a||^2, out[1] = ||b||^2 (one CTA)
+__global__ void k_norms2(const double *__restrict__ a, const double *__restrict__ b, size_t n,
+                         double *__restrict__ out) {
+    __shared__ double red[2][32];
+    double sa = 0.0, sb = 0.0;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+        sa = fma(a[i], a[i], sa);
+        sb = fma(b[i], b[i], sb);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = sa;
+        red[1][threadIdx.x >> 5] = sb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) {
+            x += red[0][wi];
+            y += red[1][wi];
+        }
+        out[0] = x;
+        out[1] = y;
+    }
+}
+
+// ---------------------------------------------------------------- driver ---
+// Workspace header (first 256 bytes): int32 status, int32 refinements,
+// double relative residual of the last solve.
+struct SolveHeader {
+    int32_t status;
+    int32_t refinements;
+    double rel_residual;
+};
+
 struct SolveLayout {
-    double *L, *Li, *LiT, *rv, *zv;
+    void *L, *Li, *LiT, *rv, *zv;  // T
+    double *hv;                   // panel right-hand sides [nrhs][PB][E]
+    void *part;                   // far-history slices [FAR_NZ][nrhs][PB][E] (T)
+    float *delta;                // mixed: correction [nrhs][n_steps][E]
+    double *r;                    // mixed: residual / right-hand side
+    void *df;                     // mixed: scratch of the double-float product
+    double *norms;                // mixed: ||r||^2, ||f||^2
     size_t bytes;
 };
 
-static SolveLayout solve_layout(int64_t E, int nrhs, void *ws, size_t cap) {
+static SolveLayout solve_layout(int64_t E, int n_steps, int nrhs, bool mixed, void *ws, size_t cap) {
     Carve c(ws, cap);
     SolveLayout S{};
-    S.L = c.take<double>((size_t)E * E);
-    S.Li = c.take<double>((size_t)E * E);
-    S.LiT = c.take<double>((size_t)E * E);
-    S.rv = c.take<double>((size_t)nrhs * E);
-    S.zv = c.take<double>((size_t)nrhs * E);
+    const size_t tb = mixed ? sizeof(float) : sizeof(double);
+    S.L = c.take<char>((size_t)E * E * tb);
+    S.Li = c.take<char>((size_t)E * E * tb);
+    S.LiT = c.take<char>((size_t)E * E * tb);
+    S.rv = c.take<char>((size_t)nrhs * E * tb);
+    S.zv = c.take<char>((size_t)nrhs * E * tb);
+    S.hv = c.take<double>((size_t)nrhs * PB * E);
+    S.part = c.take<char>((size_t)FAR_NZ * nrhs * PB * E * tb);
+    if (mixed) {
+        const size_t n = (size_t)nrhs * n_steps * E;
+        S.delta = c.take<float>(n);
+        S.r = c.take<double>(n);
+        S.df = c.take<char>(toeplitz_df_bytes(E, n_steps, nrhs));
+        S.norms = c.take<double>(2);
+    }
     S.bytes = c.off;
     return S;
 }
 
-template <class AT>
-static stb_status run_solve(const AT *V, int E, int n_steps, int nrhs, const double *f, double *w,
-                            const SolveLayout &S, int32_t *status, cudaStream_t s) {
+// V^0 = L L^T, then L^{-1} and its transpose, all in T.
+template <class AT, class T>
+static stb_status factorize(const AT *V, int E, const SolveLayout &S, int32_t *status,
+                            cudaStream_t s) {
     stb_status st;
+    T *L = (T *)S.L, *Li = (T *)S.Li, *LiT = (T *)S.LiT;
     const size_t EE = (size_t)E * E;
     count_launch(s);
-    k_copy_to_f64<AT><<<(unsigned)((EE + 255) / 256), 256, 0, s>>>(V, EE, S.L);
-    if ((st = check_launch("k_copy_to_f64"))) return st;
+    k_copy_convert<AT, T><<<(unsigned)((EE + 255) / 256), 256, 0, s>>>(V, EE, L);
+    if ((st = check_launch("k_copy_convert"))) return st;
     const int nb = (E + NB - 1) / NB;
     for (int kb = 0; kb < nb; ++kb) {
         count_launch(s);
-        k_potrf_diag<<<1, 256, 0, s>>>(S.L, E, kb, status);
+        k_potrf_diag<T><<<1, 256, 0, s>>>(L, E, kb, status);
         if ((st = check_launch("k_potrf_diag"))) return st;
         const int m = nb - kb - 1;
         if (m == 0) break;
         count_launch(s);
-        k_trsm_panel<<<m, 128, 0, s>>>(S.L, E, kb);
+        k_trsm_panel<T><<<m, 128, 0, s>>>(L, E, kb);
         if ((st = check_launch("k_trsm_panel"))) return st;
         count_launch(s);
-        k_syrk_update<<<m * (m + 1) / 2, 256, 0, s>>>(S.L, E, kb, nb);
+        k_syrk_update<T><<<m * (m + 1) / 2, 256, 0, s>>>(L, E, kb);
         if ((st = check_launch("k_syrk_update"))) return st;
     }
-    STB_CUDA(cudaMemsetAsync(S.Li, 0, EE * sizeof(double), s));
+    STB_CUDA(cudaMemsetAsync(Li, 0, EE * sizeof(T), s));
     count_launch(s);
-    k_trtri_diag<<<nb, 64, 0, s>>>(S.L, S.Li, E);
+    k_trtri_diag<T><<<nb, 64, 0, s>>>(L, Li, E);
     if ((st = check_launch("k_trtri_diag"))) return st;
     for (int i = 1; i < nb; ++i) {
         count_launch(s);
-        k_trtri_row<<<i, 256, 0, s>>>(S.L, S.Li, E, i);
+        k_trtri_row<T><<<i, 256, 0, s>>>(L, Li, E, i);
         if ((st = check_launch("k_trtri_row"))) return st;
     }
     count_launch(s);
-    k_transpose<<<dim3((E + 31) / 32, (E + 31) / 32), dim3(32, 8), 0, s>>>(S.Li, S.LiT, E);
-    if ((st = check_launch("k_transpose"))) return st;
+    k_transpose<T><<<dim3((E + 31) / 32, (E + 31) / 32), dim3(32, 8), 0, s>>>(Li, LiT, E);
+    return check_launch("k_transpose");
+}
+
+// March in time: x^k = L^{-T} L^{-1} (rhs^k - sum_{d>=1} V^d x^{k-d}) into x
+// (T), in panels of PB steps: one far-history pass per panel, then per step
+// the near history (d < PB, inside the panel) and the two triangular products.
+template <class AT, class T>
+static stb_status march(const AT *V, int E, int n_steps, int nrhs, const double *rhs, T *x,
+                        const SolveLayout &S, cudaStream_t s) {
+    stb_status st;
     const unsigned rows_blocks = (unsigned)((E * 32 + 255) / 256);
     const size_t SE = (size_t)n_steps * E;
-    for (int k = 0; k < n_steps; ++k) {
-        for (int r0 = 0; r0 < nrhs; r0 += MAXR) {
+    T *rv = (T *)S.rv, *zv = (T *)S.zv, *part = (T *)S.part;
+    const bool vec = E % 4 == 0 && reinterpret_cast<uintptr_t>(V) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(x) % 16 == 0;
+    const int rows_cta = 8 * (nrhs == 1 ? far_rows_per_warp<T, 1>() : far_rows_per_warp<T, 2>());
+    const unsigned far_rows = (unsigned)((E + rows_cta - 1) / rows_cta);
+    for (int kp = 0; kp < n_steps; kp += PB) {
+        const int nb = min(PB, n_steps - kp);
+        int nz = 0;
+        if (kp > 0) {  // about 8 resident CTAs on each of the 152 SMs
+            const int n_d = kp + nb - 1;
+            nz = min(min(FAR_NZ, n_d), max(1, (int)((8 * 152 + far_rows - 1) / far_rows)));
+            const int dz = (n_d + nz - 1) / nz;
+            nz = (n_d + dz - 1) / dz;
+            const auto kern = nrhs == 1 ? (vec ? k_history_far<AT, T, 1, true>
+                                               : k_history_far<AT, T, 1, false>)
+                                        : (vec ? k_history_far<AT, T, 2, true>
+                                               : k_history_far<AT, T, 2, false>);
             count_launch(s);
-            k_history<AT><<<rows_blocks, 256, 0, s>>>(V, E, n_steps, r0, min(MAXR, nrhs - r0), k, f,
-                                                      w, S.rv);
-            if ((st = check_launch("k_history"))) return st;
+            kern<<<dim3(far_rows, (unsigned)nz), 256, 0, s>>>(V, E, n_steps, nrhs, kp, nb, dz, x,
+                                                              part);
+            if ((st = check_launch("k_history_far"))) return st;
         }
+        const size_t nred = (size_t)nrhs * nb * E;
         count_launch(s);
-        k_trmv<<<rows_blocks, 256, 0, s>>>(S.Li, E, nrhs, 1, S.rv, E, S.zv, E);
-        if ((st = check_launch("k_trmv(L^-1)"))) return st;
-        count_launch(s);
-        k_trmv<<<rows_blocks, 256, 0, s>>>(S.LiT, E, nrhs, 0, S.zv, E, w + (size_t)k * E, SE);
-        if ((st = check_launch("k_trmv(L^-T)"))) return st;
+        k_far_reduce<T><<<(unsigned)((nred + 255) / 256), 256, 0, s>>>(part, nz, E, n_steps, nrhs, kp, nb,
+                                                                       rhs, S.hv);
+        if ((st = check_launch("k_far_reduce"))) return st;
+        for (int c = 0; c < nb; ++c) {
+            const int k = kp + c;
+            for (int r0 = 0; r0 < nrhs; r0 += MAXR) {
+                count_launch(s);
+                k_history<AT, T><<<rows_blocks, 256, 0, s>>>(V, E, n_steps, r0, min(MAXR, nrhs - r0),
+                                                             k, c, S.hv, (size_t)PB * E,
+                                                             (size_t)c * E, x, rv);
+                if ((st = check_launch("k_history"))) return st;
+            }
+            count_launch(s);
+            k_trmv<T><<<rows_blocks, 256, 0, s>>>((const T *)S.Li, E, nrhs, 1, rv, E, zv, E);
+            if ((st = check_launch("k_trmv(L^-1)"))) return st;
+            count_launch(s);
+            k_trmv<T><<<rows_blocks, 256, 0, s>>>((const T *)S.LiT, E, nrhs, 0, zv, E,
+                                                  x + (size_t)k * E, SE);
+            if ((st = check_launch("k_trmv(L^-T)"))) return st;
+        }
     }
+    return STB_OK;
+}
+
+constexpr double REFINE_TOL = 1e-10;
+constexpr int MAX_REFINE = 8;
+
+static stb_status solve_mixed(const float *V, int E, int n_steps, int nrhs, const double *f,
+                              double *w, const SolveLayout &S, int32_t *status, void *ws,
+                              cudaStream_t s) {
+    stb_status st = factorize<float, float>(V, E, S, status, s);
+    if (st) return st;
+    const size_t n = (size_t)nrhs * n_steps * E;
+    STB_CUDA(cudaMemsetAsync(w, 0, n * sizeof(double), s));
+    const double *rhs = f;  // first pass solves with f itself
+    SolveHeader hdr{STB_OK, 0, 0.0};
+    for (int it = 0; it <= MAX_REFINE; ++it) {
+        if ((st = march<float, float>(V, E, n_steps, nrhs, rhs, S.delta, S, s))) return st;
+        count_launch(s);
+        k_update<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, S.delta, n);
+        if ((st = check_launch("k_update"))) return st;
+        if ((st = toeplitz_df(V, E, n_steps, nrhs, w, DF_RESIDUAL, f, 0.0, S.r, S.df, s))) return st;
+        count_launch(s);
+        k_norms2<<<1, 1024, 0, s>>>(S.r, f, n, S.norms);
+        if ((st = check_launch("k_norms2"))) return st;
+        double nrm[2];
+        STB_CUDA(cudaMemcpyAsync(nrm, S.norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
+        STB_CUDA(cudaStreamSynchronize(s));
+        hdr.refinements = it;
+        hdr.rel_residual = nrm[1] > 0.0 ? std::sqrt(nrm[0] / nrm[1]) : std::sqrt(nrm[0]);
+        if (hdr.rel_residual <= REFINE_TOL || !std::isfinite(hdr.rel_residual)) break;
+        rhs = S.r;
+    }
+    int32_t dev_status = 0;
+    STB_CUDA(cudaMemcpyAsync(&dev_status, status, sizeof dev_status, cudaMemcpyDeviceToHost, s));
+    STB_CUDA(cudaStreamSynchronize(s));
+    hdr.status = dev_status;
+    if (dev_status == STB_OK && !(hdr.rel_residual <= REFINE_TOL)) hdr.status = STB_ERR_NOT_CONVERGED;
+    STB_CUDA(cudaMemcpyAsync(ws, &hdr, sizeof hdr, cudaMemcpyHostToDevice, s));
+    STB_CUDA(cudaStreamSynchronize(s));
     return STB_OK;
 }
 
@@ -429,8 +690,10 @@ using namespace stb;
 
 extern "C" stb_status stb_solve_workspace_size(const stb_mesh *mesh, const stb_params *p,
                                                int32_t nrhs, size_t *bytes) {
-    if (!mesh || !p || !bytes || nrhs < 1) return fail(STB_ERR_INVALID_ARG, "invalid argument");
-    *bytes = align256(solve_layout(mesh->m.n_tris, nrhs, nullptr, 0).bytes);
+    if (!mesh || !p || !bytes || nrhs < 1 || p->n_steps < 1)
+        return fail(STB_ERR_INVALID_ARG, "invalid argument");
+    const bool mixed = p->precision == STB_PREC_MIXED;
+    *bytes = align256(solve_layout(mesh->m.n_tris, p->n_steps, nrhs, mixed, nullptr, 0).bytes);
     return STB_OK;
 }
 
@@ -441,18 +704,40 @@ extern "C" stb_status stb_dirichlet_solve(const stb_mesh *mesh, const stb_params
     if (p->n_steps < 1) return fail(STB_ERR_INVALID_ARG, "n_steps must be >= 1");
     if (p->storage != STB_STORE_F64 && p->storage != STB_STORE_F32)
         return fail(STB_ERR_INVALID_ARG, "bad storage");
+    const bool mixed = p->precision == STB_PREC_MIXED;
+    if (mixed && p->storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "mixed-precision solve needs STB_STORE_F32 blocks");
     const int64_t E = mesh->m.n_tris;
     if (E > 65535) return fail(STB_ERR_INVALID_ARG, "E must be <= 65535");
-    SolveLayout S = solve_layout(E, nrhs, ws, ws_bytes);
+    SolveLayout S = solve_layout(E, p->n_steps, nrhs, mixed, ws, ws_bytes);
     stb_status st = check_workspace(ws, ws_bytes, S.bytes);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
     int32_t *status = status_word(ws);
-    if (p->storage == STB_STORE_F64)
-        st = run_solve<double>((const double *)V, (int)E, p->n_steps, nrhs, f, w, S, status, s);
-    else
-        st = run_solve<float>((const float *)V, (int)E, p->n_steps, nrhs, f, w, S, status, s);
-    if (st) return st;
+    if (mixed) {
+        st = solve_mixed((const float *)V, (int)E, p->n_steps, nrhs, f, w, S, status, ws, s);
+        if (st) return st;
+    } else {
+        if (p->storage == STB_STORE_F64) {
+            st = factorize<double, double>((const double *)V, (int)E, S, status, s);
+            if (!st) st = march<double, double>((const double *)V, (int)E, p->n_steps, nrhs, f, w, S, s);
+        } else {
+            st = factorize<float, double>((const float *)V, (int)E, S, status, s);
+            if (!st) st = march<float, double>((const float *)V, (int)E, p->n_steps, nrhs, f, w, S, s);
+        }
+        if (st) return st;
+    }
     return stb_workspace_status(ws, stream);
+}
+
+extern "C" stb_status stb_solve_report(const void *ws, stb_stream stream, int32_t *refinements,
+                                       double *rel_residual) {
+    if (!ws) return fail(STB_ERR_INVALID_ARG, "workspace is NULL");
+    SolveHeader hdr{};
+    STB_CUDA(cudaMemcpyAsync(&hdr, ws, sizeof hdr, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    STB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (refinements) *refinements = hdr.refinements;
+    if (rel_residual) *rel_residual = hdr.rel_residual;
+    return STB_OK;
 }

@@ -10,6 +10,7 @@
 
 #include "stb_internal.h"
 #include "stb_toeplitz.h"
+#include "stb_toeplitz_tc.h"
 
 namespace stb {
 
@@ -106,6 +107,119 @@ stb_status toeplitz_fp64(const void *A, int32_t storage, int64_t E, int32_t n_st
     return check_launch("k_toeplitz_reduce");
 }
 
+// ------------------------------------------------- double-float product ---
+__global__ void k_split(const double *__restrict__ x, size_t n, float2 *__restrict__ xs) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    const float hi = (float)v;
+    xs[i] = make_float2(hi, (float)(v - (double)hi));
+}
+
+// a (w_hi + w_lo) = p + e (p the FP32 product, e its error by FMA) plus the
+// small w_lo term, accumulated into (hi, lo) by an error-free two-sum.
+__device__ __forceinline__ void df_acc(float a, float2 x, float &hi, float &lo) {
+    const float p = a * x.x;
+    const float e = fmaf(a, x.x, -p);
+    const float t = fmaf(a, x.y, e);
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += err + t;
+}
+
+__global__ void __launch_bounds__(MV_THREADS)
+k_toeplitz_df_partial(const float *__restrict__ A, int E, int n_steps, int nrhs,
+                      const float2 *__restrict__ xs, double *__restrict__ part) {
+    __shared__ float As[TM][TJ + 1];
+    __shared__ float2 Xs[TK][TJ + 1];
+    const int n_kt = (n_steps + TK - 1) / TK;
+    const int lt = blockIdx.x, kt = blockIdx.y % n_kt, r = blockIdx.y / n_kt, dr = blockIdx.z;
+    const int l0 = lt * TM, k0 = kt * TK, d0 = dr * TD;
+    if (d0 > k0 + TK - 1 || d0 >= n_steps) return;
+    const int d1 = min(min(d0 + TD, n_steps), k0 + TK);
+    const int tx = threadIdx.x % TK, ty = threadIdx.x / TK;
+    constexpr int RPT = TM / (MV_THREADS / TK);  // rows per thread
+    float hi[RPT], lo[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) hi[i] = lo[i] = 0.f;
+    const size_t EE = (size_t)E * E;
+    const float2 *xr = xs + (size_t)r * n_steps * E;
+    for (int d = d0; d < d1; ++d) {
+        const float *Ad = A + (size_t)d * EE;
+        for (int j0 = 0; j0 < E; j0 += TJ) {
+            for (int t = threadIdx.x; t < TM * TJ; t += MV_THREADS) {
+                int i = t / TJ, jj = t % TJ, l = l0 + i, j = j0 + jj;
+                As[i][jj] = (l < E && j < E) ? Ad[(size_t)l * E + j] : 0.f;
+            }
+            for (int t = threadIdx.x; t < TK * TJ; t += MV_THREADS) {
+                int c = t / TJ, jj = t % TJ, k = k0 + c, j = j0 + jj;
+                Xs[c][jj] = (k < n_steps && k - d >= 0 && j < E) ? xr[(size_t)(k - d) * E + j]
+                                                                   : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int jj = 0; jj < TJ; ++jj) {
+                const float2 xv = Xs[tx][jj];
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) df_acc(As[ty * RPT + i][jj], xv, hi[i], lo[i]);
+            }
+            __syncthreads();
+        }
+    }
+    const int k = k0 + tx;
+    if (k >= n_steps) return;
+    double *pr = part + (((size_t)dr * nrhs + r) * n_steps + k) * E;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        int l = l0 + ty * RPT + i;
+        if (l < E) pr[l] = (double)hi[i] + (double)lo[i];
+    }
+}
+
+__global__ void k_toeplitz_df_reduce(const double *__restrict__ part, int E, int n_steps, int nrhs,
+                                     int mode, const double *__restrict__ f, double beta,
+                                     double *__restrict__ y) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)nrhs * n_steps * E;
+    if (idx >= total) return;
+    int k = (int)((idx / E) % n_steps);
+    double s = 0.0;
+    for (int dr = 0; dr * TD <= k; ++dr) s += part[dr * total + idx];
+    if (mode == DF_RESIDUAL)
+        y[idx] = f[idx] - s;
+    else
+        y[idx] = beta == 0.0 ? s : fma(beta, y[idx], s);
+}
+
+size_t toeplitz_df_bytes(int64_t E, int32_t n_steps, int32_t nrhs) {
+    return toeplitz_partial_bytes(E, n_steps, nrhs) +
+           align256((size_t)nrhs * n_steps * E * sizeof(float2));
+}
+
+stb_status toeplitz_df(const float *A, int64_t E, int32_t n_steps, int32_t nrhs, const double *x,
+                       int mode, const double *f, double beta, double *y, void *scratch,
+                       cudaStream_t s) {
+    double *part = static_cast<double *>(scratch);
+    float2 *xs = reinterpret_cast<float2 *>(static_cast<char *>(scratch) +
+                                            toeplitz_partial_bytes(E, n_steps, nrhs));
+    const size_t total = (size_t)nrhs * n_steps * E;
+    count_launch(s);
+    k_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(x, total, xs);
+    stb_status st = check_launch("k_split");
+    if (st) return st;
+    int n_kt = (n_steps + TK - 1) / TK, n_dr = (n_steps + TD - 1) / TD;
+    dim3 grid((unsigned)((E + TM - 1) / TM), (unsigned)(n_kt * nrhs), (unsigned)n_dr);
+    count_launch(s);
+    k_toeplitz_df_partial<<<grid, MV_THREADS, 0, s>>>(A, (int)E, n_steps, nrhs, xs, part);
+    if ((st = check_launch("k_toeplitz_df_partial"))) return st;
+    count_launch(s);
+    k_toeplitz_df_reduce<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, (int)E, n_steps, nrhs,
+                                                                         mode, f, beta, y);
+    return check_launch("k_toeplitz_df_reduce");
+}
+
 // Scratch of stb_toeplitz_matvec_static: every device that loads the library
 // holds these bytes until the process exits.  Host code must not hand the
 // symbol itself to a kernel (on the host it names a host-side shadow); the
@@ -178,4 +292,38 @@ extern "C" stb_status stb_toeplitz_matvec(const void *A, int32_t a_storage, int6
     STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
     double *part = reinterpret_cast<double *>(static_cast<char *>(ws) + 256);
     return toeplitz_fp64(A, a_storage, E, n_steps, nrhs, x, beta, y, part, s);
+}
+
+extern "C" stb_status stb_toeplitz_ex_workspace_size(int64_t E, int32_t n_steps, int32_t nrhs,
+                                                     int32_t arith, size_t *bytes) {
+    stb_status st = stb_toeplitz_workspace_size(E, n_steps, nrhs, bytes);
+    if (st) return st;
+    switch (arith) {
+    case STB_ARITH_FP64: return STB_OK;
+    case STB_ARITH_DF: *bytes = 256 + toeplitz_df_bytes(E, n_steps, nrhs); return STB_OK;
+    case STB_ARITH_TF32: *bytes = 256 + toeplitz_tc_bytes(E, n_steps, nrhs); return STB_OK;
+    default: return fail(STB_ERR_INVALID_ARG, "arith must be STB_ARITH_FP64, _DF or _TF32");
+    }
+}
+
+extern "C" stb_status stb_toeplitz_matvec_ex(const void *A, int32_t a_storage, int64_t E,
+                                             int32_t n_steps, int32_t nrhs, const double *x,
+                                             double beta, double *y, int32_t arith, void *ws,
+                                             size_t ws_bytes, stb_stream stream) {
+    if (arith == STB_ARITH_FP64)
+        return stb_toeplitz_matvec(A, a_storage, E, n_steps, nrhs, x, beta, y, ws, ws_bytes, stream);
+    if (!A || !x || !y) return fail(STB_ERR_INVALID_ARG, "A, x and y must be given");
+    if (a_storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "STB_ARITH_DF and STB_ARITH_TF32 need STB_STORE_F32 blocks");
+    size_t need;
+    stb_status st = stb_toeplitz_ex_workspace_size(E, n_steps, nrhs, arith, &need);
+    if (st) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    void *scratch = static_cast<char *>(ws) + 256;
+    if (arith == STB_ARITH_DF)
+        return toeplitz_df((const float *)A, E, n_steps, nrhs, x, DF_AXPBY, nullptr, beta, y,
+                           scratch, s);
+    return toeplitz_tc((const float *)A, E, n_steps, nrhs, x, beta, y, scratch, status_word(ws), s);
 }

@@ -7,4 +7,15 @@ size_t toeplitz_partial_bytes(int64_t E, int32_t n_steps, int32_t nrhs);
 // y = beta y + T(A) x in FP64; `part` has toeplitz_partial_bytes() bytes.
 stb_status toeplitz_fp64(const void *A, int32_t storage, int64_t E, int32_t n_steps, int32_t nrhs,
                          const double *x, double beta, double *y, double *part, cudaStream_t s);
+
+// The same product for FP32 blocks in FP32-pair ("double-float") arithmetic:
+// exact FP32 products with a two-float split of x, error-free two-sums, so
+// the result carries about 44 significant bits without FP64 instructions.
+//   mode DF_AXPBY:    y = beta y + T(A) x
+//   mode DF_RESIDUAL: y = f - T(A) x
+enum { DF_AXPBY = 0, DF_RESIDUAL = 1 };
+size_t toeplitz_df_bytes(int64_t E, int32_t n_steps, int32_t nrhs);
+stb_status toeplitz_df(const float *A, int64_t E, int32_t n_steps, int32_t nrhs, const double *x,
+                       int mode, const double *f, double beta, double *y, void *scratch,
+                       cudaStream_t s);
 }  // namespace stb

@@ -243,6 +243,80 @@ def test_toeplitz_matvec_vs_oracle():
         assert np.abs(got - expect).max() <= 4 * EPS * scale
 
 
+def _matvec_ex(A32, x, y0, beta, arith):
+    n_steps, E = A32.shape[0], A32.shape[1]
+    nrhs = x.shape[0]
+    Ad = torch.tensor(A32, dtype=torch.float32, device="cuda")
+    xd = torch.tensor(x, device="cuda")
+    yd = torch.tensor(y0, device="cuda")
+    ws = torch.empty(capi.stb_toeplitz_ex_workspace_size(E, n_steps, nrhs, arith), dtype=torch.uint8,
+                     device="cuda")
+    capi.stb_toeplitz_matvec_ex(Ad, capi.STB_STORE_F32, E, n_steps, nrhs, xd, beta, yd, arith, ws)
+    capi.stb_workspace_status(ws)
+    return yd.cpu().numpy()
+
+
+# (E, n_steps, nrhs): one 64-column box; two time tiles with a ragged tail;
+# three right-hand sides (boxes of two, one unused); five right-hand sides
+# (boxes of four, a partly used second group); rows not a multiple of 128
+@pytest.mark.parametrize("E,n_steps,nrhs", [(256, 16, 1), (200, 70, 1), (200, 11, 3), (132, 9, 5),
+                                            (388, 130, 2)])
+def test_toeplitz_matvec_tf32_tensor_cores(E, n_steps, nrhs):
+    """tcgen05 TF32 product: blocks read as TF32 (10 stored mantissa bits,
+    truncated or rounded: relative error <= 2^-10), x rounded to TF32
+    (<= 2^-11), FP32 accumulation (<= K 2^-23 with any rounding of the adder):
+    |y - y_exact| <= (2^-10 + 2^-10 + K 2^-23) sum_d |A^d| |x^{k-d}|, K = E (k+1)
+    terms."""
+    rng = np.random.default_rng(11)
+    A = rng.normal(size=(n_steps, E, E)).astype(np.float32).astype(np.float64)
+    x = rng.normal(size=(nrhs, n_steps, E))
+    y0 = rng.normal(size=(nrhs, n_steps, E))
+    got = _matvec_ex(A, x, y0, -0.75, capi.STB_ARITH_TF32)
+    exact = -0.75 * y0 + oracle.toeplitz_matvec(A, x)
+    mag = oracle.toeplitz_matvec(np.abs(A), np.abs(x))
+    K = E * (np.arange(n_steps) + 1.0)
+    bound = (2.0 ** -10 + 2.0 ** -10 + K[None, :, None] * 2.0 ** -23) * mag + 1e-14 * np.abs(y0)
+    err = np.abs(got - exact)
+    assert np.all(err <= bound), float((err / bound).max())
+    rel = np.linalg.norm(got - exact) / np.linalg.norm(exact)
+    assert rel < 2e-3, rel
+    print("TF32 matvec E=%d n=%d nrhs=%d: rel error %.2e, worst err/bound %.2f"
+          % (E, n_steps, nrhs, rel, (err / bound).max()))
+
+
+def test_toeplitz_matvec_double_float():
+    """FP32 blocks in FP32-pair arithmetic: exact products, two-float split of
+    x (about 48 bits), error-free sums: far below FP32 rounding."""
+    rng = np.random.default_rng(12)
+    E, n_steps, nrhs = 150, 13, 2
+    A = rng.normal(size=(n_steps, E, E)).astype(np.float32).astype(np.float64)
+    x = rng.normal(size=(nrhs, n_steps, E))
+    y0 = rng.normal(size=(nrhs, n_steps, E))
+    got = _matvec_ex(A, x, y0, 2.0, capi.STB_ARITH_DF)
+    exact = 2.0 * y0 + oracle.toeplitz_matvec(A, x)
+    mag = oracle.toeplitz_matvec(np.abs(A), np.abs(x)) + 2.0 * np.abs(y0)
+    err = np.abs(got - exact)
+    assert np.all(err <= 2.0 ** -40 * mag), float((err / mag).max())
+
+
+def test_toeplitz_matvec_ex_rejects():
+    E, n_steps = 150, 4  # E not a multiple of 4: no TF32 tensor maps
+    A = torch.zeros((n_steps, E, E), dtype=torch.float32, device="cuda")
+    x = torch.zeros((1, n_steps, E), dtype=torch.float64, device="cuda")
+    ws = torch.empty(capi.stb_toeplitz_ex_workspace_size(E, n_steps, 1, capi.STB_ARITH_TF32),
+                     dtype=torch.uint8, device="cuda")
+    with pytest.raises(capi.StbError) as e:
+        capi.stb_toeplitz_matvec_ex(A, capi.STB_STORE_F32, E, n_steps, 1, x, 0.0, x.clone(),
+                                    capi.STB_ARITH_TF32, ws)
+    assert e.value.code == -1
+    A64 = torch.zeros((n_steps, 152, 152), dtype=torch.float64, device="cuda")
+    with pytest.raises(capi.StbError):
+        capi.stb_toeplitz_matvec_ex(A64, capi.STB_STORE_F64, 152, n_steps, 1, x, 0.0, x.clone(),
+                                    capi.STB_ARITH_DF, ws)
+    with pytest.raises(capi.StbError):
+        capi.stb_toeplitz_ex_workspace_size(E, n_steps, 1, 7)
+
+
 @pytest.fixture(scope="module")
 def c1_problem():
     wl = workloads.workload("cube192_e16")
@@ -312,6 +386,129 @@ def test_full_pipeline_matches_oracle_pipeline(c1_problem):
     assert np.linalg.norm(w - wo) / np.linalg.norm(wo) < 1e-8
     e2, r2 = oracle.neumann_error(nodes, tris, alpha, T, n, src, wo)
     assert abs(prob.relative_error() - math.sqrt(e2 / r2)) < 1e-8
+
+
+def test_mixed_projection_and_rhs(c1_problem):
+    """Mixed precision: data projection in FP32 arithmetic (relative error of
+    a few FP32 ulps per element mean); right-hand side with the stored FP32 K
+    in double-float arithmetic (as accurate as FP64 up to ~2^-44)."""
+    wl = c1_problem["wl"]
+    nodes, tris, alpha, T, n, src = (wl["nodes"], wl["tris"], wl["alpha"], wl["T"], wl["n_steps"],
+                                     wl["sources"])
+    prob = pipeline.DirichletProblem(nodes, tris, alpha, T, n, src, precision=capi.STB_PREC_MIXED,
+                                     storage=capi.STB_STORE_F32)
+    prob.project()
+    go = oracle.project_dirichlet(nodes, tris, alpha, T, n, src)
+    g = prob.g.cpu().numpy()
+    assert np.abs(g - go).max() <= 1e-5 * np.abs(go).max()
+    prob.assemble()
+    prob.g.copy_(torch.tensor(go))
+    prob.rhs()
+    area, _ = oracle.triangle_geometry(nodes, tris)
+    K32 = prob.K.double().cpu().numpy()
+    fo = oracle.dirichlet_rhs(area, K32, go, T)
+    f = prob.f.cpu().numpy()
+    assert np.linalg.norm(f - fo) <= 1e-12 * np.linalg.norm(fo)
+
+
+def test_mixed_solve_refines_to_the_fp32_system(c1_problem):
+    """Mixed precision: FP32 factorisation and march, refined with a
+    double-float residual until ||f - V_h w|| <= 1e-10 ||f||.  The result must
+    solve the stored (FP32) system -- all of it: FP32 rounding leaves the
+    stored V^0 symmetric only to ~1e-7, so the reference is the FP64 residual
+    of the full block system and its dense FP64 solve (difference bounded by
+    cond(V_h) times the residual)."""
+    wl = c1_problem["wl"]
+    nodes, tris, alpha, T, n, src = (wl["nodes"], wl["tris"], wl["alpha"], wl["T"], wl["n_steps"],
+                                     wl["sources"])
+    prob = pipeline.DirichletProblem(nodes, tris, alpha, T, n, src, precision=capi.STB_PREC_MIXED,
+                                     storage=capi.STB_STORE_F32)
+    prob.assemble()
+    prob.project()
+    prob.rhs()
+    prob.solve()
+    it, res = capi.stb_solve_report(prob.ws_solve)
+    assert 1 <= it <= 8 and res <= 1e-10, (it, res)
+    V32 = prob.V.double().cpu().numpy()
+    f = prob.f.cpu().numpy()
+    w = prob.w.cpu().numpy()
+    r64 = f - oracle.toeplitz_matvec(V32, w)
+    res64 = np.linalg.norm(r64) / np.linalg.norm(f)
+    assert res64 <= 2e-10, res64
+    E = len(tris)
+    M = np.zeros((n * E, n * E))
+    for k in range(n):
+        for i in range(k + 1):
+            M[k * E:(k + 1) * E, i * E:(i + 1) * E] = V32[k - i]
+    wo = np.linalg.solve(M, f[0].reshape(-1))
+    kappa = np.linalg.cond(M)
+    rel = np.linalg.norm(w[0].reshape(-1) - wo) / np.linalg.norm(wo)
+    assert rel <= 4 * kappa * 2e-10, (rel, kappa)
+    print("mixed solve: %d refinements, residual %.2e (FP64 recheck %.2e), |w - w_dense|/|w| %.2e, "
+          "cond %.1f" % (it, res, res64, rel, kappa))
+
+
+def _split_first_triangle(nodes, tris):
+    """Split triangle 0 at its centroid into three (coplanar, conforming):
+    E = 12 n^2 + 2, which is not a multiple of 4."""
+    a, b, c = tris[0]
+    m = len(nodes)
+    nodes = np.vstack([nodes, nodes[[a, b, c]].mean(axis=0)])
+    tris = np.vstack([[[a, b, m], [b, c, m], [c, a, m]], tris[1:]]).astype(np.int32)
+    return nodes, tris
+
+
+def _dense_block_system(V, n, E):
+    M = np.zeros((n * E, n * E))
+    for k in range(n):
+        for i in range(k + 1):
+            M[k * E:(k + 1) * E, i * E:(i + 1) * E] = V[k - i]
+    return M
+
+
+@pytest.mark.parametrize("split,n_steps,nrhs", [(False, 19, 3), (True, 19, 3), (True, 9, 1)])
+def test_solve_panels_rhs_groups_ragged_rows(split, n_steps, nrhs):
+    """Forward substitution with ragged time panels (n_steps not a multiple of
+    the panel width 8), several right-hand sides (rhs groups of the far-history
+    kernel), and E = 194 (no vector loads) against E = 192: FP64 solve versus
+    the dense FP64 solve; mixed solve (FP32 blocks) by its FP64 residual."""
+    nodes, tris = workloads.cube_mesh(4)
+    if split:
+        nodes, tris = _split_first_triangle(nodes, tris)
+    E = len(tris)
+    alpha, T = 0.8, 0.7
+    rng = np.random.default_rng(21)
+    f = rng.normal(size=(nrhs, n_steps, E))
+    for precision, storage in ((capi.STB_PREC_FP64, capi.STB_STORE_F64),
+                               (capi.STB_PREC_MIXED, capi.STB_STORE_F32)):
+        mesh = capi.Mesh(nodes, tris)
+        p = capi.stb_default_params(alpha, T, n_steps, precision=precision, storage=storage)
+        dt = torch.float64 if storage == capi.STB_STORE_F64 else torch.float32
+        V = torch.empty((n_steps, E, E), dtype=dt, device="cuda")
+        ws = torch.empty(capi.stb_assemble_workspace_size(mesh, p), dtype=torch.uint8, device="cuda")
+        capi.stb_assemble(mesh, p, V, None, ws)
+        fd = torch.tensor(f, device="cuda")
+        wd = torch.empty_like(fd)
+        wss = torch.empty(capi.stb_solve_workspace_size(mesh, p, nrhs), dtype=torch.uint8,
+                          device="cuda")
+        capi.stb_dirichlet_solve(mesh, p, V, fd, nrhs, wd, wss)
+        w = wd.cpu().numpy()
+        Vh = V.double().cpu().numpy()
+        r64 = f - oracle.toeplitz_matvec(Vh, w)
+        res = np.linalg.norm(r64) / np.linalg.norm(f)
+        if precision == capi.STB_PREC_FP64:
+            M = _dense_block_system(Vh, n_steps, E)
+            kappa = np.linalg.cond(M)
+            wo = np.linalg.solve(M, f.reshape(nrhs, -1).T).T.reshape(nrhs, n_steps, E)
+            rel = np.linalg.norm(w - wo) / np.linalg.norm(wo)
+            assert rel <= 16 * kappa * EPS, (rel, kappa)
+            assert res <= 64 * kappa * EPS, res
+        else:
+            it, rep = capi.stb_solve_report(wss)
+            assert 1 <= it <= 8 and rep <= 1e-10, (it, rep)
+            assert res <= 2e-10, res
+        print("solve E=%d n=%d nrhs=%d prec=%d: residual %.2e cond %.1f"
+              % (E, n_steps, nrhs, precision, res, kappa))
 
 
 def test_not_spd_is_reported():
