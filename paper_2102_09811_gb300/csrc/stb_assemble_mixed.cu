@@ -16,7 +16,8 @@
 //  * d >= 2 from the definition eq. V_d reduced to one time variable,
 //      V^d(r) = int_{-h}^{h} (h - |s|) G(r, dh + s) ds,   K^d: G -> (r.n_y)/(2 delta) G,
 //    by Gauss-Legendre on every interval [kh, (k+1)h] (6 nodes for k = 1,
-//    4 for k >= 2); one exp2 per node feeds two blocks (d = k, k + 1).
+//    then 4, 3 or 2 as k grows, see mixed_chunk_ng); one exp2 per node feeds
+//    two blocks (d = k, k + 1).
 // The regularised rules of touching pairs are stored in difference form so
 // that x - y keeps its relative accuracy as it shrinks.
 #include <cmath>
@@ -85,24 +86,56 @@ __device__ __forceinline__ void k_d01(float rho, float irho, const MixConsts &g,
     }
 }
 
-// Node sums of interval k >= 2 (table `iv`, see stb_assemble.h) for one point
-// with squared distance rr: fall = (sum cVf e, sum cKf e) feeds block k,
-// rise = (sum cVr e, sum cKr e) feeds block k + 1, e = exp2(rr b).
-__device__ __forceinline__ void interval_sums(const float *iv, float rr, float2 &fall,
-                                              float2 &rise) {
-    const float4 b = *reinterpret_cast<const float4 *>(iv);
-    const float2 rr2 = make_float2(rr, rr);
-    const float2 t01 = __fmul2_rn(rr2, make_float2(b.x, b.y));
-    const float2 t23 = __fmul2_rn(rr2, make_float2(b.z, b.w));
-    const float e[MIX_NG] = {ex2(t01.x), ex2(t01.y), ex2(t23.x), ex2(t23.y)};
-    fall = make_float2(0.f, 0.f);
-    rise = make_float2(0.f, 0.f);
+// 16-byte table load; SMEM: from shared memory, as a volatile access so that
+// the compiler does not hoist a whole chunk of table entries into registers
+// out of the quadrature-point loops.
+template <bool SMEM>
+__device__ __forceinline__ float4 ld_tab(const float *p) {
+    if constexpr (SMEM) {
+        float4 v;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "r"((uint32_t)__cvta_generic_to_shared(p)));
+        return v;
+    } else {
+        return *reinterpret_cast<const float4 *>(p);
+    }
+}
+
+// Node sums of one interval k >= 2 (NG nodes, table `iv`, see stb_assemble.h)
+// for NP points with squared distances rr2[p] = (rr, rr): fall[p] =
+// (sum cVf e, sum cKf e) feeds block k, rise[p] = (sum cVr e, sum cKr e)
+// feeds block k + 1, e = exp2(rr b).  The table entries are loaded once for
+// all NP points.
+template <int NG, int NP, bool SMEM>
+__device__ __forceinline__ void interval_sums(const float *iv, const float2 (&rr2)[NP],
+                                              float2 (&fall)[NP], float2 (&rise)[NP]) {
+    const float4 b = ld_tab<SMEM>(iv);
+    float e[NP][4];
 #pragma unroll
-    for (int q = 0; q < MIX_NG; ++q) {
-        const float4 c = *reinterpret_cast<const float4 *>(iv + 4 + 4 * q);
-        const float2 ee = make_float2(e[q], e[q]);
-        fall = __ffma2_rn(make_float2(c.x, c.y), ee, fall);
-        rise = __ffma2_rn(make_float2(c.z, c.w), ee, rise);
+    for (int p = 0; p < NP; ++p) {
+        const float2 t01 = __fmul2_rn(rr2[p], make_float2(b.x, b.y));
+        e[p][0] = ex2(t01.x);
+        e[p][1] = ex2(t01.y);
+        if (NG == 3) {
+            e[p][2] = ex2(rr2[p].x * b.z);
+        } else if (NG == 4) {
+            const float2 t23 = __fmul2_rn(rr2[p], make_float2(b.z, b.w));
+            e[p][2] = ex2(t23.x);
+            e[p][3] = ex2(t23.y);
+        }
+        fall[p] = make_float2(0.f, 0.f);
+        rise[p] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+        const float4 c = ld_tab<SMEM>(iv + 4 + 4 * q);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const float2 ee = make_float2(e[p][q], e[p][q]);
+            fall[p] = __ffma2_rn(make_float2(c.x, c.y), ee, fall[p]);
+            rise[p] = __ffma2_rn(make_float2(c.z, c.w), ee, rise[p]);
+        }
     }
 }
 
@@ -113,9 +146,64 @@ template <> __device__ __forceinline__ void store_m<float>(float *p, float v) { 
 constexpr int MREG_THREADS = 128;
 constexpr int MAX_RULE_M = 256;
 
+// One chunk of blocks d0..d0+MIX_CH-1 (intervals u = 0..MIX_CH, k = d0-1+u)
+// for NP quadrature points with rr2[p] = (rr, rr) and wp[p] = (w, w r.n_y).
+// FIRST: d0 = 2, whose interval k = 1 was summed in pass 1.  Intervals past
+// n_steps-1 carry zero weights, so the loop runs without guards.
+template <int NG, int NP, bool FIRST>
+__device__ __forceinline__ void chunk_points(const float *tab, const float2 (&rr2)[NP],
+                                             const float2 (&wp)[NP], float2 (&acc)[MIX_CH]) {
+#pragma unroll
+    for (int u = FIRST ? 1 : 0; u <= MIX_CH; ++u) {
+        float2 fall[NP], rise[NP];
+        interval_sums<NG, NP, true>(tab + u * (4 + 4 * NG), rr2, fall, rise);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if (u >= 1) acc[u - 1] = __ffma2_rn(wp[p], fall[p], acc[u - 1]);  // block k
+            if (u < MIX_CH) acc[u] = __ffma2_rn(wp[p], rise[p], acc[u]);      // block k+1
+        }
+    }
+}
+
+// All nq x nq points of a separated pair for one chunk, test points in twos
+// so that every table entry loaded from shared memory serves two points.
+template <int NG, bool FIRST>
+__device__ __forceinline__ void chunk_sum(const float *tab, const float *__restrict__ rule, int nq,
+                                          const float4 *xa, const float (&D)[3],
+                                          const float (&B1)[3], const float (&B2)[3],
+                                          const float (&n)[3], float2 (&acc)[MIX_CH]) {
+    for (int b = 0; b < nq; ++b) {
+        const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
+        const float r0b = D[0] - (t1 * B1[0] + t2 * B2[0]);
+        const float r1b = D[1] - (t1 * B1[1] + t2 * B2[1]);
+        const float r2b = D[2] - (t1 * B1[2] + t2 * B2[2]);
+        auto point = [&](int a, float2 &rr2, float2 &wp) {
+            const float4 xq = xa[a];
+            const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
+            const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+            const float rn = r0 * n[0] + r1 * n[1] + r2 * n[2];
+            const float w = xq.w * wb;
+            rr2 = make_float2(rr, rr);
+            wp = make_float2(w, w * rn);
+        };
+        int a = 0;
+        for (; a + 1 < nq; a += 2) {
+            float2 rr2[2], wp[2];
+            point(a, rr2[0], wp[0]);
+            point(a + 1, rr2[1], wp[1]);
+            chunk_points<NG, 2, FIRST>(tab, rr2, wp, acc);
+        }
+        if (a < nq) {
+            float2 rr2[1], wp[1];
+            point(a, rr2[0], wp[0]);
+            chunk_points<NG, 1, FIRST>(tab, rr2, wp, acc);
+        }
+    }
+}
+
 // ------------------------------------------------------ separated pairs ---
-template <int CH, class OutT>
-__global__ void __launch_bounds__(MREG_THREADS)
+template <class OutT>
+__global__ void __launch_bounds__(MREG_THREADS, 5)
 k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E,
                 const float *__restrict__ rule, int nq, const float *__restrict__ nodes,
                 int n_nodes_f, int n_steps, MixConsts g, OutT *__restrict__ V,
@@ -192,48 +280,62 @@ k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris
         if (K) store_m(K + EE + ij, scale * k1);
     }
 
-    // blocks d >= 2 in chunks [d0, d0 + CH): intervals k = d0 - 1 .. d0 + CH - 1
-    for (int d0 = 2; d0 < n_steps; d0 += CH) {
-        float2 acc[CH];  // (V, K) of blocks d0 .. d0 + CH - 1
+    // blocks d >= 2 in chunks [d0, d0 + MIX_CH): intervals k = d0 - 1 .. d0 + MIX_CH - 1
+    const float *tab = nd + MIX_K1;
+    for (int d0 = 2; d0 < n_steps; d0 += MIX_CH) {
+        float2 acc[MIX_CH];  // (V, K) of blocks d0 .. d0 + MIX_CH - 1
 #pragma unroll
-        for (int u = 0; u < CH; ++u) acc[u] = make_float2(0.f, 0.f);
-        if (d0 == 2) acc[0] = make_float2(v2, k2);
-        for (int b = 0; b < nq; ++b) {
-            const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
-            const float r0b = D[0] - (t1 * B1[0] + t2 * B2[0]);
-            const float r1b = D[1] - (t1 * B1[1] + t2 * B2[1]);
-            const float r2b = D[2] - (t1 * B1[2] + t2 * B2[2]);
-            for (int a = 0; a < nq; ++a) {
-                const float4 xq = xa[a];
-                const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
-                const float rr = r0 * r0 + r1 * r1 + r2 * r2;
-                const float rn = r0 * n[0] + r1 * n[1] + r2 * n[2];
-                const float w = xq.w * wb;
-                const float2 wp = make_float2(w, w * rn);
-#pragma unroll
-                for (int u = 0; u <= CH; ++u) {
-                    const int k = d0 - 1 + u;
-                    if (k < 2 || k > n_steps - 1) continue;
-                    float2 fall, rise;
-                    interval_sums(nd + MIX_K1 + (k - 2) * MIX_IV, rr, fall, rise);
-                    if (u >= 1) acc[u - 1] = __ffma2_rn(wp, fall, acc[u - 1]);      // block k
-                    if (u < CH && k + 1 < n_steps) acc[u] = __ffma2_rn(wp, rise, acc[u]);  // block k+1
-                }
-            }
+        for (int u = 0; u < MIX_CH; ++u) acc[u] = make_float2(0.f, 0.f);
+        const int ng = mixed_chunk_ng(d0);
+        if (d0 == 2) {
+            acc[0] = make_float2(v2, k2);
+            chunk_sum<4, true>(tab, rule, nq, xa, D, B1, B2, n, acc);
+        } else if (ng == 4) {
+            chunk_sum<4, false>(tab, rule, nq, xa, D, B1, B2, n, acc);
+        } else if (ng == 3) {
+            chunk_sum<3, false>(tab, rule, nq, xa, D, B1, B2, n, acc);
+        } else {
+            chunk_sum<2, false>(tab, rule, nq, xa, D, B1, B2, n, acc);
         }
 #pragma unroll
-        for (int u = 0; u < CH; ++u) {
+        for (int u = 0; u < MIX_CH; ++u) {
             const int d = d0 + u;
             if (d < n_steps) {
                 store_m(V + (size_t)d * EE + ij, scale * acc[u].x);
                 if (K) store_m(K + (size_t)d * EE + ij, scale * acc[u].y);
             }
         }
+        tab += (MIX_CH + 1) * mixed_iv_floats(ng);
     }
 }
 
 // ------------------------------------------------------- touching pairs ---
 constexpr int MSS_THREADS = 128;
+
+// One chunk of a touching pair's blocks for one point: acc[u] (V),
+// acc[CH + u] (K at (a,b)), acc[2 CH + u] (K at (b,a)) of block d0 + u.
+template <int NG, int CH>
+__device__ __forceinline__ void ss_chunk(const float *tab, int d0, int n_steps, float rr, float w,
+                                         float wa, float wb, float (&acc)[3 * CH]) {
+    const float2 rr2[1] = {make_float2(rr, rr)};
+#pragma unroll
+    for (int u = 0; u <= CH; ++u) {
+        const int k = d0 - 1 + u;
+        if (k < 2 || k > n_steps - 1) continue;
+        float2 fall[1], rise[1];
+        interval_sums<NG, 1, false>(tab + u * (4 + 4 * NG), rr2, fall, rise);
+        if (u >= 1) {
+            acc[u - 1] = fmaf(w, fall[0].x, acc[u - 1]);
+            acc[CH + u - 1] = fmaf(wa, fall[0].y, acc[CH + u - 1]);
+            acc[2 * CH + u - 1] = fmaf(wb, fall[0].y, acc[2 * CH + u - 1]);
+        }
+        if (u < CH && k + 1 < n_steps) {
+            acc[u] = fmaf(w, rise[0].x, acc[u]);
+            acc[CH + u] = fmaf(wa, rise[0].y, acc[CH + u]);
+            acc[2 * CH + u] = fmaf(wb, rise[0].y, acc[2 * CH + u]);
+        }
+    }
+}
 
 struct MixSS {
     const float *p0[4], *p1[4], *p2[4], *p3[4], *w[4];
@@ -350,32 +452,20 @@ k_singular_mixed(const double *__restrict__ geo, const TouchPair *__restrict__ p
     const float v2 = fin[6], ka2 = fin[7], kb2 = fin[8];  // already scaled
     __syncthreads();
 
+    const float *ntab = nodes + MIX_K1;
     for (int d0 = 2; d0 < n_steps; d0 += CH) {
         float acc[3 * CH];
 #pragma unroll
         for (int i = 0; i < 3 * CH; ++i) acc[i] = 0.f;
+        const int ng = mixed_chunk_ng(d0);
         for (int p = threadIdx.x; p < npt; p += MSS_THREADS) {
             float rr, rab, rba, w;
             point(p, rr, rab, rba, w);
-            const float wa = w * rab, wb = w * rba;
-#pragma unroll
-            for (int u = 0; u <= CH; ++u) {
-                const int k = d0 - 1 + u;
-                if (k < 2 || k > n_steps - 1) continue;
-                float2 fall, rise;
-                interval_sums(nodes + MIX_K1 + (k - 2) * MIX_IV, rr, fall, rise);
-                if (u >= 1) {
-                    acc[u - 1] = fmaf(w, fall.x, acc[u - 1]);
-                    acc[CH + u - 1] = fmaf(wa, fall.y, acc[CH + u - 1]);
-                    acc[2 * CH + u - 1] = fmaf(wb, fall.y, acc[2 * CH + u - 1]);
-                }
-                if (u < CH && k + 1 < n_steps) {
-                    acc[u] = fmaf(w, rise.x, acc[u]);
-                    acc[CH + u] = fmaf(wa, rise.y, acc[CH + u]);
-                    acc[2 * CH + u] = fmaf(wb, rise.y, acc[2 * CH + u]);
-                }
-            }
+            if (ng == 4) ss_chunk<4, CH>(ntab, d0, n_steps, rr, w, w * rab, w * rba, acc);
+            else if (ng == 3) ss_chunk<3, CH>(ntab, d0, n_steps, rr, w, w * rab, w * rba, acc);
+            else ss_chunk<2, CH>(ntab, d0, n_steps, rr, w, w * rab, w * rba, acc);
         }
+        ntab += (CH + 1) * mixed_iv_floats(ng);
         reduce(acc, 3 * CH);
         if (threadIdx.x == 0) {
             for (int u = 0; u < CH; ++u) {
@@ -428,9 +518,8 @@ void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<flo
         wf = h * wg * h * (1.0 - ug) * a_;
         wr = h * wg * h * ug * a_;
     };
-    std::vector<double> u1(MIX_NG1), w1(MIX_NG1), u(MIX_NG), wq(MIX_NG);
+    std::vector<double> u1(MIX_NG1), w1(MIX_NG1), u(4), wq(4);
     gauss_legendre01(MIX_NG1, u1.data(), w1.data());
-    gauss_legendre01(MIX_NG, u.data(), wq.data());
     for (int q = 0; q < MIX_NG1; ++q) {
         double b, wf, wr, delta;
         node(1, u1[q], w1[q], b, wf, wr, delta);
@@ -439,16 +528,23 @@ void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<flo
         o[1] = (float)wr;
         o[2] = (float)(wr / (2.0 * delta));
     }
-    for (int k = 2; k <= p.n_steps - 1; ++k) {
-        float *o = nodes.data() + MIX_K1 + (size_t)(k - 2) * MIX_IV;
-        for (int q = 0; q < MIX_NG; ++q) {
-            double b, wf, wr, delta;
-            node(k, u[q], wq[q], b, wf, wr, delta);
-            o[q] = (float)b;
-            o[4 + 4 * q + 0] = (float)wf;
-            o[4 + 4 * q + 1] = (float)(wf / (2.0 * delta));
-            o[4 + 4 * q + 2] = (float)wr;
-            o[4 + 4 * q + 3] = (float)(wr / (2.0 * delta));
+    size_t off = MIX_K1;
+    for (int d0 = 2; d0 < p.n_steps; d0 += MIX_CH) {
+        const int ng = mixed_chunk_ng(d0);
+        gauss_legendre01(ng, u.data(), wq.data());
+        for (int uu = 0; uu <= MIX_CH; ++uu, off += mixed_iv_floats(ng)) {
+            const int k = d0 - 1 + uu;
+            if (k < 2 || k > p.n_steps - 1) continue;  // zero weights
+            float *o = nodes.data() + off;
+            for (int q = 0; q < ng; ++q) {
+                double b, wf, wr, delta;
+                node(k, u[q], wq[q], b, wf, wr, delta);
+                o[q] = (float)b;
+                o[4 + 4 * q + 0] = (float)wf;
+                o[4 + 4 * q + 1] = (float)(wf / (2.0 * delta));
+                o[4 + 4 * q + 2] = (float)wr;
+                o[4 + 4 * q + 3] = (float)(wr / (2.0 * delta));
+            }
         }
     }
 }
@@ -456,7 +552,7 @@ void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<flo
 template <class OutT>
 static stb_status run_mixed_t(const Mesh &m, const stb_params &p, OutT *V, OutT *K,
                               const AssemblyLayout &L, cudaStream_t s) {
-    constexpr int CH = 16;
+    constexpr int CH = MIX_CH;
     const int E = (int)m.n_tris;
     const int nq = p.quad_regular * p.quad_regular;
     const double pi = 3.14159265358979323846, al = p.alpha, h = p.T / p.n_steps;
@@ -468,11 +564,11 @@ static stb_status run_mixed_t(const Mesh &m, const stb_params &p, OutT *V, OutT 
     g.pK = (float)(1.0 / (4.0 * pi * al));
     const int nf = (int)mixed_node_floats(p.n_steps);
     const size_t smem = sizeof(float) * (4 * MAX_RULE_M + (size_t)nf);
-    STB_CUDA(cudaFuncSetAttribute(k_regular_mixed<CH, OutT>,
+    STB_CUDA(cudaFuncSetAttribute(k_regular_mixed<OutT>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((E + MREG_THREADS - 1) / MREG_THREADS, E);
     count_launch(s);
-    k_regular_mixed<CH, OutT><<<grid, MREG_THREADS, smem, s>>>(L.geo, m.d_tris, E, L.mrule, nq,
+    k_regular_mixed<OutT><<<grid, MREG_THREADS, smem, s>>>(L.geo, m.d_tris, E, L.mrule, nq,
                                                                L.mnodes, nf, p.n_steps, g, V, K);
     stb_status st = check_launch("k_regular_mixed");
     if (st) return st;

@@ -190,14 +190,19 @@ def test_mixed_c1_blocks():
     print("mixed C1 max block error: V %.2e K %.2e" % (max(ev), max(ek)))
 
 
+# one to three steps; a partial first chunk; chunks with 4 and 3 time nodes;
+# chunks with 2 nodes (d0 >= 98), full and cut by n_steps, also at small alpha
 @pytest.mark.parametrize("n_face,n_steps,alpha,T", [(2, 1, 1.0, 0.5), (2, 2, 1.0, 0.5), (2, 3, 0.1, 1.0),
-                                                   (2, 13, 10.0, 0.3), (2, 40, 0.5, 2.0)])
+                                                   (2, 13, 10.0, 0.3), (2, 40, 0.5, 2.0),
+                                                   (2, 130, 1.0, 2.0), (2, 100, 0.2, 1.0),
+                                                   (2, 130, 0.05, 1.0)])
 def test_mixed_ragged(n_face, n_steps, alpha, T):
     nodes, tris = workloads.cube_mesh(n_face)
     Vo, Ko = oracle.assemble_rows(nodes, tris, alpha, T, n_steps, np.arange(len(tris)))
     V, K = gpu_assemble_mixed(nodes, tris, alpha, T, n_steps)
     ev, ek = block_errors(V, Vo), block_errors(K, Ko)
     assert max(ev) < MIXED_BOUND and max(ek) < MIXED_BOUND, (ev, ek)
+    print("mixed n_steps=%d alpha=%g: max block error V %.2e K %.2e" % (n_steps, alpha, max(ev), max(ek)))
 
 
 def test_mixed_icosphere():
