@@ -20,33 +20,33 @@ struct AssemblyLayout {
 // Mixed path time quadrature of eq. V_d reduced to one variable,
 //   V^d(r) = int_{(d-1)h}^{dh} (s-(d-1)h) G(r,s) ds + int_{dh}^{(d+1)h} ((d+1)h-s) G(r,s) ds,
 // Gauss-Legendre per interval [kh, (k+1)h]: MIX_NG1 nodes on k = 1; the
-// intervals k >= 2 are evaluated in chunks of MIX_CH blocks d0..d0+MIX_CH-1
-// (intervals k = d0-1..d0+MIX_CH-1) with mixed_chunk_ng(d0) nodes each.
+// intervals k >= 2 are evaluated in chunks of MIX_CH blocks d0..d0+MIX_CH-1:
+// chunk d0 evaluates the intervals k = d0..d0+MIX_CH-1, each once, with
+// mixed_chunk_ng(d0) nodes; the falling side of interval k feeds block k,
+// the rising side block k+1 (the last one carried into the next chunk).
 // The count follows the Gauss error on one interval of the hat-weighted
 // kernel tau^{-3/2} exp(-a/tau), tau = t/h, a = r^2/(4 alpha h): measured
 // relative to the entry wherever the entry is at least 1e-4 of its r = 0
 // value, 4 nodes stay below 8e-7 from k = 2 on, 3 nodes below 1e-8 from
 // k = 16 on and 2 nodes below 2e-7 from k = 96 on.  A chunk takes the count
-// of its first interval.
+// of its first interval, k = d0.
 constexpr int MIX_NG1 = 6;
 constexpr int MIX_CH = 16;
-__host__ __device__ inline int mixed_chunk_ng(int d0) {
-    return d0 - 1 < 16 ? 4 : d0 - 1 < 96 ? 3 : 2;
-}
+__host__ __device__ inline int mixed_chunk_ng(int d0) { return d0 < 16 ? 4 : d0 < 96 ? 3 : 2; }
 // Node table: interval k = 1 as MIX_NG1 float4 (b, cVr, cKr, 0) (only its
-// rising side, block 2, is needed); then per chunk MIX_CH + 1 intervals of
+// rising side, block 2, is needed); then per chunk MIX_CH intervals of
 // mixed_iv_floats(ng) floats: float4 (b_0..b_3, unused entries 0), then per
 // node float4 (cVf, cKf, cVr, cKr).  b is the exp2 scale
 // -log2(e)/(4 alpha delta); c* fold the Gauss weight, the hat weight (falling
 // side: block k, rising side: block k+1) and (4 pi alpha delta)^{-3/2} (K:
 // times 1/(2 delta)).  Intervals past k = n_steps-1 (the tail of the last
-// chunk) and k = 1 in the first chunk have zero weights.
+// chunk) have zero weights.
 constexpr int MIX_K1 = 4 * MIX_NG1;
 __host__ __device__ inline int mixed_iv_floats(int ng) { return 4 + 4 * ng; }
 inline size_t mixed_node_floats(int n_steps) {
     size_t n = MIX_K1;
     for (int d0 = 2; d0 < n_steps; d0 += MIX_CH)
-        n += (size_t)(MIX_CH + 1) * mixed_iv_floats(mixed_chunk_ng(d0));
+        n += (size_t)MIX_CH * mixed_iv_floats(mixed_chunk_ng(d0));
     return n;
 }
 void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<float> &ss,

@@ -146,64 +146,92 @@ template <> __device__ __forceinline__ void store_m<float>(float *p, float v) { 
 constexpr int MREG_THREADS = 128;
 constexpr int MAX_RULE_M = 256;
 
-// One chunk of blocks d0..d0+MIX_CH-1 (intervals u = 0..MIX_CH, k = d0-1+u)
-// for NP quadrature points with rr2[p] = (rr, rr) and wp[p] = (w, w r.n_y).
-// FIRST: d0 = 2, whose interval k = 1 was summed in pass 1.  Intervals past
-// n_steps-1 carry zero weights, so the loop runs without guards.
-template <int NG, int NP, bool FIRST>
-__device__ __forceinline__ void chunk_points(const float *tab, const float2 (&rr2)[NP],
-                                             const float2 (&wp)[NP], float2 (&acc)[MIX_CH]) {
+// Intervals per pass over the quadrature points of a pair.
+constexpr int MIX_G = 4;
+
+// Node sums of MIX_G intervals (tables at tab, stride 4 + 4 NG floats) for one
+// quadrature point: E[g][.] += w e, F[g][.] += w (r.n_y) e, e = exp2(rr b), with
+// the nodes packed in pairs ((0,1), (2,3)) so that one packed FMA serves two.
+template <int NG>
+__device__ __forceinline__ void point_nodes(const float *tab, float2 rr2, float2 w2, float2 wrn2,
+                                            float2 (&E)[MIX_G][2], float2 (&F)[MIX_G][2]) {
 #pragma unroll
-    for (int u = FIRST ? 1 : 0; u <= MIX_CH; ++u) {
-        float2 fall[NP], rise[NP];
-        interval_sums<NG, NP, true>(tab + u * (4 + 4 * NG), rr2, fall, rise);
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            if (u >= 1) acc[u - 1] = __ffma2_rn(wp[p], fall[p], acc[u - 1]);  // block k
-            if (u < MIX_CH) acc[u] = __ffma2_rn(wp[p], rise[p], acc[u]);      // block k+1
+    for (int g = 0; g < MIX_G; ++g) {
+        const float4 b = ld_tab<true>(tab + g * (4 + 4 * NG));
+        const float2 t01 = __fmul2_rn(rr2, make_float2(b.x, b.y));
+        const float2 e01 = make_float2(ex2(t01.x), ex2(t01.y));
+        E[g][0] = __ffma2_rn(w2, e01, E[g][0]);
+        F[g][0] = __ffma2_rn(wrn2, e01, F[g][0]);
+        if (NG == 4) {
+            const float2 t23 = __fmul2_rn(rr2, make_float2(b.z, b.w));
+            const float2 e23 = make_float2(ex2(t23.x), ex2(t23.y));
+            E[g][1] = __ffma2_rn(w2, e23, E[g][1]);
+            F[g][1] = __ffma2_rn(wrn2, e23, F[g][1]);
+        } else if (NG == 3) {
+            const float e2 = ex2(rr2.x * b.z);
+            E[g][1].x = fmaf(w2.x, e2, E[g][1].x);
+            F[g][1].x = fmaf(wrn2.x, e2, F[g][1].x);
         }
     }
 }
 
-// All nq x nq points of a separated pair for one chunk, test points in twos
-// so that every table entry loaded from shared memory serves two points.
-template <int NG, bool FIRST>
-__device__ __forceinline__ void chunk_sum(const float *tab, const float *__restrict__ rule, int nq,
+// Chunk of blocks d0..d0+MIX_CH-1 of one separated pair: the intervals
+// k = d0..d0+MIX_CH-1 in passes of MIX_G over all nq x nq points.  Per pass
+// the points are contracted first (E, F: sums of w e and w (r.n_y) e per
+// interval and node), then the node weights are applied once per interval:
+// falling side -> acc[u] (block k = d0 + u), rising side -> acc[u + 1].
+// n_pass: passes holding at least one interval k <= n_steps - 1.
+template <int NG>
+__device__ __forceinline__ void chunk_sum(const float *tab, int n_pass,
+                                          const float *__restrict__ rule, int nq,
                                           const float4 *xa, const float (&D)[3],
                                           const float (&B1)[3], const float (&B2)[3],
-                                          const float (&n)[3], float2 (&acc)[MIX_CH]) {
-    for (int b = 0; b < nq; ++b) {
-        const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
-        const float r0b = D[0] - (t1 * B1[0] + t2 * B2[0]);
-        const float r1b = D[1] - (t1 * B1[1] + t2 * B2[1]);
-        const float r2b = D[2] - (t1 * B1[2] + t2 * B2[2]);
-        auto point = [&](int a, float2 &rr2, float2 &wp) {
-            const float4 xq = xa[a];
-            const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
-            const float rr = r0 * r0 + r1 * r1 + r2 * r2;
-            const float rn = r0 * n[0] + r1 * n[1] + r2 * n[2];
-            const float w = xq.w * wb;
-            rr2 = make_float2(rr, rr);
-            wp = make_float2(w, w * rn);
-        };
-        int a = 0;
-        for (; a + 1 < nq; a += 2) {
-            float2 rr2[2], wp[2];
-            point(a, rr2[0], wp[0]);
-            point(a + 1, rr2[1], wp[1]);
-            chunk_points<NG, 2, FIRST>(tab, rr2, wp, acc);
+                                          const float (&n)[3], float2 (&acc)[MIX_CH + 1]) {
+    constexpr int IVF = 4 + 4 * NG;
+#pragma unroll
+    for (int pass = 0; pass < MIX_CH / MIX_G; ++pass) {
+        if (pass >= n_pass) break;
+        const float *tg = tab + pass * MIX_G * IVF;
+        float2 E[MIX_G][2], F[MIX_G][2];
+#pragma unroll
+        for (int g = 0; g < MIX_G; ++g)
+            E[g][0] = E[g][1] = F[g][0] = F[g][1] = make_float2(0.f, 0.f);
+        for (int b = 0; b < nq; ++b) {
+            const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
+            const float r0b = D[0] - (t1 * B1[0] + t2 * B2[0]);
+            const float r1b = D[1] - (t1 * B1[1] + t2 * B2[1]);
+            const float r2b = D[2] - (t1 * B1[2] + t2 * B2[2]);
+            for (int a = 0; a < nq; ++a) {
+                const float4 xq = xa[a];
+                const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
+                const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+                const float rn = r0 * n[0] + r1 * n[1] + r2 * n[2];
+                const float w = xq.w * wb, wrn = w * rn;
+                point_nodes<NG>(tg, make_float2(rr, rr), make_float2(w, w), make_float2(wrn, wrn),
+                                E, F);
+            }
         }
-        if (a < nq) {
-            float2 rr2[1], wp[1];
-            point(a, rr2[0], wp[0]);
-            chunk_points<NG, 1, FIRST>(tab, rr2, wp, acc);
+#pragma unroll
+        for (int g = 0; g < MIX_G; ++g) {
+            const float *iv = tg + g * IVF;
+            const float Eq[4] = {E[g][0].x, E[g][0].y, E[g][1].x, E[g][1].y};
+            const float Fq[4] = {F[g][0].x, F[g][0].y, F[g][1].x, F[g][1].y};
+            float2 fall = make_float2(0.f, 0.f), rise = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < NG; ++q) {
+                const float4 c = ld_tab<true>(iv + 4 + 4 * q);
+                fall = __ffma2_rn(make_float2(c.x, c.y), make_float2(Eq[q], Fq[q]), fall);
+                rise = __ffma2_rn(make_float2(c.z, c.w), make_float2(Eq[q], Fq[q]), rise);
+            }
+            const int u = pass * MIX_G + g;
+            acc[u] = __fadd2_rn(acc[u], fall);
+            acc[u + 1] = __fadd2_rn(acc[u + 1], rise);
         }
     }
 }
 
-// ------------------------------------------------------ separated pairs ---
 template <class OutT>
-__global__ void __launch_bounds__(MREG_THREADS, 5)
+__global__ void __launch_bounds__(MREG_THREADS)
 k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E,
                 const float *__restrict__ rule, int nq, const float *__restrict__ nodes,
                 int n_nodes_f, int n_steps, MixConsts g, OutT *__restrict__ V,
@@ -280,23 +308,24 @@ k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris
         if (K) store_m(K + EE + ij, scale * k1);
     }
 
-    // blocks d >= 2 in chunks [d0, d0 + MIX_CH): intervals k = d0 - 1 .. d0 + MIX_CH - 1
+    // blocks d >= 2 in chunks of MIX_CH; chunk d0 evaluates the intervals
+    // k = d0..d0+MIX_CH-1, and the rising side of interval d0-1 (from the
+    // previous chunk, or pass 1 for d0 = 2) is carried into block d0
     const float *tab = nd + MIX_K1;
+    float2 carry = make_float2(v2, k2);
     for (int d0 = 2; d0 < n_steps; d0 += MIX_CH) {
-        float2 acc[MIX_CH];  // (V, K) of blocks d0 .. d0 + MIX_CH - 1
+        float2 acc[MIX_CH + 1];
+        acc[0] = carry;
 #pragma unroll
-        for (int u = 0; u < MIX_CH; ++u) acc[u] = make_float2(0.f, 0.f);
+        for (int u = 1; u <= MIX_CH; ++u) acc[u] = make_float2(0.f, 0.f);
         const int ng = mixed_chunk_ng(d0);
-        if (d0 == 2) {
-            acc[0] = make_float2(v2, k2);
-            chunk_sum<4, true>(tab, rule, nq, xa, D, B1, B2, n, acc);
-        } else if (ng == 4) {
-            chunk_sum<4, false>(tab, rule, nq, xa, D, B1, B2, n, acc);
-        } else if (ng == 3) {
-            chunk_sum<3, false>(tab, rule, nq, xa, D, B1, B2, n, acc);
-        } else {
-            chunk_sum<2, false>(tab, rule, nq, xa, D, B1, B2, n, acc);
-        }
+        const int n_pass = (min(MIX_CH, n_steps - d0) + MIX_G - 1) / MIX_G;
+        if (ng == 4)
+            chunk_sum<4>(tab, n_pass, rule, nq, xa, D, B1, B2, n, acc);
+        else if (ng == 3)
+            chunk_sum<3>(tab, n_pass, rule, nq, xa, D, B1, B2, n, acc);
+        else
+            chunk_sum<2>(tab, n_pass, rule, nq, xa, D, B1, B2, n, acc);
 #pragma unroll
         for (int u = 0; u < MIX_CH; ++u) {
             const int d = d0 + u;
@@ -305,35 +334,34 @@ k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris
                 if (K) store_m(K + (size_t)d * EE + ij, scale * acc[u].y);
             }
         }
-        tab += (MIX_CH + 1) * mixed_iv_floats(ng);
+        carry = acc[MIX_CH];
+        tab += MIX_CH * mixed_iv_floats(ng);
     }
 }
 
 // ------------------------------------------------------- touching pairs ---
 constexpr int MSS_THREADS = 128;
 
-// One chunk of a touching pair's blocks for one point: acc[u] (V),
-// acc[CH + u] (K at (a,b)), acc[2 CH + u] (K at (b,a)) of block d0 + u.
+// One chunk of a touching pair's blocks for one point: intervals
+// k = d0 + u (u < CH); the falling side feeds block k (index u), the rising
+// side block k + 1 (index u + 1, u + 1 = CH being the carry into the next
+// chunk): acc[i] (V), acc[CH + 1 + i] (K at (a,b)), acc[2 (CH + 1) + i] (K at (b,a)).
 template <int NG, int CH>
 __device__ __forceinline__ void ss_chunk(const float *tab, int d0, int n_steps, float rr, float w,
-                                         float wa, float wb, float (&acc)[3 * CH]) {
+                                         float wa, float wb, float (&acc)[3 * (CH + 1)]) {
     const float2 rr2[1] = {make_float2(rr, rr)};
+    constexpr int S = CH + 1;
 #pragma unroll
-    for (int u = 0; u <= CH; ++u) {
-        const int k = d0 - 1 + u;
-        if (k < 2 || k > n_steps - 1) continue;
+    for (int u = 0; u < CH; ++u) {
+        if (d0 + u > n_steps - 1) break;
         float2 fall[1], rise[1];
         interval_sums<NG, 1, false>(tab + u * (4 + 4 * NG), rr2, fall, rise);
-        if (u >= 1) {
-            acc[u - 1] = fmaf(w, fall[0].x, acc[u - 1]);
-            acc[CH + u - 1] = fmaf(wa, fall[0].y, acc[CH + u - 1]);
-            acc[2 * CH + u - 1] = fmaf(wb, fall[0].y, acc[2 * CH + u - 1]);
-        }
-        if (u < CH && k + 1 < n_steps) {
-            acc[u] = fmaf(w, rise[0].x, acc[u]);
-            acc[CH + u] = fmaf(wa, rise[0].y, acc[CH + u]);
-            acc[2 * CH + u] = fmaf(wb, rise[0].y, acc[2 * CH + u]);
-        }
+        acc[u] = fmaf(w, fall[0].x, acc[u]);
+        acc[S + u] = fmaf(wa, fall[0].y, acc[S + u]);
+        acc[2 * S + u] = fmaf(wb, fall[0].y, acc[2 * S + u]);
+        acc[u + 1] = fmaf(w, rise[0].x, acc[u + 1]);
+        acc[S + u + 1] = fmaf(wa, rise[0].y, acc[S + u + 1]);
+        acc[2 * S + u + 1] = fmaf(wb, rise[0].y, acc[2 * S + u + 1]);
     }
 }
 
@@ -449,14 +477,15 @@ k_singular_mixed(const double *__restrict__ geo, const TouchPair *__restrict__ p
             }
         }
     }
-    const float v2 = fin[6], ka2 = fin[7], kb2 = fin[8];  // already scaled
+    float cv = fin[6], ca = fin[7], cb = fin[8];  // carry into block d0 (already scaled)
     __syncthreads();
 
+    constexpr int S = CH + 1;
     const float *ntab = nodes + MIX_K1;
     for (int d0 = 2; d0 < n_steps; d0 += CH) {
-        float acc[3 * CH];
+        float acc[3 * S];
 #pragma unroll
-        for (int i = 0; i < 3 * CH; ++i) acc[i] = 0.f;
+        for (int i = 0; i < 3 * S; ++i) acc[i] = 0.f;
         const int ng = mixed_chunk_ng(d0);
         for (int p = threadIdx.x; p < npt; p += MSS_THREADS) {
             float rr, rab, rba, w;
@@ -465,17 +494,17 @@ k_singular_mixed(const double *__restrict__ geo, const TouchPair *__restrict__ p
             else if (ng == 3) ss_chunk<3, CH>(ntab, d0, n_steps, rr, w, w * rab, w * rba, acc);
             else ss_chunk<2, CH>(ntab, d0, n_steps, rr, w, w * rab, w * rba, acc);
         }
-        ntab += (CH + 1) * mixed_iv_floats(ng);
-        reduce(acc, 3 * CH);
+        ntab += CH * mixed_iv_floats(ng);
+        reduce(acc, 3 * S);
         if (threadIdx.x == 0) {
             for (int u = 0; u < CH; ++u) {
                 const int d = d0 + u;
                 if (d >= n_steps) break;
-                float bv = fin[u], ba = fin[CH + u], bb = fin[2 * CH + u];
-                if (d == 2) {
-                    bv += v2;
-                    ba += ka2;
-                    bb += kb2;
+                float bv = fin[u], ba = fin[S + u], bb = fin[2 * S + u];
+                if (u == 0) {
+                    bv += cv;
+                    ba += ca;
+                    bb += cb;
                 }
                 const size_t off = (size_t)d * EE;
                 store_m(V + off + iab, bv);
@@ -486,6 +515,9 @@ k_singular_mixed(const double *__restrict__ geo, const TouchPair *__restrict__ p
                 }
             }
         }
+        cv = fin[CH];
+        ca = fin[S + CH];
+        cb = fin[2 * S + CH];
         __syncthreads();
     }
 }
@@ -532,9 +564,9 @@ void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<flo
     for (int d0 = 2; d0 < p.n_steps; d0 += MIX_CH) {
         const int ng = mixed_chunk_ng(d0);
         gauss_legendre01(ng, u.data(), wq.data());
-        for (int uu = 0; uu <= MIX_CH; ++uu, off += mixed_iv_floats(ng)) {
-            const int k = d0 - 1 + uu;
-            if (k < 2 || k > p.n_steps - 1) continue;  // zero weights
+        for (int uu = 0; uu < MIX_CH; ++uu, off += mixed_iv_floats(ng)) {
+            const int k = d0 + uu;
+            if (k > p.n_steps - 1) continue;  // zero weights
             float *o = nodes.data() + off;
             for (int q = 0; q < ng; ++q) {
                 double b, wf, wr, delta;
