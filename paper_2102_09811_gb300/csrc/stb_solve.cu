@@ -3,10 +3,11 @@
 // substitution in time:
 //     w^k = (V^0)^{-1} ( f^k - sum_{d=1}^{k} V^d w^{k-d} ),  k = 0..E_t-1.
 // V^0 is symmetric positive definite; it is factorised once, V^0 = L L^T, by
-// a right-looking blocked Cholesky (64 x 64 tiles), L is inverted blockwise,
-// and every time step is then three matrix-vector kernels: the history sum
-// (reads V^1..V^k once, all right-hand sides together), z = L^{-1} r and
-// w^k = L^{-T} z.
+// a right-looking blocked Cholesky (64 x 64 tiles), L is inverted blockwise
+// and (V^0)^{-1} = L^{-T} L^{-1} formed explicitly; every time step is then
+// two matrix-vector kernels: the history sum (reads the blocks V^d once, all
+// right-hand sides together) and w^k = (V^0)^{-1} r.  Steps are grouped in
+// panels of 8 whose history from earlier panels is one blocked product.
 //
 // FP64 precision: everything in FP64.
 // Mixed precision: the factorisation and the march run in FP32 and are wrapped
@@ -157,6 +158,35 @@ __global__ void __launch_bounds__(256) k_syrk_update(T *__restrict__ L, int E, i
         }
 }
 
+// (V^0)^{-1} = L^{-T} L^{-1} from U = L^{-T} (upper triangular):
+// M_IJ = sum_{c >= max(I,J)} U_Ic U_Jc^T, tile pairs I >= J, both halves written.
+template <class T>
+__global__ void __launch_bounds__(256) k_inverse_spd(const T *__restrict__ U, T *__restrict__ M,
+                                                     int E) {
+    __shared__ T Ps[NB][33], Qs[NB][33];
+    const int t = blockIdx.x;
+    int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+    while (ii * (ii + 1) / 2 > t) --ii;
+    const int jj = t - ii * (ii + 1) / 2;
+    const int i0 = ii * NB, j0 = jj * NB;
+    TileAcc<T> acc;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc.v[u][v] = (T)0;
+    tile_mma_abt<T>(acc, U, E, i0, i0, U, E, j0, i0, E, E - i0, Ps, Qs);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    for (int u = 0; u < 4; ++u)
+        for (int v = 0; v < 4; ++v) {
+            const int r = i0 + 4 * ty + u, c = j0 + 4 * tx + v;
+            if (r < E && c < E) {
+                M[(size_t)r * E + c] = acc.v[u][v];
+                M[(size_t)c * E + r] = acc.v[u][v];
+            }
+        }
+}
+
 // Inverse of every diagonal tile of L (lower triangular), in parallel.
 template <class T>
 __global__ void __launch_bounds__(64) k_trtri_diag(const T *__restrict__ L, T *__restrict__ Li,
@@ -185,29 +215,30 @@ __global__ void __launch_bounds__(64) k_trtri_diag(const T *__restrict__ L, T *_
     }
 }
 
-// Tile row i of L^{-1}: Li_ij = -Li_ii sum_{m=j}^{i-1} L_im Li_mj, j < i.
+// Batched tile product for the recursive inversion of L: task (i, j, mlo, mhi)
+// writes tile C_ij = alpha sum_{m=mlo}^{mhi} A_im B_mj (tiles of NB x NB).
 template <class T>
-__global__ void __launch_bounds__(256) k_trtri_row(const T *__restrict__ L, T *__restrict__ Li,
-                                                   int E, int i) {
+__global__ void __launch_bounds__(256)
+k_tile_gemm(const int4 *__restrict__ tasks, const T *__restrict__ A, const T *__restrict__ B,
+            T *__restrict__ C, int E, T alpha) {
     __shared__ T Ps[NB][33], Qs[NB][33];
-    __shared__ T Tt[NB][NB + 1];  // T^T, T = sum L_im Li_mj
-    const int j = blockIdx.x;
-    const int i0 = i * NB, j0 = j * NB;
+    const int4 tk = tasks[blockIdx.x];
+    const int i0 = tk.x * NB, j0 = tk.y * NB;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     TileAcc<T> acc;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc.v[u][v] = (T)0;
-    for (int m = j; m < i; ++m) {
+    for (int m = tk.z; m <= tk.w; ++m) {
         const int m0 = m * NB;
-        // acc[r][c] += sum_k L[i0+r][m0+k] * Li[m0+k][j0+c]  (Q[c][k] = Li[m0+k][j0+c])
         for (int k0 = 0; k0 < NB; k0 += 32) {
             for (int t = threadIdx.x; t < NB * 32; t += blockDim.x) {
-                int r = t / 32, kk = t % 32;
-                int gr = i0 + r, gk = m0 + k0 + kk, gc = j0 + r;
-                Ps[r][kk] = (gr < E && gk < E) ? L[(size_t)gr * E + gk] : (T)0;
-                Qs[r][kk] = (gk < E && gc < E) ? Li[(size_t)gk * E + gc] : (T)0;
+                const int r = t / 32, kk = t % 32, gr = i0 + r, gk = m0 + k0 + kk;
+                Ps[r][kk] = (gr < E && gk < E) ? A[(size_t)gr * E + gk] : (T)0;
+                // B rows read along their columns (coalesced), stored transposed
+                const int c = t % NB, kq = t / NB, gq = m0 + k0 + kq, gc = j0 + c;
+                Qs[c][kq] = (gq < E && gc < E) ? B[(size_t)gq * E + gc] : (T)0;
             }
             __syncthreads();
 #pragma unroll 4
@@ -227,41 +258,41 @@ __global__ void __launch_bounds__(256) k_trtri_row(const T *__restrict__ L, T *_
         }
     }
     for (int u = 0; u < 4; ++u)
-        for (int v = 0; v < 4; ++v) Tt[4 * tx + v][4 * ty + u] = acc.v[u][v];
-    __syncthreads();
-    TileAcc<T> out;
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) out.v[u][v] = (T)0;
-    for (int k0 = 0; k0 < NB; k0 += 32) {
-        for (int t = threadIdx.x; t < NB * 32; t += blockDim.x) {
-            int r = t / 32, kk = t % 32;
-            int gr = i0 + r, gk = i0 + k0 + kk;
-            Ps[r][kk] = (gr < E && gk < E) ? Li[(size_t)gr * E + gk] : (T)0;
-            Qs[r][kk] = Tt[r][k0 + kk];
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < 32; ++kk) {
-            T a[4], b[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a[u] = Ps[4 * ty + u][kk];
-                b[u] = Qs[4 * tx + u][kk];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) out.v[u][v] = fma(a[u], b[v], out.v[u][v]);
-        }
-        __syncthreads();
-    }
-    for (int u = 0; u < 4; ++u)
         for (int v = 0; v < 4; ++v) {
-            int r = i0 + 4 * ty + u, c = j0 + 4 * tx + v;
-            if (r < E && c < E) Li[(size_t)r * E + c] = -out.v[u][v];
+            const int r = i0 + 4 * ty + u, c = j0 + 4 * tx + v;
+            if (r < E && c < E) C[(size_t)r * E + c] = alpha * acc.v[u][v];
         }
+}
+
+// Task lists of the recursive inversion of the lower-triangular tile matrix
+// L (nb x nb tiles): a node [a, b) with children [a, c), [c, b) whose
+// inverses are known gets  Li_21 = -Li_22 (L_21 Li_11),  as two batched
+// products per tree level (deepest level first):
+//   phase 1: W_ij = sum_{m=j}^{c-1} L_im Li_mj      (i in [c,b), j in [a,c))
+//   phase 2: Li_ij = -sum_{m=c}^{i} Li_im W_mj
+struct InvLevel {
+    std::vector<int4> p1, p2;
+};
+
+static void inv_tasks(int a, int b, int depth, std::vector<InvLevel> &lv) {
+    if (b - a < 2) return;
+    const int c = a + (b - a) / 2;
+    inv_tasks(a, c, depth + 1, lv);
+    inv_tasks(c, b, depth + 1, lv);
+    if ((int)lv.size() <= depth) lv.resize(depth + 1);
+    for (int i = c; i < b; ++i)
+        for (int j = a; j < c; ++j) {
+            lv[depth].p1.push_back(make_int4(i, j, j, c - 1));
+            lv[depth].p2.push_back(make_int4(i, j, c, i));
+        }
+}
+
+static size_t inv_task_count(int nb) {
+    std::vector<InvLevel> lv;
+    inv_tasks(0, nb, 0, lv);
+    size_t n = 0;
+    for (auto &l : lv) n += l.p1.size() + l.p2.size();
+    return n;
 }
 
 template <class T>
@@ -429,15 +460,17 @@ __global__ void k_far_reduce(const T *__restrict__ part, int nz, int E, int n_st
     hv[((size_t)r * PB + c) * E + l] = f[(size_t)r * n_steps * E + (size_t)(kp + c) * E + l] - s;
 }
 
-// out_r[l] = sum_{j in tri(l)} M[l][j] in_r[j]; lower: j <= l, else j >= l.
+// out_r[l] = sum_j M[l][j] in_r[j] over j >= l (part TRI_UPPER), j <= l
+// (TRI_LOWER) or all j (FULL).
+enum { TRI_UPPER = 0, TRI_LOWER = 1, FULL = 2 };
 template <class T>
 __global__ void __launch_bounds__(256)
-k_trmv(const T *__restrict__ M, int E, int nrhs, int lower, const T *__restrict__ in,
+k_trmv(const T *__restrict__ M, int E, int nrhs, int part, const T *__restrict__ in,
        size_t in_stride, T *__restrict__ out, size_t out_stride) {
     const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (l >= E) return;
     const T *row = M + (size_t)l * E;
-    const int jlo = lower ? 0 : l, jhi = lower ? l + 1 : E;
+    const int jlo = part == TRI_UPPER ? l : 0, jhi = part == TRI_LOWER ? l + 1 : E;
     for (int r0 = 0; r0 < nrhs; r0 += MAXR) {
         T acc[MAXR];
 #pragma unroll
@@ -518,9 +551,10 @@ struct SolveHeader {
 };
 
 struct SolveLayout {
-    void *L, *Li, *LiT, *rv, *zv;  // T
+    void *L, *Li, *LiT, *rv;  // T (L holds (V^0)^{-1} after the factorisation)
     double *hv;                   // panel right-hand sides [nrhs][PB][E]
     void *part;                   // far-history slices [FAR_NZ][nrhs][PB][E] (T)
+    int4 *tasks;                  // task lists of the recursive inversion of L
     float *delta;                // mixed: correction [nrhs][n_steps][E]
     double *r;                    // mixed: residual / right-hand side
     void *df;                     // mixed: scratch of the double-float product
@@ -536,9 +570,9 @@ static SolveLayout solve_layout(int64_t E, int n_steps, int nrhs, bool mixed, vo
     S.Li = c.take<char>((size_t)E * E * tb);
     S.LiT = c.take<char>((size_t)E * E * tb);
     S.rv = c.take<char>((size_t)nrhs * E * tb);
-    S.zv = c.take<char>((size_t)nrhs * E * tb);
     S.hv = c.take<double>((size_t)nrhs * PB * E);
     S.part = c.take<char>((size_t)FAR_NZ * nrhs * PB * E * tb);
+    S.tasks = c.take<int4>(inv_task_count((int)((E + NB - 1) / NB)));
     if (mixed) {
         const size_t n = (size_t)nrhs * n_steps * E;
         S.delta = c.take<float>(n);
@@ -550,7 +584,8 @@ static SolveLayout solve_layout(int64_t E, int n_steps, int nrhs, bool mixed, vo
     return S;
 }
 
-// V^0 = L L^T, then L^{-1} and its transpose, all in T.
+// V^0 = L L^T, then L^{-1}, its transpose and (V^0)^{-1} = L^{-T} L^{-1}
+// (written over L), all in T.
 template <class AT, class T>
 static stb_status factorize(const AT *V, int E, const SolveLayout &S, int32_t *status,
                             cudaStream_t s) {
@@ -578,14 +613,42 @@ static stb_status factorize(const AT *V, int E, const SolveLayout &S, int32_t *s
     count_launch(s);
     k_trtri_diag<T><<<nb, 64, 0, s>>>(L, Li, E);
     if ((st = check_launch("k_trtri_diag"))) return st;
-    for (int i = 1; i < nb; ++i) {
-        count_launch(s);
-        k_trtri_row<T><<<i, 256, 0, s>>>(L, Li, E, i);
-        if ((st = check_launch("k_trtri_row"))) return st;
+    {  // off-diagonal tiles of L^{-1}: recursive halving, deepest level first
+        std::vector<InvLevel> lv;
+        inv_tasks(0, nb, 0, lv);
+        std::vector<int4> all;
+        for (auto &l : lv) {
+            all.insert(all.end(), l.p1.begin(), l.p1.end());
+            all.insert(all.end(), l.p2.begin(), l.p2.end());
+        }
+        if (!all.empty()) {
+            STB_CUDA(cudaMemcpyAsync(S.tasks, all.data(), all.size() * sizeof(int4),
+                                     cudaMemcpyHostToDevice, s));
+            size_t off = 0;
+            std::vector<size_t> offs(lv.size());
+            for (size_t d = 0; d < lv.size(); ++d) {
+                offs[d] = off;
+                off += lv[d].p1.size() + lv[d].p2.size();
+            }
+            T *W = LiT;  // scratch until the transpose below
+            for (int d = (int)lv.size() - 1; d >= 0; --d) {
+                const int4 *t1 = S.tasks + offs[d], *t2 = t1 + lv[d].p1.size();
+                count_launch(s);
+                k_tile_gemm<T><<<(unsigned)lv[d].p1.size(), 256, 0, s>>>(t1, L, Li, W, E, (T)1);
+                if ((st = check_launch("k_tile_gemm(L21 Li11)"))) return st;
+                count_launch(s);
+                k_tile_gemm<T><<<(unsigned)lv[d].p2.size(), 256, 0, s>>>(t2, Li, W, Li, E, (T)-1);
+                if ((st = check_launch("k_tile_gemm(Li22 W)"))) return st;
+            }
+        }
     }
     count_launch(s);
     k_transpose<T><<<dim3((E + 31) / 32, (E + 31) / 32), dim3(32, 8), 0, s>>>(Li, LiT, E);
-    return check_launch("k_transpose");
+    if ((st = check_launch("k_transpose"))) return st;
+    // (V^0)^{-1} = L^{-T} L^{-1} into the storage of L (no longer needed)
+    count_launch(s);
+    k_inverse_spd<T><<<nb * (nb + 1) / 2, 256, 0, s>>>(LiT, L, E);
+    return check_launch("k_inverse_spd");
 }
 
 // March in time: x^k = L^{-T} L^{-1} (rhs^k - sum_{d>=1} V^d x^{k-d}) into x
@@ -597,7 +660,7 @@ static stb_status march(const AT *V, int E, int n_steps, int nrhs, const double 
     stb_status st;
     const unsigned rows_blocks = (unsigned)((E * 32 + 255) / 256);
     const size_t SE = (size_t)n_steps * E;
-    T *rv = (T *)S.rv, *zv = (T *)S.zv, *part = (T *)S.part;
+    T *rv = (T *)S.rv, *part = (T *)S.part;
     const bool vec = E % 4 == 0 && reinterpret_cast<uintptr_t>(V) % 16 == 0 &&
                      reinterpret_cast<uintptr_t>(x) % 16 == 0;
     const int rows_cta = 8 * (nrhs == 1 ? far_rows_per_warp<T, 1>() : far_rows_per_warp<T, 2>());
@@ -634,12 +697,9 @@ static stb_status march(const AT *V, int E, int n_steps, int nrhs, const double 
                 if ((st = check_launch("k_history"))) return st;
             }
             count_launch(s);
-            k_trmv<T><<<rows_blocks, 256, 0, s>>>((const T *)S.Li, E, nrhs, 1, rv, E, zv, E);
-            if ((st = check_launch("k_trmv(L^-1)"))) return st;
-            count_launch(s);
-            k_trmv<T><<<rows_blocks, 256, 0, s>>>((const T *)S.LiT, E, nrhs, 0, zv, E,
+            k_trmv<T><<<rows_blocks, 256, 0, s>>>((const T *)S.L, E, nrhs, FULL, rv, E,
                                                   x + (size_t)k * E, SE);
-            if ((st = check_launch("k_trmv(L^-T)"))) return st;
+            if ((st = check_launch("k_matvec((V^0)^-1)"))) return st;
         }
     }
     return STB_OK;

@@ -108,6 +108,14 @@ stb_status toeplitz_fp64(const void *A, int32_t storage, int64_t E, int32_t n_st
 }
 
 // ------------------------------------------------- double-float product ---
+// Blocks d per item: half of TD, so that a 64-step product over 3072 rows
+// runs about 2.5 waves of resident CTAs instead of 1.3.
+constexpr int DF_TD = 4;
+
+static size_t df_partial_bytes(int64_t E, int32_t n_steps, int32_t nrhs) {
+    const size_t n_dr = (n_steps + DF_TD - 1) / DF_TD;
+    return align256(n_dr * (size_t)nrhs * n_steps * E * sizeof(double));
+}
 __global__ void k_split(const double *__restrict__ x, size_t n, float2 *__restrict__ xs) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -116,65 +124,129 @@ __global__ void k_split(const double *__restrict__ x, size_t n, float2 *__restri
     xs[i] = make_float2(hi, (float)(v - (double)hi));
 }
 
-// a (w_hi + w_lo) = p + e (p the FP32 product, e its error by FMA) plus the
-// small w_lo term, accumulated into (hi, lo) by an error-free two-sum.
-__device__ __forceinline__ void df_acc(float a, float2 x, float &hi, float &lo) {
-    const float p = a * x.x;
-    const float e = fmaf(a, x.x, -p);
-    const float t = fmaf(a, x.y, e);
-    const float s = hi + p;
-    const float bb = s - hi;
-    const float err = (hi - (s - bb)) + (p - bb);
+// Two rows at once in packed FP32x2 arithmetic: a (w_hi + w_lo) = p + e
+// (p the FP32 product, e its error by FMA) plus the small w_lo term,
+// accumulated into (hi, lo) by an error-free two-sum.  Differences are
+// written as u - v = fma(v, -1, u) (exact negation, one rounding) and the
+// product is formed negated, pn = -p, so that no separate negation is needed.
+__device__ __forceinline__ float2 sub2(float2 u, float2 v) {
+    return __ffma2_rn(v, make_float2(-1.f, -1.f), u);
+}
+__device__ __forceinline__ void df_acc2(float2 a, float2 xh, float2 nxh, float2 xl, float2 &hi,
+                                        float2 &lo) {
+    const float2 pn = __fmul2_rn(a, nxh);       // -p
+    const float2 e = __ffma2_rn(a, xh, pn);      // a xh - p, exact
+    const float2 t = __ffma2_rn(a, xl, e);
+    const float2 s = sub2(hi, pn);               // hi + p
+    const float2 bb = sub2(s, hi);
+    const float2 c2 = sub2(hi, sub2(s, bb));     // hi - (s - bb)
+    const float2 c3n = __fadd2_rn(pn, bb);       // -(p - bb)
+    const float2 err = sub2(c2, c3n);
     hi = s;
-    lo += err + t;
+    lo = __fadd2_rn(lo, __fadd2_rn(err, t));
 }
 
+// Item (64 rows l, 16 columns k, 8 blocks d) of the double-float product.
+// A thread owns one column and 8 rows (4 packed pairs); the A tile is stored
+// transposed in shared memory so that a pair of rows is one 8-byte word, and
+// x as (hi, hi, lo, lo) so that both operands of the packed ops load as is.
+// The (d, j) tiles are visited in one flat sequence and the next tile is
+// loaded into registers while the current one is being multiplied.  VEC:
+// E % 4 == 0 and A 16-byte aligned (rows loaded as float4).
+template <bool VEC>
 __global__ void __launch_bounds__(MV_THREADS)
 k_toeplitz_df_partial(const float *__restrict__ A, int E, int n_steps, int nrhs,
                       const float2 *__restrict__ xs, double *__restrict__ part) {
-    __shared__ float As[TM][TJ + 1];
-    __shared__ float2 Xs[TK][TJ + 1];
+    __shared__ __align__(16) float As[TJ][TM + 4];
+    __shared__ __align__(16) float4 Xs[TJ][TK];
     const int n_kt = (n_steps + TK - 1) / TK;
     const int lt = blockIdx.x, kt = blockIdx.y % n_kt, r = blockIdx.y / n_kt, dr = blockIdx.z;
-    const int l0 = lt * TM, k0 = kt * TK, d0 = dr * TD;
+    const int l0 = lt * TM, k0 = kt * TK, d0 = dr * DF_TD;
     if (d0 > k0 + TK - 1 || d0 >= n_steps) return;
-    const int d1 = min(min(d0 + TD, n_steps), k0 + TK);
+    const int d1 = min(min(d0 + DF_TD, n_steps), k0 + TK);
     const int tx = threadIdx.x % TK, ty = threadIdx.x / TK;
-    constexpr int RPT = TM / (MV_THREADS / TK);  // rows per thread
-    float hi[RPT], lo[RPT];
+    constexpr int RPT = TM / (MV_THREADS / TK);  // rows per thread (8)
+    constexpr int AV = TM * TJ / 4 / MV_THREADS;  // float4 of the A tile per thread (4)
+    constexpr int XV = TK * TJ / MV_THREADS;      // x values of the tile per thread (4)
+    float2 hi[RPT / 2], lo[RPT / 2];
 #pragma unroll
-    for (int i = 0; i < RPT; ++i) hi[i] = lo[i] = 0.f;
+    for (int i = 0; i < RPT / 2; ++i) hi[i] = lo[i] = make_float2(0.f, 0.f);
     const size_t EE = (size_t)E * E;
     const float2 *xr = xs + (size_t)r * n_steps * E;
-    for (int d = d0; d < d1; ++d) {
+    const int n_j = (E + TJ - 1) / TJ, n_it = (d1 - d0) * n_j;
+
+    float4 ra[AV];
+    float2 rx[XV];
+    auto load_tile = [&](int it) {
+        const int d = d0 + it / n_j, j0 = (it % n_j) * TJ;
         const float *Ad = A + (size_t)d * EE;
-        for (int j0 = 0; j0 < E; j0 += TJ) {
-            for (int t = threadIdx.x; t < TM * TJ; t += MV_THREADS) {
-                int i = t / TJ, jj = t % TJ, l = l0 + i, j = j0 + jj;
-                As[i][jj] = (l < E && j < E) ? Ad[(size_t)l * E + j] : 0.f;
-            }
-            for (int t = threadIdx.x; t < TK * TJ; t += MV_THREADS) {
-                int c = t / TJ, jj = t % TJ, k = k0 + c, j = j0 + jj;
-                Xs[c][jj] = (k < n_steps && k - d >= 0 && j < E) ? xr[(size_t)(k - d) * E + j]
-                                                                   : make_float2(0.f, 0.f);
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int jj = 0; jj < TJ; ++jj) {
-                const float2 xv = Xs[tx][jj];
 #pragma unroll
-                for (int i = 0; i < RPT; ++i) df_acc(As[ty * RPT + i][jj], xv, hi[i], lo[i]);
+        for (int v = 0; v < AV; ++v) {
+            const int t = threadIdx.x + v * MV_THREADS;
+            const int i = t / (TJ / 4), j = j0 + 4 * (t % (TJ / 4)), l = l0 + i;
+            if (VEC) {
+                ra[v] = (l < E && j < E) ? __ldg(reinterpret_cast<const float4 *>(Ad + (size_t)l * E + j))
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                const float *row = Ad + (size_t)l * E;
+                const bool ok = l < E;
+                ra[v] = make_float4(ok && j < E ? row[j] : 0.f, ok && j + 1 < E ? row[j + 1] : 0.f,
+                                    ok && j + 2 < E ? row[j + 2] : 0.f,
+                                    ok && j + 3 < E ? row[j + 3] : 0.f);
             }
-            __syncthreads();
         }
+#pragma unroll
+        for (int v = 0; v < XV; ++v) {
+            const int t = threadIdx.x + v * MV_THREADS;
+            const int jj = t / TK, c = t % TK, k = k0 + c, j = j0 + jj;
+            rx[v] = (k < n_steps && k - d >= 0 && j < E) ? xr[(size_t)(k - d) * E + j]
+                                                         : make_float2(0.f, 0.f);
+        }
+    };
+    auto store_tile = [&]() {
+#pragma unroll
+        for (int v = 0; v < AV; ++v) {
+            const int t = threadIdx.x + v * MV_THREADS;
+            const int i = t / (TJ / 4), jq = 4 * (t % (TJ / 4));
+            As[jq][i] = ra[v].x;
+            As[jq + 1][i] = ra[v].y;
+            As[jq + 2][i] = ra[v].z;
+            As[jq + 3][i] = ra[v].w;
+        }
+#pragma unroll
+        for (int v = 0; v < XV; ++v) {
+            const int t = threadIdx.x + v * MV_THREADS;
+            Xs[t / TK][t % TK] = make_float4(rx[v].x, rx[v].x, rx[v].y, rx[v].y);
+        }
+    };
+
+    load_tile(0);
+    for (int it = 0; it < n_it; ++it) {
+        store_tile();
+        __syncthreads();
+        if (it + 1 < n_it) load_tile(it + 1);
+#pragma unroll 4
+        for (int jj = 0; jj < TJ; ++jj) {
+            const float4 xv = Xs[jj][tx];
+            const float2 xh = make_float2(xv.x, xv.y), xl = make_float2(xv.z, xv.w);
+            const float2 nxh = make_float2(-xv.x, -xv.y);
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[jj][ty * RPT]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[jj][ty * RPT + 4]);
+            df_acc2(make_float2(a0.x, a0.y), xh, nxh, xl, hi[0], lo[0]);
+            df_acc2(make_float2(a0.z, a0.w), xh, nxh, xl, hi[1], lo[1]);
+            df_acc2(make_float2(a1.x, a1.y), xh, nxh, xl, hi[2], lo[2]);
+            df_acc2(make_float2(a1.z, a1.w), xh, nxh, xl, hi[3], lo[3]);
+        }
+        __syncthreads();
     }
     const int k = k0 + tx;
     if (k >= n_steps) return;
     double *pr = part + (((size_t)dr * nrhs + r) * n_steps + k) * E;
 #pragma unroll
-    for (int i = 0; i < RPT; ++i) {
-        int l = l0 + ty * RPT + i;
-        if (l < E) pr[l] = (double)hi[i] + (double)lo[i];
+    for (int i = 0; i < RPT / 2; ++i) {
+        const int l = l0 + ty * RPT + 2 * i;
+        if (l < E) pr[l] = (double)hi[i].x + (double)lo[i].x;
+        if (l + 1 < E) pr[l + 1] = (double)hi[i].y + (double)lo[i].y;
     }
 }
 
@@ -186,7 +258,7 @@ __global__ void k_toeplitz_df_reduce(const double *__restrict__ part, int E, int
     if (idx >= total) return;
     int k = (int)((idx / E) % n_steps);
     double s = 0.0;
-    for (int dr = 0; dr * TD <= k; ++dr) s += part[dr * total + idx];
+    for (int dr = 0; dr * DF_TD <= k; ++dr) s += part[dr * total + idx];
     if (mode == DF_RESIDUAL)
         y[idx] = f[idx] - s;
     else
@@ -194,8 +266,7 @@ __global__ void k_toeplitz_df_reduce(const double *__restrict__ part, int E, int
 }
 
 size_t toeplitz_df_bytes(int64_t E, int32_t n_steps, int32_t nrhs) {
-    return toeplitz_partial_bytes(E, n_steps, nrhs) +
-           align256((size_t)nrhs * n_steps * E * sizeof(float2));
+    return df_partial_bytes(E, n_steps, nrhs) + align256((size_t)nrhs * n_steps * E * sizeof(float2));
 }
 
 stb_status toeplitz_df(const float *A, int64_t E, int32_t n_steps, int32_t nrhs, const double *x,
@@ -203,16 +274,19 @@ stb_status toeplitz_df(const float *A, int64_t E, int32_t n_steps, int32_t nrhs,
                        cudaStream_t s) {
     double *part = static_cast<double *>(scratch);
     float2 *xs = reinterpret_cast<float2 *>(static_cast<char *>(scratch) +
-                                            toeplitz_partial_bytes(E, n_steps, nrhs));
+                                            df_partial_bytes(E, n_steps, nrhs));
     const size_t total = (size_t)nrhs * n_steps * E;
     count_launch(s);
     k_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(x, total, xs);
     stb_status st = check_launch("k_split");
     if (st) return st;
-    int n_kt = (n_steps + TK - 1) / TK, n_dr = (n_steps + TD - 1) / TD;
+    int n_kt = (n_steps + TK - 1) / TK, n_dr = (n_steps + DF_TD - 1) / DF_TD;
     dim3 grid((unsigned)((E + TM - 1) / TM), (unsigned)(n_kt * nrhs), (unsigned)n_dr);
     count_launch(s);
-    k_toeplitz_df_partial<<<grid, MV_THREADS, 0, s>>>(A, (int)E, n_steps, nrhs, xs, part);
+    if (E % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0)
+        k_toeplitz_df_partial<true><<<grid, MV_THREADS, 0, s>>>(A, (int)E, n_steps, nrhs, xs, part);
+    else
+        k_toeplitz_df_partial<false><<<grid, MV_THREADS, 0, s>>>(A, (int)E, n_steps, nrhs, xs, part);
     if ((st = check_launch("k_toeplitz_df_partial"))) return st;
     count_launch(s);
     k_toeplitz_df_reduce<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, (int)E, n_steps, nrhs,
