@@ -48,6 +48,25 @@ FP64_FLOPS_PER_EVAL = 137.34
 MUFU_PEAK_TEX2 = 152 * 32 * 2.07e9 / 1e12
 
 
+# ncu, k_regular_mixed on the 16-step cube (3072 triangles, alpha 0.5): DRAM
+# read 17.40 MB + write 1144.84 MB for 2 x 16 x 3072^2 block entries.
+REGULAR_MIXED_DRAM_BYTES_PER_ENTRY = (17.396736e6 + 1144.844e6) / (2 * 16 * 3072.0 ** 2)
+
+
+def mixed_nodes_per_point(n_steps):
+    """exp2 evaluations per quadrature point of the mixed separated-pair
+    kernel: 6 nodes on interval k = 1 (when n_steps > 2), then chunks of 16
+    blocks d0.. whose intervals k = d0..d0+15 (k <= n_steps - 1) take 4, 3 or
+    2 nodes (d0 < 16, d0 < 96, otherwise)."""
+    if n_steps <= 2:
+        return 0
+    nodes = 6
+    for d0 in range(2, n_steps, 16):
+        ng = 4 if d0 < 16 else (3 if d0 < 96 else 2)
+        nodes += ng * (min(d0 + 16, n_steps) - d0)
+    return nodes
+
+
 def _measured_hbm_gbs():
     try:
         with open(MEASURED_PEAKS) as fh:
@@ -57,6 +76,8 @@ def _measured_hbm_gbs():
 
 
 HBM_PEAK_GBS = _measured_hbm_gbs()
+# FP32 pipe: 128 lanes per SM per clock (one FP32 operation each)
+FP32_OP_PEAK = 152 * 128 * 2.07e9
 
 
 def parse():
@@ -193,16 +214,20 @@ def _roofline(name, trace_entry, ms_step, n_reg_pairs, q, n_steps):
             ach = FP64_FLOPS_PER_EVAL * evals / (launch_ms / 1e3) / 1e12
             roof.update({"achieved": ach, "frac": ach / FP64_PEAK_TFLOPS})
     elif name == "k_regular_mixed":
-        # exp2 evaluations: 6 on interval k = 1 and MIX_NG = 4 on every interval
-        # k = 2..E_t-1, each interval evaluated by the two chunks that share it
-        chunks = max(0, (n_steps - 2 + 15) // 16)
-        nodes = 6 + 4 * max(0, n_steps - 2) + 4 * max(0, chunks - 1)
-        ex2 = float(n_reg_pairs) * pts * nodes
+        ex2 = float(n_reg_pairs) * pts * mixed_nodes_per_point(n_steps)
         roof.update({"bound": "alu", "unit": "Tex2/s", "peak": MUFU_PEAK_TEX2,
                      "peak_source": "MUFU pipe: 152 SM x 32 ex2/clk x 2.07 GHz (measured 9.995 Tex2/s)",
                      "units_per_launch": ex2, "unit_name": "MUFU.EX2 time-node evaluations"})
         ach = ex2 / (launch_ms / 1e3) / 1e12
-        roof.update({"achieved": ach, "frac": ach / MUFU_PEAK_TEX2})
+        # DRAM bytes of one launch: ncu capture of this kernel on the 16-step
+        # cube (one launch, 2 x 16 x 3072^2 entries), scaled by the entries
+        # written (the traffic is the block stores)
+        entries = 2.0 * n_steps * float(n_reg_pairs)
+        roof.update({"achieved": ach, "frac": ach / MUFU_PEAK_TEX2,
+                     "traffic": REGULAR_MIXED_DRAM_BYTES_PER_ENTRY * entries,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                       "cube3072_e16 launch scaled by entries written",
+                     "algorithmic_bytes": 4.0 * entries})
     else:
         roof.update({"bound": None, "achieved": None, "peak": None, "frac": None})
     return roof
@@ -294,8 +319,16 @@ def run_gpu(args):
         b_.record(stream)
         torch.cuda.synchronize()
         mv_ms = a_.elapsed_time(b_) / reps
-        matvec[label] = {"ms": mv_ms, "tflops": flops / (mv_ms / 1e3) / 1e12,
-                         "block_gbs": a_bytes / (mv_ms / 1e3) / 1e9, "rel_err_vs_fp64": rel}
+        macs = flops / 2.0
+        entry = {"ms": mv_ms, "tflops": flops / (mv_ms / 1e3) / 1e12,
+                 "block_gbs": a_bytes / (mv_ms / 1e3) / 1e9, "rel_err_vs_fp64": rel}
+        if label == "fp64":  # FP64 FMA pipe, one DFMA per multiply-add
+            entry["frac_of_fp64_fma_peak"] = macs / (mv_ms / 1e3) / (FP64_PEAK_TFLOPS * 1e12 / 2)
+        elif label == "df":  # FP32 pipe, 11 FP32 operations per multiply-add
+            entry["frac_of_fp32_op_peak"] = 11.0 * macs / (mv_ms / 1e3) / FP32_OP_PEAK
+        else:  # HBM: every block read once
+            entry["frac_of_hbm_peak"] = a_bytes / (mv_ms / 1e3) / 1e9 / HBM_PEAK_GBS
+        matvec[label] = entry
         del ws
     best = "tf32" if "tf32" in matvec else "fp64"
     mv_tflops, mv_ms = matvec[best]["tflops"], matvec[best]["ms"]
