@@ -64,11 +64,27 @@ typedef int32_t stb_status;
 
 /* Arithmetic of the assembly. */
 #define STB_PREC_FP64 0  /* every quadrature point and time level in FP64 (the paper's) */
-#define STB_PREC_MIXED 1 /* reserved: mixed-precision assembly                            */
+#define STB_PREC_MIXED 1 /* FP32 quadrature points in cancellation-free forms (block error
+                            <= 2e-6 stated), FP32 solve inside double-float refinement   */
 
 /* Element type of V/K storage. */
 #define STB_STORE_F64 0
 #define STB_STORE_F32 1
+
+/* Flags (stb_params.flags).
+ * STB_FLAG_NO_SYNC: the call only enqueues device work.  No host
+ *   synchronisation and no copy from pageable host memory (host arrays such
+ *   as the sources must then be page-locked), so a sequence of such calls
+ *   can be captured into a CUDA graph and replayed.  The mixed solve then
+ *   runs a fixed number of refinement steps, STB_FLAG_REFINE(n) (n = 1..15,
+ *   default 1), e.g. the count a synchronous solve of the same problem
+ *   reported, and writes its convergence into the workspace status word
+ *   (STB_ERR_NOT_CONVERGED if ||f - V_h w|| > 1e-10 ||f||), read afterwards by
+ *   stb_workspace_status or stb_solve_report.  stb_assemble uploads its
+ *   tables from pageable host memory and does not take the flag; graphs
+ *   capture stb_batch_launch after stb_batch_prepare instead. */
+#define STB_FLAG_NO_SYNC 1
+#define STB_FLAG_REFINE(n) (((n) & 15) << 8)
 
 typedef struct stb_params {
     double alpha;          /* heat capacity constant alpha > 0 (eq. heat_eq)           */
@@ -78,7 +94,7 @@ typedef struct stb_params {
     int32_t quad_singular; /* m: m^4 Gauss points per sub-domain (eq. ss), 1..12         */
     int32_t precision;     /* STB_PREC_*                                                */
     int32_t storage;       /* STB_STORE_*                                               */
-    int32_t reserved;      /* must be 0                                                 */
+    int32_t flags;         /* STB_FLAG_* bits, 0 = none                                  */
 } stb_params;
 
 /* Default parameters (q = 3, m = 4, FP64, F64 storage) for given alpha, T, E_t. */
@@ -119,6 +135,47 @@ stb_status stb_assemble_workspace_size(const stb_mesh *mesh, const stb_params *p
                                        size_t *bytes);
 stb_status stb_assemble(const stb_mesh *mesh, const stb_params *params, void *V, void *K,
                         void *workspace, size_t workspace_bytes, stb_stream stream);
+
+/* ---- many problems in one launch (no counterpart in the paper) -------------------
+ * Mixed-precision assembly (eq. V_mat / eq. K_mat blocks, as stb_assemble with
+ * STB_PREC_MIXED and STB_STORE_F32) of n independent problems, each with its
+ * own mesh, parameters (alpha, T, n_steps, quadrature orders) and output
+ * blocks.  The separated pairs of all problems run in one persistent launch
+ * whose CTAs claim (problem, row, block of `tile` columns) work items from a
+ * device counter, so meshes of uneven size and step count share the SMs; the
+ * touching pairs of all problems run in one more launch.  Per problem there
+ * are in addition three small set-up launches (geometry, classification).
+ * tile: columns per work item, 64, 128 or 256; 0 = the value stb_batch_tune
+ * chose on this device for a batch of the same shape (128 if none).
+ * The workspace is shared by all items (stb_batch_workspace_size). */
+typedef struct {
+    const stb_mesh *mesh;
+    stb_params params; /* precision STB_PREC_MIXED, storage STB_STORE_F32 */
+    float *V;          /* device [params.n_steps][E][E] */
+    float *K;          /* device, same shape; NULL: V only */
+} stb_batch_item;
+stb_status stb_batch_workspace_size(const stb_batch_item *items, int32_t n, size_t *bytes);
+/* = stb_batch_prepare + stb_batch_launch. */
+stb_status stb_batch_assemble(const stb_batch_item *items, int32_t n, int32_t tile,
+                              void *workspace, size_t workspace_bytes, stb_stream stream);
+/* Set-up: uploads every problem's tables and the work-item descriptors for
+ * this tile from host memory, then computes geometry and pair classes.  Not
+ * capturable into a CUDA graph; call once for a workspace. */
+stb_status stb_batch_prepare(const stb_batch_item *items, int32_t n, int32_t tile,
+                             void *workspace, size_t workspace_bytes, stb_stream stream);
+/* The batched launches only (same items, tile and workspace as the preceding
+ * stb_batch_prepare): a device memset and two kernels, no host
+ * synchronisation and no host copy, so the call can be captured into a CUDA
+ * graph and replayed. */
+stb_status stb_batch_launch(const stb_batch_item *items, int32_t n, int32_t tile,
+                            void *workspace, size_t workspace_bytes, stb_stream stream);
+/* Tile autotuner: times the separated-pair launch of this batch on a sample
+ * (every 16th work item) for tile = 64, 128 and 256 with CUDA events, keeps
+ * the fastest for batches of the same shape on this device (used by tile = 0)
+ * and returns it in *tile.  It writes into the items' blocks (assemble
+ * afterwards) and synchronises `stream`. */
+stb_status stb_batch_tune(const stb_batch_item *items, int32_t n, void *workspace,
+                          size_t workspace_bytes, stb_stream stream, int32_t *tile);
 
 /* ---- Dirichlet data (Sec. 3.4, Sec. 6.1) --------------------------------------
  * sources: HOST array [nrhs][n_src][5] of (y1, y2, y3, t0, weight); right-hand

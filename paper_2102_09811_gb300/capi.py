@@ -17,6 +17,13 @@ STB_OK = 0
 STB_PREC_FP64, STB_PREC_MIXED = 0, 1
 STB_STORE_F64, STB_STORE_F32 = 0, 1
 STB_ARITH_FP64, STB_ARITH_DF, STB_ARITH_TF32 = 0, 1, 2
+STB_FLAG_NO_SYNC = 1
+
+
+def STB_FLAG_REFINE(n):
+    return (n & 15) << 8
+
+
 
 _lib = None
 
@@ -25,7 +32,12 @@ class stb_params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("T", ctypes.c_double), ("n_steps", ctypes.c_int32),
                 ("quad_regular", ctypes.c_int32), ("quad_singular", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("storage", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
+
+
+class stb_batch_item(ctypes.Structure):
+    _fields_ = [("mesh", ctypes.c_void_p), ("params", stb_params), ("V", ctypes.c_void_p),
+                ("K", ctypes.c_void_p)]
 
 
 class StbError(RuntimeError):
@@ -57,6 +69,11 @@ _SIGS = {
     "stb_toeplitz_matvec_static": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _D, _P, _P]),
     "stb_toeplitz_ex_workspace_size": (_I32, [_I64, _I32, _I32, _I32, _PSZ]),
     "stb_toeplitz_matvec_ex": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _D, _P, _I32, _P, _SZ, _P]),
+    "stb_batch_workspace_size": (_I32, [_P, _I32, _PSZ]),
+    "stb_batch_assemble": (_I32, [_P, _I32, _I32, _P, _SZ, _P]),
+    "stb_batch_prepare": (_I32, [_P, _I32, _I32, _P, _SZ, _P]),
+    "stb_batch_launch": (_I32, [_P, _I32, _I32, _P, _SZ, _P]),
+    "stb_batch_tune": (_I32, [_P, _I32, _P, _SZ, _P, ctypes.POINTER(_I32)]),
     "stb_rhs_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
     "stb_dirichlet_rhs": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
     "stb_solve_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
@@ -119,6 +136,13 @@ def _stream(stream):
 
 
 def _host_f64(a):
+    """Host array and its pointer: a numpy array (copied to float64 if
+    needed), or a CPU torch tensor of float64 (e.g. page-locked, for calls
+    with STB_FLAG_NO_SYNC), passed as is."""
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or a.dtype.itemsize != 8 or not a.is_contiguous() or not a.is_floating_point():
+            raise ValueError("expected a contiguous float64 CPU tensor")
+        return a, ctypes.c_void_p(a.data_ptr())
     a = np.ascontiguousarray(a, dtype=np.float64)
     return a, a.ctypes.data_as(ctypes.c_void_p)
 
@@ -223,6 +247,53 @@ def stb_toeplitz_matvec_static(A, a_storage, E, n_steps, nrhs, x, beta, y, strea
     _check(_library().stb_toeplitz_matvec_static(_ptr(A), a_storage, E, n_steps, nrhs, _ptr(x), beta,
                                                  _ptr(y), _stream(stream)),
            "stb_toeplitz_matvec_static")
+
+
+def _batch_items(meshes, params, V, K):
+    """ctypes array of stb_batch_item from lists (K entries may be None)."""
+    n = len(meshes)
+    arr = (stb_batch_item * n)()
+    for i in range(n):
+        arr[i].mesh = meshes[i].handle
+        arr[i].params = params[i]
+        arr[i].V = _ptr(V[i]).value
+        arr[i].K = _ptr(K[i]).value if K[i] is not None else None
+    return arr
+
+
+def stb_batch_workspace_size(meshes, params, V, K):
+    items = _batch_items(meshes, params, V, K)
+    return _size(_library().stb_batch_workspace_size, items, len(meshes))
+
+
+def stb_batch_assemble(meshes, params, V, K, tile, workspace, stream=None):
+    items = _batch_items(meshes, params, V, K)
+    _check(_library().stb_batch_assemble(items, len(meshes), tile, _ptr(workspace),
+                                         workspace.numel() * workspace.element_size(),
+                                         _stream(stream)), "stb_batch_assemble")
+
+
+def stb_batch_prepare(meshes, params, V, K, tile, workspace, stream=None):
+    items = _batch_items(meshes, params, V, K)
+    _check(_library().stb_batch_prepare(items, len(meshes), tile, _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(),
+                                        _stream(stream)), "stb_batch_prepare")
+
+
+def stb_batch_launch(meshes, params, V, K, tile, workspace, stream=None):
+    items = _batch_items(meshes, params, V, K)
+    _check(_library().stb_batch_launch(items, len(meshes), tile, _ptr(workspace),
+                                       workspace.numel() * workspace.element_size(),
+                                       _stream(stream)), "stb_batch_launch")
+
+
+def stb_batch_tune(meshes, params, V, K, workspace, stream=None):
+    items = _batch_items(meshes, params, V, K)
+    tile = _I32()
+    _check(_library().stb_batch_tune(items, len(meshes), _ptr(workspace),
+                                     workspace.numel() * workspace.element_size(), _stream(stream),
+                                     ctypes.byref(tile)), "stb_batch_tune")
+    return tile.value
 
 
 def stb_rhs_workspace_size(mesh, params, nrhs):

@@ -496,7 +496,7 @@ k_singular_f64(const double *__restrict__ geo, const TouchPair *__restrict__ pai
 }
 
 // ----------------------------------------------------------------- driver ---
-static AssemblyLayout layout(const Mesh &m, const stb_params &p, void *ws, size_t cap) {
+AssemblyLayout assembly_layout(const Mesh &m, const stb_params &p, void *ws, size_t cap) {
     Carve c(ws, cap);
     AssemblyLayout L{};
     L.geo = c.take<double>((size_t)m.n_tris * GEO_STRIDE);
@@ -522,7 +522,7 @@ static AssemblyLayout layout(const Mesh &m, const stb_params &p, void *ws, size_
     return L;
 }
 
-static stb_status check_params(const stb_params *p) {
+stb_status check_assembly_params(const stb_params *p) {
     if (!p) return fail(STB_ERR_INVALID_ARG, "params is NULL");
     if (!(p->alpha > 0.0) || !(p->T > 0.0) || !std::isfinite(p->alpha) || !std::isfinite(p->T))
         return fail(STB_ERR_INVALID_ARG, "alpha and T must be positive and finite");
@@ -538,7 +538,8 @@ static stb_status check_params(const stb_params *p) {
         return fail(STB_ERR_INVALID_ARG, "mixed precision supports n_steps <= 1024");
     if (p->storage != STB_STORE_F64 && p->storage != STB_STORE_F32)
         return fail(STB_ERR_INVALID_ARG, "storage must be STB_STORE_F64 or STB_STORE_F32");
-    if (p->reserved != 0) return fail(STB_ERR_INVALID_ARG, "reserved must be 0");
+    if (p->flags & ~(STB_FLAG_NO_SYNC | STB_FLAG_REFINE(15)))
+        return fail(STB_ERR_INVALID_ARG, "unknown flags");
     return STB_OK;
 }
 
@@ -594,23 +595,42 @@ static stb_status run_assembly(const Mesh &m, const stb_params &p, OutT *V, OutT
 
 using namespace stb;
 
+// Mixed path: upload the FP32 tables, then geometry and pair classification.
+stb_status stb::prepare_mixed(const Mesh &m, const stb_params &p, const AssemblyLayout &L,
+                         int32_t *status, cudaStream_t s) {
+    upload_psi_coeffs(s);
+    std::vector<float> rule, ss, nodes, host;
+    mixed_tables(p, rule, ss, nodes);
+    host = rule;
+    host.resize((size_t)(L.mss - L.mrule), 0.f);
+    host.insert(host.end(), ss.begin(), ss.end());
+    host.resize((size_t)(L.mnodes - L.mrule), 0.f);
+    host.insert(host.end(), nodes.begin(), nodes.end());
+    STB_CUDA(cudaMemcpyAsync(L.mrule, host.data(), host.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, s));
+    STB_CUDA(cudaMemsetAsync(L.pairs, 0xff, sizeof(TouchPair) * (m.n_touch > 0 ? m.n_touch : 1), s));
+    stb_status st = launch_geometry(m, L.geo, s);
+    if (st) return st;
+    return launch_classify(m, L.row_count, L.row_off, L.pairs, status, s);
+}
+
 extern "C" stb_status stb_assemble_workspace_size(const stb_mesh *mesh, const stb_params *params,
                                                   size_t *bytes) {
     if (!mesh || !bytes) return fail(STB_ERR_INVALID_ARG, "mesh and bytes must be given");
-    stb_status st = check_params(params);
+    stb_status st = check_assembly_params(params);
     if (st) return st;
-    *bytes = align256(layout(mesh->m, *params, nullptr, 0).bytes);
+    *bytes = align256(assembly_layout(mesh->m, *params, nullptr, 0).bytes);
     return STB_OK;
 }
 
 extern "C" stb_status stb_assemble(const stb_mesh *mesh, const stb_params *params, void *V, void *K,
                                    void *ws, size_t ws_bytes, stb_stream stream) {
     if (!mesh || !V) return fail(STB_ERR_INVALID_ARG, "mesh and V must be given");
-    stb_status st = check_params(params);
+    stb_status st = check_assembly_params(params);
     if (st) return st;
     const Mesh &m = mesh->m;
     if (m.n_tris > 65535) return fail(STB_ERR_INVALID_ARG, "dense assembly supports E <= 65535");
-    AssemblyLayout L = layout(m, *params, ws, ws_bytes);
+    AssemblyLayout L = assembly_layout(m, *params, ws, ws_bytes);
     if ((st = check_workspace(ws, ws_bytes, L.bytes))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     upload_psi_coeffs(s);
@@ -618,18 +638,7 @@ extern "C" stb_status stb_assemble(const stb_mesh *mesh, const stb_params *param
     STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
     int32_t *status = status_word(ws);
     if (params->precision == STB_PREC_MIXED) {
-        std::vector<float> rule, ss, nodes, host;
-        mixed_tables(*params, rule, ss, nodes);
-        host = rule;
-        host.resize((size_t)(L.mss - L.mrule), 0.f);
-        host.insert(host.end(), ss.begin(), ss.end());
-        host.resize((size_t)(L.mnodes - L.mrule), 0.f);
-        host.insert(host.end(), nodes.begin(), nodes.end());
-        STB_CUDA(cudaMemcpyAsync(L.mrule, host.data(), host.size() * sizeof(float),
-                                 cudaMemcpyHostToDevice, s));
-        STB_CUDA(cudaMemsetAsync(L.pairs, 0xff, sizeof(TouchPair) * (m.n_touch > 0 ? m.n_touch : 1), s));
-        if ((st = launch_geometry(m, L.geo, s))) return st;
-        if ((st = launch_classify(m, L.row_count, L.row_off, L.pairs, status, s))) return st;
+        if ((st = prepare_mixed(m, *params, L, status, s))) return st;
         return run_assembly_mixed(m, *params, V, K, L, s);
     }
     // FP64 host tables: regular rule, regularised rules, level constants

@@ -51,7 +51,27 @@ inline size_t mixed_node_floats(int n_steps) {
 }
 void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<float> &ss,
                   std::vector<float> &nodes);
+// Workspace layout of one problem (ws = nullptr: sizes only, L.bytes).
+AssemblyLayout assembly_layout(const Mesh &m, const stb_params &p, void *ws, size_t cap);
+stb_status check_assembly_params(const stb_params *p);
+// Mixed path set-up of one problem: tables, geometry, pair classification.
+stb_status prepare_mixed(const Mesh &m, const stb_params &p, const AssemblyLayout &L,
+                         int32_t *status, cudaStream_t s);
 stb_status run_assembly_mixed(const Mesh &m, const stb_params &p, void *V, void *K,
                               const AssemblyLayout &L, cudaStream_t s);
+
+// Batched mixed assembly (one persistent launch for the separated pairs of
+// all problems, one launch for their touching pairs).  upload_batch copies
+// the problems' descriptors for work items of `tile` columns (host memory,
+// not capturable); launch_batch only launches (capturable).
+struct BatchDesc;
+size_t batch_desc_bytes(int n);
+stb_status upload_batch(const Mesh *const *meshes, const stb_params *params,
+                        const AssemblyLayout *layouts, float *const *V, float *const *K, int n,
+                        BatchDesc *d_descs, int tile, cudaStream_t s);
+stb_status launch_batch(const Mesh *const *meshes, const stb_params *params,
+                        const AssemblyLayout *layouts, float *const *V, float *const *K, int n,
+                        const BatchDesc *d_descs, unsigned long long *counter, int tile, int stride,
+                        cudaStream_t s);
 
 }  // namespace stb

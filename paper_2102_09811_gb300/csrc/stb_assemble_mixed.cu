@@ -230,28 +230,30 @@ __device__ __forceinline__ void chunk_sum(const float *tab, int n_pass,
     }
 }
 
-template <class OutT>
-__global__ void __launch_bounds__(MREG_THREADS)
-k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E,
-                const float *__restrict__ rule, int nq, const float *__restrict__ nodes,
-                int n_nodes_f, int n_steps, MixConsts g, OutT *__restrict__ V,
-                OutT *__restrict__ K) {
-    extern __shared__ float smf[];
-    float4 *xa = reinterpret_cast<float4 *>(smf);  // x_a - P0_l and w_a
-    float *nd = smf + 4 * MAX_RULE_M;             // time nodes
-    const int l = blockIdx.y;
-    const int j = blockIdx.x * MREG_THREADS + threadIdx.x;
-    const double *gl = geo + (size_t)l * GEO_STRIDE;
-    for (int a = threadIdx.x; a < nq; a += MREG_THREADS) {
+// Test points of row l into shared memory: x_a - P0_l (FP32) and w_a.
+__device__ __forceinline__ void load_test_points(const double *__restrict__ gl,
+                                                 const float *__restrict__ rule, int nq,
+                                                 float4 *xa) {
+    for (int a = threadIdx.x; a < nq; a += blockDim.x) {
         double s1 = rule[4 * a], s2 = rule[4 * a + 1];
         double p[3];
         for (int c = 0; c < 3; ++c)
             p[c] = s1 * (gl[GEO_V1 + c] - gl[GEO_V0 + c]) + s2 * (gl[GEO_V2 + c] - gl[GEO_V1 + c]);
         xa[a] = make_float4((float)p[0], (float)p[1], (float)p[2], rule[4 * a + 2]);
     }
-    for (int i = threadIdx.x; i < n_nodes_f; i += MREG_THREADS) nd[i] = nodes[i];
-    __syncthreads();
-    if (j >= E) return;
+}
+
+// All blocks of V (and K, unless null) for the ordered pair (l, j) of one
+// problem; touching pairs are left to the regularised-rule kernel.  xa: the
+// test points of row l, nd: the time-node table (both in shared memory).
+template <class OutT>
+__device__ __forceinline__ void regular_pair_mixed(const double *__restrict__ geo,
+                                                   const int32_t *__restrict__ tris, int E,
+                                                   const float *__restrict__ rule, int nq,
+                                                   const float4 *xa, const float *nd,
+                                                   int n_steps, const MixConsts &g,
+                                                   OutT *__restrict__ V, OutT *__restrict__ K,
+                                                   int l, int j) {
     const int32_t tl[3] = {tris[3 * l], tris[3 * l + 1], tris[3 * l + 2]};
     const int32_t tj[3] = {tris[3 * j], tris[3 * j + 1], tris[3 * j + 2]};
     {
@@ -259,7 +261,7 @@ k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris
         for (int i = 0; i < 3; ++i) t |= (tl[i] == tj[0]) | (tl[i] == tj[1]) | (tl[i] == tj[2]);
         if (t) return;
     }
-    const double *gj = geo + (size_t)j * GEO_STRIDE;
+    const double *gl = geo + (size_t)l * GEO_STRIDE, *gj = geo + (size_t)j * GEO_STRIDE;
     float D[3], B1[3], B2[3], n[3];
     for (int c = 0; c < 3; ++c) {
         D[c] = (float)(gl[GEO_V0 + c] - gj[GEO_V0 + c]);
@@ -339,6 +341,24 @@ k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris
     }
 }
 
+
+template <class OutT>
+__global__ void __launch_bounds__(MREG_THREADS)
+k_regular_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E,
+                const float *__restrict__ rule, int nq, const float *__restrict__ nodes,
+                int n_nodes_f, int n_steps, MixConsts g, OutT *__restrict__ V,
+                OutT *__restrict__ K) {
+    extern __shared__ float smf[];
+    float4 *xa = reinterpret_cast<float4 *>(smf);  // x_a - P0_l and w_a
+    float *nd = smf + 4 * MAX_RULE_M;             // time nodes
+    const int l = blockIdx.y;
+    const int j = blockIdx.x * MREG_THREADS + threadIdx.x;
+    load_test_points(geo + (size_t)l * GEO_STRIDE, rule, nq, xa);
+    for (int i = threadIdx.x; i < n_nodes_f; i += MREG_THREADS) nd[i] = nodes[i];
+    __syncthreads();
+    if (j < E) regular_pair_mixed<OutT>(geo, tris, E, rule, nq, xa, nd, n_steps, g, V, K, l, j);
+}
+
 // ------------------------------------------------------- touching pairs ---
 constexpr int MSS_THREADS = 128;
 
@@ -370,14 +390,16 @@ struct MixSS {
     int n[4];
 };
 
+// All blocks of the touching pair P (both orders) of one problem: one CTA of
+// MSS_THREADS threads shares the points of the regularised rule.
 template <int CH, class OutT>
-__global__ void __launch_bounds__(MSS_THREADS)
-k_singular_mixed(const double *__restrict__ geo, const TouchPair *__restrict__ pairs, int E,
-                 MixSS tab, const float *__restrict__ nodes, int n_steps, MixConsts g,
-                 OutT *__restrict__ V, OutT *__restrict__ K) {
+__device__ __forceinline__ void singular_pair_mixed(const double *__restrict__ geo,
+                                                    const TouchPair P, int E, const MixSS &tab,
+                                                    const float *__restrict__ nodes, int n_steps,
+                                                    const MixConsts &g, OutT *__restrict__ V,
+                                                    OutT *__restrict__ K) {
     __shared__ float red[MSS_THREADS / 32][3 * CH + 9];
     __shared__ float fin[3 * CH + 9];
-    const TouchPair P = pairs[blockIdx.x];
     const int a = P.a, b = P.b, cls = P.cls;
     if (a < 0 || b < a || b >= E || cls < PAIR_VERTEX || cls > PAIR_IDENTICAL) return;
     const double *ga = geo + (size_t)a * GEO_STRIDE, *gb = geo + (size_t)b * GEO_STRIDE;
@@ -522,6 +544,14 @@ k_singular_mixed(const double *__restrict__ geo, const TouchPair *__restrict__ p
     }
 }
 
+template <int CH, class OutT>
+__global__ void __launch_bounds__(MSS_THREADS)
+k_singular_mixed(const double *__restrict__ geo, const TouchPair *__restrict__ pairs, int E,
+                 MixSS tab, const float *__restrict__ nodes, int n_steps, MixConsts g,
+                 OutT *__restrict__ V, OutT *__restrict__ K) {
+    singular_pair_mixed<CH, OutT>(geo, pairs[blockIdx.x], E, tab, nodes, n_steps, g, V, K);
+}
+
 // ------------------------------------------------------------ host side ---
 void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<float> &ss,
                   std::vector<float> &nodes) {
@@ -581,12 +611,7 @@ void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<flo
     }
 }
 
-template <class OutT>
-static stb_status run_mixed_t(const Mesh &m, const stb_params &p, OutT *V, OutT *K,
-                              const AssemblyLayout &L, cudaStream_t s) {
-    constexpr int CH = MIX_CH;
-    const int E = (int)m.n_tris;
-    const int nq = p.quad_regular * p.quad_regular;
+static MixConsts mix_consts(const stb_params &p) {
     const double pi = 3.14159265358979323846, al = p.alpha, h = p.T / p.n_steps;
     MixConsts g;
     g.c1 = (float)(1.0 / (2.0 * std::sqrt(al * h)));
@@ -594,6 +619,32 @@ static stb_status run_mixed_t(const Mesh &m, const stb_params &p, OutT *V, OutT 
     g.pV1 = (float)(std::sqrt(h) / (4.0 * pi * std::pow(al, 1.5)));
     g.pV2 = (float)(std::sqrt(2.0 * h) / (4.0 * pi * std::pow(al, 1.5)));
     g.pK = (float)(1.0 / (4.0 * pi * al));
+    return g;
+}
+
+static MixSS mix_ss(const AssemblyLayout &L) {
+    MixSS tab{};
+    const float *base = L.mss;
+    for (int cls = 1; cls <= 3; ++cls) {
+        const size_t n = L.ss_n[cls];
+        tab.p0[cls] = base;
+        tab.p1[cls] = base + n;
+        tab.p2[cls] = base + 2 * n;
+        tab.p3[cls] = base + 3 * n;
+        tab.w[cls] = base + 4 * n;
+        tab.n[cls] = (int)n;
+        base += 5 * n;
+    }
+    return tab;
+}
+
+template <class OutT>
+static stb_status run_mixed_t(const Mesh &m, const stb_params &p, OutT *V, OutT *K,
+                              const AssemblyLayout &L, cudaStream_t s) {
+    constexpr int CH = MIX_CH;
+    const int E = (int)m.n_tris;
+    const int nq = p.quad_regular * p.quad_regular;
+    const MixConsts g = mix_consts(p);
     const int nf = (int)mixed_node_floats(p.n_steps);
     const size_t smem = sizeof(float) * (4 * MAX_RULE_M + (size_t)nf);
     STB_CUDA(cudaFuncSetAttribute(k_regular_mixed<OutT>,
@@ -605,18 +656,7 @@ static stb_status run_mixed_t(const Mesh &m, const stb_params &p, OutT *V, OutT 
     stb_status st = check_launch("k_regular_mixed");
     if (st) return st;
     if (m.n_touch > 0) {
-        MixSS tab{};
-        const float *base = L.mss;
-        for (int cls = 1; cls <= 3; ++cls) {
-            const size_t n = L.ss_n[cls];
-            tab.p0[cls] = base;
-            tab.p1[cls] = base + n;
-            tab.p2[cls] = base + 2 * n;
-            tab.p3[cls] = base + 3 * n;
-            tab.w[cls] = base + 4 * n;
-            tab.n[cls] = (int)n;
-            base += 5 * n;
-        }
+        const MixSS tab = mix_ss(L);
         count_launch(s);
         k_singular_mixed<CH, OutT><<<(unsigned)m.n_touch, MSS_THREADS, 0, s>>>(
             L.geo, L.pairs, E, tab, L.mnodes, p.n_steps, g, V, K);
@@ -630,6 +670,184 @@ stb_status run_assembly_mixed(const Mesh &m, const stb_params &p, void *V, void 
     if (p.storage == STB_STORE_F64)
         return run_mixed_t<double>(m, p, (double *)V, (double *)K, L, s);
     return run_mixed_t<float>(m, p, (float *)V, (float *)K, L, s);
+}
+
+// -------------------------------------------------------------- batches ---
+// Many independent problems (meshes, alpha, steps) in one persistent launch
+// for their separated pairs and one launch for their touching pairs, all in
+// mixed precision with FP32 storage.  The work items of the persistent
+// kernel are (problem, row l, block of NT columns), numbered problem by
+// problem; every CTA claims items from a global counter, so problems of
+// uneven size and step count balance across the SMs, and a CTA reloads the
+// time-node table only when its next item belongs to another problem.
+struct BatchDesc {
+    const double *geo;
+    const int32_t *tris;
+    const float *rule, *nodes;
+    const TouchPair *pairs;
+    float *V, *K;
+    MixSS ss;
+    MixConsts g;
+    long long item0;  // first work item of this problem
+    int E, nq, n_steps, n_nodes_f, jblocks, touch0, n_touch, pad;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_regular_mixed_batch(const BatchDesc *__restrict__ descs, int n_desc, long long n_items,
+                      int stride, unsigned long long *__restrict__ counter) {
+    extern __shared__ float smf[];
+    float4 *xa = reinterpret_cast<float4 *>(smf);
+    float *nd = smf + 4 * MAX_RULE_M;
+    __shared__ long long s_item;
+    __shared__ int s_prob;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(counter, 1ull) * stride;
+            int pr = -1;
+            if (it < n_items) {  // last problem whose first item is <= it
+                int lo = 0, hi = n_desc - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (descs[mid].item0 <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                pr = lo;
+            }
+            s_item = it;
+            s_prob = pr;
+        }
+        __syncthreads();
+        const long long it = s_item;
+        const int pr = s_prob;
+        if (pr < 0) break;
+        const BatchDesc &D = descs[pr];
+        const long long local = it - D.item0;
+        const int l = (int)(local / D.jblocks), jb = (int)(local % D.jblocks);
+        if (pr != cur) {
+            for (int i = threadIdx.x; i < D.n_nodes_f; i += NT) nd[i] = D.nodes[i];
+            cur = pr;
+        }
+        load_test_points(D.geo + (size_t)l * GEO_STRIDE, D.rule, D.nq, xa);
+        __syncthreads();
+        const int j = jb * NT + threadIdx.x;
+        if (j < D.E) {
+            const MixConsts g = D.g;
+            regular_pair_mixed<float>(D.geo, D.tris, D.E, D.rule, D.nq, xa, nd, D.n_steps, g, D.V,
+                                      D.K, l, j);
+        }
+        __syncthreads();  // shared tables are rewritten by the next item
+    }
+}
+
+__global__ void __launch_bounds__(MSS_THREADS)
+k_singular_mixed_batch(const BatchDesc *__restrict__ descs, int n_desc) {
+    const int b = blockIdx.x;
+    int lo = 0, hi = n_desc - 1;  // last problem whose first touching pair is <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (descs[mid].touch0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchDesc &D = descs[lo];
+    if (b - D.touch0 >= D.n_touch) return;
+    const MixSS ss = D.ss;
+    const MixConsts g = D.g;
+    singular_pair_mixed<MIX_CH, float>(D.geo, D.pairs[b - D.touch0], D.E, ss, D.nodes, D.n_steps, g,
+                                       D.V, D.K);
+}
+
+size_t batch_desc_bytes(int n) { return align256((size_t)n * sizeof(BatchDesc)); }
+
+template <int NT>
+static stb_status launch_batch_regular(const BatchDesc *d_descs, int n, long long n_items,
+                                       int stride, unsigned long long *counter, size_t smem,
+                                       cudaStream_t s) {
+    STB_CUDA(cudaFuncSetAttribute(k_regular_mixed_batch<NT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    STB_CUDA(cudaGetDevice(&dev));
+    STB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    STB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_regular_mixed_batch<NT>, NT,
+                                                           smem));
+    if (per_sm < 1) return fail(STB_ERR_CUDA, "batched kernel does not fit on an SM");
+    const long long claims = (n_items + stride - 1) / stride;
+    const long long grid = std::min<long long>((long long)sms * per_sm, std::max(1LL, claims));
+    STB_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+    count_launch(s);
+    k_regular_mixed_batch<NT><<<(unsigned)grid, NT, smem, s>>>(d_descs, n, n_items, stride, counter);
+    return check_launch("k_regular_mixed_batch");
+}
+
+// Descriptors of problem i (prepared by prepare_mixed into layouts[i]) for
+// work items of `tile` columns; totals for the launch.
+static void batch_descs(const Mesh *const *meshes, const stb_params *params,
+                        const AssemblyLayout *layouts, float *const *V, float *const *K, int n,
+                        int tile, std::vector<BatchDesc> &h, long long &items, int &touch,
+                        int &max_nf) {
+    h.assign(n, BatchDesc{});
+    items = 0;
+    touch = 0;
+    max_nf = 0;
+    for (int i = 0; i < n; ++i) {
+        const Mesh &m = *meshes[i];
+        const stb_params &p = params[i];
+        BatchDesc &D = h[i];
+        D.geo = layouts[i].geo;
+        D.tris = m.d_tris;
+        D.rule = layouts[i].mrule;
+        D.nodes = layouts[i].mnodes;
+        D.pairs = layouts[i].pairs;
+        D.V = V[i];
+        D.K = K[i];
+        D.ss = mix_ss(layouts[i]);
+        D.g = mix_consts(p);
+        D.E = (int)m.n_tris;
+        D.nq = p.quad_regular * p.quad_regular;
+        D.n_steps = p.n_steps;
+        D.n_nodes_f = (int)mixed_node_floats(p.n_steps);
+        D.jblocks = (D.E + tile - 1) / tile;
+        D.item0 = items;
+        D.touch0 = touch;
+        D.n_touch = (int)m.n_touch;
+        items += (long long)D.E * D.jblocks;
+        touch += D.n_touch;
+        max_nf = std::max(max_nf, D.n_nodes_f);
+    }
+}
+
+stb_status upload_batch(const Mesh *const *meshes, const stb_params *params,
+                        const AssemblyLayout *layouts, float *const *V, float *const *K, int n,
+                        BatchDesc *d_descs, int tile, cudaStream_t s) {
+    std::vector<BatchDesc> h;
+    long long items;
+    int touch, max_nf;
+    batch_descs(meshes, params, layouts, V, K, n, tile, h, items, touch, max_nf);
+    STB_CUDA(cudaMemcpyAsync(d_descs, h.data(), h.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice,
+                             s));
+    return STB_OK;
+}
+
+// Launches only (descriptors uploaded by upload_batch with the same tile).
+// stride > 1 runs every stride-th work item of the separated pairs and no
+// touching pairs (timing samples of the tile tuner).
+stb_status launch_batch(const Mesh *const *meshes, const stb_params *params,
+                        const AssemblyLayout *layouts, float *const *V, float *const *K, int n,
+                        const BatchDesc *d_descs, unsigned long long *counter, int tile, int stride,
+                        cudaStream_t s) {
+    std::vector<BatchDesc> h;
+    long long items;
+    int touch, max_nf;
+    batch_descs(meshes, params, layouts, V, K, n, tile, h, items, touch, max_nf);
+    const size_t smem = sizeof(float) * (4 * MAX_RULE_M + (size_t)max_nf);
+    stb_status st = tile == 64    ? launch_batch_regular<64>(d_descs, n, items, stride, counter, smem, s)
+                    : tile == 256 ? launch_batch_regular<256>(d_descs, n, items, stride, counter, smem, s)
+                                  : launch_batch_regular<128>(d_descs, n, items, stride, counter, smem, s);
+    if (st || stride > 1 || touch == 0) return st;
+    count_launch(s);
+    k_singular_mixed_batch<<<(unsigned)touch, MSS_THREADS, 0, s>>>(d_descs, n);
+    return check_launch("k_singular_mixed_batch");
 }
 
 }  // namespace stb

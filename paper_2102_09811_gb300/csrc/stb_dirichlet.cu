@@ -5,6 +5,9 @@
 // space rule (conical, q x q) and time rule (Gauss, n_time) live in shared
 // memory.
 #include <cmath>
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "stb_internal.h"
@@ -219,12 +222,35 @@ static stb_status check_rule_args(int nrhs, int n_src, int q, int nt) {
     return STB_OK;
 }
 
+// Rule tables per (q, n_time) in page-locked host memory, built once and
+// kept for the life of the process, so that the copy below is a plain
+// asynchronous copy (and can be captured into a CUDA graph once the first,
+// uncaptured call has built the table).
+static stb_status pinned_rules(int q, int nt, const double **out, size_t *count) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, std::pair<double *, size_t>> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto f = cache.find({q, nt});
+    if (f == cache.end()) {
+        std::vector<double> host;
+        host_rules(q, nt, host);
+        double *pinned = nullptr;
+        STB_CUDA(cudaMallocHost(&pinned, host.size() * sizeof(double)));
+        std::copy(host.begin(), host.end(), pinned);
+        f = cache.emplace(std::make_pair(q, nt), std::make_pair(pinned, host.size())).first;
+    }
+    *out = f->second.first;
+    *count = f->second.second;
+    return STB_OK;
+}
+
 static stb_status upload_rules_sources(const DirLayout &L, int q, int nt, const double *sources,
                                        int nrhs, int n_src, cudaStream_t s) {
-    std::vector<double> host;
-    host_rules(q, nt, host);
-    STB_CUDA(cudaMemcpyAsync(L.rule, host.data(), host.size() * sizeof(double),
-                             cudaMemcpyHostToDevice, s));
+    const double *rules;
+    size_t count;
+    stb_status st = pinned_rules(q, nt, &rules, &count);
+    if (st) return st;
+    STB_CUDA(cudaMemcpyAsync(L.rule, rules, count * sizeof(double), cudaMemcpyHostToDevice, s));
     STB_CUDA(cudaMemcpyAsync(L.src, sources, sizeof(double) * 5 * (size_t)nrhs * n_src,
                              cudaMemcpyHostToDevice, s));
     return STB_OK;

@@ -342,7 +342,7 @@ stb_params stb_default_params(double alpha, double T, int32_t n_steps) {
     p.quad_singular = 4;
     p.precision = STB_PREC_FP64;
     p.storage = STB_STORE_F64;
-    p.reserved = 0;
+    p.flags = 0;
     return p;
 }
 

@@ -16,6 +16,7 @@
 // products of the stored FP32 blocks with a two-float split of w, error-free
 // two-sums), so that no O(E^2 E_t^2) work runs on the scarce FP64 pipe.  The
 // refinement stops at ||f - V_h w|| <= 1e-10 ||f||.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -287,6 +288,43 @@ static void inv_tasks(int a, int b, int depth, std::vector<InvLevel> &lv) {
         }
 }
 
+// The same task lists written on the device (no host copy, so the
+// factorisation can be captured into a CUDA graph): per tree depth, the
+// phase-1 tasks at off[depth] and the phase-2 tasks cnt[depth] later, nodes
+// of one depth in the left-to-right order of the host recursion above.
+constexpr int INV_MAX_DEPTH = 32;
+struct InvOffs {
+    int off[INV_MAX_DEPTH], cnt[INV_MAX_DEPTH];
+};
+
+__global__ void k_inv_tasks(int nb, int n_levels, InvOffs o, int4 *out) {
+    for (int d = 0; d < n_levels; ++d) {
+        int fill = 0;
+        // nodes of depth d left to right: paths of d halving choices, first
+        // choice in the highest bit (0 = left half)
+        for (long long path = 0; path < (1LL << d); ++path) {
+            int a = 0, b = nb;
+            bool ok = true;
+            for (int k = d - 1; k >= 0 && ok; --k) {
+                if (b - a < 2) {
+                    ok = false;
+                } else {
+                    const int c = a + (b - a) / 2;
+                    if ((path >> k) & 1) a = c;
+                    else b = c;
+                }
+            }
+            if (!ok || b - a < 2) continue;
+            const int c = a + (b - a) / 2;
+            for (int i = c; i < b; ++i)
+                for (int j = a; j < c; ++j, ++fill) {
+                    out[o.off[d] + fill] = make_int4(i, j, j, c - 1);
+                    out[o.off[d] + o.cnt[d] + fill] = make_int4(i, j, c, i);
+                }
+        }
+    }
+}
+
 static size_t inv_task_count(int nb) {
     std::vector<InvLevel> lv;
     inv_tasks(0, nb, 0, lv);
@@ -541,6 +579,18 @@ __global__ void k_norms2(const double *__restrict__ a, const double *__restrict_
     }
 }
 
+// Device-side end of a refinement without host synchronisation: the
+// relative residual from out[0] = ||r||^2, out[1] = ||f||^2 into the
+// workspace header, and STB_ERR_NOT_CONVERGED if it exceeds tol.
+__global__ void k_refine_report(const double *__restrict__ norms, double tol, int32_t refinements,
+                                int32_t *__restrict__ hdr_status, int32_t *__restrict__ hdr_refine,
+                                double *__restrict__ hdr_residual) {
+    const double rel = norms[1] > 0.0 ? sqrt(norms[0] / norms[1]) : sqrt(norms[0]);
+    *hdr_refine = refinements;
+    *hdr_residual = rel;
+    if (!(rel <= tol)) atomicCAS(hdr_status, 0, STB_ERR_NOT_CONVERGED);
+}
+
 // ---------------------------------------------------------------- driver ---
 // Workspace header (first 256 bytes): int32 status, int32 refinements,
 // double relative residual of the last solve.
@@ -615,29 +665,27 @@ static stb_status factorize(const AT *V, int E, const SolveLayout &S, int32_t *s
     if ((st = check_launch("k_trtri_diag"))) return st;
     {  // off-diagonal tiles of L^{-1}: recursive halving, deepest level first
         std::vector<InvLevel> lv;
-        inv_tasks(0, nb, 0, lv);
-        std::vector<int4> all;
-        for (auto &l : lv) {
-            all.insert(all.end(), l.p1.begin(), l.p1.end());
-            all.insert(all.end(), l.p2.begin(), l.p2.end());
-        }
-        if (!all.empty()) {
-            STB_CUDA(cudaMemcpyAsync(S.tasks, all.data(), all.size() * sizeof(int4),
-                                     cudaMemcpyHostToDevice, s));
-            size_t off = 0;
-            std::vector<size_t> offs(lv.size());
+        inv_tasks(0, nb, 0, lv);  // host copy: only the counts are used
+        if (!lv.empty()) {
+            if ((int)lv.size() > INV_MAX_DEPTH) return fail(STB_ERR_INVALID_ARG, "E too large");
+            InvOffs o{};
+            int off = 0;
             for (size_t d = 0; d < lv.size(); ++d) {
-                offs[d] = off;
-                off += lv[d].p1.size() + lv[d].p2.size();
+                o.off[d] = off;
+                o.cnt[d] = (int)lv[d].p1.size();
+                off += 2 * o.cnt[d];
             }
+            count_launch(s);
+            k_inv_tasks<<<1, 1, 0, s>>>(nb, (int)lv.size(), o, S.tasks);
+            if ((st = check_launch("k_inv_tasks"))) return st;
             T *W = LiT;  // scratch until the transpose below
             for (int d = (int)lv.size() - 1; d >= 0; --d) {
-                const int4 *t1 = S.tasks + offs[d], *t2 = t1 + lv[d].p1.size();
+                const int4 *t1 = S.tasks + o.off[d], *t2 = t1 + o.cnt[d];
                 count_launch(s);
-                k_tile_gemm<T><<<(unsigned)lv[d].p1.size(), 256, 0, s>>>(t1, L, Li, W, E, (T)1);
+                k_tile_gemm<T><<<(unsigned)o.cnt[d], 256, 0, s>>>(t1, L, Li, W, E, (T)1);
                 if ((st = check_launch("k_tile_gemm(L21 Li11)"))) return st;
                 count_launch(s);
-                k_tile_gemm<T><<<(unsigned)lv[d].p2.size(), 256, 0, s>>>(t2, Li, W, Li, E, (T)-1);
+                k_tile_gemm<T><<<(unsigned)o.cnt[d], 256, 0, s>>>(t2, Li, W, Li, E, (T)-1);
                 if ((st = check_launch("k_tile_gemm(Li22 W)"))) return st;
             }
         }
@@ -710,29 +758,38 @@ constexpr int MAX_REFINE = 8;
 
 static stb_status solve_mixed(const float *V, int E, int n_steps, int nrhs, const double *f,
                               double *w, const SolveLayout &S, int32_t *status, void *ws,
-                              cudaStream_t s) {
+                              bool no_sync, int fixed_refine, cudaStream_t s) {
     stb_status st = factorize<float, float>(V, E, S, status, s);
     if (st) return st;
     const size_t n = (size_t)nrhs * n_steps * E;
     STB_CUDA(cudaMemsetAsync(w, 0, n * sizeof(double), s));
     const double *rhs = f;  // first pass solves with f itself
     SolveHeader hdr{STB_OK, 0, 0.0};
-    for (int it = 0; it <= MAX_REFINE; ++it) {
+    const int max_refine = no_sync ? fixed_refine : MAX_REFINE;
+    for (int it = 0; it <= max_refine; ++it) {
         if ((st = march<float, float>(V, E, n_steps, nrhs, rhs, S.delta, S, s))) return st;
         count_launch(s);
         k_update<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, S.delta, n);
         if ((st = check_launch("k_update"))) return st;
         if ((st = toeplitz_df(V, E, n_steps, nrhs, w, DF_RESIDUAL, f, 0.0, S.r, S.df, s))) return st;
+        rhs = S.r;
+        if (no_sync && it < max_refine) continue;  // fixed count: no norms until the end
         count_launch(s);
         k_norms2<<<1, 1024, 0, s>>>(S.r, f, n, S.norms);
         if ((st = check_launch("k_norms2"))) return st;
+        if (no_sync) {
+            SolveHeader *dh = static_cast<SolveHeader *>(ws);
+            count_launch(s);
+            k_refine_report<<<1, 1, 0, s>>>(S.norms, REFINE_TOL, it, &dh->status, &dh->refinements,
+                                            &dh->rel_residual);
+            return check_launch("k_refine_report");
+        }
         double nrm[2];
         STB_CUDA(cudaMemcpyAsync(nrm, S.norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
         STB_CUDA(cudaStreamSynchronize(s));
         hdr.refinements = it;
         hdr.rel_residual = nrm[1] > 0.0 ? std::sqrt(nrm[0] / nrm[1]) : std::sqrt(nrm[0]);
         if (hdr.rel_residual <= REFINE_TOL || !std::isfinite(hdr.rel_residual)) break;
-        rhs = S.r;
     }
     int32_t dev_status = 0;
     STB_CUDA(cudaMemcpyAsync(&dev_status, status, sizeof dev_status, cudaMemcpyDeviceToHost, s));
@@ -776,7 +833,9 @@ extern "C" stb_status stb_dirichlet_solve(const stb_mesh *mesh, const stb_params
     STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
     int32_t *status = status_word(ws);
     if (mixed) {
-        st = solve_mixed((const float *)V, (int)E, p->n_steps, nrhs, f, w, S, status, ws, s);
+        st = solve_mixed((const float *)V, (int)E, p->n_steps, nrhs, f, w, S, status, ws,
+                         (p->flags & STB_FLAG_NO_SYNC) != 0,
+                         std::max(1, (p->flags >> 8) & 15), s);
         if (st) return st;
     } else {
         if (p->storage == STB_STORE_F64) {
@@ -788,6 +847,7 @@ extern "C" stb_status stb_dirichlet_solve(const stb_mesh *mesh, const stb_params
         }
         if (st) return st;
     }
+    if (p->flags & STB_FLAG_NO_SYNC) return STB_OK;  // status stays in the workspace
     return stb_workspace_status(ws, stream);
 }
 

@@ -79,3 +79,137 @@ class DirichletProblem:
     def relative_error(self):
         e = self.err.cpu()
         return math.sqrt(float(e[0]) / float(e[1]))
+
+
+class BatchPipeline:
+    """Many independent Dirichlet problems, mixed precision, FP32 storage.
+
+    problems: list of dicts with nodes, tris, alpha, T, n_steps, sources.
+    The problems are grouped into waves whose V and K fit `wave_bytes` (one
+    arena of that size, shared by the waves).  Per wave, stb_batch_prepare
+    uploads the tables once; everything after it -- the batched assembly
+    launches, and per problem the projection, right-hand side, solve (with
+    the refinement count of a first, synchronous pass) and error -- is captured
+    into one CUDA graph on the first run and replayed on later runs.  The
+    captured calls carry STB_FLAG_NO_SYNC; sources are kept in page-locked
+    host memory.
+    """
+
+    def __init__(self, problems, wave_bytes=48e9, device="cuda", tile=0, tune=True,
+                 q_space=8, n_time=16):
+        dev = torch.device(device)
+        self.device, self.q_space, self.n_time, self.tile, self.tune = dev, q_space, n_time, tile, tune
+        self.items = []
+        for p in problems:
+            mesh = capi.Mesh(p["nodes"], p["tris"])
+            prm = capi.stb_default_params(p["alpha"], p["T"], p["n_steps"],
+                                          precision=capi.STB_PREC_MIXED, storage=capi.STB_STORE_F32)
+            src = torch.tensor(p["sources"], dtype=torch.float64).pin_memory()
+            nrhs, n_src = src.shape[0], src.shape[1]
+            E, n = mesh.n_tris, p["n_steps"]
+            vec = (nrhs, n, E)
+            it = dict(mesh=mesh, params=prm, sources=src, E=E, n_steps=n, nrhs=nrhs,
+                      g=torch.zeros(vec, dtype=torch.float64, device=dev),
+                      f=torch.zeros(vec, dtype=torch.float64, device=dev),
+                      w=torch.zeros(vec, dtype=torch.float64, device=dev),
+                      err=torch.zeros(2, dtype=torch.float64, device=dev),
+                      ws_solve=_ws(capi.stb_solve_workspace_size(mesh, prm, nrhs), dev),
+                      vk_bytes=8 * E * E * n)
+            it["ws_project"] = capi.stb_project_workspace_size(mesh, nrhs, n_src, q_space, n_time)
+            it["ws_rhs"] = capi.stb_rhs_workspace_size(mesh, prm, nrhs)
+            it["ws_error"] = capi.stb_error_workspace_size(mesh, prm, nrhs, n_src, q_space, n_time)
+            self.items.append(it)
+        order = sorted(range(len(self.items)), key=lambda i: -self.items[i]["vk_bytes"])
+        self.waves, cur, size = [], [], 0
+        for i in order:
+            b = self.items[i]["vk_bytes"]
+            if b > wave_bytes:
+                raise ValueError("problem %d needs %d bytes of blocks, more than wave_bytes" % (i, b))
+            if cur and size + b > wave_bytes:
+                self.waves.append(cur)
+                cur, size = [], 0
+            cur.append(i)
+            size += b
+        if cur:
+            self.waves.append(cur)
+        arena = max(sum(self.items[i]["vk_bytes"] for i in w) for w in self.waves)
+        self.arena = torch.empty(arena // 4, dtype=torch.float32, device=dev)
+        shared = max(max(it["ws_project"], it["ws_rhs"], it["ws_error"]) for it in self.items)
+        self.ws_shared = _ws(shared, dev)
+        self.graphs = [None] * len(self.waves)
+        self.wave_state = [None] * len(self.waves)
+
+    def _wave_buffers(self, w):
+        """V, K views of the arena for the problems of wave w."""
+        V, K, off = [], [], 0
+        for i in self.waves[w]:
+            it = self.items[i]
+            n = it["n_steps"] * it["E"] * it["E"]
+            V.append(self.arena[off:off + n].view(it["n_steps"], it["E"], it["E"]))
+            K.append(self.arena[off + n:off + 2 * n].view(it["n_steps"], it["E"], it["E"]))
+            off += 2 * n
+        return V, K
+
+    def _enqueue(self, w, stream):
+        """The capturable part of wave w (after stb_batch_prepare)."""
+        meshes, params, V, K, tile, ws = self.wave_state[w]
+        capi.stb_batch_launch(meshes, params, V, K, tile, ws, stream)
+        for k, i in enumerate(self.waves[w]):
+            it = self.items[i]
+            m, p = it["mesh"], it["params"]
+            capi.stb_project_dirichlet(m, p, it["sources"], it["g"], self.ws_shared, self.q_space,
+                                       self.n_time, stream)
+            capi.stb_dirichlet_rhs(m, p, K[k], it["g"], it["nrhs"], it["f"], self.ws_shared, stream)
+            capi.stb_dirichlet_solve(m, p, V[k], it["f"], it["nrhs"], it["w"], it["ws_solve"],
+                                     stream)
+            capi.stb_neumann_error(m, p, it["sources"], it["w"], it["err"], self.ws_shared,
+                                   self.q_space, self.n_time, stream)
+
+    def _build(self, w, stream):
+        meshes = [self.items[i]["mesh"] for i in self.waves[w]]
+        params = [self.items[i]["params"] for i in self.waves[w]]
+        V, K = self._wave_buffers(w)
+        ws = _ws(capi.stb_batch_workspace_size(meshes, params, V, K), self.device)
+        tile = self.tile
+        if tile == 0 and self.tune:
+            tile = capi.stb_batch_tune(meshes, params, V, K, ws, stream)
+        capi.stb_batch_prepare(meshes, params, V, K, tile, ws, stream)
+        self.wave_state[w] = (meshes, params, V, K, tile, ws)
+        # one uncaptured pass with synchronous solves: builds the page-locked
+        # rule tables and gives each problem's refinement count, which the
+        # captured solves then run without host synchronisation
+        for p in params:
+            p.flags = 0
+        self._enqueue(w, stream)
+        torch.cuda.synchronize()
+        for i, p in zip(self.waves[w], params):
+            r, _ = capi.stb_solve_report(self.items[i]["ws_solve"])
+            p.flags = capi.STB_FLAG_NO_SYNC | capi.STB_FLAG_REFINE(max(1, r))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._enqueue(w, torch.cuda.current_stream())
+        self.graphs[w] = g
+
+    def run(self, stream=None):
+        """All waves: replays each wave's graph (built on the first call)."""
+        s = stream if stream is not None else torch.cuda.current_stream()
+        for w in range(len(self.waves)):
+            if self.graphs[w] is None:
+                self._build(w, s)
+            self.graphs[w].replay()
+
+    def relative_errors(self):
+        return [math.sqrt(float(e[0]) / float(e[1])) for e in (it["err"].cpu() for it in self.items)]
+
+    def reports(self):
+        """(refinements, relative residual, status) of every problem's solve."""
+        out = []
+        for it in self.items:
+            r, res = capi.stb_solve_report(it["ws_solve"])
+            try:
+                capi.stb_workspace_status(it["ws_solve"])
+                st = 0
+            except capi.StbError as e:
+                st = e.code
+            out.append((r, res, st))
+        return out

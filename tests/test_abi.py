@@ -39,7 +39,7 @@ def test_status_strings_and_defaults():
         assert lib.stb_status_string(code).decode() not in ("", "unknown status")
     p = capi.stb_default_params(0.5, 2.0, 10)
     assert (p.alpha, p.T, p.n_steps, p.quad_regular, p.quad_singular, p.precision, p.storage,
-            p.reserved) == (0.5, 2.0, 10, 3, 4, 0, 0, 0)
+            p.flags) == (0.5, 2.0, 10, 3, 4, 0, 0, 0)
 
 
 def test_launch_count_starts_without_gpu_work():
