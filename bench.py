@@ -92,6 +92,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--wave-gb", type=float, default=48.0,
+                    help="V+K bytes per memory wave of the batch64 workload")
     ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
 
@@ -151,39 +153,86 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_rate(wl, alpha, seconds):
-    """The FP64 oracle (single thread) on whole rows of V and K: entries/s."""
+def cpu_oracle_rate(wl, alpha, seconds, threads=1):
+    """The FP64 oracle on whole rows of V and K: entries/s.  threads > 1
+    runs rows on that many host threads at once (the oracle's C code runs
+    with the interpreter lock released), like an OpenMP loop over test
+    triangles with dynamic scheduling."""
+    import threading
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle
     E, n = len(wl["tris"]), wl["n_steps"]
-    rows_done, t_used, row = 0, 0.0, 0
-    while t_used < seconds and rows_done < E:
-        t0 = time.perf_counter()
-        oracle.assemble_rows(wl["nodes"], wl["tris"], alpha, wl["T"], n, np.array([row]))
-        t_used += time.perf_counter() - t0
-        rows_done += 1
-        row = (row + 977) % E
-    return 2.0 * n * E * rows_done / t_used, rows_done, t_used
+    state = {"next": 0, "done": 0}
+    lock = threading.Lock()
+    t0 = time.perf_counter()
+
+    def worker():
+        while time.perf_counter() - t0 < seconds:
+            with lock:  # every row once, spread over the mesh
+                k = state["next"]
+                state["next"] += 1
+            if k >= E:
+                return
+            row = (977 * k) % E
+            oracle.assemble_rows(wl["nodes"], wl["tris"], alpha, wl["T"], n, np.array([row]))
+            with lock:
+                state["done"] += 1
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        for f in [ex.submit(worker) for _ in range(threads)]:
+            f.result()
+    t_used = time.perf_counter() - t0
+    return 2.0 * n * E * state["done"] / t_used, state["done"], t_used
+
+
+def host_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def max_over_ranks(value, world, device):
+    """Maximum of a per-rank float over all ranks (the job's time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, ms, world):
+    """Units of all ranks per second: every rank processes the same work."""
+    return world * units_per_rank_step * steps / (ms / 1e3)
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    if args.workload == "batch64":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm times "
+                          "single workloads; batch64 is measured on the GPU only"}), flush=True)
+        return
     wl = workloads.workload(args.workload)
     alphas = [float(a) for a in args.alphas.split(",")]
     E, n = len(wl["tris"]), wl["n_steps"]
     per_step = max(1.0, args.cpu_seconds / 3.0)
+    threads = host_threads()
     for i in range(args.warmup):
-        cpu_oracle_rate(wl, alphas[i % len(alphas)], per_step / 4)
+        cpu_oracle_rate(wl, alphas[i % len(alphas)], per_step / 4, threads)
     rates, rows_total, secs_total = [], 0, 0.0
     for i in range(args.steps):
-        r, rows, secs = cpu_oracle_rate(wl, alphas[i % len(alphas)], per_step)
+        r, rows, secs = cpu_oracle_rate(wl, alphas[i % len(alphas)], per_step, threads)
         rates.append(r)
         rows_total += rows
         secs_total += secs
     value = 2.0 * n * E * rows_total / secs_total
-    sample = "%d whole rows (all %d blocks of V and K) of %s, alpha cycling %s" % (
-        rows_total, n, args.workload, alphas)
+    sample = "%d whole rows (all %d blocks of V and K) of %s, alpha cycling %s, %d host threads" % (
+        rows_total, n, args.workload, alphas, threads)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * 2 * n * E * E * len(alphas) / value,
@@ -191,7 +240,7 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": args.workload, "E": E, "n_steps": n, "alphas": alphas,
                        "quad_regular": 3, "quad_singular": 4},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -281,13 +330,9 @@ def run_gpu(args):
     capi.stb_trace_enable(False)
     launches = capi.stb_launch_count() - launches0
     trace = capi.stb_trace_read()
-    ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(start.elapsed_time(end), world, "cuda")
     entries = 2.0 * n * E * E * len(alphas)
-    value = world * entries * args.steps / (ms / 1e3)
+    value = whole_job_rate(entries, args.steps, ms, world)
     rel_err = [p.relative_error() for p in probs]
     n_reg_pairs = E * E - 2 * mesh.n_touching + E  # ordered separated pairs
     name = max(trace.items(), key=lambda kv: kv[1][1])[0]
@@ -334,6 +379,20 @@ def run_gpu(args):
     mv_tflops, mv_ms = matvec[best]["tflops"], matvec[best]["ms"]
     matvec["blocks_read_gb"] = a_bytes / 1e9
     matvec["hbm_peak_gbs"] = HBM_PEAK_GBS
+
+    # stage times of one problem (CUDA events, outside the timed region) and
+    # the refinement report of its solve
+    stage_ms = {}
+    for label, fn in (("assemble", p0.assemble), ("project", p0.project), ("rhs", p0.rhs),
+                      ("solve", p0.solve), ("error", p0.error)):
+        a_.record(stream)
+        fn(stream)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        stage_ms[label] = a_.elapsed_time(b_)
+    refinements, rel_residual = capi.stb_solve_report(p0.ws_solve)
+    solve_info = {"stage_ms": stage_ms, "refinements": refinements, "rel_residual": rel_residual,
+                  "alpha": alphas[0]}
 
     # the other precision: FP64 assembly of one problem for "mixed vs FP64"
     cmp = None
@@ -395,16 +454,79 @@ def run_gpu(args):
                              % (2 * (4 if mixed else 8) * n * E * E * len(alphas) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "mixed_vs_fp64": cmp, "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
-            "rel_l2_error_w": rel_err, "gpu_launches": launches,
+            "rel_l2_error_w": rel_err, "solve": solve_info, "gpu_launches": launches,
             "kernels_ms": {k: v[1] for k, v in trace.items()}, "roofline": roof, "e2e": e2e}
     if rank == 0:
         line["clocks"] = clk.summary()
         if world == 1 and not args.no_cpu_baseline:
-            rate, rows, secs = cpu_oracle_rate(wl, alphas[0], args.cpu_seconds)
-            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            threads = host_threads()
+            rate, rows, secs = cpu_oracle_rate(wl, alphas[0], args.cpu_seconds, threads)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                     "sample": "%d whole rows (all %d blocks of V and K) of %s, "
-                                              "alpha=%g, %.1f s" % (rows, n, args.workload,
-                                                                     alphas[0], secs)}
+                                              "alpha=%g, %.1f s on %d host threads"
+                                              % (rows, n, args.workload, alphas[0], secs, threads)}
+            rate1, rows1, secs1 = cpu_oracle_rate(wl, alphas[0], args.cpu_seconds / 4, 1)
+            line["cpu_baseline_one_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
+                                               "kind": "oracle",
+                                               "sample": "%d whole rows, %.1f s" % (rows1, secs1)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_batch(args):
+    """The 64-problem batch (ellipsoids from seed 0) through the graph-captured
+    batch pipeline: every run replays one CUDA graph per memory wave."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2102_09811_gb300 import capi, pipeline
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    probs = workloads.batch_workload(seed=0)
+    bp = pipeline.BatchPipeline(probs, wave_bytes=args.wave_gb * 1e9)
+    entries = sum(2.0 * len(p["tris"]) ** 2 * p["n_steps"] for p in probs)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, args.warmup)):  # the first run builds and tunes the graphs
+        bp.run(stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier()
+        start.record(stream)
+        for _ in range(args.steps):
+            bp.run(stream)
+        end.record(stream)
+        barrier()
+    ms = max_over_ranks(start.elapsed_time(end), world, "cuda")
+    value = whole_job_rate(entries, args.steps, ms, world)
+    reports = bp.reports()
+    errs = bp.relative_errors()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64", "problems": len(probs), "waves": len(bp.waves),
+                       "wave_gb": args.wave_gb, "precision": "mixed, FP32 storage",
+                       "graph": "one CUDA graph per wave (batched assembly, projection, RHS, "
+                                "solve, error)",
+                       "l2": "no flush: every step writes %.0f GB of V/K blocks" % (4 * entries / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "gpu_launches": args.steps * sum(bp.graph_launches),
+            "refinements_max": max(r for r, _, _ in reports),
+            "rel_residual_max": max(res for _, res, _ in reports),
+            "solve_status": sorted(set(st for _, _, st in reports)),
+            "rel_l2_error_w_range": [min(errs), max(errs)], "e2e": None}
+    if rank == 0:
+        line["clocks"] = clk.summary()
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -414,6 +536,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_gpu(args)
 

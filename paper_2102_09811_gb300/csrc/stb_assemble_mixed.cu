@@ -29,6 +29,7 @@ namespace stb {
 
 struct MixConsts {
     float c1, c2;    // 1/(2 sqrt(alpha h)), 1/(2 sqrt(2 alpha h))
+    float ic1, ic2;  // 1/c1, 1/c2
     float pV1, pV2;  // sqrt(h)/(4 pi alpha^{3/2}), sqrt(2h)/(4 pi alpha^{3/2})
     float pK;        // 1/(4 pi alpha)
 };
@@ -41,8 +42,9 @@ __device__ __forceinline__ float ex2(float x) {
     return y;
 }
 
-// psi(x) = erf(x)/2 - erf(x)/(4x^2) + exp(-x^2)/(2 sqrt(pi) x) (bracket of eq. dG)
-__device__ __forceinline__ float psi32(float x, float erfx, float ex) {
+// psi(x) = erf(x)/2 - erf(x)/(4x^2) + exp(-x^2)/(2 sqrt(pi) x) (bracket of
+// eq. dG); ix = 1/x
+__device__ __forceinline__ float psi32(float x, float ix, float erfx, float ex) {
     if (x < 0.5f) {
         // (2/sqrt(pi)) sum_m (-1)^m x^{2m+1} / (m! (2m+1)(2m+3)), m <= 6
         float x2 = x * x;
@@ -55,7 +57,7 @@ __device__ __forceinline__ float psi32(float x, float erfx, float ex) {
         p = fmaf(p, x2, 1.0f / 3.0f);                       // m = 0
         return 2.0f * ISQRTPI * x * p;
     }
-    return 0.5f * erfx - erfx / (4.0f * x * x) + 0.5f * ISQRTPI * ex / x;
+    return 0.5f * erfx - 0.25f * erfx * ix * ix + 0.5f * ISQRTPI * ex * ix;
 }
 
 // Blocks d = 0 and d = 1 of one quadrature point, without the factor of the
@@ -63,7 +65,7 @@ __device__ __forceinline__ float psi32(float x, float erfx, float ex) {
 __device__ __forceinline__ void k_d01(float rho, float irho, const MixConsts &g, float &v0,
                                       float &v1, float &k0, float &k1) {
     const float x1 = rho * g.c1, x2 = rho * g.c2;
-    const float ix1 = irho / g.c1, ix2 = irho / g.c2;
+    const float ix1 = irho * g.ic1, ix2 = irho * g.ic2;
     const float ec1 = erfcf(x1), ec2 = erfcf(x2);
     const float ee1 = expf(-x1 * x1), ee2 = expf(-x2 * x2);
     const float H1 = g.pV1 * ((x1 + 0.5f * ix1) * ec1 - ee1 * ISQRTPI);
@@ -75,7 +77,7 @@ __device__ __forceinline__ void k_d01(float rho, float irho, const MixConsts &g,
         const float Hh1 = g.pV1 * (x1 * ec1 - 0.5f * ef1 * ix1 - ee1 * ISQRTPI);
         const float Hh2 = g.pV2 * (x2 * ec2 - 0.5f * ef2 * ix2 - ee2 * ISQRTPI);
         v1 = Hh2 - 2.0f * Hh1;
-        k1 = -kf * (2.0f * psi32(x1, ef1, ee1) - psi32(x2, ef2, ee2) - 0.5f);
+        k1 = -kf * (2.0f * psi32(x1, ix1, ef1, ee1) - psi32(x2, ix2, ef2, ee2) - 0.5f);
     } else {
         const float H2 = g.pV2 * ((x2 + 0.5f * ix2) * ec2 - ee2 * ISQRTPI);
         v1 = H2 - 2.0f * H1;
@@ -616,6 +618,8 @@ static MixConsts mix_consts(const stb_params &p) {
     MixConsts g;
     g.c1 = (float)(1.0 / (2.0 * std::sqrt(al * h)));
     g.c2 = (float)(1.0 / (2.0 * std::sqrt(2.0 * al * h)));
+    g.ic1 = (float)(2.0 * std::sqrt(al * h));
+    g.ic2 = (float)(2.0 * std::sqrt(2.0 * al * h));
     g.pV1 = (float)(std::sqrt(h) / (4.0 * pi * std::pow(al, 1.5)));
     g.pV2 = (float)(std::sqrt(2.0 * h) / (4.0 * pi * std::pow(al, 1.5)));
     g.pK = (float)(1.0 / (4.0 * pi * al));

@@ -137,6 +137,7 @@ class BatchPipeline:
         shared = max(max(it["ws_project"], it["ws_rhs"], it["ws_error"]) for it in self.items)
         self.ws_shared = _ws(shared, dev)
         self.graphs = [None] * len(self.waves)
+        self.graph_launches = [0] * len(self.waves)  # library kernels per replay
         self.wave_state = [None] * len(self.waves)
 
     def _wave_buffers(self, w):
@@ -186,8 +187,10 @@ class BatchPipeline:
             r, _ = capi.stb_solve_report(self.items[i]["ws_solve"])
             p.flags = capi.STB_FLAG_NO_SYNC | capi.STB_FLAG_REFINE(max(1, r))
         g = torch.cuda.CUDAGraph()
+        n0 = capi.stb_launch_count()
         with torch.cuda.graph(g):
             self._enqueue(w, torch.cuda.current_stream())
+        self.graph_launches[w] = capi.stb_launch_count() - n0
         self.graphs[w] = g
 
     def run(self, stream=None):
