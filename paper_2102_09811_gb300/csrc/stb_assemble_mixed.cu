@@ -149,7 +149,7 @@ constexpr int MREG_THREADS = 128;
 constexpr int MAX_RULE_M = 256;
 
 // Intervals per pass over the quadrature points of a pair.
-constexpr int MIX_G = 4;
+constexpr int MIX_G = 8;
 
 // Node sums of MIX_G intervals (tables at tab, stride 4 + 4 NG floats) for one
 // quadrature point: E[g][.] += w e, F[g][.] += w (r.n_y) e, e = exp2(rr b), with

@@ -12,10 +12,10 @@
 // FP64 precision: everything in FP64.
 // Mixed precision: the factorisation and the march run in FP32 and are wrapped
 // in iterative refinement,  w <- w + march(f - V_h w),  whose residual is
-// formed with FP32-pair ("double-float") products and sums (exact FP32
-// products of the stored FP32 blocks with a two-float split of w, error-free
-// two-sums), so that no O(E^2 E_t^2) work runs on the scarce FP64 pipe.  The
-// refinement stops at ||f - V_h w|| <= 1e-10 ||f||.
+// updated as r <- r - V_h delta with FP32-pair ("double-float") products and
+// sums (exact FP32 products of the stored FP32 blocks with the FP32
+// correction delta, error-free two-sums), so that no O(E^2 E_t^2) work runs
+// on the scarce FP64 pipe.  The refinement stops at ||r|| <= 1e-10 ||f||.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -771,7 +771,11 @@ static stb_status solve_mixed(const float *V, int E, int n_steps, int nrhs, cons
         count_launch(s);
         k_update<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, S.delta, n);
         if ((st = check_launch("k_update"))) return st;
-        if ((st = toeplitz_df(V, E, n_steps, nrhs, w, DF_RESIDUAL, f, 0.0, S.r, S.df, s))) return st;
+        // r_it = r_{it-1} - V_h delta_it (r_{-1} = f): the FP32 correction is
+        // exact in the double-float product, which then needs no split of x
+        if ((st = toeplitz_df_f32x(V, E, n_steps, nrhs, S.delta, DF_RESIDUAL, it == 0 ? f : S.r,
+                                   0.0, S.r, S.df, s)))
+            return st;
         rhs = S.r;
         if (no_sync && it < max_refine) continue;  // fixed count: no norms until the end
         count_launch(s);

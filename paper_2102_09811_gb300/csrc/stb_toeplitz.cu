@@ -132,11 +132,12 @@ __global__ void k_split(const double *__restrict__ x, size_t n, float2 *__restri
 __device__ __forceinline__ float2 sub2(float2 u, float2 v) {
     return __ffma2_rn(v, make_float2(-1.f, -1.f), u);
 }
+template <bool SPLIT>
 __device__ __forceinline__ void df_acc2(float2 a, float2 xh, float2 nxh, float2 xl, float2 &hi,
                                         float2 &lo) {
     const float2 pn = __fmul2_rn(a, nxh);       // -p
     const float2 e = __ffma2_rn(a, xh, pn);      // a xh - p, exact
-    const float2 t = __ffma2_rn(a, xl, e);
+    const float2 t = SPLIT ? __ffma2_rn(a, xl, e) : e;  // x single-float: no low part
     const float2 s = sub2(hi, pn);               // hi + p
     const float2 bb = sub2(s, hi);
     const float2 c2 = sub2(hi, sub2(s, bb));     // hi - (s - bb)
@@ -152,11 +153,13 @@ __device__ __forceinline__ void df_acc2(float2 a, float2 xh, float2 nxh, float2 
 // x as (hi, hi, lo, lo) so that both operands of the packed ops load as is.
 // The (d, j) tiles are visited in one flat sequence and the next tile is
 // loaded into registers while the current one is being multiplied.  VEC:
-// E % 4 == 0 and A 16-byte aligned (rows loaded as float4).
-template <bool VEC>
+// E % 4 == 0 and A 16-byte aligned (rows loaded as float4).  SPLIT: x is a
+// two-float split xs of an FP64 vector; otherwise x is the FP32 vector xf.
+template <bool VEC, bool SPLIT>
 __global__ void __launch_bounds__(MV_THREADS)
 k_toeplitz_df_partial(const float *__restrict__ A, int E, int n_steps, int nrhs,
-                      const float2 *__restrict__ xs, double *__restrict__ part) {
+                      const float2 *__restrict__ xs, const float *__restrict__ xf,
+                      double *__restrict__ part) {
     __shared__ __align__(16) float As[TJ][TM + 4];
     __shared__ __align__(16) float4 Xs[TJ][TK];
     const int n_kt = (n_steps + TK - 1) / TK;
@@ -172,7 +175,8 @@ k_toeplitz_df_partial(const float *__restrict__ A, int E, int n_steps, int nrhs,
 #pragma unroll
     for (int i = 0; i < RPT / 2; ++i) hi[i] = lo[i] = make_float2(0.f, 0.f);
     const size_t EE = (size_t)E * E;
-    const float2 *xr = xs + (size_t)r * n_steps * E;
+    const float2 *xr = SPLIT ? xs + (size_t)r * n_steps * E : nullptr;
+    const float *xfr = SPLIT ? nullptr : xf + (size_t)r * n_steps * E;
     const int n_j = (E + TJ - 1) / TJ, n_it = (d1 - d0) * n_j;
 
     float4 ra[AV];
@@ -199,8 +203,11 @@ k_toeplitz_df_partial(const float *__restrict__ A, int E, int n_steps, int nrhs,
         for (int v = 0; v < XV; ++v) {
             const int t = threadIdx.x + v * MV_THREADS;
             const int jj = t / TK, c = t % TK, k = k0 + c, j = j0 + jj;
-            rx[v] = (k < n_steps && k - d >= 0 && j < E) ? xr[(size_t)(k - d) * E + j]
-                                                         : make_float2(0.f, 0.f);
+            const bool in = k < n_steps && k - d >= 0 && j < E;
+            if (SPLIT)
+                rx[v] = in ? xr[(size_t)(k - d) * E + j] : make_float2(0.f, 0.f);
+            else
+                rx[v] = make_float2(in ? xfr[(size_t)(k - d) * E + j] : 0.f, 0.f);
         }
     };
     auto store_tile = [&]() {
@@ -232,10 +239,10 @@ k_toeplitz_df_partial(const float *__restrict__ A, int E, int n_steps, int nrhs,
             const float2 nxh = make_float2(-xv.x, -xv.y);
             const float4 a0 = *reinterpret_cast<const float4 *>(&As[jj][ty * RPT]);
             const float4 a1 = *reinterpret_cast<const float4 *>(&As[jj][ty * RPT + 4]);
-            df_acc2(make_float2(a0.x, a0.y), xh, nxh, xl, hi[0], lo[0]);
-            df_acc2(make_float2(a0.z, a0.w), xh, nxh, xl, hi[1], lo[1]);
-            df_acc2(make_float2(a1.x, a1.y), xh, nxh, xl, hi[2], lo[2]);
-            df_acc2(make_float2(a1.z, a1.w), xh, nxh, xl, hi[3], lo[3]);
+            df_acc2<SPLIT>(make_float2(a0.x, a0.y), xh, nxh, xl, hi[0], lo[0]);
+            df_acc2<SPLIT>(make_float2(a0.z, a0.w), xh, nxh, xl, hi[1], lo[1]);
+            df_acc2<SPLIT>(make_float2(a1.x, a1.y), xh, nxh, xl, hi[2], lo[2]);
+            df_acc2<SPLIT>(make_float2(a1.z, a1.w), xh, nxh, xl, hi[3], lo[3]);
         }
         __syncthreads();
     }
@@ -269,29 +276,44 @@ size_t toeplitz_df_bytes(int64_t E, int32_t n_steps, int32_t nrhs) {
     return df_partial_bytes(E, n_steps, nrhs) + align256((size_t)nrhs * n_steps * E * sizeof(float2));
 }
 
-stb_status toeplitz_df(const float *A, int64_t E, int32_t n_steps, int32_t nrhs, const double *x,
-                       int mode, const double *f, double beta, double *y, void *scratch,
-                       cudaStream_t s) {
+static stb_status toeplitz_df_run(const float *A, int64_t E, int32_t n_steps, int32_t nrhs,
+                                  const double *x, const float *xf, int mode, const double *f,
+                                  double beta, double *y, void *scratch, cudaStream_t s) {
     double *part = static_cast<double *>(scratch);
     float2 *xs = reinterpret_cast<float2 *>(static_cast<char *>(scratch) +
                                             df_partial_bytes(E, n_steps, nrhs));
     const size_t total = (size_t)nrhs * n_steps * E;
-    count_launch(s);
-    k_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(x, total, xs);
-    stb_status st = check_launch("k_split");
-    if (st) return st;
+    stb_status st;
+    if (x) {
+        count_launch(s);
+        k_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(x, total, xs);
+        if ((st = check_launch("k_split"))) return st;
+    }
     int n_kt = (n_steps + TK - 1) / TK, n_dr = (n_steps + DF_TD - 1) / DF_TD;
     dim3 grid((unsigned)((E + TM - 1) / TM), (unsigned)(n_kt * nrhs), (unsigned)n_dr);
+    const bool vec = E % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
+    const auto kern = x ? (vec ? k_toeplitz_df_partial<true, true> : k_toeplitz_df_partial<false, true>)
+                        : (vec ? k_toeplitz_df_partial<true, false>
+                               : k_toeplitz_df_partial<false, false>);
     count_launch(s);
-    if (E % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0)
-        k_toeplitz_df_partial<true><<<grid, MV_THREADS, 0, s>>>(A, (int)E, n_steps, nrhs, xs, part);
-    else
-        k_toeplitz_df_partial<false><<<grid, MV_THREADS, 0, s>>>(A, (int)E, n_steps, nrhs, xs, part);
+    kern<<<grid, MV_THREADS, 0, s>>>(A, (int)E, n_steps, nrhs, xs, xf, part);
     if ((st = check_launch("k_toeplitz_df_partial"))) return st;
     count_launch(s);
     k_toeplitz_df_reduce<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, (int)E, n_steps, nrhs,
                                                                          mode, f, beta, y);
     return check_launch("k_toeplitz_df_reduce");
+}
+
+stb_status toeplitz_df(const float *A, int64_t E, int32_t n_steps, int32_t nrhs, const double *x,
+                       int mode, const double *f, double beta, double *y, void *scratch,
+                       cudaStream_t s) {
+    return toeplitz_df_run(A, E, n_steps, nrhs, x, nullptr, mode, f, beta, y, scratch, s);
+}
+
+stb_status toeplitz_df_f32x(const float *A, int64_t E, int32_t n_steps, int32_t nrhs,
+                            const float *x, int mode, const double *f, double beta, double *y,
+                            void *scratch, cudaStream_t s) {
+    return toeplitz_df_run(A, E, n_steps, nrhs, nullptr, x, mode, f, beta, y, scratch, s);
 }
 
 // Scratch of stb_toeplitz_matvec_static: every device that loads the library

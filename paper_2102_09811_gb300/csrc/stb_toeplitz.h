@@ -18,4 +18,9 @@ size_t toeplitz_df_bytes(int64_t E, int32_t n_steps, int32_t nrhs);
 stb_status toeplitz_df(const float *A, int64_t E, int32_t n_steps, int32_t nrhs, const double *x,
                        int mode, const double *f, double beta, double *y, void *scratch,
                        cudaStream_t s);
+// The same with an FP32 vector x (exactly representable: no low part);
+// f may alias y in mode DF_RESIDUAL.
+stb_status toeplitz_df_f32x(const float *A, int64_t E, int32_t n_steps, int32_t nrhs,
+                            const float *x, int mode, const double *f, double beta, double *y,
+                            void *scratch, cudaStream_t s);
 }  // namespace stb
