@@ -73,6 +73,12 @@ def lib():
         L.orc_dirichlet_solve.argtypes = [_P, _I64, _I32, _I32, _P, _P]
         L.orc_neumann_error.argtypes = [_P, _I64, _P, _I64, _D, _D, _I32, _P,
                                         _I32, _I32, _P, _I32, _I32, _P, _P]
+        L.orc_assemble_k1_rows.argtypes = [_P, _I64, _P, _I64, _D, _D, _I32, _I32,
+                                           _I32, _P, _I64, _P]
+        L.orc_project_dirichlet_p1.argtypes = [_P, _I64, _P, _I64, _D, _D, _I32,
+                                               _P, _I32, _I32, _I32, _I32, _P]
+        L.orc_toeplitz_matvec_rect.argtypes = [_P, _I64, _I64, _I32, _I32, _P, _P]
+        L.orc_dirichlet_rhs_p1.argtypes = [_P, _P, _P, _I64, _I64, _D, _I32, _I32, _P, _P]
         _lib = L
     return _lib
 
@@ -282,3 +288,57 @@ def neumann_error(nodes, tris, alpha, T, n_steps, sources, w, q_space=8, n_time=
                                    _p(w), q_space, n_time, ctypes.byref(e2),
                                    ctypes.byref(r2)), "neumann_error")
     return e2.value, r2.value
+
+
+# ---- piecewise-linear trial space in space (Sec. 3.2, Sec. 3.4) --------------
+def assemble_k1_rows(nodes, tris, alpha, T, n_steps, rows, q_reg=3, m_ss=4):
+    """Rows of the blocks of K_h with nodal hat trial functions:
+    [n_rows, n_steps, n_nodes]."""
+    nodes, tris = _f64(nodes), _i32(tris)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    K1 = np.zeros((rows.shape[0], n_steps, nodes.shape[0]))
+    _check(lib().orc_assemble_k1_rows(_p(nodes), nodes.shape[0], _p(tris), tris.shape[0], alpha,
+                                      T, n_steps, q_reg, m_ss, _p(rows), rows.shape[0], _p(K1)),
+           "assemble_k1_rows")
+    return K1
+
+
+def assemble_k1(nodes, tris, alpha, T, n_steps, q_reg=3, m_ss=4):
+    """All blocks of K_h (piecewise-linear trial): [n_steps, E, n_nodes]."""
+    E = np.asarray(tris).shape[0]
+    K1 = assemble_k1_rows(nodes, tris, alpha, T, n_steps, np.arange(E), q_reg, m_ss)
+    return np.ascontiguousarray(K1.transpose(1, 0, 2))
+
+
+def project_dirichlet_p1(nodes, tris, alpha, T, n_steps, sources, q_space=8, n_time=16):
+    """L2 projection of the Dirichlet datum into X_h^{1,0}: [nrhs, n_steps, n_nodes]."""
+    nodes, tris, src = _f64(nodes), _i32(tris), _f64(sources)
+    nrhs, n_src = src.shape[0], src.shape[1]
+    g1 = np.zeros((nrhs, n_steps, nodes.shape[0]))
+    rc = lib().orc_project_dirichlet_p1(_p(nodes), nodes.shape[0], _p(tris), tris.shape[0],
+                                        alpha, T, n_steps, _p(src), n_src, nrhs, q_space,
+                                        n_time, _p(g1))
+    if rc == -5:
+        raise np.linalg.LinAlgError("p1 mass matrix is not positive definite")
+    _check(rc, "project_dirichlet_p1")
+    return g1
+
+
+def toeplitz_matvec_rect(A, x):
+    """A [n_steps, E, N], x [nrhs, n_steps, N] -> y [nrhs, n_steps, E]."""
+    A, x = _f64(A), _f64(x)
+    n_steps, E, N = A.shape
+    y = np.zeros((x.shape[0], n_steps, E))
+    _check(lib().orc_toeplitz_matvec_rect(_p(A), E, N, n_steps, x.shape[0], _p(x), _p(y)),
+           "toeplitz_matvec_rect")
+    return y
+
+
+def dirichlet_rhs_p1(area, tris, K1, g1, T):
+    """(1/2 M_h + K_h) g1 with the p0 x p1 mass: [nrhs, n_steps, E]."""
+    area, tris, K1, g1 = _f64(area), _i32(tris), _f64(K1), _f64(g1)
+    n_steps, E, N = K1.shape
+    f = np.zeros((g1.shape[0], n_steps, E))
+    _check(lib().orc_dirichlet_rhs_p1(_p(area), _p(tris), _p(K1), E, N, T, n_steps,
+                                      g1.shape[0], _p(g1), _p(f)), "dirichlet_rhs_p1")
+    return f

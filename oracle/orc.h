@@ -108,6 +108,26 @@ int orc_neumann_error(const double *nodes, int64_t n_nodes,
                       int32_t nrhs, const double *w, int32_t q_space,
                       int32_t n_time, double *err2, double *ref2);
 
+/* ---- piecewise-linear trial space in space (Sec. 3.2, Sec. 3.4) -----------
+ * K1 [n_rows][n_steps][n_nodes]: rows of the blocks of K_h with the trial
+ * functions phi_i (nodal hat functions); g1 [nrhs][n_steps][n_nodes]: the
+ * L2(Sigma_h) projection of the Dirichlet datum into X_h^{1,0}; the
+ * right-hand side (1/2 M_h + K_h) g1 with the p0 x p1 mass matrix.           */
+int orc_assemble_k1_rows(const double *nodes, int64_t n_nodes,
+                         const int32_t *tris, int64_t E, double alpha, double T,
+                         int32_t n_steps, int32_t q_reg, int32_t m_ss,
+                         const int64_t *rows, int64_t n_rows, double *K1);
+int orc_project_dirichlet_p1(const double *nodes, int64_t n_nodes,
+                             const int32_t *tris, int64_t E, double alpha,
+                             double T, int32_t n_steps, const double *sources,
+                             int32_t n_src, int32_t nrhs, int32_t q_space,
+                             int32_t n_time, double *g1);
+int orc_toeplitz_matvec_rect(const double *A, int64_t E, int64_t N, int32_t n_steps,
+                             int32_t nrhs, const double *x, double *y);
+int orc_dirichlet_rhs_p1(const double *area, const int32_t *tris, const double *K1,
+                         int64_t E, int64_t N, double T, int32_t n_steps, int32_t nrhs,
+                         const double *g1, double *f);
+
 #ifdef __cplusplus
 }
 #endif

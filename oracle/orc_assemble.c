@@ -112,6 +112,10 @@ typedef struct {
     int n;
     double *rho, *rn, *w;
     int cls;
+    /* optional (lam[0] != NULL): barycentric coordinates of y in the trial
+     * triangle and the nodes they belong to (piecewise linear trial space) */
+    double *lam[3];
+    int32_t node[3];
 } pair_points;
 
 typedef struct {
@@ -185,8 +189,15 @@ static void pair_points_build(const rules *R, const double *nodes,
                 pp->rho[k] = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
                 pp->rn[k] = r0 * n[0] + r1 * n[1] + r2 * n[2];
                 pp->w[k] = scale * R->rw[a] * R->rw[b];
+                if (pp->lam[0]) { /* chi = (1-s1) P0 + (s1-s2) P1 + s2 P2 */
+                    pp->lam[0][k] = 1.0 - R->rs1[b];
+                    pp->lam[1][k] = R->rs1[b] - R->rs2[b];
+                    pp->lam[2][k] = R->rs2[b];
+                }
                 ++k;
             }
+        for (int c = 0; c < 3; ++c)
+            pp->node[c] = tj[c];
     } else {
         const double *Pa[3], *Pb[3];
         for (int c = 0; c < 3; ++c) {
@@ -206,8 +217,16 @@ static void pair_points_build(const rules *R, const double *nodes,
             pp->rho[k] = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
             pp->rn[k] = r0 * n[0] + r1 * n[1] + r2 * n[2];
             pp->w[k] = scale * t[4][q];
+            if (pp->lam[0]) { /* y on b (coordinates t2, t3) when l = a, else on a */
+                double u1 = l == ia ? t[2][q] : t[0][q], u2 = l == ia ? t[3][q] : t[1][q];
+                pp->lam[0][k] = 1.0 - u1;
+                pp->lam[1][k] = u1 - u2;
+                pp->lam[2][k] = u2;
+            }
             ++k;
         }
+        for (int c = 0; c < 3; ++c)
+            pp->node[c] = l == ia ? tb[ob[c]] : ta[oa[c]];
     }
     pp->n = k;
 }
@@ -231,6 +250,23 @@ static void level_sums(const pair_points *pp, int level, double h,
     }
     *sv = v;
     *sk = pp->cls == ORC_IDENTICAL ? 0.0 : k;
+}
+
+/* K sums of one pair at one level weighted by the trial triangle's
+ * barycentric coordinates: sk[v] = sum_q w_q lam_v(y_q) alpha dG/dn_y(...). */
+static void level_sums_k1(const pair_points *pp, int level, double h,
+                          double alpha, double *sk)
+{
+    double delta = level < 0 ? 0.0 : level * h;
+    sk[0] = sk[1] = sk[2] = 0.0;
+    if (pp->cls == ORC_IDENTICAL)
+        return;
+    for (int q = 0; q < pp->n; ++q) {
+        double k = level < 0 ? orc_dn_G_dtau(pp->rn[q], pp->rho[q], 0.0, alpha)
+                             : orc_dn_G_dtau_dt(pp->rn[q], pp->rho[q], delta, alpha);
+        for (int v = 0; v < 3; ++v)
+            sk[v] += pp->w[q] * pp->lam[v][q] * k;
+    }
 }
 
 static int geometry_alloc(const double *nodes, int64_t n_nodes,
@@ -260,6 +296,7 @@ int orc_pair_sums(const double *nodes, int64_t n_nodes, const int32_t *tris,
         if (R.nss[c] > nmax)
             nmax = R.nss[c];
     pair_points pp;
+    memset(&pp, 0, sizeof pp);
     pp.rho = malloc(sizeof(double) * nmax);
     pp.rn = malloc(sizeof(double) * nmax);
     pp.w = malloc(sizeof(double) * nmax);
@@ -321,6 +358,7 @@ int orc_assemble_rows(const double *nodes, int64_t n_nodes,
         if (R.nss[c] > nmax)
             nmax = R.nss[c];
     pair_points pp;
+    memset(&pp, 0, sizeof pp);
     pp.rho = malloc(sizeof(double) * nmax);
     pp.rn = malloc(sizeof(double) * nmax);
     pp.w = malloc(sizeof(double) * nmax);
@@ -357,6 +395,72 @@ int orc_assemble_rows(const double *nodes, int64_t n_nodes,
     free(pp.rho);
     free(pp.rn);
     free(pp.w);
+    rc = 0;
+done:
+    rules_free(&R);
+    free(area);
+    free(normal);
+    return rc;
+}
+
+/* Rows of all blocks of K_h with the piecewise-linear trial space of Sec. 3.2
+ * (the paper's discretisation of the double layer): K1^d[l][i] =
+ * int_{gamma_l} int_{Gamma_h} phi_i(y) K^d(x - y), i over the mesh nodes, as
+ * second differences of the level sums (Table deltad, eq. K_d / eq. K0).
+ * K1: [n_rows][n_steps][n_nodes]. */
+int orc_assemble_k1_rows(const double *nodes, int64_t n_nodes,
+                         const int32_t *tris, int64_t E, double alpha, double T,
+                         int32_t n_steps, int32_t q_reg, int32_t m_ss,
+                         const int64_t *rows, int64_t n_rows, double *K1)
+{
+    if (E < 1 || n_nodes < 3 || n_steps < 1 || !(alpha > 0.0) || !(T > 0.0) || n_rows < 0)
+        return -1;
+    for (int64_t r = 0; r < n_rows; ++r)
+        if (rows[r] < 0 || rows[r] >= E)
+            return -1;
+    rules R;
+    double *area = NULL, *normal = NULL;
+    int rc = -1;
+    if (rules_init(&R, q_reg, m_ss))
+        goto done;
+    if (geometry_alloc(nodes, n_nodes, tris, E, &area, &normal))
+        goto done;
+    double h = T / n_steps;
+    memset(K1, 0, sizeof(double) * n_rows * n_steps * n_nodes);
+    int nmax = R.nreg * R.nreg;
+    for (int c = 1; c <= 3; ++c)
+        if (R.nss[c] > nmax)
+            nmax = R.nss[c];
+    pair_points pp;
+    memset(&pp, 0, sizeof pp);
+    pp.rho = malloc(sizeof(double) * nmax);
+    pp.rn = malloc(sizeof(double) * nmax);
+    pp.w = malloc(sizeof(double) * nmax);
+    for (int v = 0; v < 3; ++v)
+        pp.lam[v] = malloc(sizeof(double) * nmax);
+    for (int i_t = 0; i_t <= n_steps; ++i_t) {
+        for (int64_t r = 0; r < n_rows; ++r) {
+            int64_t l = rows[r];
+            double *Kr = K1 + r * (int64_t)n_steps * n_nodes;
+            for (int64_t j = 0; j < E; ++j) {
+                pair_points_build(&R, nodes, tris, area, normal, l, j, &pp);
+                double sk[3];
+                level_sums_k1(&pp, i_t, h, alpha, sk);
+                for (int v = 0; v < 3; ++v)
+                    scatter(Kr, n_nodes, n_steps, i_t, pp.node[v], sk[v]);
+                if (i_t == 0) { /* eq. K0: the h dG^{dtau}/dn(., 0) term of block 0 */
+                    level_sums_k1(&pp, -1, h, alpha, sk);
+                    for (int v = 0; v < 3; ++v)
+                        Kr[pp.node[v]] += h * sk[v];
+                }
+            }
+        }
+    }
+    free(pp.rho);
+    free(pp.rn);
+    free(pp.w);
+    for (int v = 0; v < 3; ++v)
+        free(pp.lam[v]);
     rc = 0;
 done:
     rules_free(&R);

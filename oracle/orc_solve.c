@@ -296,3 +296,153 @@ done:
     free(normal);
     return rc;
 }
+
+/* ---- piecewise-linear Dirichlet data (Sec. 3.2, Sec. 3.4) ------------------ */
+
+/* Dense Cholesky of the SPD matrix A (n x n, overwritten by L, lower part);
+ * -5 if a pivot is not positive. */
+static int cholesky(double *A, int64_t n)
+{
+    for (int64_t c = 0; c < n; ++c) {
+        double s = A[c * n + c];
+        for (int64_t k = 0; k < c; ++k)
+            s -= A[c * n + k] * A[c * n + k];
+        if (!(s > 0.0))
+            return -5;
+        double lcc = sqrt(s);
+        A[c * n + c] = lcc;
+        for (int64_t i = c + 1; i < n; ++i) {
+            double t = A[i * n + c];
+            for (int64_t k = 0; k < c; ++k)
+                t -= A[i * n + k] * A[c * n + k];
+            A[i * n + c] = t / lcc;
+        }
+    }
+    return 0;
+}
+
+static void cholesky_solve(const double *L, int64_t n, double *x)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double t = x[i];
+        for (int64_t k = 0; k < i; ++k)
+            t -= L[i * n + k] * x[k];
+        x[i] = t / L[i * n + i];
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double t = x[i];
+        for (int64_t k = i + 1; k < n; ++k)
+            t -= L[k * n + i] * x[k];
+        x[i] = t / L[i * n + i];
+    }
+}
+
+/* L2(Sigma_h) projection of g into X_h^{1,0} (piecewise linear in space,
+ * piecewise constant in time): per step k the nodal vector g1^k solves
+ *   M1 g1^k = b^k,  M1[i][m] = int_Gamma phi_i phi_m,
+ *   b^k[i] = h^{-1} int_{t_k}^{t_{k+1}} int_Gamma g phi_i,
+ * M1 from its exact element values Delta/12 (1 + delta_im), b^k by the
+ * q_space conical rule and n_time Gauss points per step.
+ * g1: [nrhs][n_steps][n_nodes]. */
+int orc_project_dirichlet_p1(const double *nodes, int64_t n_nodes,
+                             const int32_t *tris, int64_t E, double alpha,
+                             double T, int32_t n_steps, const double *sources,
+                             int32_t n_src, int32_t nrhs, int32_t q_space,
+                             int32_t n_time, double *g1)
+{
+    if (E < 1 || n_nodes < 3 || n_steps < 1 || nrhs < 1 || n_src < 1 || q_space < 1 ||
+        q_space > 32 || n_time < 1 || n_time > 64)
+        return -1;
+    int nq = q_space * q_space;
+    double *s1 = malloc(sizeof(double) * nq), *s2 = malloc(sizeof(double) * nq);
+    double *sw = malloc(sizeof(double) * nq), tx[64], tw[64];
+    double *area = malloc(sizeof(double) * E), *normal = malloc(sizeof(double) * 3 * E);
+    double *M = calloc((size_t)n_nodes * n_nodes, sizeof(double));
+    int rc = -1;
+    if (orc_triangle_rule(q_space, s1, s2, sw) || orc_gauss_legendre01(n_time, tx, tw) ||
+        orc_triangle_geometry(nodes, n_nodes, tris, E, area, normal))
+        goto done;
+    for (int64_t j = 0; j < E; ++j)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                M[(int64_t)tris[3 * j + a] * n_nodes + tris[3 * j + b]] +=
+                    area[j] / 12.0 * (a == b ? 2.0 : 1.0);
+    if ((rc = cholesky(M, n_nodes)) != 0)
+        goto done;
+    rc = -1;
+    double h = T / n_steps;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k) {
+            double *bk = g1 + ((int64_t)r * n_steps + k) * n_nodes;
+            memset(bk, 0, sizeof(double) * n_nodes);
+            for (int64_t j = 0; j < E; ++j) {
+                const int32_t *t3 = tris + 3 * j;
+                for (int a = 0; a < nq; ++a) {
+                    double x[3], lam[3] = {1.0 - s1[a], s1[a] - s2[a], s2[a]};
+                    chi_plain(nodes + 3 * t3[0], nodes + 3 * t3[1], nodes + 3 * t3[2],
+                              s1[a], s2[a], x);
+                    double acc = 0.0;
+                    for (int b = 0; b < n_time; ++b)
+                        acc += tw[b] * dirichlet_datum(sources + (int64_t)r * n_src * 5, n_src,
+                                                       alpha, x, (k + tx[b]) * h);
+                    /* (2 Delta sw) in space, (h tw) / h in time */
+                    for (int v = 0; v < 3; ++v)
+                        bk[t3[v]] += 2.0 * area[j] * sw[a] * lam[v] * acc;
+                }
+            }
+            cholesky_solve(M, n_nodes, bk);
+        }
+    rc = 0;
+done:
+    free(s1);
+    free(s2);
+    free(sw);
+    free(area);
+    free(normal);
+    free(M);
+    return rc;
+}
+
+/* y_r^k = sum_{d=0}^{k} A^d x_r^{k-d} with rectangular blocks A^d [E][N]:
+ * A [n_steps][E][N], x [nrhs][n_steps][N], y [nrhs][n_steps][E]. */
+int orc_toeplitz_matvec_rect(const double *A, int64_t E, int64_t N, int32_t n_steps,
+                             int32_t nrhs, const double *x, double *y)
+{
+    if (E < 1 || N < 1 || n_steps < 1 || nrhs < 1)
+        return -1;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k)
+            for (int64_t l = 0; l < E; ++l) {
+                double acc = 0.0;
+                for (int d = 0; d <= k; ++d) {
+                    const double *Arow = A + ((int64_t)d * E + l) * N;
+                    const double *xv = x + ((int64_t)r * n_steps + (k - d)) * N;
+                    for (int64_t i = 0; i < N; ++i)
+                        acc += Arow[i] * xv[i];
+                }
+                y[((int64_t)r * n_steps + k) * E + l] = acc;
+            }
+    return 0;
+}
+
+/* f = (1/2 M_h + K_h) g1 with the p0 x p1 mass M_h = h blockdiag(M01),
+ * M01[l][i] = int_{gamma_l} phi_i = Delta_l / 3 for the nodes i of l
+ * (Sec. 3.4), and K_h the piecewise-linear double layer K1 [n_steps][E][N]. */
+int orc_dirichlet_rhs_p1(const double *area, const int32_t *tris, const double *K1,
+                         int64_t E, int64_t N, double T, int32_t n_steps, int32_t nrhs,
+                         const double *g1, double *f)
+{
+    if (orc_toeplitz_matvec_rect(K1, E, N, n_steps, nrhs, g1, f))
+        return -1;
+    double h = T / n_steps;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k)
+            for (int64_t l = 0; l < E; ++l) {
+                const double *gk = g1 + ((int64_t)r * n_steps + k) * N;
+                double m = 0.0;
+                for (int v = 0; v < 3; ++v)
+                    m += gk[tris[3 * l + v]];
+                f[((int64_t)r * n_steps + k) * E + l] += 0.5 * h * area[l] / 3.0 * m;
+            }
+    return 0;
+}
