@@ -177,6 +177,24 @@ stb_status stb_batch_launch(const stb_batch_item *items, int32_t n, int32_t tile
 stb_status stb_batch_tune(const stb_batch_item *items, int32_t n, void *workspace,
                           size_t workspace_bytes, stb_stream stream, int32_t *tile);
 
+/* ---- double layer with piecewise-linear trial functions (Sec. 3.2) -------------
+ * K1: device [n_steps][E][n_nodes] of params->storage (the caller's buffer,
+ * overwritten).  K1^d[l][i] is the block-d entry of K_h between the constant
+ * test function of triangle l and the nodal hat function phi_i of X_h^{1,0}
+ * (continuous, piecewise linear in space): the K integrand of stb_assemble
+ * weighted by the barycentric coordinate of node i at the trial point, by the
+ * same rules (regular Gauss for separated pairs, the regularised rules for
+ * touching pairs; identical pairs give zero since r . n_y = 0) and the same
+ * second differences in time (eq. K0, eq. K_d).  Needs STB_PREC_FP64.  The
+ * contributions of the triangles around node i are added with atomics, so
+ * two runs may differ in the last bits.  Workspace from
+ * stb_assemble_k1_workspace_size; the device status word reports as for
+ * stb_assemble. */
+stb_status stb_assemble_k1_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                          size_t *bytes);
+stb_status stb_assemble_k1(const stb_mesh *mesh, const stb_params *params, void *K1,
+                           void *workspace, size_t workspace_bytes, stb_stream stream);
+
 /* ---- Dirichlet data (Sec. 3.4, Sec. 6.1) --------------------------------------
  * sources: HOST array [nrhs][n_src][5] of (y1, y2, y3, t0, weight); right-hand
  * side r has the Dirichlet datum g_r(x,t) = sum_s weight_s G_alpha(x - y_s, t - t0_s)
@@ -190,6 +208,35 @@ stb_status stb_project_dirichlet(const stb_mesh *mesh, const stb_params *params,
                                  const double *sources, int32_t nrhs, int32_t n_src,
                                  int32_t q_space, int32_t n_time, double *g, void *workspace,
                                  size_t workspace_bytes, stb_stream stream);
+
+/* ---- piecewise-linear Dirichlet data (Sec. 3.4) ---------------------------------
+ * g1 (device FP64 [nrhs][n_steps][n_nodes]) receives the L2(Sigma_h)
+ * projection of g_r (sources as for stb_project_dirichlet) into
+ * X_h^{1,0} x (piecewise constants in time): per step k, M1 g1^k = b^k with
+ * the hat-function mass matrix M1[i][i'] = sum over the triangles j holding
+ * both nodes of Delta_j (1 + [i = i']) / 12 and the moments
+ * b^k_i = h^{-1} int_{t_k}^{t_{k+1}} int_Gamma g_r phi_i (q_space x q_space
+ * conical rule, n_time Gauss points; FP64, or FP32 moments with
+ * STB_PREC_MIXED).  M1 is inverted densely in FP64 (n_nodes <= 65535; every
+ * node must belong to a triangle, else STB_ERR_INVALID_ARG).  The moments
+ * are added with atomics (last bits may differ between runs). */
+stb_status stb_project_p1_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                         int32_t nrhs, int32_t n_src, int32_t q_space,
+                                         int32_t n_time, size_t *bytes);
+stb_status stb_project_dirichlet_p1(const stb_mesh *mesh, const stb_params *params,
+                                    const double *sources, int32_t nrhs, int32_t n_src,
+                                    int32_t q_space, int32_t n_time, double *g1, void *workspace,
+                                    size_t workspace_bytes, stb_stream stream);
+/* f (device FP64 [nrhs][n_steps][E], overwritten) = (1/2 M_h + K_h) g1 with
+ * piecewise-linear data: K_h = K1 of stb_assemble_k1 (params->storage) as a
+ * block-Toeplitz product with E x n_nodes blocks, and the p0 x p1 mass
+ * M_h = h blockdiag(M01), M01[l][i] = int_{gamma_l} phi_i = Delta_l / 3 for
+ * the three nodes i of triangle l.  FP64 arithmetic for either storage. */
+stb_status stb_rhs_p1_workspace_size(const stb_mesh *mesh, const stb_params *params, int32_t nrhs,
+                                     size_t *bytes);
+stb_status stb_dirichlet_rhs_p1(const stb_mesh *mesh, const stb_params *params, const void *K1,
+                                const double *g1, int32_t nrhs, double *f, void *workspace,
+                                size_t workspace_bytes, stb_stream stream);
 
 /* ---- block-Toeplitz matrix-vector product (eq. V_mat) ---------------------------
  *   y_r^k = beta y_r^k + sum_{d=0}^{k} A^d x_r^{k-d},  k = 0..n_steps-1,

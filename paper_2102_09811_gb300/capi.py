@@ -62,7 +62,13 @@ _SIGS = {
     "stb_mesh_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "stb_assemble_workspace_size": (_I32, [_P, _PAR, _PSZ]),
     "stb_assemble": (_I32, [_P, _PAR, _P, _P, _P, _SZ, _P]),
+    "stb_assemble_k1_workspace_size": (_I32, [_P, _PAR, _PSZ]),
+    "stb_assemble_k1": (_I32, [_P, _PAR, _P, _P, _SZ, _P]),
     "stb_project_workspace_size": (_I32, [_P, _I32, _I32, _I32, _I32, _PSZ]),
+    "stb_project_p1_workspace_size": (_I32, [_P, _PAR, _I32, _I32, _I32, _I32, _PSZ]),
+    "stb_project_dirichlet_p1": (_I32, [_P, _PAR, _P, _I32, _I32, _I32, _I32, _P, _P, _SZ, _P]),
+    "stb_rhs_p1_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
+    "stb_dirichlet_rhs_p1": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
     "stb_project_dirichlet": (_I32, [_P, _PAR, _P, _I32, _I32, _I32, _I32, _P, _P, _SZ, _P]),
     "stb_toeplitz_workspace_size": (_I32, [_I64, _I32, _I32, _PSZ]),
     "stb_toeplitz_matvec": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _D, _P, _P, _SZ, _P]),
@@ -208,6 +214,16 @@ def stb_assemble(mesh, params, V, K, workspace, stream=None):
                                    _stream(stream)), "stb_assemble")
 
 
+def stb_assemble_k1_workspace_size(mesh, params):
+    return _size(_library().stb_assemble_k1_workspace_size, mesh.handle, ctypes.byref(params))
+
+
+def stb_assemble_k1(mesh, params, K1, workspace, stream=None):
+    _check(_library().stb_assemble_k1(mesh.handle, ctypes.byref(params), _ptr(K1), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(),
+                                      _stream(stream)), "stb_assemble_k1")
+
+
 def stb_project_workspace_size(mesh, nrhs, n_src, q_space=8, n_time=16):
     return _size(_library().stb_project_workspace_size, mesh.handle, nrhs, n_src, q_space, n_time)
 
@@ -219,6 +235,32 @@ def stb_project_dirichlet(mesh, params, sources, g, workspace, q_space=8, n_time
                                             q_space, n_time, _ptr(g), _ptr(workspace),
                                             workspace.numel() * workspace.element_size(),
                                             _stream(stream)), "stb_project_dirichlet")
+
+
+def stb_project_p1_workspace_size(mesh, params, nrhs, n_src, q_space=8, n_time=16):
+    return _size(_library().stb_project_p1_workspace_size, mesh.handle, ctypes.byref(params), nrhs,
+                 n_src, q_space, n_time)
+
+
+def stb_project_dirichlet_p1(mesh, params, sources, g1, workspace, q_space=8, n_time=16,
+                             stream=None):
+    src, sp = _host_f64(sources)
+    nrhs, n_src = src.shape[0], src.shape[1]
+    _check(_library().stb_project_dirichlet_p1(mesh.handle, ctypes.byref(params), sp, nrhs, n_src,
+                                               q_space, n_time, _ptr(g1), _ptr(workspace),
+                                               workspace.numel() * workspace.element_size(),
+                                               _stream(stream)), "stb_project_dirichlet_p1")
+
+
+def stb_rhs_p1_workspace_size(mesh, params, nrhs):
+    return _size(_library().stb_rhs_p1_workspace_size, mesh.handle, ctypes.byref(params), nrhs)
+
+
+def stb_dirichlet_rhs_p1(mesh, params, K1, g1, nrhs, f, workspace, stream=None):
+    _check(_library().stb_dirichlet_rhs_p1(mesh.handle, ctypes.byref(params), _ptr(K1), _ptr(g1),
+                                           nrhs, _ptr(f), _ptr(workspace),
+                                           workspace.numel() * workspace.element_size(),
+                                           _stream(stream)), "stb_dirichlet_rhs_p1")
 
 
 def stb_toeplitz_workspace_size(E, n_steps, nrhs):

@@ -554,6 +554,265 @@ static Globals make_globals(const stb_params &p) {
     return g;
 }
 
+// ---------------------------------------- piecewise-linear trial space ---
+// K_h with nodal hat trial functions (Sec. 3.2): the K sums of a pair
+// weighted by the barycentric coordinates of the trial point, their second
+// differences per vertex, added to K1[d][l][node] (several trial triangles
+// share a node, so the blocks are accumulated with atomics and must start
+// at zero).
+__device__ __forceinline__ void atomic_add_out(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_out(float *p, double v) { atomicAdd(p, (float)v); }
+
+template <int CH, class OutT>
+__global__ void __launch_bounds__(REG_THREADS)
+k_regular_k1_f64(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E, int N,
+                 const double *__restrict__ rule, int nq, const double *__restrict__ levels,
+                 int n_steps, Globals g, OutT *__restrict__ K1) {
+    extern __shared__ double sm[];
+    double *xa = sm;                   // [nq][4]: x_a (3) and w_a
+    double *lv = sm + 4 * MAX_RULE;    // [n_steps+1][LV_STRIDE]
+    const int l = blockIdx.y;
+    const int j = blockIdx.x * REG_THREADS + threadIdx.x;
+    const double *gl = geo + (size_t)l * GEO_STRIDE;
+    for (int a = threadIdx.x; a < nq; a += REG_THREADS) {
+        double s1 = rule[3 * a], s2 = rule[3 * a + 1];
+        for (int c = 0; c < 3; ++c)
+            xa[4 * a + c] = gl[GEO_V0 + c] + s1 * (gl[GEO_V1 + c] - gl[GEO_V0 + c]) +
+                            s2 * (gl[GEO_V2 + c] - gl[GEO_V1 + c]);
+        xa[4 * a + 3] = rule[3 * a + 2];
+    }
+    for (int i = threadIdx.x; i < (n_steps + 1) * LV_STRIDE; i += REG_THREADS) lv[i] = levels[i];
+    __syncthreads();
+    if (j >= E) return;
+    const int32_t tl[3] = {tris[3 * l], tris[3 * l + 1], tris[3 * l + 2]};
+    const int32_t tj[3] = {tris[3 * j], tris[3 * j + 1], tris[3 * j + 2]};
+    if (touches(tl, tj)) return;  // the regularised-rule kernel
+
+    const double *gj = geo + (size_t)j * GEO_STRIDE;
+    double P0[3], e1[3], e2[3], n[3];
+    for (int c = 0; c < 3; ++c) {
+        P0[c] = gj[GEO_V0 + c];
+        e1[c] = gj[GEO_V1 + c] - gj[GEO_V0 + c];
+        e2[c] = gj[GEO_V2 + c] - gj[GEO_V1 + c];
+        n[c] = gj[GEO_N + c];
+    }
+    const double scale = 4.0 * gl[GEO_AREA] * gj[GEO_AREA];
+    const size_t EN = (size_t)E * N;
+    OutT *row = K1 + (size_t)l * N;
+
+    // level 0 (delta -> 0 limit) and the delta = 0 singular integrand
+    double s0[3] = {0, 0, 0}, ss[3] = {0, 0, 0};
+    for (int b = 0; b < nq; ++b) {
+        double t1 = rule[3 * b], t2 = rule[3 * b + 1], wb = rule[3 * b + 2];
+        const double lam[3] = {1.0 - t1, t1 - t2, t2};
+        double y0 = P0[0] + t1 * e1[0] + t2 * e2[0];
+        double y1 = P0[1] + t1 * e1[1] + t2 * e2[1];
+        double y2 = P0[2] + t1 * e1[2] + t2 * e2[2];
+        for (int a = 0; a < nq; ++a) {
+            double r0 = xa[4 * a] - y0, r1 = xa[4 * a + 1] - y1, r2 = xa[4 * a + 2] - y2;
+            double rr = r0 * r0 + r1 * r1 + r2 * r2;
+            double irho = rsqrt(rr);
+            double rnr = (r0 * n[0] + r1 * n[1] + r2 * n[2]) * irho;
+            double w = xa[4 * a + 3] * wb;
+            double k0 = w * (-g.Ap * rnr), ks = w * g.Fs * rnr * irho * irho;
+            for (int v = 0; v < 3; ++v) {
+                s0[v] = fma(lam[v], k0, s0[v]);
+                ss[v] = fma(lam[v], ks, ss[v]);
+            }
+        }
+    }
+    double p2[3], p1[3], sing[3];
+    for (int v = 0; v < 3; ++v) {
+        p2[v] = 0.0;
+        p1[v] = scale * s0[v];
+        sing[v] = scale * ss[v];
+    }
+
+    for (int c0 = 1; c0 <= n_steps; c0 += CH) {
+        double sk[3][CH];
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int u = 0; u < CH; ++u) sk[v][u] = 0.0;
+        for (int b = 0; b < nq; ++b) {
+            double t1 = rule[3 * b], t2 = rule[3 * b + 1], wb = rule[3 * b + 2];
+            const double lam[3] = {1.0 - t1, t1 - t2, t2};
+            double y0 = P0[0] + t1 * e1[0] + t2 * e2[0];
+            double y1 = P0[1] + t1 * e1[1] + t2 * e2[1];
+            double y2 = P0[2] + t1 * e1[2] + t2 * e2[2];
+            for (int a = 0; a < nq; ++a) {
+                double r0 = xa[4 * a] - y0, r1 = xa[4 * a + 1] - y1, r2 = xa[4 * a + 2] - y2;
+                double rr = r0 * r0 + r1 * r1 + r2 * r2;
+                double irho = rsqrt(rr), rho = rr * irho;
+                double rnr = (r0 * n[0] + r1 * n[1] + r2 * n[2]) * irho;
+                double wk = xa[4 * a + 3] * wb * rnr;
+                const double wl[3] = {wk * lam[0], wk * lam[1], wk * lam[2]};
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    if (c0 + u <= n_steps) {
+                        double v, kf;
+                        eval_level(rho, irho, lv + (c0 + u) * LV_STRIDE, g, v, kf);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) sk[q][u] = fma(wl[q], kf, sk[q][u]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            int i = c0 + u;
+            if (i <= n_steps) {
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    double c = scale * sk[v][u];
+                    double bk = i == 1 ? g.h * sing[v] - c + p1[v]      // eq. K0
+                                       : 2.0 * p1[v] - c - p2[v];      // eq. K_d, d = i - 1
+                    atomic_add_out(row + (size_t)(i - 1) * EN + tj[v], bk);
+                    p2[v] = p1[v];
+                    p1[v] = c;
+                }
+            }
+        }
+    }
+}
+
+// Touching pairs: one CTA per unordered pair (a, b); entry (a, b) has its
+// trial points on b (coordinates t1, t2 in b's rotated vertex order), entry
+// (b, a) on a.  Identical pairs contribute nothing (r . n_y = 0).
+template <int CH, class OutT>
+__global__ void __launch_bounds__(SS_THREADS)
+k_singular_k1_f64(const double *__restrict__ geo, const int32_t *__restrict__ tris,
+                  const TouchPair *__restrict__ pairs, int E, int N, SSTables tab,
+                  const double *__restrict__ levels, int n_steps, Globals g,
+                  OutT *__restrict__ K1) {
+    __shared__ double red[SS_THREADS / 32][6 * CH + 12];
+    __shared__ double fin[6 * CH + 12];
+    const TouchPair P = pairs[blockIdx.x];
+    const int a = P.a, b = P.b, cls = P.cls;
+    if (a < 0 || b < a || b >= E || cls < PAIR_VERTEX || cls >= PAIR_IDENTICAL) return;
+    const double *ga = geo + (size_t)a * GEO_STRIDE, *gb = geo + (size_t)b * GEO_STRIDE;
+    const int oa[3] = {P.perm & 3, (P.perm >> 2) & 3, (P.perm >> 4) & 3};
+    const int ob[3] = {(P.perm >> 6) & 3, (P.perm >> 8) & 3, (P.perm >> 10) & 3};
+    int na_node[3], nb_node[3];
+    double A0[3], A1[3], A2[3], B0[3], B1[3], B2[3], na[3], nb[3];
+    for (int c = 0; c < 3; ++c) {
+        na_node[c] = tris[3 * a + oa[c]];
+        nb_node[c] = tris[3 * b + ob[c]];
+        A0[c] = ga[3 * oa[0] + c];
+        A1[c] = ga[3 * oa[1] + c] - ga[3 * oa[0] + c];
+        A2[c] = ga[3 * oa[2] + c] - ga[3 * oa[1] + c];
+        B0[c] = gb[3 * ob[0] + c];
+        B1[c] = gb[3 * ob[1] + c] - gb[3 * ob[0] + c];
+        B2[c] = gb[3 * ob[2] + c] - gb[3 * ob[1] + c];
+        na[c] = ga[GEO_N + c];
+        nb[c] = gb[GEO_N + c];
+    }
+    const double scale = 4.0 * ga[GEO_AREA] * gb[GEO_AREA];
+    const int npt = tab.n[cls];
+    const double *S1 = tab.s1[cls], *S2 = tab.s2[cls], *T1 = tab.t1[cls], *T2 = tab.t2[cls],
+                 *W = tab.w[cls];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t EN = (size_t)E * N;
+
+    // weights of point p: (a,b) -> lam_b(t) w rab, (b,a) -> lam_a(s) w rba
+    auto point = [&](int p, double &rho, double &irho, double (&wab)[3], double (&wba)[3]) {
+        double s1 = S1[p], s2 = S2[p], t1 = T1[p], t2 = T2[p];
+        double r[3];
+        for (int c = 0; c < 3; ++c)
+            r[c] = (A0[c] + s1 * A1[c] + s2 * A2[c]) - (B0[c] + t1 * B1[c] + t2 * B2[c]);
+        double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        irho = rsqrt(rr);
+        rho = rr * irho;
+        double rab = (r[0] * nb[0] + r[1] * nb[1] + r[2] * nb[2]) * irho;
+        double rba = -(r[0] * na[0] + r[1] * na[1] + r[2] * na[2]) * irho;
+        double w = W[p];
+        const double lb[3] = {1.0 - t1, t1 - t2, t2}, la[3] = {1.0 - s1, s1 - s2, s2};
+        for (int v = 0; v < 3; ++v) {
+            wab[v] = w * rab * lb[v];
+            wba[v] = w * rba * la[v];
+        }
+    };
+    auto reduce = [&](double *vals, int nv) {
+        for (int k = 0; k < nv; ++k) {
+            double v = vals[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < nv) {
+            double s = 0.0;
+            for (int wi = 0; wi < SS_THREADS / 32; ++wi) s += red[wi][threadIdx.x];
+            fin[threadIdx.x] = scale * s;
+        }
+        __syncthreads();
+    };
+
+    // level 0 and the delta = 0 integrand: z[v] (a,b), z[3+v] (b,a), then singular
+    double z[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) z[k] = 0.0;
+    for (int p = threadIdx.x; p < npt; p += SS_THREADS) {
+        double rho, irho, wab[3], wba[3];
+        point(p, rho, irho, wab, wba);
+        for (int v = 0; v < 3; ++v) {
+            z[v] = fma(wab[v], -g.Ap, z[v]);
+            z[3 + v] = fma(wba[v], -g.Ap, z[3 + v]);
+            z[6 + v] = fma(wab[v], g.Fs * irho * irho, z[6 + v]);
+            z[9 + v] = fma(wba[v], g.Fs * irho * irho, z[9 + v]);
+        }
+    }
+    reduce(z, 12);
+    double p1[6], p2[6], sing[6];
+    for (int k = 0; k < 6; ++k) {
+        p1[k] = fin[k];
+        p2[k] = 0.0;
+        sing[k] = fin[6 + k];
+    }
+    __syncthreads();
+
+    for (int c0 = 1; c0 <= n_steps; c0 += CH) {
+        double acc[6 * CH];
+#pragma unroll
+        for (int k = 0; k < 6 * CH; ++k) acc[k] = 0.0;
+        for (int p = threadIdx.x; p < npt; p += SS_THREADS) {
+            double rho, irho, wab[3], wba[3];
+            point(p, rho, irho, wab, wba);
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                if (c0 + u <= n_steps) {
+                    double v, kf;
+                    eval_level(rho, irho, levels + (c0 + u) * LV_STRIDE, g, v, kf);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        acc[q * CH + u] = fma(wab[q], kf, acc[q * CH + u]);
+                        acc[(3 + q) * CH + u] = fma(wba[q], kf, acc[(3 + q) * CH + u]);
+                    }
+                }
+            }
+        }
+        reduce(acc, 6 * CH);
+        if (threadIdx.x == 0) {
+            for (int u = 0; u < CH; ++u) {
+                int i = c0 + u;
+                if (i > n_steps) break;
+                for (int k = 0; k < 6; ++k) {
+                    double c = fin[k * CH + u];
+                    double bk = i == 1 ? g.h * sing[k] - c + p1[k] : 2.0 * p1[k] - c - p2[k];
+                    // k < 3: row a, trial node of b; k >= 3: row b, trial node of a
+                    const size_t off = (size_t)(i - 1) * EN;
+                    if (k < 3)
+                        atomic_add_out(K1 + off + (size_t)a * N + nb_node[k], bk);
+                    else
+                        atomic_add_out(K1 + off + (size_t)b * N + na_node[k - 3], bk);
+                    p2[k] = p1[k];
+                    p1[k] = c;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <class OutT>
 static stb_status run_assembly(const Mesh &m, const stb_params &p, OutT *V, OutT *K,
                                const AssemblyLayout &L, int32_t *status, cudaStream_t s) {
@@ -591,9 +850,95 @@ static stb_status run_assembly(const Mesh &m, const stb_params &p, OutT *V, OutT
     return STB_OK;
 }
 
+template <class OutT>
+static stb_status run_assembly_k1(const Mesh &m, const stb_params &p, OutT *K1,
+                                  const AssemblyLayout &L, cudaStream_t s) {
+    constexpr int CH = 8;
+    const int E = (int)m.n_tris, N = (int)m.n_nodes;
+    const int nq = p.quad_regular * p.quad_regular;
+    Globals g = make_globals(p);
+    STB_CUDA(cudaMemsetAsync(K1, 0, sizeof(OutT) * (size_t)p.n_steps * E * N, s));
+    size_t smem = sizeof(double) * (4 * MAX_RULE + (size_t)(p.n_steps + 1) * LV_STRIDE);
+    STB_CUDA(cudaFuncSetAttribute(k_regular_k1_f64<CH, OutT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((E + REG_THREADS - 1) / REG_THREADS, E);
+    count_launch(s);
+    k_regular_k1_f64<CH, OutT><<<grid, REG_THREADS, smem, s>>>(L.geo, m.d_tris, E, N, L.rule, nq,
+                                                               L.levels, p.n_steps, g, K1);
+    stb_status st = check_launch("k_regular_k1_f64");
+    if (st || m.n_touch == 0) return st;
+    SSTables tab{};
+    const double *base = L.ss;
+    for (int cls = 1; cls <= 3; ++cls) {
+        size_t n = L.ss_n[cls];
+        tab.s1[cls] = base;
+        tab.s2[cls] = base + n;
+        tab.t1[cls] = base + 2 * n;
+        tab.t2[cls] = base + 3 * n;
+        tab.w[cls] = base + 4 * n;
+        tab.n[cls] = (int)n;
+        base += 5 * n;
+    }
+    count_launch(s);
+    k_singular_k1_f64<CH, OutT><<<(unsigned)m.n_touch, SS_THREADS, 0, s>>>(
+        L.geo, m.d_tris, L.pairs, E, N, tab, L.levels, p.n_steps, g, K1);
+    return check_launch("k_singular_k1_f64");
+}
+
 }  // namespace stb
 
 using namespace stb;
+
+// FP64 path: upload the host tables (regular rule, regularised rules, level
+// constants), then geometry and pair classification.
+stb_status stb::prepare_fp64(const Mesh &m, const stb_params &p, const AssemblyLayout &L,
+                             int32_t *status, cudaStream_t s) {
+    upload_psi_coeffs(s);
+    stb_status st;
+    // FP64 host tables: regular rule, regularised rules, level constants
+    std::vector<double> host;
+    {
+        std::vector<double> a, b, c, d, w;
+        triangle_rule(p.quad_regular, a, b, w);
+        for (size_t i = 0; i < w.size(); ++i) {
+            host.push_back(a[i]);
+            host.push_back(b[i]);
+            host.push_back(w[i]);
+        }
+        size_t rule_pad = (size_t)((char *)L.ss - (char *)L.rule) / sizeof(double);
+        host.resize(rule_pad, 0.0);
+        for (int cls = 1; cls <= 3; ++cls) {
+            ss_rule(cls, p.quad_singular, a, b, c, d, w);
+            host.insert(host.end(), a.begin(), a.end());
+            host.insert(host.end(), b.begin(), b.end());
+            host.insert(host.end(), c.begin(), c.end());
+            host.insert(host.end(), d.begin(), d.end());
+            host.insert(host.end(), w.begin(), w.end());
+        }
+        size_t lev_pad = (size_t)((char *)L.levels - (char *)L.rule) / sizeof(double);
+        host.resize(lev_pad, 0.0);
+        const double pi = 3.14159265358979323846, al = p.alpha;
+        const double h = p.T / p.n_steps;
+        for (int i = 0; i <= p.n_steps; ++i) {
+            double lvv[LV_STRIDE] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (i > 0) {
+                double delta = i * h, sd = std::sqrt(delta);
+                lvv[LV_C] = 1.0 / (2.0 * std::sqrt(al * delta));
+                lvv[LV_B] = delta / (4.0 * pi * al);
+                lvv[LV_CC] = sd / (4.0 * pi * std::sqrt(pi * al * al * al));
+                lvv[LV_D] = delta / (4.0 * pi);
+                lvv[LV_E] = sd / (4.0 * pi * std::sqrt(pi * al));
+            }
+            host.insert(host.end(), lvv, lvv + LV_STRIDE);
+        }
+    }
+    STB_CUDA(cudaMemcpyAsync(L.rule, host.data(), host.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, s));
+    STB_CUDA(cudaMemsetAsync(L.pairs, 0xff, sizeof(TouchPair) * (m.n_touch > 0 ? m.n_touch : 1), s));
+    if ((st = launch_geometry(m, L.geo, s))) return st;
+    if ((st = launch_classify(m, L.row_count, L.row_off, L.pairs, status, s))) return st;
+    return STB_OK;
+}
 
 // Mixed path: upload the FP32 tables, then geometry and pair classification.
 stb_status stb::prepare_mixed(const Mesh &m, const stb_params &p, const AssemblyLayout &L,
@@ -641,49 +986,36 @@ extern "C" stb_status stb_assemble(const stb_mesh *mesh, const stb_params *param
         if ((st = prepare_mixed(m, *params, L, status, s))) return st;
         return run_assembly_mixed(m, *params, V, K, L, s);
     }
-    // FP64 host tables: regular rule, regularised rules, level constants
-    std::vector<double> host;
-    {
-        std::vector<double> a, b, c, d, w;
-        triangle_rule(params->quad_regular, a, b, w);
-        for (size_t i = 0; i < w.size(); ++i) {
-            host.push_back(a[i]);
-            host.push_back(b[i]);
-            host.push_back(w[i]);
-        }
-        size_t rule_pad = (size_t)((char *)L.ss - (char *)L.rule) / sizeof(double);
-        host.resize(rule_pad, 0.0);
-        for (int cls = 1; cls <= 3; ++cls) {
-            ss_rule(cls, params->quad_singular, a, b, c, d, w);
-            host.insert(host.end(), a.begin(), a.end());
-            host.insert(host.end(), b.begin(), b.end());
-            host.insert(host.end(), c.begin(), c.end());
-            host.insert(host.end(), d.begin(), d.end());
-            host.insert(host.end(), w.begin(), w.end());
-        }
-        size_t lev_pad = (size_t)((char *)L.levels - (char *)L.rule) / sizeof(double);
-        host.resize(lev_pad, 0.0);
-        const double pi = 3.14159265358979323846, al = params->alpha;
-        const double h = params->T / params->n_steps;
-        for (int i = 0; i <= params->n_steps; ++i) {
-            double lvv[LV_STRIDE] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (i > 0) {
-                double delta = i * h, sd = std::sqrt(delta);
-                lvv[LV_C] = 1.0 / (2.0 * std::sqrt(al * delta));
-                lvv[LV_B] = delta / (4.0 * pi * al);
-                lvv[LV_CC] = sd / (4.0 * pi * std::sqrt(pi * al * al * al));
-                lvv[LV_D] = delta / (4.0 * pi);
-                lvv[LV_E] = sd / (4.0 * pi * std::sqrt(pi * al));
-            }
-            host.insert(host.end(), lvv, lvv + LV_STRIDE);
-        }
-    }
-    STB_CUDA(cudaMemcpyAsync(L.rule, host.data(), host.size() * sizeof(double),
-                             cudaMemcpyHostToDevice, s));
-    STB_CUDA(cudaMemsetAsync(L.pairs, 0xff, sizeof(TouchPair) * (m.n_touch > 0 ? m.n_touch : 1), s));
-    if ((st = launch_geometry(m, L.geo, s))) return st;
-    if ((st = launch_classify(m, L.row_count, L.row_off, L.pairs, status, s))) return st;
+    if ((st = prepare_fp64(m, *params, L, status, s))) return st;
     if (params->storage == STB_STORE_F64)
         return run_assembly<double>(m, *params, (double *)V, (double *)K, L, status, s);
     return run_assembly<float>(m, *params, (float *)V, (float *)K, L, status, s);
+}
+
+extern "C" stb_status stb_assemble_k1_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                                     size_t *bytes) {
+    if (!mesh || !bytes || !params) return fail(STB_ERR_INVALID_ARG, "mesh, params and bytes must be given");
+    stb_status st = check_assembly_params(params);
+    if (st) return st;
+    if (params->precision != STB_PREC_FP64)
+        return fail(STB_ERR_INVALID_ARG, "the piecewise-linear double layer is assembled in FP64");
+    *bytes = align256(assembly_layout(mesh->m, *params, nullptr, 0).bytes);
+    return STB_OK;
+}
+
+extern "C" stb_status stb_assemble_k1(const stb_mesh *mesh, const stb_params *params, void *K1,
+                                      void *ws, size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !K1) return fail(STB_ERR_INVALID_ARG, "mesh and K1 must be given");
+    size_t need;
+    stb_status st = stb_assemble_k1_workspace_size(mesh, params, &need);
+    if (st) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    const Mesh &m = mesh->m;
+    if (m.n_tris > 65535) return fail(STB_ERR_INVALID_ARG, "dense assembly supports E <= 65535");
+    AssemblyLayout L = assembly_layout(m, *params, ws, ws_bytes);
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = prepare_fp64(m, *params, L, status_word(ws), s))) return st;
+    if (params->storage == STB_STORE_F64) return run_assembly_k1<double>(m, *params, (double *)K1, L, s);
+    return run_assembly_k1<float>(m, *params, (float *)K1, L, s);
 }

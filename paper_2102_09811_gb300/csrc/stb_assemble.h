@@ -54,6 +54,9 @@ void mixed_tables(const stb_params &p, std::vector<float> &rule, std::vector<flo
 // Workspace layout of one problem (ws = nullptr: sizes only, L.bytes).
 AssemblyLayout assembly_layout(const Mesh &m, const stb_params &p, void *ws, size_t cap);
 stb_status check_assembly_params(const stb_params *p);
+// FP64 path set-up of one problem: tables, geometry, pair classification.
+stb_status prepare_fp64(const Mesh &m, const stb_params &p, const AssemblyLayout &L,
+                        int32_t *status, cudaStream_t s);
 // Mixed path set-up of one problem: tables, geometry, pair classification.
 stb_status prepare_mixed(const Mesh &m, const stb_params &p, const AssemblyLayout &L,
                          int32_t *status, cudaStream_t s);

@@ -10,6 +10,7 @@
 #include <mutex>
 #include <vector>
 
+#include "stb_dense.h"
 #include "stb_internal.h"
 #include "stb_toeplitz.h"
 
@@ -256,6 +257,114 @@ static stb_status upload_rules_sources(const DirLayout &L, int q, int nt, const 
     return STB_OK;
 }
 
+// ------------------------------------ piecewise-linear data (Sec. 3.4) ---
+// Nodal moments b_{r,k,i} = h^{-1} int_{t_k}^{t_{k+1}} int_Gamma g_r phi_i of
+// the hat functions phi_i: per element (r, k, j) the three vertex moments
+// 2 Delta_j sum_a w_a lambda_v(a) (time mean of g_r at x_a), added to the
+// nodes of triangle j (atomics: b starts at zero).
+template <class R>
+__global__ void __launch_bounds__(DIR_THREADS)
+k_project_p1(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E, int N,
+             const double *__restrict__ rule, int nq, int nt, const double *__restrict__ src,
+             int n_src, int n_steps, double h_, double alpha_, double *__restrict__ b) {
+    __shared__ R rs[3 * MAX_QS * MAX_QS + 2 * MAX_NT];
+    __shared__ R sr[5 * MAX_SRC];
+    const R h = (R)h_, alpha = (R)alpha_;
+    for (int i = threadIdx.x; i < 3 * nq + 2 * nt; i += DIR_THREADS) rs[i] = rule[i];
+    const int r = blockIdx.y;
+    for (int i = threadIdx.x; i < 5 * n_src; i += DIR_THREADS) sr[i] = src[(size_t)r * n_src * 5 + i];
+    __syncthreads();
+    size_t idx = (size_t)blockIdx.x * DIR_THREADS + threadIdx.x;  // (k, j)
+    if (idx >= (size_t)n_steps * E) return;
+    const int k = (int)(idx / E), j = (int)(idx % E);
+    const double *gj = geo + (size_t)j * GEO_STRIDE;
+    const R *tx = rs + 3 * nq, *tw = tx + nt;
+    R acc[3] = {0, 0, 0};
+    for (int a = 0; a < nq; ++a) {
+        R s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
+        R x[3];
+        for (int c = 0; c < 3; ++c)
+            x[c] = (R)(gj[c] + (double)s1 * (gj[3 + c] - gj[c]) + (double)s2 * (gj[6 + c] - gj[3 + c]));
+        R inner = 0;
+        for (int q = 0; q < nt; ++q) {
+            R t = (k + tx[q]) * h, gv = 0;
+            for (int si = 0; si < n_src; ++si) {
+                const R *S = sr + 5 * si;
+                R d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
+                gv = fma(S[4], heat<R>(d0 * d0 + d1 * d1 + d2 * d2, t - S[3], alpha), gv);
+            }
+            inner = fma(tw[q], gv, inner);
+        }
+        const R wi = wa * inner;
+        acc[0] = fma(1 - s1, wi, acc[0]);
+        acc[1] = fma(s1 - s2, wi, acc[1]);
+        acc[2] = fma(s2, wi, acc[2]);
+    }
+    double *bk = b + ((size_t)r * n_steps + k) * N;
+    const double area2 = 2.0 * gj[GEO_AREA];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) atomicAdd(bk + tris[3 * j + v], area2 * (double)acc[v]);
+}
+
+// Mass matrix of the hat functions: M1[i][i'] += Delta_j / 12 (1 + [i = i'])
+// over the vertices i, i' of every triangle j (M1 starts at zero).
+__global__ void k_mass_p1(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E,
+                          int N, double *__restrict__ M) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= E) return;
+    const double m = geo[(size_t)j * GEO_STRIDE + GEO_AREA] / 12.0;
+    const int t[3] = {tris[3 * j], tris[3 * j + 1], tris[3 * j + 2]};
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) atomicAdd(M + (size_t)t[a] * N + t[c], a == c ? 2.0 * m : m);
+}
+
+// f_{r,k,l} += (h/2) (Delta_l / 3) sum over the vertices i of l of g1_{r,k,i}
+// (the p0 x p1 mass matrix: int_{gamma_l} phi_i = Delta_l / 3)
+__global__ void k_add_mass_p1(const double *__restrict__ geo, const int32_t *__restrict__ tris,
+                              int E, int N, size_t total, double h, const double *__restrict__ g1,
+                              double *__restrict__ f) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int l = (int)(idx % E);
+    const double *gk = g1 + (idx / E) * N;
+    const double m = gk[tris[3 * l]] + gk[tris[3 * l + 1]] + gk[tris[3 * l + 2]];
+    f[idx] = fma(0.5 * h * geo[(size_t)l * GEO_STRIDE + GEO_AREA] / 3.0, m, f[idx]);
+}
+
+// Every node must belong to a triangle, else M1 is singular.
+static stb_status check_nodes_used(const Mesh &m) {
+    std::vector<char> used(m.n_nodes, 0);
+    for (int32_t t : m.tris) used[t] = 1;
+    for (int64_t i = 0; i < m.n_nodes; ++i)
+        if (!used[i]) return fail(STB_ERR_INVALID_ARG, "node %lld belongs to no triangle", (long long)i);
+    if (m.n_nodes > 65535) return fail(STB_ERR_INVALID_ARG, "n_nodes must be <= 65535");
+    return STB_OK;
+}
+
+// Workspace of the p1 projection: rules, sources and geometry, the mass
+// matrix, the moments, the scratch of its inverse.
+struct P1Layout {
+    DirLayout d;
+    double *M, *b;
+    void *inv;
+    size_t inv_bytes, bytes;
+};
+
+static P1Layout p1_layout(const Mesh &m, int n_steps, int nrhs, int n_src, int q, int nt, void *ws,
+                          size_t cap) {
+    P1Layout P{};
+    P.d = dir_layout(m, nrhs, n_src, q, nt, ws, cap, 0);
+    Carve c(ws, cap);
+    c.off = P.d.bytes;
+    const size_t N = (size_t)m.n_nodes;
+    P.M = c.take<double>(N * N);
+    P.b = c.take<double>((size_t)nrhs * n_steps * N);
+    P.inv_bytes = spd_inverse_bytes((int64_t)N);
+    P.inv = c.take<char>(P.inv_bytes);
+    P.bytes = c.off;
+    return P;
+}
+
 }  // namespace stb
 
 using namespace stb;
@@ -394,4 +503,97 @@ extern "C" stb_status stb_neumann_error(const stb_mesh *mesh, const stb_params *
     count_launch(s);
     k_sum_pairs<<<1, 1024, 0, s>>>(L.part, nblk, out);
     return check_launch("k_sum_pairs");
+}
+
+// ---------------------------------------- piecewise-linear data (Sec. 3.4) ---
+extern "C" stb_status stb_project_p1_workspace_size(const stb_mesh *mesh, const stb_params *p,
+                                                    int32_t nrhs, int32_t n_src, int32_t q,
+                                                    int32_t nt, size_t *bytes) {
+    if (!mesh || !p || !bytes || p->n_steps < 1) return fail(STB_ERR_INVALID_ARG, "invalid argument");
+    stb_status st = check_rule_args(nrhs, n_src, q, nt);
+    if (st) return st;
+    if ((st = check_nodes_used(mesh->m))) return st;
+    *bytes = align256(p1_layout(mesh->m, p->n_steps, nrhs, n_src, q, nt, nullptr, 0).bytes);
+    return STB_OK;
+}
+
+extern "C" stb_status stb_project_dirichlet_p1(const stb_mesh *mesh, const stb_params *p,
+                                               const double *sources, int32_t nrhs, int32_t n_src,
+                                               int32_t q, int32_t nt, double *g1, void *ws,
+                                               size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !p || !sources || !g1) return fail(STB_ERR_INVALID_ARG, "null argument");
+    if (!(p->alpha > 0) || !(p->T > 0) || p->n_steps < 1)
+        return fail(STB_ERR_INVALID_ARG, "alpha, T and n_steps must be positive");
+    size_t need;
+    stb_status st = stb_project_p1_workspace_size(mesh, p, nrhs, n_src, q, nt, &need);
+    if (st) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    const Mesh &m = mesh->m;
+    const int E = (int)m.n_tris, N = (int)m.n_nodes;
+    P1Layout P = p1_layout(m, p->n_steps, nrhs, n_src, q, nt, ws, ws_bytes);
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = upload_rules_sources(P.d, q, nt, sources, nrhs, n_src, s))) return st;
+    if ((st = launch_geometry(m, P.d.geo, s))) return st;
+    // mass matrix and its inverse
+    STB_CUDA(cudaMemsetAsync(P.M, 0, sizeof(double) * (size_t)N * N, s));
+    count_launch(s);
+    k_mass_p1<<<(E + 127) / 128, 128, 0, s>>>(P.d.geo, m.d_tris, E, N, P.M);
+    if ((st = check_launch("k_mass_p1"))) return st;
+    double *inv = nullptr;
+    if ((st = spd_inverse(P.M, N, P.inv, P.inv_bytes, status_word(ws), &inv, s))) return st;
+    // moments, then g1 = M1^{-1} b for every (r, k)
+    const size_t nb = (size_t)nrhs * p->n_steps * N;
+    STB_CUDA(cudaMemsetAsync(P.b, 0, sizeof(double) * nb, s));
+    const size_t n = (size_t)p->n_steps * E;
+    dim3 grid((unsigned)((n + DIR_THREADS - 1) / DIR_THREADS), (unsigned)nrhs);
+    count_launch(s);
+    if (p->precision == STB_PREC_MIXED)
+        k_project_p1<float><<<grid, DIR_THREADS, 0, s>>>(P.d.geo, m.d_tris, E, N, P.d.rule, q * q,
+                                                         nt, P.d.src, n_src, p->n_steps,
+                                                         p->T / p->n_steps, p->alpha, P.b);
+    else
+        k_project_p1<double><<<grid, DIR_THREADS, 0, s>>>(P.d.geo, m.d_tris, E, N, P.d.rule, q * q,
+                                                          nt, P.d.src, n_src, p->n_steps,
+                                                          p->T / p->n_steps, p->alpha, P.b);
+    if ((st = check_launch("k_project_p1"))) return st;
+    return dense_apply(inv, N, (int64_t)nrhs * p->n_steps, P.b, g1, s);
+}
+
+extern "C" stb_status stb_rhs_p1_workspace_size(const stb_mesh *mesh, const stb_params *p,
+                                                int32_t nrhs, size_t *bytes) {
+    if (!mesh || !p || !bytes || nrhs < 1 || p->n_steps < 1)
+        return fail(STB_ERR_INVALID_ARG, "invalid argument");
+    Carve c(nullptr, 0);
+    c.take<double>((size_t)mesh->m.n_tris * GEO_STRIDE);
+    c.take<char>(toeplitz_partial_bytes(mesh->m.n_tris, p->n_steps, nrhs));
+    *bytes = align256(c.off);
+    return STB_OK;
+}
+
+extern "C" stb_status stb_dirichlet_rhs_p1(const stb_mesh *mesh, const stb_params *p,
+                                           const void *K1, const double *g1, int32_t nrhs,
+                                           double *f, void *ws, size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !p || !K1 || !g1 || !f) return fail(STB_ERR_INVALID_ARG, "null argument");
+    if (p->storage != STB_STORE_F64 && p->storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "bad storage");
+    size_t need;
+    stb_status st = stb_rhs_p1_workspace_size(mesh, p, nrhs, &need);
+    if (st) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    const Mesh &m = mesh->m;
+    Carve c(ws, ws_bytes);
+    double *geo = c.take<double>((size_t)m.n_tris * GEO_STRIDE);
+    double *part = (double *)c.take<char>(toeplitz_partial_bytes(m.n_tris, p->n_steps, nrhs));
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = launch_geometry(m, geo, s))) return st;
+    if ((st = toeplitz_fp64_rect(K1, p->storage, m.n_tris, m.n_nodes, p->n_steps, nrhs, g1, 0.0, f,
+                                 part, s)))
+        return st;
+    const size_t total = (size_t)nrhs * p->n_steps * m.n_tris;
+    count_launch(s);
+    k_add_mass_p1<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        geo, m.d_tris, (int)m.n_tris, (int)m.n_nodes, total, p->T / p->n_steps, g1, f);
+    return check_launch("k_add_mass_p1");
 }

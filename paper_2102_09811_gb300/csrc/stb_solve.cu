@@ -20,6 +20,7 @@
 #include <cmath>
 #include <vector>
 
+#include "stb_dense.h"
 #include "stb_internal.h"
 #include "stb_toeplitz.h"
 
@@ -803,6 +804,33 @@ static stb_status solve_mixed(const float *V, int E, int n_steps, int nrhs, cons
     STB_CUDA(cudaMemcpyAsync(ws, &hdr, sizeof hdr, cudaMemcpyHostToDevice, s));
     STB_CUDA(cudaStreamSynchronize(s));
     return STB_OK;
+}
+
+// ---------------------------------------------- dense SPD helpers ---
+// The factorisation and explicit inverse above, for any SPD FP64 matrix (the
+// piecewise-linear mass matrix of the L2 projection, Sec. 3.4).
+size_t spd_inverse_bytes(int64_t n) {
+    return align256(solve_layout(n, 1, 1, false, nullptr, 0).bytes);
+}
+
+stb_status spd_inverse(const double *M, int64_t n, void *scratch, size_t cap, int32_t *status,
+                       double **inv, cudaStream_t s) {
+    if (n < 1 || n > 65535) return fail(STB_ERR_INVALID_ARG, "SPD inverse needs 1 <= n <= 65535");
+    SolveLayout S = solve_layout(n, 1, 1, false, scratch, cap);
+    if (!scratch || S.bytes > cap) return fail(STB_ERR_INVALID_ARG, "SPD inverse scratch too small");
+    *inv = (double *)S.L;
+    return factorize<double, double>(M, (int)n, S, status, s);
+}
+
+// out_v = A in_v for nvec vectors of length n (A row-major n x n)
+stb_status dense_apply(const double *A, int64_t n, int64_t nvec, const double *in, double *out,
+                       cudaStream_t s) {
+    if (n < 1 || n > 65535 || nvec < 1 || nvec > INT32_MAX)
+        return fail(STB_ERR_INVALID_ARG, "bad dense product size");
+    count_launch(s);
+    k_trmv<double><<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(A, (int)n, (int)nvec, FULL, in,
+                                                                   (size_t)n, out, (size_t)n);
+    return check_launch("k_trmv");
 }
 
 }  // namespace stb

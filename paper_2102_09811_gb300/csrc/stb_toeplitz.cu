@@ -22,7 +22,7 @@ constexpr int MV_THREADS = 128;
 
 template <class AT>
 __global__ void __launch_bounds__(MV_THREADS)
-k_toeplitz_partial(const AT *__restrict__ A, int E, int n_steps, int nrhs,
+k_toeplitz_partial(const AT *__restrict__ A, int E, int N, int n_steps, int nrhs,
                    const double *__restrict__ x, double *__restrict__ part) {
     __shared__ double As[TM][TJ + 1];
     __shared__ double Xs[TK][TJ + 1];
@@ -35,18 +35,18 @@ k_toeplitz_partial(const AT *__restrict__ A, int E, int n_steps, int nrhs,
     double acc[TM / (MV_THREADS / TK)];
 #pragma unroll
     for (int i = 0; i < TM / (MV_THREADS / TK); ++i) acc[i] = 0.0;
-    const size_t EE = (size_t)E * E;
-    const double *xr = x + (size_t)r * n_steps * E;
+    const size_t EN = (size_t)E * N;
+    const double *xr = x + (size_t)r * n_steps * N;
     for (int d = d0; d < d1; ++d) {
-        const AT *Ad = A + (size_t)d * EE;
-        for (int j0 = 0; j0 < E; j0 += TJ) {
+        const AT *Ad = A + (size_t)d * EN;
+        for (int j0 = 0; j0 < N; j0 += TJ) {
             for (int t = threadIdx.x; t < TM * TJ; t += MV_THREADS) {
                 int i = t / TJ, jj = t % TJ, l = l0 + i, j = j0 + jj;
-                As[i][jj] = (l < E && j < E) ? (double)Ad[(size_t)l * E + j] : 0.0;
+                As[i][jj] = (l < E && j < N) ? (double)Ad[(size_t)l * N + j] : 0.0;
             }
             for (int t = threadIdx.x; t < TK * TJ; t += MV_THREADS) {
                 int c = t / TJ, jj = t % TJ, k = k0 + c, j = j0 + jj;
-                Xs[c][jj] = (k < n_steps && k - d >= 0 && j < E) ? xr[(size_t)(k - d) * E + j] : 0.0;
+                Xs[c][jj] = (k < n_steps && k - d >= 0 && j < N) ? xr[(size_t)(k - d) * N + j] : 0.0;
             }
             __syncthreads();
 #pragma unroll 8
@@ -89,15 +89,21 @@ size_t toeplitz_partial_bytes(int64_t E, int32_t n_steps, int32_t nrhs) {
 
 stb_status toeplitz_fp64(const void *A, int32_t storage, int64_t E, int32_t n_steps, int32_t nrhs,
                          const double *x, double beta, double *y, double *part, cudaStream_t s) {
+    return toeplitz_fp64_rect(A, storage, E, E, n_steps, nrhs, x, beta, y, part, s);
+}
+
+stb_status toeplitz_fp64_rect(const void *A, int32_t storage, int64_t E, int64_t N, int32_t n_steps,
+                              int32_t nrhs, const double *x, double beta, double *y, double *part,
+                              cudaStream_t s) {
     int n_kt = (n_steps + TK - 1) / TK, n_dr = (n_steps + TD - 1) / TD;
     dim3 grid((unsigned)((E + TM - 1) / TM), (unsigned)(n_kt * nrhs), (unsigned)n_dr);
     count_launch(s);
     if (storage == STB_STORE_F64)
-        k_toeplitz_partial<double><<<grid, MV_THREADS, 0, s>>>((const double *)A, (int)E, n_steps,
-                                                               nrhs, x, part);
+        k_toeplitz_partial<double><<<grid, MV_THREADS, 0, s>>>((const double *)A, (int)E, (int)N,
+                                                               n_steps, nrhs, x, part);
     else
-        k_toeplitz_partial<float><<<grid, MV_THREADS, 0, s>>>((const float *)A, (int)E, n_steps,
-                                                              nrhs, x, part);
+        k_toeplitz_partial<float><<<grid, MV_THREADS, 0, s>>>((const float *)A, (int)E, (int)N,
+                                                              n_steps, nrhs, x, part);
     stb_status st = check_launch("k_toeplitz_partial");
     if (st) return st;
     size_t total = (size_t)nrhs * n_steps * E;

@@ -20,11 +20,18 @@ class DirichletProblem:
     """Buffers and calls for one mesh / parameter set / list of sources.
 
     sources: numpy [nrhs, n_src, 5] of (y1, y2, y3, t0, weight).
+    data: "p0" projects the Dirichlet datum into piecewise constants in space
+    (K_h with E x E blocks); "p1" into the continuous piecewise-linear space
+    X_h^{1,0} (Sec. 3.2, Sec. 3.4: K_h with E x n_nodes blocks, assembled in
+    FP64 arithmetic; the p0 x p1 mass in the right-hand side).
     """
 
     def __init__(self, nodes, tris, alpha, T, n_steps, sources, quad_regular=3, quad_singular=4,
                  storage=capi.STB_STORE_F64, q_space=8, n_time=16, device="cuda", mesh=None,
-                 precision=capi.STB_PREC_FP64):
+                 precision=capi.STB_PREC_FP64, data="p0"):
+        if data not in ("p0", "p1"):
+            raise ValueError("data must be 'p0' or 'p1'")
+        self.data = data
         self.mesh = mesh if mesh is not None else capi.Mesh(nodes, tris)
         self.params = capi.stb_default_params(alpha, T, n_steps, quad_regular, quad_singular,
                                               precision=precision, storage=storage)
@@ -35,29 +42,44 @@ class DirichletProblem:
         self.E, self.n_steps, self.device = E, n_steps, dev
         dt = torch.float64 if storage == capi.STB_STORE_F64 else torch.float32
         self.V = torch.empty((n_steps, E, E), dtype=dt, device=dev)
-        self.K = torch.empty((n_steps, E, E), dtype=dt, device=dev)
+        N = self.mesh.n_nodes if data == "p1" else E
+        self.K = torch.empty((n_steps, E, N), dtype=dt, device=dev)
         vec = (self.nrhs, n_steps, E)
-        self.g = torch.empty(vec, dtype=torch.float64, device=dev)
+        self.g = torch.empty((self.nrhs, n_steps, N), dtype=torch.float64, device=dev)
         self.f = torch.empty(vec, dtype=torch.float64, device=dev)
         self.w = torch.empty(vec, dtype=torch.float64, device=dev)
         self.err = torch.zeros(2, dtype=torch.float64, device=dev)
         m, p = self.mesh, self.params
         self.ws_assemble = _ws(capi.stb_assemble_workspace_size(m, p), dev)
-        self.ws_project = _ws(capi.stb_project_workspace_size(m, self.nrhs, self.n_src, q_space, n_time), dev)
-        self.ws_rhs = _ws(capi.stb_rhs_workspace_size(m, p, self.nrhs), dev)
+        if data == "p1":
+            self.params_k1 = capi.stb_default_params(alpha, T, n_steps, quad_regular, quad_singular,
+                                                     precision=capi.STB_PREC_FP64, storage=storage)
+            self.ws_k1 = _ws(capi.stb_assemble_k1_workspace_size(m, self.params_k1), dev)
+            self.ws_project = _ws(capi.stb_project_p1_workspace_size(m, p, self.nrhs, self.n_src,
+                                                                     q_space, n_time), dev)
+            self.ws_rhs = _ws(capi.stb_rhs_p1_workspace_size(m, p, self.nrhs), dev)
+        else:
+            self.ws_project = _ws(capi.stb_project_workspace_size(m, self.nrhs, self.n_src, q_space,
+                                                                  n_time), dev)
+            self.ws_rhs = _ws(capi.stb_rhs_workspace_size(m, p, self.nrhs), dev)
         self.ws_solve = _ws(capi.stb_solve_workspace_size(m, p, self.nrhs), dev)
         self.ws_error = _ws(capi.stb_error_workspace_size(m, p, self.nrhs, self.n_src, q_space, n_time), dev)
 
     def assemble(self, stream=None):
-        capi.stb_assemble(self.mesh, self.params, self.V, self.K, self.ws_assemble, stream)
+        if self.data == "p1":
+            capi.stb_assemble(self.mesh, self.params, self.V, None, self.ws_assemble, stream)
+            capi.stb_assemble_k1(self.mesh, self.params_k1, self.K, self.ws_k1, stream)
+        else:
+            capi.stb_assemble(self.mesh, self.params, self.V, self.K, self.ws_assemble, stream)
 
     def project(self, stream=None):
-        capi.stb_project_dirichlet(self.mesh, self.params, self.sources, self.g, self.ws_project,
-                                   self.q_space, self.n_time, stream)
+        fn = capi.stb_project_dirichlet_p1 if self.data == "p1" else capi.stb_project_dirichlet
+        fn(self.mesh, self.params, self.sources, self.g, self.ws_project, self.q_space, self.n_time,
+           stream)
 
     def rhs(self, stream=None):
-        capi.stb_dirichlet_rhs(self.mesh, self.params, self.K, self.g, self.nrhs, self.f,
-                               self.ws_rhs, stream)
+        fn = capi.stb_dirichlet_rhs_p1 if self.data == "p1" else capi.stb_dirichlet_rhs
+        fn(self.mesh, self.params, self.K, self.g, self.nrhs, self.f, self.ws_rhs, stream)
 
     def solve(self, stream=None):
         capi.stb_dirichlet_solve(self.mesh, self.params, self.V, self.f, self.nrhs, self.w,
