@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--wave-gb", type=float, default=48.0,
                     help="V+K bytes per memory wave of the batch64 workload")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-p1", action="store_true",
+                    help="skip the piecewise-linear data pipeline report (outside the timed region)")
     return ap.parse_args()
 
 
@@ -418,6 +420,37 @@ def run_gpu(args):
                "alpha": alphas[0], "mixed_vs_fp64_max_block_rel_err": {"V": max(errs_v), "K": max(errs_k)}}
         del pf
 
+    # the paper's own discretisation of the data (piecewise-linear in space,
+    # Sec. 3.2 / 3.4) for the first problem: stage times after one warm-up
+    # pass, the K1 kernels' share and the point-level evaluation rate
+    p1 = None
+    if not args.no_p1:
+        pp = pipeline.DirichletProblem(nodes, tris, alphas[0], wl["T"], n, src, mesh=mesh,
+                                       precision=prec, storage=storage, data="p1")
+        pp.run(stream)
+        torch.cuda.synchronize()
+        capi.stb_trace_enable(True)
+        capi.stb_trace_reset()
+        p1_ms = {}
+        for label, fn in (("assemble", pp.assemble), ("project", pp.project), ("rhs", pp.rhs),
+                          ("solve", pp.solve), ("error", pp.error)):
+            a_.record(stream)
+            fn(stream)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            p1_ms[label] = a_.elapsed_time(b_)
+        capi.stb_trace_enable(False)
+        tr1 = capi.stb_trace_read()
+        k1_ms = tr1.get("k_regular_k1_f64", (1, 0.0))[1]
+        evals = float(n_reg_pairs) * 81.0 * (n + 1)
+        p1 = {"alpha": alphas[0], "stage_ms": p1_ms, "rel_l2_error_w": pp.relative_error(),
+              "k_regular_k1_f64_ms": k1_ms,
+              "k_singular_k1_f64_ms": tr1.get("k_singular_k1_f64", (1, 0.0))[1],
+              "k1_point_level_evals_per_s": evals / (k1_ms / 1e3) if k1_ms else None,
+              "k1_entries": float(n) * E * mesh.n_nodes,
+              "kernels_ms": {k: v[1] for k, v in tr1.items()}}
+        del pp
+
     # end to end through the public API from host buffers (mesh, sources in;
     # solution and error norms out)
     e2e = None
@@ -453,7 +486,7 @@ def run_gpu(args):
                        "l2": "no flush: every step writes %.1f GB of V/K blocks (>> 129 MB L2)"
                              % (2 * (4 if mixed else 8) * n * E * E * len(alphas) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "mixed_vs_fp64": cmp, "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
+            "mixed_vs_fp64": cmp, "p1_data": p1, "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
             "rel_l2_error_w": rel_err, "solve": solve_info, "gpu_launches": launches,
             "kernels_ms": {k: v[1] for k, v in trace.items()}, "roofline": roof, "e2e": e2e}
     if rank == 0:

@@ -78,6 +78,8 @@ def lib():
         L.orc_project_dirichlet_p1.argtypes = [_P, _I64, _P, _I64, _D, _D, _I32,
                                                _P, _I32, _I32, _I32, _I32, _P]
         L.orc_toeplitz_matvec_rect.argtypes = [_P, _I64, _I64, _I32, _I32, _P, _P]
+        L.orc_potentials.argtypes = [_P, _I64, _P, _I64, _D, _D, _I32, _P, _P, _I32, _P, _I64,
+                                     _I32, _P, _P]
         L.orc_dirichlet_rhs_p1.argtypes = [_P, _P, _P, _I64, _I64, _D, _I32, _I32, _P, _P]
         _lib = L
     return _lib
@@ -342,3 +344,25 @@ def dirichlet_rhs_p1(area, tris, K1, g1, T):
     _check(lib().orc_dirichlet_rhs_p1(_p(area), _p(tris), _p(K1), E, N, T, n_steps,
                                       g1.shape[0], _p(g1), _p(f)), "dirichlet_rhs_p1")
     return f
+
+
+# ---- potentials: the discretised representation formula (Sec. 3.5) ----------
+def potentials(nodes, tris, alpha, T, n_steps, points, w=None, u1=None, q=4):
+    """Single-layer potential of w [nrhs, n_steps, E] (piecewise constant)
+    and double-layer potential of u1 [nrhs, n_steps, n_nodes] (piecewise
+    linear in space) at points [n_pts, 4] = (x1, x2, x3, t) off the
+    boundary: (slp, dlp), each [nrhs, n_pts] or None."""
+    nodes, tris, pts = _f64(nodes), _i32(tris), _f64(points)
+    if w is None and u1 is None:
+        raise ValueError("need w or u1")
+    w = None if w is None else _f64(w)
+    u1 = None if u1 is None else _f64(u1)
+    nrhs = (w if w is not None else u1).shape[0]
+    slp = np.zeros((nrhs, pts.shape[0])) if w is not None else None
+    dlp = np.zeros((nrhs, pts.shape[0])) if u1 is not None else None
+    _check(lib().orc_potentials(_p(nodes), nodes.shape[0], _p(tris), tris.shape[0], alpha, T,
+                                n_steps, None if w is None else _p(w),
+                                None if u1 is None else _p(u1), nrhs, _p(pts), pts.shape[0], q,
+                                None if slp is None else _p(slp),
+                                None if dlp is None else _p(dlp)), "potentials")
+    return slp, dlp

@@ -9,7 +9,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["orc_kernels.c", "orc_quad.c", "orc_assemble.c", "orc_solve.c"]
+SOURCES = ["orc_kernels.c", "orc_quad.c", "orc_assemble.c", "orc_solve.c", "orc_potentials.c"]
 LIB = os.path.join(HERE, "_build", "liborc.so")
 
 

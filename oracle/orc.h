@@ -128,6 +128,17 @@ int orc_dirichlet_rhs_p1(const double *area, const int32_t *tris, const double *
                          int64_t E, int64_t N, double T, int32_t n_steps, int32_t nrhs,
                          const double *g1, double *f);
 
+/* ---- potentials: the discretised representation formula (Sec. 3.5) --------
+ * At points (x, t) off Gamma_h, points [n_pts][4] = (x1, x2, x3, t),
+ * 0 <= t <= T: slp [nrhs][n_pts] = V~ w_h (w [nrhs][n_steps][E], piecewise
+ * constant), dlp [nrhs][n_pts] = W u_h (u1 [nrhs][n_steps][n_nodes],
+ * piecewise linear in space); either output may be NULL.  The q x q conical
+ * rule on every triangle, exact temporal antiderivatives.                   */
+int orc_potentials(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                   double alpha, double T, int32_t n_steps, const double *w, const double *u1,
+                   int32_t nrhs, const double *points, int64_t n_pts, int32_t q,
+                   double *slp, double *dlp);
+
 #ifdef __cplusplus
 }
 #endif
