@@ -49,8 +49,8 @@ MUFU_PEAK_TEX2 = 152 * 32 * 2.07e9 / 1e12
 
 
 # ncu, k_regular_mixed on the 16-step cube (3072 triangles, alpha 0.5): DRAM
-# read 17.40 MB + write 1144.84 MB for 2 x 16 x 3072^2 block entries.
-REGULAR_MIXED_DRAM_BYTES_PER_ENTRY = (17.396736e6 + 1144.844e6) / (2 * 16 * 3072.0 ** 2)
+# read 15.19 MB + write 1144.27 MB for 2 x 16 x 3072^2 block entries.
+REGULAR_MIXED_DRAM_BYTES_PER_ENTRY = (15.18848e6 + 1144.265e6) / (2 * 16 * 3072.0 ** 2)
 
 
 def mixed_nodes_per_point(n_steps):
