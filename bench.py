@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--wave-gb", type=float, default=48.0,
                     help="V+K bytes per memory wave of the batch64 workload")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-potentials", action="store_true",
+                    help="skip the potential evaluation report (outside the timed region)")
     ap.add_argument("--no-p1", action="store_true",
                     help="skip the piecewise-linear data pipeline report (outside the timed region)")
     return ap.parse_args()
@@ -284,6 +286,56 @@ def _roofline(name, trace_entry, ms_step, n_reg_pairs, q, n_steps):
     return roof
 
 
+def potentials_report(capi, stream, a_, b_):
+    """Times of the single- plus double-layer potential at the 34848 points
+    of the potential benchmark: per-point kernel and the level-block form."""
+    import torch
+    nodes, tris = workloads.cube_mesh(16, lo=-1.0, hi=1.0)
+    T, n, alpha = 1.0, 32, 0.5
+    mesh = capi.Mesh(nodes, tris)
+    prm = capi.stb_default_params(alpha, T, n)
+    pts = workloads.reprsc_points(n, T)
+    P = len(pts) // n
+    rng = np.random.default_rng(1089)
+    w = torch.tensor(rng.normal(size=(1, n, len(tris))), device="cuda")
+    u1 = torch.tensor(rng.normal(size=(1, n, len(nodes))), device="cuda")
+    out = {"workload": "cube (-1,1)^3, 3072 triangles, 32 steps, 1089 points x 32 step midpoints",
+           "q_space": 4}
+    pts_d = torch.tensor(pts, device="cuda")
+    s1 = torch.empty((1, len(pts)), dtype=torch.float64, device="cuda")
+    d1 = torch.empty_like(s1)
+    ws = torch.empty(capi.stb_potentials_workspace_size(mesh, prm, 1, len(pts), 4),
+                     dtype=torch.uint8, device="cuda")
+    capi.stb_potentials(mesh, prm, pts_d, w, u1, 1, s1, d1, ws)
+    a_.record(stream)
+    capi.stb_potentials(mesh, prm, pts_d, w, u1, 1, s1, d1, ws)
+    b_.record(stream)
+    torch.cuda.synchronize()
+    out["per_point_ms"] = a_.elapsed_time(b_)
+    del ws
+    p3 = torch.tensor(pts[:P, :3], device="cuda")
+    s2 = torch.empty((1, n, P), dtype=torch.float64, device="cuda")
+    d2 = torch.empty_like(s2)
+    ws = torch.empty(capi.stb_potentials_grid_workspace_size(mesh, prm, 1, P, 4),
+                     dtype=torch.uint8, device="cuda")
+    eps = 0.5 * T / n
+    capi.stb_potentials_grid(mesh, prm, p3, eps, w, u1, 1, s2, d2, ws)
+    a_.record(stream)
+    capi.stb_potentials_grid(mesh, prm, p3, eps, w, u1, 1, s2, d2, ws)
+    b_.record(stream)
+    torch.cuda.synchronize()
+    out["level_blocks_ms"] = a_.elapsed_time(b_)
+    out["max_rel_diff_between_forms"] = float(max(
+        (s2.reshape(1, -1) - s1).abs().max() / s1.abs().max(),
+        (d2.reshape(1, -1) - d1).abs().max() / d1.abs().max()))
+    evals = float(P) * len(tris) * 16 * n
+    out["level_evaluations_per_s"] = evals / (out["level_blocks_ms"] / 1e3)
+    out["paper_36_threads_s"] = {"single_layer": 0.31, "double_layer": 0.82,
+                                 "note": "Table reprsc, 2 x 18-core Xeon Gold 6240; context"}
+    del ws
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -451,6 +503,14 @@ def run_gpu(args):
               "kernels_ms": {k: v[1] for k, v in tr1.items()}}
         del pp
 
+    # the representation formula's potentials on the workload of the paper's
+    # potential benchmark (Table reprsc: cube (-1,1)^3, 3072 triangles, 32
+    # steps, 33 x 33 points x 32 step midpoints = 34848 points), seeded
+    # densities; both kernels, FP64
+    pots = None
+    if not args.no_potentials:
+        pots = potentials_report(capi, stream, a_, b_)
+
     # end to end through the public API from host buffers (mesh, sources in;
     # solution and error norms out)
     e2e = None
@@ -486,7 +546,7 @@ def run_gpu(args):
                        "l2": "no flush: every step writes %.1f GB of V/K blocks (>> 129 MB L2)"
                              % (2 * (4 if mixed else 8) * n * E * E * len(alphas) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "mixed_vs_fp64": cmp, "p1_data": p1, "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
+            "mixed_vs_fp64": cmp, "p1_data": p1, "potentials": pots, "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
             "rel_l2_error_w": rel_err, "solve": solve_info, "gpu_launches": launches,
             "kernels_ms": {k: v[1] for k, v in trace.items()}, "roofline": roof, "e2e": e2e}
     if rank == 0:

@@ -238,6 +238,47 @@ stb_status stb_dirichlet_rhs_p1(const stb_mesh *mesh, const stb_params *params, 
                                 const double *g1, int32_t nrhs, double *f, void *workspace,
                                 size_t workspace_bytes, stb_stream stream);
 
+/* ---- potentials: the representation formula at points off Gamma (Sec. 3.5) --------
+ * u_h(x,t) = V~ w_h(x,t) - W u_h(x,t) (eq. repr).  points: device FP64
+ * [n_pts][4] = (x1, x2, x3, t) with 0 <= t <= T and x off Gamma_h (a point on
+ * Gamma_h divides by zero); a time outside [0, T] leaves STB_ERR_INVALID_ARG
+ * in the workspace status word and that point's outputs at zero.
+ * w: device FP64 [nrhs][n_steps][E] (piecewise constant, e.g. the solution
+ * of stb_dirichlet_solve); u1: device FP64 [nrhs][n_steps][n_nodes] (piecewise
+ * linear in space, e.g. the data of stb_project_dirichlet_p1).
+ * slp = V~ w_h, dlp = W u_h: device FP64 [nrhs][n_pts]; either may be NULL
+ * (then its density is not read).  With t = t_k + eps, k = min(floor(t/h),
+ * E_t - 1), both are the paper's sums over the past steps of antiderivative
+ * differences (eq. G_dtau, eq. dn_G_dtau and their delta = 0 limits), formed
+ * in FP64 with a q_space x q_space conical rule per triangle
+ * (1 <= q_space <= 5). */
+stb_status stb_potentials_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                         int32_t nrhs, int64_t n_pts, int32_t q_space,
+                                         size_t *bytes);
+stb_status stb_potentials(const stb_mesh *mesh, const stb_params *params, const double *points,
+                          int64_t n_pts, const double *w, const double *u1, int32_t nrhs,
+                          int32_t q_space, double *slp, double *dlp, void *workspace,
+                          size_t workspace_bytes, stb_stream stream);
+/* The same potentials at every step for fixed points: points3 device FP64
+ * [n_pts][3] (n_pts <= 65535 per call), times t_k + eps for k = 0..n_steps-1
+ * with one 0 <= eps <= T/n_steps; slp, dlp: device FP64 [nrhs][n_steps][n_pts].
+ * The antiderivative at level d h + eps does not depend on k, so it is
+ * evaluated once per (point, triangle, rule point, level) into level blocks
+ * of n_steps x n_pts x E (single layer) and n_steps x n_pts x n_nodes (double
+ * layer, accumulated per node with atomics) in the workspace, and the
+ * potentials are block-Toeplitz products of these blocks with the backward
+ * differences of the densities in time (FP64).  Workspace from
+ * stb_potentials_grid_workspace_size (about 8 n_steps n_pts (E + n_nodes)
+ * bytes). */
+stb_status stb_potentials_grid_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                              int32_t nrhs, int64_t n_pts, int32_t q_space,
+                                              size_t *bytes);
+stb_status stb_potentials_grid(const stb_mesh *mesh, const stb_params *params,
+                               const double *points3, int64_t n_pts, double eps, const double *w,
+                               const double *u1, int32_t nrhs, int32_t q_space, double *slp,
+                               double *dlp, void *workspace, size_t workspace_bytes,
+                               stb_stream stream);
+
 /* ---- block-Toeplitz matrix-vector product (eq. V_mat) ---------------------------
  *   y_r^k = beta y_r^k + sum_{d=0}^{k} A^d x_r^{k-d},  k = 0..n_steps-1,
  * A: device [n_steps][E][E] of `a_storage`; x, y: device FP64

@@ -68,6 +68,11 @@ _SIGS = {
     "stb_project_p1_workspace_size": (_I32, [_P, _PAR, _I32, _I32, _I32, _I32, _PSZ]),
     "stb_project_dirichlet_p1": (_I32, [_P, _PAR, _P, _I32, _I32, _I32, _I32, _P, _P, _SZ, _P]),
     "stb_rhs_p1_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
+    "stb_potentials_workspace_size": (_I32, [_P, _PAR, _I32, _I64, _I32, _PSZ]),
+    "stb_potentials": (_I32, [_P, _PAR, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P, _SZ, _P]),
+    "stb_potentials_grid_workspace_size": (_I32, [_P, _PAR, _I32, _I64, _I32, _PSZ]),
+    "stb_potentials_grid": (_I32, [_P, _PAR, _P, _I64, _D, _P, _P, _I32, _I32, _P, _P, _P, _SZ,
+                                   _P]),
     "stb_dirichlet_rhs_p1": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
     "stb_project_dirichlet": (_I32, [_P, _PAR, _P, _I32, _I32, _I32, _I32, _P, _P, _SZ, _P]),
     "stb_toeplitz_workspace_size": (_I32, [_I64, _I32, _I32, _PSZ]),
@@ -261,6 +266,36 @@ def stb_dirichlet_rhs_p1(mesh, params, K1, g1, nrhs, f, workspace, stream=None):
                                            nrhs, _ptr(f), _ptr(workspace),
                                            workspace.numel() * workspace.element_size(),
                                            _stream(stream)), "stb_dirichlet_rhs_p1")
+
+
+def stb_potentials_workspace_size(mesh, params, nrhs, n_pts, q_space=4):
+    return _size(_library().stb_potentials_workspace_size, mesh.handle, ctypes.byref(params), nrhs,
+                 n_pts, q_space)
+
+
+def stb_potentials(mesh, params, points, w, u1, nrhs, slp, dlp, workspace, q_space=4,
+                   stream=None):
+    """points: CUDA float64 [n_pts, 4]; w / u1 / slp / dlp: CUDA tensors or None."""
+    _check(_library().stb_potentials(mesh.handle, ctypes.byref(params), _ptr(points),
+                                     points.shape[0], _ptr(w), _ptr(u1), nrhs, q_space, _ptr(slp),
+                                     _ptr(dlp), _ptr(workspace),
+                                     workspace.numel() * workspace.element_size(),
+                                     _stream(stream)), "stb_potentials")
+
+
+def stb_potentials_grid_workspace_size(mesh, params, nrhs, n_pts, q_space=4):
+    return _size(_library().stb_potentials_grid_workspace_size, mesh.handle, ctypes.byref(params),
+                 nrhs, n_pts, q_space)
+
+
+def stb_potentials_grid(mesh, params, points3, eps, w, u1, nrhs, slp, dlp, workspace, q_space=4,
+                        stream=None):
+    """points3: CUDA float64 [n_pts, 3]; slp / dlp: [nrhs, n_steps, n_pts] or None."""
+    _check(_library().stb_potentials_grid(mesh.handle, ctypes.byref(params), _ptr(points3),
+                                          points3.shape[0], eps, _ptr(w), _ptr(u1), nrhs, q_space,
+                                          _ptr(slp), _ptr(dlp), _ptr(workspace),
+                                          workspace.numel() * workspace.element_size(),
+                                          _stream(stream)), "stb_potentials_grid")
 
 
 def stb_toeplitz_workspace_size(E, n_steps, nrhs):

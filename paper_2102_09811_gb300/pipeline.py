@@ -98,6 +98,24 @@ class DirichletProblem:
         self.error(stream)
         return self.err
 
+    def representation(self, points, q_space=4, stream=None):
+        """u_h = V~ w_h - W g_h at points [n_pts, 4] = (x1, x2, x3, t) inside
+        the domain (eq. repr, Sec. 3.5), after run(); needs data="p1" (the
+        double layer acts on the piecewise-linear Dirichlet data).  Returns
+        a device tensor [nrhs, n_pts]."""
+        if self.data != "p1":
+            raise ValueError("the representation formula needs data='p1'")
+        pts = torch.as_tensor(points, dtype=torch.float64).to(self.device).contiguous()
+        n_pts = pts.shape[0]
+        slp = torch.empty((self.nrhs, n_pts), dtype=torch.float64, device=self.device)
+        dlp = torch.empty_like(slp)
+        ws = _ws(capi.stb_potentials_workspace_size(self.mesh, self.params, self.nrhs, n_pts,
+                                                    q_space), self.device)
+        capi.stb_potentials(self.mesh, self.params, pts, self.w, self.g, self.nrhs, slp, dlp, ws,
+                            q_space, stream)
+        capi.stb_workspace_status(ws, stream)
+        return slp - dlp
+
     def relative_error(self):
         e = self.err.cpu()
         return math.sqrt(float(e[0]) / float(e[1]))

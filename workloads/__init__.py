@@ -144,6 +144,19 @@ def point_source(y, t0=0.0, weight=1.0):
 # points per separated pair), m_ss = 4 (4^4 Gauss points per sub-domain of
 # the regularised rules), projection with a 8x8 conical rule and 16 time points.
 
+def reprsc_points(n_steps=32, T=1.0, n_side=33):
+    """Evaluation points of the potential benchmark (Sec. 6.2, Table reprsc:
+    1089 x 32 = 34848 space-time points): an n_side x n_side grid on the
+    plane x3 = 0 over [-0.5, 0.5]^2, at the midpoint (k + 1/2) h of every
+    step.  Returns [n_side^2 * n_steps, 4] = (x1, x2, x3, t), time-major."""
+    g = np.linspace(-0.5, 0.5, n_side)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    xy = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], axis=1)
+    h = T / n_steps
+    return np.concatenate([np.concatenate([xy, np.full((len(xy), 1), (k + 0.5) * h)], axis=1)
+                           for k in range(n_steps)])
+
+
 def workload(name, alpha=None):
     """Returns dict(nodes, tris, alpha, T, n_steps, sources, name)."""
     if name == "cube192_e16":
