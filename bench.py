@@ -493,14 +493,19 @@ def run_gpu(args):
             p1_ms[label] = a_.elapsed_time(b_)
         capi.stb_trace_enable(False)
         tr1 = capi.stb_trace_read()
-        k1_ms = tr1.get("k_regular_k1_f64", (1, 0.0))[1]
-        evals = float(n_reg_pairs) * 81.0 * (n + 1)
+        kind = "mixed" if "k_regular_k1_mixed" in tr1 else "f64"
+        k1_ms = tr1.get("k_regular_k1_" + kind, (1, 0.0))[1]
         p1 = {"alpha": alphas[0], "stage_ms": p1_ms, "rel_l2_error_w": pp.relative_error(),
-              "k_regular_k1_f64_ms": k1_ms,
-              "k_singular_k1_f64_ms": tr1.get("k_singular_k1_f64", (1, 0.0))[1],
-              "k1_point_level_evals_per_s": evals / (k1_ms / 1e3) if k1_ms else None,
+              "k1_arithmetic": kind, "k_regular_k1_ms": k1_ms,
+              "k_singular_k1_ms": tr1.get("k_singular_k1_" + kind, (1, 0.0))[1],
               "k1_entries": float(n) * E * mesh.n_nodes,
               "kernels_ms": {k: v[1] for k, v in tr1.items()}}
+        if kind == "mixed" and k1_ms:  # one exp2 per node and point, as for V, K
+            ex2 = float(n_reg_pairs) * 81.0 * mixed_nodes_per_point(n)
+            p1["k_regular_k1_tex2_per_s"] = ex2 / (k1_ms / 1e3) / 1e12
+            p1["k_regular_k1_frac_of_mufu_peak"] = p1["k_regular_k1_tex2_per_s"] / MUFU_PEAK_TEX2
+        elif k1_ms:
+            p1["k1_point_level_evals_per_s"] = float(n_reg_pairs) * 81.0 * n / (k1_ms / 1e3)
         del pp
 
     # the representation formula's potentials on the workload of the paper's

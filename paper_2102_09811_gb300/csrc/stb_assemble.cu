@@ -992,14 +992,23 @@ extern "C" stb_status stb_assemble(const stb_mesh *mesh, const stb_params *param
     return run_assembly<float>(m, *params, (float *)V, (float *)K, L, status, s);
 }
 
+// Coordinates of the regularised rules for the mixed piecewise-linear K:
+// (s1, s2, t1, t2) per class 1..3.
+static size_t k1_coords_floats(const stb_params &p) {
+    size_t n = 0;
+    for (int cls = 1; cls <= 3; ++cls) n += 4 * (size_t)ss_rule_size(cls, p.quad_singular);
+    return n;
+}
+
 extern "C" stb_status stb_assemble_k1_workspace_size(const stb_mesh *mesh, const stb_params *params,
                                                      size_t *bytes) {
     if (!mesh || !bytes || !params) return fail(STB_ERR_INVALID_ARG, "mesh, params and bytes must be given");
     stb_status st = check_assembly_params(params);
     if (st) return st;
-    if (params->precision != STB_PREC_FP64)
-        return fail(STB_ERR_INVALID_ARG, "the piecewise-linear double layer is assembled in FP64");
-    *bytes = align256(assembly_layout(mesh->m, *params, nullptr, 0).bytes);
+    if (params->precision == STB_PREC_MIXED && params->storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "mixed precision needs STB_STORE_F32 blocks");
+    *bytes = align256(assembly_layout(mesh->m, *params, nullptr, 0).bytes) +
+             (params->precision == STB_PREC_MIXED ? align256(k1_coords_floats(*params) * 4) : 0);
     return STB_OK;
 }
 
@@ -1015,6 +1024,21 @@ extern "C" stb_status stb_assemble_k1(const stb_mesh *mesh, const stb_params *pa
     AssemblyLayout L = assembly_layout(m, *params, ws, ws_bytes);
     cudaStream_t s = (cudaStream_t)stream;
     STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if (params->precision == STB_PREC_MIXED) {
+        if ((st = prepare_mixed(m, *params, L, status_word(ws), s))) return st;
+        // the rules' coordinates, FP32, behind the assembly layout
+        float *coords = reinterpret_cast<float *>(static_cast<char *>(ws) + align256(L.bytes));
+        std::vector<float> host;
+        std::vector<double> s1, s2, t1, t2, w;
+        for (int cls = 1; cls <= 3; ++cls) {
+            ss_rule(cls, params->quad_singular, s1, s2, t1, t2, w);
+            for (auto *v : {&s1, &s2, &t1, &t2})
+                for (double x : *v) host.push_back((float)x);
+        }
+        STB_CUDA(cudaMemcpyAsync(coords, host.data(), host.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, s));
+        return run_assembly_k1_mixed(m, *params, (float *)K1, L, coords, s);
+    }
     if ((st = prepare_fp64(m, *params, L, status_word(ws), s))) return st;
     if (params->storage == STB_STORE_F64) return run_assembly_k1<double>(m, *params, (double *)K1, L, s);
     return run_assembly_k1<float>(m, *params, (float *)K1, L, s);

@@ -60,6 +60,12 @@ stb_status prepare_fp64(const Mesh &m, const stb_params &p, const AssemblyLayout
 // Mixed path set-up of one problem: tables, geometry, pair classification.
 stb_status prepare_mixed(const Mesh &m, const stb_params &p, const AssemblyLayout &L,
                          int32_t *status, cudaStream_t s);
+// Mixed-precision K with piecewise-linear trial functions into FP32 K1
+// [n_steps][E][n_nodes] (zeroed here, filled with atomics); coords: the
+// regularised rules' coordinates (s1, s2, t1, t2) per class, as FP32, in
+// the order of the difference-form rules.
+stb_status run_assembly_k1_mixed(const Mesh &m, const stb_params &p, float *K1,
+                                 const AssemblyLayout &L, const float *coords, cudaStream_t s);
 stb_status run_assembly_mixed(const Mesh &m, const stb_params &p, void *V, void *K,
                               const AssemblyLayout &L, cudaStream_t s);
 

@@ -676,6 +676,399 @@ stb_status run_assembly_mixed(const Mesh &m, const stb_params &p, void *V, void 
     return run_mixed_t<float>(m, p, (float *)V, (float *)K, L, s);
 }
 
+// ------------------------------ piecewise-linear trial space, mixed ---
+// K_h with nodal hat trial functions (Sec. 3.2) in the forms of the mixed
+// path: the K integrand of a pair weighted by the barycentric coordinates
+// lambda_v of the trial point, added per vertex to K1[d][l][node] with FP32
+// atomics (K1 starts at zero).  Separated pairs: the trial weight and
+// lambda depend only on the trial point b, so the test points a are summed
+// first (one packed FMA per exp2, as for the p0 blocks) and the three
+// vertex weights are applied once per trial point.
+constexpr int K1_G = 4;  // intervals per pass over the points
+
+// F[g][.] += wrn e for K1_G intervals, e = exp2(rr b), nodes packed in pairs
+template <int NG>
+__device__ __forceinline__ void point_nodes_k1(const float *tab, float2 rr2, float2 wrn2,
+                                               float2 (&F)[K1_G][2]) {
+#pragma unroll
+    for (int g = 0; g < K1_G; ++g) {
+        const float4 b = ld_tab<true>(tab + g * (4 + 4 * NG));
+        const float2 t01 = __fmul2_rn(rr2, make_float2(b.x, b.y));
+        F[g][0] = __ffma2_rn(wrn2, make_float2(ex2(t01.x), ex2(t01.y)), F[g][0]);
+        if (NG == 4) {
+            const float2 t23 = __fmul2_rn(rr2, make_float2(b.z, b.w));
+            F[g][1] = __ffma2_rn(wrn2, make_float2(ex2(t23.x), ex2(t23.y)), F[g][1]);
+        } else if (NG == 3) {
+            F[g][1].x = fmaf(wrn2.x, ex2(rr2.x * b.z), F[g][1].x);
+        }
+    }
+}
+
+// Blocks d0..d0+n_int-1 of one separated pair (the intervals k = d0.. of one
+// table chunk, n_int <= MIX_CH), in passes of K1_G intervals; carry[v]: the
+// rising side of interval d0-1 per vertex (scaled), updated to that of the
+// last interval.  Completed blocks go out with atomics.
+template <int NG>
+__device__ __forceinline__ void chunk_k1(const float *tab, int d0, int n_int,
+                                         const float *__restrict__ rule, int nq,
+                                         const float4 *xa, const float (&D)[3],
+                                         const float (&B1)[3], const float (&B2)[3],
+                                         const float (&n)[3], float scale, float (&carry)[3],
+                                         float *__restrict__ out, size_t EN, const int (&tj)[3]) {
+    constexpr int IVF = 4 + 4 * NG;
+    for (int u0 = 0; u0 < n_int; u0 += K1_G) {
+        const float *tg = tab + u0 * IVF;
+        float2 Fv[3][K1_G][2];
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int g = 0; g < K1_G; ++g) Fv[v][g][0] = Fv[v][g][1] = make_float2(0.f, 0.f);
+        for (int b = 0; b < nq; ++b) {
+            const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
+            const float r0b = D[0] - (t1 * B1[0] + t2 * B2[0]);
+            const float r1b = D[1] - (t1 * B1[1] + t2 * B2[1]);
+            const float r2b = D[2] - (t1 * B1[2] + t2 * B2[2]);
+            float2 Fb[K1_G][2];
+#pragma unroll
+            for (int g = 0; g < K1_G; ++g) Fb[g][0] = Fb[g][1] = make_float2(0.f, 0.f);
+            for (int a = 0; a < nq; ++a) {
+                const float4 xq = xa[a];
+                const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
+                const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+                const float wrn = xq.w * (r0 * n[0] + r1 * n[1] + r2 * n[2]);
+                point_nodes_k1<NG>(tg, make_float2(rr, rr), make_float2(wrn, wrn), Fb);
+            }
+            const float lw[3] = {(1.f - t1) * wb, (t1 - t2) * wb, t2 * wb};
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                const float2 l2 = make_float2(lw[v], lw[v]);
+#pragma unroll
+                for (int g = 0; g < K1_G; ++g) {
+                    Fv[v][g][0] = __ffma2_rn(l2, Fb[g][0], Fv[v][g][0]);
+                    Fv[v][g][1] = __ffma2_rn(l2, Fb[g][1], Fv[v][g][1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < K1_G; ++g) {
+            if (u0 + g >= n_int) break;
+            const float *iv = tg + g * IVF;
+            float fall[3] = {0.f, 0.f, 0.f}, rise[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < NG; ++q) {
+                const float4 c = ld_tab<true>(iv + 4 + 4 * q);  // (cVf, cKf, cVr, cKr)
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const float f = (q & 1) ? Fv[v][g][q >> 1].y : Fv[v][g][q >> 1].x;
+                    fall[v] = fmaf(c.y, f, fall[v]);
+                    rise[v] = fmaf(c.w, f, rise[v]);
+                }
+            }
+            float *blk = out + (size_t)(d0 + u0 + g) * EN;
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                atomicAdd(blk + tj[v], fmaf(scale, fall[v], carry[v]));
+                carry[v] = scale * rise[v];
+            }
+        }
+    }
+}
+
+// All blocks of K1 for the separated ordered pair (l, j).
+__device__ __forceinline__ void regular_pair_k1_mixed(const double *__restrict__ geo,
+                                                      const int32_t *__restrict__ tris, int E,
+                                                      int N, const float *__restrict__ rule,
+                                                      int nq, const float4 *xa, const float *nd,
+                                                      int n_steps, const MixConsts &g,
+                                                      float *__restrict__ K1, int l, int j) {
+    const int32_t tl[3] = {tris[3 * l], tris[3 * l + 1], tris[3 * l + 2]};
+    const int tj[3] = {tris[3 * j], tris[3 * j + 1], tris[3 * j + 2]};
+    {
+        bool t = false;
+        for (int i = 0; i < 3; ++i) t |= (tl[i] == tj[0]) | (tl[i] == tj[1]) | (tl[i] == tj[2]);
+        if (t) return;
+    }
+    const double *gl = geo + (size_t)l * GEO_STRIDE, *gj = geo + (size_t)j * GEO_STRIDE;
+    float D[3], B1[3], B2[3], n[3];
+    for (int c = 0; c < 3; ++c) {
+        D[c] = (float)(gl[GEO_V0 + c] - gj[GEO_V0 + c]);
+        B1[c] = (float)(gj[GEO_V1 + c] - gj[GEO_V0 + c]);
+        B2[c] = (float)(gj[GEO_V2 + c] - gj[GEO_V1 + c]);
+        n[c] = (float)gj[GEO_N + c];
+    }
+    const float scale = (float)(4.0 * gl[GEO_AREA] * gj[GEO_AREA]);
+    const size_t EN = (size_t)E * N;
+    float *out = K1 + (size_t)l * N;
+
+    // pass 1: blocks 0 and 1 (closed forms) and the k = 1 interval of block 2
+    float k0[3] = {0.f, 0.f, 0.f}, k1[3] = {0.f, 0.f, 0.f}, k2[3] = {0.f, 0.f, 0.f};
+    for (int b = 0; b < nq; ++b) {
+        const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
+        const float r0b = D[0] - (t1 * B1[0] + t2 * B2[0]);
+        const float r1b = D[1] - (t1 * B1[1] + t2 * B2[1]);
+        const float r2b = D[2] - (t1 * B1[2] + t2 * B2[2]);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        for (int a = 0; a < nq; ++a) {
+            const float4 xq = xa[a];
+            const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
+            const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+            const float irho = rsqrtf(rr), rho = rr * irho;
+            const float wrn = xq.w * (r0 * n[0] + r1 * n[1] + r2 * n[2]);
+            float a0, a1, c0, c1;
+            k_d01(rho, irho, g, a0, a1, c0, c1);
+            s0 = fmaf(wrn, c0, s0);
+            s1 = fmaf(wrn, c1, s1);
+            if (n_steps > 2) {
+#pragma unroll
+                for (int q = 0; q < MIX_NG1; ++q) {
+                    const float4 c = reinterpret_cast<const float4 *>(nd)[q];
+                    s2 = fmaf(wrn * c.z, ex2(rr * c.x), s2);
+                }
+            }
+        }
+        const float lw[3] = {(1.f - t1) * wb, (t1 - t2) * wb, t2 * wb};
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            k0[v] = fmaf(lw[v], s0, k0[v]);
+            k1[v] = fmaf(lw[v], s1, k1[v]);
+            k2[v] = fmaf(lw[v], s2, k2[v]);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        atomicAdd(out + tj[v], scale * k0[v]);
+        if (n_steps > 1) atomicAdd(out + EN + tj[v], scale * k1[v]);
+    }
+    float carry[3] = {scale * k2[0], scale * k2[1], scale * k2[2]};
+    const float *tab = nd + MIX_K1;
+    for (int d0 = 2; d0 < n_steps; d0 += MIX_CH) {
+        const int ng = mixed_chunk_ng(d0), n_int = min(MIX_CH, n_steps - d0);
+        if (ng == 4)
+            chunk_k1<4>(tab, d0, n_int, rule, nq, xa, D, B1, B2, n, scale, carry, out, EN, tj);
+        else if (ng == 3)
+            chunk_k1<3>(tab, d0, n_int, rule, nq, xa, D, B1, B2, n, scale, carry, out, EN, tj);
+        else
+            chunk_k1<2>(tab, d0, n_int, rule, nq, xa, D, B1, B2, n, scale, carry, out, EN, tj);
+        tab += MIX_CH * mixed_iv_floats(ng);
+    }
+}
+
+__global__ void __launch_bounds__(MREG_THREADS)
+k_regular_k1_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E, int N,
+                   const float *__restrict__ rule, int nq, const float *__restrict__ nodes,
+                   int n_nodes_f, int n_steps, MixConsts g, float *__restrict__ K1) {
+    extern __shared__ float smf[];
+    float4 *xa = reinterpret_cast<float4 *>(smf);
+    float *nd = smf + 4 * MAX_RULE_M;
+    const int l = blockIdx.y;
+    const int j = blockIdx.x * MREG_THREADS + threadIdx.x;
+    load_test_points(geo + (size_t)l * GEO_STRIDE, rule, nq, xa);
+    for (int i = threadIdx.x; i < n_nodes_f; i += MREG_THREADS) nd[i] = nodes[i];
+    __syncthreads();
+    if (j < E) regular_pair_k1_mixed(geo, tris, E, N, rule, nq, xa, nd, n_steps, g, K1, l, j);
+}
+
+// Touching pairs: one CTA per unordered pair (a, b), the difference-form
+// rule for r and the rule's coordinates (s1, s2) on a, (t1, t2) on b in the
+// pair's rotated vertex orders for the barycentric weights: entry (a, b) has
+// its trial point on b, entry (b, a) on a.  Identical pairs give zero.
+// Sub-chunks of K1_SCH intervals keep 6 (K1_SCH + 1) sums per thread.
+constexpr int K1_SCH = 8;
+
+struct MixK1Coords {
+    const float *s1[4], *s2[4], *t1[4], *t2[4];
+};
+
+__global__ void __launch_bounds__(MSS_THREADS)
+k_singular_k1_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris,
+                    const TouchPair *__restrict__ pairs, int E, int N, MixSS tab, MixK1Coords co,
+                    const float *__restrict__ nodes, int n_steps, MixConsts g,
+                    float *__restrict__ K1) {
+    constexpr int S = K1_SCH + 1;
+    __shared__ float red[MSS_THREADS / 32][6 * S];
+    __shared__ float fin[6 * S];
+    const TouchPair P = pairs[blockIdx.x];
+    const int a = P.a, b = P.b, cls = P.cls;
+    if (a < 0 || b < a || b >= E || cls < PAIR_VERTEX || cls >= PAIR_IDENTICAL) return;
+    const double *ga = geo + (size_t)a * GEO_STRIDE, *gb = geo + (size_t)b * GEO_STRIDE;
+    const int oa[3] = {P.perm & 3, (P.perm >> 2) & 3, (P.perm >> 4) & 3};
+    const int ob[3] = {(P.perm >> 6) & 3, (P.perm >> 8) & 3, (P.perm >> 10) & 3};
+    float X[4][3], na[3], nb[3];
+    for (int c = 0; c < 3; ++c) {
+        const double A1 = ga[3 * oa[1] + c] - ga[3 * oa[0] + c], A2 = ga[3 * oa[2] + c] - ga[3 * oa[1] + c];
+        const double Bv1 = gb[3 * ob[1] + c] - gb[3 * ob[0] + c], Bv2 = gb[3 * ob[2] + c] - gb[3 * ob[1] + c];
+        if (cls == PAIR_EDGE) {
+            X[0][c] = (float)-A1; X[1][c] = (float)A2; X[2][c] = (float)-Bv2; X[3][c] = 0.f;
+        } else {
+            X[0][c] = (float)A1; X[1][c] = (float)A2; X[2][c] = (float)-Bv1; X[3][c] = (float)-Bv2;
+        }
+        na[c] = (float)ga[GEO_N + c];
+        nb[c] = (float)gb[GEO_N + c];
+    }
+    int nodes_a[3], nodes_b[3];
+    for (int c = 0; c < 3; ++c) {
+        nodes_a[c] = tris[3 * a + oa[c]];
+        nodes_b[c] = tris[3 * b + ob[c]];
+    }
+    const float scale = (float)(4.0 * ga[GEO_AREA] * gb[GEO_AREA]);
+    const int npt = tab.n[cls];
+    const float *R0 = tab.p0[cls], *R1 = tab.p1[cls], *R2 = tab.p2[cls], *R3 = tab.p3[cls],
+                *W = tab.w[cls];
+    const float *S1 = co.s1[cls], *S2 = co.s2[cls], *T1 = co.t1[cls], *T2 = co.t2[cls];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t EN = (size_t)E * N;
+
+    // point p: r^2 and the weights w (r.n_b) lambda_b(t) (entry (a,b)) and
+    // w (r'.n_a) lambda_a(s) (entry (b,a), r' = -r)
+    auto point = [&](int p, float &rr, float (&wab)[3], float (&wba)[3]) {
+        const float q0 = R0[p], q1 = R1[p], q2 = R2[p], q3 = R3[p];
+        float r[3];
+        for (int c = 0; c < 3; ++c) r[c] = q0 * X[0][c] + q1 * X[1][c] + q2 * X[2][c] + q3 * X[3][c];
+        rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        const float w = W[p];
+        const float rab = w * (r[0] * nb[0] + r[1] * nb[1] + r[2] * nb[2]);
+        const float rba = -w * (r[0] * na[0] + r[1] * na[1] + r[2] * na[2]);
+        const float s1 = S1[p], s2 = S2[p], t1 = T1[p], t2 = T2[p];
+        wab[0] = rab * (1.f - t1); wab[1] = rab * (t1 - t2); wab[2] = rab * t2;
+        wba[0] = rba * (1.f - s1); wba[1] = rba * (s1 - s2); wba[2] = rba * s2;
+    };
+    auto reduce = [&](float *vals, int nv) {
+        for (int k = 0; k < nv; ++k) {
+            float v = vals[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < nv) {
+            float sum = 0.f;
+            for (int wi = 0; wi < MSS_THREADS / 32; ++wi) sum += red[wi][threadIdx.x];
+            fin[threadIdx.x] = scale * sum;
+        }
+        __syncthreads();
+    };
+    // entry e (0..2: (a,b) at node nodes_b[e]; 3..5: (b,a) at node nodes_a[e-3])
+    auto emit = [&](int d, int e, float val) {
+        float *blk = K1 + (size_t)d * EN;
+        if (e < 3)
+            atomicAdd(blk + (size_t)a * N + nodes_b[e], val);
+        else
+            atomicAdd(blk + (size_t)b * N + nodes_a[e - 3], val);
+    };
+
+    // pass 1: blocks 0, 1 and the k = 1 interval of block 2 (18 sums)
+    float z[18];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) z[i] = 0.f;
+    for (int p = threadIdx.x; p < npt; p += MSS_THREADS) {
+        float rr, wab[3], wba[3];
+        point(p, rr, wab, wba);
+        const float irho = rsqrtf(rr), rho = rr * irho;
+        float a0, a1, c0, c1;
+        k_d01(rho, irho, g, a0, a1, c0, c1);
+        float c2 = 0.f;
+        if (n_steps > 2) {
+#pragma unroll
+            for (int q = 0; q < MIX_NG1; ++q) {
+                const float4 c = reinterpret_cast<const float4 *>(nodes)[q];
+                c2 = fmaf(c.z, ex2(rr * c.x), c2);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            z[v] = fmaf(wab[v], c0, z[v]);
+            z[3 + v] = fmaf(wba[v], c0, z[3 + v]);
+            z[6 + v] = fmaf(wab[v], c1, z[6 + v]);
+            z[9 + v] = fmaf(wba[v], c1, z[9 + v]);
+            z[12 + v] = fmaf(wab[v], c2, z[12 + v]);
+            z[15 + v] = fmaf(wba[v], c2, z[15 + v]);
+        }
+    }
+    reduce(z, 18);
+    if (threadIdx.x == 0) {
+        for (int e = 0; e < 6; ++e) {
+            emit(0, e, fin[e]);
+            if (n_steps > 1) emit(1, e, fin[6 + e]);
+        }
+    }
+    float carry[6];
+    for (int e = 0; e < 6; ++e) carry[e] = fin[12 + e];
+    __syncthreads();
+
+    const float *ntab = nodes + MIX_K1;
+    for (int d0 = 2; d0 < n_steps; d0 += MIX_CH) {
+        const int ng = mixed_chunk_ng(d0), ivf = mixed_iv_floats(ng);
+        for (int h0 = 0; h0 < MIX_CH && d0 + h0 < n_steps; h0 += K1_SCH) {
+            const int n_int = min(K1_SCH, n_steps - d0 - h0);
+            float acc[6 * S];
+#pragma unroll
+            for (int i = 0; i < 6 * S; ++i) acc[i] = 0.f;
+            const float *tb = ntab + h0 * ivf;
+            for (int p = threadIdx.x; p < npt; p += MSS_THREADS) {
+                float rr, wab[3], wba[3];
+                point(p, rr, wab, wba);
+                const float2 rr2[1] = {make_float2(rr, rr)};
+#pragma unroll
+                for (int u = 0; u < K1_SCH; ++u) {
+                    if (u >= n_int) break;
+                    float2 fall[1], rise[1];
+                    if (ng == 4) interval_sums<4, 1, false>(tb + u * ivf, rr2, fall, rise);
+                    else if (ng == 3) interval_sums<3, 1, false>(tb + u * ivf, rr2, fall, rise);
+                    else interval_sums<2, 1, false>(tb + u * ivf, rr2, fall, rise);
+#pragma unroll
+                    for (int v = 0; v < 3; ++v) {
+                        acc[v * S + u] = fmaf(wab[v], fall[0].y, acc[v * S + u]);
+                        acc[v * S + u + 1] = fmaf(wab[v], rise[0].y, acc[v * S + u + 1]);
+                        acc[(3 + v) * S + u] = fmaf(wba[v], fall[0].y, acc[(3 + v) * S + u]);
+                        acc[(3 + v) * S + u + 1] = fmaf(wba[v], rise[0].y, acc[(3 + v) * S + u + 1]);
+                    }
+                }
+            }
+            reduce(acc, 6 * S);
+            if (threadIdx.x == 0) {
+                for (int u = 0; u < n_int; ++u)
+                    for (int e = 0; e < 6; ++e)
+                        emit(d0 + h0 + u, e, fin[e * S + u] + (u == 0 ? carry[e] : 0.f));
+            }
+            for (int e = 0; e < 6; ++e) carry[e] = fin[e * S + n_int];
+            __syncthreads();
+        }
+        ntab += MIX_CH * ivf;
+    }
+}
+
+stb_status run_assembly_k1_mixed(const Mesh &m, const stb_params &p, float *K1,
+                                 const AssemblyLayout &L, const float *coords, cudaStream_t s) {
+    const int E = (int)m.n_tris, N = (int)m.n_nodes;
+    const int nq = p.quad_regular * p.quad_regular;
+    const MixConsts g = mix_consts(p);
+    const int nf = (int)mixed_node_floats(p.n_steps);
+    STB_CUDA(cudaMemsetAsync(K1, 0, sizeof(float) * (size_t)p.n_steps * E * N, s));
+    const size_t smem = sizeof(float) * (4 * MAX_RULE_M + (size_t)nf);
+    STB_CUDA(cudaFuncSetAttribute(k_regular_k1_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    dim3 grid((E + MREG_THREADS - 1) / MREG_THREADS, E);
+    count_launch(s);
+    k_regular_k1_mixed<<<grid, MREG_THREADS, smem, s>>>(L.geo, m.d_tris, E, N, L.mrule, nq,
+                                                         L.mnodes, nf, p.n_steps, g, K1);
+    stb_status st = check_launch("k_regular_k1_mixed");
+    if (st || m.n_touch == 0) return st;
+    const MixSS tab = mix_ss(L);
+    MixK1Coords co{};
+    const float *base = coords;
+    for (int cls = 1; cls <= 3; ++cls) {
+        const size_t n = L.ss_n[cls];
+        co.s1[cls] = base;
+        co.s2[cls] = base + n;
+        co.t1[cls] = base + 2 * n;
+        co.t2[cls] = base + 3 * n;
+        base += 4 * n;
+    }
+    count_launch(s);
+    k_singular_k1_mixed<<<(unsigned)m.n_touch, MSS_THREADS, 0, s>>>(
+        L.geo, m.d_tris, L.pairs, E, N, tab, co, L.mnodes, p.n_steps, g, K1);
+    return check_launch("k_singular_k1_mixed");
+}
+
 // -------------------------------------------------------------- batches ---
 // Many independent problems (meshes, alpha, steps) in one persistent launch
 // for their separated pairs and one launch for their touching pairs, all in

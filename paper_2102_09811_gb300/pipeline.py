@@ -22,8 +22,8 @@ class DirichletProblem:
     sources: numpy [nrhs, n_src, 5] of (y1, y2, y3, t0, weight).
     data: "p0" projects the Dirichlet datum into piecewise constants in space
     (K_h with E x E blocks); "p1" into the continuous piecewise-linear space
-    X_h^{1,0} (Sec. 3.2, Sec. 3.4: K_h with E x n_nodes blocks, assembled in
-    FP64 arithmetic; the p0 x p1 mass in the right-hand side).
+    X_h^{1,0} (Sec. 3.2, Sec. 3.4: K_h with E x n_nodes blocks; the p0 x p1
+    mass in the right-hand side).
     """
 
     def __init__(self, nodes, tris, alpha, T, n_steps, sources, quad_regular=3, quad_singular=4,
@@ -52,8 +52,11 @@ class DirichletProblem:
         m, p = self.mesh, self.params
         self.ws_assemble = _ws(capi.stb_assemble_workspace_size(m, p), dev)
         if data == "p1":
+            # K1 in mixed precision where its FP32 storage allows, else FP64
+            k1_prec = (capi.STB_PREC_MIXED if precision == capi.STB_PREC_MIXED and
+                       storage == capi.STB_STORE_F32 else capi.STB_PREC_FP64)
             self.params_k1 = capi.stb_default_params(alpha, T, n_steps, quad_regular, quad_singular,
-                                                     precision=capi.STB_PREC_FP64, storage=storage)
+                                                     precision=k1_prec, storage=storage)
             self.ws_k1 = _ws(capi.stb_assemble_k1_workspace_size(m, self.params_k1), dev)
             self.ws_project = _ws(capi.stb_project_p1_workspace_size(m, p, self.nrhs, self.n_src,
                                                                      q_space, n_time), dev)

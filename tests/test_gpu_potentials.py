@@ -226,7 +226,7 @@ def _repr_rows():
     return test_oracle_potentials.load_repr_golden(), test_oracle_potentials.repr_points()
 
 
-@pytest.mark.parametrize("row", [0, 1, 2])
+@pytest.mark.parametrize("row", [0, 1, 2, pytest.param(3, marks=pytest.mark.slow)])
 def test_table_dirconv_representation_on_gpu(row):
     """Table dirconv, representation column (cube (-1,1)^3, alpha = 0.5,
     source (0,0,1.5), p1 data, w_h computed): u_h = V~ w_h - W g_h at the
