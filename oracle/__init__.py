@@ -78,6 +78,13 @@ def lib():
         L.orc_project_dirichlet_p1.argtypes = [_P, _I64, _P, _I64, _D, _D, _I32,
                                                _P, _I32, _I32, _I32, _I32, _P]
         L.orc_toeplitz_matvec_rect.argtypes = [_P, _I64, _I64, _I32, _I32, _P, _P]
+        L.orc_assemble_d2_tris.argtypes = [_P, _I64, _P, _I64, _D, _D, _I32, _I32, _I32, _P,
+                                           _I64, _P]
+        L.orc_surface_curls.argtypes = [_P, _I64, _P, _I64, _P]
+        L.orc_assemble_d1.argtypes = [_P, _I64, _P, _I64, _D, _I32, _P, _P]
+        L.orc_neumann_rhs.argtypes = [_P, _P, _P, _I64, _I64, _D, _I32, _I32, _P, _P]
+        L.orc_dirichlet_error_p1.argtypes = [_P, _I64, _P, _I64, _D, _D, _I32, _P, _I32, _I32,
+                                             _P, _I32, _I32, _P, _P]
         L.orc_potentials.argtypes = [_P, _I64, _P, _I64, _D, _D, _I32, _P, _P, _I32, _P, _I64,
                                      _I32, _P, _P]
         L.orc_dirichlet_rhs_p1.argtypes = [_P, _P, _P, _I64, _I64, _D, _I32, _I32, _P, _P]
@@ -366,3 +373,58 @@ def potentials(nodes, tris, alpha, T, n_steps, points, w=None, u1=None, q=4):
                                 None if slp is None else _p(slp),
                                 None if dlp is None else _p(dlp)), "potentials")
     return slp, dlp
+
+
+# ---- hypersingular operator and the Neumann problem (Sec. 3.3, Sec. 3.4) ------
+def assemble_d2(nodes, tris, alpha, T, n_steps, test_tris=None, q_reg=3, m_ss=4):
+    """D^2 blocks [n_steps, N, N] from the pairs of the given test triangles
+    (all by default) with every trial triangle."""
+    nodes, tris = _f64(nodes), _i32(tris)
+    E, N = tris.shape[0], nodes.shape[0]
+    rows = np.arange(E) if test_tris is None else np.asarray(test_tris)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    D2 = np.zeros((n_steps, N, N))
+    _check(lib().orc_assemble_d2_tris(_p(nodes), N, _p(tris), E, alpha, T, n_steps, q_reg, m_ss,
+                                      _p(rows), rows.shape[0], _p(D2)), "assemble_d2_tris")
+    return D2
+
+
+def surface_curls(nodes, tris):
+    """[E, 3, 3]: surface curl of the hat function of vertex v on triangle m."""
+    nodes, tris = _f64(nodes), _i32(tris)
+    out = np.zeros((tris.shape[0], 3, 3))
+    _check(lib().orc_surface_curls(_p(nodes), nodes.shape[0], _p(tris), tris.shape[0], _p(out)),
+           "surface_curls")
+    return out
+
+
+def assemble_d1(nodes, tris, alpha, V):
+    """D^1 = T^T (alpha^2 V^d (x) I_3) T from V [n_steps, E, E]: [n_steps, N, N]."""
+    nodes, tris, V = _f64(nodes), _i32(tris), _f64(V)
+    n_steps, N = V.shape[0], nodes.shape[0]
+    D1 = np.zeros((n_steps, N, N))
+    _check(lib().orc_assemble_d1(_p(nodes), N, _p(tris), tris.shape[0], alpha, n_steps, _p(V),
+                                 _p(D1)), "assemble_d1")
+    return D1
+
+
+def neumann_rhs(area, tris, K1, hd, T):
+    """(1/2 M_h^{T_x} - K_h^{T_x}) h: [nrhs, n_steps, N]."""
+    area, tris, K1, hd = _f64(area), _i32(tris), _f64(K1), _f64(hd)
+    n_steps, E, N = K1.shape
+    f = np.zeros((hd.shape[0], n_steps, N))
+    _check(lib().orc_neumann_rhs(_p(area), _p(tris), _p(K1), E, N, T, n_steps, hd.shape[0],
+                                 _p(hd), _p(f)), "neumann_rhs")
+    return f
+
+
+def dirichlet_error_p1(nodes, tris, alpha, T, n_steps, sources, u1, q_space=8, n_time=16):
+    """(err2, ref2) of piecewise-linear Dirichlet data u1 [nrhs, n_steps, N]."""
+    nodes, tris, src, u1 = _f64(nodes), _i32(tris), _f64(sources), _f64(u1)
+    e2, r2 = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().orc_dirichlet_error_p1(_p(nodes), nodes.shape[0], _p(tris), tris.shape[0], alpha,
+                                        T, n_steps, _p(src), src.shape[1], src.shape[0], _p(u1),
+                                        q_space, n_time, ctypes.byref(e2), ctypes.byref(r2)),
+           "dirichlet_error_p1")
+    return e2.value, r2.value
+

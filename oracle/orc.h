@@ -128,6 +128,28 @@ int orc_dirichlet_rhs_p1(const double *area, const int32_t *tris, const double *
                          int64_t E, int64_t N, double T, int32_t n_steps, int32_t nrhs,
                          const double *g1, double *f);
 
+/* ---- hypersingular operator and the Neumann problem (Sec. 3.3, Sec. 3.4) ----
+ * D_h = D_h^1 + D_h^2, blocks [n_steps][N][N]: D2 from the test triangles
+ * test_tris (added into D2), D1 = T^T (alpha^2 V^d (x) I_3) T from the
+ * single-layer blocks V [n_steps][E][E] (overwritten), the surface curls of
+ * the hat functions curl [E][3 vertices][3]; the Neumann right-hand side
+ * (1/2 M_h^{T_x} - K_h^{T_x}) h (h [nrhs][n_steps][E] -> f [nrhs][n_steps][N])
+ * and the L2(Sigma_h) error of piecewise-linear Dirichlet data.            */
+int orc_assemble_d2_tris(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                         double alpha, double T, int32_t n_steps, int32_t q_reg, int32_t m_ss,
+                         const int64_t *test_tris, int64_t n_test, double *D2);
+int orc_surface_curls(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                      double *curl);
+int orc_assemble_d1(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                    double alpha, int32_t n_steps, const double *V, double *D1);
+int orc_neumann_rhs(const double *area, const int32_t *tris, const double *K1, int64_t E,
+                    int64_t N, double T, int32_t n_steps, int32_t nrhs, const double *hd,
+                    double *f);
+int orc_dirichlet_error_p1(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                           double alpha, double T, int32_t n_steps, const double *sources,
+                           int32_t n_src, int32_t nrhs, const double *u1, int32_t q_space,
+                           int32_t n_time, double *err2, double *ref2);
+
 /* ---- potentials: the discretised representation formula (Sec. 3.5) --------
  * At points (x, t) off Gamma_h, points [n_pts][4] = (x1, x2, x3, t),
  * 0 <= t <= T: slp [nrhs][n_pts] = V~ w_h (w [nrhs][n_steps][E], piecewise

@@ -116,6 +116,9 @@ typedef struct {
      * triangle and the nodes they belong to (piecewise linear trial space) */
     double *lam[3];
     int32_t node[3];
+    /* optional (lamx[0] != NULL): the same for x in the test triangle */
+    double *lamx[3];
+    int32_t nodex[3];
 } pair_points;
 
 typedef struct {
@@ -194,10 +197,17 @@ static void pair_points_build(const rules *R, const double *nodes,
                     pp->lam[1][k] = R->rs1[b] - R->rs2[b];
                     pp->lam[2][k] = R->rs2[b];
                 }
+                if (pp->lamx[0]) {
+                    pp->lamx[0][k] = 1.0 - R->rs1[a];
+                    pp->lamx[1][k] = R->rs1[a] - R->rs2[a];
+                    pp->lamx[2][k] = R->rs2[a];
+                }
                 ++k;
             }
-        for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < 3; ++c) {
             pp->node[c] = tj[c];
+            pp->nodex[c] = tl[c];
+        }
     } else {
         const double *Pa[3], *Pb[3];
         for (int c = 0; c < 3; ++c) {
@@ -223,10 +233,18 @@ static void pair_points_build(const rules *R, const double *nodes,
                 pp->lam[1][k] = u1 - u2;
                 pp->lam[2][k] = u2;
             }
+            if (pp->lamx[0]) { /* x on a (coordinates t0, t1) when l = a, else on b */
+                double u1 = l == ia ? t[0][q] : t[2][q], u2 = l == ia ? t[1][q] : t[3][q];
+                pp->lamx[0][k] = 1.0 - u1;
+                pp->lamx[1][k] = u1 - u2;
+                pp->lamx[2][k] = u2;
+            }
             ++k;
         }
-        for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < 3; ++c) {
             pp->node[c] = l == ia ? tb[ob[c]] : ta[oa[c]];
+            pp->nodex[c] = l == ia ? ta[oa[c]] : tb[ob[c]];
+        }
     }
     pp->n = k;
 }
@@ -468,3 +486,176 @@ done:
     free(normal);
     return rc;
 }
+
+/* ---- hypersingular operator (Sec. 3.3) -------------------------------------
+ * D_h = D_h^1 + D_h^2 on X_h^{1,0} x X_h^{1,0}, blocks [n_steps][N][N].
+ *
+ * D^{2,d}[i][j] = int int n_x . n_y phi_i(x) phi_j(y) D^{2,d}(x - y) with
+ *   D^{2,0}(r) = alpha [G^{dtau}(r, 0) - G^{dtau}(r, h)],
+ *   D^{2,d}(r) = alpha [2 G^{dtau}(r, dh) - G^{dtau}(r, (d+1)h) - G^{dtau}(r, (d-1)h)]
+ * (eq. D2d with G^{dt} = -G^{dtau}; the delta = 0 value is the limit of
+ * eq. G_dtau_lim_d), integrated by the same rules as V.  The test
+ * triangles test_tris[0..n_test) add their pairs with every trial triangle
+ * into D2 (not zeroed here), so that rows of triangles can be split across
+ * threads and summed.                                                      */
+int orc_assemble_d2_tris(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                         double alpha, double T, int32_t n_steps, int32_t q_reg, int32_t m_ss,
+                         const int64_t *test_tris, int64_t n_test, double *D2)
+{
+    if (E < 1 || n_nodes < 3 || n_steps < 1 || !(alpha > 0.0) || !(T > 0.0) || n_test < 0)
+        return -1;
+    for (int64_t r = 0; r < n_test; ++r)
+        if (test_tris[r] < 0 || test_tris[r] >= E)
+            return -1;
+    rules R;
+    double *area = NULL, *normal = NULL;
+    int rc = -1;
+    if (rules_init(&R, q_reg, m_ss))
+        goto done;
+    if (geometry_alloc(nodes, n_nodes, tris, E, &area, &normal))
+        goto done;
+    double h = T / n_steps;
+    int nmax = R.nreg * R.nreg;
+    for (int c = 1; c <= 3; ++c)
+        if (R.nss[c] > nmax)
+            nmax = R.nss[c];
+    pair_points pp;
+    memset(&pp, 0, sizeof pp);
+    pp.rho = malloc(sizeof(double) * nmax);
+    pp.rn = malloc(sizeof(double) * nmax);
+    pp.w = malloc(sizeof(double) * nmax);
+    for (int v = 0; v < 3; ++v) {
+        pp.lam[v] = malloc(sizeof(double) * nmax);
+        pp.lamx[v] = malloc(sizeof(double) * nmax);
+    }
+    const int64_t NN = n_nodes * n_nodes;
+    for (int64_t r = 0; r < n_test; ++r) {
+        int64_t l = test_tris[r];
+        for (int64_t j = 0; j < E; ++j) {
+            pair_points_build(&R, nodes, tris, area, normal, l, j, &pp);
+            const double nn = normal[3 * l] * normal[3 * j] + normal[3 * l + 1] * normal[3 * j + 1] +
+                              normal[3 * l + 2] * normal[3 * j + 2];
+            for (int i_t = 0; i_t <= n_steps; ++i_t) {
+                /* S[a][b] = sum_q w_q lam_a(x_q) lam_b(y_q) G^{dtau}(rho_q, i_t h) */
+                double S[3][3] = {{0}};
+                for (int q = 0; q < pp.n; ++q) {
+                    double g = pp.w[q] * orc_G_dtau(pp.rho[q], i_t * h, alpha);
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b)
+                            S[a][b] += pp.lamx[a][q] * pp.lam[b][q] * g;
+                }
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        double v = alpha * nn * S[a][b];
+                        int64_t ij = (int64_t)pp.nodex[a] * n_nodes + pp.node[b];
+                        /* level i_t feeds d = i_t (+2, or +1 for i_t = 0), d = i_t - 1
+                         * and d = i_t + 1 (-1 each) */
+                        if (i_t == 0) {
+                            D2[ij] += v;
+                        } else if (i_t < n_steps) {
+                            D2[(int64_t)i_t * NN + ij] += 2.0 * v;
+                        }
+                        if (i_t >= 1)
+                            D2[(int64_t)(i_t - 1) * NN + ij] -= v;
+                        if (i_t + 1 < n_steps)
+                            D2[(int64_t)(i_t + 1) * NN + ij] -= v;
+                    }
+            }
+        }
+    }
+    free(pp.rho);
+    free(pp.rn);
+    free(pp.w);
+    for (int v = 0; v < 3; ++v) {
+        free(pp.lam[v]);
+        free(pp.lamx[v]);
+    }
+    rc = 0;
+done:
+    rules_free(&R);
+    free(area);
+    free(normal);
+    return rc;
+}
+
+/* Surface curls of the hat functions, constant on each triangle:
+ * curl phi_v = n x grad phi_v with grad phi_v = n x (P_{v+2} - P_{v+1}) / (2 Delta)
+ * (the in-plane normal of the opposite edge, pointing to P_v, of length
+ * 1 / height); curl[(3 m + v) * 3 + o] for vertex v of triangle m. */
+int orc_surface_curls(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                      double *curl)
+{
+    double *area = NULL, *normal = NULL;
+    if (geometry_alloc(nodes, n_nodes, tris, E, &area, &normal)) {
+        free(area);
+        free(normal);
+        return -1;
+    }
+    for (int64_t m = 0; m < E; ++m) {
+        const double *n = normal + 3 * m;
+        for (int v = 0; v < 3; ++v) {
+            const double *A = nodes + 3 * tris[3 * m + (v + 1) % 3];
+            const double *B = nodes + 3 * tris[3 * m + (v + 2) % 3];
+            double e[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]}, g[3];
+            g[0] = (n[1] * e[2] - n[2] * e[1]) / (2.0 * area[m]);
+            g[1] = (n[2] * e[0] - n[0] * e[2]) / (2.0 * area[m]);
+            g[2] = (n[0] * e[1] - n[1] * e[0]) / (2.0 * area[m]);
+            double *c = curl + (3 * m + v) * 3;
+            c[0] = n[1] * g[2] - n[2] * g[1];
+            c[1] = n[2] * g[0] - n[0] * g[2];
+            c[2] = n[0] * g[1] - n[1] * g[0];
+        }
+    }
+    free(area);
+    free(normal);
+    return 0;
+}
+
+/* D^{1,d} = T^T (alpha^2 V^d (x) I_3) T (eq. D_1_sp_trafo), T_o[m][j] the
+ * o-th component of the surface curl of phi_j on triangle m; V [n_steps][E][E]
+ * the single-layer blocks.  D1 [n_steps][N][N] is overwritten.             */
+int orc_assemble_d1(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                    double alpha, int32_t n_steps, const double *V, double *D1)
+{
+    if (E < 1 || n_nodes < 3 || n_steps < 1)
+        return -1;
+    double *curl = malloc(sizeof(double) * 9 * E);
+    double *Tm = calloc((size_t)3 * E * n_nodes, sizeof(double)); /* T [3][E][N] */
+    double *W = malloc(sizeof(double) * 3 * E * n_nodes);          /* V T_o      */
+    int rc = -1;
+    if (!curl || !Tm || !W || orc_surface_curls(nodes, n_nodes, tris, E, curl))
+        goto done;
+    for (int64_t m = 0; m < E; ++m)
+        for (int v = 0; v < 3; ++v)
+            for (int o = 0; o < 3; ++o)
+                Tm[((int64_t)o * E + m) * n_nodes + tris[3 * m + v]] += curl[(3 * m + v) * 3 + o];
+    const int64_t NN = n_nodes * n_nodes, EE = E * E;
+    for (int d = 0; d < n_steps; ++d) {
+        const double *Vd = V + d * EE;
+        for (int o = 0; o < 3; ++o)
+            for (int64_t nn = 0; nn < E; ++nn)
+                for (int64_t j = 0; j < n_nodes; ++j) {
+                    double acc = 0.0;
+                    for (int64_t m = 0; m < E; ++m)
+                        acc += Vd[nn * E + m] * Tm[((int64_t)o * E + m) * n_nodes + j];
+                    W[((int64_t)o * E + nn) * n_nodes + j] = acc;
+                }
+        double *Dd = D1 + d * NN;
+        for (int64_t i = 0; i < n_nodes; ++i)
+            for (int64_t j = 0; j < n_nodes; ++j) {
+                double acc = 0.0;
+                for (int o = 0; o < 3; ++o)
+                    for (int64_t nn = 0; nn < E; ++nn)
+                        acc += Tm[((int64_t)o * E + nn) * n_nodes + i] *
+                               W[((int64_t)o * E + nn) * n_nodes + j];
+                Dd[i * n_nodes + j] = alpha * alpha * acc;
+            }
+    }
+    rc = 0;
+done:
+    free(curl);
+    free(Tm);
+    free(W);
+    return rc;
+}
+

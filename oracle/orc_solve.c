@@ -446,3 +446,93 @@ int orc_dirichlet_rhs_p1(const double *area, const int32_t *tris, const double *
             }
     return 0;
 }
+
+/* ---- Neumann problem (Sec. 3.4) -------------------------------------------
+ * Right-hand side of D_h u = (1/2 M_h^{T_x} - K_h^{T_x}) h with h in X_h^{0,0}
+ * ([nrhs][n_steps][E]), K1 [n_steps][E][N] the piecewise-linear double layer
+ * and M_h^{T_x} the blockwise transpose of the p0 x p1 mass:
+ *   f_k[i] = (h_t / 2) sum_{l : i in l} Delta_l / 3 h_{k,l}
+ *            - sum_{d=0}^{k} sum_l K1^d[l][i] h_{k-d,l},
+ * f [nrhs][n_steps][N].                                                     */
+int orc_neumann_rhs(const double *area, const int32_t *tris, const double *K1, int64_t E,
+                    int64_t N, double T, int32_t n_steps, int32_t nrhs, const double *hd,
+                    double *f)
+{
+    if (E < 1 || N < 1 || n_steps < 1 || nrhs < 1)
+        return -1;
+    double ht = T / n_steps;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k) {
+            double *fk = f + ((int64_t)r * n_steps + k) * N;
+            for (int64_t i = 0; i < N; ++i)
+                fk[i] = 0.0;
+            const double *hk = hd + ((int64_t)r * n_steps + k) * E;
+            for (int64_t l = 0; l < E; ++l)
+                for (int v = 0; v < 3; ++v)
+                    fk[tris[3 * l + v]] += 0.5 * ht * area[l] / 3.0 * hk[l];
+            for (int d = 0; d <= k; ++d) {
+                const double *Kd = K1 + (int64_t)d * E * N;
+                const double *hv = hd + ((int64_t)r * n_steps + (k - d)) * E;
+                for (int64_t l = 0; l < E; ++l)
+                    for (int64_t i = 0; i < N; ++i)
+                        fk[i] -= Kd[l * N + i] * hv[l];
+            }
+        }
+    return 0;
+}
+
+/* Error of piecewise-linear Dirichlet data u1 [nrhs][n_steps][N] against the
+ * exterior-source datum g (Sec. 6.1): err2 = sum_r ||g_r - u_h,r||^2 and
+ * ref2 = sum_r ||g_r||^2 in L2(Sigma_h), u_h(x, t) = sum_v lambda_v(x)
+ * u1_{k, node v} on step k, by the q_space x q_space conical rule and n_time
+ * Gauss points per step.                                                    */
+int orc_dirichlet_error_p1(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                           double alpha, double T, int32_t n_steps, const double *sources,
+                           int32_t n_src, int32_t nrhs, const double *u1, int32_t q_space,
+                           int32_t n_time, double *err2, double *ref2)
+{
+    if (E < 1 || n_steps < 1 || nrhs < 1 || q_space < 1 || q_space > 32 || n_time < 1 ||
+        n_time > 64)
+        return -1;
+    int nq = q_space * q_space;
+    double *s1 = malloc(sizeof(double) * nq), *s2 = malloc(sizeof(double) * nq);
+    double *sw = malloc(sizeof(double) * nq), tx[64], tw[64];
+    double *area = malloc(sizeof(double) * E), *normal = malloc(sizeof(double) * 3 * E);
+    int rc = -1;
+    if (orc_triangle_rule(q_space, s1, s2, sw) || orc_gauss_legendre01(n_time, tx, tw) ||
+        orc_triangle_geometry(nodes, n_nodes, tris, E, area, normal))
+        goto done;
+    double h = T / n_steps, e2 = 0.0, r2 = 0.0;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k)
+            for (int64_t j = 0; j < E; ++j) {
+                const int32_t *t3 = tris + 3 * j;
+                const double *uk = u1 + ((int64_t)r * n_steps + k) * n_nodes;
+                double ae = 0.0, ar = 0.0;
+                for (int a = 0; a < nq; ++a) {
+                    double x[3];
+                    chi_plain(nodes + 3 * t3[0], nodes + 3 * t3[1], nodes + 3 * t3[2],
+                              s1[a], s2[a], x);
+                    double uh = (1.0 - s1[a]) * uk[t3[0]] + (s1[a] - s2[a]) * uk[t3[1]] +
+                                s2[a] * uk[t3[2]];
+                    for (int b = 0; b < n_time; ++b) {
+                        double g = dirichlet_datum(sources + (int64_t)r * n_src * 5, n_src, alpha,
+                                                   x, (k + tx[b]) * h);
+                        ae += sw[a] * tw[b] * (g - uh) * (g - uh);
+                        ar += sw[a] * tw[b] * g * g;
+                    }
+                }
+                e2 += 2.0 * area[j] * h * ae;
+                r2 += 2.0 * area[j] * h * ar;
+            }
+    *err2 = e2;
+    *ref2 = r2;
+    rc = 0;
+done:
+    free(s1);
+    free(s2);
+    free(sw);
+    free(area);
+    free(normal);
+    return rc;
+}

@@ -25,9 +25,15 @@ import itertools
 import numpy as np
 
 
-def cube_mesh(n, lo=0.0, hi=1.0):
+def cube_mesh(n, lo=0.0, hi=1.0, diagonal="main"):
+    """Surface of the cube [lo, hi]^3, n x n squares per face, each split in
+    two triangles along the diagonal from local (0,0) to (1,1) ("main"), from
+    (1,0) to (0,1) ("anti"), or alternating between the two in a checkerboard
+    ("alternating"); counter-clockwise seen from outside."""
     if n < 1:
         raise ValueError("n must be >= 1")
+    if diagonal not in ("main", "anti", "alternating"):
+        raise ValueError("diagonal must be main, anti or alternating")
     h = (hi - lo) / n
     index = {}
     nodes = []
@@ -54,8 +60,12 @@ def cube_mesh(n, lo=0.0, hi=1.0):
                         p[t2] = k + dk
                         return node(p)
                     p00, p10, p11, p01 = corner(0, 0), corner(1, 0), corner(1, 1), corner(0, 1)
-                    tris.append([p00, p10, p11])
-                    tris.append([p00, p11, p01])
+                    if diagonal == "main" or (diagonal == "alternating" and (i + k) % 2 == 0):
+                        tris.append([p00, p10, p11])
+                        tris.append([p00, p11, p01])
+                    else:
+                        tris.append([p00, p10, p01])
+                        tris.append([p10, p11, p01])
     return np.asarray(nodes, dtype=np.float64), np.asarray(tris, dtype=np.int32)
 
 
