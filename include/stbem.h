@@ -279,6 +279,52 @@ stb_status stb_potentials_grid(const stb_mesh *mesh, const stb_params *params,
                                double *dlp, void *workspace, size_t workspace_bytes,
                                stb_stream stream);
 
+/* ---- hypersingular operator and the Neumann problem (Sec. 3.3, Sec. 3.4) ----------
+ * D: device [n_steps][n_nodes][n_nodes] of params->storage (overwritten) receives
+ * D_h = D_h^1 + D_h^2 on X_h^{1,0}: D^{1,d} = T^T (alpha^2 V^d (x) I_3) T
+ * (eq. D_1_sp_trafo, T the surface curls of the hat functions on every
+ * triangle) from the caller's single-layer blocks V (device [n_steps][E][E],
+ * same storage, as assembled by stb_assemble), and D^{2,d} (eq. D2d: second
+ * differences in time of G^{dtau}, weighted by n_x . n_y phi_i(x) phi_j(y)) by
+ * the rules of stb_assemble.  Needs STB_PREC_FP64, n_nodes <= 65535 and at most
+ * 32 triangles per node; the D^2 contributions are added with atomics (last
+ * bits may differ between runs). */
+stb_status stb_assemble_d_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                         size_t *bytes);
+stb_status stb_assemble_d(const stb_mesh *mesh, const stb_params *params, const void *V, void *D,
+                          void *workspace, size_t workspace_bytes, stb_stream stream);
+/* hd (device FP64 [nrhs][n_steps][E], overwritten): the L2 projection of the
+ * Neumann datum w_r = alpha du_r/dn of the sources (as for
+ * stb_project_dirichlet, whose workspace size it shares) into X_h^{0,0}. */
+stb_status stb_project_neumann(const stb_mesh *mesh, const stb_params *params,
+                               const double *sources, int32_t nrhs, int32_t n_src,
+                               int32_t q_space, int32_t n_time, double *hd, void *workspace,
+                               size_t workspace_bytes, stb_stream stream);
+/* f (device FP64 [nrhs][n_steps][n_nodes], overwritten) = (1/2 M_h^{T_x} -
+ * K_h^{T_x}) hd: K1 of stb_assemble_k1 transposed blockwise (Sec. 3.2's
+ * remark) as a block-Toeplitz product, and the transposed p0 x p1 mass
+ * (Delta_l / 3 to each node of l).  FP64 arithmetic for either storage. */
+stb_status stb_neumann_rhs_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                          int32_t nrhs, size_t *bytes);
+stb_status stb_neumann_rhs(const stb_mesh *mesh, const stb_params *params, const void *K1,
+                           const double *hd, int32_t nrhs, double *f, void *workspace,
+                           size_t workspace_bytes, stb_stream stream);
+/* D_h u = f by the block forward substitution of stb_dirichlet_solve with
+ * n_nodes x n_nodes blocks (D^0 symmetric positive definite): u, f device FP64
+ * [nrhs][n_steps][n_nodes]; same precisions, flags and reports. */
+stb_status stb_neumann_solve_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                            int32_t nrhs, size_t *bytes);
+stb_status stb_neumann_solve(const stb_mesh *mesh, const stb_params *params, const void *D,
+                             const double *f, int32_t nrhs, double *u, void *workspace,
+                             size_t workspace_bytes, stb_stream stream);
+/* out[0] = sum_r ||g_r - u_h,r||^2, out[1] = sum_r ||g_r||^2 in L2(Sigma_h) for
+ * piecewise-linear u1 (device FP64 [nrhs][n_steps][n_nodes]) against the
+ * Dirichlet datum of the sources; workspace of stb_error_workspace_size. */
+stb_status stb_dirichlet_error_p1(const stb_mesh *mesh, const stb_params *params,
+                                  const double *sources, int32_t nrhs, int32_t n_src,
+                                  const double *u1, int32_t q_space, int32_t n_time, double *out,
+                                  void *workspace, size_t workspace_bytes, stb_stream stream);
+
 /* ---- block-Toeplitz matrix-vector product (eq. V_mat) ---------------------------
  *   y_r^k = beta y_r^k + sum_{d=0}^{k} A^d x_r^{k-d},  k = 0..n_steps-1,
  * A: device [n_steps][E][E] of `a_storage`; x, y: device FP64

@@ -68,6 +68,14 @@ _SIGS = {
     "stb_project_p1_workspace_size": (_I32, [_P, _PAR, _I32, _I32, _I32, _I32, _PSZ]),
     "stb_project_dirichlet_p1": (_I32, [_P, _PAR, _P, _I32, _I32, _I32, _I32, _P, _P, _SZ, _P]),
     "stb_rhs_p1_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
+    "stb_assemble_d_workspace_size": (_I32, [_P, _PAR, _PSZ]),
+    "stb_assemble_d": (_I32, [_P, _PAR, _P, _P, _P, _SZ, _P]),
+    "stb_project_neumann": (_I32, [_P, _PAR, _P, _I32, _I32, _I32, _I32, _P, _P, _SZ, _P]),
+    "stb_neumann_rhs_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
+    "stb_neumann_rhs": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
+    "stb_neumann_solve_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
+    "stb_neumann_solve": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
+    "stb_dirichlet_error_p1": (_I32, [_P, _PAR, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _SZ, _P]),
     "stb_potentials_workspace_size": (_I32, [_P, _PAR, _I32, _I64, _I32, _PSZ]),
     "stb_potentials": (_I32, [_P, _PAR, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P, _SZ, _P]),
     "stb_potentials_grid_workspace_size": (_I32, [_P, _PAR, _I32, _I64, _I32, _PSZ]),
@@ -296,6 +304,58 @@ def stb_potentials_grid(mesh, params, points3, eps, w, u1, nrhs, slp, dlp, works
                                           _ptr(slp), _ptr(dlp), _ptr(workspace),
                                           workspace.numel() * workspace.element_size(),
                                           _stream(stream)), "stb_potentials_grid")
+
+
+def stb_assemble_d_workspace_size(mesh, params):
+    return _size(_library().stb_assemble_d_workspace_size, mesh.handle, ctypes.byref(params))
+
+
+def stb_assemble_d(mesh, params, V, D, workspace, stream=None):
+    _check(_library().stb_assemble_d(mesh.handle, ctypes.byref(params), _ptr(V), _ptr(D),
+                                     _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                     _stream(stream)), "stb_assemble_d")
+
+
+def stb_project_neumann(mesh, params, sources, hd, workspace, q_space=8, n_time=16, stream=None):
+    src, sp = _host_f64(sources)
+    nrhs, n_src = src.shape[0], src.shape[1]
+    _check(_library().stb_project_neumann(mesh.handle, ctypes.byref(params), sp, nrhs, n_src,
+                                          q_space, n_time, _ptr(hd), _ptr(workspace),
+                                          workspace.numel() * workspace.element_size(),
+                                          _stream(stream)), "stb_project_neumann")
+
+
+def stb_neumann_rhs_workspace_size(mesh, params, nrhs):
+    return _size(_library().stb_neumann_rhs_workspace_size, mesh.handle, ctypes.byref(params), nrhs)
+
+
+def stb_neumann_rhs(mesh, params, K1, hd, nrhs, f, workspace, stream=None):
+    _check(_library().stb_neumann_rhs(mesh.handle, ctypes.byref(params), _ptr(K1), _ptr(hd), nrhs,
+                                      _ptr(f), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(),
+                                      _stream(stream)), "stb_neumann_rhs")
+
+
+def stb_neumann_solve_workspace_size(mesh, params, nrhs):
+    return _size(_library().stb_neumann_solve_workspace_size, mesh.handle, ctypes.byref(params),
+                 nrhs)
+
+
+def stb_neumann_solve(mesh, params, D, f, nrhs, u, workspace, stream=None):
+    _check(_library().stb_neumann_solve(mesh.handle, ctypes.byref(params), _ptr(D), _ptr(f), nrhs,
+                                        _ptr(u), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(),
+                                        _stream(stream)), "stb_neumann_solve")
+
+
+def stb_dirichlet_error_p1(mesh, params, sources, u1, out, workspace, q_space=8, n_time=16,
+                           stream=None):
+    src, sp = _host_f64(sources)
+    nrhs, n_src = src.shape[0], src.shape[1]
+    _check(_library().stb_dirichlet_error_p1(mesh.handle, ctypes.byref(params), sp, nrhs, n_src,
+                                             _ptr(u1), q_space, n_time, _ptr(out), _ptr(workspace),
+                                             workspace.numel() * workspace.element_size(),
+                                             _stream(stream)), "stb_dirichlet_error_p1")
 
 
 def stb_toeplitz_workspace_size(E, n_steps, nrhs):

@@ -813,6 +813,230 @@ k_singular_k1_f64(const double *__restrict__ geo, const int32_t *__restrict__ tr
     }
 }
 
+// --------------------------------------------- hypersingular operator ---
+// D_h = D_h^1 + D_h^2 on X_h^{1,0} (Sec. 3.3), blocks [n_steps][N][N].
+// D^{1,d} = T^T (alpha^2 V^d (x) I_3) T (eq. D_1_sp_trafo): T holds the
+// surface curls of the hat functions, constant on each triangle, so entry
+// (i, j) sums alpha^2 (c_{n,i} . c_{m,j}) V^d[n][m] over the triangles n
+// around node i and m around node j (node stars, CSR).  One thread per
+// (block, i, j); FP64 sums; the block is overwritten.
+template <class T>
+__global__ void __launch_bounds__(128)
+k_hypersingular_d1(const T *__restrict__ V, int E, int N, const int32_t *__restrict__ star_off,
+                   const int32_t *__restrict__ star_tri, const double *__restrict__ star_curl,
+                   double alpha2, T *__restrict__ D) {
+    constexpr int MAX_STAR = 32;
+    __shared__ int s_tri[MAX_STAR];
+    __shared__ double s_c[MAX_STAR][3];
+    const int i = blockIdx.y, d = blockIdx.z;
+    const int i0 = star_off[i], ni = min(star_off[i + 1] - i0, MAX_STAR);
+    for (int t = threadIdx.x; t < ni; t += blockDim.x) {
+        s_tri[t] = star_tri[i0 + t];
+        for (int o = 0; o < 3; ++o) s_c[t][o] = star_curl[3 * (size_t)(i0 + t) + o];
+    }
+    __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const T *Vd = V + (size_t)d * E * E;
+    const int j0 = star_off[j], j1 = star_off[j + 1];
+    double acc = 0.0;
+    for (int b = j0; b < j1; ++b) {
+        const int m = star_tri[b];
+        const double c0 = star_curl[3 * (size_t)b], c1 = star_curl[3 * (size_t)b + 1],
+                     c2 = star_curl[3 * (size_t)b + 2];
+        for (int a = 0; a < ni; ++a) {
+            const double cc = s_c[a][0] * c0 + s_c[a][1] * c1 + s_c[a][2] * c2;
+            acc = fma(cc, (double)Vd[(size_t)s_tri[a] * E + m], acc);
+        }
+    }
+    D[((size_t)d * N + i) * N + j] = (T)(alpha2 * acc);
+}
+
+// D^{2,d}[i][j] = int int n_x . n_y phi_i(x) phi_j(y) D^{2,d}(x - y) with
+// D^{2,0} = alpha (S_0 - S_1), D^{2,d} = alpha (2 S_d - S_{d+1} - S_{d-1}),
+// S_i the integral of G^{dtau}(., i h) (eq. D2d with G^{dt} = -G^{dtau}; at
+// i = 0 the limit of eq. G_dtau_lim_d, 1/(4 pi alpha rho)), added to D with
+// atomics.  Separated pairs: one thread per ordered pair (l, j), the test
+// points' barycentric weights summed first per trial point.
+__device__ __forceinline__ void atomic_add_d(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_d(float *p, double v) { atomicAdd(p, (float)v); }
+
+template <class OutT>
+__global__ void __launch_bounds__(REG_THREADS)
+k_regular_d2_f64(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E, int N,
+                 const double *__restrict__ rule, int nq, int n_steps, double alpha, double h,
+                 OutT *__restrict__ D) {
+    __shared__ double xa[4 * MAX_RULE];  // x_a (3) and w_a
+    const int l = blockIdx.y;
+    const int j = blockIdx.x * REG_THREADS + threadIdx.x;
+    const double *gl = geo + (size_t)l * GEO_STRIDE;
+    for (int a = threadIdx.x; a < nq; a += REG_THREADS) {
+        const double s1 = rule[3 * a], s2 = rule[3 * a + 1];
+        for (int c = 0; c < 3; ++c)
+            xa[4 * a + c] = gl[GEO_V0 + c] + s1 * (gl[GEO_V1 + c] - gl[GEO_V0 + c]) +
+                            s2 * (gl[GEO_V2 + c] - gl[GEO_V1 + c]);
+        xa[4 * a + 3] = rule[3 * a + 2];
+    }
+    __syncthreads();
+    if (j >= E) return;
+    const int32_t tl[3] = {tris[3 * l], tris[3 * l + 1], tris[3 * l + 2]};
+    const int32_t tj[3] = {tris[3 * j], tris[3 * j + 1], tris[3 * j + 2]};
+    if (touches(tl, tj)) return;
+    const double *gj = geo + (size_t)j * GEO_STRIDE;
+    double P0[3], e1[3], e2[3];
+    for (int c = 0; c < 3; ++c) {
+        P0[c] = gj[GEO_V0 + c];
+        e1[c] = gj[GEO_V1 + c] - gj[GEO_V0 + c];
+        e2[c] = gj[GEO_V2 + c] - gj[GEO_V1 + c];
+    }
+    const double nn = gl[GEO_N] * gj[GEO_N] + gl[GEO_N + 1] * gj[GEO_N + 1] + gl[GEO_N + 2] * gj[GEO_N + 2];
+    const double c = alpha * nn * 4.0 * gl[GEO_AREA] * gj[GEO_AREA] / (4.0 * 3.14159265358979323846 * alpha);
+    const size_t NN = (size_t)N * N;
+    double p1[9], p2[9];  // S_{i-1}, S_{i-2}
+    for (int i = 0; i <= n_steps; ++i) {
+        const double ci = i == 0 ? 0.0 : 0.5 / sqrt(alpha * h * i);  // x = rho ci
+        double S[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) S[k] = 0.0;
+        for (int b = 0; b < nq; ++b) {
+            const double t1 = rule[3 * b], t2 = rule[3 * b + 1], wb = rule[3 * b + 2];
+            const double y0 = P0[0] + t1 * e1[0] + t2 * e2[0];
+            const double y1 = P0[1] + t1 * e1[1] + t2 * e2[1];
+            const double y2 = P0[2] + t1 * e1[2] + t2 * e2[2];
+            double sa[3] = {0.0, 0.0, 0.0};
+            for (int a = 0; a < nq; ++a) {
+                const double r0 = xa[4 * a] - y0, r1 = xa[4 * a + 1] - y1, r2 = xa[4 * a + 2] - y2;
+                const double irho = rsqrt(r0 * r0 + r1 * r1 + r2 * r2);
+                const double g = xa[4 * a + 3] * irho * (i == 0 ? 1.0 : erf(ci / irho));
+                const double s1a = rule[3 * a], s2a = rule[3 * a + 1];
+                sa[0] = fma(1.0 - s1a, g, sa[0]);
+                sa[1] = fma(s1a - s2a, g, sa[1]);
+                sa[2] = fma(s2a, g, sa[2]);
+            }
+            const double lb[3] = {(1.0 - t1) * wb, (t1 - t2) * wb, t2 * wb};
+#pragma unroll
+            for (int va = 0; va < 3; ++va)
+#pragma unroll
+                for (int vb = 0; vb < 3; ++vb) S[3 * va + vb] = fma(sa[va], lb[vb], S[3 * va + vb]);
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) S[k] *= c;
+        if (i >= 1) {  // block d = i - 1 is complete
+            const int d = i - 1;
+#pragma unroll
+            for (int va = 0; va < 3; ++va)
+#pragma unroll
+                for (int vb = 0; vb < 3; ++vb) {
+                    const int k = 3 * va + vb;
+                    const double v = d == 0 ? p1[k] - S[k] : 2.0 * p1[k] - S[k] - p2[k];
+                    atomic_add_d(D + d * NN + (size_t)tl[va] * N + tj[vb], v);
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            p2[k] = p1[k];
+            p1[k] = S[k];
+        }
+    }
+}
+
+// Touching pairs: one CTA per unordered pair (a, b) and its regularised rule
+// (coordinates s on a, t on b, rotated vertex orders); entry (a, b) and, for
+// a != b, the mirrored entry (b, a) receive the same sums.
+template <class OutT>
+__global__ void __launch_bounds__(SS_THREADS)
+k_singular_d2_f64(const double *__restrict__ geo, const int32_t *__restrict__ tris,
+                  const TouchPair *__restrict__ pairs, int E, int N, SSTables tab, int n_steps,
+                  double alpha, double h, OutT *__restrict__ D) {
+    constexpr int CH = 4;
+    __shared__ double red[SS_THREADS / 32][9 * CH];
+    __shared__ double fin[9 * CH];
+    const TouchPair P = pairs[blockIdx.x];
+    const int a = P.a, b = P.b, cls = P.cls;
+    if (a < 0 || b < a || b >= E || cls < PAIR_VERTEX || cls > PAIR_IDENTICAL) return;
+    const double *ga = geo + (size_t)a * GEO_STRIDE, *gb = geo + (size_t)b * GEO_STRIDE;
+    const int oa[3] = {P.perm & 3, (P.perm >> 2) & 3, (P.perm >> 4) & 3};
+    const int ob[3] = {(P.perm >> 6) & 3, (P.perm >> 8) & 3, (P.perm >> 10) & 3};
+    int na_node[3], nb_node[3];
+    double A0[3], A1[3], A2[3], B0[3], B1[3], B2[3];
+    for (int c = 0; c < 3; ++c) {
+        na_node[c] = tris[3 * a + oa[c]];
+        nb_node[c] = tris[3 * b + ob[c]];
+        A0[c] = ga[3 * oa[0] + c];
+        A1[c] = ga[3 * oa[1] + c] - ga[3 * oa[0] + c];
+        A2[c] = ga[3 * oa[2] + c] - ga[3 * oa[1] + c];
+        B0[c] = gb[3 * ob[0] + c];
+        B1[c] = gb[3 * ob[1] + c] - gb[3 * ob[0] + c];
+        B2[c] = gb[3 * ob[2] + c] - gb[3 * ob[1] + c];
+    }
+    const double nn = ga[GEO_N] * gb[GEO_N] + ga[GEO_N + 1] * gb[GEO_N + 1] + ga[GEO_N + 2] * gb[GEO_N + 2];
+    const double scale = alpha * nn * 4.0 * ga[GEO_AREA] * gb[GEO_AREA] /
+                         (4.0 * 3.14159265358979323846 * alpha);
+    const int npt = tab.n[cls];
+    const double *S1 = tab.s1[cls], *S2 = tab.s2[cls], *T1 = tab.t1[cls], *T2 = tab.t2[cls],
+                 *W = tab.w[cls];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t NN = (size_t)N * N;
+    double p1[9], p2[9];
+    for (int c0 = 0; c0 <= n_steps; c0 += CH) {
+        double acc[9 * CH];
+#pragma unroll
+        for (int k = 0; k < 9 * CH; ++k) acc[k] = 0.0;
+        for (int p = threadIdx.x; p < npt; p += SS_THREADS) {
+            const double s1 = S1[p], s2 = S2[p], t1 = T1[p], t2 = T2[p];
+            double r[3];
+            for (int c = 0; c < 3; ++c)
+                r[c] = (A0[c] + s1 * A1[c] + s2 * A2[c]) - (B0[c] + t1 * B1[c] + t2 * B2[c]);
+            const double irho = rsqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            const double la[3] = {1.0 - s1, s1 - s2, s2}, lb[3] = {1.0 - t1, t1 - t2, t2};
+            const double w = W[p] * irho;
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int i = c0 + u;
+                if (i > n_steps) break;
+                const double g = w * (i == 0 ? 1.0 : erf(0.5 / (irho * sqrt(alpha * h * i))));
+#pragma unroll
+                for (int va = 0; va < 3; ++va)
+#pragma unroll
+                    for (int vb = 0; vb < 3; ++vb)
+                        acc[9 * u + 3 * va + vb] = fma(la[va] * lb[vb], g, acc[9 * u + 3 * va + vb]);
+            }
+        }
+        for (int k = 0; k < 9 * CH; ++k) {
+            double v = acc[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 9 * CH) {
+            double sum = 0.0;
+            for (int wi = 0; wi < SS_THREADS / 32; ++wi) sum += red[wi][threadIdx.x];
+            fin[threadIdx.x] = scale * sum;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int u = 0; u < CH; ++u) {
+                const int i = c0 + u;
+                if (i > n_steps) break;
+                for (int k = 0; k < 9; ++k) {
+                    const double S = fin[9 * u + k];
+                    if (i >= 1) {
+                        const int d = i - 1;
+                        const double v = d == 0 ? p1[k] - S : 2.0 * p1[k] - S - p2[k];
+                        const int va = k / 3, vb = k % 3;
+                        atomic_add_d(D + d * NN + (size_t)na_node[va] * N + nb_node[vb], v);
+                        if (cls != PAIR_IDENTICAL)
+                            atomic_add_d(D + d * NN + (size_t)nb_node[vb] * N + na_node[va], v);
+                    }
+                    p2[k] = p1[k];
+                    p1[k] = S;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <class OutT>
 static stb_status run_assembly(const Mesh &m, const stb_params &p, OutT *V, OutT *K,
                                const AssemblyLayout &L, int32_t *status, cudaStream_t s) {
@@ -883,6 +1107,86 @@ static stb_status run_assembly_k1(const Mesh &m, const stb_params &p, OutT *K1,
     k_singular_k1_f64<CH, OutT><<<(unsigned)m.n_touch, SS_THREADS, 0, s>>>(
         L.geo, m.d_tris, L.pairs, E, N, tab, L.levels, p.n_steps, g, K1);
     return check_launch("k_singular_k1_f64");
+}
+
+// Node stars of the mesh for D^1: for node i the triangles around it
+// (CSR) and the surface curl of phi_i on each, curl phi_v = (P_{v+1} -
+// P_{v+2}) / (2 Delta) (the in-plane gradient of the barycentric
+// coordinate turned by the normal; vertices cyclic, counter-clockwise).
+struct NodeStars {
+    std::vector<int32_t> off, tri;
+    std::vector<double> curl;
+    int max_star = 0;
+};
+
+static NodeStars node_stars(const Mesh &m) {
+    NodeStars S;
+    const int64_t N = m.n_nodes, E = m.n_tris;
+    S.off.assign(N + 1, 0);
+    for (int64_t e = 0; e < E; ++e)
+        for (int v = 0; v < 3; ++v) ++S.off[m.tris[3 * e + v] + 1];
+    for (int64_t i = 0; i < N; ++i) {
+        S.max_star = std::max(S.max_star, S.off[i + 1]);
+        S.off[i + 1] += S.off[i];
+    }
+    S.tri.assign(3 * E, 0);
+    S.curl.assign(9 * E, 0.0);
+    std::vector<int32_t> fill(S.off.begin(), S.off.end() - 1);
+    for (int64_t e = 0; e < E; ++e) {
+        const double *P[3];
+        for (int v = 0; v < 3; ++v) P[v] = m.nodes.data() + 3 * (size_t)m.tris[3 * e + v];
+        const double u[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+        const double w[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+        const double cx = u[1] * w[2] - u[2] * w[1], cy = u[2] * w[0] - u[0] * w[2],
+                     cz = u[0] * w[1] - u[1] * w[0];
+        const double two_area = std::sqrt(cx * cx + cy * cy + cz * cz);
+        for (int v = 0; v < 3; ++v) {
+            const int32_t i = m.tris[3 * e + v];
+            const int32_t b = fill[i]++;
+            S.tri[b] = (int32_t)e;
+            const double *A = P[(v + 1) % 3], *B = P[(v + 2) % 3];
+            for (int o = 0; o < 3; ++o) S.curl[3 * (size_t)b + o] = (A[o] - B[o]) / two_area;
+        }
+    }
+    return S;
+}
+
+template <class OutT>
+static stb_status run_hypersingular(const Mesh &m, const stb_params &p, const OutT *V, OutT *D,
+                                    const AssemblyLayout &L, const int32_t *star_off,
+                                    const int32_t *star_tri, const double *star_curl,
+                                    cudaStream_t s) {
+    const int E = (int)m.n_tris, N = (int)m.n_nodes;
+    const double h = p.T / p.n_steps;
+    dim3 g1((N + 127) / 128, N, p.n_steps);
+    count_launch(s);
+    k_hypersingular_d1<OutT><<<g1, 128, 0, s>>>(V, E, N, star_off, star_tri, star_curl,
+                                               p.alpha * p.alpha, D);
+    stb_status st = check_launch("k_hypersingular_d1");
+    if (st) return st;
+    dim3 g2((E + REG_THREADS - 1) / REG_THREADS, E);
+    count_launch(s);
+    k_regular_d2_f64<OutT><<<g2, REG_THREADS, 0, s>>>(L.geo, m.d_tris, E, N, L.rule,
+                                                       p.quad_regular * p.quad_regular,
+                                                       p.n_steps, p.alpha, h, D);
+    if ((st = check_launch("k_regular_d2_f64"))) return st;
+    if (m.n_touch == 0) return STB_OK;
+    SSTables tab{};
+    const double *base = L.ss;
+    for (int cls = 1; cls <= 3; ++cls) {
+        size_t n = L.ss_n[cls];
+        tab.s1[cls] = base;
+        tab.s2[cls] = base + n;
+        tab.t1[cls] = base + 2 * n;
+        tab.t2[cls] = base + 3 * n;
+        tab.w[cls] = base + 4 * n;
+        tab.n[cls] = (int)n;
+        base += 5 * n;
+    }
+    count_launch(s);
+    k_singular_d2_f64<OutT><<<(unsigned)m.n_touch, SS_THREADS, 0, s>>>(
+        L.geo, m.d_tris, L.pairs, E, N, tab, p.n_steps, p.alpha, h, D);
+    return check_launch("k_singular_d2_f64");
 }
 
 }  // namespace stb
@@ -1043,3 +1347,61 @@ extern "C" stb_status stb_assemble_k1(const stb_mesh *mesh, const stb_params *pa
     if (params->storage == STB_STORE_F64) return run_assembly_k1<double>(m, *params, (double *)K1, L, s);
     return run_assembly_k1<float>(m, *params, (float *)K1, L, s);
 }
+
+// ---- hypersingular operator (Sec. 3.3) --------------------------------------
+static size_t stars_bytes(const Mesh &m) {
+    return align256(sizeof(int32_t) * (m.n_nodes + 1)) + align256(sizeof(int32_t) * 3 * m.n_tris) +
+           align256(sizeof(double) * 9 * m.n_tris);
+}
+
+extern "C" stb_status stb_assemble_d_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                                    size_t *bytes) {
+    if (!mesh || !bytes || !params) return fail(STB_ERR_INVALID_ARG, "mesh, params and bytes must be given");
+    stb_status st = check_assembly_params(params);
+    if (st) return st;
+    if (params->precision != STB_PREC_FP64)
+        return fail(STB_ERR_INVALID_ARG, "the hypersingular operator is assembled in FP64");
+    if (mesh->m.n_nodes > 65535) return fail(STB_ERR_INVALID_ARG, "n_nodes must be <= 65535");
+    *bytes = align256(assembly_layout(mesh->m, *params, nullptr, 0).bytes) + stars_bytes(mesh->m);
+    return STB_OK;
+}
+
+extern "C" stb_status stb_assemble_d(const stb_mesh *mesh, const stb_params *params, const void *V,
+                                     void *D, void *ws, size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !V || !D) return fail(STB_ERR_INVALID_ARG, "mesh, V and D must be given");
+    size_t need;
+    stb_status st = stb_assemble_d_workspace_size(mesh, params, &need);
+    if (st) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    const Mesh &m = mesh->m;
+    if (m.n_tris > 65535) return fail(STB_ERR_INVALID_ARG, "dense assembly supports E <= 65535");
+    const NodeStars S = node_stars(m);
+    if (S.max_star > 32) return fail(STB_ERR_INVALID_ARG, "a node belongs to more than 32 triangles");
+    AssemblyLayout L = assembly_layout(m, *params, ws, ws_bytes);
+    char *p = static_cast<char *>(ws) + align256(L.bytes);
+    int32_t *star_off = reinterpret_cast<int32_t *>(p);
+    p += align256(sizeof(int32_t) * (m.n_nodes + 1));
+    int32_t *star_tri = reinterpret_cast<int32_t *>(p);
+    p += align256(sizeof(int32_t) * 3 * m.n_tris);
+    double *star_curl = reinterpret_cast<double *>(p);
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = prepare_fp64(m, *params, L, status_word(ws), s))) return st;
+    STB_CUDA(cudaMemcpyAsync(star_off, S.off.data(), sizeof(int32_t) * S.off.size(),
+                             cudaMemcpyHostToDevice, s));
+    STB_CUDA(cudaMemcpyAsync(star_tri, S.tri.data(), sizeof(int32_t) * S.tri.size(),
+                             cudaMemcpyHostToDevice, s));
+    STB_CUDA(cudaMemcpyAsync(star_curl, S.curl.data(), sizeof(double) * S.curl.size(),
+                             cudaMemcpyHostToDevice, s));
+    if (params->storage == STB_STORE_F64)
+        st = run_hypersingular<double>(m, *params, (const double *)V, (double *)D, L, star_off,
+                                       star_tri, star_curl, s);
+    else
+        st = run_hypersingular<float>(m, *params, (const float *)V, (float *)D, L, star_off,
+                                      star_tri, star_curl, s);
+    if (st) return st;
+    // the host tables above are copied from pageable memory before the
+    // copies return; nothing else refers to them
+    return STB_OK;
+}
+

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "stb_dense.h"
+#include "stb_heat.h"
 #include "stb_internal.h"
 #include "stb_toeplitz.h"
 
@@ -21,21 +22,6 @@ constexpr int MAX_QS = 32;   // q_space <= 32
 constexpr int MAX_NT = 64;   // n_time <= 64
 constexpr int MAX_SRC = 64;  // sources per right-hand side
 
-// G_alpha(r, tau) (Sec. 2), zero for tau <= 0; rr = |r|^2.  FP64, or FP32
-// (mixed precision: exp2 on the MUFU pipe and a reciprocal square root).
-template <class R> __device__ __forceinline__ R heat(R rr, R tau, R alpha);
-template <> __device__ __forceinline__ double heat<double>(double rr, double tau, double alpha) {
-    if (tau <= 0.0) return 0.0;
-    const double s = 4.0 * 3.14159265358979323846 * alpha * tau;
-    return exp(-rr / (4.0 * alpha * tau)) / (s * sqrt(s));
-}
-template <> __device__ __forceinline__ float heat<float>(float rr, float tau, float alpha) {
-    if (tau <= 0.0f) return 0.0f;
-    const float s = 4.0f * 3.14159265f * alpha * tau;
-    float e;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-rr / (4.0f * alpha * tau) * 1.44269504f));
-    return e * rsqrtf(s * s * s);
-}
 
 struct DirLayout {
     double *geo, *rule, *src, *part;
@@ -68,8 +54,10 @@ static void host_rules(int q, int nt, std::vector<double> &out) {
     out.insert(out.end(), tw.begin(), tw.end());
 }
 
-// g_{r,k,j} = (h Delta_j)^{-1} int_{t_k}^{t_{k+1}} int_{gamma_j} g_r  (element mean)
-template <class R>
+// g_{r,k,j} = (h Delta_j)^{-1} int_{t_k}^{t_{k+1}} int_{gamma_j} g_r  (element mean);
+// NEU: of the Neumann datum w_r = alpha du_r/dn_x = -sum_s weight_s G (x - y_s).n_x
+// / (2 (t - t0_s)) instead of the Dirichlet datum
+template <class R, bool NEU = false>
 __global__ void __launch_bounds__(DIR_THREADS)
 k_project(const double *__restrict__ geo, int E, const double *__restrict__ rule, int nq, int nt,
           const double *__restrict__ src, int n_src, int nrhs, int n_steps, double h_, double alpha_,
@@ -86,6 +74,7 @@ k_project(const double *__restrict__ geo, int E, const double *__restrict__ rule
     const int k = (int)(idx / E), j = (int)(idx % E);
     const double *gj = geo + (size_t)j * GEO_STRIDE;
     const R *tx = rs + 3 * nq, *tw = tx + nt;
+    const R nx = (R)gj[GEO_N], ny = (R)gj[GEO_N + 1], nz = (R)gj[GEO_N + 2];
     R acc = 0;
     for (int a = 0; a < nq; ++a) {
         R s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
@@ -98,13 +87,110 @@ k_project(const double *__restrict__ geo, int E, const double *__restrict__ rule
             for (int s = 0; s < n_src; ++s) {
                 const R *S = sr + 5 * s;
                 R d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
-                gv = fma(S[4], heat<R>(d0 * d0 + d1 * d1 + d2 * d2, t - S[3], alpha), gv);
+                if (NEU) {
+                    const R tau = t - S[3];
+                    if (tau <= (R)0) continue;
+                    const R dn = d0 * nx + d1 * ny + d2 * nz;
+                    gv -= S[4] * heat<R>(d0 * d0 + d1 * d1 + d2 * d2, tau, alpha) * dn / ((R)2 * tau);
+                } else {
+                    gv = fma(S[4], heat<R>(d0 * d0 + d1 * d1 + d2 * d2, t - S[3], alpha), gv);
+                }
             }
             inner = fma(tw[b], gv, inner);
         }
         acc = fma(wa, inner, acc);
     }
     g[(size_t)r * n_steps * E + idx] = 2.0 * (double)acc;
+}
+
+// Out-partials of sum (g - u_h)^2 and sum g^2 over Sigma_h for piecewise-linear
+// u_h (u_h = sum_v lambda_v u1_{k, node v} on step k) and the Dirichlet datum g.
+template <class R>
+__global__ void __launch_bounds__(DIR_THREADS)
+k_error_p1(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E, int N,
+           const double *__restrict__ rule, int nq, int nt, const double *__restrict__ src,
+           int n_src, int nrhs, int n_steps, double h_, double alpha_,
+           const double *__restrict__ u1, double *__restrict__ part) {
+    __shared__ R rs[3 * MAX_QS * MAX_QS + 2 * MAX_NT];
+    __shared__ R sr[5 * MAX_SRC];
+    const R h = (R)h_, alpha = (R)alpha_;
+    __shared__ double red[2][DIR_THREADS / 32];
+    for (int i = threadIdx.x; i < 3 * nq + 2 * nt; i += DIR_THREADS) rs[i] = rule[i];
+    const int r = blockIdx.y;
+    for (int i = threadIdx.x; i < 5 * n_src; i += DIR_THREADS) sr[i] = src[(size_t)r * n_src * 5 + i];
+    __syncthreads();
+    size_t idx = (size_t)blockIdx.x * DIR_THREADS + threadIdx.x;
+    double e2 = 0.0, r2 = 0.0;
+    if (idx < (size_t)n_steps * E) {
+        const int k = (int)(idx / E), j = (int)(idx % E);
+        const double *gj = geo + (size_t)j * GEO_STRIDE;
+        const R *tx = rs + 3 * nq, *tw = tx + nt;
+        const double *uk = u1 + ((size_t)r * n_steps + k) * N;
+        const R u0 = (R)uk[tris[3 * j]], u1v = (R)uk[tris[3 * j + 1]], u2 = (R)uk[tris[3 * j + 2]];
+        R e2r = 0, r2r = 0;
+        for (int a = 0; a < nq; ++a) {
+            R s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
+            R x[3];
+            for (int c = 0; c < 3; ++c)
+                x[c] = (R)(gj[c] + (double)s1 * (gj[3 + c] - gj[c]) + (double)s2 * (gj[6 + c] - gj[3 + c]));
+            const R uh = (1 - s1) * u0 + (s1 - s2) * u1v + s2 * u2;
+            R ie = 0, ir = 0;
+            for (int b = 0; b < nt; ++b) {
+                R t = (k + tx[b]) * h, gv = 0;
+                for (int s = 0; s < n_src; ++s) {
+                    const R *S = sr + 5 * s;
+                    R d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
+                    gv = fma(S[4], heat<R>(d0 * d0 + d1 * d1 + d2 * d2, t - S[3], alpha), gv);
+                }
+                ie = fma(tw[b], (gv - uh) * (gv - uh), ie);
+                ir = fma(tw[b], gv * gv, ir);
+            }
+            e2r = fma(wa, ie, e2r);
+            r2r = fma(wa, ir, r2r);
+        }
+        double f = 2.0 * gj[GEO_AREA] * h_;
+        e2 = (double)e2r * f;
+        r2 = (double)r2r * f;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = e2;
+        red[1][threadIdx.x >> 5] = r2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double se = 0.0, sr2 = 0.0;
+        for (int w = 0; w < DIR_THREADS / 32; ++w) {
+            se += red[0][w];
+            sr2 += red[1][w];
+        }
+        size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        part[2 * b] = se;
+        part[2 * b + 1] = sr2;
+    }
+}
+
+// f_{r,k,i} = (h/2) sum_{l around i} Delta_l / 3 h_{r,k,l} - f_{r,k,i}: the
+// transposed p0 x p1 mass minus the product already in f, one thread per
+// (r, k, l) with atomics after negating f (k_negate).
+__global__ void k_negate(double *__restrict__ f, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) f[i] = -f[i];
+}
+__global__ void k_add_mass_p1t(const double *__restrict__ geo, const int32_t *__restrict__ tris,
+                               int E, int N, size_t total, double h, const double *__restrict__ hd,
+                               double *__restrict__ f) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (r, k, l)
+    if (idx >= total) return;
+    const int l = (int)(idx % E);
+    double *fk = f + (idx / E) * N;
+    const double v = 0.5 * h * geo[(size_t)l * GEO_STRIDE + GEO_AREA] / 3.0 * hd[idx];
+    atomicAdd(fk + tris[3 * l], v);
+    atomicAdd(fk + tris[3 * l + 1], v);
+    atomicAdd(fk + tris[3 * l + 2], v);
 }
 
 // out-partials of sum (w - w_h)^2 and sum w^2 over Sigma_h (Sec. 6.1), with
@@ -597,3 +683,113 @@ extern "C" stb_status stb_dirichlet_rhs_p1(const stb_mesh *mesh, const stb_param
         geo, m.d_tris, (int)m.n_tris, (int)m.n_nodes, total, p->T / p->n_steps, g1, f);
     return check_launch("k_add_mass_p1");
 }
+
+// ---------------------------------------------- Neumann problem (Sec. 3.4) ---
+extern "C" stb_status stb_project_neumann(const stb_mesh *mesh, const stb_params *p,
+                                          const double *sources, int32_t nrhs, int32_t n_src,
+                                          int32_t q, int32_t nt, double *hd, void *ws,
+                                          size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !p || !sources || !hd) return fail(STB_ERR_INVALID_ARG, "null argument");
+    if (!(p->alpha > 0) || !(p->T > 0) || p->n_steps < 1)
+        return fail(STB_ERR_INVALID_ARG, "alpha, T and n_steps must be positive");
+    stb_status st = check_rule_args(nrhs, n_src, q, nt);
+    if (st) return st;
+    const Mesh &m = mesh->m;
+    DirLayout L = dir_layout(m, nrhs, n_src, q, nt, ws, ws_bytes, 0);
+    if ((st = check_workspace(ws, ws_bytes, L.bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = upload_rules_sources(L, q, nt, sources, nrhs, n_src, s))) return st;
+    if ((st = launch_geometry(m, L.geo, s))) return st;
+    size_t n = (size_t)p->n_steps * m.n_tris;
+    dim3 grid((unsigned)((n + DIR_THREADS - 1) / DIR_THREADS), (unsigned)nrhs);
+    count_launch(s);
+    if (p->precision == STB_PREC_MIXED)
+        k_project<float, true><<<grid, DIR_THREADS, 0, s>>>(L.geo, (int)m.n_tris, L.rule, q * q, nt,
+                                                            L.src, n_src, nrhs, p->n_steps,
+                                                            p->T / p->n_steps, p->alpha, hd);
+    else
+        k_project<double, true><<<grid, DIR_THREADS, 0, s>>>(L.geo, (int)m.n_tris, L.rule, q * q, nt,
+                                                             L.src, n_src, nrhs, p->n_steps,
+                                                             p->T / p->n_steps, p->alpha, hd);
+    return check_launch("k_project(neumann)");
+}
+
+extern "C" stb_status stb_dirichlet_error_p1(const stb_mesh *mesh, const stb_params *p,
+                                             const double *sources, int32_t nrhs, int32_t n_src,
+                                             const double *u1, int32_t q, int32_t nt, double *out,
+                                             void *ws, size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !p || !sources || !u1 || !out) return fail(STB_ERR_INVALID_ARG, "null argument");
+    if (!(p->alpha > 0) || !(p->T > 0) || p->n_steps < 1)
+        return fail(STB_ERR_INVALID_ARG, "alpha, T and n_steps must be positive");
+    stb_status st = check_rule_args(nrhs, n_src, q, nt);
+    if (st) return st;
+    const Mesh &m = mesh->m;
+    const size_t nblk = error_blocks(m, p->n_steps, nrhs);
+    DirLayout L = dir_layout(m, nrhs, n_src, q, nt, ws, ws_bytes, 2 * nblk);
+    if ((st = check_workspace(ws, ws_bytes, L.bytes))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = upload_rules_sources(L, q, nt, sources, nrhs, n_src, s))) return st;
+    if ((st = launch_geometry(m, L.geo, s))) return st;
+    size_t n = (size_t)p->n_steps * m.n_tris;
+    dim3 grid((unsigned)((n + DIR_THREADS - 1) / DIR_THREADS), (unsigned)nrhs);
+    count_launch(s);
+    if (p->precision == STB_PREC_MIXED)
+        k_error_p1<float><<<grid, DIR_THREADS, 0, s>>>(L.geo, m.d_tris, (int)m.n_tris, (int)m.n_nodes,
+                                                       L.rule, q * q, nt, L.src, n_src, nrhs,
+                                                       p->n_steps, p->T / p->n_steps, p->alpha, u1,
+                                                       L.part);
+    else
+        k_error_p1<double><<<grid, DIR_THREADS, 0, s>>>(L.geo, m.d_tris, (int)m.n_tris,
+                                                        (int)m.n_nodes, L.rule, q * q, nt, L.src,
+                                                        n_src, nrhs, p->n_steps, p->T / p->n_steps,
+                                                        p->alpha, u1, L.part);
+    if ((st = check_launch("k_error_p1"))) return st;
+    count_launch(s);
+    k_sum_pairs<<<1, 1024, 0, s>>>(L.part, nblk, out);
+    return check_launch("k_sum_pairs");
+}
+
+extern "C" stb_status stb_neumann_rhs_workspace_size(const stb_mesh *mesh, const stb_params *p,
+                                                     int32_t nrhs, size_t *bytes) {
+    if (!mesh || !p || !bytes || nrhs < 1 || p->n_steps < 1)
+        return fail(STB_ERR_INVALID_ARG, "invalid argument");
+    Carve c(nullptr, 0);
+    c.take<double>((size_t)mesh->m.n_tris * GEO_STRIDE);
+    c.take<char>(toeplitz_partial_bytes(mesh->m.n_nodes, p->n_steps, nrhs));
+    *bytes = align256(c.off);
+    return STB_OK;
+}
+
+extern "C" stb_status stb_neumann_rhs(const stb_mesh *mesh, const stb_params *p, const void *K1,
+                                      const double *hd, int32_t nrhs, double *f, void *ws,
+                                      size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !p || !K1 || !hd || !f) return fail(STB_ERR_INVALID_ARG, "null argument");
+    if (p->storage != STB_STORE_F64 && p->storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "bad storage");
+    size_t need;
+    stb_status st = stb_neumann_rhs_workspace_size(mesh, p, nrhs, &need);
+    if (st) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    const Mesh &m = mesh->m;
+    Carve c(ws, ws_bytes);
+    double *geo = c.take<double>((size_t)m.n_tris * GEO_STRIDE);
+    double *part = (double *)c.take<char>(toeplitz_partial_bytes(m.n_nodes, p->n_steps, nrhs));
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = launch_geometry(m, geo, s))) return st;
+    if ((st = toeplitz_fp64_rect_t(K1, p->storage, m.n_tris, m.n_nodes, p->n_steps, nrhs, hd, 0.0,
+                                   f, part, s)))
+        return st;
+    const size_t nf = (size_t)nrhs * p->n_steps * m.n_nodes;
+    count_launch(s);
+    k_negate<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(f, nf);
+    if ((st = check_launch("k_negate"))) return st;
+    const size_t total = (size_t)nrhs * p->n_steps * m.n_tris;
+    count_launch(s);
+    k_add_mass_p1t<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        geo, m.d_tris, (int)m.n_tris, (int)m.n_nodes, total, p->T / p->n_steps, hd, f);
+    return check_launch("k_add_mass_p1t");
+}
+

@@ -837,26 +837,56 @@ stb_status dense_apply(const double *A, int64_t n, int64_t nvec, const double *i
 
 using namespace stb;
 
-extern "C" stb_status stb_solve_workspace_size(const stb_mesh *mesh, const stb_params *p,
-                                               int32_t nrhs, size_t *bytes) {
-    if (!mesh || !p || !bytes || nrhs < 1 || p->n_steps < 1)
+// The forward-substitution solve for blocks of size E x E (E triangles for
+// V_h w = f, E nodes for D_h u = f).
+static stb_status solve_size(int64_t E, const stb_params *p, int32_t nrhs, size_t *bytes) {
+    if (!p || !bytes || nrhs < 1 || p->n_steps < 1)
         return fail(STB_ERR_INVALID_ARG, "invalid argument");
     const bool mixed = p->precision == STB_PREC_MIXED;
-    *bytes = align256(solve_layout(mesh->m.n_tris, p->n_steps, nrhs, mixed, nullptr, 0).bytes);
+    *bytes = align256(solve_layout(E, p->n_steps, nrhs, mixed, nullptr, 0).bytes);
     return STB_OK;
+}
+
+static stb_status solve_blocks(int64_t E, const stb_params *p, const void *V, const double *f,
+                               int32_t nrhs, double *w, void *ws, size_t ws_bytes,
+                               stb_stream stream);
+
+extern "C" stb_status stb_solve_workspace_size(const stb_mesh *mesh, const stb_params *p,
+                                               int32_t nrhs, size_t *bytes) {
+    if (!mesh) return fail(STB_ERR_INVALID_ARG, "invalid argument");
+    return solve_size(mesh->m.n_tris, p, nrhs, bytes);
 }
 
 extern "C" stb_status stb_dirichlet_solve(const stb_mesh *mesh, const stb_params *p, const void *V,
                                           const double *f, int32_t nrhs, double *w, void *ws,
                                           size_t ws_bytes, stb_stream stream) {
-    if (!mesh || !p || !V || !f || !w || nrhs < 1) return fail(STB_ERR_INVALID_ARG, "null argument");
+    if (!mesh) return fail(STB_ERR_INVALID_ARG, "null argument");
+    return solve_blocks(mesh->m.n_tris, p, V, f, nrhs, w, ws, ws_bytes, stream);
+}
+
+extern "C" stb_status stb_neumann_solve_workspace_size(const stb_mesh *mesh, const stb_params *p,
+                                                       int32_t nrhs, size_t *bytes) {
+    if (!mesh) return fail(STB_ERR_INVALID_ARG, "invalid argument");
+    return solve_size(mesh->m.n_nodes, p, nrhs, bytes);
+}
+
+extern "C" stb_status stb_neumann_solve(const stb_mesh *mesh, const stb_params *p, const void *D,
+                                        const double *f, int32_t nrhs, double *u, void *ws,
+                                        size_t ws_bytes, stb_stream stream) {
+    if (!mesh) return fail(STB_ERR_INVALID_ARG, "null argument");
+    return solve_blocks(mesh->m.n_nodes, p, D, f, nrhs, u, ws, ws_bytes, stream);
+}
+
+static stb_status solve_blocks(int64_t E, const stb_params *p, const void *V, const double *f,
+                               int32_t nrhs, double *w, void *ws, size_t ws_bytes,
+                               stb_stream stream) {
+    if (!p || !V || !f || !w || nrhs < 1) return fail(STB_ERR_INVALID_ARG, "null argument");
     if (p->n_steps < 1) return fail(STB_ERR_INVALID_ARG, "n_steps must be >= 1");
     if (p->storage != STB_STORE_F64 && p->storage != STB_STORE_F32)
         return fail(STB_ERR_INVALID_ARG, "bad storage");
     const bool mixed = p->precision == STB_PREC_MIXED;
     if (mixed && p->storage != STB_STORE_F32)
         return fail(STB_ERR_INVALID_ARG, "mixed-precision solve needs STB_STORE_F32 blocks");
-    const int64_t E = mesh->m.n_tris;
     if (E > 65535) return fail(STB_ERR_INVALID_ARG, "E must be <= 65535");
     SolveLayout S = solve_layout(E, p->n_steps, nrhs, mixed, ws, ws_bytes);
     stb_status st = check_workspace(ws, ws_bytes, S.bytes);

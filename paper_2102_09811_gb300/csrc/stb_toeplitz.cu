@@ -20,7 +20,9 @@ constexpr int TD = 8;    // blocks d per item
 constexpr int TJ = 32;   // contraction chunk
 constexpr int MV_THREADS = 128;
 
-template <class AT>
+// TRANS: every block is stored transposed, as As^d [N][E] with
+// A^d[l][j] = As^d[j][l] (the blockwise transpose of Sec. 3.2's remark).
+template <class AT, bool TRANS = false>
 __global__ void __launch_bounds__(MV_THREADS)
 k_toeplitz_partial(const AT *__restrict__ A, int E, int N, int n_steps, int nrhs,
                    const double *__restrict__ x, double *__restrict__ part) {
@@ -40,9 +42,16 @@ k_toeplitz_partial(const AT *__restrict__ A, int E, int N, int n_steps, int nrhs
     for (int d = d0; d < d1; ++d) {
         const AT *Ad = A + (size_t)d * EN;
         for (int j0 = 0; j0 < N; j0 += TJ) {
-            for (int t = threadIdx.x; t < TM * TJ; t += MV_THREADS) {
-                int i = t / TJ, jj = t % TJ, l = l0 + i, j = j0 + jj;
-                As[i][jj] = (l < E && j < N) ? (double)Ad[(size_t)l * N + j] : 0.0;
+            if (TRANS) {  // stored [N][E]: consecutive threads read consecutive l
+                for (int t = threadIdx.x; t < TM * TJ; t += MV_THREADS) {
+                    int jj = t / TM, i = t % TM, l = l0 + i, j = j0 + jj;
+                    As[i][jj] = (l < E && j < N) ? (double)Ad[(size_t)j * E + l] : 0.0;
+                }
+            } else {
+                for (int t = threadIdx.x; t < TM * TJ; t += MV_THREADS) {
+                    int i = t / TJ, jj = t % TJ, l = l0 + i, j = j0 + jj;
+                    As[i][jj] = (l < E && j < N) ? (double)Ad[(size_t)l * N + j] : 0.0;
+                }
             }
             for (int t = threadIdx.x; t < TK * TJ; t += MV_THREADS) {
                 int c = t / TJ, jj = t % TJ, k = k0 + c, j = j0 + jj;
@@ -90,6 +99,34 @@ size_t toeplitz_partial_bytes(int64_t E, int32_t n_steps, int32_t nrhs) {
 stb_status toeplitz_fp64(const void *A, int32_t storage, int64_t E, int32_t n_steps, int32_t nrhs,
                          const double *x, double beta, double *y, double *part, cudaStream_t s) {
     return toeplitz_fp64_rect(A, storage, E, E, n_steps, nrhs, x, beta, y, part, s);
+}
+
+template <bool TRANS>
+static stb_status toeplitz_rect_run(const void *A, int32_t storage, int64_t E, int64_t N,
+                                    int32_t n_steps, int32_t nrhs, const double *x, double beta,
+                                    double *y, double *part, cudaStream_t s) {
+    int n_kt = (n_steps + TK - 1) / TK, n_dr = (n_steps + TD - 1) / TD;
+    dim3 grid((unsigned)((E + TM - 1) / TM), (unsigned)(n_kt * nrhs), (unsigned)n_dr);
+    count_launch(s);
+    if (storage == STB_STORE_F64)
+        k_toeplitz_partial<double, TRANS><<<grid, MV_THREADS, 0, s>>>(
+            (const double *)A, (int)E, (int)N, n_steps, nrhs, x, part);
+    else
+        k_toeplitz_partial<float, TRANS><<<grid, MV_THREADS, 0, s>>>(
+            (const float *)A, (int)E, (int)N, n_steps, nrhs, x, part);
+    stb_status st = check_launch("k_toeplitz_partial");
+    if (st) return st;
+    size_t total = (size_t)nrhs * n_steps * E;
+    count_launch(s);
+    k_toeplitz_reduce<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, (int)E, n_steps, nrhs,
+                                                                      beta, y);
+    return check_launch("k_toeplitz_reduce");
+}
+
+stb_status toeplitz_fp64_rect_t(const void *A, int32_t storage, int64_t E, int64_t N,
+                                int32_t n_steps, int32_t nrhs, const double *x, double beta,
+                                double *y, double *part, cudaStream_t s) {
+    return toeplitz_rect_run<true>(A, storage, N, E, n_steps, nrhs, x, beta, y, part, s);
 }
 
 stb_status toeplitz_fp64_rect(const void *A, int32_t storage, int64_t E, int64_t N, int32_t n_steps,

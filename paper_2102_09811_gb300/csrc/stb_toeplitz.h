@@ -7,6 +7,12 @@ size_t toeplitz_partial_bytes(int64_t E, int32_t n_steps, int32_t nrhs);
 // y = beta y + T(A) x in FP64; `part` has toeplitz_partial_bytes() bytes.
 stb_status toeplitz_fp64(const void *A, int32_t storage, int64_t E, int32_t n_steps, int32_t nrhs,
                          const double *x, double beta, double *y, double *part, cudaStream_t s);
+// The blockwise transpose: y^k = beta y^k + sum_d (A^d)^T x^{k-d} with A^d
+// stored [E][N], x [nrhs][n_steps][E], y [nrhs][n_steps][N]; `part` has
+// toeplitz_partial_bytes(N, ...) bytes.
+stb_status toeplitz_fp64_rect_t(const void *A, int32_t storage, int64_t E, int64_t N,
+                                int32_t n_steps, int32_t nrhs, const double *x, double beta,
+                                double *y, double *part, cudaStream_t s);
 // The same with rectangular blocks A^d [E][N]: x [nrhs][n_steps][N],
 // y [nrhs][n_steps][E]; `part` has toeplitz_partial_bytes(E, ...) bytes.
 stb_status toeplitz_fp64_rect(const void *A, int32_t storage, int64_t E, int64_t N, int32_t n_steps,

@@ -124,6 +124,96 @@ class DirichletProblem:
         return math.sqrt(float(e[0]) / float(e[1]))
 
 
+class NeumannProblem:
+    """The Neumann problem D_h u = (1/2 M_h^{T_x} - K_h^{T_x}) h (Sec. 3.3,
+    Sec. 3.4) for exterior heat sources: Neumann data projected into
+    X_h^{0,0}, the Dirichlet datum computed in X_h^{1,0}.  V (for D_h^1), K
+    with piecewise-linear trial functions and D_h are assembled in the given
+    precision where the library has it (D_h^2: FP64 arithmetic), stored in
+    `storage`.
+    """
+
+    def __init__(self, nodes, tris, alpha, T, n_steps, sources, quad_regular=3, quad_singular=4,
+                 storage=capi.STB_STORE_F64, q_space=8, n_time=16, device="cuda", mesh=None,
+                 precision=capi.STB_PREC_FP64):
+        self.mesh = mesh if mesh is not None else capi.Mesh(nodes, tris)
+        mk = lambda prec: capi.stb_default_params(alpha, T, n_steps, quad_regular, quad_singular,
+                                                  precision=prec, storage=storage)
+        self.params = mk(precision)
+        mixed_ok = precision == capi.STB_PREC_MIXED and storage == capi.STB_STORE_F32
+        self.params_k1 = mk(capi.STB_PREC_MIXED if mixed_ok else capi.STB_PREC_FP64)
+        self.params_d = mk(capi.STB_PREC_FP64)
+        self.sources = sources
+        self.nrhs, self.n_src = sources.shape[0], sources.shape[1]
+        self.q_space, self.n_time = q_space, n_time
+        E, N, dev = self.mesh.n_tris, self.mesh.n_nodes, torch.device(device)
+        self.E, self.N, self.n_steps, self.device = E, N, n_steps, dev
+        dt = torch.float64 if storage == capi.STB_STORE_F64 else torch.float32
+        self.V = torch.empty((n_steps, E, E), dtype=dt, device=dev)
+        self.K = torch.empty((n_steps, E, N), dtype=dt, device=dev)
+        self.D = torch.empty((n_steps, N, N), dtype=dt, device=dev)
+        self.hd = torch.empty((self.nrhs, n_steps, E), dtype=torch.float64, device=dev)
+        self.f = torch.empty((self.nrhs, n_steps, N), dtype=torch.float64, device=dev)
+        self.u = torch.empty((self.nrhs, n_steps, N), dtype=torch.float64, device=dev)
+        self.err = torch.zeros(2, dtype=torch.float64, device=dev)
+        m, p = self.mesh, self.params
+        self.ws_v = _ws(capi.stb_assemble_workspace_size(m, p), dev)
+        self.ws_k1 = _ws(capi.stb_assemble_k1_workspace_size(m, self.params_k1), dev)
+        self.ws_d = _ws(capi.stb_assemble_d_workspace_size(m, self.params_d), dev)
+        self.ws_project = _ws(capi.stb_project_workspace_size(m, self.nrhs, self.n_src, q_space,
+                                                              n_time), dev)
+        self.ws_rhs = _ws(capi.stb_neumann_rhs_workspace_size(m, p, self.nrhs), dev)
+        self.ws_solve = _ws(capi.stb_neumann_solve_workspace_size(m, p, self.nrhs), dev)
+        self.ws_error = _ws(capi.stb_error_workspace_size(m, p, self.nrhs, self.n_src, q_space,
+                                                          n_time), dev)
+
+    def assemble(self, stream=None):
+        capi.stb_assemble(self.mesh, self.params, self.V, None, self.ws_v, stream)
+        capi.stb_assemble_k1(self.mesh, self.params_k1, self.K, self.ws_k1, stream)
+        capi.stb_assemble_d(self.mesh, self.params_d, self.V, self.D, self.ws_d, stream)
+
+    def project(self, stream=None):
+        capi.stb_project_neumann(self.mesh, self.params, self.sources, self.hd, self.ws_project,
+                                 self.q_space, self.n_time, stream)
+
+    def rhs(self, stream=None):
+        capi.stb_neumann_rhs(self.mesh, self.params, self.K, self.hd, self.nrhs, self.f,
+                             self.ws_rhs, stream)
+
+    def solve(self, stream=None):
+        capi.stb_neumann_solve(self.mesh, self.params, self.D, self.f, self.nrhs, self.u,
+                               self.ws_solve, stream)
+
+    def error(self, stream=None):
+        capi.stb_dirichlet_error_p1(self.mesh, self.params, self.sources, self.u, self.err,
+                                    self.ws_error, self.q_space, self.n_time, stream)
+
+    def run(self, stream=None):
+        self.assemble(stream)
+        self.project(stream)
+        self.rhs(stream)
+        self.solve(stream)
+        self.error(stream)
+        return self.err
+
+    def relative_error(self):
+        e = self.err.cpu()
+        return math.sqrt(float(e[0]) / float(e[1]))
+
+    def representation(self, points, q_space=4, stream=None):
+        """u_h = V~ h_h - W u_h at points [n_pts, 4] inside the domain."""
+        pts = torch.as_tensor(points, dtype=torch.float64).to(self.device).contiguous()
+        n_pts = pts.shape[0]
+        slp = torch.empty((self.nrhs, n_pts), dtype=torch.float64, device=self.device)
+        dlp = torch.empty_like(slp)
+        ws = _ws(capi.stb_potentials_workspace_size(self.mesh, self.params, self.nrhs, n_pts,
+                                                    q_space), self.device)
+        capi.stb_potentials(self.mesh, self.params, pts, self.hd, self.u, self.nrhs, slp, dlp, ws,
+                            q_space, stream)
+        capi.stb_workspace_status(ws, stream)
+        return slp - dlp
+
+
 class BatchPipeline:
     """Many independent Dirichlet problems, mixed precision, FP32 storage.
 

@@ -1,0 +1,181 @@
+"""GPU parity of the hypersingular operator D_h = D_h^1 + D_h^2 and of the
+Neumann problem D_h u = (1/2 M_h^{T_x} - K_h^{T_x}) h (Sec. 3.3, Sec. 3.4)
+through the C ABI against the FP64 oracle on the same seeded inputs, and the
+paper's Table neuconv.
+
+Tolerances.  D^{2,d} holds second differences of G^{dtau} (eq. D2d), which
+cancel like those of V^d, and D^1 is formed from the library's own V (itself
+within the V tolerance of the oracle's); per block the relative Frobenius
+difference is required below 1e-10 (a wrong weight, node, sign or level is
+O(1)).  The data kernels follow the FP64 rounding bounds of the p0 ones.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from paper_2102_09811_gb300 import capi, pipeline
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_device():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    capi._library()
+
+
+def _mesh(name):
+    return {"cube2": lambda: workloads.cube_mesh(2), "cube4": lambda: workloads.cube_mesh(4),
+            "ico3": lambda: workloads.icosphere(3)}[name]()
+
+
+def gpu_d(nodes, tris, alpha, T, n_steps, storage=capi.STB_STORE_F64):
+    mesh = capi.Mesh(nodes, tris)
+    p = capi.stb_default_params(alpha, T, n_steps, storage=storage)
+    dt = torch.float64 if storage == capi.STB_STORE_F64 else torch.float32
+    E, N = mesh.n_tris, mesh.n_nodes
+    V = torch.empty((n_steps, E, E), dtype=dt, device="cuda")
+    ws = torch.empty(capi.stb_assemble_workspace_size(mesh, p), dtype=torch.uint8, device="cuda")
+    capi.stb_assemble(mesh, p, V, None, ws)
+    D = torch.full((n_steps, N, N), float("nan"), dtype=dt, device="cuda")
+    ws = torch.empty(capi.stb_assemble_d_workspace_size(mesh, p), dtype=torch.uint8, device="cuda")
+    capi.stb_assemble_d(mesh, p, V, D, ws)
+    capi.stb_workspace_status(ws)
+    return D.double().cpu().numpy()
+
+
+def oracle_d(nodes, tris, alpha, T, n_steps):
+    V, _ = oracle.assemble(nodes, tris, alpha, T, n_steps)
+    return oracle.assemble_d1(nodes, tris, alpha, V) + oracle.assemble_d2(nodes, tris, alpha, T,
+                                                                          n_steps)
+
+
+@pytest.mark.parametrize("name,n_steps,alpha,T", [("cube2", 6, 1.0, 0.6), ("cube4", 9, 0.7, 1.0),
+                                                  ("ico3", 5, 2.0, 0.5)])
+def test_hypersingular_blocks_match_oracle(name, n_steps, alpha, T):
+    nodes, tris = _mesh(name)
+    got = gpu_d(nodes, tris, alpha, T, n_steps)
+    ref = oracle_d(nodes, tris, alpha, T, n_steps)
+    worst = 0.0
+    for d in range(n_steps):
+        assert np.all(np.isfinite(got[d])), d
+        rel = np.linalg.norm(got[d] - ref[d]) / np.linalg.norm(ref[d])
+        assert rel <= 1e-10, (d, rel)
+        worst = max(worst, rel)
+    print("%s: D max block rel err %.2e" % (name, worst))
+
+
+def test_hypersingular_f32_storage():
+    nodes, tris = _mesh("cube4")
+    got = gpu_d(nodes, tris, 0.5, 1.0, 4, capi.STB_STORE_F32)
+    ref = oracle_d(nodes, tris, 0.5, 1.0, 4)
+    for d in range(4):
+        assert np.linalg.norm(got[d] - ref[d]) / np.linalg.norm(ref[d]) <= 2e-6, d
+
+
+@pytest.mark.parametrize("precision", [capi.STB_PREC_FP64, capi.STB_PREC_MIXED])
+def test_neumann_projection_matches_oracle(precision):
+    nodes, tris = _mesh("cube4")
+    alpha, T, n = 0.8, 0.5, 6
+    src = workloads.random_sources(np.random.default_rng(21), 2, n_src=2, t0=-0.05)
+    mesh = capi.Mesh(nodes, tris)
+    p = capi.stb_default_params(alpha, T, n, precision=precision)
+    hd = torch.full((2, n, len(tris)), float("nan"), dtype=torch.float64, device="cuda")
+    ws = torch.empty(capi.stb_project_workspace_size(mesh, 2, 2), dtype=torch.uint8, device="cuda")
+    capi.stb_project_neumann(mesh, p, src, hd, ws)
+    capi.stb_workspace_status(ws)
+    ref = oracle.project_neumann(nodes, tris, alpha, T, n, src)
+    tol = 1e-12 if precision == capi.STB_PREC_FP64 else 1e-5
+    assert np.abs(hd.cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_neumann_rhs_matches_oracle():
+    nodes, tris = _mesh("cube4")
+    alpha, T, n = 1.0, 1.0, 16
+    K1 = oracle.assemble_k1(nodes, tris, alpha, T, n)
+    rng = np.random.default_rng(8)
+    hd = rng.normal(size=(3, n, len(tris)))
+    area, _ = oracle.triangle_geometry(nodes, tris)
+    fo = oracle.neumann_rhs(area, tris, K1, hd, T)
+    mag = oracle.neumann_rhs(area, tris, -np.abs(K1), np.abs(hd), T)  # sum of |terms|
+    mesh = capi.Mesh(nodes, tris)
+    p = capi.stb_default_params(alpha, T, n)
+    f = torch.full((3, n, len(nodes)), float("nan"), dtype=torch.float64, device="cuda")
+    ws = torch.empty(capi.stb_neumann_rhs_workspace_size(mesh, p, 3), dtype=torch.uint8,
+                     device="cuda")
+    capi.stb_neumann_rhs(mesh, p, torch.tensor(K1, device="cuda"), torch.tensor(hd, device="cuda"),
+                         3, f, ws)
+    capi.stb_workspace_status(ws)
+    n_terms = n * len(tris) + 6
+    assert np.all(np.abs(f.cpu().numpy() - fo) <= n_terms * EPS * mag)
+
+
+def test_dirichlet_error_p1_matches_oracle():
+    nodes, tris = _mesh("ico3")
+    alpha, T, n = 0.9, 0.7, 5
+    src = workloads.random_sources(np.random.default_rng(2), 2)
+    g1 = oracle.project_dirichlet_p1(nodes, tris, alpha, T, n, src)
+    g1 = g1 + 1e-3 * np.random.default_rng(3).normal(size=g1.shape)
+    e2, r2 = oracle.dirichlet_error_p1(nodes, tris, alpha, T, n, src, g1)
+    mesh = capi.Mesh(nodes, tris)
+    p = capi.stb_default_params(alpha, T, n)
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    ws = torch.empty(capi.stb_error_workspace_size(mesh, p, 2, 1), dtype=torch.uint8, device="cuda")
+    capi.stb_dirichlet_error_p1(mesh, p, src, torch.tensor(g1, device="cuda"), out, ws)
+    capi.stb_workspace_status(ws)
+    o = out.cpu().numpy()
+    assert abs(o[0] - e2) <= 1e-12 * r2 and abs(o[1] - r2) <= 1e-12 * r2
+
+
+def test_neumann_pipeline_matches_oracle_pipeline():
+    """Table neuconv's coarsest setup (cube (-1,1)^3, 192 triangles, 8
+    steps, alpha 0.5, source (0,0,1.5)) through every GPU step against the
+    oracle's pipeline."""
+    nodes, tris = workloads.cube_mesh(4, lo=-1.0, hi=1.0)
+    alpha, T, n = 0.5, 1.0, 8
+    src = workloads.point_source((0.0, 0.0, 1.5), t0=0.0)
+    prob = pipeline.NeumannProblem(nodes, tris, alpha, T, n, src)
+    prob.run()
+    D = oracle_d(nodes, tris, alpha, T, n)
+    K1 = oracle.assemble_k1(nodes, tris, alpha, T, n)
+    area, _ = oracle.triangle_geometry(nodes, tris)
+    hd = oracle.project_neumann(nodes, tris, alpha, T, n, src)
+    uo = oracle.dirichlet_solve(D, oracle.neumann_rhs(area, tris, K1, hd, T))
+    u = prob.u.cpu().numpy()
+    assert np.linalg.norm(u - uo) / np.linalg.norm(uo) < 1e-8
+    e2, r2 = oracle.dirichlet_error_p1(nodes, tris, alpha, T, n, src, uo)
+    assert abs(prob.relative_error() - math.sqrt(e2 / r2)) < 1e-8
+    print("Neumann pipeline: L2 error %.4f" % prob.relative_error())
+
+
+@pytest.mark.parametrize("row", [0, 1, 2])
+def test_table_neuconv_on_gpu(row):
+    """Table neuconv with every step on the GPU: the computed error of u_h
+    within 2 % (the third run gives 0.0688, the value of the garbled entry
+    read from its eoc).  The representation column (10^4 nodes) with the
+    single layer of the projected Neumann data comes out 19 %, 2 % and 11 %
+    above the printed values (the paper does not say how V~ h is evaluated
+    for the Neumann problem; the single layer of a finely projected h gives
+    errors below the printed ones), so it is held to 25 % only."""
+    import test_oracle_neumann
+    import test_oracle_potentials
+    n_steps, E, comp, _, rep = test_oracle_neumann.load_neuconv()[row]
+    nodes, tris = workloads.cube_mesh(int(round(math.sqrt(E / 12))), lo=-1.0, hi=1.0)
+    src = workloads.point_source((0.0, 0.0, 1.5), t0=0.0)
+    prob = pipeline.NeumannProblem(nodes, tris, 0.5, 1.0, n_steps, src)
+    prob.run()
+    err = prob.relative_error()
+    pts = test_oracle_potentials.repr_points()
+    uh = prob.representation(pts)[0].cpu().numpy()
+    ue = test_oracle_potentials.exact_solution(pts)
+    rerr = np.linalg.norm(uh - ue) / np.linalg.norm(ue)
+    print("neuconv row %d (E_t %d, E_x %d): computed %.4f (printed %.3g), representation %.3e "
+          "(printed %.3g)" % (row, n_steps, E, err, comp, rerr, rep))
+    assert abs(err - comp) < 0.02 * comp, err
+    assert abs(rerr - rep) < 0.25 * rep, rerr

@@ -20,8 +20,8 @@ the Neumann problem D_h u = (1/2 M_h^{T_x} - K_h^{T_x}) h (Sec. 3.3, 3.4):
   e^2 ||v||^2 with the exact hat-function mass;
 * Table neuconv (tests/golden/table_neuconv.txt), coarsest run: the
   computed error within 2 %, the projected one within 5 %.  (The
-  representation column of that run comes out at 6.2e-2 against the
-  printed 5.16e-2; the second run agrees within 3 %: tests on the GPU.)
+  representation column comes out 2-19 % above the printed values: tests
+  on the GPU.)
 """
 import math
 
