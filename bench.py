@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-potentials", action="store_true",
                     help="skip the potential evaluation report (outside the timed region)")
+    ap.add_argument("--no-neumann", action="store_true",
+                    help="skip the Neumann problem report (outside the timed region)")
     ap.add_argument("--no-p1", action="store_true",
                     help="skip the piecewise-linear data pipeline report (outside the timed region)")
     return ap.parse_args()
@@ -508,6 +510,31 @@ def run_gpu(args):
             p1["k1_point_level_evals_per_s"] = float(n_reg_pairs) * 81.0 * n / (k1_ms / 1e3)
         del pp
 
+    # the Neumann problem (Sec. 3.3) on the same mesh and steps, first alpha:
+    # stage times after a warm-up pass, the hypersingular kernels' times
+    neu = None
+    if not args.no_neumann:
+        pn = pipeline.NeumannProblem(nodes, tris, alphas[0], wl["T"], n, src, mesh=mesh,
+                                     precision=prec, storage=storage)
+        pn.run(stream)
+        torch.cuda.synchronize()
+        capi.stb_trace_enable(True)
+        capi.stb_trace_reset()
+        nms = {}
+        for label, fn in (("assemble", pn.assemble), ("project", pn.project), ("rhs", pn.rhs),
+                          ("solve", pn.solve), ("error", pn.error)):
+            a_.record(stream)
+            fn(stream)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            nms[label] = a_.elapsed_time(b_)
+        capi.stb_trace_enable(False)
+        trn = capi.stb_trace_read()
+        neu = {"alpha": alphas[0], "stage_ms": nms, "rel_l2_error_u": pn.relative_error(),
+               "kernels_ms": {k: v[1] for k, v in trn.items()}}
+        del pn
+        torch.cuda.empty_cache()
+
     # the representation formula's potentials on the workload of the paper's
     # potential benchmark (Table reprsc: cube (-1,1)^3, 3072 triangles, 32
     # steps, 33 x 33 points x 32 step midpoints = 34848 points), seeded
@@ -551,7 +578,8 @@ def run_gpu(args):
                        "l2": "no flush: every step writes %.1f GB of V/K blocks (>> 129 MB L2)"
                              % (2 * (4 if mixed else 8) * n * E * E * len(alphas) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "mixed_vs_fp64": cmp, "p1_data": p1, "potentials": pots, "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
+            "mixed_vs_fp64": cmp, "p1_data": p1, "neumann": neu, "potentials": pots,
+            "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
             "rel_l2_error_w": rel_err, "solve": solve_info, "gpu_launches": launches,
             "kernels_ms": {k: v[1] for k, v in trace.items()}, "roofline": roof, "e2e": e2e}
     if rank == 0:

@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "stb_assemble.h"
@@ -1153,9 +1154,9 @@ static NodeStars node_stars(const Mesh &m) {
 
 template <class OutT>
 static stb_status run_hypersingular(const Mesh &m, const stb_params &p, const OutT *V, OutT *D,
-                                    const AssemblyLayout &L, const int32_t *star_off,
-                                    const int32_t *star_tri, const double *star_curl,
-                                    cudaStream_t s) {
+                                    const AssemblyLayout &L, const AssemblyLayout *Lmix,
+                                    const int32_t *star_off, const int32_t *star_tri,
+                                    const double *star_curl, cudaStream_t s) {
     const int E = (int)m.n_tris, N = (int)m.n_nodes;
     const double h = p.T / p.n_steps;
     dim3 g1((N + 127) / 128, N, p.n_steps);
@@ -1164,12 +1165,21 @@ static stb_status run_hypersingular(const Mesh &m, const stb_params &p, const Ou
                                                p.alpha * p.alpha, D);
     stb_status st = check_launch("k_hypersingular_d1");
     if (st) return st;
-    dim3 g2((E + REG_THREADS - 1) / REG_THREADS, E);
-    count_launch(s);
-    k_regular_d2_f64<OutT><<<g2, REG_THREADS, 0, s>>>(L.geo, m.d_tris, E, N, L.rule,
-                                                       p.quad_regular * p.quad_regular,
-                                                       p.n_steps, p.alpha, h, D);
-    if ((st = check_launch("k_regular_d2_f64"))) return st;
+    if constexpr (std::is_same<OutT, float>::value) {
+        if (Lmix) {  // separated pairs in mixed precision
+            stb_params pm = p;
+            pm.precision = STB_PREC_MIXED;
+            if ((st = run_d2_regular_mixed(m, pm, D, *Lmix, s))) return st;
+        }
+    }
+    if (!Lmix) {
+        dim3 g2((E + REG_THREADS - 1) / REG_THREADS, E);
+        count_launch(s);
+        k_regular_d2_f64<OutT><<<g2, REG_THREADS, 0, s>>>(L.geo, m.d_tris, E, N, L.rule,
+                                                           p.quad_regular * p.quad_regular,
+                                                           p.n_steps, p.alpha, h, D);
+        if ((st = check_launch("k_regular_d2_f64"))) return st;
+    }
     if (m.n_touch == 0) return STB_OK;
     SSTables tab{};
     const double *base = L.ss;
@@ -1359,10 +1369,14 @@ extern "C" stb_status stb_assemble_d_workspace_size(const stb_mesh *mesh, const 
     if (!mesh || !bytes || !params) return fail(STB_ERR_INVALID_ARG, "mesh, params and bytes must be given");
     stb_status st = check_assembly_params(params);
     if (st) return st;
-    if (params->precision != STB_PREC_FP64)
-        return fail(STB_ERR_INVALID_ARG, "the hypersingular operator is assembled in FP64");
+    if (params->precision == STB_PREC_MIXED && params->storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "mixed precision needs STB_STORE_F32 blocks");
     if (mesh->m.n_nodes > 65535) return fail(STB_ERR_INVALID_ARG, "n_nodes must be <= 65535");
-    *bytes = align256(assembly_layout(mesh->m, *params, nullptr, 0).bytes) + stars_bytes(mesh->m);
+    stb_params p64 = *params;
+    p64.precision = STB_PREC_FP64;
+    *bytes = align256(assembly_layout(mesh->m, p64, nullptr, 0).bytes) + stars_bytes(mesh->m);
+    if (params->precision == STB_PREC_MIXED)
+        *bytes += align256(assembly_layout(mesh->m, *params, nullptr, 0).bytes);
     return STB_OK;
 }
 
@@ -1377,16 +1391,28 @@ extern "C" stb_status stb_assemble_d(const stb_mesh *mesh, const stb_params *par
     if (m.n_tris > 65535) return fail(STB_ERR_INVALID_ARG, "dense assembly supports E <= 65535");
     const NodeStars S = node_stars(m);
     if (S.max_star > 32) return fail(STB_ERR_INVALID_ARG, "a node belongs to more than 32 triangles");
-    AssemblyLayout L = assembly_layout(m, *params, ws, ws_bytes);
+    // FP64 tables (touching pairs, and separated pairs in FP64), then the
+    // node stars, then (mixed) a second problem layout with the FP32 tables
+    stb_params p64 = *params;
+    p64.precision = STB_PREC_FP64;
+    AssemblyLayout L = assembly_layout(m, p64, ws, ws_bytes);
     char *p = static_cast<char *>(ws) + align256(L.bytes);
     int32_t *star_off = reinterpret_cast<int32_t *>(p);
     p += align256(sizeof(int32_t) * (m.n_nodes + 1));
     int32_t *star_tri = reinterpret_cast<int32_t *>(p);
     p += align256(sizeof(int32_t) * 3 * m.n_tris);
     double *star_curl = reinterpret_cast<double *>(p);
+    p += align256(sizeof(double) * 9 * m.n_tris);
+    const bool mixed = params->precision == STB_PREC_MIXED;
+    AssemblyLayout Lm{};
+    if (mixed) {  // Carve starts 256 bytes in: the status word of this sub-layout is unused
+        const size_t off = (size_t)(p - static_cast<char *>(ws));
+        Lm = assembly_layout(m, *params, p, ws_bytes - off);
+    }
     cudaStream_t s = (cudaStream_t)stream;
     STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
-    if ((st = prepare_fp64(m, *params, L, status_word(ws), s))) return st;
+    if ((st = prepare_fp64(m, p64, L, status_word(ws), s))) return st;
+    if (mixed && (st = prepare_mixed(m, *params, Lm, status_word(ws), s))) return st;
     STB_CUDA(cudaMemcpyAsync(star_off, S.off.data(), sizeof(int32_t) * S.off.size(),
                              cudaMemcpyHostToDevice, s));
     STB_CUDA(cudaMemcpyAsync(star_tri, S.tri.data(), sizeof(int32_t) * S.tri.size(),
@@ -1394,11 +1420,11 @@ extern "C" stb_status stb_assemble_d(const stb_mesh *mesh, const stb_params *par
     STB_CUDA(cudaMemcpyAsync(star_curl, S.curl.data(), sizeof(double) * S.curl.size(),
                              cudaMemcpyHostToDevice, s));
     if (params->storage == STB_STORE_F64)
-        st = run_hypersingular<double>(m, *params, (const double *)V, (double *)D, L, star_off,
-                                       star_tri, star_curl, s);
+        st = run_hypersingular<double>(m, p64, (const double *)V, (double *)D, L, nullptr,
+                                       star_off, star_tri, star_curl, s);
     else
-        st = run_hypersingular<float>(m, *params, (const float *)V, (float *)D, L, star_off,
-                                      star_tri, star_curl, s);
+        st = run_hypersingular<float>(m, p64, (const float *)V, (float *)D, L,
+                                      mixed ? &Lm : nullptr, star_off, star_tri, star_curl, s);
     if (st) return st;
     // the host tables above are copied from pageable memory before the
     // copies return; nothing else refers to them

@@ -1069,6 +1069,230 @@ stb_status run_assembly_k1_mixed(const Mesh &m, const stb_params &p, float *K1,
     return check_launch("k_singular_k1_mixed");
 }
 
+// ---------------------------------- hypersingular operator D^2, mixed ---
+// D^{2,d} (eq. D2d) without differencing antiderivatives: blocks 0 and 1 from
+// the closed forms alpha F(h) and alpha (F(2h) - 2 F(h)), F(delta) =
+// int_0^delta G = erfc(rho / (2 sqrt(alpha delta))) / (4 pi alpha rho); block
+// d >= 2 as the hat-weighted time integral of dG/ds (the second difference
+// of F is the hat convolution of F'' = dG/ds), by the Gauss nodes of the
+// mixed tables: per node the factor of the K tables, with
+//   alpha dG/ds = -alpha G / (2 delta) (3 - rho^2 / (2 alpha delta))
+//             = -alpha cK (3 + 2 ln2 t) e / w,  t = rho^2 b,  e = exp2(t).
+// p1 x p1 weights: the test points' barycentric weights are summed first
+// per trial point, the node weights applied per trial point, and the nine
+// vertex-pair values of a completed block go out with atomics into D
+// (which holds D^1).
+constexpr int D2_G = 2;         // intervals per pass over the points
+constexpr float TWO_LN2 = 1.3862943611198906f;
+
+// Separated pair (l, j): all blocks of D^2.
+__device__ __forceinline__ void regular_pair_d2_mixed(const double *__restrict__ geo,
+                                                      const int32_t *__restrict__ tris, int E,
+                                                      int N, const float *__restrict__ rule,
+                                                      int nq, const float4 *xa,
+                                                      const float4 *xl, const float *nd,
+                                                      int n_steps, const MixConsts &g,
+                                                      float alpha, float *__restrict__ D,
+                                                      int l, int j) {
+    const int tl[3] = {tris[3 * l], tris[3 * l + 1], tris[3 * l + 2]};
+    const int tj[3] = {tris[3 * j], tris[3 * j + 1], tris[3 * j + 2]};
+    {
+        bool t = false;
+        for (int i = 0; i < 3; ++i) t |= (tl[i] == tj[0]) | (tl[i] == tj[1]) | (tl[i] == tj[2]);
+        if (t) return;
+    }
+    const double *gl = geo + (size_t)l * GEO_STRIDE, *gj = geo + (size_t)j * GEO_STRIDE;
+    float Dv[3], B1[3], B2[3];
+    for (int c = 0; c < 3; ++c) {
+        Dv[c] = (float)(gl[GEO_V0 + c] - gj[GEO_V0 + c]);
+        B1[c] = (float)(gj[GEO_V1 + c] - gj[GEO_V0 + c]);
+        B2[c] = (float)(gj[GEO_V2 + c] - gj[GEO_V1 + c]);
+    }
+    const double nn = gl[GEO_N] * gj[GEO_N] + gl[GEO_N + 1] * gj[GEO_N + 1] + gl[GEO_N + 2] * gj[GEO_N + 2];
+    const float scale = (float)(4.0 * gl[GEO_AREA] * gj[GEO_AREA] * nn);
+    const size_t NN = (size_t)N * N;
+    auto emit = [&](int d, const float (&v)[9]) {
+        float *blk = D + (size_t)d * NN;
+#pragma unroll
+        for (int va = 0; va < 3; ++va)
+#pragma unroll
+            for (int vb = 0; vb < 3; ++vb) atomicAdd(blk + (size_t)tl[va] * N + tj[vb], v[3 * va + vb]);
+    };
+    const float pG = 0.25f / 3.14159265f;  // alpha F = erfc / (4 pi rho)
+
+    // pass 1: blocks 0 and 1 (closed forms) and the k = 1 interval of block 2
+    float b0[9], b1[9], b2[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) b0[k] = b1[k] = b2[k] = 0.f;
+    for (int b = 0; b < nq; ++b) {
+        const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
+        const float r0b = Dv[0] - (t1 * B1[0] + t2 * B2[0]);
+        const float r1b = Dv[1] - (t1 * B1[1] + t2 * B2[1]);
+        const float r2b = Dv[2] - (t1 * B1[2] + t2 * B2[2]);
+        float s0[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < nq; ++a) {
+            const float4 xq = xa[a], lq = xl[a];  // lq: w_a lambda_v(a), v = 0..2
+            const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
+            const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+            const float irho = rsqrtf(rr), rho = rr * irho;
+            const float e1 = erfcf(rho * g.c1), e2 = erfcf(rho * g.c2);
+            const float f0 = pG * irho * e1, f1 = pG * irho * (e2 - 2.f * e1);
+            float f2 = 0.f;
+            if (n_steps > 2) {
+#pragma unroll
+                for (int q = 0; q < MIX_NG1; ++q) {
+                    const float4 c = reinterpret_cast<const float4 *>(nd)[q];
+                    const float t = rr * c.x;
+                    f2 = fmaf(-alpha * c.z * fmaf(TWO_LN2, t, 3.f), ex2(t), f2);
+                }
+            }
+            const float lw[3] = {lq.x, lq.y, lq.z};
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                s0[v] = fmaf(lw[v], f0, s0[v]);
+                s1[v] = fmaf(lw[v], f1, s1[v]);
+                s2[v] = fmaf(lw[v], f2, s2[v]);
+            }
+        }
+        const float lb[3] = {(1.f - t1) * wb, (t1 - t2) * wb, t2 * wb};
+#pragma unroll
+        for (int va = 0; va < 3; ++va)
+#pragma unroll
+            for (int vb = 0; vb < 3; ++vb) {
+                b0[3 * va + vb] = fmaf(s0[va], lb[vb], b0[3 * va + vb]);
+                b1[3 * va + vb] = fmaf(s1[va], lb[vb], b1[3 * va + vb]);
+                b2[3 * va + vb] = fmaf(s2[va], lb[vb], b2[3 * va + vb]);
+            }
+    }
+    float carry[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        b0[k] *= scale;
+        b1[k] *= scale;
+        carry[k] = scale * b2[k];
+    }
+    emit(0, b0);
+    if (n_steps > 1) emit(1, b1);
+
+    // blocks d >= 2: table chunks of MIX_CH intervals, passes of D2_G
+    const float *tab = nd + MIX_K1;
+    for (int d0 = 2; d0 < n_steps; d0 += MIX_CH) {
+        const int ng = mixed_chunk_ng(d0), ivf = mixed_iv_floats(ng);
+        const int n_int = min(MIX_CH, n_steps - d0);
+        for (int u0 = 0; u0 < n_int; u0 += D2_G) {
+            const float *tg = tab + u0 * ivf;
+            float fall[D2_G][9], rise[D2_G][9];
+#pragma unroll
+            for (int gg = 0; gg < D2_G; ++gg)
+#pragma unroll
+                for (int k = 0; k < 9; ++k) fall[gg][k] = rise[gg][k] = 0.f;
+            for (int b = 0; b < nq; ++b) {
+                const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
+                const float r0b = Dv[0] - (t1 * B1[0] + t2 * B2[0]);
+                const float r1b = Dv[1] - (t1 * B1[1] + t2 * B2[1]);
+                const float r2b = Dv[2] - (t1 * B1[2] + t2 * B2[2]);
+                float C[D2_G][4][3];  // per interval, node, test vertex
+#pragma unroll
+                for (int gg = 0; gg < D2_G; ++gg)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) C[gg][q][0] = C[gg][q][1] = C[gg][q][2] = 0.f;
+                for (int a = 0; a < nq; ++a) {
+                    const float4 xq = xa[a], lq = xl[a];
+                    const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
+                    const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+#pragma unroll
+                    for (int gg = 0; gg < D2_G; ++gg) {
+                        const float4 bb = ld_tab<true>(tg + gg * ivf);
+                        const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (q >= ng) break;
+                            const float t = rr * bq[q];
+                            const float f = fmaf(TWO_LN2, t, 3.f) * ex2(t);
+                            C[gg][q][0] = fmaf(lq.x, f, C[gg][q][0]);
+                            C[gg][q][1] = fmaf(lq.y, f, C[gg][q][1]);
+                            C[gg][q][2] = fmaf(lq.z, f, C[gg][q][2]);
+                        }
+                    }
+                }
+                const float lb[3] = {(1.f - t1) * wb, (t1 - t2) * wb, t2 * wb};
+#pragma unroll
+                for (int gg = 0; gg < D2_G; ++gg) {
+                    if (u0 + gg >= n_int) break;
+                    float Fa[3] = {0.f, 0.f, 0.f}, Ra[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (q >= ng) break;
+                        const float4 c = ld_tab<true>(tg + gg * ivf + 4 + 4 * q);  // (cVf, cKf, cVr, cKr)
+#pragma unroll
+                        for (int va = 0; va < 3; ++va) {
+                            Fa[va] = fmaf(c.y, C[gg][q][va], Fa[va]);
+                            Ra[va] = fmaf(c.w, C[gg][q][va], Ra[va]);
+                        }
+                    }
+#pragma unroll
+                    for (int va = 0; va < 3; ++va)
+#pragma unroll
+                        for (int vb = 0; vb < 3; ++vb) {
+                            fall[gg][3 * va + vb] = fmaf(Fa[va], lb[vb], fall[gg][3 * va + vb]);
+                            rise[gg][3 * va + vb] = fmaf(Ra[va], lb[vb], rise[gg][3 * va + vb]);
+                        }
+                }
+            }
+            const float sa = -alpha * scale;
+#pragma unroll
+            for (int gg = 0; gg < D2_G; ++gg) {
+                if (u0 + gg >= n_int) break;
+                float v[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    v[k] = fmaf(sa, fall[gg][k], carry[k]);
+                    carry[k] = sa * rise[gg][k];
+                }
+                emit(d0 + u0 + gg, v);
+            }
+        }
+        tab += MIX_CH * ivf;
+    }
+}
+
+__global__ void __launch_bounds__(MREG_THREADS)
+k_regular_d2_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E, int N,
+                   const float *__restrict__ rule, int nq, const float *__restrict__ nodes,
+                   int n_nodes_f, int n_steps, MixConsts g, float alpha, float *__restrict__ D) {
+    extern __shared__ float smf[];
+    float4 *xa = reinterpret_cast<float4 *>(smf);       // x_a - P0_l and w_a
+    float4 *xl = xa + MAX_RULE_M;                       // w_a lambda_v(a)
+    float *nd = smf + 8 * MAX_RULE_M;                   // time nodes
+    const int l = blockIdx.y;
+    const int j = blockIdx.x * MREG_THREADS + threadIdx.x;
+    load_test_points(geo + (size_t)l * GEO_STRIDE, rule, nq, xa);
+    for (int a = threadIdx.x; a < nq; a += MREG_THREADS) {
+        const float s1 = rule[4 * a], s2 = rule[4 * a + 1], w = rule[4 * a + 2];
+        xl[a] = make_float4((1.f - s1) * w, (s1 - s2) * w, s2 * w, 0.f);
+    }
+    for (int i = threadIdx.x; i < n_nodes_f; i += MREG_THREADS) nd[i] = nodes[i];
+    __syncthreads();
+    if (j < E) regular_pair_d2_mixed(geo, tris, E, N, rule, nq, xa, xl, nd, n_steps, g, alpha, D, l, j);
+}
+
+stb_status run_d2_regular_mixed(const Mesh &m, const stb_params &p, float *D,
+                                const AssemblyLayout &L, cudaStream_t s) {
+    const int E = (int)m.n_tris, N = (int)m.n_nodes;
+    const int nq = p.quad_regular * p.quad_regular;
+    const MixConsts g = mix_consts(p);
+    const int nf = (int)mixed_node_floats(p.n_steps);
+    const size_t smem = sizeof(float) * (8 * MAX_RULE_M + (size_t)nf);
+    STB_CUDA(cudaFuncSetAttribute(k_regular_d2_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    dim3 grid((E + MREG_THREADS - 1) / MREG_THREADS, E);
+    count_launch(s);
+    k_regular_d2_mixed<<<grid, MREG_THREADS, smem, s>>>(L.geo, m.d_tris, E, N, L.mrule, nq,
+                                                         L.mnodes, nf, p.n_steps, g,
+                                                         (float)p.alpha, D);
+    return check_launch("k_regular_d2_mixed");
+}
+
 // -------------------------------------------------------------- batches ---
 // Many independent problems (meshes, alpha, steps) in one persistent launch
 // for their separated pairs and one launch for their touching pairs, all in

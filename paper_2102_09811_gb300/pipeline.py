@@ -142,7 +142,7 @@ class NeumannProblem:
         self.params = mk(precision)
         mixed_ok = precision == capi.STB_PREC_MIXED and storage == capi.STB_STORE_F32
         self.params_k1 = mk(capi.STB_PREC_MIXED if mixed_ok else capi.STB_PREC_FP64)
-        self.params_d = mk(capi.STB_PREC_FP64)
+        self.params_d = mk(capi.STB_PREC_MIXED if mixed_ok else capi.STB_PREC_FP64)
         self.sources = sources
         self.nrhs, self.n_src = sources.shape[0], sources.shape[1]
         self.q_space, self.n_time = q_space, n_time
