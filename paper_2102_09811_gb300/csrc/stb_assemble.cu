@@ -1155,8 +1155,9 @@ static NodeStars node_stars(const Mesh &m) {
 template <class OutT>
 static stb_status run_hypersingular(const Mesh &m, const stb_params &p, const OutT *V, OutT *D,
                                     const AssemblyLayout &L, const AssemblyLayout *Lmix,
-                                    const int32_t *star_off, const int32_t *star_tri,
-                                    const double *star_curl, cudaStream_t s) {
+                                    const float *coords, const int32_t *star_off,
+                                    const int32_t *star_tri, const double *star_curl,
+                                    cudaStream_t s) {
     const int E = (int)m.n_tris, N = (int)m.n_nodes;
     const double h = p.T / p.n_steps;
     dim3 g1((N + 127) / 128, N, p.n_steps);
@@ -1166,10 +1167,11 @@ static stb_status run_hypersingular(const Mesh &m, const stb_params &p, const Ou
     stb_status st = check_launch("k_hypersingular_d1");
     if (st) return st;
     if constexpr (std::is_same<OutT, float>::value) {
-        if (Lmix) {  // separated pairs in mixed precision
+        if (Lmix) {  // mixed precision: separated and touching pairs
             stb_params pm = p;
             pm.precision = STB_PREC_MIXED;
             if ((st = run_d2_regular_mixed(m, pm, D, *Lmix, s))) return st;
+            return run_d2_singular_mixed(m, pm, D, *Lmix, coords, s);
         }
     }
     if (!Lmix) {
@@ -1376,7 +1378,8 @@ extern "C" stb_status stb_assemble_d_workspace_size(const stb_mesh *mesh, const 
     p64.precision = STB_PREC_FP64;
     *bytes = align256(assembly_layout(mesh->m, p64, nullptr, 0).bytes) + stars_bytes(mesh->m);
     if (params->precision == STB_PREC_MIXED)
-        *bytes += align256(assembly_layout(mesh->m, *params, nullptr, 0).bytes);
+        *bytes += align256(assembly_layout(mesh->m, *params, nullptr, 0).bytes) +
+                  align256(k1_coords_floats(*params) * 4);
     return STB_OK;
 }
 
@@ -1405,14 +1408,27 @@ extern "C" stb_status stb_assemble_d(const stb_mesh *mesh, const stb_params *par
     p += align256(sizeof(double) * 9 * m.n_tris);
     const bool mixed = params->precision == STB_PREC_MIXED;
     AssemblyLayout Lm{};
+    float *coords = nullptr;
     if (mixed) {  // Carve starts 256 bytes in: the status word of this sub-layout is unused
         const size_t off = (size_t)(p - static_cast<char *>(ws));
         Lm = assembly_layout(m, *params, p, ws_bytes - off);
+        coords = reinterpret_cast<float *>(p + align256(Lm.bytes));
     }
     cudaStream_t s = (cudaStream_t)stream;
     STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
     if ((st = prepare_fp64(m, p64, L, status_word(ws), s))) return st;
-    if (mixed && (st = prepare_mixed(m, *params, Lm, status_word(ws), s))) return st;
+    if (mixed) {
+        if ((st = prepare_mixed(m, *params, Lm, status_word(ws), s))) return st;
+        std::vector<float> host;
+        std::vector<double> s1, s2, t1, t2, w;
+        for (int cls = 1; cls <= 3; ++cls) {
+            ss_rule(cls, params->quad_singular, s1, s2, t1, t2, w);
+            for (auto *v : {&s1, &s2, &t1, &t2})
+                for (double x : *v) host.push_back((float)x);
+        }
+        STB_CUDA(cudaMemcpyAsync(coords, host.data(), host.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, s));
+    }
     STB_CUDA(cudaMemcpyAsync(star_off, S.off.data(), sizeof(int32_t) * S.off.size(),
                              cudaMemcpyHostToDevice, s));
     STB_CUDA(cudaMemcpyAsync(star_tri, S.tri.data(), sizeof(int32_t) * S.tri.size(),
@@ -1421,10 +1437,11 @@ extern "C" stb_status stb_assemble_d(const stb_mesh *mesh, const stb_params *par
                              cudaMemcpyHostToDevice, s));
     if (params->storage == STB_STORE_F64)
         st = run_hypersingular<double>(m, p64, (const double *)V, (double *)D, L, nullptr,
-                                       star_off, star_tri, star_curl, s);
+                                       nullptr, star_off, star_tri, star_curl, s);
     else
         st = run_hypersingular<float>(m, p64, (const float *)V, (float *)D, L,
-                                      mixed ? &Lm : nullptr, star_off, star_tri, star_curl, s);
+                                      mixed ? &Lm : nullptr, coords, star_off, star_tri,
+                                      star_curl, s);
     if (st) return st;
     // the host tables above are copied from pageable memory before the
     // copies return; nothing else refers to them

@@ -67,6 +67,9 @@ stb_status prepare_mixed(const Mesh &m, const stb_params &p, const AssemblyLayou
 // Mixed-precision D^2 of the separated pairs added into FP32 D [n_steps][N][N].
 stb_status run_d2_regular_mixed(const Mesh &m, const stb_params &p, float *D,
                                 const AssemblyLayout &L, cudaStream_t s);
+// Mixed-precision D^2 of the touching pairs (coords as for K1 below).
+stb_status run_d2_singular_mixed(const Mesh &m, const stb_params &p, float *D,
+                                 const AssemblyLayout &L, const float *coords, cudaStream_t s);
 stb_status run_assembly_k1_mixed(const Mesh &m, const stb_params &p, float *K1,
                                  const AssemblyLayout &L, const float *coords, cudaStream_t s);
 stb_status run_assembly_mixed(const Mesh &m, const stb_params &p, void *V, void *K,

@@ -1276,6 +1276,197 @@ k_regular_d2_mixed(const double *__restrict__ geo, const int32_t *__restrict__ t
     if (j < E) regular_pair_d2_mixed(geo, tris, E, N, rule, nq, xa, xl, nd, n_steps, g, alpha, D, l, j);
 }
 
+// Touching pairs of D^2 in mixed precision: one CTA per unordered pair, the
+// difference-form rule for r and the rules' coordinates for the barycentric
+// weights; entry (a, b) and, for a != b, the mirrored (b, a) receive the
+// same nine values.  Sub-chunks of D2_SCH intervals.
+constexpr int D2_SCH = 4;
+
+__global__ void __launch_bounds__(MSS_THREADS)
+k_singular_d2_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris,
+                    const TouchPair *__restrict__ pairs, int E, int N, MixSS tab, MixK1Coords co,
+                    const float *__restrict__ nodes, int n_steps, MixConsts g, float alpha,
+                    float *__restrict__ D) {
+    constexpr int S = D2_SCH + 1;
+    __shared__ float red[MSS_THREADS / 32][9 * S];
+    __shared__ float fin[9 * S];
+    const TouchPair P = pairs[blockIdx.x];
+    const int a = P.a, b = P.b, cls = P.cls;
+    if (a < 0 || b < a || b >= E || cls < PAIR_VERTEX || cls > PAIR_IDENTICAL) return;
+    const double *ga = geo + (size_t)a * GEO_STRIDE, *gb = geo + (size_t)b * GEO_STRIDE;
+    const int oa[3] = {P.perm & 3, (P.perm >> 2) & 3, (P.perm >> 4) & 3};
+    const int ob[3] = {(P.perm >> 6) & 3, (P.perm >> 8) & 3, (P.perm >> 10) & 3};
+    float X[4][3];
+    for (int c = 0; c < 3; ++c) {
+        const double A1 = ga[3 * oa[1] + c] - ga[3 * oa[0] + c], A2 = ga[3 * oa[2] + c] - ga[3 * oa[1] + c];
+        const double Bv1 = gb[3 * ob[1] + c] - gb[3 * ob[0] + c], Bv2 = gb[3 * ob[2] + c] - gb[3 * ob[1] + c];
+        if (cls == PAIR_IDENTICAL) {
+            X[0][c] = (float)-A1; X[1][c] = (float)-A2; X[2][c] = 0.f; X[3][c] = 0.f;
+        } else if (cls == PAIR_EDGE) {
+            X[0][c] = (float)-A1; X[1][c] = (float)A2; X[2][c] = (float)-Bv2; X[3][c] = 0.f;
+        } else {
+            X[0][c] = (float)A1; X[1][c] = (float)A2; X[2][c] = (float)-Bv1; X[3][c] = (float)-Bv2;
+        }
+    }
+    int na_node[3], nb_node[3];
+    for (int c = 0; c < 3; ++c) {
+        na_node[c] = tris[3 * a + oa[c]];
+        nb_node[c] = tris[3 * b + ob[c]];
+    }
+    const double nn = ga[GEO_N] * gb[GEO_N] + ga[GEO_N + 1] * gb[GEO_N + 1] + ga[GEO_N + 2] * gb[GEO_N + 2];
+    const float scale = (float)(4.0 * ga[GEO_AREA] * gb[GEO_AREA] * nn);
+    const bool ident = cls == PAIR_IDENTICAL;
+    const int npt = tab.n[cls];
+    const float *R0 = tab.p0[cls], *R1 = tab.p1[cls], *R2 = tab.p2[cls], *R3 = tab.p3[cls],
+                *W = tab.w[cls];
+    const float *S1 = co.s1[cls], *S2 = co.s2[cls], *T1 = co.t1[cls], *T2 = co.t2[cls];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t NN = (size_t)N * N;
+    const float pG = 0.25f / 3.14159265f;
+
+    // point p: r^2 and the nine weights w lambda_va(s) lambda_vb(t)
+    auto point = [&](int p, float &rr, float (&wl)[9]) {
+        const float q0 = R0[p], q1 = R1[p], q2 = R2[p], q3 = R3[p];
+        float r[3];
+        for (int c = 0; c < 3; ++c) r[c] = q0 * X[0][c] + q1 * X[1][c] + q2 * X[2][c] + q3 * X[3][c];
+        rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        const float w = W[p], s1 = S1[p], s2 = S2[p], t1 = T1[p], t2 = T2[p];
+        const float la[3] = {w * (1.f - s1), w * (s1 - s2), w * s2}, lb[3] = {1.f - t1, t1 - t2, t2};
+#pragma unroll
+        for (int va = 0; va < 3; ++va)
+#pragma unroll
+            for (int vb = 0; vb < 3; ++vb) wl[3 * va + vb] = la[va] * lb[vb];
+    };
+    auto reduce = [&](float *vals, int nv) {
+        for (int k = 0; k < nv; ++k) {
+            float v = vals[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < nv) {
+            float sum = 0.f;
+            for (int wi = 0; wi < MSS_THREADS / 32; ++wi) sum += red[wi][threadIdx.x];
+            fin[threadIdx.x] = scale * sum;
+        }
+        __syncthreads();
+    };
+    auto emit = [&](int d, int k, float val) {
+        const int va = k / 3, vb = k % 3;
+        float *blk = D + (size_t)d * NN;
+        atomicAdd(blk + (size_t)na_node[va] * N + nb_node[vb], val);
+        if (!ident) atomicAdd(blk + (size_t)nb_node[vb] * N + na_node[va], val);
+    };
+
+    // pass 1: blocks 0, 1 and the k = 1 interval of block 2 (27 sums)
+    {
+        float z[27];
+#pragma unroll
+        for (int i = 0; i < 27; ++i) z[i] = 0.f;
+        for (int p = threadIdx.x; p < npt; p += MSS_THREADS) {
+            float rr, wl[9];
+            point(p, rr, wl);
+            const float irho = rsqrtf(rr), rho = rr * irho;
+            const float e1 = erfcf(rho * g.c1), e2 = erfcf(rho * g.c2);
+            const float f0 = pG * irho * e1, f1 = pG * irho * (e2 - 2.f * e1);
+            float f2 = 0.f;
+            if (n_steps > 2) {
+#pragma unroll
+                for (int q = 0; q < MIX_NG1; ++q) {
+                    const float4 c = reinterpret_cast<const float4 *>(nodes)[q];
+                    const float t = rr * c.x;
+                    f2 = fmaf(-alpha * c.z * fmaf(TWO_LN2, t, 3.f), ex2(t), f2);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                z[k] = fmaf(wl[k], f0, z[k]);
+                z[9 + k] = fmaf(wl[k], f1, z[9 + k]);
+                z[18 + k] = fmaf(wl[k], f2, z[18 + k]);
+            }
+        }
+        // reduce in three rounds of nine (fin holds 9 S >= 27 entries)
+        reduce(z, 27);
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 9; ++k) {
+            emit(0, k, fin[k]);
+            if (n_steps > 1) emit(1, k, fin[9 + k]);
+        }
+    }
+    float carry[9];
+    for (int k = 0; k < 9; ++k) carry[k] = fin[18 + k];
+    __syncthreads();
+
+    const float *ntab = nodes + MIX_K1;
+    for (int d0 = 2; d0 < n_steps; d0 += MIX_CH) {
+        const int ng = mixed_chunk_ng(d0), ivf = mixed_iv_floats(ng);
+        for (int h0 = 0; h0 < MIX_CH && d0 + h0 < n_steps; h0 += D2_SCH) {
+            const int n_int = min(D2_SCH, n_steps - d0 - h0);
+            float acc[9 * S];
+#pragma unroll
+            for (int i = 0; i < 9 * S; ++i) acc[i] = 0.f;
+            const float *tb = ntab + h0 * ivf;
+            for (int p = threadIdx.x; p < npt; p += MSS_THREADS) {
+                float rr, wl[9];
+                point(p, rr, wl);
+#pragma unroll
+                for (int u = 0; u < D2_SCH; ++u) {
+                    if (u >= n_int) break;
+                    const float4 bb = ld_tab<false>(tb + u * ivf);
+                    const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
+                    float fall = 0.f, rise = 0.f;
+                    for (int q = 0; q < ng; ++q) {
+                        const float t = rr * bq[q];
+                        const float f = fmaf(TWO_LN2, t, 3.f) * ex2(t);
+                        const float4 c = ld_tab<false>(tb + u * ivf + 4 + 4 * q);
+                        fall = fmaf(c.y, f, fall);
+                        rise = fmaf(c.w, f, rise);
+                    }
+                    fall *= -alpha;
+                    rise *= -alpha;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        acc[k * S + u] = fmaf(wl[k], fall, acc[k * S + u]);
+                        acc[k * S + u + 1] = fmaf(wl[k], rise, acc[k * S + u + 1]);
+                    }
+                }
+            }
+            reduce(acc, 9 * S);
+            if (threadIdx.x == 0) {
+                for (int u = 0; u < n_int; ++u)
+                    for (int k = 0; k < 9; ++k)
+                        emit(d0 + h0 + u, k, fin[k * S + u] + (u == 0 ? carry[k] : 0.f));
+            }
+            for (int k = 0; k < 9; ++k) carry[k] = fin[k * S + n_int];
+            __syncthreads();
+        }
+        ntab += MIX_CH * ivf;
+    }
+}
+
+stb_status run_d2_singular_mixed(const Mesh &m, const stb_params &p, float *D,
+                                 const AssemblyLayout &L, const float *coords, cudaStream_t s) {
+    if (m.n_touch == 0) return STB_OK;
+    const MixConsts g = mix_consts(p);
+    const MixSS tab = mix_ss(L);
+    MixK1Coords co{};
+    const float *base = coords;
+    for (int cls = 1; cls <= 3; ++cls) {
+        const size_t n = L.ss_n[cls];
+        co.s1[cls] = base;
+        co.s2[cls] = base + n;
+        co.t1[cls] = base + 2 * n;
+        co.t2[cls] = base + 3 * n;
+        base += 4 * n;
+    }
+    count_launch(s);
+    k_singular_d2_mixed<<<(unsigned)m.n_touch, MSS_THREADS, 0, s>>>(
+        L.geo, m.d_tris, L.pairs, (int)m.n_tris, (int)m.n_nodes, tab, co, L.mnodes, p.n_steps, g,
+        (float)p.alpha, D);
+    return check_launch("k_singular_d2_mixed");
+}
+
 stb_status run_d2_regular_mixed(const Mesh &m, const stb_params &p, float *D,
                                 const AssemblyLayout &L, cudaStream_t s) {
     const int E = (int)m.n_tris, N = (int)m.n_nodes;

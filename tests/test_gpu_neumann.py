@@ -93,7 +93,8 @@ def test_hypersingular_mixed_blocks_match_oracle(name, n_steps, alpha, T):
     """Mixed precision: D^1 from the mixed V (FP32 points, stated V bound
     2e-6 per block), D^2 of separated pairs in the cancellation-free forms
     (closed forms for blocks 0, 1; hat-weighted Gauss nodes of dG/ds from
-    block 2 on), touching pairs in FP64; per block within 1e-5."""
+    block 2 on), touching pairs likewise with the difference-form rules;
+    per block within 1e-5."""
     nodes, tris = _mesh(name)
     got = gpu_d_mixed(nodes, tris, alpha, T, n_steps)
     ref = oracle_d(nodes, tris, alpha, T, n_steps)
