@@ -474,6 +474,28 @@ def run_gpu(args):
                "alpha": alphas[0], "mixed_vs_fp64_max_block_rel_err": {"V": max(errs_v), "K": max(errs_k)}}
         del pf
 
+    # V and the right-hand side without storing K (matrix-free K g), first
+    # problem: time against assembly + stored-K right-hand side
+    mfree = None
+    if mixed and p0.nrhs * n <= 128:
+        f_mf = torch.empty_like(p0.f)
+        ws_mf = torch.empty(capi.stb_assemble_vrhs_workspace_size(mesh, p0.params, p0.nrhs),
+                            dtype=torch.uint8, device="cuda")
+        capi.stb_assemble_vrhs(mesh, p0.params, p0.V, p0.g, p0.nrhs, f_mf, ws_mf, stream)
+        torch.cuda.synchronize()
+        a_.record(stream)
+        capi.stb_assemble_vrhs(mesh, p0.params, p0.V, p0.g, p0.nrhs, f_mf, ws_mf, stream)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        mf_ms = a_.elapsed_time(b_)
+        p0.assemble(stream)
+        p0.rhs(stream)
+        torch.cuda.synchronize()
+        mfree = {"ms": mf_ms, "stored_path_ms": stage_ms["assemble"] + stage_ms["rhs"],
+                 "rel_diff_f": float((torch.linalg.norm(f_mf - p0.f) / torch.linalg.norm(p0.f))),
+                 "k_bytes_not_stored": 4.0 * n * E * E}
+        del ws_mf, f_mf
+
     # the paper's own discretisation of the data (piecewise-linear in space,
     # Sec. 3.2 / 3.4) for the first problem: stage times after one warm-up
     # pass, the K1 kernels' share and the point-level evaluation rate
@@ -578,7 +600,8 @@ def run_gpu(args):
                        "l2": "no flush: every step writes %.1f GB of V/K blocks (>> 129 MB L2)"
                              % (2 * (4 if mixed else 8) * n * E * E * len(alphas) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "mixed_vs_fp64": cmp, "p1_data": p1, "neumann": neu, "potentials": pots,
+            "mixed_vs_fp64": cmp, "matrix_free_rhs": mfree, "p1_data": p1, "neumann": neu,
+            "potentials": pots,
             "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
             "rel_l2_error_w": rel_err, "solve": solve_info, "gpu_launches": launches,
             "kernels_ms": {k: v[1] for k, v in trace.items()}, "roofline": roof, "e2e": e2e}

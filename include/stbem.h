@@ -325,6 +325,22 @@ stb_status stb_dirichlet_error_p1(const stb_mesh *mesh, const stb_params *params
                                   const double *u1, int32_t q_space, int32_t n_time, double *out,
                                   void *workspace, size_t workspace_bytes, stb_stream stream);
 
+/* ---- V_h and the right-hand side without storing K_h (matrix-free K g) ----------
+ * For the Dirichlet problem with piecewise-constant data: V (device FP32
+ * [n_steps][E][E], overwritten) as stb_assemble writes it, and f (device FP64
+ * [nrhs][n_steps][E], overwritten) = (1/2 M_h + K_h) g for g (device FP64
+ * [nrhs][n_steps][E]), the blocks of K_h contracted with g as they are formed
+ * (never stored: half the memory of the assembly).  Needs STB_PREC_MIXED,
+ * STB_STORE_F32 and nrhs * n_steps <= 128.  The products of K with g are
+ * summed in FP32 per CTA of 128 columns and added in FP64 (relative error of
+ * the order of the mixed block error); atomics: last bits may differ between
+ * runs. */
+stb_status stb_assemble_vrhs_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                            int32_t nrhs, size_t *bytes);
+stb_status stb_assemble_vrhs(const stb_mesh *mesh, const stb_params *params, void *V,
+                             const double *g, int32_t nrhs, double *f, void *workspace,
+                             size_t workspace_bytes, stb_stream stream);
+
 /* ---- block-Toeplitz matrix-vector product (eq. V_mat) ---------------------------
  *   y_r^k = beta y_r^k + sum_{d=0}^{k} A^d x_r^{k-d},  k = 0..n_steps-1,
  * A: device [n_steps][E][E] of `a_storage`; x, y: device FP64

@@ -76,6 +76,8 @@ _SIGS = {
     "stb_neumann_solve_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
     "stb_neumann_solve": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
     "stb_dirichlet_error_p1": (_I32, [_P, _PAR, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _SZ, _P]),
+    "stb_assemble_vrhs_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
+    "stb_assemble_vrhs": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
     "stb_potentials_workspace_size": (_I32, [_P, _PAR, _I32, _I64, _I32, _PSZ]),
     "stb_potentials": (_I32, [_P, _PAR, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P, _SZ, _P]),
     "stb_potentials_grid_workspace_size": (_I32, [_P, _PAR, _I32, _I64, _I32, _PSZ]),
@@ -356,6 +358,18 @@ def stb_dirichlet_error_p1(mesh, params, sources, u1, out, workspace, q_space=8,
                                              _ptr(u1), q_space, n_time, _ptr(out), _ptr(workspace),
                                              workspace.numel() * workspace.element_size(),
                                              _stream(stream)), "stb_dirichlet_error_p1")
+
+
+def stb_assemble_vrhs_workspace_size(mesh, params, nrhs):
+    return _size(_library().stb_assemble_vrhs_workspace_size, mesh.handle, ctypes.byref(params),
+                 nrhs)
+
+
+def stb_assemble_vrhs(mesh, params, V, g, nrhs, f, workspace, stream=None):
+    _check(_library().stb_assemble_vrhs(mesh.handle, ctypes.byref(params), _ptr(V), _ptr(g), nrhs,
+                                        _ptr(f), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(),
+                                        _stream(stream)), "stb_assemble_vrhs")
 
 
 def stb_toeplitz_workspace_size(E, n_steps, nrhs):

@@ -1448,3 +1448,38 @@ extern "C" stb_status stb_assemble_d(const stb_mesh *mesh, const stb_params *par
     return STB_OK;
 }
 
+// ---- V and the right-hand side without K (matrix-free K g) -------------------
+extern "C" stb_status stb_assemble_vrhs_workspace_size(const stb_mesh *mesh,
+                                                       const stb_params *params, int32_t nrhs,
+                                                       size_t *bytes) {
+    if (!mesh || !bytes || !params) return fail(STB_ERR_INVALID_ARG, "mesh, params and bytes must be given");
+    stb_status st = check_assembly_params(params);
+    if (st) return st;
+    if (params->precision != STB_PREC_MIXED || params->storage != STB_STORE_F32)
+        return fail(STB_ERR_INVALID_ARG, "the matrix-free right-hand side needs STB_PREC_MIXED and STB_STORE_F32");
+    if (nrhs < 1 || (int64_t)nrhs * params->n_steps > 128)
+        return fail(STB_ERR_INVALID_ARG, "need 1 <= nrhs and nrhs * n_steps <= 128");
+    if (params->quad_regular * params->quad_regular > 256)
+        return fail(STB_ERR_INVALID_ARG, "quad_regular must be <= 16");
+    *bytes = align256(assembly_layout(mesh->m, *params, nullptr, 0).bytes);
+    return STB_OK;
+}
+
+extern "C" stb_status stb_assemble_vrhs(const stb_mesh *mesh, const stb_params *params, void *V,
+                                        const double *g, int32_t nrhs, double *f, void *ws,
+                                        size_t ws_bytes, stb_stream stream) {
+    if (!mesh || !V || !g || !f) return fail(STB_ERR_INVALID_ARG, "mesh, V, g and f must be given");
+    size_t need;
+    stb_status st = stb_assemble_vrhs_workspace_size(mesh, params, nrhs, &need);
+    if (st) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    const Mesh &m = mesh->m;
+    if (m.n_tris > 65535) return fail(STB_ERR_INVALID_ARG, "dense assembly supports E <= 65535");
+    AssemblyLayout L = assembly_layout(m, *params, ws, ws_bytes);
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = prepare_mixed(m, *params, L, status_word(ws), s))) return st;
+    STB_CUDA(cudaMemsetAsync(f, 0, sizeof(double) * (size_t)nrhs * params->n_steps * m.n_tris, s));
+    return run_vrhs_mixed(m, *params, (float *)V, g, nrhs, f, L, s);
+}
+

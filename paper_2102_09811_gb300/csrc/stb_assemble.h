@@ -70,6 +70,9 @@ stb_status run_d2_regular_mixed(const Mesh &m, const stb_params &p, float *D,
 // Mixed-precision D^2 of the touching pairs (coords as for K1 below).
 stb_status run_d2_singular_mixed(const Mesh &m, const stb_params &p, float *D,
                                  const AssemblyLayout &L, const float *coords, cudaStream_t s);
+// V (FP32) and f = (1/2 M_h + K_h) g without storing K (f zeroed by the caller).
+stb_status run_vrhs_mixed(const Mesh &m, const stb_params &p, float *V, const double *gd,
+                          int nrhs, double *f, const AssemblyLayout &L, cudaStream_t s);
 stb_status run_assembly_k1_mixed(const Mesh &m, const stb_params &p, float *K1,
                                  const AssemblyLayout &L, const float *coords, cudaStream_t s);
 stb_status run_assembly_mixed(const Mesh &m, const stb_params &p, void *V, void *K,

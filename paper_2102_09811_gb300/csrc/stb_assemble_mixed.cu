@@ -394,12 +394,14 @@ struct MixSS {
 
 // All blocks of the touching pair P (both orders) of one problem: one CTA of
 // MSS_THREADS threads shares the points of the regularised rule.
+// kp (optional): instead of K, the pair's K blocks go to kp[d] (entry (a,b))
+// and kp[n_steps + d] (entry (b,a)).
 template <int CH, class OutT>
 __device__ __forceinline__ void singular_pair_mixed(const double *__restrict__ geo,
                                                     const TouchPair P, int E, const MixSS &tab,
                                                     const float *__restrict__ nodes, int n_steps,
                                                     const MixConsts &g, OutT *__restrict__ V,
-                                                    OutT *__restrict__ K) {
+                                                    OutT *__restrict__ K, float *kp = nullptr) {
     __shared__ float red[MSS_THREADS / 32][3 * CH + 9];
     __shared__ float fin[3 * CH + 9];
     const int a = P.a, b = P.b, cls = P.cls;
@@ -488,14 +490,20 @@ __device__ __forceinline__ void singular_pair_mixed(const double *__restrict__ g
     if (threadIdx.x == 0) {
         store_m(V + iab, fin[0]);
         if (!ident) store_m(V + iba, fin[0]);
-        if (K) {
+        if (kp) {
+            kp[0] = ident ? 0.f : fin[2];
+            kp[n_steps] = ident ? 0.f : fin[4];
+        } else if (K) {
             store_m(K + iab, ident ? 0.f : fin[2]);
             if (!ident) store_m(K + iba, fin[4]);
         }
         if (n_steps > 1) {
             store_m(V + EE + iab, fin[1]);
             if (!ident) store_m(V + EE + iba, fin[1]);
-            if (K) {
+            if (kp) {
+                kp[1] = ident ? 0.f : fin[3];
+                kp[n_steps + 1] = ident ? 0.f : fin[5];
+            } else if (K) {
                 store_m(K + EE + iab, ident ? 0.f : fin[3]);
                 if (!ident) store_m(K + EE + iba, fin[5]);
             }
@@ -533,7 +541,10 @@ __device__ __forceinline__ void singular_pair_mixed(const double *__restrict__ g
                 const size_t off = (size_t)d * EE;
                 store_m(V + off + iab, bv);
                 if (!ident) store_m(V + off + iba, bv);
-                if (K) {
+                if (kp) {
+                    kp[d] = ident ? 0.f : ba;
+                    kp[n_steps + d] = ident ? 0.f : bb;
+                } else if (K) {
                     store_m(K + off + iab, ident ? 0.f : ba);
                     if (!ident) store_m(K + off + iba, bb);
                 }
@@ -1482,6 +1493,233 @@ stb_status run_d2_regular_mixed(const Mesh &m, const stb_params &p, float *D,
                                                          L.mnodes, nf, p.n_steps, g,
                                                          (float)p.alpha, D);
     return check_launch("k_regular_d2_mixed");
+}
+
+// ------------------------------------ matrix-free K g (no K storage) ---
+// V is stored as by k_regular_mixed; the blocks of K are contracted with the
+// Dirichlet data as they are formed, f^k[l] += sum_{d <= k} K^d[l][j]
+// g^{k-d}[j], so K is never written (half the memory of the assembly).
+// The CTA's row l and 128 columns j: g of those columns sits in shared
+// memory (n_steps x nrhs <= VRHS_MAX columns of 128 floats); per completed
+// block range and tile of VRHS_KT steps k every thread forms its partial
+// products, a warp sums them with shuffles and lane 0 adds them to the row's
+// shared sums, which go to f (FP64 atomics) at the end.  Every thread of a
+// CTA runs the same loop (touching pairs and the ragged tail contribute
+// zero), so the shuffles see full warps.
+constexpr int VRHS_MAX = 128;  // n_steps * nrhs
+constexpr int VRHS_KT = 8;
+
+// f partial: for the blocks dlo..dlo+cnt-1 (values Kv[u], scaled), all k.
+template <int CNT>
+__device__ __forceinline__ void vrhs_contract(const float (&Kv)[CNT], int dlo, int cnt,
+                                              int n_steps, int nrhs, const float *gs,
+                                              float *sf, bool active) {
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < nrhs; ++r) {
+        const float *g = gs + (size_t)r * n_steps * MREG_THREADS;  // [i][tid]
+        for (int k0 = dlo; k0 < n_steps; k0 += VRHS_KT) {
+            float v[VRHS_KT];
+#pragma unroll
+            for (int t = 0; t < VRHS_KT; ++t) v[t] = 0.f;
+            if (active) {
+#pragma unroll
+                for (int u = 0; u < CNT; ++u) {
+                    if (u >= cnt) break;
+                    const int d = dlo + u;
+#pragma unroll
+                    for (int t = 0; t < VRHS_KT; ++t) {
+                        const int k = k0 + t;
+                        if (k >= d && k < n_steps)
+                            v[t] = fmaf(Kv[u], g[(size_t)(k - d) * MREG_THREADS + threadIdx.x], v[t]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < VRHS_KT; ++t) {
+                float x = v[t];
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0 && k0 + t < n_steps) atomicAdd(sf + r * n_steps + k0 + t, x);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(MREG_THREADS)
+k_regular_vrhs_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E,
+                     const float *__restrict__ rule, int nq, const float *__restrict__ nodes,
+                     int n_nodes_f, int n_steps, MixConsts g, float *__restrict__ V,
+                     const double *__restrict__ gd, int nrhs, double *__restrict__ f) {
+    extern __shared__ float smf[];
+    float4 *xa = reinterpret_cast<float4 *>(smf);
+    float *nd = smf + 4 * MAX_RULE_M;
+    float *gs = nd + n_nodes_f;                           // [nrhs][n_steps][128]
+    float *sf = gs + (size_t)nrhs * n_steps * MREG_THREADS; // [nrhs][n_steps]
+    const int l = blockIdx.y;
+    const int j = blockIdx.x * MREG_THREADS + threadIdx.x;
+    load_test_points(geo + (size_t)l * GEO_STRIDE, rule, nq, xa);
+    for (int i = threadIdx.x; i < n_nodes_f; i += MREG_THREADS) nd[i] = nodes[i];
+    for (int i = threadIdx.x; i < nrhs * n_steps; i += MREG_THREADS) sf[i] = 0.f;
+    for (int ri = 0; ri < nrhs * n_steps; ++ri)  // row (r, i) of g for the CTA's columns
+        gs[(size_t)ri * MREG_THREADS + threadIdx.x] =
+            j < E ? (float)gd[(size_t)ri * E + j] : 0.f;
+    __syncthreads();
+
+    const int jj = j < E ? j : E - 1;
+    const int32_t tl[3] = {tris[3 * l], tris[3 * l + 1], tris[3 * l + 2]};
+    const int32_t tj[3] = {tris[3 * jj], tris[3 * jj + 1], tris[3 * jj + 2]};
+    bool touch = false;
+    for (int i = 0; i < 3; ++i) touch |= (tl[i] == tj[0]) | (tl[i] == tj[1]) | (tl[i] == tj[2]);
+    const bool active = j < E && !touch;
+    // a touching or ragged thread evaluates a separated stand-in pair (its
+    // values are discarded) so that every thread runs the same loop
+    const int jc = active ? jj : (l + E / 2) % E;
+    const double *gl = geo + (size_t)l * GEO_STRIDE, *gj = geo + (size_t)jc * GEO_STRIDE;
+    float D[3], B1[3], B2[3], n[3];
+    for (int c = 0; c < 3; ++c) {
+        D[c] = (float)(gl[GEO_V0 + c] - gj[GEO_V0 + c]);
+        B1[c] = (float)(gj[GEO_V1 + c] - gj[GEO_V0 + c]);
+        B2[c] = (float)(gj[GEO_V2 + c] - gj[GEO_V1 + c]);
+        n[c] = (float)gj[GEO_N + c];
+    }
+    const float scale = (float)(4.0 * gl[GEO_AREA] * gj[GEO_AREA]);
+    const size_t EE = (size_t)E * E, ij = (size_t)l * E + jj;
+
+    float v0 = 0.f, v1 = 0.f, k0 = 0.f, k1 = 0.f, v2 = 0.f, k2 = 0.f;
+    for (int b = 0; b < nq; ++b) {
+        const float t1 = rule[4 * b], t2 = rule[4 * b + 1], wb = rule[4 * b + 2];
+        const float r0b = D[0] - (t1 * B1[0] + t2 * B2[0]);
+        const float r1b = D[1] - (t1 * B1[1] + t2 * B2[1]);
+        const float r2b = D[2] - (t1 * B1[2] + t2 * B2[2]);
+        for (int a = 0; a < nq; ++a) {
+            const float4 xq = xa[a];
+            const float r0 = r0b + xq.x, r1 = r1b + xq.y, r2 = r2b + xq.z;
+            const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+            const float irho = rsqrtf(rr), rho = rr * irho;
+            const float rn = r0 * n[0] + r1 * n[1] + r2 * n[2];
+            const float w = xq.w * wb, wrn = w * rn;
+            float a0, a1, c0, c1;
+            k_d01(rho, irho, g, a0, a1, c0, c1);
+            v0 = fmaf(w, a0, v0);
+            v1 = fmaf(w, a1, v1);
+            k0 = fmaf(wrn, c0, k0);
+            k1 = fmaf(wrn, c1, k1);
+            if (n_steps > 2) {
+#pragma unroll
+                for (int q = 0; q < MIX_NG1; ++q) {
+                    const float4 c = reinterpret_cast<const float4 *>(nd)[q];
+                    const float e = ex2(rr * c.x);
+                    v2 = fmaf(w * c.y, e, v2);
+                    k2 = fmaf(wrn * c.z, e, k2);
+                }
+            }
+        }
+    }
+    if (active) {
+        V[ij] = scale * v0;
+        if (n_steps > 1) V[EE + ij] = scale * v1;
+    }
+    {
+        const float Kv[2] = {scale * k0, scale * k1};
+        vrhs_contract<2>(Kv, 0, min(2, n_steps), n_steps, nrhs, gs, sf, active);
+    }
+    const float *tab = nd + MIX_K1;
+    float2 carry = make_float2(v2, k2);
+    for (int d0 = 2; d0 < n_steps; d0 += MIX_CH) {
+        float2 acc[MIX_CH + 1];
+        acc[0] = carry;
+#pragma unroll
+        for (int u = 1; u <= MIX_CH; ++u) acc[u] = make_float2(0.f, 0.f);
+        const int ng = mixed_chunk_ng(d0);
+        const int n_pass = (min(MIX_CH, n_steps - d0) + MIX_G - 1) / MIX_G;
+        if (ng == 4)
+            chunk_sum<4>(tab, n_pass, rule, nq, xa, D, B1, B2, n, acc);
+        else if (ng == 3)
+            chunk_sum<3>(tab, n_pass, rule, nq, xa, D, B1, B2, n, acc);
+        else
+            chunk_sum<2>(tab, n_pass, rule, nq, xa, D, B1, B2, n, acc);
+        const int cnt = min(MIX_CH, n_steps - d0);
+        float Kv[MIX_CH];
+#pragma unroll
+        for (int u = 0; u < MIX_CH; ++u) {
+            Kv[u] = scale * acc[u].y;
+            if (active && u < cnt) V[(size_t)(d0 + u) * EE + ij] = scale * acc[u].x;
+        }
+        vrhs_contract<MIX_CH>(Kv, d0, cnt, n_steps, nrhs, gs, sf, active);
+        carry = acc[MIX_CH];
+        tab += MIX_CH * mixed_iv_floats(ng);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nrhs * n_steps; i += MREG_THREADS)
+        atomicAdd(f + (size_t)i * E + l, (double)sf[i]);
+}
+
+// Touching pairs: V of both orders stored, the K blocks of both orders kept
+// in shared memory (written by thread 0 of the p0 pair routine) and
+// contracted with g by all threads at the end.
+template <int CH>
+__global__ void __launch_bounds__(MSS_THREADS)
+k_singular_vrhs_mixed(const double *__restrict__ geo, const TouchPair *__restrict__ pairs, int E,
+                      MixSS tab, const float *__restrict__ nodes, int n_steps, MixConsts g,
+                      float *__restrict__ V, const double *__restrict__ gd, int nrhs,
+                      double *__restrict__ f) {
+    const TouchPair P = pairs[blockIdx.x];
+    const int a = P.a, b = P.b;
+    if (a < 0 || b < a || b >= E) return;
+    __shared__ float kp[2 * VRHS_MAX];
+    singular_pair_mixed<CH, float>(geo, P, E, tab, nodes, n_steps, g, V, nullptr, kp);
+    __syncthreads();
+    if (P.cls == PAIR_IDENTICAL) return;  // K = 0
+    const float *kab = kp, *kba = kp + n_steps;
+    for (int rk = threadIdx.x; rk < nrhs * n_steps; rk += MSS_THREADS) {
+        const int r = rk / n_steps, k = rk % n_steps;
+        const double *gr = gd + (size_t)r * n_steps * E;
+        double sa = 0.0, sb = 0.0;
+        for (int d = 0; d <= k; ++d) {
+            sa = fma((double)kab[d], gr[(size_t)(k - d) * E + b], sa);
+            sb = fma((double)kba[d], gr[(size_t)(k - d) * E + a], sb);
+        }
+        atomicAdd(f + ((size_t)r * n_steps + k) * E + a, sa);
+        atomicAdd(f + ((size_t)r * n_steps + k) * E + b, sb);
+    }
+}
+
+// f += (h/2) Delta_l g (the mass part of the right-hand side)
+__global__ void k_vrhs_mass(const double *__restrict__ geo, int E, size_t total, double h,
+                            const double *__restrict__ gd, double *__restrict__ f) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    f[idx] = fma(0.5 * h * geo[(size_t)(idx % E) * GEO_STRIDE + GEO_AREA], gd[idx], f[idx]);
+}
+
+stb_status run_vrhs_mixed(const Mesh &m, const stb_params &p, float *V, const double *gd,
+                          int nrhs, double *f, const AssemblyLayout &L, cudaStream_t s) {
+    const int E = (int)m.n_tris;
+    const int nq = p.quad_regular * p.quad_regular;
+    const MixConsts g = mix_consts(p);
+    const int nf = (int)mixed_node_floats(p.n_steps);
+    const size_t smem = sizeof(float) * (4 * MAX_RULE_M + (size_t)nf +
+                                         (size_t)nrhs * p.n_steps * (MREG_THREADS + 1));
+    STB_CUDA(cudaFuncSetAttribute(k_regular_vrhs_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    dim3 grid((E + MREG_THREADS - 1) / MREG_THREADS, E);
+    count_launch(s);
+    k_regular_vrhs_mixed<<<grid, MREG_THREADS, smem, s>>>(L.geo, m.d_tris, E, L.mrule, nq,
+                                                           L.mnodes, nf, p.n_steps, g, V, gd, nrhs,
+                                                           f);
+    stb_status st = check_launch("k_regular_vrhs_mixed");
+    if (st) return st;
+    if (m.n_touch > 0) {
+        const MixSS tab = mix_ss(L);
+        count_launch(s);
+        k_singular_vrhs_mixed<MIX_CH><<<(unsigned)m.n_touch, MSS_THREADS, 0, s>>>(
+            L.geo, L.pairs, E, tab, L.mnodes, p.n_steps, g, V, gd, nrhs, f);
+        if ((st = check_launch("k_singular_vrhs_mixed"))) return st;
+    }
+    const size_t total = (size_t)nrhs * p.n_steps * E;
+    count_launch(s);
+    k_vrhs_mass<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(L.geo, E, total,
+                                                                p.T / p.n_steps, gd, f);
+    return check_launch("k_vrhs_mass");
 }
 
 // -------------------------------------------------------------- batches ---
