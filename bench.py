@@ -252,6 +252,42 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+PEAK_SOURCE = {"fp64": "nominal: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz",
+               "mufu": "nominal: 152 SM x 32 ex2/clk x 2.07 GHz",
+               "fp32": "nominal: 152 SM x 128 lanes x 2.07 GHz"}
+
+
+def measure_pipe_peaks(capi, torch):
+    """Replace the nominal FP64 / FP32 / MUFU peaks by the library's probes
+    on this device (stb_measure_peaks), and time a cuBLAS TF32 GEMM for
+    context; returns the record for the JSON line."""
+    global FP64_PEAK_TFLOPS, FP32_OP_PEAK, MUFU_PEAK_TEX2
+    f64, f32, ex2 = capi.stb_measure_peaks()
+    FP64_PEAK_TFLOPS = 2.0 * f64 / 1e12
+    FP32_OP_PEAK = f32
+    MUFU_PEAK_TEX2 = ex2 / 1e12
+    for k in PEAK_SOURCE:
+        PEAK_SOURCE[k] = "measured (stb_measure_peaks: eight independent chains per thread)"
+    rec = {"fp64_tflops": FP64_PEAK_TFLOPS, "fp32_fma_per_s": f32, "mufu_tex2_per_s": ex2 / 1e12}
+    try:  # TF32 tensor-core reference: cuBLAS SGEMM with TF32 allowed
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        a = torch.randn(8192, 8192, device="cuda")
+        c = a @ a
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            c = a @ a
+        e1.record()
+        torch.cuda.synchronize()
+        rec["cublas_tf32_tflops"] = 5 * 2 * 8192.0 ** 3 / (e0.elapsed_time(e1) / 1e3) / 1e12
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        del a, c
+    except RuntimeError:
+        rec["cublas_tf32_tflops"] = None
+    return rec
+
+
 def _roofline(name, trace_entry, ms_step, n_reg_pairs, q, n_steps):
     """Roofline of the step's dominant kernel from the live trace (q: points
     per direction of the conical rule, so (q*q)^2 points per pair)."""
@@ -262,8 +298,7 @@ def _roofline(name, trace_entry, ms_step, n_reg_pairs, q, n_steps):
     if name == "k_regular_f64":
         evals = float(n_reg_pairs) * pts * n_steps  # levels 1..E_t
         roof.update({"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
-                     "peak_source": "FP64 FMA pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz "
-                                    "(measured 1.255 TFLOP/s, nominal 1.25)",
+                     "peak_source": "FP64 FMA pipe, " + PEAK_SOURCE["fp64"],
                      "units_per_launch": evals, "unit_name": "separated-pair point-level evaluations"})
         if FP64_FLOPS_PER_EVAL:
             ach = FP64_FLOPS_PER_EVAL * evals / (launch_ms / 1e3) / 1e12
@@ -271,7 +306,7 @@ def _roofline(name, trace_entry, ms_step, n_reg_pairs, q, n_steps):
     elif name == "k_regular_mixed":
         ex2 = float(n_reg_pairs) * pts * mixed_nodes_per_point(n_steps)
         roof.update({"bound": "alu", "unit": "Tex2/s", "peak": MUFU_PEAK_TEX2,
-                     "peak_source": "MUFU pipe: 152 SM x 32 ex2/clk x 2.07 GHz (measured 9.995 Tex2/s)",
+                     "peak_source": "MUFU ex2 pipe, " + PEAK_SOURCE["mufu"],
                      "units_per_launch": ex2, "unit_name": "MUFU.EX2 time-node evaluations"})
         ach = ex2 / (launch_ms / 1e3) / 1e12
         # DRAM bytes of one launch: ncu capture of this kernel on the 16-step
@@ -355,6 +390,7 @@ def run_gpu(args):
     mixed = args.precision == "mixed"
     prec = capi.STB_PREC_MIXED if mixed else capi.STB_PREC_FP64
     storage = capi.STB_STORE_F32 if mixed else capi.STB_STORE_F64
+    pipe_peaks = measure_pipe_peaks(capi, torch)
     mesh = capi.Mesh(nodes, tris)
     probs = [pipeline.DirichletProblem(nodes, tris, a, wl["T"], n, src, mesh=mesh, precision=prec,
                                        storage=storage) for a in alphas]
@@ -604,7 +640,8 @@ def run_gpu(args):
             "potentials": pots,
             "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
             "rel_l2_error_w": rel_err, "solve": solve_info, "gpu_launches": launches,
-            "kernels_ms": {k: v[1] for k, v in trace.items()}, "roofline": roof, "e2e": e2e}
+            "kernels_ms": {k: v[1] for k, v in trace.items()}, "roofline": roof,
+            "measured_pipe_peaks": pipe_peaks, "e2e": e2e}
     if rank == 0:
         line["clocks"] = clk.summary()
         if world == 1 and not args.no_cpu_baseline:

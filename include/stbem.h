@@ -438,6 +438,15 @@ stb_status stb_neumann_error(const stb_mesh *mesh, const stb_params *params,
  * synchronises `stream`. */
 stb_status stb_workspace_status(const void *workspace, stb_stream stream);
 
+/* ---- pipe throughput probes (no counterpart in the paper) ---------------------
+ * Measures, on the current device, the FP64 FMA, FP32 FMA and MUFU exp2 rates
+ * (operations per second; one FMA counts as one operation) with eight
+ * independent chains per thread on 4 CTAs of 256 threads per SM, about 10 ms
+ * of work each; allocates and frees a small scratch buffer and synchronises
+ * `stream`.  These are the denominators of the arithmetic rooflines. */
+stb_status stb_measure_peaks(double *fp64_fma_per_s, double *fp32_fma_per_s, double *ex2_per_s,
+                             stb_stream stream);
+
 /* ---- kernel tracing (no counterpart in the paper; timing of the kernels) ------
  * While enabled, every kernel the library launches is bracketed by two CUDA
  * events recorded on its launch stream.  stb_trace_read synchronises those

@@ -103,6 +103,7 @@ _SIGS = {
     "stb_error_workspace_size": (_I32, [_P, _PAR, _I32, _I32, _I32, _I32, _PSZ]),
     "stb_neumann_error": (_I32, [_P, _PAR, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _SZ, _P]),
     "stb_workspace_status": (_I32, [_P, _P]),
+    "stb_measure_peaks": (_I32, [ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "stb_trace_enable": (_I32, [_I32]),
     "stb_trace_reset": (_I32, []),
     "stb_trace_read": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
@@ -493,6 +494,14 @@ def stb_neumann_error(mesh, params, sources, w, out, workspace, q_space=8, n_tim
 
 def stb_workspace_status(workspace, stream=None):
     _check(_library().stb_workspace_status(_ptr(workspace), _stream(stream)), "stb_workspace_status")
+
+
+def stb_measure_peaks(stream=None):
+    """(FP64 FMA/s, FP32 FMA/s, MUFU exp2/s) measured on the current device."""
+    a, b, c = _D(), _D(), _D()
+    _check(_library().stb_measure_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                        _stream(stream)), "stb_measure_peaks")
+    return a.value, b.value, c.value
 
 
 def stb_trace_enable(on=True):
