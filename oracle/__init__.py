@@ -85,6 +85,15 @@ def lib():
         L.orc_neumann_rhs.argtypes = [_P, _P, _P, _I64, _I64, _D, _I32, _I32, _P, _P]
         L.orc_dirichlet_error_p1.argtypes = [_P, _I64, _P, _I64, _D, _D, _I32, _P, _I32, _I32,
                                              _P, _I32, _I32, _P, _P]
+        L.orc_assemble_rows_nu.argtypes = [_P, _I64, _P, _I64, _D, _P, _I32, _I32, _I32, _P,
+                                           _I64, _P, _P]
+        L.orc_matvec_nu.argtypes = [_P, _I64, _I32, _I32, _P, _P]
+        L.orc_solve_nu.argtypes = [_P, _I64, _I32, _I32, _P, _P]
+        L.orc_project_dirichlet_nu.argtypes = [_P, _I64, _P, _I64, _D, _P, _I32, _P, _I32, _I32,
+                                               _I32, _I32, _P]
+        L.orc_dirichlet_rhs_nu.argtypes = [_P, _P, _I64, _P, _I32, _I32, _P, _P]
+        L.orc_neumann_error_nu.argtypes = [_P, _I64, _P, _I64, _D, _P, _I32, _P, _I32, _I32, _P,
+                                           _I32, _I32, _P, _P]
         L.orc_potentials.argtypes = [_P, _I64, _P, _I64, _D, _D, _I32, _P, _P, _I32, _P, _I64,
                                      _I32, _P, _P]
         L.orc_dirichlet_rhs_p1.argtypes = [_P, _P, _P, _I64, _I64, _D, _I32, _I32, _P, _P]
@@ -426,5 +435,83 @@ def dirichlet_error_p1(nodes, tris, alpha, T, n_steps, sources, u1, q_space=8, n
                                         T, n_steps, _p(src), src.shape[1], src.shape[0], _p(u1),
                                         q_space, n_time, ctypes.byref(e2), ctypes.byref(r2)),
            "dirichlet_error_p1")
+    return e2.value, r2.value
+
+
+# ---- non-uniform time grids (Sec. 7) -------------------------------------------
+def n_blocks(n_steps):
+    return n_steps * (n_steps + 1) // 2
+
+
+def block_index(k, i):
+    """Packed index of the block A^{k,i}, k >= i."""
+    return k * (k + 1) // 2 + i
+
+
+def assemble_rows_nu(nodes, tris, alpha, times, rows, q_reg=3, m_ss=4):
+    """Rows of the blocks V^{k,i}, K^{k,i}: [n_rows, n_blocks, E] each."""
+    nodes, tris, times = _f64(nodes), _i32(tris), _f64(times)
+    n = times.shape[0] - 1
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    E = tris.shape[0]
+    V = np.zeros((rows.shape[0], n_blocks(n), E))
+    K = np.zeros_like(V)
+    _check(lib().orc_assemble_rows_nu(_p(nodes), nodes.shape[0], _p(tris), E, alpha, _p(times), n,
+                                      q_reg, m_ss, _p(rows), rows.shape[0], _p(V), _p(K)),
+           "assemble_rows_nu")
+    return V, K
+
+
+def assemble_nu(nodes, tris, alpha, times, q_reg=3, m_ss=4):
+    """All blocks [n_blocks, E, E] of V and K on the grid `times`."""
+    E = np.asarray(tris).shape[0]
+    V, K = assemble_rows_nu(nodes, tris, alpha, times, np.arange(E), q_reg, m_ss)
+    return (np.ascontiguousarray(V.transpose(1, 0, 2)), np.ascontiguousarray(K.transpose(1, 0, 2)))
+
+
+def matvec_nu(A, x):
+    A, x = _f64(A), _f64(x)
+    E, n = A.shape[1], x.shape[1]
+    y = np.zeros_like(x)
+    _check(lib().orc_matvec_nu(_p(A), E, n, x.shape[0], _p(x), _p(y)), "matvec_nu")
+    return y
+
+
+def solve_nu(V, f):
+    V, f = _f64(V), _f64(f)
+    w = np.zeros_like(f)
+    rc = lib().orc_solve_nu(_p(V), V.shape[1], f.shape[1], f.shape[0], _p(f), _p(w))
+    if rc == -5:
+        raise np.linalg.LinAlgError("a diagonal block is not positive definite")
+    _check(rc, "solve_nu")
+    return w
+
+
+def project_dirichlet_nu(nodes, tris, alpha, times, sources, q_space=8, n_time=16):
+    nodes, tris, times, src = _f64(nodes), _i32(tris), _f64(times), _f64(sources)
+    n = times.shape[0] - 1
+    g = np.zeros((src.shape[0], n, tris.shape[0]))
+    _check(lib().orc_project_dirichlet_nu(_p(nodes), nodes.shape[0], _p(tris), tris.shape[0],
+                                          alpha, _p(times), n, _p(src), src.shape[1],
+                                          src.shape[0], q_space, n_time, _p(g)),
+           "project_dirichlet_nu")
+    return g
+
+
+def dirichlet_rhs_nu(area, K, times, g):
+    area, K, times, g = _f64(area), _f64(K), _f64(times), _f64(g)
+    f = np.zeros_like(g)
+    _check(lib().orc_dirichlet_rhs_nu(_p(area), _p(K), K.shape[1], _p(times), g.shape[1],
+                                      g.shape[0], _p(g), _p(f)), "dirichlet_rhs_nu")
+    return f
+
+
+def neumann_error_nu(nodes, tris, alpha, times, sources, w, q_space=8, n_time=16):
+    nodes, tris, times, src, w = _f64(nodes), _i32(tris), _f64(times), _f64(sources), _f64(w)
+    e2, r2 = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().orc_neumann_error_nu(_p(nodes), nodes.shape[0], _p(tris), tris.shape[0], alpha,
+                                      _p(times), times.shape[0] - 1, _p(src), src.shape[1],
+                                      src.shape[0], _p(w), q_space, n_time, ctypes.byref(e2),
+                                      ctypes.byref(r2)), "neumann_error_nu")
     return e2.value, r2.value
 

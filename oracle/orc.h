@@ -150,6 +150,28 @@ int orc_dirichlet_error_p1(const double *nodes, int64_t n_nodes, const int32_t *
                            int32_t n_src, int32_t nrhs, const double *u1, int32_t q_space,
                            int32_t n_time, double *err2, double *ref2);
 
+/* ---- non-uniform time grids (Sec. 7) ----------------------------------------
+ * times [n_steps + 1] strictly increasing from 0; blocks A^{k,i}, k >= i,
+ * packed at b(k,i) = k(k+1)/2 + i: V, K rows [n_rows][n_blocks][E]; matrices
+ * [n_blocks][E][E] for the product and the solve.                          */
+int orc_assemble_rows_nu(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                         double alpha, const double *times, int32_t n_steps, int32_t q_reg,
+                         int32_t m_ss, const int64_t *rows, int64_t n_rows, double *V, double *K);
+int orc_matvec_nu(const double *A, int64_t E, int32_t n_steps, int32_t nrhs, const double *x,
+                  double *y);
+int orc_solve_nu(const double *V, int64_t E, int32_t n_steps, int32_t nrhs, const double *f,
+                 double *w);
+int orc_project_dirichlet_nu(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                             double alpha, const double *times, int32_t n_steps,
+                             const double *sources, int32_t n_src, int32_t nrhs, int32_t q_space,
+                             int32_t n_time, double *g);
+int orc_dirichlet_rhs_nu(const double *area, const double *K, int64_t E, const double *times,
+                         int32_t n_steps, int32_t nrhs, const double *g, double *f);
+int orc_neumann_error_nu(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                         double alpha, const double *times, int32_t n_steps,
+                         const double *sources, int32_t n_src, int32_t nrhs, const double *w,
+                         int32_t q_space, int32_t n_time, double *err2, double *ref2);
+
 /* ---- potentials: the discretised representation formula (Sec. 3.5) --------
  * At points (x, t) off Gamma_h, points [n_pts][4] = (x1, x2, x3, t),
  * 0 <= t <= T: slp [nrhs][n_pts] = V~ w_h (w [nrhs][n_steps][E], piecewise

@@ -659,3 +659,104 @@ done:
     return rc;
 }
 
+/* ---- non-uniform time grids (Sec. 7: the antiderivatives carry over) -------
+ * Time grid t_0 = 0 < t_1 < ... < t_n; blocks A^{k,i} (k >= i) of the block
+ * lower-triangular matrices, packed at b(k,i) = k(k+1)/2 + i.  With
+ * Phi = G^{dtau dt} (and its scaled normal derivative for K), whose second
+ * derivative in delta is -G, the double time integral over
+ * [t_k, t_{k+1}] x [t_i, t_{i+1}] is
+ *   A^{k,i} = S(t_{k+1} - t_{i+1}) - S(t_k - t_{i+1}) - S(t_{k+1} - t_i) + S(t_k - t_i)
+ * for k > i (S the pair's spatial sum of Phi; S(0) the delta -> 0 limit), and
+ *   A^{k,k} = h_k S_*(0) - S(h_k) + S(0),   h_k = t_{k+1} - t_k
+ * on the diagonal (eq. V0 / eq. K0 with the step h_k).                       */
+static void level_sums_delta(const pair_points *pp, double delta, double alpha, double *sv,
+                             double *sk)
+{
+    double v = 0.0, k = 0.0;
+    for (int q = 0; q < pp->n; ++q) {
+        v += pp->w[q] * orc_G_dtau_dt(pp->rho[q], delta, alpha);
+        k += pp->w[q] * orc_dn_G_dtau_dt(pp->rn[q], pp->rho[q], delta, alpha);
+    }
+    *sv = v;
+    *sk = pp->cls == ORC_IDENTICAL ? 0.0 : k;
+}
+
+int orc_assemble_rows_nu(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                         double alpha, const double *times, int32_t n_steps, int32_t q_reg,
+                         int32_t m_ss, const int64_t *rows, int64_t n_rows, double *V, double *K)
+{
+    if (E < 1 || n_steps < 1 || !(alpha > 0.0) || n_rows < 0 || !times || times[0] != 0.0)
+        return -1;
+    for (int k = 0; k < n_steps; ++k)
+        if (!(times[k + 1] > times[k]))
+            return -1;
+    for (int64_t r = 0; r < n_rows; ++r)
+        if (rows[r] < 0 || rows[r] >= E)
+            return -1;
+    rules R;
+    double *area = NULL, *normal = NULL;
+    int rc = -1;
+    if (rules_init(&R, q_reg, m_ss))
+        goto done;
+    if (geometry_alloc(nodes, n_nodes, tris, E, &area, &normal))
+        goto done;
+    const int64_t nblk = (int64_t)n_steps * (n_steps + 1) / 2;
+    int nmax = R.nreg * R.nreg;
+    for (int c = 1; c <= 3; ++c)
+        if (R.nss[c] > nmax)
+            nmax = R.nss[c];
+    pair_points pp;
+    memset(&pp, 0, sizeof pp);
+    pp.rho = malloc(sizeof(double) * nmax);
+    pp.rn = malloc(sizeof(double) * nmax);
+    pp.w = malloc(sizeof(double) * nmax);
+    for (int64_t r = 0; r < n_rows; ++r) {
+        int64_t l = rows[r];
+        double *Vr = V + r * nblk * E, *Kr = K + r * nblk * E;
+        for (int64_t j = 0; j < E; ++j) {
+            pair_points_build(&R, nodes, tris, area, normal, l, j, &pp);
+            double s0v, s0k, ssv, ssk;
+            level_sums_delta(&pp, 0.0, alpha, &s0v, &s0k);
+            /* the delta = 0 singular integrand G^{dtau}(., 0) */
+            ssv = 0.0;
+            ssk = 0.0;
+            for (int q = 0; q < pp.n; ++q) {
+                ssv += pp.w[q] * orc_G_dtau(pp.rho[q], 0.0, alpha);
+                ssk += pp.w[q] * orc_dn_G_dtau(pp.rn[q], pp.rho[q], 0.0, alpha);
+            }
+            if (pp.cls == ORC_IDENTICAL)
+                ssk = 0.0;
+            for (int k = 0; k < n_steps; ++k)
+                for (int i = 0; i <= k; ++i) {
+                    double v, kk;
+                    if (i == k) {
+                        double h = times[k + 1] - times[k], sv, sk;
+                        level_sums_delta(&pp, h, alpha, &sv, &sk);
+                        v = h * ssv - sv + s0v;
+                        kk = h * ssk - sk + s0k;
+                    } else {
+                        double a1, b1, a2, b2, a3, b3, a4, b4;
+                        level_sums_delta(&pp, times[k + 1] - times[i + 1], alpha, &a1, &b1);
+                        level_sums_delta(&pp, times[k] - times[i + 1], alpha, &a2, &b2);
+                        level_sums_delta(&pp, times[k + 1] - times[i], alpha, &a3, &b3);
+                        level_sums_delta(&pp, times[k] - times[i], alpha, &a4, &b4);
+                        v = a1 - a2 - a3 + a4;
+                        kk = b1 - b2 - b3 + b4;
+                    }
+                    int64_t b = (int64_t)k * (k + 1) / 2 + i;
+                    Vr[b * E + j] = v;
+                    Kr[b * E + j] = kk;
+                }
+        }
+    }
+    free(pp.rho);
+    free(pp.rn);
+    free(pp.w);
+    rc = 0;
+done:
+    rules_free(&R);
+    free(area);
+    free(normal);
+    return rc;
+}
+

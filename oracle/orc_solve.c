@@ -536,3 +536,171 @@ done:
     free(normal);
     return rc;
 }
+
+/* ---- non-uniform time grids ----------------------------------------------
+ * Blocks packed at b(k,i) = k(k+1)/2 + i (k >= i), times [n_steps + 1],
+ * vectors [nrhs][n_steps][E].                                               */
+
+/* y^k = sum_{i <= k} A^{k,i} x^i */
+int orc_matvec_nu(const double *A, int64_t E, int32_t n_steps, int32_t nrhs, const double *x,
+                  double *y)
+{
+    if (E < 1 || n_steps < 1 || nrhs < 1)
+        return -1;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k)
+            for (int64_t l = 0; l < E; ++l) {
+                double acc = 0.0;
+                for (int i = 0; i <= k; ++i) {
+                    const double *row = A + (((int64_t)k * (k + 1) / 2 + i) * E + l) * E;
+                    const double *xv = x + ((int64_t)r * n_steps + i) * E;
+                    for (int64_t j = 0; j < E; ++j)
+                        acc += row[j] * xv[j];
+                }
+                y[((int64_t)r * n_steps + k) * E + l] = acc;
+            }
+    return 0;
+}
+
+/* Block forward substitution: w^k = (V^{k,k})^{-1} (f^k - sum_{i<k} V^{k,i} w^i),
+ * each diagonal block by its own dense Cholesky factorisation. */
+int orc_solve_nu(const double *V, int64_t E, int32_t n_steps, int32_t nrhs, const double *f,
+                 double *w)
+{
+    if (E < 1 || n_steps < 1 || nrhs < 1)
+        return -1;
+    double *L = malloc(sizeof(double) * E * E);
+    double *rhs = malloc(sizeof(double) * E);
+    int rc = 0;
+    for (int k = 0; k < n_steps && rc == 0; ++k) {
+        memcpy(L, V + ((int64_t)k * (k + 1) / 2 + k) * E * E, sizeof(double) * E * E);
+        if ((rc = cholesky(L, E)) != 0)
+            break;
+        for (int r = 0; r < nrhs; ++r) {
+            const double *fk = f + ((int64_t)r * n_steps + k) * E;
+            for (int64_t l = 0; l < E; ++l) {
+                double acc = fk[l];
+                for (int i = 0; i < k; ++i) {
+                    const double *row = V + (((int64_t)k * (k + 1) / 2 + i) * E + l) * E;
+                    const double *wv = w + ((int64_t)r * n_steps + i) * E;
+                    for (int64_t j = 0; j < E; ++j)
+                        acc -= row[j] * wv[j];
+                }
+                rhs[l] = acc;
+            }
+            cholesky_solve(L, E, rhs);
+            memcpy(w + ((int64_t)r * n_steps + k) * E, rhs, sizeof(double) * E);
+        }
+    }
+    free(L);
+    free(rhs);
+    return rc;
+}
+
+/* Element means of the Dirichlet datum over [t_k, t_{k+1}] x gamma_j. */
+int orc_project_dirichlet_nu(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                             double alpha, const double *times, int32_t n_steps,
+                             const double *sources, int32_t n_src, int32_t nrhs, int32_t q_space,
+                             int32_t n_time, double *g)
+{
+    if (E < 1 || n_steps < 1 || nrhs < 1 || n_src < 1 || q_space < 1 || q_space > 32 ||
+        n_time < 1 || n_time > 64)
+        return -1;
+    int nq = q_space * q_space;
+    double *s1 = malloc(sizeof(double) * nq), *s2 = malloc(sizeof(double) * nq);
+    double *sw = malloc(sizeof(double) * nq), tx[64], tw[64];
+    int rc = -1;
+    if (orc_triangle_rule(q_space, s1, s2, sw) || orc_gauss_legendre01(n_time, tx, tw))
+        goto done;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k) {
+            const double t0 = times[k], hk = times[k + 1] - times[k];
+            for (int64_t j = 0; j < E; ++j) {
+                const int32_t *t3 = tris + 3 * j;
+                double acc = 0.0;
+                for (int a = 0; a < nq; ++a) {
+                    double x[3];
+                    chi_plain(nodes + 3 * t3[0], nodes + 3 * t3[1], nodes + 3 * t3[2], s1[a],
+                              s2[a], x);
+                    for (int b = 0; b < n_time; ++b)
+                        acc += sw[a] * tw[b] *
+                               dirichlet_datum(sources + (int64_t)r * n_src * 5, n_src, alpha, x,
+                                               t0 + tx[b] * hk);
+                }
+                g[((int64_t)r * n_steps + k) * E + j] = 2.0 * acc;
+            }
+        }
+    rc = 0;
+done:
+    free(s1);
+    free(s2);
+    free(sw);
+    return rc;
+}
+
+/* f^k = (h_k / 2) Delta g^k + sum_{i <= k} K^{k,i} g^i */
+int orc_dirichlet_rhs_nu(const double *area, const double *K, int64_t E, const double *times,
+                         int32_t n_steps, int32_t nrhs, const double *g, double *f)
+{
+    if (orc_matvec_nu(K, E, n_steps, nrhs, g, f))
+        return -1;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k)
+            for (int64_t l = 0; l < E; ++l) {
+                int64_t idx = ((int64_t)r * n_steps + k) * E + l;
+                f[idx] += 0.5 * (times[k + 1] - times[k]) * area[l] * g[idx];
+            }
+    return 0;
+}
+
+/* L2(Sigma_h) error of piecewise-constant w against the Neumann datum. */
+int orc_neumann_error_nu(const double *nodes, int64_t n_nodes, const int32_t *tris, int64_t E,
+                         double alpha, const double *times, int32_t n_steps,
+                         const double *sources, int32_t n_src, int32_t nrhs, const double *w,
+                         int32_t q_space, int32_t n_time, double *err2, double *ref2)
+{
+    if (E < 1 || n_steps < 1 || nrhs < 1 || q_space < 1 || q_space > 32 || n_time < 1 ||
+        n_time > 64)
+        return -1;
+    int nq = q_space * q_space;
+    double *s1 = malloc(sizeof(double) * nq), *s2 = malloc(sizeof(double) * nq);
+    double *sw = malloc(sizeof(double) * nq), tx[64], tw[64];
+    double *area = malloc(sizeof(double) * E), *normal = malloc(sizeof(double) * 3 * E);
+    int rc = -1;
+    if (orc_triangle_rule(q_space, s1, s2, sw) || orc_gauss_legendre01(n_time, tx, tw) ||
+        orc_triangle_geometry(nodes, n_nodes, tris, E, area, normal))
+        goto done;
+    double e2 = 0.0, r2 = 0.0;
+    for (int r = 0; r < nrhs; ++r)
+        for (int k = 0; k < n_steps; ++k) {
+            const double t0 = times[k], hk = times[k + 1] - times[k];
+            for (int64_t j = 0; j < E; ++j) {
+                const int32_t *t3 = tris + 3 * j;
+                double wh = w[((int64_t)r * n_steps + k) * E + j];
+                double ae = 0.0, ar = 0.0;
+                for (int a = 0; a < nq; ++a) {
+                    double x[3];
+                    chi_plain(nodes + 3 * t3[0], nodes + 3 * t3[1], nodes + 3 * t3[2], s1[a],
+                              s2[a], x);
+                    for (int b = 0; b < n_time; ++b) {
+                        double we = neumann_datum(sources + (int64_t)r * n_src * 5, n_src, alpha,
+                                                  x, normal + 3 * j, t0 + tx[b] * hk);
+                        ae += sw[a] * tw[b] * (we - wh) * (we - wh);
+                        ar += sw[a] * tw[b] * we * we;
+                    }
+                }
+                e2 += 2.0 * area[j] * hk * ae;
+                r2 += 2.0 * area[j] * hk * ar;
+            }
+        }
+    *err2 = e2;
+    *ref2 = r2;
+    rc = 0;
+done:
+    free(s1);
+    free(s2);
+    free(sw);
+    free(area);
+    free(normal);
+    return rc;
+}
