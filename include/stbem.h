@@ -341,6 +341,56 @@ stb_status stb_assemble_vrhs(const stb_mesh *mesh, const stb_params *params, voi
                              const double *g, int32_t nrhs, double *f, void *workspace,
                              size_t workspace_bytes, stb_stream stream);
 
+/* ---- non-uniform time grids (Sec. 7: the antiderivatives carry over) ------------
+ * times: HOST FP64 [n_steps + 1], times[0] = 0, strictly increasing
+ * (params->n_steps steps; params->T is not used).  The matrices stay block
+ * lower triangular but are not Toeplitz: blocks A^{k,i}, k >= i, packed at
+ * b(k,i) = k(k+1)/2 + i, each E x E FP64 row-major.
+ * stb_assemble_nu: V, K (device FP64 [n_steps(n_steps+1)/2][E][E],
+ *   overwritten): A^{k,i} = S(t_{k+1}-t_{i+1}) - S(t_k-t_{i+1}) - S(t_{k+1}-t_i)
+ *   + S(t_k-t_i) for k > i and h_k S_*(0) - S(h_k) + S(0) on the diagonal
+ *   (eq. V0 / eq. K0 with the local step), S the pair's spatial sum of
+ *   G^{dtau dt} (or its scaled normal derivative) by the rules of
+ *   stb_assemble; every distinct time difference is evaluated once per
+ *   point.  Needs STB_PREC_FP64, STB_STORE_F64, n_steps <= 256.
+ * stb_matvec_nu: y^k = sum_{i <= k} A^{k,i} x^i (x, y device FP64
+ *   [nrhs][n_steps][E]).
+ * stb_solve_nu: w^k = (V^{k,k})^{-1} (f^k - sum_{i<k} V^{k,i} w^i), every
+ *   diagonal block inverted (blocked Cholesky); synchronises `stream`.
+ * stb_project_dirichlet_nu / stb_neumann_error_nu / stb_dirichlet_rhs_nu:
+ *   the data projection, the L2(Sigma_h) error and f = (1/2 M_h + K_h) g
+ *   (M_h = blockdiag(h_k diag(Delta_l))) on the grid; sources as for
+ *   stb_project_dirichlet; the first two share stb_project_nu_workspace_size. */
+stb_status stb_assemble_nu_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                          const double *times, size_t *bytes);
+stb_status stb_assemble_nu(const stb_mesh *mesh, const stb_params *params, const double *times,
+                           double *V, double *K, void *workspace, size_t workspace_bytes,
+                           stb_stream stream);
+stb_status stb_matvec_nu(const double *A, int64_t E, int32_t n_steps, int32_t nrhs,
+                         const double *x, double *y, stb_stream stream);
+stb_status stb_solve_nu_workspace_size(int64_t E, int32_t n_steps, int32_t nrhs, size_t *bytes);
+stb_status stb_solve_nu(const double *V, int64_t E, int32_t n_steps, int32_t nrhs,
+                        const double *f, double *w, void *workspace, size_t workspace_bytes,
+                        stb_stream stream);
+stb_status stb_project_nu_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                         int32_t nrhs, int32_t n_src, int32_t q_space,
+                                         int32_t n_time, size_t *bytes);
+stb_status stb_project_dirichlet_nu(const stb_mesh *mesh, const stb_params *params,
+                                    const double *times, const double *sources, int32_t nrhs,
+                                    int32_t n_src, int32_t q_space, int32_t n_time, double *g,
+                                    void *workspace, size_t workspace_bytes, stb_stream stream);
+stb_status stb_neumann_error_nu(const stb_mesh *mesh, const stb_params *params,
+                                const double *times, const double *sources, int32_t nrhs,
+                                int32_t n_src, const double *w, int32_t q_space, int32_t n_time,
+                                double *out, void *workspace, size_t workspace_bytes,
+                                stb_stream stream);
+stb_status stb_dirichlet_rhs_nu_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                               size_t *bytes);
+stb_status stb_dirichlet_rhs_nu(const stb_mesh *mesh, const stb_params *params,
+                                const double *times, const double *K, const double *g,
+                                int32_t nrhs, double *f, void *workspace, size_t workspace_bytes,
+                                stb_stream stream);
+
 /* ---- block-Toeplitz matrix-vector product (eq. V_mat) ---------------------------
  *   y_r^k = beta y_r^k + sum_{d=0}^{k} A^d x_r^{k-d},  k = 0..n_steps-1,
  * A: device [n_steps][E][E] of `a_storage`; x, y: device FP64

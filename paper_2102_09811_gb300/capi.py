@@ -78,6 +78,18 @@ _SIGS = {
     "stb_dirichlet_error_p1": (_I32, [_P, _PAR, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _SZ, _P]),
     "stb_assemble_vrhs_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
     "stb_assemble_vrhs": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
+    "stb_assemble_nu_workspace_size": (_I32, [_P, _PAR, _P, _PSZ]),
+    "stb_assemble_nu": (_I32, [_P, _PAR, _P, _P, _P, _P, _SZ, _P]),
+    "stb_matvec_nu": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
+    "stb_solve_nu_workspace_size": (_I32, [_I64, _I32, _I32, _PSZ]),
+    "stb_solve_nu": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P, _SZ, _P]),
+    "stb_project_nu_workspace_size": (_I32, [_P, _PAR, _I32, _I32, _I32, _I32, _PSZ]),
+    "stb_project_dirichlet_nu": (_I32, [_P, _PAR, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _SZ,
+                                        _P]),
+    "stb_neumann_error_nu": (_I32, [_P, _PAR, _P, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _SZ,
+                                    _P]),
+    "stb_dirichlet_rhs_nu_workspace_size": (_I32, [_P, _PAR, _PSZ]),
+    "stb_dirichlet_rhs_nu": (_I32, [_P, _PAR, _P, _P, _P, _I32, _P, _P, _SZ, _P]),
     "stb_potentials_workspace_size": (_I32, [_P, _PAR, _I32, _I64, _I32, _PSZ]),
     "stb_potentials": (_I32, [_P, _PAR, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P, _SZ, _P]),
     "stb_potentials_grid_workspace_size": (_I32, [_P, _PAR, _I32, _I64, _I32, _PSZ]),
@@ -371,6 +383,78 @@ def stb_assemble_vrhs(mesh, params, V, g, nrhs, f, workspace, stream=None):
                                         _ptr(f), _ptr(workspace),
                                         workspace.numel() * workspace.element_size(),
                                         _stream(stream)), "stb_assemble_vrhs")
+
+
+# ---- non-uniform time grids -------------------------------------------------------
+def _times(times):
+    t, tp = _host_f64(times)
+    return t, tp
+
+
+def stb_assemble_nu_workspace_size(mesh, params, times):
+    t, tp = _times(times)
+    return _size(_library().stb_assemble_nu_workspace_size, mesh.handle, ctypes.byref(params), tp)
+
+
+def stb_assemble_nu(mesh, params, times, V, K, workspace, stream=None):
+    t, tp = _times(times)
+    _check(_library().stb_assemble_nu(mesh.handle, ctypes.byref(params), tp, _ptr(V), _ptr(K),
+                                      _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                      _stream(stream)), "stb_assemble_nu")
+
+
+def stb_matvec_nu(A, E, n_steps, nrhs, x, y, stream=None):
+    _check(_library().stb_matvec_nu(_ptr(A), E, n_steps, nrhs, _ptr(x), _ptr(y), _stream(stream)),
+           "stb_matvec_nu")
+
+
+def stb_solve_nu_workspace_size(E, n_steps, nrhs):
+    return _size(_library().stb_solve_nu_workspace_size, E, n_steps, nrhs)
+
+
+def stb_solve_nu(V, E, n_steps, nrhs, f, w, workspace, stream=None):
+    _check(_library().stb_solve_nu(_ptr(V), E, n_steps, nrhs, _ptr(f), _ptr(w), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _stream(stream)),
+           "stb_solve_nu")
+
+
+def stb_project_nu_workspace_size(mesh, params, nrhs, n_src, q_space=8, n_time=16):
+    return _size(_library().stb_project_nu_workspace_size, mesh.handle, ctypes.byref(params), nrhs,
+                 n_src, q_space, n_time)
+
+
+def stb_project_dirichlet_nu(mesh, params, times, sources, g, workspace, q_space=8, n_time=16,
+                             stream=None):
+    t, tp = _times(times)
+    src, sp = _host_f64(sources)
+    _check(_library().stb_project_dirichlet_nu(mesh.handle, ctypes.byref(params), tp, sp,
+                                               src.shape[0], src.shape[1], q_space, n_time,
+                                               _ptr(g), _ptr(workspace),
+                                               workspace.numel() * workspace.element_size(),
+                                               _stream(stream)), "stb_project_dirichlet_nu")
+
+
+def stb_neumann_error_nu(mesh, params, times, sources, w, out, workspace, q_space=8, n_time=16,
+                         stream=None):
+    t, tp = _times(times)
+    src, sp = _host_f64(sources)
+    _check(_library().stb_neumann_error_nu(mesh.handle, ctypes.byref(params), tp, sp, src.shape[0],
+                                           src.shape[1], _ptr(w), q_space, n_time, _ptr(out),
+                                           _ptr(workspace),
+                                           workspace.numel() * workspace.element_size(),
+                                           _stream(stream)), "stb_neumann_error_nu")
+
+
+def stb_dirichlet_rhs_nu_workspace_size(mesh, params):
+    return _size(_library().stb_dirichlet_rhs_nu_workspace_size, mesh.handle, ctypes.byref(params))
+
+
+def stb_dirichlet_rhs_nu(mesh, params, times, K, g, nrhs, f, workspace, stream=None):
+    t, tp = _times(times)
+    _check(_library().stb_dirichlet_rhs_nu(mesh.handle, ctypes.byref(params), tp, _ptr(K), _ptr(g),
+                                           nrhs, _ptr(f), _ptr(workspace),
+                                           workspace.numel() * workspace.element_size(),
+                                           _stream(stream)), "stb_dirichlet_rhs_nu")
 
 
 def stb_toeplitz_workspace_size(E, n_steps, nrhs):

@@ -18,6 +18,7 @@
 //    shared memory, and one thread writes V^d and K^d of both (a,b) and (b,a):
 //    the rule is built once for the ordered pair, so V^d is symmetric.
 #include <cmath>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <type_traits>
@@ -1038,6 +1039,232 @@ k_singular_d2_f64(const double *__restrict__ geo, const int32_t *__restrict__ tr
     }
 }
 
+// ------------------------------------------------ non-uniform time grids ---
+// On a grid t_0 = 0 < t_1 < ... < t_n the blocks A^{k,i} (k >= i, packed at
+// b(k,i) = k(k+1)/2 + i) are four-corner combinations of the spatial sums S
+// of G^{dtau dt} (and of its scaled normal derivative) at the time
+// differences t_a - t_b; the diagonal adds h_k times the delta = 0
+// singular sums (eq. V0 / eq. K0 with the local step).  The host lists the
+// distinct differences ("levels", level 0 = delta 0) and, per level, the
+// blocks it enters with its coefficient (CSR); a thread that owns the entry
+// (l, j) of every block evaluates each level once and adds it to the blocks
+// of its list.  The blocks must start at zero; FP64 storage only (the
+// corner terms cancel).
+struct NuLists {
+    const double *levels;      // [n_levels][LV_STRIDE]
+    const int32_t *off;        // [n_levels + 2]: levels 0..n_levels-1, then the singular list
+    const int32_t *blk;
+    const double *coef;
+    int n_levels;
+};
+
+template <int CH>
+__global__ void __launch_bounds__(REG_THREADS)
+k_regular_nu_f64(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E,
+                 const double *__restrict__ rule, int nq, NuLists lists, Globals g,
+                 double *__restrict__ V, double *__restrict__ K) {
+    __shared__ double xa[4 * MAX_RULE];
+    const int l = blockIdx.y;
+    const int j = blockIdx.x * REG_THREADS + threadIdx.x;
+    const double *gl = geo + (size_t)l * GEO_STRIDE;
+    for (int a = threadIdx.x; a < nq; a += REG_THREADS) {
+        double s1 = rule[3 * a], s2 = rule[3 * a + 1];
+        for (int c = 0; c < 3; ++c)
+            xa[4 * a + c] = gl[GEO_V0 + c] + s1 * (gl[GEO_V1 + c] - gl[GEO_V0 + c]) +
+                            s2 * (gl[GEO_V2 + c] - gl[GEO_V1 + c]);
+        xa[4 * a + 3] = rule[3 * a + 2];
+    }
+    __syncthreads();
+    if (j >= E) return;
+    const int32_t tl[3] = {tris[3 * l], tris[3 * l + 1], tris[3 * l + 2]};
+    const int32_t tj[3] = {tris[3 * j], tris[3 * j + 1], tris[3 * j + 2]};
+    if (touches(tl, tj)) return;
+    const double *gj = geo + (size_t)j * GEO_STRIDE;
+    double P0[3], e1[3], e2[3], n[3];
+    for (int c = 0; c < 3; ++c) {
+        P0[c] = gj[GEO_V0 + c];
+        e1[c] = gj[GEO_V1 + c] - gj[GEO_V0 + c];
+        e2[c] = gj[GEO_V2 + c] - gj[GEO_V1 + c];
+        n[c] = gj[GEO_N + c];
+    }
+    const double scale = 4.0 * gl[GEO_AREA] * gj[GEO_AREA];
+    const size_t EE = (size_t)E * E, ij = (size_t)l * E + j;
+    auto add = [&](int L, double sv, double sk) {
+        for (int e = lists.off[L]; e < lists.off[L + 1]; ++e) {
+            const size_t o = (size_t)lists.blk[e] * EE + ij;
+            V[o] += lists.coef[e] * sv;
+            K[o] += lists.coef[e] * sk;
+        }
+    };
+    // level 0 (delta -> 0 limits) and the delta = 0 singular sums
+    double s0v = 0, s0k = 0, ssv = 0, ssk = 0;
+    for (int b = 0; b < nq; ++b) {
+        double t1 = rule[3 * b], t2 = rule[3 * b + 1], wb = rule[3 * b + 2];
+        double y0 = P0[0] + t1 * e1[0] + t2 * e2[0];
+        double y1 = P0[1] + t1 * e1[1] + t2 * e2[1];
+        double y2 = P0[2] + t1 * e1[2] + t2 * e2[2];
+        for (int a = 0; a < nq; ++a) {
+            double r0 = xa[4 * a] - y0, r1 = xa[4 * a + 1] - y1, r2 = xa[4 * a + 2] - y2;
+            double rr = r0 * r0 + r1 * r1 + r2 * r2;
+            double irho = rsqrt(rr), rho = rr * irho;
+            double rnr = (r0 * n[0] + r1 * n[1] + r2 * n[2]) * irho;
+            double w = xa[4 * a + 3] * wb;
+            s0v = fma(w, g.A * rho, s0v);
+            s0k = fma(w, -g.Ap * rnr, s0k);
+            ssv = fma(w, g.F * irho, ssv);
+            ssk = fma(w, g.Fs * rnr * irho * irho, ssk);
+        }
+    }
+    add(0, scale * s0v, scale * s0k);
+    add(lists.n_levels, scale * ssv, scale * ssk);
+    for (int c0 = 1; c0 < lists.n_levels; c0 += CH) {
+        double sv[CH], sk[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) sv[u] = sk[u] = 0.0;
+        for (int b = 0; b < nq; ++b) {
+            double t1 = rule[3 * b], t2 = rule[3 * b + 1], wb = rule[3 * b + 2];
+            double y0 = P0[0] + t1 * e1[0] + t2 * e2[0];
+            double y1 = P0[1] + t1 * e1[1] + t2 * e2[1];
+            double y2 = P0[2] + t1 * e1[2] + t2 * e2[2];
+            for (int a = 0; a < nq; ++a) {
+                double r0 = xa[4 * a] - y0, r1 = xa[4 * a + 1] - y1, r2 = xa[4 * a + 2] - y2;
+                double rr = r0 * r0 + r1 * r1 + r2 * r2;
+                double irho = rsqrt(rr), rho = rr * irho;
+                double rnr = (r0 * n[0] + r1 * n[1] + r2 * n[2]) * irho;
+                double w = xa[4 * a + 3] * wb, wk = w * rnr;
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    if (c0 + u < lists.n_levels) {
+                        double v, kf;
+                        eval_level(rho, irho, lists.levels + (c0 + u) * LV_STRIDE, g, v, kf);
+                        sv[u] = fma(w, v, sv[u]);
+                        sk[u] = fma(wk, kf, sk[u]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (c0 + u < lists.n_levels) add(c0 + u, scale * sv[u], scale * sk[u]);
+    }
+}
+
+template <int CH>
+__global__ void __launch_bounds__(SS_THREADS)
+k_singular_nu_f64(const double *__restrict__ geo, const TouchPair *__restrict__ pairs, int E,
+                  SSTables tab, NuLists lists, Globals g, double *__restrict__ V,
+                  double *__restrict__ K) {
+    __shared__ double red[SS_THREADS / 32][3 * CH + 8];
+    __shared__ double fin[3 * CH + 8];
+    const TouchPair P = pairs[blockIdx.x];
+    const int a = P.a, b = P.b, cls = P.cls;
+    if (a < 0 || b < a || b >= E || cls < PAIR_VERTEX || cls > PAIR_IDENTICAL) return;
+    const double *ga = geo + (size_t)a * GEO_STRIDE, *gb = geo + (size_t)b * GEO_STRIDE;
+    double A0[3], A1[3], A2[3], B0[3], B1[3], B2[3], na[3], nb[3];
+    {
+        int oa0 = P.perm & 3, oa1 = (P.perm >> 2) & 3, oa2 = (P.perm >> 4) & 3;
+        int ob0 = (P.perm >> 6) & 3, ob1 = (P.perm >> 8) & 3, ob2 = (P.perm >> 10) & 3;
+        for (int c = 0; c < 3; ++c) {
+            A0[c] = ga[3 * oa0 + c];
+            A1[c] = ga[3 * oa1 + c] - ga[3 * oa0 + c];
+            A2[c] = ga[3 * oa2 + c] - ga[3 * oa1 + c];
+            B0[c] = gb[3 * ob0 + c];
+            B1[c] = gb[3 * ob1 + c] - gb[3 * ob0 + c];
+            B2[c] = gb[3 * ob2 + c] - gb[3 * ob1 + c];
+            na[c] = ga[GEO_N + c];
+            nb[c] = gb[GEO_N + c];
+        }
+    }
+    const double scale = 4.0 * ga[GEO_AREA] * gb[GEO_AREA];
+    const bool ident = cls == PAIR_IDENTICAL;
+    const int npt = tab.n[cls];
+    const double *S1 = tab.s1[cls], *S2 = tab.s2[cls], *T1 = tab.t1[cls], *T2 = tab.t2[cls],
+                 *W = tab.w[cls];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t EE = (size_t)E * E, iab = (size_t)a * E + b, iba = (size_t)b * E + a;
+    auto point = [&](int p, double &rho, double &irho, double &rab, double &rba, double &w) {
+        double s1 = S1[p], s2 = S2[p], t1 = T1[p], t2 = T2[p];
+        double r[3];
+        for (int c = 0; c < 3; ++c)
+            r[c] = (A0[c] + s1 * A1[c] + s2 * A2[c]) - (B0[c] + t1 * B1[c] + t2 * B2[c]);
+        double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        irho = rsqrt(rr);
+        rho = rr * irho;
+        rab = (r[0] * nb[0] + r[1] * nb[1] + r[2] * nb[2]) * irho;
+        rba = -(r[0] * na[0] + r[1] * na[1] + r[2] * na[2]) * irho;
+        w = W[p];
+    };
+    auto reduce = [&](double *vals, int nv) {
+        for (int k = 0; k < nv; ++k) {
+            double v = vals[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < nv) {
+            double s = 0.0;
+            for (int wi = 0; wi < SS_THREADS / 32; ++wi) s += red[wi][threadIdx.x];
+            fin[threadIdx.x] = scale * s;
+        }
+        __syncthreads();
+    };
+    // thread 0 adds level L's sums (V, K at (a,b), K at (b,a)) to its blocks
+    auto add = [&](int L, double cv, double ca, double cb) {
+        for (int e = lists.off[L]; e < lists.off[L + 1]; ++e) {
+            const size_t o = (size_t)lists.blk[e] * EE;
+            const double c = lists.coef[e];
+            V[o + iab] += c * cv;
+            if (!ident) {
+                V[o + iba] += c * cv;
+                K[o + iab] += c * ca;
+                K[o + iba] += c * cb;
+            }
+        }
+    };
+    double z[6] = {0, 0, 0, 0, 0, 0};
+    for (int p = threadIdx.x; p < npt; p += SS_THREADS) {
+        double rho, irho, rab, rba, w;
+        point(p, rho, irho, rab, rba, w);
+        z[0] = fma(w, g.A * rho, z[0]);
+        z[1] = fma(w, -g.Ap * rab, z[1]);
+        z[2] = fma(w, -g.Ap * rba, z[2]);
+        z[3] = fma(w, g.F * irho, z[3]);
+        z[4] = fma(w, g.Fs * rab * irho * irho, z[4]);
+        z[5] = fma(w, g.Fs * rba * irho * irho, z[5]);
+    }
+    reduce(z, 6);
+    if (threadIdx.x == 0) {
+        add(0, fin[0], fin[1], fin[2]);
+        add(lists.n_levels, fin[3], fin[4], fin[5]);
+    }
+    __syncthreads();
+    for (int c0 = 1; c0 < lists.n_levels; c0 += CH) {
+        double acc[3 * CH];
+#pragma unroll
+        for (int k = 0; k < 3 * CH; ++k) acc[k] = 0.0;
+        for (int p = threadIdx.x; p < npt; p += SS_THREADS) {
+            double rho, irho, rab, rba, w;
+            point(p, rho, irho, rab, rba, w);
+            double wa = w * rab, wb = w * rba;
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                if (c0 + u < lists.n_levels) {
+                    double v, kf;
+                    eval_level(rho, irho, lists.levels + (c0 + u) * LV_STRIDE, g, v, kf);
+                    acc[u] = fma(w, v, acc[u]);
+                    acc[CH + u] = fma(wa, kf, acc[CH + u]);
+                    acc[2 * CH + u] = fma(wb, kf, acc[2 * CH + u]);
+                }
+            }
+        }
+        reduce(acc, 3 * CH);
+        if (threadIdx.x == 0)
+            for (int u = 0; u < CH && c0 + u < lists.n_levels; ++u)
+                add(c0 + u, fin[u], fin[CH + u], fin[2 * CH + u]);
+        __syncthreads();
+    }
+}
+
 template <class OutT>
 static stb_status run_assembly(const Mesh &m, const stb_params &p, OutT *V, OutT *K,
                                const AssemblyLayout &L, int32_t *status, cudaStream_t s) {
@@ -1481,5 +1708,164 @@ extern "C" stb_status stb_assemble_vrhs(const stb_mesh *mesh, const stb_params *
     if ((st = prepare_mixed(m, *params, L, status_word(ws), s))) return st;
     STB_CUDA(cudaMemsetAsync(f, 0, sizeof(double) * (size_t)nrhs * params->n_steps * m.n_tris, s));
     return run_vrhs_mixed(m, *params, (float *)V, g, nrhs, f, L, s);
+}
+
+// ---- non-uniform time grids (Sec. 7) ----------------------------------------
+namespace {
+struct NuHost {
+    std::vector<double> levels;  // [n_levels][LV_STRIDE]
+    std::vector<int32_t> off, blk;
+    std::vector<double> coef;
+    int n_levels = 0;
+};
+
+stb_status nu_check(const stb_params *p, const double *times) {
+    if (!times) return fail(STB_ERR_INVALID_ARG, "times must be given");
+    if (times[0] != 0.0) return fail(STB_ERR_INVALID_ARG, "times[0] must be 0");
+    for (int k = 0; k < p->n_steps; ++k)
+        if (!(times[k + 1] > times[k]) || !std::isfinite(times[k + 1]))
+            return fail(STB_ERR_INVALID_ARG, "times must increase strictly (step %d)", k);
+    if (p->n_steps > 256) return fail(STB_ERR_INVALID_ARG, "non-uniform grids support n_steps <= 256");
+    return STB_OK;
+}
+
+// The distinct time differences and, per difference, the blocks it enters.
+NuHost nu_lists(const stb_params &p, const double *t) {
+    const int n = p.n_steps;
+    std::map<double, int> index;
+    index[0.0] = 0;
+    std::vector<std::vector<std::pair<int32_t, double>>> per(1);
+    std::vector<std::pair<int32_t, double>> sing;
+    auto level = [&](double d) {
+        auto it = index.find(d);
+        if (it != index.end()) return it->second;
+        const int L = (int)per.size();
+        index[d] = L;
+        per.emplace_back();
+        return L;
+    };
+    for (int k = 0; k < n; ++k)
+        for (int i = 0; i <= k; ++i) {
+            const int32_t b = k * (k + 1) / 2 + i;
+            if (i == k) {
+                const double h = t[k + 1] - t[k];
+                per[level(h)].push_back({b, -1.0});
+                per[0].push_back({b, 1.0});
+                sing.push_back({b, h});
+            } else {
+                per[level(t[k + 1] - t[i + 1])].push_back({b, 1.0});
+                per[level(t[k] - t[i + 1])].push_back({b, -1.0});
+                per[level(t[k + 1] - t[i])].push_back({b, -1.0});
+                per[level(t[k] - t[i])].push_back({b, 1.0});
+            }
+        }
+    NuHost H;
+    H.n_levels = (int)per.size();
+    H.levels.assign((size_t)H.n_levels * LV_STRIDE, 0.0);
+    const double pi = 3.14159265358979323846, al = p.alpha;
+    for (auto &kv : index) {
+        if (kv.second == 0) continue;
+        const double delta = kv.first, sd = std::sqrt(delta);
+        double *lv = H.levels.data() + (size_t)kv.second * LV_STRIDE;
+        lv[LV_C] = 1.0 / (2.0 * std::sqrt(al * delta));
+        lv[LV_B] = delta / (4.0 * pi * al);
+        lv[LV_CC] = sd / (4.0 * pi * std::sqrt(pi * al * al * al));
+        lv[LV_D] = delta / (4.0 * pi);
+        lv[LV_E] = sd / (4.0 * pi * std::sqrt(pi * al));
+    }
+    H.off.push_back(0);
+    for (int L = 0; L <= H.n_levels; ++L) {
+        const auto &lst = L < H.n_levels ? per[L] : sing;
+        for (auto &e : lst) {
+            H.blk.push_back(e.first);
+            H.coef.push_back(e.second);
+        }
+        H.off.push_back((int32_t)H.blk.size());
+    }
+    return H;
+}
+
+size_t nu_table_bytes(const NuHost &H) {
+    return align256(sizeof(double) * H.levels.size()) + align256(sizeof(int32_t) * H.off.size()) +
+           align256(sizeof(int32_t) * H.blk.size()) + align256(sizeof(double) * H.coef.size());
+}
+}  // namespace
+
+extern "C" stb_status stb_assemble_nu_workspace_size(const stb_mesh *mesh, const stb_params *params,
+                                                     const double *times, size_t *bytes) {
+    if (!mesh || !params || !bytes) return fail(STB_ERR_INVALID_ARG, "mesh, params and bytes must be given");
+    stb_status st = nu_check(params, times);
+    if (st) return st;
+    stb_params p = *params;
+    p.T = times[p.n_steps];
+    if ((st = check_assembly_params(&p))) return st;
+    if (p.precision != STB_PREC_FP64 || p.storage != STB_STORE_F64)
+        return fail(STB_ERR_INVALID_ARG, "non-uniform grids need STB_PREC_FP64 and STB_STORE_F64");
+    *bytes = align256(assembly_layout(mesh->m, p, nullptr, 0).bytes) + nu_table_bytes(nu_lists(p, times));
+    return STB_OK;
+}
+
+extern "C" stb_status stb_assemble_nu(const stb_mesh *mesh, const stb_params *params,
+                                      const double *times, double *V, double *K, void *ws,
+                                      size_t ws_bytes, stb_stream stream) {
+    if (!V || !K) return fail(STB_ERR_INVALID_ARG, "V and K must be given");
+    size_t need;
+    stb_status st = stb_assemble_nu_workspace_size(mesh, params, times, &need);
+    if (st) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    const Mesh &m = mesh->m;
+    if (m.n_tris > 65535) return fail(STB_ERR_INVALID_ARG, "dense assembly supports E <= 65535");
+    stb_params p = *params;
+    p.T = times[p.n_steps];
+    const NuHost H = nu_lists(p, times);
+    AssemblyLayout L = assembly_layout(m, p, ws, ws_bytes);
+    char *q = static_cast<char *>(ws) + align256(L.bytes);
+    double *d_lv = reinterpret_cast<double *>(q);
+    q += align256(sizeof(double) * H.levels.size());
+    int32_t *d_off = reinterpret_cast<int32_t *>(q);
+    q += align256(sizeof(int32_t) * H.off.size());
+    int32_t *d_blk = reinterpret_cast<int32_t *>(q);
+    q += align256(sizeof(int32_t) * H.blk.size());
+    double *d_coef = reinterpret_cast<double *>(q);
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = prepare_fp64(m, p, L, status_word(ws), s))) return st;
+    STB_CUDA(cudaMemcpyAsync(d_lv, H.levels.data(), sizeof(double) * H.levels.size(),
+                             cudaMemcpyHostToDevice, s));
+    STB_CUDA(cudaMemcpyAsync(d_off, H.off.data(), sizeof(int32_t) * H.off.size(),
+                             cudaMemcpyHostToDevice, s));
+    STB_CUDA(cudaMemcpyAsync(d_blk, H.blk.data(), sizeof(int32_t) * H.blk.size(),
+                             cudaMemcpyHostToDevice, s));
+    STB_CUDA(cudaMemcpyAsync(d_coef, H.coef.data(), sizeof(double) * H.coef.size(),
+                             cudaMemcpyHostToDevice, s));
+    const int E = (int)m.n_tris;
+    const size_t nblk = (size_t)p.n_steps * (p.n_steps + 1) / 2;
+    STB_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * nblk * E * E, s));
+    STB_CUDA(cudaMemsetAsync(K, 0, sizeof(double) * nblk * E * E, s));
+    NuLists lists{d_lv, d_off, d_blk, d_coef, H.n_levels};
+    Globals g = make_globals(p);
+    dim3 grid((E + REG_THREADS - 1) / REG_THREADS, E);
+    count_launch(s);
+    k_regular_nu_f64<4><<<grid, REG_THREADS, 0, s>>>(L.geo, m.d_tris, E, L.rule,
+                                                     p.quad_regular * p.quad_regular, lists, g, V,
+                                                     K);
+    if ((st = check_launch("k_regular_nu_f64"))) return st;
+    if (m.n_touch == 0) return STB_OK;
+    SSTables tab{};
+    const double *base = L.ss;
+    for (int cls = 1; cls <= 3; ++cls) {
+        size_t n = L.ss_n[cls];
+        tab.s1[cls] = base;
+        tab.s2[cls] = base + n;
+        tab.t1[cls] = base + 2 * n;
+        tab.t2[cls] = base + 3 * n;
+        tab.w[cls] = base + 4 * n;
+        tab.n[cls] = (int)n;
+        base += 5 * n;
+    }
+    count_launch(s);
+    k_singular_nu_f64<4><<<(unsigned)m.n_touch, SS_THREADS, 0, s>>>(L.geo, L.pairs, E, tab, lists,
+                                                                    g, V, K);
+    return check_launch("k_singular_nu_f64");
 }
 

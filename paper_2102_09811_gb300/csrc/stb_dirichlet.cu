@@ -13,6 +13,7 @@
 #include "stb_dense.h"
 #include "stb_heat.h"
 #include "stb_internal.h"
+#include "stb_nonuniform.h"
 #include "stb_toeplitz.h"
 
 namespace stb {
@@ -61,7 +62,7 @@ template <class R, bool NEU = false>
 __global__ void __launch_bounds__(DIR_THREADS)
 k_project(const double *__restrict__ geo, int E, const double *__restrict__ rule, int nq, int nt,
           const double *__restrict__ src, int n_src, int nrhs, int n_steps, double h_, double alpha_,
-          double *__restrict__ g) {
+          double *__restrict__ g, const double *__restrict__ times = nullptr) {
     __shared__ R rs[3 * MAX_QS * MAX_QS + 2 * MAX_NT];
     __shared__ R sr[5 * MAX_SRC];
     const R h = (R)h_, alpha = (R)alpha_;
@@ -83,7 +84,7 @@ k_project(const double *__restrict__ geo, int E, const double *__restrict__ rule
             x[c] = (R)(gj[c] + (double)s1 * (gj[3 + c] - gj[c]) + (double)s2 * (gj[6 + c] - gj[3 + c]));
         R inner = 0;
         for (int b = 0; b < nt; ++b) {
-            R t = (k + tx[b]) * h, gv = 0;
+            R t = times ? (R)(times[k] + (double)tx[b] * (times[k + 1] - times[k])) : (k + tx[b]) * h, gv = 0;
             for (int s = 0; s < n_src; ++s) {
                 const R *S = sr + 5 * s;
                 R d0 = x[0] - S[0], d1 = x[1] - S[1], d2 = x[2] - S[2];
@@ -199,7 +200,8 @@ template <class R>
 __global__ void __launch_bounds__(DIR_THREADS)
 k_error(const double *__restrict__ geo, int E, const double *__restrict__ rule, int nq, int nt,
         const double *__restrict__ src, int n_src, int nrhs, int n_steps, double h_, double alpha_,
-        const double *__restrict__ wh, double *__restrict__ part) {
+        const double *__restrict__ wh, double *__restrict__ part,
+        const double *__restrict__ times = nullptr) {
     __shared__ R rs[3 * MAX_QS * MAX_QS + 2 * MAX_NT];
     __shared__ R sr[5 * MAX_SRC];
     const R h = (R)h_, alpha = (R)alpha_;
@@ -224,7 +226,7 @@ k_error(const double *__restrict__ geo, int E, const double *__restrict__ rule, 
                 x[c] = (R)(gj[c] + (double)s1 * (gj[3 + c] - gj[c]) + (double)s2 * (gj[6 + c] - gj[3 + c]));
             R ie = 0, ir = 0;
             for (int b = 0; b < nt; ++b) {
-                R t = (k + tx[b]) * h, wv = 0;
+                R t = times ? (R)(times[k] + (double)tx[b] * (times[k + 1] - times[k])) : (k + tx[b]) * h, wv = 0;
                 for (int s = 0; s < n_src; ++s) {
                     const R *S = sr + 5 * s;
                     R tau = t - S[3];
@@ -239,7 +241,7 @@ k_error(const double *__restrict__ geo, int E, const double *__restrict__ rule, 
             e2r = fma(wa, ie, e2r);
             r2r = fma(wa, ir, r2r);
         }
-        double f = 2.0 * gj[GEO_AREA] * h_;
+        double f = 2.0 * gj[GEO_AREA] * (times ? times[k + 1] - times[k] : h_);
         e2 = (double)e2r * f;
         r2 = (double)r2r * f;
     }
@@ -791,5 +793,129 @@ extern "C" stb_status stb_neumann_rhs(const stb_mesh *mesh, const stb_params *p,
     k_add_mass_p1t<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
         geo, m.d_tris, (int)m.n_tris, (int)m.n_nodes, total, p->T / p->n_steps, hd, f);
     return check_launch("k_add_mass_p1t");
+}
+
+// ------------------------------------------ non-uniform time grids (Sec. 7) ---
+static stb_status nu_times_check(const stb_params *p, const double *times) {
+    if (!p || !times) return fail(STB_ERR_INVALID_ARG, "params and times must be given");
+    if (p->n_steps < 1 || times[0] != 0.0) return fail(STB_ERR_INVALID_ARG, "need n_steps >= 1, times[0] = 0");
+    for (int k = 0; k < p->n_steps; ++k)
+        if (!(times[k + 1] > times[k])) return fail(STB_ERR_INVALID_ARG, "times must increase strictly");
+    return STB_OK;
+}
+
+// f^k += (h_k / 2) Delta_l g^k
+__global__ void k_add_mass_nu(const double *__restrict__ geo, int E, int n_steps, size_t total,
+                              const double *__restrict__ times, const double *__restrict__ g,
+                              double *__restrict__ f) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int l = (int)(idx % E), k = (int)((idx / E) % n_steps);
+    const double h = times[k + 1] - times[k];
+    f[idx] = fma(0.5 * h * geo[(size_t)l * GEO_STRIDE + GEO_AREA], g[idx], f[idx]);
+}
+
+extern "C" stb_status stb_project_nu_workspace_size(const stb_mesh *mesh, const stb_params *p,
+                                                    int32_t nrhs, int32_t n_src, int32_t q,
+                                                    int32_t nt, size_t *bytes) {
+    if (!mesh || !p || !bytes) return fail(STB_ERR_INVALID_ARG, "invalid argument");
+    stb_status st = check_rule_args(nrhs, n_src, q, nt);
+    if (st) return st;
+    const size_t nblk = error_blocks(mesh->m, p->n_steps, nrhs);
+    *bytes = align256(dir_layout(mesh->m, nrhs, n_src, q, nt, nullptr, 0, 2 * nblk).bytes) +
+             align256(sizeof(double) * (p->n_steps + 1));
+    return STB_OK;
+}
+
+// project (mode 0) or error (mode 1) on a non-uniform grid
+static stb_status nu_data(int mode, const stb_mesh *mesh, const stb_params *p, const double *times,
+                          const double *sources, int32_t nrhs, int32_t n_src, int32_t q,
+                          int32_t nt, const double *w, double *out, void *ws, size_t ws_bytes,
+                          cudaStream_t s) {
+    if (!mesh || !sources || !out || (mode == 1 && !w)) return fail(STB_ERR_INVALID_ARG, "null argument");
+    stb_status st = nu_times_check(p, times);
+    if (st) return st;
+    if (!(p->alpha > 0)) return fail(STB_ERR_INVALID_ARG, "alpha must be positive");
+    size_t need;
+    if ((st = stb_project_nu_workspace_size(mesh, p, nrhs, n_src, q, nt, &need))) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    const Mesh &m = mesh->m;
+    const size_t nblk = error_blocks(m, p->n_steps, nrhs);
+    DirLayout L = dir_layout(m, nrhs, n_src, q, nt, ws, ws_bytes, 2 * nblk);
+    double *d_times = reinterpret_cast<double *>(static_cast<char *>(ws) + align256(L.bytes));
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    if ((st = upload_rules_sources(L, q, nt, sources, nrhs, n_src, s))) return st;
+    STB_CUDA(cudaMemcpyAsync(d_times, times, sizeof(double) * (p->n_steps + 1),
+                             cudaMemcpyHostToDevice, s));
+    if ((st = launch_geometry(m, L.geo, s))) return st;
+    const size_t n = (size_t)p->n_steps * m.n_tris;
+    dim3 grid((unsigned)((n + DIR_THREADS - 1) / DIR_THREADS), (unsigned)nrhs);
+    count_launch(s);
+    if (mode == 0) {
+        k_project<double><<<grid, DIR_THREADS, 0, s>>>(L.geo, (int)m.n_tris, L.rule, q * q, nt,
+                                                       L.src, n_src, nrhs, p->n_steps, 0.0,
+                                                       p->alpha, out, d_times);
+        return check_launch("k_project(non-uniform)");
+    }
+    k_error<double><<<grid, DIR_THREADS, 0, s>>>(L.geo, (int)m.n_tris, L.rule, q * q, nt, L.src,
+                                                 n_src, nrhs, p->n_steps, 0.0, p->alpha, w, L.part,
+                                                 d_times);
+    if ((st = check_launch("k_error(non-uniform)"))) return st;
+    count_launch(s);
+    k_sum_pairs<<<1, 1024, 0, s>>>(L.part, nblk, out);
+    return check_launch("k_sum_pairs");
+}
+
+extern "C" stb_status stb_project_dirichlet_nu(const stb_mesh *mesh, const stb_params *p,
+                                               const double *times, const double *sources,
+                                               int32_t nrhs, int32_t n_src, int32_t q, int32_t nt,
+                                               double *g, void *ws, size_t ws_bytes,
+                                               stb_stream stream) {
+    return nu_data(0, mesh, p, times, sources, nrhs, n_src, q, nt, nullptr, g, ws, ws_bytes,
+                   (cudaStream_t)stream);
+}
+
+extern "C" stb_status stb_neumann_error_nu(const stb_mesh *mesh, const stb_params *p,
+                                           const double *times, const double *sources,
+                                           int32_t nrhs, int32_t n_src, const double *w, int32_t q,
+                                           int32_t nt, double *out, void *ws, size_t ws_bytes,
+                                           stb_stream stream) {
+    return nu_data(1, mesh, p, times, sources, nrhs, n_src, q, nt, w, out, ws, ws_bytes,
+                   (cudaStream_t)stream);
+}
+
+extern "C" stb_status stb_dirichlet_rhs_nu_workspace_size(const stb_mesh *mesh,
+                                                          const stb_params *p, size_t *bytes) {
+    if (!mesh || !p || !bytes || p->n_steps < 1) return fail(STB_ERR_INVALID_ARG, "invalid argument");
+    *bytes = align256(256 + align256(sizeof(double) * mesh->m.n_tris * GEO_STRIDE) +
+                      align256(sizeof(double) * (p->n_steps + 1)));
+    return STB_OK;
+}
+
+extern "C" stb_status stb_dirichlet_rhs_nu(const stb_mesh *mesh, const stb_params *p,
+                                           const double *times, const double *K, const double *g,
+                                           int32_t nrhs, double *f, void *ws, size_t ws_bytes,
+                                           stb_stream stream) {
+    if (!mesh || !K || !g || !f || nrhs < 1) return fail(STB_ERR_INVALID_ARG, "null argument");
+    stb_status st = nu_times_check(p, times);
+    if (st) return st;
+    size_t need;
+    if ((st = stb_dirichlet_rhs_nu_workspace_size(mesh, p, &need))) return st;
+    if ((st = check_workspace(ws, ws_bytes, need))) return st;
+    const Mesh &m = mesh->m;
+    Carve c(ws, ws_bytes);
+    double *geo = c.take<double>((size_t)m.n_tris * GEO_STRIDE);
+    double *d_times = c.take<double>(p->n_steps + 1);
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    STB_CUDA(cudaMemcpyAsync(d_times, times, sizeof(double) * (p->n_steps + 1),
+                             cudaMemcpyHostToDevice, s));
+    if ((st = launch_geometry(m, geo, s))) return st;
+    if ((st = matvec_nu(K, m.n_tris, p->n_steps, nrhs, g, f, s))) return st;
+    const size_t total = (size_t)nrhs * p->n_steps * m.n_tris;
+    count_launch(s);
+    k_add_mass_nu<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(geo, (int)m.n_tris, p->n_steps,
+                                                                  total, d_times, g, f);
+    return check_launch("k_add_mass_nu");
 }
 

@@ -7,6 +7,8 @@ order; all arithmetic happens in the CUDA kernels.
 """
 import math
 
+import numpy as np
+
 import torch
 
 from . import capi
@@ -212,6 +214,56 @@ class NeumannProblem:
                             q_space, stream)
         capi.stb_workspace_status(ws, stream)
         return slp - dlp
+
+
+class NonUniformDirichletProblem:
+    """The Dirichlet problem on a non-uniform time grid `times` (Sec. 7; FP64):
+    block lower-triangular V, K with packed blocks, data projection over the
+    steps, right-hand side, forward substitution with a factorisation per
+    diagonal block, and the L2(Sigma_h) error."""
+
+    def __init__(self, nodes, tris, alpha, times, sources, quad_regular=3, quad_singular=4,
+                 q_space=8, n_time=16, device="cuda", mesh=None):
+        self.mesh = mesh if mesh is not None else capi.Mesh(nodes, tris)
+        self.times = np.ascontiguousarray(times, dtype=np.float64)
+        n = len(self.times) - 1
+        self.params = capi.stb_default_params(alpha, float(self.times[-1]), n, quad_regular,
+                                              quad_singular)
+        self.sources = sources
+        self.nrhs, self.n_src = sources.shape[0], sources.shape[1]
+        self.q_space, self.n_time = q_space, n_time
+        E, dev = self.mesh.n_tris, torch.device(device)
+        self.E, self.n_steps, self.device = E, n, dev
+        nblk = n * (n + 1) // 2
+        self.V = torch.empty((nblk, E, E), dtype=torch.float64, device=dev)
+        self.K = torch.empty((nblk, E, E), dtype=torch.float64, device=dev)
+        vec = (self.nrhs, n, E)
+        self.g = torch.empty(vec, dtype=torch.float64, device=dev)
+        self.f = torch.empty(vec, dtype=torch.float64, device=dev)
+        self.w = torch.empty(vec, dtype=torch.float64, device=dev)
+        self.err = torch.zeros(2, dtype=torch.float64, device=dev)
+        m, p = self.mesh, self.params
+        self.ws_assemble = _ws(capi.stb_assemble_nu_workspace_size(m, p, self.times), dev)
+        self.ws_data = _ws(capi.stb_project_nu_workspace_size(m, p, self.nrhs, self.n_src, q_space,
+                                                              n_time), dev)
+        self.ws_rhs = _ws(capi.stb_dirichlet_rhs_nu_workspace_size(m, p), dev)
+        self.ws_solve = _ws(capi.stb_solve_nu_workspace_size(E, n, self.nrhs), dev)
+
+    def run(self, stream=None):
+        m, p, t = self.mesh, self.params, self.times
+        capi.stb_assemble_nu(m, p, t, self.V, self.K, self.ws_assemble, stream)
+        capi.stb_project_dirichlet_nu(m, p, t, self.sources, self.g, self.ws_data, self.q_space,
+                                      self.n_time, stream)
+        capi.stb_dirichlet_rhs_nu(m, p, t, self.K, self.g, self.nrhs, self.f, self.ws_rhs, stream)
+        capi.stb_solve_nu(self.V, self.E, self.n_steps, self.nrhs, self.f, self.w, self.ws_solve,
+                          stream)
+        capi.stb_neumann_error_nu(m, p, t, self.sources, self.w, self.err, self.ws_data,
+                                  self.q_space, self.n_time, stream)
+        return self.err
+
+    def relative_error(self):
+        e = self.err.cpu()
+        return math.sqrt(float(e[0]) / float(e[1]))
 
 
 class BatchPipeline:
