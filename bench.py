@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-potentials", action="store_true",
                     help="skip the potential evaluation report (outside the timed region)")
+    ap.add_argument("--no-nonuniform", action="store_true",
+                    help="skip the non-uniform time grid report (outside the timed region)")
     ap.add_argument("--no-neumann", action="store_true",
                     help="skip the Neumann problem report (outside the timed region)")
     ap.add_argument("--no-p1", action="store_true",
@@ -321,6 +323,37 @@ def _roofline(name, trace_entry, ms_step, n_reg_pairs, q, n_steps):
     else:
         roof.update({"bound": None, "achieved": None, "peak": None, "frac": None})
     return roof
+
+
+def nonuniform_report(capi, pipeline, torch, stream, a_, b_):
+    """FP64 Dirichlet problem on a geometric time grid (ratio 1.2, 16 steps,
+    T = 1) and on the uniform grid of the same step count: assembly and
+    solve times, relative L2 errors of w_h (source (1.5,1.5,1.5), t0 = 0)."""
+    nodes, tris = workloads.cube_mesh(8)
+    src = workloads.point_source((1.5, 1.5, 1.5), t0=0.0)
+    n, ratio = 16, 1.2
+    steps = ratio ** np.arange(n)
+    times = np.concatenate([[0.0], np.cumsum(steps / steps.sum())])
+    times[-1] = 1.0
+    out = {"workload": "cube, 768 triangles, 16 steps, T = 1, alpha 1",
+           "grid": "geometric, ratio %.1f" % ratio}
+    for label, t in (("geometric", times), ("uniform", np.arange(n + 1) / n)):
+        pr = pipeline.NonUniformDirichletProblem(nodes, tris, 1.0, t, src)
+        pr.run(stream)
+        torch.cuda.synchronize()
+        a_.record(stream)
+        capi.stb_assemble_nu(pr.mesh, pr.params, pr.times, pr.V, pr.K, pr.ws_assemble, stream)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        asm_ms = a_.elapsed_time(b_)
+        a_.record(stream)
+        capi.stb_solve_nu(pr.V, pr.E, pr.n_steps, pr.nrhs, pr.f, pr.w, pr.ws_solve, stream)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        out[label] = {"assembly_ms": asm_ms, "solve_ms": a_.elapsed_time(b_),
+                      "rel_l2_error_w": pr.relative_error()}
+        del pr
+    return out
 
 
 def potentials_report(capi, stream, a_, b_):
@@ -593,6 +626,13 @@ def run_gpu(args):
         del pn
         torch.cuda.empty_cache()
 
+    # a non-uniform (geometric) time grid against the uniform one, FP64, on a
+    # cube of 768 triangles with 16 steps: times, the number of distinct time
+    # differences and the errors
+    nonuni = None
+    if not args.no_nonuniform:
+        nonuni = nonuniform_report(capi, pipeline, torch, stream, a_, b_)
+
     # the representation formula's potentials on the workload of the paper's
     # potential benchmark (Table reprsc: cube (-1,1)^3, 3072 triangles, 32
     # steps, 33 x 33 points x 32 step midpoints = 34848 points), seeded
@@ -637,7 +677,7 @@ def run_gpu(args):
                              % (2 * (4 if mixed else 8) * n * E * E * len(alphas) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "mixed_vs_fp64": cmp, "matrix_free_rhs": mfree, "p1_data": p1, "neumann": neu,
-            "potentials": pots,
+            "potentials": pots, "nonuniform": nonuni,
             "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
             "rel_l2_error_w": rel_err, "solve": solve_info, "gpu_launches": launches,
             "kernels_ms": {k: v[1] for k, v in trace.items()}, "roofline": roof,
