@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-potentials", action="store_true",
                     help="skip the potential evaluation report (outside the timed region)")
+    ap.add_argument("--serial", action="store_true",
+                    help="run the problems of a step one after the other on one stream")
     ap.add_argument("--no-nonuniform", action="store_true",
                     help="skip the non-uniform time grid report (outside the timed region)")
     ap.add_argument("--no-neumann", action="store_true",
@@ -428,10 +430,48 @@ def run_gpu(args):
     probs = [pipeline.DirichletProblem(nodes, tris, a, wl["T"], n, src, mesh=mesh, precision=prec,
                                        storage=storage) for a in alphas]
     stream = torch.cuda.current_stream()
+    # one stream per problem: the problems are independent, so the latency-
+    # bound phases of one (the march, the factorisation) overlap the compute-
+    # bound assembly of another (set up after the synchronous warm-up)
+    streams = [stream] * len(probs)
+
+    trace_assembly = [False]  # trace the first problem's assembly kernels only
+
+    def run_problem(i, p, s, after=None):
+        if after is not None:  # the previous problem's assembly
+            s.wait_event(after)
+        if i == 0 and trace_assembly[0]:
+            capi.stb_trace_enable(True)
+            p.assemble(s)
+            capi.stb_trace_enable(False)
+        else:
+            p.assemble(s)
+        done = torch.cuda.Event()
+        done.record(s)
+        p.project(s)
+        p.rhs(s)
+        p.solve(s)
+        p.error(s)
+        return done
 
     def step():
-        for p in probs:
-            p.run(stream)
+        if streams[0] is stream:
+            for i, p in enumerate(probs):
+                run_problem(i, p, stream)
+            return
+        # the assemblies (compute-bound, each filling the GPU) run one after
+        # the other; each problem's data, right-hand side, solve and error
+        # (latency-bound phases) overlap the next problem's assembly
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        prev = None
+        for i, (p, s) in enumerate(zip(probs, streams)):
+            s.wait_event(ev)
+            prev = run_problem(i, p, s, prev)
+        for s in streams:
+            e = torch.cuda.Event()
+            e.record(s)
+            stream.wait_event(e)
 
     def barrier():
         if world > 1:
@@ -441,7 +481,21 @@ def run_gpu(args):
     for _ in range(args.warmup):
         step()
     barrier()
-    capi.stb_trace_enable(True)
+    concurrent = not args.serial and len(probs) > 1
+    if concurrent and args.warmup == 0:  # a synchronous pass gives the refinement counts
+        step()
+        barrier()
+    if concurrent:  # refinement counts of the synchronous warm-up solves
+        for p in probs:
+            p.set_async(p.solve_status()[0])
+        streams[:] = [torch.cuda.Stream() for _ in probs]
+    # the timed steps trace (CUDA events around each launch) the assembly of
+    # the first problem only: the dominant kernel's live launch times at
+    # negligible cost (tracing every launch slows the host-bound march)
+    trace_assembly[0] = True
+    step()
+    barrier()
+    capi.stb_trace_reset()
     capi.stb_trace_reset()
     launches0 = capi.stb_launch_count()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -459,9 +513,14 @@ def run_gpu(args):
     entries = 2.0 * n * E * E * len(alphas)
     value = whole_job_rate(entries, args.steps, ms, world)
     rel_err = [p.relative_error() for p in probs]
+    solve_status = [p.solve_status() for p in probs]
+    if any(st != 0 for _, _, st in solve_status):
+        raise RuntimeError("a solve of the timed steps did not converge: %s" % solve_status)
     n_reg_pairs = E * E - 2 * mesh.n_touching + E  # ordered separated pairs
-    name = max(trace.items(), key=lambda kv: kv[1][1])[0]
-    roof = _roofline(name, trace[name], ms / 1.0, n_reg_pairs, 3, n)
+    name = "k_regular_mixed" if mixed else "k_regular_f64"
+    # share of the step: the traced (first) problem's launches stand for all
+    roof = _roofline(name, trace[name], ms / len(probs), n_reg_pairs, 3, n)
+    roof["traced_launches"] = "the first problem's assembly, every timed step"
 
     # block-Toeplitz matvec on the assembled V of the first problem, in each
     # arithmetic the stored blocks allow; errors relative to the FP64 product
@@ -508,6 +567,8 @@ def run_gpu(args):
     # stage times of one problem (CUDA events, outside the timed region) and
     # the refinement report of its solve
     stage_ms = {}
+    capi.stb_trace_reset()
+    capi.stb_trace_enable(True)
     for label, fn in (("assemble", p0.assemble), ("project", p0.project), ("rhs", p0.rhs),
                       ("solve", p0.solve), ("error", p0.error)):
         a_.record(stream)
@@ -515,9 +576,11 @@ def run_gpu(args):
         b_.record(stream)
         torch.cuda.synchronize()
         stage_ms[label] = a_.elapsed_time(b_)
+    capi.stb_trace_enable(False)
+    one = capi.stb_trace_read()
     refinements, rel_residual = capi.stb_solve_report(p0.ws_solve)
     solve_info = {"stage_ms": stage_ms, "refinements": refinements, "rel_residual": rel_residual,
-                  "alpha": alphas[0]}
+                  "alpha": alphas[0], "kernels_ms_one_problem": {k: v[1] for k, v in one.items()}}
 
     # the other precision: FP64 assembly of one problem for "mixed vs FP64"
     cmp = None
@@ -650,15 +713,28 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            for a in alphas:
+            prs, outs = [], []
+            for i, a in enumerate(alphas):
                 pr = pipeline.DirichletProblem(nodes, tris, a, wl["T"], n, src, precision=prec,
                                                storage=storage)
-                pr.run(stream)
-                w_host = pr.w.cpu()
-                err_host = pr.err.cpu()
+                s_i = streams[i]
+                if concurrent:  # the refinement count of the timed problems
+                    pr.set_async(probs[i].solve_status()[0])
+                    s_i.wait_stream(stream)
+                pr.run(s_i)
+                with torch.cuda.stream(s_i):
+                    w_host = torch.empty(pr.w.shape, dtype=pr.w.dtype, pin_memory=True)
+                    err_host = torch.empty(pr.err.shape, dtype=pr.err.dtype, pin_memory=True)
+                    w_host.copy_(pr.w, non_blocking=True)
+                    err_host.copy_(pr.err, non_blocking=True)
+                prs.append(pr)
+                outs.append((w_host, err_host))
                 h2d += nodes.nbytes + tris.nbytes + src.nbytes
                 d2h += w_host.numel() * 8 + err_host.numel() * 8
-                del pr
+            torch.cuda.synchronize()
+            if concurrent:
+                assert all(pr.solve_status()[2] == 0 for pr in prs), "an asynchronous solve failed"
+            del prs, outs
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         e2e = {"value": world * entries * n_e2e / e2e_s, "unit": UNIT,
@@ -679,8 +755,11 @@ def run_gpu(args):
             "mixed_vs_fp64": cmp, "matrix_free_rhs": mfree, "p1_data": p1, "neumann": neu,
             "potentials": pots, "nonuniform": nonuni,
             "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
-            "rel_l2_error_w": rel_err, "solve": solve_info, "gpu_launches": launches,
-            "kernels_ms": {k: v[1] for k, v in trace.items()}, "roofline": roof,
+            "rel_l2_error_w": rel_err, "solve": solve_info,
+            "timed_solves": [{"refinements": r, "rel_residual": res} for r, res, _ in solve_status],
+            "concurrent_problems": concurrent, "gpu_launches": launches,
+            "kernels_ms_first_problem_assembly": {k: v[1] for k, v in trace.items()},
+            "roofline": roof,
             "measured_pipe_peaks": pipe_peaks, "e2e": e2e}
     if rank == 0:
         line["clocks"] = clk.summary()

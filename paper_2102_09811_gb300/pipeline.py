@@ -94,6 +94,27 @@ class DirichletProblem:
         capi.stb_neumann_error(self.mesh, self.params, self.sources, self.w, self.err, self.ws_error,
                                self.q_space, self.n_time, stream)
 
+    def set_async(self, refinements):
+        """From now on every call only enqueues device work: the solve runs
+        `refinements` refinement steps (mixed precision; the count of an
+        earlier synchronous solve) and leaves its convergence in the solve
+        workspace's status word (STB_FLAG_NO_SYNC), the sources sit in
+        page-locked memory so that their upload does not wait for the stream.
+        Several problems can then run concurrently on their own streams."""
+        self.params.flags = capi.STB_FLAG_NO_SYNC | capi.STB_FLAG_REFINE(max(1, refinements))
+        if not hasattr(self.sources, "data_ptr"):
+            self.sources = torch.tensor(self.sources, dtype=torch.float64).pin_memory()
+
+    def solve_status(self):
+        """(refinements, relative residual, status code) of the last solve."""
+        r, res = capi.stb_solve_report(self.ws_solve)
+        try:
+            capi.stb_workspace_status(self.ws_solve)
+            st = 0
+        except capi.StbError as e:
+            st = e.code
+        return r, res, st
+
     def run(self, stream=None):
         """Every step of the path; returns the device tensor [err2, ref2]."""
         self.assemble(stream)
