@@ -51,6 +51,55 @@ MUFU_PEAK_TEX2 = 152 * 32 * 2.07e9 / 1e12
 # ncu, k_regular_mixed on the 16-step cube (3072 triangles, alpha 0.5): DRAM
 # read 15.19 MB + write 1144.27 MB for 2 x 16 x 3072^2 block entries.
 REGULAR_MIXED_DRAM_BYTES_PER_ENTRY = (15.18848e6 + 1144.265e6) / (2 * 16 * 3072.0 ** 2)
+# FP64 pipe operations (DFMA, DMUL and DADD, each one slot of the pipe; ncu
+# SASS op counters) per evaluation of both potentials -- one point, trial
+# triangle, rule point and level -- in k_potential_levels: 1.5509e11
+# operations for 1089 x 3072 x 16 x 32 evaluations (profiles/).
+POT_FP64_OPS_PER_EVAL = 90.545
+# the same for k_regular_nu_f64 (separated pairs, non-uniform grid), per
+# quadrature point and positive time difference, the level-0 limits and the
+# block updates included: 4.8016e11 operations for 579,896 ordered separated
+# pairs x 81 points x 136 differences (768 triangles, geometric 16-step grid;
+# profiles/).
+NU_FP64_OPS_PER_EVAL = 75.17
+
+
+def _alu_roofline(kernel, ms, units, unit_name, rate_unit, peak, peak_source, scale=1.0):
+    """Roofline record of one launch of an ALU-bound kernel: `units` pipe
+    operations (x scale per unit) in `ms` against `peak` (rate_unit)."""
+    if not ms:
+        return None
+    ach = units * scale / (ms / 1e3) / (1e12 if rate_unit.startswith("T") else 1.0)
+    return {"kernel": kernel, "launch_ms": ms, "bound": "alu", "unit": rate_unit,
+            "achieved": ach, "peak": peak, "frac": ach / peak if peak else None,
+            "peak_source": peak_source,
+            "units_per_launch": units, "unit_name": unit_name}
+
+
+def oracle_sample(fn, units, unit, sample):
+    """The oracle timed on one host thread for one bounded call fn() that
+    computes `units` results: rate in `unit`."""
+    t0 = time.perf_counter()
+    fn()
+    secs = time.perf_counter() - t0
+    return {"value": units / secs, "unit": unit, "cores": 1, "kind": "oracle",
+            "sample": "%s, %.2f s" % (sample, secs)}
+
+
+def nu_levels(times):
+    """Positive time differences of a grid that the non-uniform assembly
+    evaluates (four corners of every block; exact double equality)."""
+    t = [float(x) for x in times]
+    n = len(t) - 1
+    lv = set()
+    for k in range(n):
+        for i in range(k + 1):
+            if i == k:
+                lv.add(t[k + 1] - t[k])
+            else:
+                lv.update((t[k + 1] - t[i + 1], t[k] - t[i + 1], t[k + 1] - t[i], t[k] - t[i]))
+    lv.discard(0.0)
+    return len(lv)
 
 
 def mixed_nodes_per_point(n_steps):
@@ -327,40 +376,69 @@ def _roofline(name, trace_entry, ms_step, n_reg_pairs, q, n_steps):
     return roof
 
 
-def nonuniform_report(capi, pipeline, torch, stream, a_, b_):
+def nonuniform_report(capi, pipeline, torch, stream, a_, b_, cpu=True):
     """FP64 Dirichlet problem on a geometric time grid (ratio 1.2, 16 steps,
     T = 1) and on the uniform grid of the same step count: assembly and
-    solve times, relative L2 errors of w_h (source (1.5,1.5,1.5), t0 = 0)."""
+    solve times, relative L2 errors of w_h (source (1.5,1.5,1.5), t0 = 0);
+    the roofline of the separated-pair kernel on the geometric grid and the
+    oracle's rows of the same blocks."""
     nodes, tris = workloads.cube_mesh(8)
     src = workloads.point_source((1.5, 1.5, 1.5), t0=0.0)
     n, ratio = 16, 1.2
     steps = ratio ** np.arange(n)
     times = np.concatenate([[0.0], np.cumsum(steps / steps.sum())])
     times[-1] = 1.0
+    E = len(tris)
     out = {"workload": "cube, 768 triangles, 16 steps, T = 1, alpha 1",
            "grid": "geometric, ratio %.1f" % ratio}
     for label, t in (("geometric", times), ("uniform", np.arange(n + 1) / n)):
         pr = pipeline.NonUniformDirichletProblem(nodes, tris, 1.0, t, src)
         pr.run(stream)
         torch.cuda.synchronize()
+        capi.stb_trace_enable(True)
+        capi.stb_trace_reset()
         a_.record(stream)
         capi.stb_assemble_nu(pr.mesh, pr.params, pr.times, pr.V, pr.K, pr.ws_assemble, stream)
         b_.record(stream)
         torch.cuda.synchronize()
+        capi.stb_trace_enable(False)
+        tr = capi.stb_trace_read()
         asm_ms = a_.elapsed_time(b_)
         a_.record(stream)
         capi.stb_solve_nu(pr.V, pr.E, pr.n_steps, pr.nrhs, pr.f, pr.w, pr.ws_solve, stream)
         b_.record(stream)
         torch.cuda.synchronize()
+        n_blocks = n * (n + 1) // 2
         out[label] = {"assembly_ms": asm_ms, "solve_ms": a_.elapsed_time(b_),
-                      "rel_l2_error_w": pr.relative_error()}
+                      "rel_l2_error_w": pr.relative_error(), "distinct_levels": nu_levels(t),
+                      "entries_per_s": 2.0 * n_blocks * E * E / (asm_ms / 1e3),
+                      "kernels_ms": {k: v[1] for k, v in tr.items()}}
+        if label == "geometric":
+            n_reg = E * E - 2 * pr.mesh.n_touching + E
+            evals = float(n_reg) * 81.0 * nu_levels(t)
+            reg_ms = tr.get("k_regular_nu_f64", (1, 0.0))[1]
+            if NU_FP64_OPS_PER_EVAL:
+                out["roofline"] = _alu_roofline(
+                    "k_regular_nu_f64", reg_ms, evals,
+                    "separated-pair point-level evaluations x FP64 operations per evaluation (ncu)",
+                    "FP64 op/s", FP64_PEAK_TFLOPS * 1e12 / 2, "FP64 pipe, " + PEAK_SOURCE["fp64"],
+                    scale=NU_FP64_OPS_PER_EVAL)
+            else:
+                out["point_level_evals_per_s"] = evals / (reg_ms / 1e3) if reg_ms else None
+            if cpu:
+                import oracle
+                rows = np.array([0, E // 2])
+                out["cpu_baseline"] = oracle_sample(
+                    lambda: oracle.assemble_rows_nu(nodes, tris, 1.0, t, rows), 2.0 * n_blocks * E * 2,
+                    "entries/s", "2 whole rows (all 136 blocks of V and K) of the geometric grid")
         del pr
     return out
 
 
-def potentials_report(capi, stream, a_, b_):
+def potentials_report(capi, stream, a_, b_, cpu=True):
     """Times of the single- plus double-layer potential at the 34848 points
-    of the potential benchmark: per-point kernel and the level-block form."""
+    of the potential benchmark: per-point kernel and the level-block form;
+    the roofline of the level kernel and the oracle at the latest points."""
     import torch
     nodes, tris = workloads.cube_mesh(16, lo=-1.0, hi=1.0)
     T, n, alpha = 1.0, 32, 0.5
@@ -369,8 +447,10 @@ def potentials_report(capi, stream, a_, b_):
     pts = workloads.reprsc_points(n, T)
     P = len(pts) // n
     rng = np.random.default_rng(1089)
-    w = torch.tensor(rng.normal(size=(1, n, len(tris))), device="cuda")
-    u1 = torch.tensor(rng.normal(size=(1, n, len(nodes))), device="cuda")
+    w_h = rng.normal(size=(1, n, len(tris)))
+    u1_h = rng.normal(size=(1, n, len(nodes)))
+    w = torch.tensor(w_h, device="cuda")
+    u1 = torch.tensor(u1_h, device="cuda")
     out = {"workload": "cube (-1,1)^3, 3072 triangles, 32 steps, 1089 points x 32 step midpoints",
            "q_space": 4}
     pts_d = torch.tensor(pts, device="cuda")
@@ -392,19 +472,37 @@ def potentials_report(capi, stream, a_, b_):
                      dtype=torch.uint8, device="cuda")
     eps = 0.5 * T / n
     capi.stb_potentials_grid(mesh, prm, p3, eps, w, u1, 1, s2, d2, ws)
+    torch.cuda.synchronize()
+    capi.stb_trace_enable(True)
+    capi.stb_trace_reset()
     a_.record(stream)
     capi.stb_potentials_grid(mesh, prm, p3, eps, w, u1, 1, s2, d2, ws)
     b_.record(stream)
     torch.cuda.synchronize()
+    capi.stb_trace_enable(False)
+    tr = capi.stb_trace_read()
     out["level_blocks_ms"] = a_.elapsed_time(b_)
+    out["kernels_ms"] = {k: v[1] for k, v in tr.items()}
     out["max_rel_diff_between_forms"] = float(max(
         (s2.reshape(1, -1) - s1).abs().max() / s1.abs().max(),
         (d2.reshape(1, -1) - d1).abs().max() / d1.abs().max()))
     evals = float(P) * len(tris) * 16 * n
     out["level_evaluations_per_s"] = evals / (out["level_blocks_ms"] / 1e3)
+    out["roofline"] = _alu_roofline(
+        "k_potential_levels", tr.get("k_potential_levels", (1, 0.0))[1], evals,
+        "point-triangle-rule point-level evaluations of both potentials x FP64 operations per "
+        "evaluation (ncu)", "FP64 op/s", FP64_PEAK_TFLOPS * 1e12 / 2,
+        "FP64 pipe, " + PEAK_SOURCE["fp64"], scale=POT_FP64_OPS_PER_EVAL)
     out["paper_36_threads_s"] = {"single_layer": 0.31, "double_layer": 0.82,
                                  "note": "Table reprsc, 2 x 18-core Xeon Gold 6240; context"}
     del ws
+    if cpu:  # the oracle at the 4 latest points (all 32 levels each)
+        import oracle
+        sel = pts[-4:]
+        out["cpu_baseline"] = oracle_sample(
+            lambda: oracle.potentials(nodes, tris, alpha, T, n, sel, w=w_h, u1=u1_h, q=4),
+            4.0 * len(tris) * 16 * n, "evaluations/s",
+            "both potentials at the 4 points of the last step midpoint (32 levels each)")
     return out
 
 
@@ -656,12 +754,25 @@ def run_gpu(args):
               "k_singular_k1_ms": tr1.get("k_singular_k1_" + kind, (1, 0.0))[1],
               "k1_entries": float(n) * E * mesh.n_nodes,
               "kernels_ms": {k: v[1] for k, v in tr1.items()}}
-        if kind == "mixed" and k1_ms:  # one exp2 per node and point, as for V, K
-            ex2 = float(n_reg_pairs) * 81.0 * mixed_nodes_per_point(n)
-            p1["k_regular_k1_tex2_per_s"] = ex2 / (k1_ms / 1e3) / 1e12
-            p1["k_regular_k1_frac_of_mufu_peak"] = p1["k_regular_k1_tex2_per_s"] / MUFU_PEAK_TEX2
+        k1_all = k1_ms + p1["k_singular_k1_ms"]
+        p1["k1_entries_per_s"] = p1["k1_entries"] / (k1_all / 1e3) if k1_all else None
+        if kind == "mixed":  # one exp2 per node and point, as for V, K
+            p1["roofline"] = _alu_roofline(
+                "k_regular_k1_mixed", k1_ms, float(n_reg_pairs) * 81.0 * mixed_nodes_per_point(n),
+                "MUFU.EX2 time-node evaluations", "Tex2/s", MUFU_PEAK_TEX2,
+                "MUFU ex2 pipe, " + PEAK_SOURCE["mufu"])
         elif k1_ms:
-            p1["k1_point_level_evals_per_s"] = float(n_reg_pairs) * 81.0 * n / (k1_ms / 1e3)
+            p1["roofline"] = _alu_roofline(
+                "k_regular_k1_f64", k1_ms, float(n_reg_pairs) * 81.0 * n,
+                "separated-pair point-level evaluations", "point-level evaluations/s", None, None)
+        if not args.no_cpu_baseline:  # the oracle's K1 on whole test-triangle rows
+            import oracle
+            rows = np.array([0, E // 2])
+            p1["cpu_baseline"] = oracle_sample(
+                lambda: oracle.assemble_k1_rows(nodes, tris, alphas[0], wl["T"], n, rows),
+                2.0 * n * mesh.n_nodes, "K1 entries/s",
+                "2 whole rows of K1 (all %d blocks x %d nodes) of %s" % (n, mesh.n_nodes,
+                                                                      args.workload))
         del pp
 
     # the Neumann problem (Sec. 3.3) on the same mesh and steps, first alpha:
@@ -686,6 +797,29 @@ def run_gpu(args):
         trn = capi.stb_trace_read()
         neu = {"alpha": alphas[0], "stage_ms": nms, "rel_l2_error_u": pn.relative_error(),
                "kernels_ms": {k: v[1] for k, v in trn.items()}}
+        d2k = "mixed" if "k_regular_d2_mixed" in trn else "f64"
+        d2_ms = trn.get("k_regular_d2_" + d2k, (1, 0.0))[1]
+        d2_all = d2_ms + trn.get("k_singular_d2_" + d2k, (1, 0.0))[1]
+        neu["d2_pair_blocks_per_s"] = float(E) * E * n / (d2_all / 1e3) if d2_all else None
+        if d2k == "mixed":  # one exp2 per node and point, as for V, K
+            neu["roofline"] = _alu_roofline(
+                "k_regular_d2_mixed", d2_ms, float(n_reg_pairs) * 81.0 * mixed_nodes_per_point(n),
+                "MUFU.EX2 time-node evaluations", "Tex2/s", MUFU_PEAK_TEX2,
+                "MUFU ex2 pipe, " + PEAK_SOURCE["mufu"])
+        # D^1: one FP64 FMA per star pair and block, (sum of star sizes)^2 =
+        # (3 E)^2 per block
+        neu["roofline_d1"] = _alu_roofline(
+            "k_hypersingular_d1", trn.get("k_hypersingular_d1", (1, 0.0))[1],
+            9.0 * E * E * n, "FP64 FMA (one per star pair and block)", "FMA/s",
+            FP64_PEAK_TFLOPS * 1e12 / 2, "FP64 pipe, " + PEAK_SOURCE["fp64"])
+        if not args.no_cpu_baseline:  # the oracle's D^2 on whole test-triangle rows
+            import oracle
+            rows = np.array([0, E // 3, E // 2])
+            neu["cpu_baseline"] = oracle_sample(
+                lambda: oracle.assemble_d2(nodes, tris, alphas[0], wl["T"], n, test_tris=rows),
+                3.0 * E * n, "triangle-pair blocks/s",
+                "D^2 of 3 test triangles (all %d trial triangles and %d blocks) of %s"
+                % (E, n, args.workload))
         del pn
         torch.cuda.empty_cache()
 
@@ -694,7 +828,8 @@ def run_gpu(args):
     # differences and the errors
     nonuni = None
     if not args.no_nonuniform:
-        nonuni = nonuniform_report(capi, pipeline, torch, stream, a_, b_)
+        nonuni = nonuniform_report(capi, pipeline, torch, stream, a_, b_,
+                                   cpu=not args.no_cpu_baseline)
 
     # the representation formula's potentials on the workload of the paper's
     # potential benchmark (Table reprsc: cube (-1,1)^3, 3072 triangles, 32
@@ -702,7 +837,7 @@ def run_gpu(args):
     # densities; both kernels, FP64
     pots = None
     if not args.no_potentials:
-        pots = potentials_report(capi, stream, a_, b_)
+        pots = potentials_report(capi, stream, a_, b_, cpu=not args.no_cpu_baseline)
 
     # end to end through the public API from host buffers (mesh, sources in;
     # solution and error norms out)

@@ -821,16 +821,20 @@ k_singular_k1_f64(const double *__restrict__ geo, const int32_t *__restrict__ tr
 // surface curls of the hat functions, constant on each triangle, so entry
 // (i, j) sums alpha^2 (c_{n,i} . c_{m,j}) V^d[n][m] over the triangles n
 // around node i and m around node j (node stars, CSR).  One thread per
-// (block, i, j); FP64 sums; the block is overwritten.
+// (i, j) and chunk of D1_CH blocks: the weight c_{n,i} . c_{m,j} of a star
+// pair is formed once and applied to the D1_CH blocks (independent gathers
+// from the same row of each block); FP64 sums; the blocks are overwritten.
+constexpr int D1_CH = 16;
+
 template <class T>
 __global__ void __launch_bounds__(128)
-k_hypersingular_d1(const T *__restrict__ V, int E, int N, const int32_t *__restrict__ star_off,
-                   const int32_t *__restrict__ star_tri, const double *__restrict__ star_curl,
-                   double alpha2, T *__restrict__ D) {
+k_hypersingular_d1(const T *__restrict__ V, int E, int N, int n_steps,
+                   const int32_t *__restrict__ star_off, const int32_t *__restrict__ star_tri,
+                   const double *__restrict__ star_curl, double alpha2, T *__restrict__ D) {
     constexpr int MAX_STAR = 32;
     __shared__ int s_tri[MAX_STAR];
     __shared__ double s_c[MAX_STAR][3];
-    const int i = blockIdx.y, d = blockIdx.z;
+    const int i = blockIdx.y, d0 = blockIdx.z * D1_CH;
     const int i0 = star_off[i], ni = min(star_off[i + 1] - i0, MAX_STAR);
     for (int t = threadIdx.x; t < ni; t += blockDim.x) {
         s_tri[t] = star_tri[i0 + t];
@@ -839,19 +843,34 @@ k_hypersingular_d1(const T *__restrict__ V, int E, int N, const int32_t *__restr
     __syncthreads();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
-    const T *Vd = V + (size_t)d * E * E;
+    const size_t EE = (size_t)E * E;
+    const int nd = min(D1_CH, n_steps - d0);
+    const T *V0 = V + (size_t)d0 * EE;
     const int j0 = star_off[j], j1 = star_off[j + 1];
-    double acc = 0.0;
+    double acc[D1_CH];
+#pragma unroll
+    for (int u = 0; u < D1_CH; ++u) acc[u] = 0.0;
     for (int b = j0; b < j1; ++b) {
         const int m = star_tri[b];
         const double c0 = star_curl[3 * (size_t)b], c1 = star_curl[3 * (size_t)b + 1],
                      c2 = star_curl[3 * (size_t)b + 2];
         for (int a = 0; a < ni; ++a) {
             const double cc = s_c[a][0] * c0 + s_c[a][1] * c1 + s_c[a][2] * c2;
-            acc = fma(cc, (double)Vd[(size_t)s_tri[a] * E + m], acc);
+            const T *p = V0 + (size_t)s_tri[a] * E + m;
+            if (nd == D1_CH) {
+#pragma unroll
+                for (int u = 0; u < D1_CH; ++u) acc[u] = fma(cc, (double)p[u * EE], acc[u]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < D1_CH; ++u)
+                    if (u < nd) acc[u] = fma(cc, (double)p[u * EE], acc[u]);
+            }
         }
     }
-    D[((size_t)d * N + i) * N + j] = (T)(alpha2 * acc);
+    T *out = D + ((size_t)d0 * N + i) * N + j;
+#pragma unroll
+    for (int u = 0; u < D1_CH; ++u)
+        if (u < nd) out[u * (size_t)N * N] = (T)(alpha2 * acc[u]);
 }
 
 // D^{2,d}[i][j] = int int n_x . n_y phi_i(x) phi_j(y) D^{2,d}(x - y) with
@@ -1387,10 +1406,10 @@ static stb_status run_hypersingular(const Mesh &m, const stb_params &p, const Ou
                                     cudaStream_t s) {
     const int E = (int)m.n_tris, N = (int)m.n_nodes;
     const double h = p.T / p.n_steps;
-    dim3 g1((N + 127) / 128, N, p.n_steps);
+    dim3 g1((N + 127) / 128, N, (p.n_steps + D1_CH - 1) / D1_CH);
     count_launch(s);
-    k_hypersingular_d1<OutT><<<g1, 128, 0, s>>>(V, E, N, star_off, star_tri, star_curl,
-                                               p.alpha * p.alpha, D);
+    k_hypersingular_d1<OutT><<<g1, 128, 0, s>>>(V, E, N, p.n_steps, star_off, star_tri,
+                                               star_curl, p.alpha * p.alpha, D);
     stb_status st = check_launch("k_hypersingular_d1");
     if (st) return st;
     if constexpr (std::is_same<OutT, float>::value) {
