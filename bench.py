@@ -431,6 +431,30 @@ def nonuniform_report(capi, pipeline, torch, stream, a_, b_, cpu=True):
                 out["cpu_baseline"] = oracle_sample(
                     lambda: oracle.assemble_rows_nu(nodes, tris, 1.0, t, rows), 2.0 * n_blocks * E * 2,
                     "entries/s", "2 whole rows (all 136 blocks of V and K) of the geometric grid")
+            # the same grid with the separated pairs in FP32: times, block
+            # errors against the FP64 blocks above, solution and error
+            pm = pipeline.NonUniformDirichletProblem(nodes, tris, 1.0, t, src, precision="mixed")
+            pm.run(stream)
+            torch.cuda.synchronize()
+            capi.stb_trace_enable(True)
+            capi.stb_trace_reset()
+            a_.record(stream)
+            capi.stb_assemble_nu(pm.mesh, pm.params, pm.times, pm.V, pm.K, pm.ws_assemble, stream)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            capi.stb_trace_enable(False)
+            trm = capi.stb_trace_read()
+            m_ms = a_.elapsed_time(b_)
+            ev = ((pm.V - pr.V).flatten(1).norm(dim=1) / pr.V.flatten(1).norm(dim=1)).max()
+            ek = ((pm.K - pr.K).flatten(1).norm(dim=1) / pr.K.flatten(1).norm(dim=1)).max()
+            out["geometric_mixed"] = {
+                "assembly_ms": m_ms, "entries_per_s": 2.0 * n_blocks * E * E / (m_ms / 1e3),
+                "speedup_vs_fp64": asm_ms / m_ms,
+                "max_block_rel_err_vs_fp64": {"V": float(ev), "K": float(ek)},
+                "rel_l2_error_w": pm.relative_error(),
+                "rel_diff_w_vs_fp64": float((pm.w - pr.w).norm() / pr.w.norm()),
+                "kernels_ms": {k: v[1] for k, v in trm.items()}}
+            del pm
         del pr
     return out
 

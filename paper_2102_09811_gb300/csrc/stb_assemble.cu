@@ -1808,6 +1808,32 @@ size_t nu_table_bytes(const NuHost &H) {
     return align256(sizeof(double) * H.levels.size()) + align256(sizeof(int32_t) * H.off.size()) +
            align256(sizeof(int32_t) * H.blk.size()) + align256(sizeof(double) * H.coef.size());
 }
+
+// Mixed path: FP32 regular rule, closed-form records, Gauss nodes, targets.
+struct NuMixHost {
+    std::vector<float> rule, ss, cf, nodes;  // rule and ss: FP32 regular and difference-form rules
+    std::vector<int32_t> targets;
+};
+
+NuMixHost nu_mixed_host(const stb_params &p, const double *t) {
+    NuMixHost M;
+    std::vector<float> unodes;
+    stb_params pm = p;
+    pm.precision = STB_PREC_MIXED;
+    mixed_tables(pm, M.rule, M.ss, unodes);
+    nu_mixed_tables(p, t, M.cf, M.nodes, M.targets);
+    return M;
+}
+
+size_t nu_mixed_bytes(const NuMixHost &M) {
+    return align256(sizeof(float) * M.rule.size()) + align256(sizeof(float) * M.ss.size()) +
+           align256(sizeof(float) * M.cf.size()) + align256(sizeof(float) * M.nodes.size()) +
+           align256(sizeof(int32_t) * M.targets.size());
+}
+
+size_t nu_mixed_bytes(const stb_params &p, const double *t) {
+    return nu_mixed_bytes(nu_mixed_host(p, t));
+}
 }  // namespace
 
 extern "C" stb_status stb_assemble_nu_workspace_size(const stb_mesh *mesh, const stb_params *params,
@@ -1818,9 +1844,12 @@ extern "C" stb_status stb_assemble_nu_workspace_size(const stb_mesh *mesh, const
     stb_params p = *params;
     p.T = times[p.n_steps];
     if ((st = check_assembly_params(&p))) return st;
-    if (p.precision != STB_PREC_FP64 || p.storage != STB_STORE_F64)
-        return fail(STB_ERR_INVALID_ARG, "non-uniform grids need STB_PREC_FP64 and STB_STORE_F64");
+    if (p.storage != STB_STORE_F64)
+        return fail(STB_ERR_INVALID_ARG, "non-uniform grids store FP64 blocks (STB_STORE_F64)");
+    const bool mixed = p.precision == STB_PREC_MIXED;
+    p.precision = STB_PREC_FP64;  // the touching pairs take the FP64 path
     *bytes = align256(assembly_layout(mesh->m, p, nullptr, 0).bytes) + nu_table_bytes(nu_lists(p, times));
+    if (mixed) *bytes += nu_mixed_bytes(p, times);
     return STB_OK;
 }
 
@@ -1836,6 +1865,8 @@ extern "C" stb_status stb_assemble_nu(const stb_mesh *mesh, const stb_params *pa
     if (m.n_tris > 65535) return fail(STB_ERR_INVALID_ARG, "dense assembly supports E <= 65535");
     stb_params p = *params;
     p.T = times[p.n_steps];
+    const bool mixed = p.precision == STB_PREC_MIXED;
+    p.precision = STB_PREC_FP64;  // layout and tables of the FP64 kernels
     const NuHost H = nu_lists(p, times);
     AssemblyLayout L = assembly_layout(m, p, ws, ws_bytes);
     char *q = static_cast<char *>(ws) + align256(L.bytes);
@@ -1846,6 +1877,22 @@ extern "C" stb_status stb_assemble_nu(const stb_mesh *mesh, const stb_params *pa
     int32_t *d_blk = reinterpret_cast<int32_t *>(q);
     q += align256(sizeof(int32_t) * H.blk.size());
     double *d_coef = reinterpret_cast<double *>(q);
+    q += align256(sizeof(double) * H.coef.size());
+    NuMixHost M;
+    float *d_mrule = nullptr, *d_mss = nullptr, *d_cf = nullptr, *d_nodes = nullptr;
+    int32_t *d_targets = nullptr;
+    if (mixed) {
+        M = nu_mixed_host(p, times);
+        d_mrule = reinterpret_cast<float *>(q);
+        q += align256(sizeof(float) * M.rule.size());
+        d_mss = reinterpret_cast<float *>(q);
+        q += align256(sizeof(float) * M.ss.size());
+        d_cf = reinterpret_cast<float *>(q);
+        q += align256(sizeof(float) * M.cf.size());
+        d_nodes = reinterpret_cast<float *>(q);
+        q += align256(sizeof(float) * M.nodes.size());
+        d_targets = reinterpret_cast<int32_t *>(q);
+    }
     cudaStream_t s = (cudaStream_t)stream;
     STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
     if ((st = prepare_fp64(m, p, L, status_word(ws), s))) return st;
@@ -1863,12 +1910,33 @@ extern "C" stb_status stb_assemble_nu(const stb_mesh *mesh, const stb_params *pa
     STB_CUDA(cudaMemsetAsync(K, 0, sizeof(double) * nblk * E * E, s));
     NuLists lists{d_lv, d_off, d_blk, d_coef, H.n_levels};
     Globals g = make_globals(p);
-    dim3 grid((E + REG_THREADS - 1) / REG_THREADS, E);
-    count_launch(s);
-    k_regular_nu_f64<4><<<grid, REG_THREADS, 0, s>>>(L.geo, m.d_tris, E, L.rule,
-                                                     p.quad_regular * p.quad_regular, lists, g, V,
-                                                     K);
-    if ((st = check_launch("k_regular_nu_f64"))) return st;
+    if (mixed) {
+        auto up = [&](void *dst, const void *src, size_t bytes) {
+            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+        };
+        STB_CUDA(up(d_mrule, M.rule.data(), sizeof(float) * M.rule.size()));
+        STB_CUDA(up(d_mss, M.ss.data(), sizeof(float) * M.ss.size()));
+        STB_CUDA(up(d_cf, M.cf.data(), sizeof(float) * M.cf.size()));
+        STB_CUDA(up(d_nodes, M.nodes.data(), sizeof(float) * M.nodes.size()));
+        STB_CUDA(up(d_targets, M.targets.data(), sizeof(int32_t) * M.targets.size()));
+        // the host tables are pageable: the copies have been staged when the
+        // calls return, so M may go out of scope afterwards
+        if ((st = run_nu_regular_mixed(m, p, L.geo, d_mrule, d_cf,
+                                       (int)(M.cf.size() / NU_CF_FLOATS), d_nodes,
+                                       (int)(M.nodes.size() / 4), d_targets, V, K, s)))
+            return st;
+        const int ss_n[4] = {0, (int)L.ss_n[1], (int)L.ss_n[2], (int)L.ss_n[3]};
+        return run_nu_singular_mixed(m, p, L.geo, L.pairs, d_mss, ss_n, d_cf,
+                                     (int)(M.cf.size() / NU_CF_FLOATS), d_nodes,
+                                     (int)(M.nodes.size() / 4), d_targets, V, K, s);
+    } else {
+        dim3 grid((E + REG_THREADS - 1) / REG_THREADS, E);
+        count_launch(s);
+        k_regular_nu_f64<4><<<grid, REG_THREADS, 0, s>>>(L.geo, m.d_tris, E, L.rule,
+                                                         p.quad_regular * p.quad_regular, lists, g,
+                                                         V, K);
+        if ((st = check_launch("k_regular_nu_f64"))) return st;
+    }
     if (m.n_touch == 0) return STB_OK;
     SSTables tab{};
     const double *base = L.ss;

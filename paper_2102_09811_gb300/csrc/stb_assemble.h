@@ -78,6 +78,26 @@ stb_status run_assembly_k1_mixed(const Mesh &m, const stb_params &p, float *K1,
 stb_status run_assembly_mixed(const Mesh &m, const stb_params &p, void *V, void *K,
                               const AssemblyLayout &L, cudaStream_t s);
 
+// Non-uniform grid, mixed precision (stb_nonuniform_mixed.cu): host tables
+// of the closed-form records (NU_CF_FLOATS floats: target offset, target
+// count << 1 | small-x form allowed, 1/(2 sqrt(alpha delta_max)), the K
+// constant of zero differences; then per difference c, 1/c, pV, sigma),
+// the Gauss nodes (float4 b, cV, cK, tag) and the target blocks; and the
+// separated-pair launch (FP64 blocks, touching pairs left out).
+constexpr int NU_CF_FLOATS = 20;
+void nu_mixed_tables(const stb_params &p, const double *t, std::vector<float> &cf,
+                     std::vector<float> &nodes, std::vector<int32_t> &targets);
+stb_status run_nu_regular_mixed(const Mesh &m, const stb_params &p, const double *geo,
+                                const float *mrule, const float *d_cf, int n_cf,
+                                const float *d_nodes, int n_nodes, const int32_t *d_targets,
+                                double *V, double *K, cudaStream_t s);
+// touching pairs of the same path (FP32 difference-form rules mss, per class
+// ss_n[cls] points)
+stb_status run_nu_singular_mixed(const Mesh &m, const stb_params &p, const double *geo,
+                                 const TouchPair *pairs, const float *mss, const int (&ss_n)[4],
+                                 const float *d_cf, int n_cf, const float *d_nodes, int n_nodes,
+                                 const int32_t *d_targets, double *V, double *K, cudaStream_t s);
+
 // Batched mixed assembly (one persistent launch for the separated pairs of
 // all problems, one launch for their touching pairs).  upload_batch copies
 // the problems' descriptors for work items of `tile` columns (host memory,

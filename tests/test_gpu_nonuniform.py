@@ -27,10 +27,10 @@ def cuda_device():
     capi._library()
 
 
-def gpu_assemble_nu(nodes, tris, alpha, times):
+def gpu_assemble_nu(nodes, tris, alpha, times, precision=capi.STB_PREC_FP64):
     mesh = capi.Mesh(nodes, tris)
     n = len(times) - 1
-    p = capi.stb_default_params(alpha, float(times[-1]), n)
+    p = capi.stb_default_params(alpha, float(times[-1]), n, precision=precision)
     nblk, E = n * (n + 1) // 2, len(tris)
     V = torch.full((nblk, E, E), float("nan"), dtype=torch.float64, device="cuda")
     K = torch.full_like(V, float("nan"))
@@ -118,3 +118,60 @@ def test_nonuniform_pipeline_matches_oracle_pipeline():
     e2, r2 = oracle.neumann_error_nu(nodes, tris, alpha, GRADED, src, wo)
     assert abs(prob.relative_error() - math.sqrt(e2 / r2)) < 1e-8
     print("graded grid: L2 error of w_h %.4f" % prob.relative_error())
+
+
+# ---- mixed precision -------------------------------------------------------------
+# Separated pairs in FP32 (closed forms over the corner differences where the
+# gap is below the shorter interval, Gauss nodes on the overlap trapezoid
+# elsewhere), touching pairs in FP64, blocks stored FP64.  The stated bound
+# of the uniform mixed path: relative Frobenius error per block <= 2e-6
+# against the FP64 oracle.
+MIXED_BOUND = 2e-6
+
+
+def geometric(n, ratio, T=1.0):
+    steps = ratio ** np.arange(n)
+    t = np.concatenate([[0.0], np.cumsum(steps / steps.sum())]) * T
+    t[-1] = T
+    return t
+
+
+# graded steps; a grid whose small steps sit between long ones (gaps below
+# the shorter interval away from k = i + 1, long plateaus cut geometrically);
+# a geometric grid; a uniform grid (shared evaluations); small and large alpha
+@pytest.mark.parametrize("name,times,alpha", [
+    ("cube2", GRADED, 1.0),
+    ("cube2", np.array([0.0, 0.3, 0.31, 0.32, 0.7, 0.705, 1.4]), 0.4),
+    ("cube4", geometric(10, 1.2), 0.5),
+    ("cube4", np.arange(9) / 8.0, 1.0),
+    ("ico2", np.array([0.0, 0.01, 0.2, 0.21, 0.5]), 5.0),
+    ("cube2", geometric(24, 1.1, 2.0), 0.1)])
+def test_nonuniform_mixed_blocks_match_oracle(name, times, alpha):
+    nodes, tris = {"cube2": lambda: workloads.cube_mesh(2), "cube4": lambda: workloads.cube_mesh(4),
+                   "ico2": lambda: workloads.icosphere(2)}[name]()
+    V, K = gpu_assemble_nu(nodes, tris, alpha, times, precision=capi.STB_PREC_MIXED)
+    Vo, Ko = oracle.assemble_nu(nodes, tris, alpha, times)
+    worst = [0.0, 0.0]
+    for b in range(V.shape[0]):
+        for c, (got, ref) in enumerate(((V[b], Vo[b]), (K[b], Ko[b]))):
+            assert np.all(np.isfinite(got)), b
+            rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert rel <= MIXED_BOUND, (b, "VK"[c], rel)
+            worst[c] = max(worst[c], rel)
+    print("%s, %d steps: mixed non-uniform max block error V %.2e K %.2e"
+          % (name, len(times) - 1, worst[0], worst[1]))
+
+
+def test_nonuniform_mixed_pipeline():
+    """The mixed assembly inside the Dirichlet pipeline: the solution within
+    a small multiple of the stated block bound of the FP64 pipeline's."""
+    nodes, tris = workloads.cube_mesh(4)
+    src = workloads.point_source((1.5, 1.5, 1.5), t0=0.0)
+    times = geometric(12, 1.2)
+    ref = pipeline.NonUniformDirichletProblem(nodes, tris, 1.0, times, src)
+    ref.run()
+    mix = pipeline.NonUniformDirichletProblem(nodes, tris, 1.0, times, src, precision="mixed")
+    mix.run()
+    w0, w1 = ref.w.cpu().numpy(), mix.w.cpu().numpy()
+    assert np.linalg.norm(w1 - w0) / np.linalg.norm(w0) < 1e-4
+    assert abs(mix.relative_error() - ref.relative_error()) < 1e-4
