@@ -352,7 +352,13 @@ stb_status stb_assemble_vrhs(const stb_mesh *mesh, const stb_params *params, voi
  *   (eq. V0 / eq. K0 with the local step), S the pair's spatial sum of
  *   G^{dtau dt} (or its scaled normal derivative) by the rules of
  *   stb_assemble; every distinct time difference is evaluated once per
- *   point.  Needs STB_PREC_FP64, STB_STORE_F64, n_steps <= 256.
+ *   point.  STB_PREC_MIXED: the same blocks from FP32 quadrature points,
+ *   written as the time integral of the pair's kernel against the overlap
+ *   weight of the two intervals (closed forms where the weight reaches lag
+ *   0, Gauss-Legendre nodes on its linear pieces elsewhere; stated bound as
+ *   for stb_assemble's mixed path: relative Frobenius error per block
+ *   <= 2e-6 against FP64), still stored FP64.  Needs STB_STORE_F64,
+ *   n_steps <= 256.
  * stb_matvec_nu: y^k = sum_{i <= k} A^{k,i} x^i (x, y device FP64
  *   [nrhs][n_steps][E]).
  * stb_solve_nu: w^k = (V^{k,k})^{-1} (f^k - sum_{i<k} V^{k,i} w^i), every
