@@ -447,7 +447,15 @@ def nonuniform_report(capi, pipeline, torch, stream, a_, b_, cpu=True):
             m_ms = a_.elapsed_time(b_)
             ev = ((pm.V - pr.V).flatten(1).norm(dim=1) / pr.V.flatten(1).norm(dim=1)).max()
             ek = ((pm.K - pr.K).flatten(1).norm(dim=1) / pr.K.flatten(1).norm(dim=1)).max()
+            cf_terms, g_nodes, _ = capi.stb_assemble_nu_mixed_counts(pm.params, t)
+            reg_m = trm.get("k_regular_nu_mixed", (1, 0.0))[1]
+            roof_m = _alu_roofline(
+                "k_regular_nu_mixed", reg_m, float(n_reg) * 81.0 * g_nodes,
+                "MUFU.EX2 Gauss-node evaluations (the %d closed-form evaluations per point, "
+                "erfc and exp each, not counted)" % cf_terms, "Tex2/s", MUFU_PEAK_TEX2,
+                "MUFU ex2 pipe, " + PEAK_SOURCE["mufu"])
             out["geometric_mixed"] = {
+                "roofline": roof_m, "gauss_nodes": g_nodes, "closed_form_evaluations": cf_terms,
                 "assembly_ms": m_ms, "entries_per_s": 2.0 * n_blocks * E * E / (m_ms / 1e3),
                 "speedup_vs_fp64": asm_ms / m_ms,
                 "max_block_rel_err_vs_fp64": {"V": float(ev), "K": float(ek)},

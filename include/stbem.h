@@ -366,7 +366,16 @@ stb_status stb_assemble_vrhs(const stb_mesh *mesh, const stb_params *params, voi
  * stb_project_dirichlet_nu / stb_neumann_error_nu / stb_dirichlet_rhs_nu:
  *   the data projection, the L2(Sigma_h) error and f = (1/2 M_h + K_h) g
  *   (M_h = blockdiag(h_k diag(Delta_l))) on the grid; sources as for
- *   stb_project_dirichlet; the first two share stb_project_nu_workspace_size. */
+ *   stb_project_dirichlet; the first two share stb_project_nu_workspace_size.
+ * stb_assemble_nu_mixed_counts: host only (no device work): the sizes of the
+ *   STB_PREC_MIXED tables for params and times -- closed-form evaluations
+ *   (corner differences t with delta_t > 0, summed over the distinct
+ *   closed-form blocks), Gauss nodes (over the distinct node lists, no
+ *   padding) and blocks with any closed-form part; each output may be NULL.
+ *   Equal differences (to 2^-44 times[n_steps]) share one evaluation. */
+stb_status stb_assemble_nu_mixed_counts(const stb_params *params, const double *times,
+                                        int64_t *closed_form_terms, int64_t *gauss_nodes,
+                                        int64_t *closed_form_blocks);
 stb_status stb_assemble_nu_workspace_size(const stb_mesh *mesh, const stb_params *params,
                                           const double *times, size_t *bytes);
 stb_status stb_assemble_nu(const stb_mesh *mesh, const stb_params *params, const double *times,

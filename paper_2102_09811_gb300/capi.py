@@ -79,6 +79,7 @@ _SIGS = {
     "stb_assemble_vrhs_workspace_size": (_I32, [_P, _PAR, _I32, _PSZ]),
     "stb_assemble_vrhs": (_I32, [_P, _PAR, _P, _P, _I32, _P, _P, _SZ, _P]),
     "stb_assemble_nu_workspace_size": (_I32, [_P, _PAR, _P, _PSZ]),
+    "stb_assemble_nu_mixed_counts": (_I32, [_PAR, _P, _P, _P, _P]),
     "stb_assemble_nu": (_I32, [_P, _PAR, _P, _P, _P, _P, _SZ, _P]),
     "stb_matvec_nu": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "stb_solve_nu_workspace_size": (_I32, [_I64, _I32, _I32, _PSZ]),
@@ -389,6 +390,17 @@ def stb_assemble_vrhs(mesh, params, V, g, nrhs, f, workspace, stream=None):
 def _times(times):
     t, tp = _host_f64(times)
     return t, tp
+
+
+def stb_assemble_nu_mixed_counts(params, times):
+    """(closed-form evaluations, Gauss nodes, blocks with a closed-form part)
+    of the mixed non-uniform tables (host only)."""
+    t, tp = _times(times)
+    out = [ctypes.c_int64(0) for _ in range(3)]
+    _check(_library().stb_assemble_nu_mixed_counts(ctypes.byref(params), tp,
+                                                   *[ctypes.byref(o) for o in out]),
+           "stb_assemble_nu_mixed_counts")
+    return tuple(int(o.value) for o in out)
 
 
 def stb_assemble_nu_workspace_size(mesh, params, times):

@@ -1836,6 +1836,32 @@ size_t nu_mixed_bytes(const stb_params &p, const double *t) {
 }
 }  // namespace
 
+extern "C" stb_status stb_assemble_nu_mixed_counts(const stb_params *params, const double *times,
+                                                   int64_t *closed_form_terms, int64_t *gauss_nodes,
+                                                   int64_t *closed_form_blocks) {
+    if (!params) return fail(STB_ERR_INVALID_ARG, "params must be given");
+    stb_status st = nu_check(params, times);
+    if (st) return st;
+    stb_params p = *params;
+    p.T = times[p.n_steps];
+    if ((st = check_assembly_params(&p))) return st;
+    std::vector<float> cf, nodes;
+    std::vector<int32_t> targets;
+    nu_mixed_tables(p, times, cf, nodes, targets);
+    int64_t terms = 0, nn = 0, blocks = 0;
+    for (size_t r = 0; r < cf.size(); r += NU_CF_FLOATS) {
+        int32_t cnt;
+        std::memcpy(&cnt, &cf[r + 1], sizeof cnt);
+        blocks += cnt >> 1;
+        for (int t = 0; t < 4; ++t) terms += cf[r + 7 + 4 * t] != 0.f ? 1 : 0;
+    }
+    for (size_t q = 0; q < nodes.size(); q += 4) nn += nodes[q + 1] != 0.f || nodes[q] != 0.f ? 1 : 0;
+    if (closed_form_terms) *closed_form_terms = terms;
+    if (gauss_nodes) *gauss_nodes = nn;
+    if (closed_form_blocks) *closed_form_blocks = blocks;
+    return STB_OK;
+}
+
 extern "C" stb_status stb_assemble_nu_workspace_size(const stb_mesh *mesh, const stb_params *params,
                                                      const double *times, size_t *bytes) {
     if (!mesh || !params || !bytes) return fail(STB_ERR_INVALID_ARG, "mesh, params and bytes must be given");
