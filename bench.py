@@ -433,7 +433,8 @@ def nonuniform_report(capi, pipeline, torch, stream, a_, b_, cpu=True):
                     "entries/s", "2 whole rows (all 136 blocks of V and K) of the geometric grid")
             # the same grid with the separated pairs in FP32: times, block
             # errors against the FP64 blocks above, solution and error
-            pm = pipeline.NonUniformDirichletProblem(nodes, tris, 1.0, t, src, precision="mixed")
+            pm = pipeline.NonUniformDirichletProblem(nodes, tris, 1.0, t, src,
+                                                     precision=capi.STB_PREC_MIXED)
             pm.run(stream)
             torch.cuda.synchronize()
             capi.stb_trace_enable(True)

@@ -239,19 +239,18 @@ class NeumannProblem:
 
 class NonUniformDirichletProblem:
     """The Dirichlet problem on a non-uniform time grid `times` (Sec. 7):
-    block lower-triangular V, K with packed blocks (FP64; precision="mixed"
-    evaluates the separated pairs in FP32), data projection over the steps,
+    block lower-triangular V, K with packed blocks (FP64; precision
+    STB_PREC_MIXED evaluates the quadrature points in FP32), data projection over the steps,
     right-hand side, forward substitution with a factorisation per diagonal
     block, and the L2(Sigma_h) error."""
 
     def __init__(self, nodes, tris, alpha, times, sources, quad_regular=3, quad_singular=4,
-                 q_space=8, n_time=16, device="cuda", mesh=None, precision="fp64"):
+                 q_space=8, n_time=16, device="cuda", mesh=None, precision=capi.STB_PREC_FP64):
         self.mesh = mesh if mesh is not None else capi.Mesh(nodes, tris)
         self.times = np.ascontiguousarray(times, dtype=np.float64)
         n = len(self.times) - 1
-        prec = {"fp64": capi.STB_PREC_FP64, "mixed": capi.STB_PREC_MIXED}[precision]
         self.params = capi.stb_default_params(alpha, float(self.times[-1]), n, quad_regular,
-                                              quad_singular, precision=prec)
+                                              quad_singular, precision=precision)
         self.sources = sources
         self.nrhs, self.n_src = sources.shape[0], sources.shape[1]
         self.q_space, self.n_time = q_space, n_time

@@ -170,7 +170,8 @@ def test_nonuniform_mixed_pipeline():
     times = geometric(12, 1.2)
     ref = pipeline.NonUniformDirichletProblem(nodes, tris, 1.0, times, src)
     ref.run()
-    mix = pipeline.NonUniformDirichletProblem(nodes, tris, 1.0, times, src, precision="mixed")
+    mix = pipeline.NonUniformDirichletProblem(nodes, tris, 1.0, times, src,
+                                              precision=capi.STB_PREC_MIXED)
     mix.run()
     w0, w1 = ref.w.cpu().numpy(), mix.w.cpu().numpy()
     assert np.linalg.norm(w1 - w0) / np.linalg.norm(w0) < 1e-4
