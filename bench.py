@@ -526,6 +526,24 @@ def potentials_report(capi, stream, a_, b_, cpu=True):
         "point-triangle-rule point-level evaluations of both potentials x FP64 operations per "
         "evaluation (ncu)", "FP64 op/s", FP64_PEAK_TFLOPS * 1e12 / 2,
         "FP64 pipe, " + PEAK_SOURCE["fp64"], scale=POT_FP64_OPS_PER_EVAL)
+    # the level blocks from FP32 quadrature points
+    prm_m = capi.stb_default_params(alpha, T, n, precision=capi.STB_PREC_MIXED)
+    s3 = torch.empty_like(s2)
+    d3 = torch.empty_like(d2)
+    capi.stb_potentials_grid(mesh, prm_m, p3, eps, w, u1, 1, s3, d3, ws)
+    torch.cuda.synchronize()
+    capi.stb_trace_enable(True)
+    capi.stb_trace_reset()
+    a_.record(stream)
+    capi.stb_potentials_grid(mesh, prm_m, p3, eps, w, u1, 1, s3, d3, ws)
+    b_.record(stream)
+    torch.cuda.synchronize()
+    capi.stb_trace_enable(False)
+    trm = capi.stb_trace_read()
+    out["level_blocks_mixed"] = {
+        "ms": a_.elapsed_time(b_), "kernels_ms": {k: v[1] for k, v in trm.items()},
+        "max_rel_diff_vs_fp64": float(max((s3 - s2).abs().max() / s2.abs().max(),
+                                          (d3 - d2).abs().max() / d2.abs().max()))}
     out["paper_36_threads_s"] = {"single_layer": 0.31, "double_layer": 0.82,
                                  "note": "Table reprsc, 2 x 18-core Xeon Gold 6240; context"}
     del ws

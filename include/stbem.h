@@ -267,7 +267,11 @@ stb_status stb_potentials(const stb_mesh *mesh, const stb_params *params, const 
  * of n_steps x n_pts x E (single layer) and n_steps x n_pts x n_nodes (double
  * layer, accumulated per node with atomics) in the workspace, and the
  * potentials are block-Toeplitz products of these blocks with the backward
- * differences of the densities in time (FP64).  Workspace from
+ * differences of the densities in time (FP64).  params->precision =
+ * STB_PREC_MIXED evaluates the level blocks from FP32 quadrature points
+ * (distances and weights formed in FP64; FP32 blocks, FP32 atomics for the
+ * double layer; the products in double-float arithmetic, FP64 results).
+ * Workspace from
  * stb_potentials_grid_workspace_size (about 8 n_steps n_pts (E + n_nodes)
  * bytes). */
 stb_status stb_potentials_grid_workspace_size(const stb_mesh *mesh, const stb_params *params,

@@ -288,6 +288,78 @@ k_potential_levels(const double *__restrict__ geo, const int32_t *__restrict__ t
     }
 }
 
+// The same level blocks from FP32 quadrature points (params->precision =
+// STB_PREC_MIXED): per rule point the distance and the weights are formed in
+// FP64 and rounded once, the level loop runs in FP32 (erfc and exp of x_d;
+// both terms of the double-layer bracket are positive, so nothing cancels),
+// Ls is stored FP32 and Ld accumulated per node with FP32 atomics.
+template <bool SLP, bool DLP>
+__global__ void __launch_bounds__(POT_THREADS)
+k_potential_levels_mixed(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E,
+                         int N, const double *__restrict__ rule, int nq,
+                         const double *__restrict__ pts3, int P, int n_steps, double h, double eps,
+                         double alpha, float *__restrict__ Ls, float *__restrict__ Ld) {
+    extern __shared__ float smf[];
+    float *s_rho = smf, *s_cs = s_rho + nq * POT_THREADS, *s_cd = s_cs + nq * POT_THREADS;
+    __shared__ float s_lam[2 * POT_MAX_Q * POT_MAX_Q];
+    for (int i = threadIdx.x; i < nq; i += POT_THREADS) {
+        s_lam[2 * i] = (float)rule[3 * i];
+        s_lam[2 * i + 1] = (float)rule[3 * i + 1];
+    }
+    __syncthreads();
+    const int tid = threadIdx.x, j = blockIdx.x * POT_THREADS + tid;
+    const int p = blockIdx.y;
+    if (j >= E) return;
+    const double *gj = geo + (size_t)j * GEO_STRIDE;
+    const double inv_4pi = 0.25 / 3.14159265358979323846;
+    const float two_over_sqrtpi = 1.12837916709551257390f;
+    const double xp[3] = {pts3[3 * (size_t)p], pts3[3 * (size_t)p + 1], pts3[3 * (size_t)p + 2]};
+    const double area2 = 2.0 * gj[GEO_AREA];
+    for (int a = 0; a < nq; ++a) {
+        const double s1 = rule[3 * a], s2 = rule[3 * a + 1], wa = rule[3 * a + 2];
+        double r[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            r[c] = xp[c] - (gj[GEO_V0 + c] + s1 * (gj[GEO_V1 + c] - gj[GEO_V0 + c]) +
+                            s2 * (gj[GEO_V2 + c] - gj[GEO_V1 + c]));
+        const double rho = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        const double rn = r[0] * gj[GEO_N] + r[1] * gj[GEO_N + 1] + r[2] * gj[GEO_N + 2];
+        s_rho[a * POT_THREADS + tid] = (float)rho;
+        s_cs[a * POT_THREADS + tid] = (float)(area2 * wa * inv_4pi / (alpha * rho));
+        s_cd[a * POT_THREADS + tid] = (float)(area2 * wa * inv_4pi * rn / (rho * rho * rho));
+    }
+    const int t0 = DLP ? tris[3 * j] : 0, t1 = DLP ? tris[3 * j + 1] : 0,
+              t2 = DLP ? tris[3 * j + 2] : 0;
+    for (int d = 0; d < n_steps; ++d) {
+        const double delta = d * h + eps;
+        float L = 0.f, L1[3] = {0.f, 0.f, 0.f};
+        if (delta > 0.0) {
+            const float ix = (float)(0.5 / sqrt(alpha * delta));
+            for (int a = 0; a < nq; ++a) {
+                const float x = s_rho[a * POT_THREADS + tid] * ix;
+                const float e = erfcf(x);
+                if (SLP) L = fmaf(s_cs[a * POT_THREADS + tid], e, L);
+                if (DLP) {
+                    const float c = s_cd[a * POT_THREADS + tid] *
+                                    fmaf(two_over_sqrtpi * x, expf(-x * x), e);
+                    const float l1 = s_lam[2 * a], l2 = s_lam[2 * a + 1];
+                    L1[0] = fmaf(1.f - l1, c, L1[0]);
+                    L1[1] = fmaf(l1 - l2, c, L1[1]);
+                    L1[2] = fmaf(l2, c, L1[2]);
+                }
+            }
+        }
+        const size_t blk = (size_t)d * P + p;
+        if (SLP) Ls[blk * E + j] = L;
+        if (DLP) {
+            float *row = Ld + blk * N;
+            atomicAdd(row + t0, L1[0]);
+            atomicAdd(row + t1, L1[1]);
+            atomicAdd(row + t2, L1[2]);
+        }
+    }
+}
+
 }  // namespace stb
 
 using namespace stb;
@@ -394,18 +466,33 @@ static GridLayout grid_layout(const Mesh &m, int n_steps, int nrhs, int64_t P, i
     L.du = dlp ? c.take<double>((size_t)nrhs * n_steps * m.n_nodes) : nullptr;
     L.Ls = slp ? c.take<double>((size_t)n_steps * P * m.n_tris) : nullptr;
     L.Ld = dlp ? c.take<double>((size_t)n_steps * P * m.n_nodes) : nullptr;
-    L.part = reinterpret_cast<double *>(c.take<char>(toeplitz_partial_bytes(P, n_steps, nrhs)));
+    // FP64 products (FP64 level blocks) or double-float products (FP32 ones)
+    const size_t prod = std::max(toeplitz_partial_bytes(P, n_steps, nrhs),
+                                 toeplitz_df_rect_bytes(P, std::max<int64_t>(m.n_tris, m.n_nodes),
+                                                        n_steps, nrhs));
+    L.part = reinterpret_cast<double *>(c.take<char>(prod));
     L.bytes = c.off;
     return L;
 }
 
 template <bool SLP, bool DLP>
 static stb_status launch_levels(const Mesh &m, const GridLayout &L, int nq, const double *pts3,
-                                int P, int n, double h, double eps, double alpha, cudaStream_t s) {
+                                int P, int n, double h, double eps, double alpha, bool mixed,
+                                cudaStream_t s) {
+    dim3 grid((unsigned)((m.n_tris + POT_THREADS - 1) / POT_THREADS), (unsigned)P);
+    if (mixed) {
+        const size_t smem = sizeof(float) * 3 * nq * POT_THREADS;
+        STB_CUDA(cudaFuncSetAttribute(k_potential_levels_mixed<SLP, DLP>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        count_launch(s);
+        k_potential_levels_mixed<SLP, DLP><<<grid, POT_THREADS, smem, s>>>(
+            L.geo, m.d_tris, (int)m.n_tris, (int)m.n_nodes, L.rule, nq, pts3, P, n, h, eps, alpha,
+            reinterpret_cast<float *>(L.Ls), reinterpret_cast<float *>(L.Ld));
+        return check_launch("k_potential_levels_mixed");
+    }
     const size_t smem = sizeof(double) * 3 * nq * POT_THREADS;
     STB_CUDA(cudaFuncSetAttribute(k_potential_levels<SLP, DLP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)((m.n_tris + POT_THREADS - 1) / POT_THREADS), (unsigned)P);
     count_launch(s);
     k_potential_levels<SLP, DLP><<<grid, POT_THREADS, smem, s>>>(
         L.geo, m.d_tris, (int)m.n_tris, (int)m.n_nodes, L.rule, nq, pts3, P, n, h, eps, alpha,
@@ -457,31 +544,39 @@ extern "C" stb_status stb_potentials_grid(const stb_mesh *mesh, const stb_params
                              cudaMemcpyHostToDevice, s));
     if ((st = launch_geometry(m, L.geo, s))) return st;
     const int P = (int)n_pts, nq = q * q;
-    if (do_d) STB_CUDA(cudaMemsetAsync(L.Ld, 0, sizeof(double) * (size_t)n * P * m.n_nodes, s));
+    const bool mixed = p->precision == STB_PREC_MIXED;
+    const int32_t lv_store = mixed ? STB_STORE_F32 : STB_STORE_F64;  // level blocks
+    if (do_d)
+        STB_CUDA(cudaMemsetAsync(L.Ld, 0, (mixed ? sizeof(float) : sizeof(double)) * (size_t)n * P *
+                                              m.n_nodes, s));
     if (do_s && do_d)
-        st = launch_levels<true, true>(m, L, nq, points3, P, n, h, eps, p->alpha, s);
+        st = launch_levels<true, true>(m, L, nq, points3, P, n, h, eps, p->alpha, mixed, s);
     else if (do_s)
-        st = launch_levels<true, false>(m, L, nq, points3, P, n, h, eps, p->alpha, s);
+        st = launch_levels<true, false>(m, L, nq, points3, P, n, h, eps, p->alpha, mixed, s);
     else
-        st = launch_levels<false, true>(m, L, nq, points3, P, n, h, eps, p->alpha, s);
+        st = launch_levels<false, true>(m, L, nq, points3, P, n, h, eps, p->alpha, mixed, s);
     if (st) return st;
     if (do_s) {
         const size_t tot = (size_t)nrhs * n * m.n_tris;
         count_launch(s);
         k_time_diff<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(w, n, m.n_tris, tot, L.dw);
         if ((st = check_launch("k_time_diff"))) return st;
-        if ((st = toeplitz_fp64_rect(L.Ls, STB_STORE_F64, P, m.n_tris, n, nrhs, L.dw, 0.0, slp,
-                                     L.part, s)))
-            return st;
+        st = mixed ? toeplitz_df_rect(reinterpret_cast<const float *>(L.Ls), P, m.n_tris, n, nrhs,
+                                      L.dw, slp, L.part, s)
+                   : toeplitz_fp64_rect(L.Ls, lv_store, P, m.n_tris, n, nrhs, L.dw, 0.0, slp,
+                                        L.part, s);
+        if (st) return st;
     }
     if (do_d) {
         const size_t tot = (size_t)nrhs * n * m.n_nodes;
         count_launch(s);
         k_time_diff<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(u1, n, m.n_nodes, tot, L.du);
         if ((st = check_launch("k_time_diff"))) return st;
-        if ((st = toeplitz_fp64_rect(L.Ld, STB_STORE_F64, P, m.n_nodes, n, nrhs, L.du, 0.0, dlp,
-                                     L.part, s)))
-            return st;
+        st = mixed ? toeplitz_df_rect(reinterpret_cast<const float *>(L.Ld), P, m.n_nodes, n, nrhs,
+                                      L.du, dlp, L.part, s)
+                   : toeplitz_fp64_rect(L.Ld, lv_store, P, m.n_nodes, n, nrhs, L.du, 0.0, dlp,
+                                        L.part, s);
+        if (st) return st;
     }
     return STB_OK;
 }

@@ -200,7 +200,7 @@ __device__ __forceinline__ void df_acc2(float2 a, float2 xh, float2 nxh, float2 
 // two-float split xs of an FP64 vector; otherwise x is the FP32 vector xf.
 template <bool VEC, bool SPLIT>
 __global__ void __launch_bounds__(MV_THREADS)
-k_toeplitz_df_partial(const float *__restrict__ A, int E, int n_steps, int nrhs,
+k_toeplitz_df_partial(const float *__restrict__ A, int E, int N, int n_steps, int nrhs,
                       const float2 *__restrict__ xs, const float *__restrict__ xf,
                       double *__restrict__ part) {
     __shared__ __align__(16) float As[TJ][TM + 4];
@@ -217,10 +217,10 @@ k_toeplitz_df_partial(const float *__restrict__ A, int E, int n_steps, int nrhs,
     float2 hi[RPT / 2], lo[RPT / 2];
 #pragma unroll
     for (int i = 0; i < RPT / 2; ++i) hi[i] = lo[i] = make_float2(0.f, 0.f);
-    const size_t EE = (size_t)E * E;
-    const float2 *xr = SPLIT ? xs + (size_t)r * n_steps * E : nullptr;
-    const float *xfr = SPLIT ? nullptr : xf + (size_t)r * n_steps * E;
-    const int n_j = (E + TJ - 1) / TJ, n_it = (d1 - d0) * n_j;
+    const size_t EE = (size_t)E * N;
+    const float2 *xr = SPLIT ? xs + (size_t)r * n_steps * N : nullptr;
+    const float *xfr = SPLIT ? nullptr : xf + (size_t)r * n_steps * N;
+    const int n_j = (N + TJ - 1) / TJ, n_it = (d1 - d0) * n_j;
 
     float4 ra[AV];
     float2 rx[XV];
@@ -232,25 +232,25 @@ k_toeplitz_df_partial(const float *__restrict__ A, int E, int n_steps, int nrhs,
             const int t = threadIdx.x + v * MV_THREADS;
             const int i = t / (TJ / 4), j = j0 + 4 * (t % (TJ / 4)), l = l0 + i;
             if (VEC) {
-                ra[v] = (l < E && j < E) ? __ldg(reinterpret_cast<const float4 *>(Ad + (size_t)l * E + j))
+                ra[v] = (l < E && j < N) ? __ldg(reinterpret_cast<const float4 *>(Ad + (size_t)l * N + j))
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
-                const float *row = Ad + (size_t)l * E;
+                const float *row = Ad + (size_t)l * N;
                 const bool ok = l < E;
-                ra[v] = make_float4(ok && j < E ? row[j] : 0.f, ok && j + 1 < E ? row[j + 1] : 0.f,
-                                    ok && j + 2 < E ? row[j + 2] : 0.f,
-                                    ok && j + 3 < E ? row[j + 3] : 0.f);
+                ra[v] = make_float4(ok && j < N ? row[j] : 0.f, ok && j + 1 < N ? row[j + 1] : 0.f,
+                                    ok && j + 2 < N ? row[j + 2] : 0.f,
+                                    ok && j + 3 < N ? row[j + 3] : 0.f);
             }
         }
 #pragma unroll
         for (int v = 0; v < XV; ++v) {
             const int t = threadIdx.x + v * MV_THREADS;
             const int jj = t / TK, c = t % TK, k = k0 + c, j = j0 + jj;
-            const bool in = k < n_steps && k - d >= 0 && j < E;
+            const bool in = k < n_steps && k - d >= 0 && j < N;
             if (SPLIT)
-                rx[v] = in ? xr[(size_t)(k - d) * E + j] : make_float2(0.f, 0.f);
+                rx[v] = in ? xr[(size_t)(k - d) * N + j] : make_float2(0.f, 0.f);
             else
-                rx[v] = make_float2(in ? xfr[(size_t)(k - d) * E + j] : 0.f, 0.f);
+                rx[v] = make_float2(in ? xfr[(size_t)(k - d) * N + j] : 0.f, 0.f);
         }
     };
     auto store_tile = [&]() {
@@ -316,30 +316,37 @@ __global__ void k_toeplitz_df_reduce(const double *__restrict__ part, int E, int
 }
 
 size_t toeplitz_df_bytes(int64_t E, int32_t n_steps, int32_t nrhs) {
-    return df_partial_bytes(E, n_steps, nrhs) + align256((size_t)nrhs * n_steps * E * sizeof(float2));
+    return toeplitz_df_rect_bytes(E, E, n_steps, nrhs);
 }
 
-static stb_status toeplitz_df_run(const float *A, int64_t E, int32_t n_steps, int32_t nrhs,
-                                  const double *x, const float *xf, int mode, const double *f,
-                                  double beta, double *y, void *scratch, cudaStream_t s) {
+size_t toeplitz_df_rect_bytes(int64_t E, int64_t N, int32_t n_steps, int32_t nrhs) {
+    return df_partial_bytes(E, n_steps, nrhs) + align256((size_t)nrhs * n_steps * N * sizeof(float2));
+}
+
+// y = A x for blocks of E rows and N columns (x: [nrhs][n_steps][N], y and
+// f: [nrhs][n_steps][E]).
+static stb_status toeplitz_df_run(const float *A, int64_t E, int64_t N, int32_t n_steps,
+                                  int32_t nrhs, const double *x, const float *xf, int mode,
+                                  const double *f, double beta, double *y, void *scratch,
+                                  cudaStream_t s) {
     double *part = static_cast<double *>(scratch);
     float2 *xs = reinterpret_cast<float2 *>(static_cast<char *>(scratch) +
                                             df_partial_bytes(E, n_steps, nrhs));
-    const size_t total = (size_t)nrhs * n_steps * E;
+    const size_t total = (size_t)nrhs * n_steps * E, total_x = (size_t)nrhs * n_steps * N;
     stb_status st;
     if (x) {
         count_launch(s);
-        k_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(x, total, xs);
+        k_split<<<(unsigned)((total_x + 255) / 256), 256, 0, s>>>(x, total_x, xs);
         if ((st = check_launch("k_split"))) return st;
     }
     int n_kt = (n_steps + TK - 1) / TK, n_dr = (n_steps + DF_TD - 1) / DF_TD;
     dim3 grid((unsigned)((E + TM - 1) / TM), (unsigned)(n_kt * nrhs), (unsigned)n_dr);
-    const bool vec = E % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
+    const bool vec = N % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
     const auto kern = x ? (vec ? k_toeplitz_df_partial<true, true> : k_toeplitz_df_partial<false, true>)
                         : (vec ? k_toeplitz_df_partial<true, false>
                                : k_toeplitz_df_partial<false, false>);
     count_launch(s);
-    kern<<<grid, MV_THREADS, 0, s>>>(A, (int)E, n_steps, nrhs, xs, xf, part);
+    kern<<<grid, MV_THREADS, 0, s>>>(A, (int)E, (int)N, n_steps, nrhs, xs, xf, part);
     if ((st = check_launch("k_toeplitz_df_partial"))) return st;
     count_launch(s);
     k_toeplitz_df_reduce<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, (int)E, n_steps, nrhs,
@@ -350,13 +357,19 @@ static stb_status toeplitz_df_run(const float *A, int64_t E, int32_t n_steps, in
 stb_status toeplitz_df(const float *A, int64_t E, int32_t n_steps, int32_t nrhs, const double *x,
                        int mode, const double *f, double beta, double *y, void *scratch,
                        cudaStream_t s) {
-    return toeplitz_df_run(A, E, n_steps, nrhs, x, nullptr, mode, f, beta, y, scratch, s);
+    return toeplitz_df_run(A, E, E, n_steps, nrhs, x, nullptr, mode, f, beta, y, scratch, s);
 }
 
 stb_status toeplitz_df_f32x(const float *A, int64_t E, int32_t n_steps, int32_t nrhs,
                             const float *x, int mode, const double *f, double beta, double *y,
                             void *scratch, cudaStream_t s) {
-    return toeplitz_df_run(A, E, n_steps, nrhs, nullptr, x, mode, f, beta, y, scratch, s);
+    return toeplitz_df_run(A, E, E, n_steps, nrhs, nullptr, x, mode, f, beta, y, scratch, s);
+}
+
+stb_status toeplitz_df_rect(const float *A, int64_t E, int64_t N, int32_t n_steps, int32_t nrhs,
+                            const double *x, double *y, void *scratch, cudaStream_t s) {
+    return toeplitz_df_run(A, E, N, n_steps, nrhs, x, nullptr, DF_AXPBY, nullptr, 0.0, y, scratch,
+                           s);
 }
 
 // Scratch of stb_toeplitz_matvec_static: every device that loads the library

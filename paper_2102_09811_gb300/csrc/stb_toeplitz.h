@@ -34,4 +34,10 @@ stb_status toeplitz_df(const float *A, int64_t E, int32_t n_steps, int32_t nrhs,
 stb_status toeplitz_df_f32x(const float *A, int64_t E, int32_t n_steps, int32_t nrhs,
                             const float *x, int mode, const double *f, double beta, double *y,
                             void *scratch, cudaStream_t s);
+// y = A x (overwritten) for FP32 blocks of E rows and N columns, FP64 x of
+// length N and y of length E per step, in the same double-float arithmetic;
+// scratch of toeplitz_df_rect_bytes.
+size_t toeplitz_df_rect_bytes(int64_t E, int64_t N, int32_t n_steps, int32_t nrhs);
+stb_status toeplitz_df_rect(const float *A, int64_t E, int64_t N, int32_t n_steps, int32_t nrhs,
+                            const double *x, double *y, void *scratch, cudaStream_t s);
 }  // namespace stb

@@ -161,9 +161,10 @@ def test_reprsc_workload_sampled_points():
     assert np.all(np.abs(dg[:, idx] - do) <= 64 * EPS * Md)
 
 
-def gpu_potentials_grid(nodes, tris, alpha, T, n_steps, pts3, eps, w=None, u1=None, q=4):
+def gpu_potentials_grid(nodes, tris, alpha, T, n_steps, pts3, eps, w=None, u1=None, q=4,
+                        precision=capi.STB_PREC_FP64):
     mesh = capi.Mesh(nodes, tris)
-    p = capi.stb_default_params(alpha, T, n_steps)
+    p = capi.stb_default_params(alpha, T, n_steps, precision=precision)
     nrhs = (w if w is not None else u1).shape[0]
     dev = lambda a: None if a is None else torch.tensor(a, dtype=torch.float64, device="cuda")
     shape = (nrhs, n_steps, len(pts3))
@@ -219,6 +220,56 @@ def test_potentials_grid_reprsc_matches_direct():
     sg, dg = sg.reshape(1, -1), dg.reshape(1, -1)  # [k][p] = the time-major point order
     assert np.max(np.abs(sg - sd)) <= 1e-11 * np.max(np.abs(sd))
     assert np.max(np.abs(dg - dd)) <= 1e-11 * np.max(np.abs(dd))
+
+
+# Level blocks from FP32 quadrature points (STB_PREC_MIXED): every level sum
+# is a sum of positive terms (erfc, and erfc + 2x exp(-x^2)/sqrt(pi) for the
+# double layer), so each level value carries a few FP32 roundings; the
+# potentials (double-float products of those values with the density differences)
+# are tested at 1e-5 of their largest value.
+MIXED_POT = 1e-5
+
+
+@pytest.mark.parametrize("n_face,n_steps,eps_frac,nrhs", [(4, 20, 0.5, 2), (2, 3, 1.0, 5)])
+def test_potentials_grid_mixed_matches_oracle(n_face, n_steps, eps_frac, nrhs):
+    nodes, tris = workloads.cube_mesh(n_face)
+    T, alpha = 1.0, 0.8
+    h = T / n_steps
+    eps = eps_frac * h
+    rng = np.random.default_rng(n_steps + 1)
+    E, N = len(tris), len(nodes)
+    w = rng.normal(size=(nrhs, n_steps, E))
+    u1 = rng.normal(size=(nrhs, n_steps, N))
+    pts3 = rng.uniform(0.2, 0.8, size=(70, 3))
+    sg, dg = gpu_potentials_grid(nodes, tris, alpha, T, n_steps, pts3, eps, w, u1,
+                                 precision=capi.STB_PREC_MIXED)
+    pts = np.concatenate([np.concatenate([pts3, np.full((70, 1), k * h + eps)], axis=1)
+                          for k in range(n_steps)])
+    pts[:, 3] = np.minimum(pts[:, 3], T)
+    so, do = oracle.potentials(nodes, tris, alpha, T, n_steps, pts, w, u1)
+    sg, dg = sg.reshape(nrhs, -1), dg.reshape(nrhs, -1)
+    es = np.max(np.abs(sg - so)) / np.max(np.abs(so))
+    ed = np.max(np.abs(dg - do)) / np.max(np.abs(do))
+    assert es <= MIXED_POT and ed <= MIXED_POT, (es, ed)
+    print("mixed level blocks: max error / max value %.2e (single), %.2e (double)" % (es, ed))
+
+
+def test_potentials_grid_mixed_reprsc():
+    """The Table reprsc workload with the mixed level blocks against the
+    FP64 level blocks."""
+    nodes, tris = workloads.cube_mesh(16, lo=-1.0, hi=1.0)
+    T, n_steps, alpha = 1.0, 32, 0.5
+    pts3 = workloads.reprsc_points(n_steps, T)[:1089, :3]
+    rng = np.random.default_rng(34)
+    w = rng.normal(size=(1, n_steps, len(tris)))
+    u1 = rng.normal(size=(1, n_steps, len(nodes)))
+    s64, d64 = gpu_potentials_grid(nodes, tris, alpha, T, n_steps, pts3, 0.5 * T / n_steps, w, u1)
+    s32, d32 = gpu_potentials_grid(nodes, tris, alpha, T, n_steps, pts3, 0.5 * T / n_steps, w, u1,
+                                   precision=capi.STB_PREC_MIXED)
+    es = np.max(np.abs(s32 - s64)) / np.max(np.abs(s64))
+    ed = np.max(np.abs(d32 - d64)) / np.max(np.abs(d64))
+    assert es <= MIXED_POT and ed <= MIXED_POT, (es, ed)
+    print("reprsc mixed vs FP64 level blocks: %.2e (single), %.2e (double)" % (es, ed))
 
 
 def _repr_rows():
