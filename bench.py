@@ -497,6 +497,18 @@ def potentials_report(capi, stream, a_, b_, cpu=True):
     b_.record(stream)
     torch.cuda.synchronize()
     out["per_point_ms"] = a_.elapsed_time(b_)
+    # the per-point kernel with FP32 level values
+    prm_pm = capi.stb_default_params(alpha, T, n, precision=capi.STB_PREC_MIXED)
+    s1m, d1m = torch.empty_like(s1), torch.empty_like(d1)
+    capi.stb_potentials(mesh, prm_pm, pts_d, w, u1, 1, s1m, d1m, ws)
+    a_.record(stream)
+    capi.stb_potentials(mesh, prm_pm, pts_d, w, u1, 1, s1m, d1m, ws)
+    b_.record(stream)
+    torch.cuda.synchronize()
+    out["per_point_mixed"] = {
+        "ms": a_.elapsed_time(b_),
+        "max_rel_diff_vs_fp64": float(max((s1m - s1).abs().max() / s1.abs().max(),
+                                          (d1m - d1).abs().max() / d1.abs().max()))}
     del ws
     p3 = torch.tensor(pts[:P, :3], device="cuda")
     s2 = torch.empty((1, n, P), dtype=torch.float64, device="cuda")

@@ -251,7 +251,9 @@ stb_status stb_dirichlet_rhs_p1(const stb_mesh *mesh, const stb_params *params, 
  * E_t - 1), both are the paper's sums over the past steps of antiderivative
  * differences (eq. G_dtau, eq. dn_G_dtau and their delta = 0 limits), formed
  * in FP64 with a q_space x q_space conical rule per triangle
- * (1 <= q_space <= 5). */
+ * (1 <= q_space <= 5); params->precision = STB_PREC_MIXED forms the
+ * antiderivative values from FP32 rule points (x - P0 of each triangle in
+ * FP64, rounded once) and sums them over the levels in FP64. */
 stb_status stb_potentials_workspace_size(const stb_mesh *mesh, const stb_params *params,
                                          int32_t nrhs, int64_t n_pts, int32_t q_space,
                                          size_t *bytes);

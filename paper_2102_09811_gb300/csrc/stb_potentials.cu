@@ -50,19 +50,27 @@ __global__ void k_time_diff(const double *__restrict__ a, int n_steps, int64_t M
     d[idx] = i == 0 ? a[idx] : a[idx] - a[idx - M];
 }
 
+__device__ __forceinline__ double erfc_r(double x) { return erfc(x); }
+__device__ __forceinline__ float erfc_r(float x) { return erfcf(x); }
+__device__ __forceinline__ double exp_r(double x) { return exp(x); }
+__device__ __forceinline__ float exp_r(float x) { return expf(x); }
+
 // Partial sums of one CTA: part[which][r][p][blk] (which 0: single layer,
-// 1: double layer).
-template <bool SLP, bool DLP>
+// 1: double layer).  R: arithmetic of the level values (double, or float
+// for the mixed path: x - P0 of the triangle formed in FP64 and rounded
+// once, the rule points, erfc and exp in FP32; the products with the
+// density differences and all sums over levels stay FP64).
+template <class R, bool SLP, bool DLP>
 __global__ void __launch_bounds__(POT_THREADS)
 k_potentials(const double *__restrict__ geo, const int32_t *__restrict__ tris, int E, int N,
              const double *__restrict__ rule, int nq, const double *__restrict__ pts,
              int64_t n_pts, const double *__restrict__ dw, const double *__restrict__ du,
              int r0, int nr, int nrhs, int n_steps, double h, double T, double alpha,
              double *__restrict__ part, int32_t *__restrict__ status) {
-    extern __shared__ double sm[];
-    double *s_rho = sm;                                // [nq][POT_THREADS]
-    double *s_cs = s_rho + nq * POT_THREADS;           // 2 Delta w_a / (4 pi alpha rho)
-    double *s_cd = s_cs + nq * POT_THREADS;            // 2 Delta w_a (r.n) / (4 pi rho^3)
+    extern __shared__ __align__(8) unsigned char sm_raw[];
+    R *s_rho = reinterpret_cast<R *>(sm_raw);     // [nq][POT_THREADS]
+    R *s_cs = s_rho + nq * POT_THREADS;           // 2 Delta w_a / (4 pi alpha rho)
+    R *s_cd = s_cs + nq * POT_THREADS;            // 2 Delta w_a (r.n) / (4 pi rho^3)
     __shared__ double s_rule[3 * POT_MAX_Q * POT_MAX_Q];
     __shared__ double red[POT_THREADS / 32][2 * POT_MAXR];
     for (int i = threadIdx.x; i < 3 * nq; i += POT_THREADS) s_rule[i] = rule[i];
@@ -73,7 +81,7 @@ k_potentials(const double *__restrict__ geo, const int32_t *__restrict__ tris, i
     const int tv0 = DLP && active ? tris[3 * j] : 0, tv1 = DLP && active ? tris[3 * j + 1] : 0,
               tv2 = DLP && active ? tris[3 * j + 2] : 0;
     const double inv_4pi = 0.25 / 3.14159265358979323846;
-    const double two_over_sqrtpi = 1.12837916709551257390;
+    const R two_over_sqrtpi = (R)1.12837916709551257390;
     __syncthreads();
 
     for (int64_t p = blockIdx.y; p < n_pts; p += gridDim.y) {
@@ -86,19 +94,46 @@ k_potentials(const double *__restrict__ geo, const int32_t *__restrict__ tris, i
         // the rule's points on gamma_j, seen from x
         if (active && valid) {
             const double area2 = 2.0 * gj[GEO_AREA];
-            for (int a = 0; a < nq; ++a) {
-                const double s1 = s_rule[3 * a], s2 = s_rule[3 * a + 1], wa = s_rule[3 * a + 2];
+            if constexpr (sizeof(R) == sizeof(float)) {
+                // difference form: x - P0 once in FP64, the rule points in FP32
+                float d0[3], e1[3], e2[3], nf[3];
                 const double xp[3] = {x0, x1, x2};
-                double r[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    r[c] = xp[c] - (gj[GEO_V0 + c] + s1 * (gj[GEO_V1 + c] - gj[GEO_V0 + c]) +
-                                    s2 * (gj[GEO_V2 + c] - gj[GEO_V1 + c]));
-                const double rho = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-                const double rn = r[0] * gj[GEO_N] + r[1] * gj[GEO_N + 1] + r[2] * gj[GEO_N + 2];
-                s_rho[a * POT_THREADS + tid] = rho;
-                s_cs[a * POT_THREADS + tid] = area2 * wa * inv_4pi / (alpha * rho);
-                s_cd[a * POT_THREADS + tid] = area2 * wa * inv_4pi * rn / (rho * rho * rho);
+                for (int c = 0; c < 3; ++c) {
+                    d0[c] = (float)(xp[c] - gj[GEO_V0 + c]);
+                    e1[c] = (float)(gj[GEO_V1 + c] - gj[GEO_V0 + c]);
+                    e2[c] = (float)(gj[GEO_V2 + c] - gj[GEO_V1 + c]);
+                    nf[c] = (float)gj[GEO_N + c];
+                }
+                const float cwa = (float)(area2 * inv_4pi), cws = (float)(area2 * inv_4pi / alpha);
+                for (int a = 0; a < nq; ++a) {
+                    const float s1 = (float)s_rule[3 * a], s2 = (float)s_rule[3 * a + 1];
+                    const float wa = (float)s_rule[3 * a + 2];
+                    float r[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) r[c] = d0[c] - (s1 * e1[c] + s2 * e2[c]);
+                    const float rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+                    const float irho = rsqrtf(rr);
+                    const float rn = r[0] * nf[0] + r[1] * nf[1] + r[2] * nf[2];
+                    s_rho[a * POT_THREADS + tid] = rr * irho;
+                    s_cs[a * POT_THREADS + tid] = cws * wa * irho;
+                    s_cd[a * POT_THREADS + tid] = cwa * wa * rn * irho * irho * irho;
+                }
+            } else {
+                for (int a = 0; a < nq; ++a) {
+                    const double s1 = s_rule[3 * a], s2 = s_rule[3 * a + 1], wa = s_rule[3 * a + 2];
+                    const double xp[3] = {x0, x1, x2};
+                    double r[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        r[c] = xp[c] - (gj[GEO_V0 + c] + s1 * (gj[GEO_V1 + c] - gj[GEO_V0 + c]) +
+                                        s2 * (gj[GEO_V2 + c] - gj[GEO_V1 + c]));
+                    const double rho = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                    const double rn = r[0] * gj[GEO_N] + r[1] * gj[GEO_N + 1] + r[2] * gj[GEO_N + 2];
+                    s_rho[a * POT_THREADS + tid] = (R)rho;
+                    s_cs[a * POT_THREADS + tid] = (R)(area2 * wa * inv_4pi / (alpha * rho));
+                    s_cd[a * POT_THREADS + tid] = (R)(area2 * wa * inv_4pi * rn / (rho * rho * rho));
+                }
             }
         }
         double acc_s[POT_MAXR], acc_d[POT_MAXR];
@@ -108,17 +143,21 @@ k_potentials(const double *__restrict__ geo, const int32_t *__restrict__ tris, i
             for (int d = 0; d <= k; ++d) {
                 const double delta = d * h + eps;
                 if (delta <= 0.0) continue;  // x_d = infinity: zero terms
-                const double ix = 0.5 / sqrt(alpha * delta);
-                double L = 0.0, L1[3] = {0.0, 0.0, 0.0};
+                R ix;  // 1 / (2 sqrt(alpha delta)), in the level arithmetic
+                if constexpr (sizeof(R) == sizeof(float))
+                    ix = 0.5f * rsqrtf((float)(alpha * delta));
+                else
+                    ix = 0.5 / sqrt(alpha * delta);
+                R L = 0, L1[3] = {0, 0, 0};
                 for (int a = 0; a < nq; ++a) {
-                    const double x = s_rho[a * POT_THREADS + tid] * ix;
-                    const double e = erfc(x);
+                    const R x = s_rho[a * POT_THREADS + tid] * ix;
+                    const R e = erfc_r(x);
                     if (SLP) L = fma(s_cs[a * POT_THREADS + tid], e, L);
                     if (DLP) {
-                        const double g = fma(two_over_sqrtpi * x, exp(-x * x), e);
-                        const double c = s_cd[a * POT_THREADS + tid] * g;
-                        const double s1 = s_rule[3 * a], s2 = s_rule[3 * a + 1];
-                        L1[0] = fma(1.0 - s1, c, L1[0]);
+                        const R g = fma(two_over_sqrtpi * x, exp_r(-x * x), e);
+                        const R c = s_cd[a * POT_THREADS + tid] * g;
+                        const R s1 = (R)s_rule[3 * a], s2 = (R)s_rule[3 * a + 1];
+                        L1[0] = fma((R)1 - s1, c, L1[0]);
                         L1[1] = fma(s1 - s2, c, L1[1]);
                         L1[2] = fma(s2, c, L1[2]);
                     }
@@ -128,12 +167,12 @@ k_potentials(const double *__restrict__ geo, const int32_t *__restrict__ tris, i
                 for (int r = 0; r < POT_MAXR; ++r) {
                     if (r >= nr) break;
                     const size_t row = ((size_t)(r0 + r) * n_steps + i);
-                    if (SLP) acc_s[r] = fma(__ldg(dw + row * E + j), L, acc_s[r]);
+                    if (SLP) acc_s[r] = fma(__ldg(dw + row * E + j), (double)L, acc_s[r]);
                     if (DLP) {
                         const double *ur = du + row * N;
-                        acc_d[r] = fma(__ldg(ur + tv0), L1[0], acc_d[r]);
-                        acc_d[r] = fma(__ldg(ur + tv1), L1[1], acc_d[r]);
-                        acc_d[r] = fma(__ldg(ur + tv2), L1[2], acc_d[r]);
+                        acc_d[r] = fma(__ldg(ur + tv0), (double)L1[0], acc_d[r]);
+                        acc_d[r] = fma(__ldg(ur + tv1), (double)L1[1], acc_d[r]);
+                        acc_d[r] = fma(__ldg(ur + tv2), (double)L1[2], acc_d[r]);
                     }
                 }
             }
@@ -416,32 +455,32 @@ extern "C" stb_status stb_potentials(const stb_mesh *mesh, const stb_params *p, 
         if ((st = check_launch("k_time_diff"))) return st;
     }
     const int nq = q * q, nblk = (int)((m.n_tris + POT_THREADS - 1) / POT_THREADS);
-    const size_t smem = sizeof(double) * 3 * nq * POT_THREADS;
+    const bool mixed = p->precision == STB_PREC_MIXED;
     dim3 grid((unsigned)nblk, (unsigned)std::min<int64_t>(n_pts, 65535));
     const double h = p->T / n;
     for (int r0 = 0; r0 < nrhs; r0 += POT_MAXR) {
         const int nr = std::min(POT_MAXR, nrhs - r0);
         count_launch(s);
-        if (do_s && do_d) {
-            STB_CUDA(cudaFuncSetAttribute(k_potentials<true, true>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_potentials<true, true><<<grid, POT_THREADS, smem, s>>>(
-                L.geo, m.d_tris, (int)m.n_tris, (int)m.n_nodes, L.rule, nq, points, n_pts, L.dw,
-                L.du, r0, nr, nrhs, n, h, p->T, p->alpha, L.part, status_word(ws));
-        } else if (do_s) {
-            STB_CUDA(cudaFuncSetAttribute(k_potentials<true, false>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_potentials<true, false><<<grid, POT_THREADS, smem, s>>>(
-                L.geo, m.d_tris, (int)m.n_tris, (int)m.n_nodes, L.rule, nq, points, n_pts, L.dw,
-                L.du, r0, nr, nrhs, n, h, p->T, p->alpha, L.part, status_word(ws));
-        } else {
-            STB_CUDA(cudaFuncSetAttribute(k_potentials<false, true>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_potentials<false, true><<<grid, POT_THREADS, smem, s>>>(
-                L.geo, m.d_tris, (int)m.n_tris, (int)m.n_nodes, L.rule, nq, points, n_pts, L.dw,
-                L.du, r0, nr, nrhs, n, h, p->T, p->alpha, L.part, status_word(ws));
-        }
-        if ((st = check_launch("k_potentials"))) return st;
+        auto go = [&](auto kern, size_t rsize) -> stb_status {
+            const size_t smem = rsize * 3 * nq * POT_THREADS;
+            STB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            kern<<<grid, POT_THREADS, smem, s>>>(L.geo, m.d_tris, (int)m.n_tris, (int)m.n_nodes,
+                                                 L.rule, nq, points, n_pts, L.dw, L.du, r0, nr,
+                                                 nrhs, n, h, p->T, p->alpha, L.part,
+                                                 status_word(ws));
+            return STB_OK;
+        };
+        if (mixed)
+            st = do_s && do_d ? go(k_potentials<float, true, true>, sizeof(float))
+                 : do_s       ? go(k_potentials<float, true, false>, sizeof(float))
+                              : go(k_potentials<float, false, true>, sizeof(float));
+        else
+            st = do_s && do_d ? go(k_potentials<double, true, true>, sizeof(double))
+                 : do_s       ? go(k_potentials<double, true, false>, sizeof(double))
+                              : go(k_potentials<double, false, true>, sizeof(double));
+        if (st) return st;
+        if ((st = check_launch(mixed ? "k_potentials_mixed" : "k_potentials"))) return st;
     }
     const size_t tot = (size_t)nrhs * n_pts;
     count_launch(s);

@@ -36,9 +36,10 @@ def cuda_device():
     capi._library()
 
 
-def gpu_potentials(nodes, tris, alpha, T, n_steps, pts, w=None, u1=None, q=4):
+def gpu_potentials(nodes, tris, alpha, T, n_steps, pts, w=None, u1=None, q=4,
+                   precision=capi.STB_PREC_FP64):
     mesh = capi.Mesh(nodes, tris)
-    p = capi.stb_default_params(alpha, T, n_steps)
+    p = capi.stb_default_params(alpha, T, n_steps, precision=precision)
     nrhs = (w if w is not None else u1).shape[0]
     dev = lambda a: None if a is None else torch.tensor(a, dtype=torch.float64, device="cuda")
     slp = torch.full((nrhs, len(pts)), float("nan"), dtype=torch.float64, device="cuda") \
@@ -252,6 +253,27 @@ def test_potentials_grid_mixed_matches_oracle(n_face, n_steps, eps_frac, nrhs):
     ed = np.max(np.abs(dg - do)) / np.max(np.abs(do))
     assert es <= MIXED_POT and ed <= MIXED_POT, (es, ed)
     print("mixed level blocks: max error / max value %.2e (single), %.2e (double)" % (es, ed))
+
+
+def test_potentials_mixed_match_oracle():
+    """The per-point kernel with FP32 level values (FP64 density sums) at
+    arbitrary space-time points, against the oracle."""
+    nodes, tris = workloads.cube_mesh(3)
+    T, n_steps, alpha = 1.0, 9, 0.6
+    rng = np.random.default_rng(19)
+    E, N = len(tris), len(nodes)
+    w = rng.normal(size=(2, n_steps, E))
+    u1 = rng.normal(size=(2, n_steps, N))
+    pts = np.concatenate([rng.uniform(0.15, 0.85, size=(60, 3)), rng.uniform(0.0, T, size=(60, 1))],
+                         axis=1)
+    sg, dg = gpu_potentials(nodes, tris, alpha, T, n_steps, pts, w, u1,
+                            precision=capi.STB_PREC_MIXED)
+    so, do = oracle.potentials(nodes, tris, alpha, T, n_steps, pts, w, u1)
+    es = np.max(np.abs(sg - so)) / np.max(np.abs(so))
+    ed = np.max(np.abs(dg - do)) / np.max(np.abs(do))
+    assert es <= MIXED_POT and ed <= MIXED_POT, (es, ed)
+    print("mixed per-point potentials: max error / max value %.2e (single), %.2e (double)"
+          % (es, ed))
 
 
 def test_potentials_grid_mixed_reprsc():
