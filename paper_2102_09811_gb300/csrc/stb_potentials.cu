@@ -328,8 +328,8 @@ k_potential_levels(const double *__restrict__ geo, const int32_t *__restrict__ t
 }
 
 // The same level blocks from FP32 quadrature points (params->precision =
-// STB_PREC_MIXED): per rule point the distance and the weights are formed in
-// FP64 and rounded once, the level loop runs in FP32 (erfc and exp of x_d;
+// STB_PREC_MIXED): x - P0 of the triangle formed in FP64 and rounded once,
+// the rule points and the level loop in FP32 (erfc and exp of x_d;
 // both terms of the double-layer bracket are positive, so nothing cancels),
 // Ls is stored FP32 and Ld accumulated per node with FP32 atomics.
 template <bool SLP, bool DLP>
@@ -354,18 +354,27 @@ k_potential_levels_mixed(const double *__restrict__ geo, const int32_t *__restri
     const float two_over_sqrtpi = 1.12837916709551257390f;
     const double xp[3] = {pts3[3 * (size_t)p], pts3[3 * (size_t)p + 1], pts3[3 * (size_t)p + 2]};
     const double area2 = 2.0 * gj[GEO_AREA];
-    for (int a = 0; a < nq; ++a) {
-        const double s1 = rule[3 * a], s2 = rule[3 * a + 1], wa = rule[3 * a + 2];
-        double r[3];
+    // difference form: x - P0 once in FP64, the rule points in FP32
+    float d0[3], e1[3], e2[3], nf[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            r[c] = xp[c] - (gj[GEO_V0 + c] + s1 * (gj[GEO_V1 + c] - gj[GEO_V0 + c]) +
-                            s2 * (gj[GEO_V2 + c] - gj[GEO_V1 + c]));
-        const double rho = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-        const double rn = r[0] * gj[GEO_N] + r[1] * gj[GEO_N + 1] + r[2] * gj[GEO_N + 2];
-        s_rho[a * POT_THREADS + tid] = (float)rho;
-        s_cs[a * POT_THREADS + tid] = (float)(area2 * wa * inv_4pi / (alpha * rho));
-        s_cd[a * POT_THREADS + tid] = (float)(area2 * wa * inv_4pi * rn / (rho * rho * rho));
+    for (int c = 0; c < 3; ++c) {
+        d0[c] = (float)(xp[c] - gj[GEO_V0 + c]);
+        e1[c] = (float)(gj[GEO_V1 + c] - gj[GEO_V0 + c]);
+        e2[c] = (float)(gj[GEO_V2 + c] - gj[GEO_V1 + c]);
+        nf[c] = (float)gj[GEO_N + c];
+    }
+    const float cwa = (float)(area2 * inv_4pi), cws = (float)(area2 * inv_4pi / alpha);
+    for (int a = 0; a < nq; ++a) {
+        const float s1 = (float)rule[3 * a], s2 = (float)rule[3 * a + 1], wa = (float)rule[3 * a + 2];
+        float r[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = d0[c] - (s1 * e1[c] + s2 * e2[c]);
+        const float rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        const float irho = rsqrtf(rr);
+        const float rn = r[0] * nf[0] + r[1] * nf[1] + r[2] * nf[2];
+        s_rho[a * POT_THREADS + tid] = rr * irho;
+        s_cs[a * POT_THREADS + tid] = cws * wa * irho;
+        s_cd[a * POT_THREADS + tid] = cwa * wa * rn * irho * irho * irho;
     }
     const int t0 = DLP ? tris[3 * j] : 0, t1 = DLP ? tris[3 * j + 1] : 0,
               t2 = DLP ? tris[3 * j + 2] : 0;
@@ -373,7 +382,7 @@ k_potential_levels_mixed(const double *__restrict__ geo, const int32_t *__restri
         const double delta = d * h + eps;
         float L = 0.f, L1[3] = {0.f, 0.f, 0.f};
         if (delta > 0.0) {
-            const float ix = (float)(0.5 / sqrt(alpha * delta));
+            const float ix = 0.5f * rsqrtf((float)(alpha * delta));  // FP32, as the levels
             for (int a = 0; a < nq; ++a) {
                 const float x = s_rho[a * POT_THREADS + tid] * ix;
                 const float e = erfcf(x);
