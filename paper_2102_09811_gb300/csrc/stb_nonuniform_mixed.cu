@@ -75,6 +75,8 @@ void nu_mixed_tables(const stb_params &p, const double *t, std::vector<float> &c
     const int n = p.n_steps;
     const double T = t[n];
     auto key = [&](double x) { return (long long)std::llround(x / T * 17592186044416.0); };
+    // (form, differences): 0 diagonal closed form, 3 closed form of the hat at
+    // k = i + 1, 1 node list of a gap a > 0, 2 node list added to a form-3 block
     using Key = std::tuple<int, long long, long long, long long>;
     std::map<Key, std::vector<int32_t>> cf_map, g_map;
     std::map<Key, std::tuple<double, double, double>> args;
@@ -93,7 +95,7 @@ void nu_mixed_tables(const stb_params &p, const double *t, std::vector<float> &c
                 args[kk] = {a, hk, hi};
             } else {  // k = i + 1: the hat of the shorter step B, plus the rest
                 const double B = std::min(hk, hi), A = std::max(hk, hi);
-                const Key kc{1, 0, key(B), key(B)};
+                const Key kc{3, 0, key(B), key(B)};  // own type: no key shared with a node list
                 cf_map[kc].push_back(b);
                 args[kc] = {0.0, B, B};
                 if (key(A) != key(B)) {
