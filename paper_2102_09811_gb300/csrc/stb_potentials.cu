@@ -55,8 +55,9 @@ __global__ void k_time_diff(const double *__restrict__ a, int n_steps, int64_t M
 // by least squares in relative error to the scaled complementary error
 // function exp(x^2) erfc(x) on [0, 12] (40,000 points, NumPy lstsq against
 // SciPy's erfcx); in FP32 Horner form P is within 3e-7 of it, and erfc
-// within 3e-7 + (the rounding of x^2 in the exponential, as in
-// exp(-x*x)) ~ 6e-8 x^2, tested through the potentials against the oracle.
+// within 4e-7 + 3e-7 x^2 relative (the second term the FP32 roundings of
+// -log2(e) x^2 and of the exp2 approximation, as for exp(-x*x)); the
+// terms where that grows are of order exp(-x^2), small in every sum.
 __device__ __forceinline__ float erfc_fit(float x, float &ee) {
     constexpr float c[12] = {-2.728515028e-06f, 3.950394690e-01f, 3.931463063e-01f,
                              3.149637282e-01f,  7.002895698e-03f, 2.484519631e-01f,
