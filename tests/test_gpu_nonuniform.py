@@ -176,3 +176,28 @@ def test_nonuniform_mixed_pipeline():
     w0, w1 = ref.w.cpu().numpy(), mix.w.cpu().numpy()
     assert np.linalg.norm(w1 - w0) / np.linalg.norm(w0) < 1e-4
     assert abs(mix.relative_error() - ref.relative_error()) < 1e-4
+
+
+# edge cases of the mixed path: one and two steps (closed forms only, and
+# the hat-plus-remainder form of unequal neighbouring steps), the
+# icosahedron (20 triangles, half the ordered pairs touching) and its
+# 80-triangle refinement (trial-triangle counts below one CTA)
+@pytest.mark.parametrize("name,times,alpha", [
+    ("cube2", np.array([0.0, 0.4]), 1.0),
+    ("cube2", np.array([0.0, 0.1, 0.5]), 0.7),
+    ("ico20", np.array([0.0, 0.2, 0.25, 0.6]), 1.5),
+    ("ico80", np.array([0.0, 0.05, 0.3, 0.31, 0.9]), 0.3)])
+def test_nonuniform_mixed_edge_cases(name, times, alpha):
+    nodes, tris = {"cube2": lambda: workloads.cube_mesh(2), "ico20": lambda: workloads.icosphere(1),
+                   "ico80": lambda: workloads.icosphere(2)}[name]()
+    V, K = gpu_assemble_nu(nodes, tris, alpha, times, precision=capi.STB_PREC_MIXED)
+    Vo, Ko = oracle.assemble_nu(nodes, tris, alpha, times)
+    for b in range(V.shape[0]):
+        for c, (got, ref) in enumerate(((V[b], Vo[b]), (K[b], Ko[b]))):
+            assert np.all(np.isfinite(got)), b
+            nr = np.linalg.norm(ref)
+            if nr == 0.0:  # K of a flat closed surface's identical pairs only
+                assert np.linalg.norm(got) <= 1e-12, (b, "VK"[c])
+                continue
+            rel = np.linalg.norm(got - ref) / nr
+            assert rel <= MIXED_BOUND, (b, "VK"[c], rel)

@@ -104,7 +104,8 @@ def test_ragged_orders_and_steps(n_face, n_steps, q, m):
 
 @pytest.mark.parametrize("nf", [1, 2])
 def test_icosphere_all_pair_classes(nf):
-    """icosahedron (every pair touches at nf = 1) and its 80-triangle refinement."""
+    """icosahedron (20 triangles: identical, edge and vertex pairs make up half
+    of the ordered pairs) and its 80-triangle refinement."""
     nodes, tris = workloads.icosphere(nf)
     alpha, T, n_steps = 1.3, 0.4, 5
     _, V, K = gpu_assemble(nodes, tris, alpha, T, n_steps)

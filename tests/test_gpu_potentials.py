@@ -319,3 +319,32 @@ def test_table_dirconv_representation_on_gpu(row):
     err = np.linalg.norm(uh - ue) / np.linalg.norm(ue)
     print("dirconv row %d: representation l2 %.4e, printed %.3g" % (row, err, l2))
     assert abs(err - l2) <= 0.02 * l2, err
+
+
+@pytest.mark.parametrize("q,nrhs,eps_frac", [(2, 5, 0.0), (5, 1, 1.0)])
+def test_potentials_mixed_orders_and_passes(q, nrhs, eps_frac):
+    """Mixed potentials at other rule orders, five right-hand sides (two
+    passes of the per-point kernel) and eps = 0 / h on the grid form, against
+    the oracle at the same points."""
+    nodes, tris = workloads.cube_mesh(2)
+    T, n_steps, alpha = 0.8, 6, 1.1
+    h = T / n_steps
+    rng = np.random.default_rng(q * 10 + nrhs)
+    w = rng.normal(size=(nrhs, n_steps, len(tris)))
+    u1 = rng.normal(size=(nrhs, n_steps, len(nodes)))
+    pts = np.concatenate([rng.uniform(0.2, 0.8, size=(25, 3)), rng.uniform(0.0, T, size=(25, 1))],
+                         axis=1)
+    sg, dg = gpu_potentials(nodes, tris, alpha, T, n_steps, pts, w, u1, q=q,
+                            precision=capi.STB_PREC_MIXED)
+    so, do = oracle.potentials(nodes, tris, alpha, T, n_steps, pts, w, u1, q=q)
+    assert np.max(np.abs(sg - so)) <= MIXED_POT * np.max(np.abs(so))
+    assert np.max(np.abs(dg - do)) <= MIXED_POT * np.max(np.abs(do))
+    pts3, eps = pts[:, :3], eps_frac * h
+    sgg, dgg = gpu_potentials_grid(nodes, tris, alpha, T, n_steps, pts3, eps, w, u1, q=q,
+                                   precision=capi.STB_PREC_MIXED)
+    pg = np.concatenate([np.concatenate([pts3, np.full((25, 1), min(k * h + eps, T))], axis=1)
+                         for k in range(n_steps)])
+    sgo, dgo = oracle.potentials(nodes, tris, alpha, T, n_steps, pg, w, u1, q=q)
+    sgg, dgg = sgg.reshape(nrhs, -1), dgg.reshape(nrhs, -1)
+    assert np.max(np.abs(sgg - sgo)) <= MIXED_POT * np.max(np.abs(sgo))
+    assert np.max(np.abs(dgg - dgo)) <= MIXED_POT * np.max(np.abs(dgo))
