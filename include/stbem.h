@@ -65,7 +65,8 @@ typedef int32_t stb_status;
 /* Arithmetic of the assembly. */
 #define STB_PREC_FP64 0  /* every quadrature point and time level in FP64 (the paper's) */
 #define STB_PREC_MIXED 1 /* FP32 quadrature points in cancellation-free forms (block error
-                            <= 2e-6 stated), FP32 solve inside double-float refinement   */
+                            <= 2e-6 stated), FP32 solve inside iterative refinement whose
+                            residual products run on the tensor cores with split operands */
 
 /* Element type of V/K storage. */
 #define STB_STORE_F64 0
@@ -432,18 +433,44 @@ stb_status stb_toeplitz_matvec(const void *A, int32_t a_storage, int64_t E, int3
  *                   Needs E % 4 == 0 and A 16-byte aligned.  Error per entry
  *                   <= (2^-10 + 2^-11) sum_d |A^d| |x^{k-d}| plus the FP32
  *                   accumulation error.
+ *   STB_ARITH_SPLIT STB_STORE_F32 blocks on the tensor cores with split
+ *                   operands: per row and 64-column chunk j0..j0+63 of a block,
+ *                   and per step vector and chunk of x, a power-of-two scale
+ *                   above the chunk's largest magnitude and five bf16 slices of
+ *                   9-bit digits (44 bits); the slice products of each level
+ *                   are summed exactly in FP32 over a chunk, the chunks in
+ *                   FP32 pairs, the slices of blocks in FP64.  Any E.  Error
+ *                   per entry about 2^-44 sum_{d,chunks} 64 max|A^d_chunk|
+ *                   max|x^{k-d}_chunk| (relative to the chunk maxima, not to
+ *                   |A||x| entrywise).  Block entries below 2^126 in magnitude.
  * Workspace from stb_toeplitz_ex_workspace_size (same arith).  STB_ARITH_TF32
- * bounds every device wait (2 s); an expired wait leaves STB_ERR_TIMEOUT in the
- * workspace status word (stb_workspace_status). */
+ * and STB_ARITH_SPLIT bound every device wait (2 s); an expired wait leaves
+ * STB_ERR_TIMEOUT in the workspace status word (stb_workspace_status). */
 #define STB_ARITH_FP64 0
 #define STB_ARITH_DF 1
 #define STB_ARITH_TF32 2
+#define STB_ARITH_SPLIT 3
 stb_status stb_toeplitz_ex_workspace_size(int64_t E, int32_t n_steps, int32_t nrhs, int32_t arith,
                                           size_t *bytes);
 stb_status stb_toeplitz_matvec_ex(const void *A, int32_t a_storage, int64_t E, int32_t n_steps,
                                   int32_t nrhs, const double *x, double beta, double *y,
                                   int32_t arith, void *workspace, size_t workspace_bytes,
                                   stb_stream stream);
+
+/* ---- self-test of the bounded device waits (no counterpart in the paper) ---------
+ * The tensor-core kernels never wait without a limit: each mbarrier wait gives
+ * up after a time limit, records STB_ERR_TIMEOUT in the status word and lets
+ * the kernel wind down.  This call exercises that path without any fault: one
+ * CTA copies the first 256 bytes of `probe` (device, 16-byte aligned) into
+ * shared memory with a bulk copy, waits for it to land with the library's
+ * bounded wait, then waits on a second mbarrier with a limit of `limit_ns`
+ * nanoseconds (1000 .. 10^10).  With `arrive` == 0 nothing ever arrives on
+ * that barrier, the wait expires and the status word of `workspace` (at least
+ * 256 bytes) receives STB_ERR_TIMEOUT; with `arrive` != 0 the kernel arrives
+ * first and the status stays STB_OK.  Asynchronous on `stream`; read the
+ * result with stb_workspace_status. */
+stb_status stb_selftest_bounded_wait(const void *probe, int64_t limit_ns, int32_t arrive,
+                                     void *workspace, size_t workspace_bytes, stb_stream stream);
 
 /* ---- the same product without any allocation (no counterpart in the paper) -------
  * For callers that cannot allocate device memory at the point of the call:
@@ -460,13 +487,19 @@ stb_status stb_toeplitz_matvec_ex(const void *A, int32_t a_storage, int64_t E, i
  * any stream capture).  All calls on one device share its scratch, which
  * keeps the last call's contents: calls that overlap on the GPU (for example
  * on two streams of the same device) race and must be serialised by the
- * caller, e.g. by issuing them on one stream. */
+ * caller, e.g. by issuing them on one stream.  The looked-up address is kept
+ * for the life of the process: after cudaDeviceReset (or any teardown of the
+ * device's primary context) the library must not be called on that device
+ * again in the same process. */
 #define STB_TOEPLITZ_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
 stb_status stb_toeplitz_matvec_static(const void *A, int32_t a_storage, int64_t E, int32_t n_steps,
                                       int32_t nrhs, const double *x, double beta, double *y,
                                       stb_stream stream);
 
-/* ---- right-hand side f = (1/2 M_h + K_h) g, M_h = h blockdiag(diag(Delta_l)) -- */
+/* ---- right-hand side f = (1/2 M_h + K_h) g, M_h = h blockdiag(diag(Delta_l)) --
+ * (Sec. 3.4).  K g in FP64 for STB_PREC_FP64; for STB_PREC_MIXED (FP32 blocks)
+ * on the tensor cores with split operands (STB_ARITH_SPLIT).  An expired
+ * bounded wait leaves STB_ERR_TIMEOUT in the workspace status word. */
 stb_status stb_rhs_workspace_size(const stb_mesh *mesh, const stb_params *params, int32_t nrhs,
                                   size_t *bytes);
 stb_status stb_dirichlet_rhs(const stb_mesh *mesh, const stb_params *params, const void *K,
@@ -480,8 +513,10 @@ stb_status stb_dirichlet_rhs(const stb_mesh *mesh, const stb_params *params, con
  * V: device [n_steps][E][E] (params->storage), f, w: device FP64
  * [nrhs][n_steps][E].  STB_PREC_FP64: every step in FP64.  STB_PREC_MIXED
  * (needs STB_STORE_F32 blocks): FP32 factorisation and march inside
- * iterative refinement w <- w + march(f - V_h w) with the residual formed in
- * FP32-pair (double-float) arithmetic, until ||f - V_h w|| <= 1e-10 ||f||
+ * iterative refinement w <- w + march(f - V_h w) with the residual products
+ * V_h delta formed on the tensor cores with split operands (STB_ARITH_SPLIT,
+ * about 2^-44 of the chunk magnitudes) and summed in FP64, until
+ * ||f - V_h w|| <= 1e-10 ||f||
  * (at most 8 refinements, else STB_ERR_NOT_CONVERGED).  Synchronises `stream`
  * at the end and returns STB_ERR_NOT_SPD if a pivot was not positive. */
 stb_status stb_solve_workspace_size(const stb_mesh *mesh, const stb_params *params, int32_t nrhs,

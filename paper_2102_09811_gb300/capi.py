@@ -16,7 +16,7 @@ from . import _build
 STB_OK = 0
 STB_PREC_FP64, STB_PREC_MIXED = 0, 1
 STB_STORE_F64, STB_STORE_F32 = 0, 1
-STB_ARITH_FP64, STB_ARITH_DF, STB_ARITH_TF32 = 0, 1, 2
+STB_ARITH_FP64, STB_ARITH_DF, STB_ARITH_TF32, STB_ARITH_SPLIT = 0, 1, 2, 3
 STB_FLAG_NO_SYNC = 1
 
 
@@ -116,6 +116,7 @@ _SIGS = {
     "stb_error_workspace_size": (_I32, [_P, _PAR, _I32, _I32, _I32, _I32, _PSZ]),
     "stb_neumann_error": (_I32, [_P, _PAR, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _SZ, _P]),
     "stb_workspace_status": (_I32, [_P, _P]),
+    "stb_selftest_bounded_wait": (_I32, [_P, _I64, _I32, _P, _SZ, _P]),
     "stb_measure_peaks": (_I32, [ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "stb_trace_enable": (_I32, [_I32]),
     "stb_trace_reset": (_I32, []),
@@ -590,6 +591,13 @@ def stb_neumann_error(mesh, params, sources, w, out, workspace, q_space=8, n_tim
 
 def stb_workspace_status(workspace, stream=None):
     _check(_library().stb_workspace_status(_ptr(workspace), _stream(stream)), "stb_workspace_status")
+
+
+def stb_selftest_bounded_wait(probe, limit_ns, arrive, workspace, stream=None):
+    _check(_library().stb_selftest_bounded_wait(_ptr(probe), int(limit_ns), 1 if arrive else 0,
+                                                _ptr(workspace),
+                                                workspace.numel() * workspace.element_size(),
+                                                _stream(stream)), "stb_selftest_bounded_wait")
 
 
 def stb_measure_peaks(stream=None):

@@ -503,7 +503,7 @@ extern "C" stb_status stb_rhs_workspace_size(const stb_mesh *mesh, const stb_par
     Carve c(nullptr, 0);
     c.take<double>((size_t)mesh->m.n_tris * GEO_STRIDE);
     c.take<char>(p->precision == STB_PREC_MIXED
-                     ? toeplitz_df_bytes(mesh->m.n_tris, p->n_steps, nrhs)
+                     ? toeplitz_split_bytes(mesh->m.n_tris, p->n_steps, nrhs)
                      : toeplitz_partial_bytes(mesh->m.n_tris, p->n_steps, nrhs));
     *bytes = align256(c.off);
     return STB_OK;
@@ -525,14 +525,14 @@ extern "C" stb_status stb_dirichlet_rhs(const stb_mesh *mesh, const stb_params *
         return fail(STB_ERR_INVALID_ARG, "mixed precision needs STB_STORE_F32 blocks");
     Carve c(ws, ws_bytes);
     double *geo = c.take<double>((size_t)m.n_tris * GEO_STRIDE);
-    void *part = c.take<char>(mixed ? toeplitz_df_bytes(m.n_tris, p->n_steps, nrhs)
+    void *part = c.take<char>(mixed ? toeplitz_split_bytes(m.n_tris, p->n_steps, nrhs)
                                     : toeplitz_partial_bytes(m.n_tris, p->n_steps, nrhs));
     cudaStream_t s = (cudaStream_t)stream;
     STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
     if ((st = launch_geometry(m, geo, s))) return st;
-    if (mixed)
-        st = toeplitz_df((const float *)K, m.n_tris, p->n_steps, nrhs, g, DF_AXPBY, nullptr, 0.0, f,
-                         part, s);
+    if (mixed)  // K g on the tensor cores with split operands
+        st = toeplitz_split((const float *)K, m.n_tris, p->n_steps, nrhs, g, DF_AXPBY, nullptr, 0.0,
+                            f, part, status_word(ws), s);
     else
         st = toeplitz_fp64(K, p->storage, m.n_tris, p->n_steps, nrhs, g, 0.0, f, (double *)part, s);
     if (st) return st;

@@ -12,10 +12,11 @@
 // FP64 precision: everything in FP64.
 // Mixed precision: the factorisation and the march run in FP32 and are wrapped
 // in iterative refinement,  w <- w + march(f - V_h w),  whose residual is
-// updated as r <- r - V_h delta with FP32-pair ("double-float") products and
-// sums (exact FP32 products of the stored FP32 blocks with the FP32
-// correction delta, error-free two-sums), so that no O(E^2 E_t^2) work runs
-// on the scarce FP64 pipe.  The refinement stops at ||r|| <= 1e-10 ||f||.
+// updated as r <- r - V_h delta with the split-operand tensor-core product
+// (bf16 digit slices of the stored FP32 blocks and of the FP32 correction
+// delta, exact FP32 sums per chunk, about 44 bits), so that no O(E^2 E_t^2)
+// work runs on the scarce FP64 pipe.  The refinement stops at
+// ||r|| <= 1e-10 ||f||.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -604,12 +605,14 @@ struct SolveHeader {
 struct SolveLayout {
     void *L, *Li, *LiT, *rv;  // T (L holds (V^0)^{-1} after the factorisation)
     double *hv;                   // panel right-hand sides [nrhs][PB][E]
-    void *part;                   // far-history slices [FAR_NZ][nrhs][PB][E] (T)
+    void *part;                   // far-history slices [nz][nrhs][PB][E] (T)
     int4 *tasks;                  // task lists of the recursive inversion of L
     float *delta;                // mixed: correction [nrhs][n_steps][E]
     double *r;                    // mixed: residual / right-hand side
-    void *df;                     // mixed: scratch of the double-float product
+    void *df;                     // mixed: scratch of the split residual product
     double *norms;                // mixed: ||r||^2, ||f||^2
+    void *xf;                     // mixed, <= 8 right-hand sides: x slices of the tensor-core far history
+    int32_t *status;              // device status word of the call
     size_t bytes;
 };
 
@@ -622,14 +625,18 @@ static SolveLayout solve_layout(int64_t E, int n_steps, int nrhs, bool mixed, vo
     S.LiT = c.take<char>((size_t)E * E * tb);
     S.rv = c.take<char>((size_t)nrhs * E * tb);
     S.hv = c.take<double>((size_t)nrhs * PB * E);
-    S.part = c.take<char>((size_t)FAR_NZ * nrhs * PB * E * tb);
+    // far-history slices: the tensor-core path of the mixed march may use more
+    const int nz_max = mixed && panel_tc_supported(nrhs) ? std::max(FAR_NZ, panel_tc_max_slices())
+                                                          : FAR_NZ;
+    S.part = c.take<char>((size_t)nz_max * nrhs * PB * E * tb);
     S.tasks = c.take<int4>(inv_task_count((int)((E + NB - 1) / NB)));
     if (mixed) {
         const size_t n = (size_t)nrhs * n_steps * E;
         S.delta = c.take<float>(n);
         S.r = c.take<double>(n);
-        S.df = c.take<char>(toeplitz_df_bytes(E, n_steps, nrhs));
+        S.df = c.take<char>(toeplitz_split_bytes(E, n_steps, nrhs));
         S.norms = c.take<double>(2);
+        if (panel_tc_supported(nrhs)) S.xf = c.take<char>(panel_tc_bytes(E, n_steps, nrhs));
     }
     S.bytes = c.off;
     return S;
@@ -714,10 +721,20 @@ static stb_status march(const AT *V, int E, int n_steps, int nrhs, const double 
                      reinterpret_cast<uintptr_t>(x) % 16 == 0;
     const int rows_cta = 8 * (nrhs == 1 ? far_rows_per_warp<T, 1>() : far_rows_per_warp<T, 2>());
     const unsigned far_rows = (unsigned)((E + rows_cta - 1) / rows_cta);
+    // FP32 blocks and FP32 march: the far history on the tensor cores
+    constexpr bool f32 = sizeof(AT) == 4 && sizeof(T) == 4;
+    const bool tc = f32 && S.xf != nullptr;
+    if (tc && (st = panel_tc_begin(E, n_steps, nrhs, S.xf, s))) return st;
     for (int kp = 0; kp < n_steps; kp += PB) {
         const int nb = min(PB, n_steps - kp);
         int nz = 0;
-        if (kp > 0) {  // about 8 resident CTAs on each of the 152 SMs
+        if (kp > 0 && tc) {
+            if constexpr (f32) {
+                if ((st = panel_tc((const float *)V, E, n_steps, nrhs, (const float *)x, kp, nb, S.xf,
+                                   (float *)part, &nz, S.status, s)))
+                    return st;
+            }
+        } else if (kp > 0) {  // about 8 resident CTAs on each of the 152 SMs
             const int n_d = kp + nb - 1;
             nz = min(min(FAR_NZ, n_d), max(1, (int)((8 * 152 + far_rows - 1) / far_rows)));
             const int dz = (n_d + nz - 1) / nz;
@@ -772,10 +789,10 @@ static stb_status solve_mixed(const float *V, int E, int n_steps, int nrhs, cons
         count_launch(s);
         k_update<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, S.delta, n);
         if ((st = check_launch("k_update"))) return st;
-        // r_it = r_{it-1} - V_h delta_it (r_{-1} = f): the FP32 correction is
-        // exact in the double-float product, which then needs no split of x
-        if ((st = toeplitz_df_f32x(V, E, n_steps, nrhs, S.delta, DF_RESIDUAL, it == 0 ? f : S.r,
-                                   0.0, S.r, S.df, s)))
+        // r_it = r_{it-1} - V_h delta_it (r_{-1} = f), the product on the
+        // tensor cores with split operands (about 2^-44 of the chunk scales)
+        if ((st = toeplitz_split_f32x(V, E, n_steps, nrhs, S.delta, DF_RESIDUAL,
+                                      it == 0 ? f : S.r, 0.0, S.r, S.df, status, s)))
             return st;
         rhs = S.r;
         if (no_sync && it < max_refine) continue;  // fixed count: no norms until the end
@@ -894,6 +911,7 @@ static stb_status solve_blocks(int64_t E, const stb_params *p, const void *V, co
     cudaStream_t s = (cudaStream_t)stream;
     STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
     int32_t *status = status_word(ws);
+    S.status = status;
     if (mixed) {
         st = solve_mixed((const float *)V, (int)E, p->n_steps, nrhs, f, w, S, status, ws,
                          (p->flags & STB_FLAG_NO_SYNC) != 0,

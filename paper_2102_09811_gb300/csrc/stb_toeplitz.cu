@@ -454,7 +454,9 @@ extern "C" stb_status stb_toeplitz_ex_workspace_size(int64_t E, int32_t n_steps,
     case STB_ARITH_FP64: return STB_OK;
     case STB_ARITH_DF: *bytes = 256 + toeplitz_df_bytes(E, n_steps, nrhs); return STB_OK;
     case STB_ARITH_TF32: *bytes = 256 + toeplitz_tc_bytes(E, n_steps, nrhs); return STB_OK;
-    default: return fail(STB_ERR_INVALID_ARG, "arith must be STB_ARITH_FP64, _DF or _TF32");
+    case STB_ARITH_SPLIT: *bytes = 256 + toeplitz_split_bytes(E, n_steps, nrhs); return STB_OK;
+    default:
+        return fail(STB_ERR_INVALID_ARG, "arith must be STB_ARITH_FP64, _DF, _TF32 or _SPLIT");
     }
 }
 
@@ -466,7 +468,8 @@ extern "C" stb_status stb_toeplitz_matvec_ex(const void *A, int32_t a_storage, i
         return stb_toeplitz_matvec(A, a_storage, E, n_steps, nrhs, x, beta, y, ws, ws_bytes, stream);
     if (!A || !x || !y) return fail(STB_ERR_INVALID_ARG, "A, x and y must be given");
     if (a_storage != STB_STORE_F32)
-        return fail(STB_ERR_INVALID_ARG, "STB_ARITH_DF and STB_ARITH_TF32 need STB_STORE_F32 blocks");
+        return fail(STB_ERR_INVALID_ARG,
+                    "STB_ARITH_DF, STB_ARITH_TF32 and STB_ARITH_SPLIT need STB_STORE_F32 blocks");
     size_t need;
     stb_status st = stb_toeplitz_ex_workspace_size(E, n_steps, nrhs, arith, &need);
     if (st) return st;
@@ -477,5 +480,8 @@ extern "C" stb_status stb_toeplitz_matvec_ex(const void *A, int32_t a_storage, i
     if (arith == STB_ARITH_DF)
         return toeplitz_df((const float *)A, E, n_steps, nrhs, x, DF_AXPBY, nullptr, beta, y,
                            scratch, s);
+    if (arith == STB_ARITH_SPLIT)
+        return toeplitz_split((const float *)A, E, n_steps, nrhs, x, DF_AXPBY, nullptr, beta, y,
+                              scratch, status_word(ws), s);
     return toeplitz_tc((const float *)A, E, n_steps, nrhs, x, beta, y, scratch, status_word(ws), s);
 }

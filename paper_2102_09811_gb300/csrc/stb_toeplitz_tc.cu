@@ -18,11 +18,9 @@
 // partial slice; k_tc_reduce adds the slices in FP64.  Blocks d > n0 + 63 meet
 // only the zero rows of Xp and are skipped.  Every mbarrier wait is bounded in
 // time and iterations; an expired wait writes STB_ERR_TIMEOUT to the status.
-#include <cuda.h>
-
 #include <mutex>
 
-#include "stb_internal.h"
+#include "stb_tc.cuh"
 #include "stb_toeplitz_tc.h"
 
 namespace stb {
@@ -31,97 +29,17 @@ constexpr int TC_M = 128, TC_NB = 64, TC_K = 32;  // rows, columns per box, K ti
 constexpr int TC_STAGES = 4;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_A_BYTES = TC_M * TC_K * 4, TC_BOX_BYTES = TC_NB * TC_K * 4;
-constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // 2 s
-constexpr uint32_t TC_WAIT_SPINS = 1u << 28;
 
 template <int NBOX>
 struct TcShape {
     static constexpr int N = TC_NB * NBOX;
     static constexpr uint32_t STAGE = TC_A_BYTES + NBOX * TC_BOX_BYTES;
     static constexpr size_t SMEM = TC_STAGES * (size_t)STAGE + 1024 /*align*/ + 256 /*barriers*/;
-    // kind::tf32 instruction descriptor: D FP32, A and B TF32, both K-major, M = 128
-    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) |
-                                      ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+    static constexpr uint32_t IDESC = idesc_tf32(TC_M, N);
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Wait for the phase of the given parity; false (and the status set) if it
-// has not completed within TC_WAIT_NS or TC_WAIT_SPINS polls.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int32_t *status) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t i = 1; i < TC_WAIT_SPINS; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 1023u) == 0 && global_ns() - t0 > TC_WAIT_NS) break;
-    }
-    atomicCAS(status, 0, STB_ERR_TIMEOUT);
-    return false;
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-// Shared-memory matrix descriptor of a K-major operand written by TMA with
-// the 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;            // leading-dimension offset (unused with this swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride offset between 8-row groups
-    d |= (uint64_t)1 << 46;            // descriptor version
-    d |= (uint64_t)2 << 61;            // 128-byte swizzle
-    return d;
-}
-template <int NBOX>
-__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(TcShape<NBOX>::IDESC), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t v[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int32_t *status) {
+    return mbar_wait_bounded(bar, parity, status, nullptr, TC_WAIT_NS);
 }
 
 // Column box ct (0 <= ct < nrhs * n_tiles), ordered by n0 first so that the
@@ -205,10 +123,10 @@ k_toeplitz_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             if (!mbar_wait(full0 + 8 * s, (it / TC_STAGES) & 1, status)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa = smem_u32(smem + s * Sh::STAGE);
-            const uint64_t da = smem_desc(sa), db = smem_desc(sa + TC_A_BYTES);
+            const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sa + TC_A_BYTES);
 #pragma unroll
             for (int k = 0; k < TC_K / 8; ++k)  // 8 TF32 = 32 bytes: +2 in the address field
-                umma_tf32<NBOX>(tmem, da + 2 * k, db + 2 * k, (it > 0 || k > 0) ? 1u : 0u);
+                umma_tf32(tmem, da + 2 * k, db + 2 * k, Sh::IDESC, (it > 0 || k > 0) ? 1u : 0u);
             umma_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
         }
         umma_commit(done);  // arrives when every MMA issued above has completed
@@ -297,23 +215,32 @@ static stb_status encode_fn(EncodeTiledFn *out) {
     return STB_OK;
 }
 
-// 2-D FP32 row-major tensor [rows][cols], box of box_rows x 32 columns
-static stb_status make_map(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols,
-                           uint32_t box_rows) {
+// 2-D row-major tensor [rows][cols] of elem_bytes-byte elements, box of
+// box_rows x box_cols elements (box_cols * elem_bytes = 128: one swizzled row)
+stb_status tc_make_map_2d(CUtensorMap *map, CUtensorMapDataType type, uint32_t elem_bytes,
+                          const void *base, uint64_t rows, uint64_t cols, uint32_t box_cols,
+                          uint32_t box_rows) {
     EncodeTiledFn fn;
     stb_status st = encode_fn(&fn);
     if (st) return st;
     const cuuint64_t dims[2] = {cols, rows};
-    const cuuint64_t strides[1] = {cols * 4};
-    const cuuint32_t box[2] = {(cuuint32_t)TC_K, box_rows};
+    const cuuint64_t strides[1] = {cols * elem_bytes};
+    const cuuint32_t box[2] = {box_cols, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult res =
-        fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box,
-           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+        fn(map, type, 2, const_cast<void *>(base), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (res != CUDA_SUCCESS)
         return fail(STB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)res);
     return STB_OK;
+}
+
+// 2-D FP32 row-major tensor [rows][cols], box of box_rows x 32 columns
+static stb_status make_map(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols,
+                           uint32_t box_rows) {
+    return tc_make_map_2d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, rows, cols, TC_K,
+                          box_rows);
 }
 
 struct TcPlan {
@@ -382,4 +309,41 @@ stb_status toeplitz_tc(const float *A, int64_t E, int32_t n_steps, int32_t nrhs,
     return check_launch("k_tc_reduce");
 }
 
+// One CTA: a bulk copy waited for with the bounded wait, then a bounded wait
+// on a barrier nothing arrives on (unless `arrive`): the expiry path of every
+// tensor-core kernel, without a fault.
+__global__ void k_selftest_wait(const void *probe, uint64_t limit_ns, int arrive,
+                                int32_t *status) {
+    __shared__ __align__(128) unsigned char buf[256];
+    __shared__ __align__(8) uint64_t bars[2];
+    if (threadIdx.x != 0) return;
+    const uint32_t b0 = smem_u32(&bars[0]), b1 = smem_u32(&bars[1]);
+    mbar_init(b0, 1);
+    mbar_init(b1, 1);
+    mbar_init_fence();
+    mbar_expect_tx(b0, sizeof buf);
+    bulk_load(smem_u32(buf), probe, sizeof buf, b0);
+    if (!mbar_wait_bounded(b0, 0, status, nullptr, TC_WAIT_NS)) return;  // the copy has landed
+    if (arrive) mbar_arrive(b1);
+    mbar_wait_bounded(b1, 0, status, nullptr, limit_ns);
+}
+
 }  // namespace stb
+
+using namespace stb;
+
+extern "C" stb_status stb_selftest_bounded_wait(const void *probe, int64_t limit_ns, int32_t arrive,
+                                                void *ws, size_t ws_bytes, stb_stream stream) {
+    if (!probe || reinterpret_cast<uintptr_t>(probe) % 16 != 0)
+        return fail(STB_ERR_INVALID_ARG, "probe must be a 16-byte aligned device pointer");
+    if (limit_ns < 1000 || limit_ns > 10000000000ll)
+        return fail(STB_ERR_INVALID_ARG, "limit_ns must lie in [1000, 1e10]");
+    stb_status st = check_workspace(ws, ws_bytes, 256);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 256, s));
+    count_launch(s);
+    k_selftest_wait<<<1, 32, 0, s>>>(probe, (uint64_t)limit_ns, arrive, status_word(ws));
+    return check_launch("k_selftest_wait");
+}
+
