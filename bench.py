@@ -6,9 +6,13 @@ blocks V^d and K^d, Dirichlet data projection, right-hand side
 (1/2 M_h + K_h) g, forward-substitution solve and the L2(Sigma_h) error.
 Metric: V,K block entries produced per second (2 E_t E^2 per problem).
 
-Default workload: cube surface with 16 x 16 squares per face (3072
-triangles), 64 uniform steps on T = 1, alpha in {0.5, 1, 2}, exterior heat
-source (1.5, 1.5, 1.5), t0 = 0.
+Default workload (the large mixed run): icosphere of radius 1 with 5120
+triangles, 256 uniform steps on T = 1, alpha = 1, Dirichlet data from 8
+seeded exterior heat-kernel sources, FP32 regular pairs and FP32 block
+storage (V and K 26.8 GB each).  The headline value is V,K entries per
+second of assembly; the whole step's rate, the refined solve, the mixed vs
+FP64 comparison on the 3072-triangle cube with 64 steps, the block-Toeplitz
+products and the 64-problem batch are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
@@ -124,6 +128,41 @@ def _measured_hbm_gbs():
         return 6800.0  # fallback figure for a GB300 copy
 
 
+
+def _measured_bf16_tflops(sustained=False):
+    try:
+        with open(MEASURED_PEAKS) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops_sustained" if sustained else "bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1700.0 if sustained else 1900.0  # fallback figures for a GB300
+
+
+def split_tensor_roofline(E, n, nrhs, ms, sustained=False):
+    """Tensor-pipe roofline of one split-operand product (STB_ARITH_SPLIT).
+    Algorithmic work: E^2 n (n+1) nrhs flops (each block once per column it
+    feeds).  Executed work: 15 bf16 slice products per multiply-add over the
+    boxes the kernel runs -- per (tile of 128 rows, box of 64 columns, block d,
+    chunk of 64 columns j) 15 x 128 x 64 x 64 multiply-adds, blocks d beyond a
+    box's last step skipped -- against the measured dense bf16 peak."""
+    rt, nc = -(-E // 128), -(-E // 64)
+    mac = 0.0
+    for r0 in range(0, nrhs, 64):
+        ng = min(64, nrhs - r0)
+        rpad = 1
+        while rpad < ng:
+            rpad *= 2
+        S = 64 // rpad
+        nblk = sum(min(n, b * S + S) for b in range(-(-n // S)))
+        mac += float(rt) * nblk * nc * 15 * 128 * 64 * 64
+    peak = _measured_bf16_tflops(sustained)
+    exe = 2.0 * mac / (ms / 1e3) / 1e12
+    return {"algorithmic_tflops": float(E) * E * n * (n + 1) * nrhs / (ms / 1e3) / 1e12,
+            "bf16_slice_tflops_executed": exe, "bf16_peak_tflops": peak,
+            "frac_of_bf16_peak": exe / peak,
+            "bf16_peak_source": "MEASURED_PEAKS.json %s cuBLAS bf16" % ("sustained" if sustained
+                                                                        else "burst")}
+
 HBM_PEAK_GBS = _measured_hbm_gbs()
 # FP32 pipe: 128 lanes per SM per clock (one FP32 operation each)
 FP32_OP_PEAK = 152 * 128 * 2.07e9
@@ -135,8 +174,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", default="cube3072_e64")
-    ap.add_argument("--alphas", default="0.5,1,2")
+    ap.add_argument("--workload", default="sphere5120_e256")
+    ap.add_argument("--alphas", default=None,
+                    help="comma-separated heat capacities (default: the workload's; "
+                         "0.5,1,2 for cube3072_e64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -154,7 +195,22 @@ def parse():
                     help="skip the Neumann problem report (outside the timed region)")
     ap.add_argument("--no-p1", action="store_true",
                     help="skip the piecewise-linear data pipeline report (outside the timed region)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 64-problem batch report (outside the timed region)")
+    ap.add_argument("--no-c2", action="store_true",
+                    help="skip the reports on the 3072-triangle cube (mixed vs FP64 assembly, the "
+                         "three-alpha step) outside the timed region")
     return ap.parse_args()
+
+
+# heat capacities of a workload when --alphas is not given
+WORKLOAD_ALPHAS = {"cube3072_e64": [0.5, 1.0, 2.0]}
+
+
+def workload_alphas(args, wl):
+    if args.alphas:
+        return [float(a) for a in args.alphas.split(",")]
+    return WORKLOAD_ALPHAS.get(args.workload, [float(wl["alpha"])])
 
 
 def dist_env():
@@ -277,7 +333,7 @@ def run_reference(args):
                           "single workloads; batch64 is measured on the GPU only"}), flush=True)
         return
     wl = workloads.workload(args.workload)
-    alphas = [float(a) for a in args.alphas.split(",")]
+    alphas = workload_alphas(args, wl)
     E, n = len(wl["tris"]), wl["n_steps"]
     per_step = max(1.0, args.cpu_seconds / 3.0)
     threads = host_threads()
@@ -301,6 +357,11 @@ def run_reference(args):
                        "quad_regular": 3, "quad_singular": 4},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
+            # the oracle times whole rows; the step time is the rate scaled to all
+            # E rows of every problem of the workload
+            "extrapolated": True,
+            "measured": {"rows": rows_total, "seconds": secs_total, "threads": threads,
+                         "entries": 2.0 * n * E * rows_total},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -374,6 +435,63 @@ def _roofline(name, trace_entry, ms_step, n_reg_pairs, q, n_steps):
     else:
         roof.update({"bound": None, "achieved": None, "peak": None, "frac": None})
     return roof
+
+
+def mixed_vs_fp64_report(capi, pipeline, torch, stream, a_, b_, alpha=0.5, reps_mixed=5,
+                         reps_fp64=2):
+    """Mixed-precision against FP64 assembly of V and K on the cube with 3072
+    triangles and 64 steps: CUDA events around the whole stb_assemble call
+    (geometry, pair classification, rule tables and kernels) for both, one
+    warm-up call each, the median of the timed calls; relative Frobenius error
+    of every mixed block against the FP64 block; then the other stages of the
+    mixed problem (projection, right-hand side, refined solve, error)."""
+    wl = workloads.workload("cube3072_e64")
+    nodes, tris, n, src = wl["nodes"], wl["tris"], wl["n_steps"], wl["sources"]
+    mesh = capi.Mesh(nodes, tris)
+    E = len(tris)
+    pm = pipeline.DirichletProblem(nodes, tris, alpha, wl["T"], n, src, mesh=mesh,
+                                   precision=capi.STB_PREC_MIXED, storage=capi.STB_STORE_F32)
+    pf = pipeline.DirichletProblem(nodes, tris, alpha, wl["T"], n, src, mesh=mesh)
+
+    def timed(fn, reps):
+        fn(stream)
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(reps):
+            a_.record(stream)
+            fn(stream)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            out.append(a_.elapsed_time(b_))
+        return out
+
+    tm = timed(pm.assemble, reps_mixed)
+    tf = timed(pf.assemble, reps_fp64)
+    errs = {}
+    for name, A, B in (("V", pm.V, pf.V), ("K", pm.K, pf.K)):
+        errs[name] = max(float(torch.linalg.norm(A[d].double() - B[d]) / torch.linalg.norm(B[d]))
+                         for d in range(n))
+    del pf
+    torch.cuda.empty_cache()
+    entries = 2.0 * n * E * E
+    mm, mf = statistics.median(tm), statistics.median(tf)
+    stages = {"assemble": mm}
+    for label, fn in (("project", pm.project), ("rhs", pm.rhs), ("solve", pm.solve),
+                      ("error", pm.error)):
+        stages[label] = statistics.median(timed(fn, 2))
+    refinements, rel_residual = capi.stb_solve_report(pm.ws_solve)
+    out = {"workload": "cube3072_e64", "alpha": alpha, "entries": entries,
+           "timing": "CUDA events around the whole stb_assemble call, one warm-up call, median "
+                     "of the timed calls",
+           "fp64_assembly_ms": mf, "fp64_runs_ms": tf, "fp64_entries_per_s": entries / (mf / 1e3),
+           "mixed_assembly_ms": mm, "mixed_runs_ms": tm, "mixed_entries_per_s": entries / (mm / 1e3),
+           "speedup": mf / mm, "max_block_rel_err_mixed_vs_fp64": errs,
+           "stated_bound_per_block": 2e-6,
+           "mixed_problem_stage_ms": stages, "mixed_solve_refinements": refinements,
+           "mixed_solve_rel_residual": rel_residual, "rel_l2_error_w": pm.relative_error()}
+    del pm
+    torch.cuda.empty_cache()
+    return out
 
 
 def nonuniform_report(capi, pipeline, torch, stream, a_, b_, cpu=True):
@@ -580,7 +698,7 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl")
     wl = workloads.workload(args.workload)
-    alphas = [float(a) for a in args.alphas.split(",")]
+    alphas = workload_alphas(args, wl)
     E, n = len(wl["tris"]), wl["n_steps"]
     nodes, tris, src = wl["nodes"], wl["tris"], wl["sources"]
     mixed = args.precision == "mixed"
@@ -597,18 +715,25 @@ def run_gpu(args):
     streams = [stream] * len(probs)
 
     trace_assembly = [False]  # trace the first problem's assembly kernels only
+    # CUDA events around every assembly of the timed steps: the metric's time
+    # (V,K entries per second of assembly, one list entry per step)
+    asm_events = []
 
     def run_problem(i, p, s, after=None):
         if after is not None:  # the previous problem's assembly
             s.wait_event(after)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a0.record(s)
         if i == 0 and trace_assembly[0]:
             capi.stb_trace_enable(True)
             p.assemble(s)
             capi.stb_trace_enable(False)
         else:
             p.assemble(s)
-        done = torch.cuda.Event()
+        done = torch.cuda.Event(enable_timing=True)
         done.record(s)
+        if asm_events:
+            asm_events[-1].append((a0, done))
         p.project(s)
         p.rhs(s)
         p.solve(s)
@@ -664,6 +789,7 @@ def run_gpu(args):
         barrier()
         start.record(stream)
         for _ in range(args.steps):
+            asm_events.append([])
             step()
         end.record(stream)
         barrier()
@@ -672,7 +798,14 @@ def run_gpu(args):
     trace = capi.stb_trace_read()
     ms = max_over_ranks(start.elapsed_time(end), world, "cuda")
     entries = 2.0 * n * E * E * len(alphas)
-    value = whole_job_rate(entries, args.steps, ms, world)
+    # the metric: entries per second of assembly (CUDA events around every
+    # problem's assembly; the best timed step, the slowest rank), and the
+    # whole step's rate beside it
+    asm_ms_steps = [sum(a.elapsed_time(b) for a, b in ev) for ev in asm_events]
+    asm_ms_best = max_over_ranks(min(asm_ms_steps), world, "cuda")
+    asm_ms_mean = max_over_ranks(statistics.mean(asm_ms_steps), world, "cuda")
+    value = world * entries / (asm_ms_best / 1e3)
+    step_rate = whole_job_rate(entries, args.steps, ms, world)
     rel_err = [p.relative_error() for p in probs]
     solve_status = [p.solve_status() for p in probs]
     if any(st != 0 for _, _, st in solve_status):
@@ -687,9 +820,15 @@ def run_gpu(args):
     # arithmetic the stored blocks allow; errors relative to the FP64 product
     p0 = probs[0]
     y = torch.empty_like(p0.w)
-    ariths = [("fp64", capi.STB_ARITH_FP64)]
+    # the SIMT FP64 and double-float forms take seconds at 8 right-hand sides x
+    # 5120^2 x 256 steps: they run only up to the 3072 x 64 size
+    small = float(E) * E * n * (n + 1) * p0.nrhs <= 1e11
+    ariths = [("fp64", capi.STB_ARITH_FP64)] if small or storage == capi.STB_STORE_F64 else []
     if storage == capi.STB_STORE_F32:
-        ariths += [("df", capi.STB_ARITH_DF), ("tf32", capi.STB_ARITH_TF32)]
+        ariths = [("split", capi.STB_ARITH_SPLIT)] + ariths
+        if small:
+            ariths += [("df", capi.STB_ARITH_DF)]
+        ariths += [("tf32", capi.STB_ARITH_TF32)]
     a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     flops = float(E) * E * n * (n + 1) * p0.nrhs
     a_bytes = float(n) * E * E * (4 if storage == capi.STB_STORE_F32 else 8)
@@ -702,7 +841,7 @@ def run_gpu(args):
         if y_ref is None:
             y_ref = y.clone()
         rel = float(torch.linalg.norm(y - y_ref) / torch.linalg.norm(y_ref))
-        reps = 5 if label == "fp64" else 20
+        reps = 5 if label == "fp64" else (20 if small else 3)
         a_.record(stream)
         for _ in range(reps):
             capi.stb_toeplitz_matvec_ex(p0.V, storage, E, n, p0.nrhs, p0.w, 0.0, y, ar, ws)
@@ -711,16 +850,19 @@ def run_gpu(args):
         mv_ms = a_.elapsed_time(b_) / reps
         macs = flops / 2.0
         entry = {"ms": mv_ms, "tflops": flops / (mv_ms / 1e3) / 1e12,
-                 "block_gbs": a_bytes / (mv_ms / 1e3) / 1e9, "rel_err_vs_fp64": rel}
+                 "block_gbs": a_bytes / (mv_ms / 1e3) / 1e9,
+                 "rel_err_vs_" + ariths[0][0]: rel}
         if label == "fp64":  # FP64 FMA pipe, one DFMA per multiply-add
             entry["frac_of_fp64_fma_peak"] = macs / (mv_ms / 1e3) / (FP64_PEAK_TFLOPS * 1e12 / 2)
         elif label == "df":  # FP32 pipe, 11 FP32 operations per multiply-add
             entry["frac_of_fp32_op_peak"] = 11.0 * macs / (mv_ms / 1e3) / FP32_OP_PEAK
+        elif label == "split":  # 15 bf16 slice products per multiply-add on the tensor cores
+            entry.update(split_tensor_roofline(E, n, p0.nrhs, mv_ms))
         else:  # HBM: every block read once
             entry["frac_of_hbm_peak"] = a_bytes / (mv_ms / 1e3) / 1e9 / HBM_PEAK_GBS
         matvec[label] = entry
         del ws
-    best = "tf32" if "tf32" in matvec else "fp64"
+    best = "split" if "split" in matvec else "fp64"
     mv_tflops, mv_ms = matvec[best]["tflops"], matvec[best]["ms"]
     matvec["blocks_read_gb"] = a_bytes / 1e9
     matvec["hbm_peak_gbs"] = HBM_PEAK_GBS
@@ -742,30 +884,30 @@ def run_gpu(args):
     refinements, rel_residual = capi.stb_solve_report(p0.ws_solve)
     solve_info = {"stage_ms": stage_ms, "refinements": refinements, "rel_residual": rel_residual,
                   "alpha": alphas[0], "kernels_ms_one_problem": {k: v[1] for k, v in one.items()}}
+    # rooflines of the solve's tensor-core kernels from the same trace: the
+    # split-operand product (right-hand side and refinement residuals) and the
+    # march's far history (HBM: the blocks each panel reads)
+    if "k_toeplitz_split" in one:
+        cnt, tot = one["k_toeplitz_split"]
+        solve_info["roofline_split_product"] = dict(
+            kernel="k_toeplitz_split", launches=cnt, launch_ms=tot / cnt, bound="tensor",
+            **split_tensor_roofline(E, n, p0.nrhs, tot / cnt, sustained=True))
+    if "k_toeplitz_panel" in one:
+        cnt, tot = one["k_toeplitz_panel"]
+        per_march = sum((kp + min(8, n - kp) - 1) for kp in range(8, n, 8)) * 4.0 * E * E
+        marches = cnt / max(1, len(range(8, n, 8)))
+        ach = per_march * marches / (tot / 1e3) / 1e9
+        solve_info["roofline_far_history"] = {
+            "kernel": "k_toeplitz_panel", "launches": cnt, "launch_ms": tot / cnt, "bound": "hbm",
+            "unit": "GB/s", "achieved": ach, "peak": HBM_PEAK_GBS, "frac": ach / HBM_PEAK_GBS,
+            "algorithmic_bytes_per_march": per_march,
+            "note": "blocks 1 .. kp+7 of V read once per panel of 8 steps (FP32)"}
 
-    # the other precision: FP64 assembly of one problem for "mixed vs FP64"
+    # the other precision on the 3072-triangle cube with 64 steps (the FP64 GPU
+    # baseline workload): both assemblies timed alike, per-block errors
     cmp = None
-    if mixed and not args.no_fp64_compare:
-        pf = pipeline.DirichletProblem(nodes, tris, alphas[0], wl["T"], n, src, mesh=mesh)
-        pf.assemble(stream)
-        torch.cuda.synchronize()
-        a_.record(stream)
-        pf.assemble(stream)
-        b_.record(stream)
-        torch.cuda.synchronize()
-        f_ms = a_.elapsed_time(b_)
-        # error of the mixed blocks against these FP64 blocks (per block, relative Frobenius)
-        errs_v = [float(torch.linalg.norm(probs[0].V[d].double() - pf.V[d]) / torch.linalg.norm(pf.V[d]))
-                  for d in range(n)]
-        errs_k = [float(torch.linalg.norm(probs[0].K[d].double() - pf.K[d]) / torch.linalg.norm(pf.K[d]))
-                  for d in range(n)]
-        mixed_ms = trace.get("k_regular_mixed", (1, 0.0))[1] + trace.get("k_singular_mixed", (1, 0.0))[1]
-        mixed_ms /= max(1, trace.get("k_regular_mixed", (1, 0))[0])
-        cmp = {"fp64_assembly_ms": f_ms, "fp64_assembly_entries_per_s": 2.0 * n * E * E / (f_ms / 1e3),
-               "mixed_assembly_ms": mixed_ms,
-               "mixed_assembly_entries_per_s": 2.0 * n * E * E / (mixed_ms / 1e3) if mixed_ms else None,
-               "alpha": alphas[0], "mixed_vs_fp64_max_block_rel_err": {"V": max(errs_v), "K": max(errs_k)}}
-        del pf
+    if mixed and not args.no_fp64_compare and not args.no_c2:
+        cmp = mixed_vs_fp64_report(capi, pipeline, torch, stream, a_, b_)
 
     # V and the right-hand side without storing K (matrix-free K g), first
     # problem: time against assembly + stored-K right-hand side
@@ -789,12 +931,20 @@ def run_gpu(args):
                  "k_bytes_not_stored": 4.0 * n * E * E}
         del ws_mf, f_mf
 
+    # the extension reports below run on the 3072-triangle cube with 64 steps
+    # (the paper's scalability mesh), whatever the headline workload
+    wlx = workloads.workload("cube3072_e64")
+    nodes_x, tris_x, n_x, src_x = wlx["nodes"], wlx["tris"], wlx["n_steps"], wlx["sources"]
+    mesh_x = capi.Mesh(nodes_x, tris_x)
+    E_x = len(tris_x)
+    n_reg_pairs_x = E_x * E_x - 2 * mesh_x.n_touching + E_x
+    alpha_x = 0.5
     # the paper's own discretisation of the data (piecewise-linear in space,
     # Sec. 3.2 / 3.4) for the first problem: stage times after one warm-up
     # pass, the K1 kernels' share and the point-level evaluation rate
     p1 = None
     if not args.no_p1:
-        pp = pipeline.DirichletProblem(nodes, tris, alphas[0], wl["T"], n, src, mesh=mesh,
+        pp = pipeline.DirichletProblem(nodes_x, tris_x, alpha_x, wlx["T"], n_x, src_x, mesh=mesh_x,
                                        precision=prec, storage=storage, data="p1")
         pp.run(stream)
         torch.cuda.synchronize()
@@ -812,37 +962,37 @@ def run_gpu(args):
         tr1 = capi.stb_trace_read()
         kind = "mixed" if "k_regular_k1_mixed" in tr1 else "f64"
         k1_ms = tr1.get("k_regular_k1_" + kind, (1, 0.0))[1]
-        p1 = {"alpha": alphas[0], "stage_ms": p1_ms, "rel_l2_error_w": pp.relative_error(),
+        p1 = {"alpha": alpha_x, "workload": "cube3072_e64", "stage_ms": p1_ms, "rel_l2_error_w": pp.relative_error(),
               "k1_arithmetic": kind, "k_regular_k1_ms": k1_ms,
               "k_singular_k1_ms": tr1.get("k_singular_k1_" + kind, (1, 0.0))[1],
-              "k1_entries": float(n) * E * mesh.n_nodes,
+              "k1_entries": float(n_x) * E_x * mesh_x.n_nodes,
               "kernels_ms": {k: v[1] for k, v in tr1.items()}}
         k1_all = k1_ms + p1["k_singular_k1_ms"]
         p1["k1_entries_per_s"] = p1["k1_entries"] / (k1_all / 1e3) if k1_all else None
         if kind == "mixed":  # one exp2 per node and point, as for V, K
             p1["roofline"] = _alu_roofline(
-                "k_regular_k1_mixed", k1_ms, float(n_reg_pairs) * 81.0 * mixed_nodes_per_point(n),
+                "k_regular_k1_mixed", k1_ms, float(n_reg_pairs_x) * 81.0 * mixed_nodes_per_point(n_x),
                 "MUFU.EX2 time-node evaluations", "Tex2/s", MUFU_PEAK_TEX2,
                 "MUFU ex2 pipe, " + PEAK_SOURCE["mufu"])
         elif k1_ms:
             p1["roofline"] = _alu_roofline(
-                "k_regular_k1_f64", k1_ms, float(n_reg_pairs) * 81.0 * n,
+                "k_regular_k1_f64", k1_ms, float(n_reg_pairs_x) * 81.0 * n_x,
                 "separated-pair point-level evaluations", "point-level evaluations/s", None, None)
         if not args.no_cpu_baseline:  # the oracle's K1 on whole test-triangle rows
             import oracle
-            rows = np.array([0, E // 2])
+            rows = np.array([0, E_x // 2])
             p1["cpu_baseline"] = oracle_sample(
-                lambda: oracle.assemble_k1_rows(nodes, tris, alphas[0], wl["T"], n, rows),
-                2.0 * n * mesh.n_nodes, "K1 entries/s",
-                "2 whole rows of K1 (all %d blocks x %d nodes) of %s" % (n, mesh.n_nodes,
-                                                                      args.workload))
+                lambda: oracle.assemble_k1_rows(nodes_x, tris_x, alpha_x, wlx["T"], n_x, rows),
+                2.0 * n_x * mesh_x.n_nodes, "K1 entries/s",
+                "2 whole rows of K1 (all %d blocks x %d nodes) of %s" % (n_x, mesh_x.n_nodes,
+                                                                      "cube3072_e64"))
         del pp
 
-    # the Neumann problem (Sec. 3.3) on the same mesh and steps, first alpha:
+    # the Neumann problem (Sec. 3.3) on the same cube:
     # stage times after a warm-up pass, the hypersingular kernels' times
     neu = None
     if not args.no_neumann:
-        pn = pipeline.NeumannProblem(nodes, tris, alphas[0], wl["T"], n, src, mesh=mesh,
+        pn = pipeline.NeumannProblem(nodes_x, tris_x, alpha_x, wlx["T"], n_x, src_x, mesh=mesh_x,
                                      precision=prec, storage=storage)
         pn.run(stream)
         torch.cuda.synchronize()
@@ -858,31 +1008,31 @@ def run_gpu(args):
             nms[label] = a_.elapsed_time(b_)
         capi.stb_trace_enable(False)
         trn = capi.stb_trace_read()
-        neu = {"alpha": alphas[0], "stage_ms": nms, "rel_l2_error_u": pn.relative_error(),
+        neu = {"alpha": alpha_x, "workload": "cube3072_e64", "stage_ms": nms, "rel_l2_error_u": pn.relative_error(),
                "kernels_ms": {k: v[1] for k, v in trn.items()}}
         d2k = "mixed" if "k_regular_d2_mixed" in trn else "f64"
         d2_ms = trn.get("k_regular_d2_" + d2k, (1, 0.0))[1]
         d2_all = d2_ms + trn.get("k_singular_d2_" + d2k, (1, 0.0))[1]
-        neu["d2_pair_blocks_per_s"] = float(E) * E * n / (d2_all / 1e3) if d2_all else None
+        neu["d2_pair_blocks_per_s"] = float(E_x) * E_x * n_x / (d2_all / 1e3) if d2_all else None
         if d2k == "mixed":  # one exp2 per node and point, as for V, K
             neu["roofline"] = _alu_roofline(
-                "k_regular_d2_mixed", d2_ms, float(n_reg_pairs) * 81.0 * mixed_nodes_per_point(n),
+                "k_regular_d2_mixed", d2_ms, float(n_reg_pairs_x) * 81.0 * mixed_nodes_per_point(n_x),
                 "MUFU.EX2 time-node evaluations", "Tex2/s", MUFU_PEAK_TEX2,
                 "MUFU ex2 pipe, " + PEAK_SOURCE["mufu"])
         # D^1: one FP64 FMA per star pair and block, (sum of star sizes)^2 =
         # (3 E)^2 per block
         neu["roofline_d1"] = _alu_roofline(
             "k_hypersingular_d1", trn.get("k_hypersingular_d1", (1, 0.0))[1],
-            9.0 * E * E * n, "FP64 FMA (one per star pair and block)", "FMA/s",
+            9.0 * E_x * E_x * n_x, "FP64 FMA (one per star pair and block)", "FMA/s",
             FP64_PEAK_TFLOPS * 1e12 / 2, "FP64 pipe, " + PEAK_SOURCE["fp64"])
         if not args.no_cpu_baseline:  # the oracle's D^2 on whole test-triangle rows
             import oracle
-            rows = np.array([0, E // 3, E // 2])
+            rows = np.array([0, E_x // 3, E_x // 2])
             neu["cpu_baseline"] = oracle_sample(
-                lambda: oracle.assemble_d2(nodes, tris, alphas[0], wl["T"], n, test_tris=rows),
-                3.0 * E * n, "triangle-pair blocks/s",
+                lambda: oracle.assemble_d2(nodes_x, tris_x, alpha_x, wlx["T"], n_x, test_tris=rows),
+                3.0 * E_x * n_x, "triangle-pair blocks/s",
                 "D^2 of 3 test triangles (all %d trial triangles and %d blocks) of %s"
-                % (E, n, args.workload))
+                % (E_x, n_x, "cube3072_e64"))
         del pn
         torch.cuda.empty_cache()
 
@@ -938,19 +1088,35 @@ def run_gpu(args):
         e2e = {"value": world * entries * n_e2e / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": h2d // n_e2e, "d2h_bytes_per_step": d2h // n_e2e}
 
+    # the 64-problem batch of ellipsoids (its own report, outside the timed region)
+    batch = None
+    if mixed and not args.no_batch:
+        del probs, p0, y
+        torch.cuda.empty_cache()
+        batch = batch_report(pipeline, torch, stream, args.wave_gb)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "value_definition": "2 E_t E^2 V,K entries per problem / assembly time (CUDA events "
+                                "around every problem's stb_assemble call in the timed steps; "
+                                "the best step, slowest rank)",
+            "assembly_ms": {"best_step": asm_ms_best, "mean_step": asm_ms_mean,
+                            "per_step": asm_ms_steps},
+            "step_entries_per_s": step_rate,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if mixed else "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "E": E, "n_steps": n, "alphas": alphas,
                        "quad_regular": 3, "quad_singular": 4,
-                       "precision": "mixed (FP32 points, stated block error <= 2e-6; FP64 solve)"
+                       "nrhs": int(src.shape[0]),
+                       "precision": "mixed (FP32 points, stated block error <= 2e-6; solve refined "
+                                    "to 1e-10 with split-operand tensor-core residuals)"
                        if mixed else "fp64",
                        "storage": "f32" if mixed else "f64",
                        "l2": "no flush: every step writes %.1f GB of V/K blocks (>> 129 MB L2)"
                              % (2 * (4 if mixed else 8) * n * E * E * len(alphas) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "mixed_vs_fp64": cmp, "matrix_free_rhs": mfree, "p1_data": p1, "neumann": neu,
+            "mixed_vs_fp64": cmp, "batch": batch, "matrix_free_rhs": mfree, "p1_data": p1,
+            "neumann": neu,
             "potentials": pots, "nonuniform": nonuni,
             "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,
             "rel_l2_error_w": rel_err, "solve": solve_info,
@@ -975,6 +1141,40 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def batch_report(pipeline, torch, stream, wave_gb, runs=2):
+    """The 64-problem batch (ellipsoids from seed 0) through the graph-captured
+    batch pipeline, outside the headline's timed region: one warm-up run
+    (builds and tunes the graphs), then `runs` timed runs of every wave's
+    CUDA graph (batched assembly, projection, right-hand side, refined solve,
+    error)."""
+    probs = workloads.batch_workload(seed=0)
+    bp = pipeline.BatchPipeline(probs, wave_bytes=wave_gb * 1e9)
+    entries = sum(2.0 * len(p["tris"]) ** 2 * p["n_steps"] for p in probs)
+    bp.run(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(runs):
+        bp.run(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / runs
+    reports = bp.reports()
+    errs = bp.relative_errors()
+    out = {"workload": "batch64", "problems": len(probs), "waves": len(bp.waves),
+           "wave_gb": wave_gb, "entries": entries, "ms_per_batch": ms,
+           "entries_per_s": entries / (ms / 1e3),
+           "timing": "CUDA events around %d replays of every wave's graph, after a warm-up run"
+                     % runs,
+           "refinements_max": max(r for r, _, _ in reports),
+           "rel_residual_max": max(res for _, res, _ in reports),
+           "solve_status": sorted(set(st for _, _, st in reports)),
+           "rel_l2_error_w_range": [min(errs), max(errs)]}
+    del bp
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(args):
@@ -1015,6 +1215,9 @@ def run_batch(args):
     reports = bp.reports()
     errs = bp.relative_errors()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "value_definition": "2 E_t E^2 V,K entries summed over the 64 problems / time of "
+                                "one whole batch (every wave's graph: assembly, projection, "
+                                "right-hand side, refined solve, error)",
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch64", "problems": len(probs), "waves": len(bp.waves),

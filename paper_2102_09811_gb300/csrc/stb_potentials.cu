@@ -51,18 +51,19 @@ __global__ void k_time_diff(const double *__restrict__ a, int n_steps, int64_t M
 }
 
 // erfc(x) and exp(-x^2) for x >= 0 in FP32 for the mixed level values:
-// erfc(x) = exp(-x^2) P(t), t = 1 / (1 + 0.7 x), P of degree 11 fitted here
-// by least squares in relative error to the scaled complementary error
-// function exp(x^2) erfc(x) on [0, 12] (40,000 points, NumPy lstsq against
-// SciPy's erfcx); in FP32 Horner form P is within 3e-7 of it, and erfc
-// within 4e-7 + 3e-7 x^2 relative (the second term the FP32 roundings of
-// -log2(e) x^2 and of the exp2 approximation, as for exp(-x*x)); the
-// terms where that grows are of order exp(-x^2), small in every sum.
+// erfc(x) = exp(-x^2) P(t), t = 1 / (1 + 0.7 x), P of degree 11 in t fitted
+// to the scaled complementary error function exp(x^2) erfc(x) on [0, 12] in
+// relative error (weighted least squares with Lawson's reweighting; the
+// table is what fit_erfc.py beside the package prints).  In FP32 Horner form
+// P is within 3e-7 of it, and erfc within 4e-7 + 3e-7 x^2 relative (the
+// second term the FP32 roundings of -log2(e) x^2 and of the exp2
+// approximation, as for exp(-x*x)); the terms where that grows are of order
+// exp(-x^2), small in every sum.
 __device__ __forceinline__ float erfc_fit(float x, float &ee) {
-    constexpr float c[12] = {-2.728515028e-06f, 3.950394690e-01f, 3.931463063e-01f,
-                             3.149637282e-01f,  7.002895698e-03f, 2.484519631e-01f,
-                             -1.062256932e+00f, 1.017343879e+00f, -1.282700449e-01f,
-                             -4.104336798e-01f, 2.875000238e-01f, -6.248490140e-02f};
+    constexpr float c[12] = {-2.967891987e-06f, 3.950489759e-01f, 3.929870725e-01f,
+                             3.164488971e-01f,  -1.607621554e-03f, 2.811871767e-01f,
+                             -1.145935178e+00f, 1.161834598e+00f, -2.941623330e-01f,
+                             -2.893261313e-01f, 2.367079258e-01f, -5.318045616e-02f};
     const float t = __frcp_rn(fmaf(0.7f, x, 1.f));
     float P = c[11];
 #pragma unroll

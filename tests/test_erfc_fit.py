@@ -6,7 +6,12 @@ coefficients are read from the CUDA source and evaluated as the kernel does
 Bounds (the source comment's): P within 3e-7 of exp(x^2) erfc(x) in FP32,
 erfc within 4e-7 + 3e-7 x^2 relative (the second term the FP32 roundings
 of -log2(e) x^2 and of the exp2) wherever erfc is a normal FP32 number.
-NumPy's exp2 stands in for the hardware's ex2.approx here."""
+The table itself must be the one the committed fit (fit_erfc.py beside the
+package) produces.
+
+NumPy's exp2 stands in for the hardware's ex2.approx here: the error of the
+hardware instruction is covered only by the GPU tests of the mixed
+potentials, which compare the kernels' level values with the FP64 oracle."""
 import os
 import re
 
@@ -60,3 +65,18 @@ def test_special_values():
     got, _ = erfc_fit(np.array([0.0, 20.0]))
     assert abs(got[0] - 1.0) <= 3e-7
     assert got[1] == 0.0  # exp2 far below the FP32 range
+
+
+def test_table_is_the_committed_fit():
+    """The CUDA table is the fit script's output rounded to FP32 (relative
+    1e-6 leaves room for another LAPACK's last bits), and that fit meets the
+    bound by itself."""
+    import importlib.util
+    path = os.path.join(os.path.dirname(SRC), os.pardir, "fit_erfc.py")
+    spec = importlib.util.spec_from_file_location("fit_erfc", path)
+    fit_erfc = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(fit_erfc)
+    c = fit_erfc.fit()
+    src = coefficients().astype(np.float64)
+    assert np.all(np.abs(c - src) <= 1e-6 * np.abs(src)), np.abs(c / src - 1).max()
+    assert fit_erfc.max_rel_error_f32(c) <= 3e-7
