@@ -409,6 +409,14 @@ def _roofline(name, trace_entry, ms_step, n_reg_pairs, q, n_steps):
     launch_ms = tot / cnt
     pts = float(q * q) ** 2
     roof = {"kernel": name, "launch_ms": launch_ms, "share_of_step": tot / ms_step, "traffic": None}
+    # the method's own unit, independent of how a kernel evaluates the time
+    # integral: one kernel evaluation per separated ordered pair, quadrature
+    # point and time level 0..E_t (Sec. 5: each level feeds up to three blocks)
+    method = float(n_reg_pairs) * pts * (n_steps + 1)
+    roof["method_units"] = {"unit": "kernel evaluations/s", "per_launch": method,
+                            "achieved": method / (launch_ms / 1e3),
+                            "definition": "separated ordered pairs x points per pair x (E_t + 1) "
+                                          "time levels"}
     if name == "k_regular_f64":
         evals = float(n_reg_pairs) * pts * n_steps  # levels 1..E_t
         roof.update({"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,

@@ -675,8 +675,12 @@ stb_status toeplitz_split_f32x(const float *A, int64_t E, int32_t n_steps, int32
 // on the tensor cores.  Both operands are split into three bf16 slices of
 // floating (per element) exponent, a = a0 + a1 + a2 exactly for an FP32 a
 // (8 + 8 + 8 significant bits, round to nearest), and the six products with
-// i + j <= 2 are accumulated in one FP32 accumulator: about 2^-22 relative
-// per term plus the FP32 accumulation, like the FP32 march it replaces.  The
+// i + j <= 2 are accumulated in FP32 tensor memory: about 2^-22 relative per
+// term.  The tensor cores round their FP32 sums toward zero, a bias of about
+// 2^-24 of the accumulator per MMA that grows with the length of the sum, so
+// the accumulator is restarted every PN_G pieces (96 MMAs) and the group sums
+// are added in registers (round to nearest), two accumulators alternating so
+// that the MMAs of one group overlap the read-back of the one before.  The
 // x slices are kept step-major, Xf[i][(PB + m) rpad + r][j], and filled
 // panel by panel (steps not yet solved stay zero), so the B tile of block d
 // is the contiguous window of N = 8 rpad rows (at least 16) starting at
@@ -686,6 +690,7 @@ constexpr int PN_NA = 6;           // A-slice slots
 constexpr int PN_NB = 4;           // B stages
 constexpr int PN_PB = 8;           // steps per panel
 constexpr int PN_MAX_Z = 64;       // slices of the block range
+constexpr int PN_G = 4;            // pieces per tensor-memory accumulation group
 constexpr int PN_THREADS = SP_THREADS;  // warp 0 TMA, warp 1 MMA, 16 workers
 
 template <int N>
@@ -694,10 +699,11 @@ struct PanelShape {
     static constexpr uint32_t BSTAGE = PN_NS * B_BYTES;
     static constexpr uint32_t OFF_B = PN_NA * SP_A_BYTES;
     static constexpr uint32_t OFF_BAR = OFF_B + PN_NB * BSTAGE;
-    static constexpr int NBAR = 2 * PN_NB + 2 * PN_NA + 1;
+    static constexpr int NBAR = 2 * PN_NB + 2 * PN_NA + 1 + 4;
     static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
     static constexpr size_t SMEM = OFF_MISC + 16 + 1024;
-    static constexpr uint32_t TMEM_COLS = N < 32 ? 32 : N;
+    static constexpr uint32_t TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;  // two accumulators
+    static constexpr int NQ = N / 4;  // columns read back by each worker
     static constexpr uint32_t IDESC = idesc_bf16(SP_M, N);
 };
 
@@ -750,7 +756,8 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
     const uint32_t bfull = sbase + Sh::OFF_BAR, bempty = bfull + 8 * PN_NB,
-                   afull = bempty + 8 * PN_NB, aempty = afull + 8 * PN_NA, done = aempty + 8 * PN_NA;
+                   afull = bempty + 8 * PN_NB, aempty = afull + 8 * PN_NA, done = aempty + 8 * PN_NA,
+                   accf = done + 8, acce = accf + 16;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Sh::OFF_MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + Sh::OFF_MISC + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -771,6 +778,10 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
             mbar_init(aempty + 8 * s, 1);
         }
         mbar_init(done, 1);  // (panel)
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf + 8 * b, 1);
+            mbar_init(acce + 8 * b, SP_WORKERS / 32);
+        }
         *abort_flag = 0;
         mbar_init_fence();
     }
@@ -803,13 +814,21 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
         }
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) {  // MMA issuer: one accumulator for the whole block range
+        if (lane == 0) {  // MMA issuer: group g of PN_G pieces into accumulator g % 2
             for (int t = 0; t < T; ++t) {
-                const int s = t % PN_NB;
+                const int s = t % PN_NB, g = t / PN_G, b = g & 1;
+                const bool first = t % PN_G == 0;
+                if (first && g >= 2) {  // the workers have read group g - 2 back
+                    if (!mbar_wait_bounded(acce + 8 * b, ((g >> 1) - 1) & 1, a.status, abort_flag,
+                                           TC_WAIT_NS))
+                        break;
+                    tc_fence_after();
+                }
                 if (!mbar_wait_bounded(bfull + 8 * s, (t / PN_NB) & 1, a.status, abort_flag, TC_WAIT_NS))
                     break;
                 tc_fence_after();
                 const uint32_t bst = sbase + Sh::OFF_B + s * Sh::BSTAGE;
+                const uint32_t dt = tmem + (uint32_t)(b * N);
                 bool ok = true;
                 for (int i = 0; i < PN_NS; ++i) {
                     const int u = PN_NS * t + i, slot = u % PN_NA;
@@ -824,13 +843,14 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
                         const uint64_t bd = smem_desc_sw128(bst + j * Sh::B_BYTES);
 #pragma unroll
                         for (int kk = 0; kk < SP_KC / 16; ++kk)
-                            umma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, Sh::IDESC,
-                                      (t == 0 && i == 0 && j == 0 && kk == 0) ? 0u : 1u);
+                            umma_bf16(dt, ad + 2 * kk, bd + 2 * kk, Sh::IDESC,
+                                      (first && i == 0 && j == 0 && kk == 0) ? 0u : 1u);
                     }
                     umma_commit(aempty + 8 * slot);
                 }
                 if (!ok) break;
                 umma_commit(bempty + 8 * s);
+                if (t % PN_G == PN_G - 1 || t == T - 1) umma_commit(accf + 8 * b);
             }
             umma_commit(done);
         }
@@ -840,10 +860,34 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
         // (q, c4) owns tile row 32q + lane and the 16 columns j of quarter c4
         const int q = warp & 3, c4 = (warp - 2) >> 2;
         const int rl = 32 * q + lane, row = m0 + rl, jq = 16 * c4;
+        // and reads back columns [c4 NQ, c4 NQ + NQ) of the group sums
+        float sum[Sh::NQ];
+#pragma unroll
+        for (int i = 0; i < Sh::NQ; ++i) sum[i] = 0.f;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c4 * Sh::NQ);
+        auto read_group = [&](int g) {
+            const int b = g & 1;
+            bool ok = mbar_wait_bounded(accf + 8 * b, (g >> 1) & 1, a.status, abort_flag, TC_WAIT_NS);
+            ok = __all_sync(0xffffffffu, ok);
+            tc_fence_after();
+            if (ok) {
+                uint32_t v[Sh::NQ];
+                if constexpr (Sh::NQ == 16) tmem_ld16_nowait(tl + (uint32_t)(b * N), v);
+                else if constexpr (Sh::NQ == 8) tmem_ld8_nowait(tl + (uint32_t)(b * N), v);
+                else tmem_ld4_nowait(tl + (uint32_t)(b * N), v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < Sh::NQ; ++i) sum[i] += __uint_as_float(v[i]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce + 8 * b);
+        };
         float4 cur[4], nxt[4];
         load16<VEC>(a.V, a.E, d0, row, jq, cur);
         PieceIter it{d0, 0};
         for (int t = 0; t < T; ++t) {
+            if (t % PN_G == 0 && t >= 2 * PN_G) read_group(t / PN_G - 2);
             it.next(a.n_chunks);  // the next piece
             if (t + 1 < T) load16<VEC>(a.V, a.E, it.d, row, it.c * SP_KC + jq, nxt);
             uint32_t w[PN_NS][8];
@@ -872,26 +916,15 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
         }
-        // epilogue: the workers of quarter 0 hold TMEM lanes 32q.., all N columns
-        if (c4 == 0) {
-            const bool ok = mbar_wait_bounded(done, 0, a.status, abort_flag, TC_WAIT_NS);
-            tc_fence_after();
-            if (ok && !*abort_flag) {
-                const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16);
-#pragma unroll 1
-                for (int c0 = 0; c0 < N; c0 += 16) {
-                    uint32_t v[16];
-                    tmem_ld16(tb + (uint32_t)c0, v);
-                    if (row < a.E) {
+        // the last two groups, then the row's NQ columns of the slice's sum
+        const int n_groups = (T + PN_G - 1) / PN_G;
+        for (int g = max(0, n_groups - 2); g < n_groups; ++g) read_group(g);
+        if (row < a.E && !*abort_flag) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int col = c0 + i, cc = col / a.rpad, r = col % a.rpad;
-                            if (cc < a.nb && r < a.nrhs)
-                                a.part[(((size_t)blockIdx.z * a.nrhs + r) * PN_PB + cc) * a.E + row] =
-                                    __uint_as_float(v[i]);
-                        }
-                    }
-                }
+            for (int i = 0; i < Sh::NQ; ++i) {
+                const int col = c4 * Sh::NQ + i, cc = col / a.rpad, r = col % a.rpad;
+                if (cc < a.nb && r < a.nrhs)
+                    a.part[(((size_t)blockIdx.z * a.nrhs + r) * PN_PB + cc) * a.E + row] = sum[i];
             }
         }
     }
