@@ -4,10 +4,11 @@
 //     w^k = (V^0)^{-1} ( f^k - sum_{d=1}^{k} V^d w^{k-d} ),  k = 0..E_t-1.
 // V^0 is symmetric positive definite; it is factorised once, V^0 = L L^T, by
 // a right-looking blocked Cholesky (64 x 64 tiles), L is inverted blockwise
-// and (V^0)^{-1} = L^{-T} L^{-1} formed explicitly; every time step is then
-// two matrix-vector kernels: the history sum (reads the blocks V^d once, all
-// right-hand sides together) and w^k = (V^0)^{-1} r.  Steps are grouped in
-// panels of 8 whose history from earlier panels is one blocked product.
+// and (V^0)^{-1} = L^{-T} L^{-1} formed explicitly.  Steps are grouped in
+// panels of 8: the history from earlier panels is one blocked product per
+// panel, and the panel's steps -- the history sum inside the panel (reads
+// the blocks V^d once, all right-hand sides together) and w^k = (V^0)^{-1} r
+// -- run in one cooperative launch with grid barriers between the phases.
 //
 // FP64 precision: everything in FP64.
 // Mixed precision: the factorisation and the march run in FP32 and are wrapped
@@ -22,6 +23,7 @@
 #include <vector>
 
 #include "stb_dense.h"
+#include "stb_grid.cuh"
 #include "stb_internal.h"
 #include "stb_toeplitz.h"
 
@@ -35,15 +37,21 @@ __global__ void k_copy_convert(const S *__restrict__ src, size_t n, T *__restric
     if (i < n) dst[i] = (T)src[i];
 }
 
+// ---------------------------------------------- blocked Cholesky ---
+// V^0 = L L^T by 64 x 64 tiles, right-looking, all panels in one cooperative
+// launch: for each tile column kb, (1) CTA 0 factorises the diagonal tile,
+// (2) the tiles below it are solved against it, (3) the trailing tiles are
+// updated, grid barriers between the phases.  L is read with __ldcg (other
+// CTAs wrote it in this launch).
+
 // Cholesky of diagonal tile kb (updates from the left already applied).
 template <class T>
-__global__ void __launch_bounds__(256) k_potrf_diag(T *__restrict__ L, int E, int kb,
-                                                    int32_t *__restrict__ status) {
-    __shared__ T Tt[NB][NB + 1];
+__device__ void potrf_tile(T *__restrict__ L, int E, int kb, int32_t *__restrict__ status,
+                           T (*Tt)[NB + 1]) {
     const int b0 = kb * NB, n = min(NB, E - b0);
     for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
         int i = t / NB, j = t % NB;
-        Tt[i][j] = (i < n && j < n && j <= i) ? L[(size_t)(b0 + i) * E + b0 + j] : (T)0;
+        Tt[i][j] = (i < n && j < n && j <= i) ? __ldcg(L + (size_t)(b0 + i) * E + b0 + j) : (T)0;
     }
     __syncthreads();
     for (int c = 0; c < n; ++c) {
@@ -72,17 +80,17 @@ __global__ void __launch_bounds__(256) k_potrf_diag(T *__restrict__ L, int E, in
     }
 }
 
-// Panel: L_ik = A_ik L_kk^{-T} for the tile rows i > kb.
+// Panel: L_ik = A_ik L_kk^{-T} for tile row i = kb + 1 + bi.
 template <class T>
-__global__ void __launch_bounds__(128) k_trsm_panel(T *__restrict__ L, int E, int kb) {
-    __shared__ T Lk[NB][NB + 1];
-    __shared__ T A[NB][NB + 1];
+__device__ void trsm_tile(T *__restrict__ L, int E, int kb, int bi, T (*Lk)[NB + 1],
+                          T (*A)[NB + 1]) {
     const int b0 = kb * NB, n = min(NB, E - b0);
-    const int i0 = (kb + 1 + blockIdx.x) * NB, mrows = min(NB, E - i0);
+    const int i0 = (kb + 1 + bi) * NB, mrows = min(NB, E - i0);
+    __syncthreads();  // the shared tiles of the previous task are consumed
     for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
         int i = t / NB, j = t % NB;
-        Lk[i][j] = (i < n && j < n) ? L[(size_t)(b0 + i) * E + b0 + j] : (T)0;
-        A[i][j] = (i < mrows && j < n) ? L[(size_t)(i0 + i) * E + b0 + j] : (T)0;
+        Lk[i][j] = (i < n && j < n) ? __ldcg(L + (size_t)(b0 + i) * E + b0 + j) : (T)0;
+        A[i][j] = (i < mrows && j < n) ? __ldcg(L + (size_t)(i0 + i) * E + b0 + j) : (T)0;
     }
     __syncthreads();
     for (int row = threadIdx.x; row < mrows; row += blockDim.x) {
@@ -100,12 +108,13 @@ __global__ void __launch_bounds__(128) k_trsm_panel(T *__restrict__ L, int E, in
 }
 
 // 64x64 tile product helper: acc (4x4 per thread, 256 threads) +=
-// P (rows of the tile) * Q^T, both read from global in 32-wide chunks.
+// P (rows of the tile) * Q^T, both read from global in 32-wide chunks (CG:
+// through L2 only, for data other CTAs of the launch wrote).
 template <class T> struct TileAcc {
     T v[4][4];
 };
 
-template <class T>
+template <class T, bool CG = false>
 __device__ __forceinline__ void tile_mma_abt(TileAcc<T> &acc, const T *P, size_t ldp, int prow,
                                              int pcol, const T *Q, size_t ldq, int qrow, int qcol,
                                              int E, int kn, T (*Ps)[33], T (*Qs)[33]) {
@@ -115,8 +124,14 @@ __device__ __forceinline__ void tile_mma_abt(TileAcc<T> &acc, const T *P, size_t
         for (int t = threadIdx.x; t < NB * 32; t += blockDim.x) {
             int r = t / 32, kk = t % 32;
             int pr = prow + r, qr = qrow + r, pc = pcol + k0 + kk, qc = qcol + k0 + kk;
-            Ps[r][kk] = (pr < E && k0 + kk < kn) ? P[(size_t)pr * ldp + pc] : (T)0;
-            Qs[r][kk] = (qr < E && k0 + kk < kn) ? Q[(size_t)qr * ldq + qc] : (T)0;
+            const T *pp = P + (size_t)pr * ldp + pc, *qp = Q + (size_t)qr * ldq + qc;
+            if constexpr (CG) {
+                Ps[r][kk] = (pr < E && k0 + kk < kn) ? __ldcg(pp) : (T)0;
+                Qs[r][kk] = (qr < E && k0 + kk < kn) ? __ldcg(qp) : (T)0;
+            } else {
+                Ps[r][kk] = (pr < E && k0 + kk < kn) ? *pp : (T)0;
+                Qs[r][kk] = (qr < E && k0 + kk < kn) ? *qp : (T)0;
+            }
         }
         __syncthreads();
 #pragma unroll 4
@@ -136,11 +151,9 @@ __device__ __forceinline__ void tile_mma_abt(TileAcc<T> &acc, const T *P, size_t
     }
 }
 
-// Trailing update A_ij -= L_ik L_jk^T for kb < j <= i.
+// Trailing update A_ij -= L_ik L_jk^T for the t-th tile pair kb < j <= i.
 template <class T>
-__global__ void __launch_bounds__(256) k_syrk_update(T *__restrict__ L, int E, int kb) {
-    __shared__ T Ps[NB][33], Qs[NB][33];
-    const int t = blockIdx.x;
+__device__ void syrk_tile(T *__restrict__ L, int E, int kb, int t, T (*Ps)[33], T (*Qs)[33]) {
     int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
     while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
     while (ii * (ii + 1) / 2 > t) --ii;
@@ -152,13 +165,40 @@ __global__ void __launch_bounds__(256) k_syrk_update(T *__restrict__ L, int E, i
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc.v[u][v] = (T)0;
-    tile_mma_abt<T>(acc, L, E, i0, b0, L, E, j0, b0, E, kn, Ps, Qs);
+    __syncthreads();  // the shared tiles of the previous task are consumed
+    tile_mma_abt<T, true>(acc, L, E, i0, b0, L, E, j0, b0, E, kn, Ps, Qs);
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     for (int u = 0; u < 4; ++u)
         for (int v = 0; v < 4; ++v) {
             int r = i0 + 4 * ty + u, c = j0 + 4 * tx + v;
-            if (r < E && c < E) L[(size_t)r * E + c] -= acc.v[u][v];
+            if (r < E && c < E) L[(size_t)r * E + c] = __ldcg(L + (size_t)r * E + c) - acc.v[u][v];
         }
+}
+
+template <class T>
+constexpr size_t potrf_smem() {
+    return 2 * (size_t)NB * (NB + 1) * sizeof(T);  // the largest phase: two tiles of trsm
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_potrf_coop(T *__restrict__ L, int E, int nb,
+                                                    int32_t *__restrict__ status, unsigned *bar) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    T(*T1)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(fsm);
+    T(*T2)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(fsm + (size_t)NB * (NB + 1) * sizeof(T));
+    T(*Ps)[33] = reinterpret_cast<T(*)[33]>(fsm);
+    T(*Qs)[33] = reinterpret_cast<T(*)[33]>(fsm + (size_t)NB * 33 * sizeof(T));
+    for (int kb = 0; kb < nb; ++kb) {
+        if (blockIdx.x == 0) potrf_tile<T>(L, E, kb, status, T1);
+        if (!grid_barrier(bar, status)) return;
+        const int m = nb - kb - 1;
+        if (m == 0) break;
+        for (int bi = blockIdx.x; bi < m; bi += gridDim.x) trsm_tile<T>(L, E, kb, bi, T1, T2);
+        if (!grid_barrier(bar, status)) return;
+        const int tiles = m * (m + 1) / 2;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x) syrk_tile<T>(L, E, kb, t, Ps, Qs);
+        if (!grid_barrier(bar, status)) return;
+    }
 }
 
 // (V^0)^{-1} = L^{-T} L^{-1} from U = L^{-T} (upper triangular):
@@ -350,55 +390,6 @@ __global__ void k_transpose(const T *__restrict__ A, T *__restrict__ B, int E) {
 
 constexpr int MAXR = 8;  // right-hand sides per pass of the march kernels
 
-// rv_r[l] = base_r[l] - sum_{d=1}^{dmax} V^d[l,:] x_r^{k-d}: one warp per row
-// l, all right-hand sides of the group [r0, r0 + nr) together so that each
-// V^d row is read once.  AT: storage of V; T: arithmetic of the march.
-template <class AT, class T>
-__global__ void __launch_bounds__(256)
-k_history(const AT *__restrict__ V, int E, int n_steps, int r0, int nr, int k, int dmax,
-          const double *__restrict__ base, size_t base_rstride, size_t base_off,
-          const T *__restrict__ x, T *__restrict__ rv) {
-    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (l >= E) return;
-    T acc[MAXR];
-#pragma unroll
-    for (int r = 0; r < MAXR; ++r) acc[r] = (T)0;
-    const size_t EE = (size_t)E * E, SE = (size_t)n_steps * E;
-    constexpr int U = 8;  // independent loads in flight per lane
-    for (int d = 1; d <= dmax; ++d) {
-        const AT *row = V + d * EE + (size_t)l * E;
-        const T *wk = x + (size_t)(k - d) * E;
-        int j0 = 0;
-        for (; j0 + 32 * U <= E; j0 += 32 * U) {
-            T v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = (T)row[j0 + 32 * u + lane];
-#pragma unroll
-            for (int r = 0; r < MAXR; ++r)
-                if (r < nr) {
-                    const T *wr = wk + (size_t)(r0 + r) * SE + j0 + lane;
-#pragma unroll
-                    for (int u = 0; u < U; ++u) acc[r] = fma(v[u], wr[32 * u], acc[r]);
-                }
-        }
-        for (int j = j0 + lane; j < E; j += 32) {
-            T v = (T)row[j];
-#pragma unroll
-            for (int r = 0; r < MAXR; ++r)
-                if (r < nr) acc[r] = fma(v, wk[(size_t)(r0 + r) * SE + j], acc[r]);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < MAXR; ++r) {
-        if (r >= nr) break;
-        T a = acc[r];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0)
-            rv[(size_t)(r0 + r) * E + l] =
-                (T)(base[(size_t)(r0 + r) * base_rstride + base_off + l] - (double)a);
-    }
-}
-
 // Far history of a panel of PB steps k = kp + c (c < nb): all contributions
 // of the steps before the panel,
 //   sum_{d : 0 <= k-d < kp} V^d[l,:] x_r^{k-d},
@@ -498,6 +489,163 @@ __global__ void k_far_reduce(const T *__restrict__ part, int nz, int E, int n_st
     double s = 0.0;
     for (int z = 0; z < nz; ++z) s += (double)part[(((size_t)z * nrhs + r) * PB + c) * E + l];
     hv[((size_t)r * PB + c) * E + l] = f[(size_t)r * n_steps * E + (size_t)(kp + c) * E + l] - s;
+}
+
+// ------------------------------------------------ the steps of a panel ---
+// One cooperative launch per panel of PB steps k = kp + c (c < nb):
+//   phase 1: rv_r = hv_r^c - sum_{d=1}^{c} V^d x_r^{k-d}   (history inside the panel)
+//   grid barrier
+//   phase 2: x_r^k = (V^0)^{-1} rv_r
+//   grid barrier (not after the last step)
+// A CTA owns blocks of 8 warps x MP_RW rows (grid-stride); the vectors of a
+// phase (x^{k-d}, or rv) are staged in shared memory chunk by chunk by the
+// whole CTA, read from L2 (__ldcg: other CTAs wrote them in this launch), and
+// each warp streams its rows of the matrix against them, four consecutive
+// columns per lane and load, MP_MR right-hand sides per pass.
+constexpr int MP_THREADS = 256;
+constexpr int MP_RW = 2;  // rows per warp
+constexpr int MP_MR = 8;  // right-hand sides per pass
+// columns per staged chunk: 16 (FP64: 8) per lane and row, 2 KB of an FP32 row
+template <class AT, class T>
+constexpr int mp_chunk() { return (sizeof(AT) == 8 || sizeof(T) == 8) ? 256 : 512; }
+
+// four consecutive T from L2 (bypassing L1), VEC: 16-byte aligned and in range
+template <class T, bool VEC>
+__device__ __forceinline__ void load4_cg(const T *p, int left, T v[4]) {
+    if constexpr (VEC && sizeof(T) == 4) {
+        const float4 q = __ldcg(reinterpret_cast<const float4 *>(p));
+        v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+    } else if constexpr (VEC) {
+        const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+        const double2 b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = u < left ? __ldcg(p + u) : (T)0;
+    }
+}
+
+// acc[i][r] += sum_j Mat[l0 + i][j] vec_r[j] (this lane's columns; rows past
+// E re-read row E-1 and are never stored), vec_r = vec + r vstride, r < nr.
+template <class MT, class T, int JC, bool VEC>
+__device__ __forceinline__ void mp_pass(const MT *__restrict__ mat, int E, int l0, const T *vec,
+                                        size_t vstride, int nr, T *stage, T (&acc)[MP_RW][MP_MR]) {
+    constexpr int G = JC / 128;  // groups of four columns per lane
+    const int lane = threadIdx.x & 31;
+    for (int j0 = 0; j0 < E; j0 += JC) {
+        const int jn = min(JC, E - j0);
+        __syncthreads();  // the previous chunk is consumed
+        for (int t = threadIdx.x; t < nr * (JC / 4); t += MP_THREADS) {
+            const int r = t / (JC / 4), jj = 4 * (t % (JC / 4));
+            T v[4] = {(T)0, (T)0, (T)0, (T)0};
+            if (jj < jn) load4_cg<T, VEC>(vec + r * vstride + j0 + jj, jn - jj, v);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) stage[r * JC + jj + u] = v[u];
+        }
+        __syncthreads();
+        T m[MP_RW][G][4];
+#pragma unroll
+        for (int i = 0; i < MP_RW; ++i)
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int jj = 128 * g + 4 * lane;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) m[i][g][u] = (T)0;
+                if (jj < jn)
+                    load4<MT, T, VEC>(mat + (size_t)min(l0 + i, E - 1) * E + j0 + jj, jn - jj,
+                                      m[i][g]);
+            }
+#pragma unroll
+        for (int r = 0; r < MP_MR; ++r) {
+            if (r >= nr) break;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const T *xs = stage + r * JC + 128 * g + 4 * lane;
+                T xv[4];
+                if constexpr (sizeof(T) == 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(xs);
+                    xv[0] = q.x, xv[1] = q.y, xv[2] = q.z, xv[3] = q.w;
+                } else {
+                    const double2 a = reinterpret_cast<const double2 *>(xs)[0];
+                    const double2 b = reinterpret_cast<const double2 *>(xs)[1];
+                    xv[0] = a.x, xv[1] = a.y, xv[2] = b.x, xv[3] = b.y;
+                }
+#pragma unroll
+                for (int i = 0; i < MP_RW; ++i)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[i][r] = fma(m[i][g][u], xv[u], acc[i][r]);
+            }
+        }
+    }
+}
+
+// sums over the warp; lane i MP_MR + r ends up holding (row i, rhs r)
+template <class T>
+__device__ __forceinline__ T mp_reduce(T (&acc)[MP_RW][MP_MR]) {
+    const int lane = threadIdx.x & 31;
+    T mine = (T)0;
+#pragma unroll
+    for (int i = 0; i < MP_RW; ++i)
+#pragma unroll
+        for (int r = 0; r < MP_MR; ++r) {
+            T a = acc[i][r];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == i * MP_MR + r) mine = a;
+        }
+    return mine;
+}
+
+template <class AT, class T, bool VEC>
+__global__ void __launch_bounds__(MP_THREADS)
+k_march_panel(const AT *__restrict__ V, const T *__restrict__ Minv, int E, int n_steps, int nrhs,
+              int kp, int nb, const double *__restrict__ hv, T *rv, T *x, unsigned *bar,
+              int32_t *status) {
+    constexpr int JC = mp_chunk<AT, T>();
+    static_assert(MP_RW * MP_MR <= 32, "one lane per (row, right-hand side)");
+    __shared__ __align__(16) T stage[MP_MR * JC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rows_cta = 8 * MP_RW, n_rb = (E + rows_cta - 1) / rows_cta;
+    const size_t EE = (size_t)E * E, SE = (size_t)n_steps * E;
+    const int li = lane / MP_MR, lr = lane % MP_MR;  // this lane's (row, rhs) of a pass
+    for (int c = 0; c < nb; ++c) {
+        const int k = kp + c;
+        for (int rb = blockIdx.x; rb < n_rb; rb += gridDim.x) {
+            const int l0 = rb * rows_cta + warp * MP_RW;
+            for (int r0 = 0; r0 < nrhs; r0 += MP_MR) {
+                const int nr = min(MP_MR, nrhs - r0);
+                T acc[MP_RW][MP_MR];
+#pragma unroll
+                for (int i = 0; i < MP_RW; ++i)
+#pragma unroll
+                    for (int r = 0; r < MP_MR; ++r) acc[i][r] = (T)0;
+                for (int d = 1; d <= c; ++d)
+                    mp_pass<AT, T, JC, VEC>(V + d * EE, E, l0, x + r0 * SE + (size_t)(k - d) * E, SE,
+                                            nr, stage, acc);
+                const T a = mp_reduce(acc);
+                const int l = l0 + li;
+                if (li < MP_RW && lr < nr && l < E)
+                    rv[(size_t)(r0 + lr) * E + l] =
+                        (T)(hv[((size_t)(r0 + lr) * PB + c) * E + l] - (double)a);
+            }
+        }
+        if (!grid_barrier(bar, status)) return;
+        for (int rb = blockIdx.x; rb < n_rb; rb += gridDim.x) {
+            const int l0 = rb * rows_cta + warp * MP_RW;
+            for (int r0 = 0; r0 < nrhs; r0 += MP_MR) {
+                const int nr = min(MP_MR, nrhs - r0);
+                T acc[MP_RW][MP_MR];
+#pragma unroll
+                for (int i = 0; i < MP_RW; ++i)
+#pragma unroll
+                    for (int r = 0; r < MP_MR; ++r) acc[i][r] = (T)0;
+                mp_pass<T, T, JC, VEC>(Minv, E, l0, rv + (size_t)r0 * E, E, nr, stage, acc);
+                const T a = mp_reduce(acc);
+                const int l = l0 + li;
+                if (li < MP_RW && lr < nr && l < E) x[(size_t)(r0 + lr) * SE + (size_t)k * E + l] = a;
+            }
+        }
+        if (c + 1 < nb && !grid_barrier(bar, status)) return;
+    }
 }
 
 // out_r[l] = sum_j M[l][j] in_r[j] over j >= l (part TRI_UPPER), j <= l
@@ -612,6 +760,7 @@ struct SolveLayout {
     void *df;                     // mixed: scratch of the split residual product
     double *norms;                // mixed: ||r||^2, ||f||^2
     void *xf;                     // mixed, <= 8 right-hand sides: x slices of the tensor-core far history
+    unsigned *bar;                // grid barrier words of the cooperative march
     int32_t *status;              // device status word of the call
     size_t bytes;
 };
@@ -630,6 +779,7 @@ static SolveLayout solve_layout(int64_t E, int n_steps, int nrhs, bool mixed, vo
                                                           : FAR_NZ;
     S.part = c.take<char>((size_t)nz_max * nrhs * PB * E * tb);
     S.tasks = c.take<int4>(inv_task_count((int)((E + NB - 1) / NB)));
+    S.bar = c.take<unsigned>(4);
     if (mixed) {
         const size_t n = (size_t)nrhs * n_steps * E;
         S.delta = c.take<float>(n);
@@ -654,18 +804,21 @@ static stb_status factorize(const AT *V, int E, const SolveLayout &S, int32_t *s
     k_copy_convert<AT, T><<<(unsigned)((EE + 255) / 256), 256, 0, s>>>(V, EE, L);
     if ((st = check_launch("k_copy_convert"))) return st;
     const int nb = (E + NB - 1) / NB;
-    for (int kb = 0; kb < nb; ++kb) {
+    {  // the blocked Cholesky: one cooperative launch (2 CTAs per SM at most)
+        const size_t smem = potrf_smem<T>();
+        STB_CUDA(cudaFuncSetAttribute(k_potrf_coop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        const int most = nb > 1 ? std::max(nb - 1, (nb - 1) * nb / 2) : 1;
+        const int grid = std::min(most, coop_grid(k_potrf_coop<T>, 256, smem, 2));
+        if (grid < 1) return fail(STB_ERR_CUDA, "factorisation: no resident grid for k_potrf_coop");
+        STB_CUDA(grid_barrier_reset(S.bar, s));
         count_launch(s);
-        k_potrf_diag<T><<<1, 256, 0, s>>>(L, E, kb, status);
-        if ((st = check_launch("k_potrf_diag"))) return st;
-        const int m = nb - kb - 1;
-        if (m == 0) break;
-        count_launch(s);
-        k_trsm_panel<T><<<m, 128, 0, s>>>(L, E, kb);
-        if ((st = check_launch("k_trsm_panel"))) return st;
-        count_launch(s);
-        k_syrk_update<T><<<m * (m + 1) / 2, 256, 0, s>>>(L, E, kb);
-        if ((st = check_launch("k_syrk_update"))) return st;
+        if (cudaError_t e = launch_coop(k_potrf_coop<T>, (unsigned)grid, 256, smem, s, L, E, nb,
+                                        status, S.bar)) {
+            cudaGetLastError();
+            return fail(STB_ERR_CUDA, "k_potrf_coop: %s", cudaGetErrorString(e));
+        }
+        if ((st = check_launch("k_potrf_coop"))) return st;
     }
     STB_CUDA(cudaMemsetAsync(Li, 0, EE * sizeof(T), s));
     count_launch(s);
@@ -708,14 +861,14 @@ static stb_status factorize(const AT *V, int E, const SolveLayout &S, int32_t *s
 }
 
 // March in time: x^k = L^{-T} L^{-1} (rhs^k - sum_{d>=1} V^d x^{k-d}) into x
-// (T), in panels of PB steps: one far-history pass per panel, then per step
-// the near history (d < PB, inside the panel) and the two triangular products.
+// (T), in panels of PB steps: one far-history pass per panel (the blocks of
+// the steps before the panel), then one cooperative launch for the panel's
+// steps (the near history inside the panel and the product with (V^0)^{-1},
+// step after step, separated by grid barriers).
 template <class AT, class T>
 static stb_status march(const AT *V, int E, int n_steps, int nrhs, const double *rhs, T *x,
                         const SolveLayout &S, cudaStream_t s) {
     stb_status st;
-    const unsigned rows_blocks = (unsigned)((E * 32 + 255) / 256);
-    const size_t SE = (size_t)n_steps * E;
     T *rv = (T *)S.rv, *part = (T *)S.part;
     const bool vec = E % 4 == 0 && reinterpret_cast<uintptr_t>(V) % 16 == 0 &&
                      reinterpret_cast<uintptr_t>(x) % 16 == 0;
@@ -725,6 +878,15 @@ static stb_status march(const AT *V, int E, int n_steps, int nrhs, const double 
     constexpr bool f32 = sizeof(AT) == 4 && sizeof(T) == 4;
     const bool tc = f32 && S.xf != nullptr;
     if (tc && (st = panel_tc_begin(E, n_steps, nrhs, S.xf, s))) return st;
+    // the cooperative panel kernel: as many CTAs as row blocks, at most what
+    // can be resident at once (4 per SM)
+    const bool mp_vec = vec && reinterpret_cast<uintptr_t>(S.L) % 16 == 0 &&
+                        reinterpret_cast<uintptr_t>(S.rv) % 16 == 0;
+    const auto mp_kern = mp_vec ? k_march_panel<AT, T, true> : k_march_panel<AT, T, false>;
+    const int mp_rows = (E + 8 * MP_RW - 1) / (8 * MP_RW);
+    const int mp_grid = std::min(mp_rows, coop_grid(mp_kern, MP_THREADS, 0, 4));
+    if (mp_grid < 1) return fail(STB_ERR_CUDA, "march: no resident grid for k_march_panel");
+    STB_CUDA(grid_barrier_reset(S.bar, s));
     for (int kp = 0; kp < n_steps; kp += PB) {
         const int nb = min(PB, n_steps - kp);
         int nz = 0;
@@ -753,20 +915,15 @@ static stb_status march(const AT *V, int E, int n_steps, int nrhs, const double 
         k_far_reduce<T><<<(unsigned)((nred + 255) / 256), 256, 0, s>>>(part, nz, E, n_steps, nrhs, kp, nb,
                                                                        rhs, S.hv);
         if ((st = check_launch("k_far_reduce"))) return st;
-        for (int c = 0; c < nb; ++c) {
-            const int k = kp + c;
-            for (int r0 = 0; r0 < nrhs; r0 += MAXR) {
-                count_launch(s);
-                k_history<AT, T><<<rows_blocks, 256, 0, s>>>(V, E, n_steps, r0, min(MAXR, nrhs - r0),
-                                                             k, c, S.hv, (size_t)PB * E,
-                                                             (size_t)c * E, x, rv);
-                if ((st = check_launch("k_history"))) return st;
-            }
-            count_launch(s);
-            k_trmv<T><<<rows_blocks, 256, 0, s>>>((const T *)S.L, E, nrhs, FULL, rv, E,
-                                                  x + (size_t)k * E, SE);
-            if ((st = check_launch("k_matvec((V^0)^-1)"))) return st;
+        // the panel's steps: near history and (V^0)^{-1}, one cooperative launch
+        count_launch(s);
+        if (cudaError_t e = launch_coop(mp_kern, (unsigned)mp_grid, MP_THREADS, 0, s, V,
+                                        (const T *)S.L, E, n_steps, nrhs, kp, nb, (const double *)S.hv,
+                                        rv, x, S.bar, S.status)) {
+            cudaGetLastError();
+            return fail(STB_ERR_CUDA, "k_march_panel: %s", cudaGetErrorString(e));
         }
+        if ((st = check_launch("k_march_panel"))) return st;
     }
     return STB_OK;
 }
