@@ -141,12 +141,15 @@ stb_status stb_assemble(const stb_mesh *mesh, const stb_params *params, void *V,
  * Mixed-precision assembly (eq. V_mat / eq. K_mat blocks, as stb_assemble with
  * STB_PREC_MIXED and STB_STORE_F32) of n independent problems, each with its
  * own mesh, parameters (alpha, T, n_steps, quadrature orders) and output
- * blocks.  The separated pairs of all problems run in one persistent launch
- * whose CTAs claim (problem, row, block of `tile` columns) work items from a
- * device counter, so meshes of uneven size and step count share the SMs; the
- * touching pairs of all problems run in one more launch.  Per problem there
- * are in addition three small set-up launches (geometry, classification).
- * tile: columns per work item, 64, 128 or 256; 0 = the value stb_batch_tune
+ * blocks.  All pair classes of all problems run in one persistent launch
+ * whose CTAs claim work items from a device counter: first every touching
+ * pair (identical, shared edge, shared vertex; one item each), then the
+ * separated pairs as (problem, row, block of `tile` columns), so meshes of
+ * uneven size and step count share the SMs.  Per problem there are in
+ * addition three small set-up launches (geometry, classification).
+ * tile: columns per work item (= threads per CTA), 128 or 256; the touching
+ * pairs run on 128 threads of a CTA either way, so every tile writes the
+ * same blocks as stb_assemble; 0 = the value stb_batch_tune
  * chose on this device for a batch of the same shape (128 if none).
  * The workspace is shared by all items (stb_batch_workspace_size). */
 typedef struct {

@@ -98,8 +98,8 @@ stb_status run_nu_singular_mixed(const Mesh &m, const stb_params &p, const doubl
                                  const float *d_cf, int n_cf, const float *d_nodes, int n_nodes,
                                  const int32_t *d_targets, double *V, double *K, cudaStream_t s);
 
-// Batched mixed assembly (one persistent launch for the separated pairs of
-// all problems, one launch for their touching pairs).  upload_batch copies
+// Batched mixed assembly (one persistent launch for all pair classes of all
+// problems: the touching pairs first, then the separated pairs).  upload_batch copies
 // the problems' descriptors for work items of `tile` columns (host memory,
 // not capturable); launch_batch only launches (capturable).
 struct BatchDesc;

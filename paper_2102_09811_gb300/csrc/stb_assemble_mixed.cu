@@ -20,6 +20,7 @@
 //    two blocks (d = k, k + 1).
 // The regularised rules of touching pairs are stored in difference form so
 // that x - y keeps its relative accuracy as it shrinks.
+#include <climits>
 #include <cmath>
 #include <vector>
 
@@ -351,17 +352,21 @@ struct MixSS {
     int n[4];
 };
 
-// All blocks of the touching pair P (both orders) of one problem: one CTA of
-// MSS_THREADS threads shares the points of the regularised rule.
+// All blocks of the touching pair P (both orders) of one problem: the first
+// NTH threads of the CTA (at least 3 CH + 9) share the points of the
+// regularised rule; further threads of a larger CTA take part only in its
+// barriers, so the sums (and their rounding) do not depend on the CTA size.
 // kp (optional): instead of K, the pair's K blocks go to kp[d] (entry (a,b))
 // and kp[n_steps + d] (entry (b,a)).
-template <int CH, class OutT>
+template <int CH, class OutT, int NTH = MSS_THREADS>
 __device__ __forceinline__ void singular_pair_mixed(const double *__restrict__ geo,
                                                     const TouchPair P, int E, const MixSS &tab,
                                                     const float *__restrict__ nodes, int n_steps,
                                                     const MixConsts &g, OutT *__restrict__ V,
                                                     OutT *__restrict__ K, float *kp = nullptr) {
-    __shared__ float red[MSS_THREADS / 32][3 * CH + 9];
+    static_assert(NTH % 32 == 0 && NTH >= 3 * CH + 9, "one thread per reduced value");
+    __shared__ float red[NTH / 32][3 * CH + 9];
+    const int p_first = threadIdx.x < NTH ? (int)threadIdx.x : INT_MAX;  // first rule point
     __shared__ float fin[3 * CH + 9];
     const int a = P.a, b = P.b, cls = P.cls;
     if (a < 0 || b < a || b >= E || cls < PAIR_VERTEX || cls > PAIR_IDENTICAL) return;
@@ -407,12 +412,12 @@ __device__ __forceinline__ void singular_pair_mixed(const double *__restrict__ g
         for (int k = 0; k < nv; ++k) {
             float v = vals[k];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp][k] = v;
+            if (lane == 0 && warp < NTH / 32) red[warp][k] = v;
         }
         __syncthreads();
         if (threadIdx.x < nv) {
             float s = 0.f;
-            for (int wi = 0; wi < MSS_THREADS / 32; ++wi) s += red[wi][threadIdx.x];
+            for (int wi = 0; wi < NTH / 32; ++wi) s += red[wi][threadIdx.x];
             fin[threadIdx.x] = scale * s;
         }
         __syncthreads();
@@ -422,7 +427,7 @@ __device__ __forceinline__ void singular_pair_mixed(const double *__restrict__ g
     float z[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) z[i] = 0.f;
-    for (int p = threadIdx.x; p < npt; p += MSS_THREADS) {
+    for (int p = p_first; p < npt; p += NTH) {
         float rr, rab, rba, w;
         point(p, rr, rab, rba, w);
         const float irho = rsqrtf(rr), rho = rr * irho;
@@ -478,7 +483,7 @@ __device__ __forceinline__ void singular_pair_mixed(const double *__restrict__ g
 #pragma unroll
         for (int i = 0; i < 3 * S; ++i) acc[i] = 0.f;
         const int ng = mixed_chunk_ng(d0);
-        for (int p = threadIdx.x; p < npt; p += MSS_THREADS) {
+        for (int p = p_first; p < npt; p += NTH) {
             float rr, rab, rba, w;
             point(p, rr, rab, rba, w);
             if (ng == 4) ss_chunk<4, CH>(ntab, d0, n_steps, rr, w, w * rab, w * rba, acc);
@@ -1683,12 +1688,14 @@ stb_status run_vrhs_mixed(const Mesh &m, const stb_params &p, float *V, const do
 
 // -------------------------------------------------------------- batches ---
 // Many independent problems (meshes, alpha, steps) in one persistent launch
-// for their separated pairs and one launch for their touching pairs, all in
-// mixed precision with FP32 storage.  The work items of the persistent
-// kernel are (problem, row l, block of NT columns), numbered problem by
-// problem; every CTA claims items from a global counter, so problems of
-// uneven size and step count balance across the SMs, and a CTA reloads the
-// time-node table only when its next item belongs to another problem.
+// for all their pair classes, mixed precision with FP32 storage.  The work
+// items are, first, every touching pair of every problem (the costly items:
+// a regularised 4-D rule per pair; put first so that none of them is left
+// for the tail), then the separated pairs as (problem, row l, block of NT
+// columns), numbered problem by problem.  Every CTA claims items from a
+// global counter, so problems of uneven size and step count balance across
+// the SMs, and a CTA reloads the time-node table only when its next
+// separated-pair item belongs to another problem.
 struct BatchDesc {
     const double *geo;
     const int32_t *tris;
@@ -1697,25 +1704,36 @@ struct BatchDesc {
     float *V, *K;
     MixSS ss;
     MixConsts g;
-    long long item0;  // first work item of this problem
+    long long item0;  // first separated-pair work item of this problem
     int E, nq, n_steps, n_nodes_f, jblocks, touch0, n_touch, pad;
 };
 
-template <int NT>
+// n_touch: touching-pair items (0 to leave them out); n_items: separated-pair
+// items; stride > 1 runs every stride-th item only (timing samples).
+template <int NT>  // 128 or 256: the touching pairs run on the first 128 threads
 __global__ void __launch_bounds__(NT)
-k_regular_mixed_batch(const BatchDesc *__restrict__ descs, int n_desc, long long n_items,
-                      int stride, unsigned long long *__restrict__ counter) {
+k_mixed_batch(const BatchDesc *__restrict__ descs, int n_desc, long long n_touch,
+              long long n_items, int stride, unsigned long long *__restrict__ counter) {
     extern __shared__ float smf[];
     float4 *xa = reinterpret_cast<float4 *>(smf);
     float *nd = smf + 4 * MAX_RULE_M;
     __shared__ long long s_item;
-    __shared__ int s_prob;
+    __shared__ int s_prob, s_touch;
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) {
-            const long long it = (long long)atomicAdd(counter, 1ull) * stride;
-            int pr = -1;
-            if (it < n_items) {  // last problem whose first item is <= it
+            long long it = (long long)atomicAdd(counter, 1ull) * stride;
+            int pr = -1, touch = 0;
+            if (it < n_touch) {  // last problem whose first touching pair is <= it
+                int lo = 0, hi = n_desc - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (descs[mid].touch0 <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                pr = lo;
+                touch = 1;
+            } else if ((it -= n_touch) < n_items) {  // last problem whose first item is <= it
                 int lo = 0, hi = n_desc - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
@@ -1726,12 +1744,24 @@ k_regular_mixed_batch(const BatchDesc *__restrict__ descs, int n_desc, long long
             }
             s_item = it;
             s_prob = pr;
+            s_touch = touch;
         }
         __syncthreads();
         const long long it = s_item;
         const int pr = s_prob;
         if (pr < 0) break;
         const BatchDesc &D = descs[pr];
+        if (s_touch) {
+            const int b = (int)(it - D.touch0);
+            if (b < D.n_touch) {
+                const MixSS ss = D.ss;
+                const MixConsts g = D.g;
+                singular_pair_mixed<MIX_CH, float, MSS_THREADS>(D.geo, D.pairs[b], D.E, ss, D.nodes,
+                                                                D.n_steps, g, D.V, D.K);
+            }
+            __syncthreads();  // the reduction arrays are reused by the next item
+            continue;
+        }
         const long long local = it - D.item0;
         const int l = (int)(local / D.jblocks), jb = (int)(local % D.jblocks);
         if (pr != cur) {
@@ -1750,43 +1780,25 @@ k_regular_mixed_batch(const BatchDesc *__restrict__ descs, int n_desc, long long
     }
 }
 
-__global__ void __launch_bounds__(MSS_THREADS)
-k_singular_mixed_batch(const BatchDesc *__restrict__ descs, int n_desc) {
-    const int b = blockIdx.x;
-    int lo = 0, hi = n_desc - 1;  // last problem whose first touching pair is <= b
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (descs[mid].touch0 <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    const BatchDesc &D = descs[lo];
-    if (b - D.touch0 >= D.n_touch) return;
-    const MixSS ss = D.ss;
-    const MixConsts g = D.g;
-    singular_pair_mixed<MIX_CH, float>(D.geo, D.pairs[b - D.touch0], D.E, ss, D.nodes, D.n_steps, g,
-                                       D.V, D.K);
-}
-
 size_t batch_desc_bytes(int n) { return align256((size_t)n * sizeof(BatchDesc)); }
 
 template <int NT>
-static stb_status launch_batch_regular(const BatchDesc *d_descs, int n, long long n_items,
-                                       int stride, unsigned long long *counter, size_t smem,
-                                       cudaStream_t s) {
-    STB_CUDA(cudaFuncSetAttribute(k_regular_mixed_batch<NT>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+static stb_status launch_batch_kernel(const BatchDesc *d_descs, int n, long long n_touch,
+                                      long long n_items, int stride, unsigned long long *counter,
+                                      size_t smem, cudaStream_t s) {
+    STB_CUDA(cudaFuncSetAttribute(k_mixed_batch<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
     int per_sm = 0, dev = 0, sms = 0;
     STB_CUDA(cudaGetDevice(&dev));
     STB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    STB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_regular_mixed_batch<NT>, NT,
-                                                           smem));
+    STB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mixed_batch<NT>, NT, smem));
     if (per_sm < 1) return fail(STB_ERR_CUDA, "batched kernel does not fit on an SM");
-    const long long claims = (n_items + stride - 1) / stride;
+    const long long claims = (n_touch + n_items + stride - 1) / stride;
     const long long grid = std::min<long long>((long long)sms * per_sm, std::max(1LL, claims));
     STB_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
     count_launch(s);
-    k_regular_mixed_batch<NT><<<(unsigned)grid, NT, smem, s>>>(d_descs, n, n_items, stride, counter);
-    return check_launch("k_regular_mixed_batch");
+    k_mixed_batch<NT><<<(unsigned)grid, NT, smem, s>>>(d_descs, n, n_touch, n_items, stride, counter);
+    return check_launch("k_mixed_batch");
 }
 
 // Descriptors of problem i (prepared by prepare_mixed into layouts[i]) for
@@ -1838,7 +1850,7 @@ stb_status upload_batch(const Mesh *const *meshes, const stb_params *params,
     return STB_OK;
 }
 
-// Launches only (descriptors uploaded by upload_batch with the same tile).
+// One launch (descriptors uploaded by upload_batch with the same tile).
 // stride > 1 runs every stride-th work item of the separated pairs and no
 // touching pairs (timing samples of the tile tuner).
 stb_status launch_batch(const Mesh *const *meshes, const stb_params *params,
@@ -1850,13 +1862,9 @@ stb_status launch_batch(const Mesh *const *meshes, const stb_params *params,
     int touch, max_nf;
     batch_descs(meshes, params, layouts, V, K, n, tile, h, items, touch, max_nf);
     const size_t smem = sizeof(float) * (4 * MAX_RULE_M + (size_t)max_nf);
-    stb_status st = tile == 64    ? launch_batch_regular<64>(d_descs, n, items, stride, counter, smem, s)
-                    : tile == 256 ? launch_batch_regular<256>(d_descs, n, items, stride, counter, smem, s)
-                                  : launch_batch_regular<128>(d_descs, n, items, stride, counter, smem, s);
-    if (st || stride > 1 || touch == 0) return st;
-    count_launch(s);
-    k_singular_mixed_batch<<<(unsigned)touch, MSS_THREADS, 0, s>>>(d_descs, n);
-    return check_launch("k_singular_mixed_batch");
+    const long long n_touch = stride > 1 ? 0 : touch;
+    return tile == 256 ? launch_batch_kernel<256>(d_descs, n, n_touch, items, stride, counter, smem, s)
+                       : launch_batch_kernel<128>(d_descs, n, n_touch, items, stride, counter, smem, s);
 }
 
 }  // namespace stb

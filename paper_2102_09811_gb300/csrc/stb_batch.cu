@@ -142,8 +142,8 @@ static stb_status batch_enter(const stb_batch_item *items, int32_t n, int32_t ti
                               size_t ws_bytes, BatchLayout &B) {
     stb_status st = batch_check(items, n);
     if (st) return st;
-    if (tile != 0 && tile != 64 && tile != 128 && tile != 256)
-        return fail(STB_ERR_INVALID_ARG, "tile must be 0, 64, 128 or 256");
+    if (tile != 0 && tile != 128 && tile != 256)
+        return fail(STB_ERR_INVALID_ARG, "tile must be 0, 128 or 256");
     B = batch_layout(items, n, ws, ws_bytes);
     return check_workspace(ws, ws_bytes, B.bytes);
 }
@@ -187,10 +187,10 @@ extern "C" stb_status stb_batch_tune(const stb_batch_item *items, int32_t n, voi
     cudaEvent_t e0, e1;
     STB_CUDA(cudaEventCreate(&e0));
     STB_CUDA(cudaEventCreate(&e1));
-    const int cand[3] = {64, 128, 256};
+    const int cand[2] = {128, 256};
     int best = 128;
     float best_ms = 0.f;
-    for (int c = 0; c < 3 && !st; ++c) {
+    for (int c = 0; c < 2 && !st; ++c) {
         st = upload_batch(A.meshes.data(), A.params.data(), B.items.data(), A.V.data(),
                           A.K.data(), n, B.descs, cand[c], s);
         if (!st) st = batch_launch(B, A, n, cand[c], 16, s);  // warm-up of this instantiation

@@ -45,38 +45,63 @@ __global__ void k_copy_convert(const S *__restrict__ src, size_t n, T *__restric
 // CTAs wrote it in this launch).
 
 // Cholesky of diagonal tile kb (updates from the left already applied).
+// Each thread keeps its elements of the tile's lower triangle (linear index
+// tid + 256 u) in registers through all 64 column steps; step c subtracts
+// a_ic a_jc / a_cc from the trailing elements (j > c) with the raw column c,
+// whose owners published it in shared memory after its last update, so a
+// step needs one barrier.  At the end a_ij / sqrt(a_jj) (i > j) and
+// sqrt(a_jj) are the entries of L.
+constexpr int POTRF_THREADS = 256;
+constexpr int POTRF_SLOTS = (NB * (NB + 1) / 2 + POTRF_THREADS - 1) / POTRF_THREADS;
 template <class T>
 __device__ void potrf_tile(T *__restrict__ L, int E, int kb, int32_t *__restrict__ status,
-                           T (*Tt)[NB + 1]) {
+                           T (*col)[NB], T *piv) {
     const int b0 = kb * NB, n = min(NB, E - b0);
-    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
-        int i = t / NB, j = t % NB;
-        Tt[i][j] = (i < n && j < n && j <= i) ? __ldcg(L + (size_t)(b0 + i) * E + b0 + j) : (T)0;
+    T val[POTRF_SLOTS];
+    int ri[POTRF_SLOTS], ci[POTRF_SLOTS];
+#pragma unroll
+    for (int u = 0; u < POTRF_SLOTS; ++u) {
+        const int t = threadIdx.x + POTRF_THREADS * u;
+        int i = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);  // row of the t-th lower element
+        while ((i + 1) * (i + 2) / 2 <= t) ++i;
+        while (i * (i + 1) / 2 > t) --i;
+        const int j = t - i * (i + 1) / 2;
+        const bool in = t < NB * (NB + 1) / 2 && i < n;
+        ri[u] = in ? i : NB;  // NB: not an element of this tile
+        ci[u] = in ? j : NB;
+        val[u] = in ? __ldcg(L + (size_t)(b0 + i) * E + b0 + j) : (T)0;
+        if (in && j == 0) col[0][i] = val[u];
     }
     __syncthreads();
     for (int c = 0; c < n; ++c) {
-        if (threadIdx.x == 0) {
-            T p = Tt[c][c];
-            if (!(p > (T)0)) {
-                atomicCAS(status, 0, STB_ERR_NOT_SPD);
-                p = (T)1;
-            }
-            Tt[c][c] = sqrt(p);
+        const T(*cc)[NB] = col + (c & 1);
+        T d = (*cc)[c];
+        if (!(d > (T)0)) {
+            if (threadIdx.x == 0) atomicCAS(status, 0, STB_ERR_NOT_SPD);
+            d = (T)1;
         }
-        __syncthreads();
-        const T inv = (T)1 / Tt[c][c];
-        for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) Tt[i][c] *= inv;
-        __syncthreads();
-        const int m = n - c - 1;  // trailing size
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            int i = c + 1 + t / m, j = c + 1 + t % m;
-            if (j <= i) Tt[i][j] = fma(-Tt[i][c], Tt[j][c], Tt[i][j]);
+        if (threadIdx.x == 0) piv[c] = d;
+        const T inv = (T)1 / d;
+#pragma unroll
+        for (int u = 0; u < POTRF_SLOTS; ++u) {
+            if (ci[u] > c && ci[u] < NB) {
+                val[u] = fma(-(*cc)[ri[u]] * inv, (*cc)[ci[u]], val[u]);
+                if (ci[u] == c + 1) col[(c + 1) & 1][ri[u]] = val[u];
+            }
         }
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-        int i = t / n, j = t % n;
-        L[(size_t)(b0 + i) * E + b0 + j] = j <= i ? Tt[i][j] : (T)0;
+#pragma unroll
+    for (int u = 0; u < POTRF_SLOTS; ++u) {
+        const int i = ri[u], j = ci[u];
+        if (i < NB) {
+            const T sj = sqrt(piv[j]);
+            L[(size_t)(b0 + i) * E + b0 + j] = i == j ? sj : val[u] / sj;
+        }
+    }
+    for (int t = threadIdx.x; t < n * n; t += POTRF_THREADS) {  // the strict upper triangle
+        const int i = t / n, j = t % n;
+        if (j > i) L[(size_t)(b0 + i) * E + b0 + j] = (T)0;
     }
 }
 
@@ -184,12 +209,13 @@ template <class T>
 __global__ void __launch_bounds__(256) k_potrf_coop(T *__restrict__ L, int E, int nb,
                                                     int32_t *__restrict__ status, unsigned *bar) {
     extern __shared__ __align__(16) unsigned char fsm[];
+    __shared__ T col[2][NB], piv[NB];
     T(*T1)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(fsm);
     T(*T2)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(fsm + (size_t)NB * (NB + 1) * sizeof(T));
     T(*Ps)[33] = reinterpret_cast<T(*)[33]>(fsm);
     T(*Qs)[33] = reinterpret_cast<T(*)[33]>(fsm + (size_t)NB * 33 * sizeof(T));
     for (int kb = 0; kb < nb; ++kb) {
-        if (blockIdx.x == 0) potrf_tile<T>(L, E, kb, status, T1);
+        if (blockIdx.x == 0) potrf_tile<T>(L, E, kb, status, col, piv);
         if (!grid_barrier(bar, status)) return;
         const int m = nb - kb - 1;
         if (m == 0) break;
@@ -804,12 +830,12 @@ static stb_status factorize(const AT *V, int E, const SolveLayout &S, int32_t *s
     k_copy_convert<AT, T><<<(unsigned)((EE + 255) / 256), 256, 0, s>>>(V, EE, L);
     if ((st = check_launch("k_copy_convert"))) return st;
     const int nb = (E + NB - 1) / NB;
-    {  // the blocked Cholesky: one cooperative launch (2 CTAs per SM at most)
+    {  // the blocked Cholesky: one cooperative launch (4 CTAs per SM at most)
         const size_t smem = potrf_smem<T>();
         STB_CUDA(cudaFuncSetAttribute(k_potrf_coop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         const int most = nb > 1 ? std::max(nb - 1, (nb - 1) * nb / 2) : 1;
-        const int grid = std::min(most, coop_grid(k_potrf_coop<T>, 256, smem, 2));
+        const int grid = std::min(most, coop_grid(k_potrf_coop<T>, 256, smem, 4));
         if (grid < 1) return fail(STB_ERR_CUDA, "factorisation: no resident grid for k_potrf_coop");
         STB_CUDA(grid_barrier_reset(S.bar, s));
         count_launch(s);
