@@ -40,7 +40,10 @@
 // CTA = 128 rows x one box x a range of blocks d; 18 warps:
 //   warp 0: TMA producer of the x slices (2-stage ring of 5 tiles),
 //   warp 1: tensor-memory allocation (512 columns: 2 buffers x 4 levels x 64)
-//   and MMA issuer (kind::f16, bf16 operands, M = 128, N = 64, K = 16),
+//   and MMA issuer (kind::f16, bf16 operands, M = 128, K = 16; A slice i
+//   meets x slices 0 .. 3-i in one MMA of N = 64 (4 - i), the levels i .. 3
+//   being adjacent accumulators, and x slice 4-i in one of N = 64: nine MMAs
+//   per 16 columns instead of fifteen, fewer re-reads of the A tile),
 //   warps 2..9: slicers -- each thread loads 32 columns of one row of the
 //   next 64-column piece of A (prefetched into L2) and forms their five
 //   slices into a 6-slot ring,
@@ -350,16 +353,28 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const SplitArgs a) {
                     }
                     tc_fence_after();
                     const uint64_t ad = smem_desc_sw128(sbase + slot * SP_A_BYTES);
-                    for (int j = 0; j < SP_NS - i; ++j) {
-                        const int lvl = min(i + j, SP_NL - 1);
-                        const uint32_t dt = tmem + (uint32_t)(buf * SP_NL * SP_N + lvl * SP_N);
-                        const uint64_t bd = smem_desc_sw128(bst + j * SP_B_BYTES);
-                        // the first product of each level in a chunk overwrites it
-                        const bool fresh = first && i == 0 && j < SP_NL;
+                    // A slice i against x slices 0 .. 3-i: the levels i .. 3 are
+                    // adjacent accumulators and the x slices adjacent tiles, so the
+                    // products are one MMA of N = 64 (4 - i) (the i = 0 MMA of a
+                    // chunk's first k step overwrites all four levels)
+                    const int nlev = SP_NL - i;
+                    if (nlev > 0) {
+                        const uint32_t dt = tmem + (uint32_t)(buf * SP_NL * SP_N + i * SP_N);
+                        const uint64_t bd = smem_desc_sw128(bst);
+                        const uint32_t idn = idesc_bf16(SP_M, SP_N * nlev);
 #pragma unroll
                         for (int kk = 0; kk < SP_KC / 16; ++kk)  // 16 bf16 = 32 bytes: +2
-                            umma_bf16(dt, ad + 2 * kk, bd + 2 * kk, SP_IDESC,
-                                      (fresh && kk == 0) ? 0u : 1u);
+                            umma_bf16(dt, ad + 2 * kk, bd + 2 * kk, idn,
+                                      (first && i == 0 && kk == 0) ? 0u : 1u);
+                    }
+                    {  // level 4: x slice 4-i into the level-3 accumulator
+                        const int j = SP_NS - 1 - i;
+                        const uint32_t dt =
+                            tmem + (uint32_t)(buf * SP_NL * SP_N + (SP_NL - 1) * SP_N);
+                        const uint64_t bd = smem_desc_sw128(bst + j * SP_B_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < SP_KC / 16; ++kk)
+                            umma_bf16(dt, ad + 2 * kk, bd + 2 * kk, SP_IDESC, 1u);
                     }
                     umma_commit(aempty + 8 * slot);  // the slot is free once read
                 }
@@ -675,12 +690,15 @@ stb_status toeplitz_split_f32x(const float *A, int64_t E, int32_t n_steps, int32
 // on the tensor cores.  Both operands are split into three bf16 slices of
 // floating (per element) exponent, a = a0 + a1 + a2 exactly for an FP32 a
 // (8 + 8 + 8 significant bits, round to nearest), and the six products with
-// i + j <= 2 are accumulated in FP32 tensor memory: about 2^-22 relative per
-// term.  The tensor cores round their FP32 sums toward zero, a bias of about
-// 2^-24 of the accumulator per MMA that grows with the length of the sum, so
-// the accumulator is restarted every PN_G pieces (96 MMAs) and the group sums
-// are added in registers (round to nearest), two accumulators alternating so
-// that the MMAs of one group overlap the read-back of the one before.  The
+// i + j <= 2 are accumulated in FP32 tensor memory, one accumulator per level
+// s = i + j (adjacent, so that A slice i meets x slices 0 .. 2-i in one MMA
+// of N (3 - i) columns): about 2^-22 relative per term.  The tensor cores
+// round their FP32 sums toward zero, a bias of about 2^-24 of the
+// accumulator per MMA that grows with the length of the sum, so the
+// accumulators are restarted every PN_G pieces (at most 48 MMAs into a level)
+// and the group sums are added in registers (round to nearest), two sets
+// alternating so that the MMAs of one group overlap the read-back of the one
+// before.  The
 // x slices are kept step-major, Xf[i][(PB + m) rpad + r][j], and filled
 // panel by panel (steps not yet solved stay zero), so the B tile of block d
 // is the contiguous window of N = 8 rpad rows (at least 16) starting at
@@ -702,9 +720,10 @@ struct PanelShape {
     static constexpr int NBAR = 2 * PN_NB + 2 * PN_NA + 1 + 4;
     static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
     static constexpr size_t SMEM = OFF_MISC + 16 + 1024;
-    static constexpr uint32_t TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;  // two accumulators
+    // two sets of three level accumulators (a power of two of at least 32 columns)
+    static constexpr uint32_t TMEM_COLS = 6 * N <= 32 ? 32 : 6 * N <= 64 ? 64 : 6 * N <= 128 ? 128
+                                        : 6 * N <= 256 ? 256 : 512;
     static constexpr int NQ = N / 4;  // columns read back by each worker
-    static constexpr uint32_t IDESC = idesc_bf16(SP_M, N);
 };
 
 struct PanelArgs {
@@ -828,7 +847,6 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
                     break;
                 tc_fence_after();
                 const uint32_t bst = sbase + Sh::OFF_B + s * Sh::BSTAGE;
-                const uint32_t dt = tmem + (uint32_t)(b * N);
                 bool ok = true;
                 for (int i = 0; i < PN_NS; ++i) {
                     const int u = PN_NS * t + i, slot = u % PN_NA;
@@ -839,13 +857,15 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
                     }
                     tc_fence_after();
                     const uint64_t ad = smem_desc_sw128(sbase + slot * SP_A_BYTES);
-                    for (int j = 0; j < PN_NS - i; ++j) {
-                        const uint64_t bd = smem_desc_sw128(bst + j * Sh::B_BYTES);
+                    // levels i .. 2 of set b from x slices 0 .. 2-i (the i = 0 MMA
+                    // of a group's first k step overwrites all three levels)
+                    const uint32_t dt = tmem + (uint32_t)((3 * b + i) * N);
+                    const uint64_t bd = smem_desc_sw128(bst);
+                    const uint32_t idn = idesc_bf16(SP_M, N * (PN_NS - i));
 #pragma unroll
-                        for (int kk = 0; kk < SP_KC / 16; ++kk)
-                            umma_bf16(dt, ad + 2 * kk, bd + 2 * kk, Sh::IDESC,
-                                      (first && i == 0 && j == 0 && kk == 0) ? 0u : 1u);
-                    }
+                    for (int kk = 0; kk < SP_KC / 16; ++kk)
+                        umma_bf16(dt, ad + 2 * kk, bd + 2 * kk, idn,
+                                  (first && i == 0 && kk == 0) ? 0u : 1u);
                     umma_commit(aempty + 8 * slot);
                 }
                 if (!ok) break;
@@ -870,14 +890,23 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
             bool ok = mbar_wait_bounded(accf + 8 * b, (g >> 1) & 1, a.status, abort_flag, TC_WAIT_NS);
             ok = __all_sync(0xffffffffu, ok);
             tc_fence_after();
-            if (ok) {
-                uint32_t v[Sh::NQ];
-                if constexpr (Sh::NQ == 16) tmem_ld16_nowait(tl + (uint32_t)(b * N), v);
-                else if constexpr (Sh::NQ == 8) tmem_ld8_nowait(tl + (uint32_t)(b * N), v);
-                else tmem_ld4_nowait(tl + (uint32_t)(b * N), v);
-                tmem_wait_ld();
+            if (ok) {  // the three levels, at most 8 columns at a time
+                constexpr int W = Sh::NQ < 8 ? Sh::NQ : 8;
 #pragma unroll
-                for (int i = 0; i < Sh::NQ; ++i) sum[i] += __uint_as_float(v[i]);
+                for (int c0 = 0; c0 < Sh::NQ; c0 += W) {
+                    uint32_t v[3][W];
+#pragma unroll
+                    for (int l = 0; l < 3; ++l) {
+                        const uint32_t ta = tl + (uint32_t)((3 * b + l) * N + c0);
+                        if constexpr (W == 8) tmem_ld8_nowait(ta, v[l]);
+                        else tmem_ld4_nowait(ta, v[l]);
+                    }
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < W; ++i)
+                        sum[c0 + i] += (__uint_as_float(v[2][i]) + __uint_as_float(v[1][i])) +
+                                       __uint_as_float(v[0][i]);
+                }
             }
             tc_fence_before();
             __syncwarp();
