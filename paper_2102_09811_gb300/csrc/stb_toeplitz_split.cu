@@ -46,7 +46,7 @@
 //   per 16 columns instead of fifteen, fewer re-reads of the A tile),
 //   warps 2..9: slicers -- each thread loads 32 columns of one row of the
 //   next 64-column piece of A (prefetched into L2) and forms their five
-//   slices into a 6-slot ring,
+//   slices into a 7-slot ring,
 //   warps 10..17: read-back -- each thread owns one tile row (TMEM lane) and
 //   32 output columns and adds every chunk's four accumulators to its
 //   running sums (high parts in registers, low parts in shared memory).
@@ -73,7 +73,7 @@ constexpr int SP_PPC = SP_RC / SP_KC;  // pieces per chunk
 constexpr int SP_E1 = SP_PPC == 2 ? 1 : 0;
 constexpr int SP_NS = 5;        // slices per operand
 constexpr int SP_NL = 4;        // accumulators per buffer (levels 0, 1, 2, 3+4)
-constexpr int SP_NA = 6;        // A-slice slots
+constexpr int SP_NA = 7;        // A-slice slots (the shared memory left after the x stages)
 constexpr int SP_SLICERS = 256;   // 8 slicer warps: 32 columns j of one row each
 constexpr int SP_READERS = 256;   // 8 read-back warps: 2 per TMEM lane quarter, 32 columns each
 constexpr int SP_WORKERS = SP_SLICERS + SP_READERS;
@@ -81,11 +81,11 @@ constexpr int SP_THREADS = 64 + SP_WORKERS;
 constexpr uint32_t SP_A_BYTES = SP_M * SP_KC * 2;          // 16 KB
 constexpr uint32_t SP_B_BYTES = SP_N * SP_KC * 2;          // 8 KB per slice
 constexpr uint32_t SP_BSTAGE = SP_NS * SP_B_BYTES;         // 40 KB
-constexpr uint32_t SP_OFF_B = SP_NA * SP_A_BYTES;          // 96 KB
+constexpr uint32_t SP_OFF_B = SP_NA * SP_A_BYTES;          // 112 KB
 // low parts of the read-back's running sums, float2 [32 column pairs][128 rows]
-constexpr uint32_t SP_OFF_AL = SP_OFF_B + 2 * SP_BSTAGE;   // 176 KB
-constexpr uint32_t SP_OFF_BAR = SP_OFF_AL + (SP_N / 2) * SP_M * 8;  // 208 KB
-// barriers: bfull[2] bempty[2] afull[6] aempty[6] accfull[2] accempty[2] drain
+constexpr uint32_t SP_OFF_AL = SP_OFF_B + 2 * SP_BSTAGE;   // 192 KB
+constexpr uint32_t SP_OFF_BAR = SP_OFF_AL + (SP_N / 2) * SP_M * 8;  // 224 KB
+// barriers: bfull[2] bempty[2] afull[SP_NA] aempty[SP_NA] accfull[2] accempty[2] drain
 constexpr int SP_NBAR = 2 + 2 + SP_NA + SP_NA + 2 + 2 + 1;
 constexpr uint32_t SP_OFF_MISC = SP_OFF_BAR + SP_NBAR * 8;
 constexpr size_t SP_SMEM = SP_OFF_MISC + 16 + 1024;  // + alignment slack
