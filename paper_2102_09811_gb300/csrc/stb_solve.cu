@@ -902,7 +902,7 @@ static stb_status march(const AT *V, int E, int n_steps, int nrhs, const double 
     const unsigned far_rows = (unsigned)((E + rows_cta - 1) / rows_cta);
     // FP32 blocks and FP32 march: the far history on the tensor cores
     constexpr bool f32 = sizeof(AT) == 4 && sizeof(T) == 4;
-    const bool tc = f32 && S.xf != nullptr;
+    const bool tc = f32 && S.xf != nullptr && panel_tc_blocks_ok((const float *)V, E);
     if (tc && (st = panel_tc_begin(E, n_steps, nrhs, S.xf, s))) return st;
     // the cooperative panel kernel: as many CTAs as row blocks, at most what
     // can be resident at once (4 per SM)

@@ -66,6 +66,7 @@ stb_status toeplitz_split_f32x(const float *A, int64_t E, int32_t n_steps, int32
 // panel_tc_begin before the first panel of a march; each call slices the
 // steps kp-8 .. kp-1 (panels in order).
 bool panel_tc_supported(int32_t nrhs);
+bool panel_tc_blocks_ok(const float *V, int64_t E);
 size_t panel_tc_bytes(int64_t E, int32_t n_steps, int32_t nrhs);
 int panel_tc_max_slices();
 stb_status panel_tc_begin(int64_t E, int32_t n_steps, int32_t nrhs, void *xf, cudaStream_t s);

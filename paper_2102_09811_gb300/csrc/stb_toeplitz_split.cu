@@ -202,32 +202,6 @@ struct SplitArgs {
     int E, n_steps, nrhs, rpad, lg_rpad, S, rowsX, n_sub, n_rc, dr_len;
 };
 
-// 16 consecutive entries j0 .. j0+15 of row `row` of block d (zero outside)
-template <bool VEC>
-__device__ __forceinline__ void load16(const float *A, int E, int d, int row, int j0,
-                                       float4 (&v)[4]) {
-    if (row >= E) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    const float *p = A + ((size_t)d * E + row) * E + j0;
-    if (VEC) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            v[q] = j0 + 4 * q < E ? __ldg(reinterpret_cast<const float4 *>(p) + q)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = j0 + 4 * q;
-            v[q] = make_float4(j < E ? __ldg(p + 4 * q) : 0.f, j + 1 < E ? __ldg(p + 4 * q + 1) : 0.f,
-                               j + 2 < E ? __ldg(p + 4 * q + 2) : 0.f,
-                               j + 3 < E ? __ldg(p + 4 * q + 3) : 0.f);
-        }
-    }
-}
-
 // 32 consecutive entries j0 .. j0+31 of row `row` of block d (zero outside)
 template <bool VEC>
 __device__ __forceinline__ void load32(const float *A, int E, int d, int row, int j0,
@@ -703,9 +677,11 @@ stb_status toeplitz_split_f32x(const float *A, int64_t E, int32_t n_steps, int32
 // panel by panel (steps not yet solved stay zero), so the B tile of block d
 // is the contiguous window of N = 8 rpad rows (at least 16) starting at
 // (PB + kp - d) rpad.
+// The FP32 A tiles (128 rows x 64 columns of a block) come by TMA, in two
+// 32-column halves with the 128-byte swizzle, into a ring of FP32 stages;
+// the workers slice them from shared memory into the bf16 slot ring.
 constexpr int PN_NS = 3;
 constexpr int PN_NA = 6;           // A-slice slots
-constexpr int PN_NB = 4;           // B stages
 constexpr int PN_PB = 8;           // steps per panel
 constexpr int PN_MAX_Z = 64;       // slices of the block range
 constexpr int PN_G = 4;            // pieces per tensor-memory accumulation group
@@ -713,17 +689,23 @@ constexpr int PN_THREADS = SP_THREADS;  // warp 0 TMA, warp 1 MMA, 16 workers
 
 template <int N>
 struct PanelShape {
+    static constexpr int NB = N == 64 ? 2 : 4;    // x-slice stages
+    static constexpr int NF = N == 16 ? 3 : 2;    // FP32 A stages
     static constexpr uint32_t B_BYTES = N * 128;                  // one slice tile
     static constexpr uint32_t BSTAGE = PN_NS * B_BYTES;
-    static constexpr uint32_t OFF_B = PN_NA * SP_A_BYTES;
-    static constexpr uint32_t OFF_BAR = OFF_B + PN_NB * BSTAGE;
-    static constexpr int NBAR = 2 * PN_NB + 2 * PN_NA + 1 + 4;
+    static constexpr uint32_t F_HALF = SP_M * 128;                // 32 FP32 columns
+    static constexpr uint32_t F_BYTES = 2 * F_HALF;               // one FP32 A tile
+    static constexpr uint32_t OFF_F = PN_NA * SP_A_BYTES;
+    static constexpr uint32_t OFF_B = OFF_F + NF * F_BYTES;
+    static constexpr uint32_t OFF_BAR = OFF_B + NB * BSTAGE;
+    static constexpr int NBAR = 2 * NB + 2 * PN_NA + 1 + 4 + 2 * NF;
     static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
     static constexpr size_t SMEM = OFF_MISC + 16 + 1024;
     // two sets of three level accumulators (a power of two of at least 32 columns)
     static constexpr uint32_t TMEM_COLS = 6 * N <= 32 ? 32 : 6 * N <= 64 ? 64 : 6 * N <= 128 ? 128
                                         : 6 * N <= 256 ? 256 : 512;
     static constexpr int NQ = N / 4;  // columns read back by each worker
+    static_assert(SMEM <= 232448, "shared memory of the panel product");
 };
 
 struct PanelArgs {
@@ -766,17 +748,18 @@ __global__ void k_panel_split_x(const float *__restrict__ x, int E, int E_pad, i
         *reinterpret_cast<uint32_t *>(Xf + ((size_t)s * rowsX + R) * E_pad + j) = w[s];
 }
 
-template <bool VEC, int N>
+template <int N>
 __global__ void __launch_bounds__(PN_THREADS, 1)
-k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
+k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapA,
+                 const PanelArgs a) {
     using Sh = PanelShape<N>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bfull = sbase + Sh::OFF_BAR, bempty = bfull + 8 * PN_NB,
-                   afull = bempty + 8 * PN_NB, aempty = afull + 8 * PN_NA, done = aempty + 8 * PN_NA,
-                   accf = done + 8, acce = accf + 16;
+    const uint32_t bfull = sbase + Sh::OFF_BAR, bempty = bfull + 8 * Sh::NB,
+                   afull = bempty + 8 * Sh::NB, aempty = afull + 8 * PN_NA, done = aempty + 8 * PN_NA,
+                   accf = done + 8, acce = accf + 16, ffull = acce + 16, fempty = ffull + 8 * Sh::NF;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Sh::OFF_MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + Sh::OFF_MISC + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -788,9 +771,13 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
     const int T = (d1 - d0) * a.n_chunks;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < PN_NB; ++s) {
+        for (int s = 0; s < Sh::NB; ++s) {
             mbar_init(bfull + 8 * s, 1);
             mbar_init(bempty + 8 * s, 1);
+        }
+        for (int s = 0; s < Sh::NF; ++s) {
+            mbar_init(ffull + 8 * s, 1);
+            mbar_init(fempty + 8 * s, SP_WORKERS / 32);
         }
         for (int s = 0; s < PN_NA; ++s) {
             mbar_init(afull + 8 * s, SP_WORKERS / 32);
@@ -811,14 +798,24 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {  // TMA producer of the x slices
+        if (lane == 0) {  // TMA producer of the FP32 A tiles and the x slices
             int issued = 0;
             PieceIter it{d0, 0};
             for (int t = 0; t < T; ++t, it.next(a.n_chunks)) {
-                const int s = t % PN_NB, u = t / PN_NB;
+                const int d = it.d, c = it.c;
+                const int f = t % Sh::NF;
+                if (!mbar_wait_bounded(fempty + 8 * f, ((t / Sh::NF) & 1) ^ 1, a.status, abort_flag,
+                                       TC_WAIT_NS))
+                    break;
+                const uint32_t fdst = sbase + Sh::OFF_F + f * Sh::F_BYTES;
+                mbar_expect_tx(ffull + 8 * f, Sh::F_BYTES);
+                // rows past E of the last row tile read the next block's rows
+                // (or the tensor's zero fill), never stored
+                tma_load_2d(fdst, &mapA, c * SP_KC, d * a.E + m0, ffull + 8 * f);
+                tma_load_2d(fdst + Sh::F_HALF, &mapA, c * SP_KC + 32, d * a.E + m0, ffull + 8 * f);
+                const int s = t % Sh::NB, u = t / Sh::NB;
                 if (!mbar_wait_bounded(bempty + 8 * s, (u & 1) ^ 1, a.status, abort_flag, TC_WAIT_NS))
                     break;
-                const int d = it.d, c = it.c;
                 const uint32_t dst = sbase + Sh::OFF_B + s * Sh::BSTAGE;
                 const int y0 = (PN_PB + a.kp - d) * a.rpad;
                 mbar_expect_tx(bfull + 8 * s, Sh::BSTAGE);
@@ -827,15 +824,19 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
                     tma_load_2d(dst + i * Sh::B_BYTES, &mapX, c * SP_KC, i * a.rowsX + y0, bfull + 8 * s);
                 issued = t + 1;
             }
-            for (int t = max(0, issued - PN_NB); t < issued; ++t)
-                mbar_wait_bounded(bfull + 8 * (t % PN_NB), (t / PN_NB) & 1, a.status, nullptr,
+            // the copies still in flight have landed before the CTA may exit
+            for (int t = max(0, issued - Sh::NB); t < issued; ++t)
+                mbar_wait_bounded(bfull + 8 * (t % Sh::NB), (t / Sh::NB) & 1, a.status, nullptr,
+                                  TC_WAIT_NS);
+            for (int t = max(0, issued - Sh::NF); t < issued; ++t)
+                mbar_wait_bounded(ffull + 8 * (t % Sh::NF), (t / Sh::NF) & 1, a.status, nullptr,
                                   TC_WAIT_NS);
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer: group g of PN_G pieces into accumulator g % 2
             for (int t = 0; t < T; ++t) {
-                const int s = t % PN_NB, g = t / PN_G, b = g & 1;
+                const int s = t % Sh::NB, g = t / PN_G, b = g & 1;
                 const bool first = t % PN_G == 0;
                 if (first && g >= 2) {  // the workers have read group g - 2 back
                     if (!mbar_wait_bounded(acce + 8 * b, ((g >> 1) - 1) & 1, a.status, abort_flag,
@@ -843,7 +844,7 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
                         break;
                     tc_fence_after();
                 }
-                if (!mbar_wait_bounded(bfull + 8 * s, (t / PN_NB) & 1, a.status, abort_flag, TC_WAIT_NS))
+                if (!mbar_wait_bounded(bfull + 8 * s, (t / Sh::NB) & 1, a.status, abort_flag, TC_WAIT_NS))
                     break;
                 tc_fence_after();
                 const uint32_t bst = sbase + Sh::OFF_B + s * Sh::BSTAGE;
@@ -879,7 +880,7 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
         // workers: slice the A chunks (three floating bf16 slices); worker
         // (q, c4) owns tile row 32q + lane and the 16 columns j of quarter c4
         const int q = warp & 3, c4 = (warp - 2) >> 2;
-        const int rl = 32 * q + lane, row = m0 + rl, jq = 16 * c4;
+        const int rl = 32 * q + lane, row = m0 + rl, jq = 16 * c4;  // jq: first column
         // and reads back columns [c4 NQ, c4 NQ + NQ) of the group sums
         float sum[Sh::NQ];
 #pragma unroll
@@ -912,13 +913,25 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
             __syncwarp();
             if (lane == 0) mbar_arrive(acce + 8 * b);
         };
-        float4 cur[4], nxt[4];
-        load16<VEC>(a.V, a.E, d0, row, jq, cur);
-        PieceIter it{d0, 0};
         for (int t = 0; t < T; ++t) {
             if (t % PN_G == 0 && t >= 2 * PN_G) read_group(t / PN_G - 2);
-            it.next(a.n_chunks);  // the next piece
-            if (t + 1 < T) load16<VEC>(a.V, a.E, it.d, row, it.c * SP_KC + jq, nxt);
+            // this thread's 16 FP32 values of the staged A tile: half c4 / 2,
+            // 16-byte chunks 4 (c4 % 2) .. +3 of row rl, stored at chunk ^ (rl % 8)
+            float4 cur[4];
+            {
+                const int f = t % Sh::NF;
+                const bool ok = mbar_wait_bounded(ffull + 8 * f, (t / Sh::NF) & 1, a.status,
+                                                  abort_flag, TC_WAIT_NS);
+                const unsigned char *half =
+                    smem + Sh::OFF_F + f * Sh::F_BYTES + (c4 >> 1) * Sh::F_HALF + rl * 128;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    cur[k] = ok ? *reinterpret_cast<const float4 *>(
+                                      half + (((4 * (c4 & 1) + k) ^ (rl & 7)) << 4))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(fempty + 8 * f);
+            }
             uint32_t w[PN_NS][8];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -942,8 +955,6 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const PanelArgs a) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(afull + 8 * slot);
             }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
         }
         // the last two groups, then the row's NQ columns of the slice's sum
         const int n_groups = (T + PN_G - 1) / PN_G;
@@ -984,6 +995,9 @@ static PanelPlan panel_plan(int64_t E, int n_steps, int nrhs) {
 }
 
 bool panel_tc_supported(int32_t nrhs) { return nrhs >= 1 && nrhs <= 8; }
+bool panel_tc_blocks_ok(const float *V, int64_t E) {  // TMA rows of V: 16-byte aligned
+    return E % 4 == 0 && reinterpret_cast<uintptr_t>(V) % 16 == 0;
+}
 
 size_t panel_tc_bytes(int64_t E, int32_t n_steps, int32_t nrhs) {
     return panel_plan(E, n_steps, nrhs).xf_bytes;
@@ -996,13 +1010,13 @@ stb_status panel_tc_begin(int64_t E, int32_t n_steps, int32_t nrhs, void *xf, cu
 }
 
 template <int N>
-static stb_status panel_launch(const CUtensorMap &map, const PanelArgs &args, const PanelPlan &p,
-                               int n_z, bool vec, cudaStream_t s) {
+static stb_status panel_launch(const CUtensorMap &map, const CUtensorMap &mapA,
+                               const PanelArgs &args, const PanelPlan &p, int n_z, cudaStream_t s) {
     using Sh = PanelShape<N>;
-    const auto kern = vec ? k_toeplitz_panel<true, N> : k_toeplitz_panel<false, N>;
+    const auto kern = k_toeplitz_panel<N>;
     STB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
     count_launch(s);
-    kern<<<dim3((unsigned)p.row_tiles, 1, (unsigned)n_z), PN_THREADS, Sh::SMEM, s>>>(map, args);
+    kern<<<dim3((unsigned)p.row_tiles, 1, (unsigned)n_z), PN_THREADS, Sh::SMEM, s>>>(map, mapA, args);
     return check_launch("k_toeplitz_panel");
 }
 
@@ -1022,9 +1036,15 @@ stb_status panel_tc(const float *V, int64_t E, int32_t n_steps, int32_t nrhs, co
             if ((st = check_launch("k_panel_split_x"))) return st;
         }
     }
-    CUtensorMap map;
+    if (!panel_tc_blocks_ok(V, E))
+        return fail(STB_ERR_INVALID_ARG, "panel product: E must be a multiple of 4, V 16-byte aligned");
+    CUtensorMap map, mapA;
     if ((st = tc_make_map_2d(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Xf,
                              (uint64_t)PN_NS * p.rowsX, (uint64_t)p.E_pad, SP_KC, (uint32_t)p.N)))
+        return st;
+    // V as n_steps E rows of E FP32 columns; boxes of 128 rows x 32 columns
+    if ((st = tc_make_map_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, V,
+                             (uint64_t)n_steps * E, (uint64_t)E, 32, SP_M)))
         return st;
     // blocks d = 1 .. kp + nb - 1, cut into at most PN_MAX_Z slices, about 16
     // waves of one CTA per SM: each CTA sums few blocks in its FP32 tensor
@@ -1039,11 +1059,10 @@ stb_status panel_tc(const float *V, int64_t E, int32_t n_steps, int32_t nrhs, co
     *n_z_out = n_z;
     PanelArgs args{V, part, status, (int)E, nrhs, p.rpad, p.rowsX, p.n_chunks, kp, nb, d_lo, d_end,
                    dr_len};
-    const bool vec = E % 4 == 0 && reinterpret_cast<uintptr_t>(V) % 16 == 0;
     switch (p.N) {
-    case 16: return panel_launch<16>(map, args, p, n_z, vec, s);
-    case 32: return panel_launch<32>(map, args, p, n_z, vec, s);
-    case 64: return panel_launch<64>(map, args, p, n_z, vec, s);
+    case 16: return panel_launch<16>(map, mapA, args, p, n_z, s);
+    case 32: return panel_launch<32>(map, mapA, args, p, n_z, s);
+    case 64: return panel_launch<64>(map, mapA, args, p, n_z, s);
     default: return fail(STB_ERR_INVALID_ARG, "panel product: at most 8 right-hand sides");
     }
 }
