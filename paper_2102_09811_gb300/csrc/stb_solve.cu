@@ -214,15 +214,26 @@ __global__ void __launch_bounds__(256) k_potrf_coop(T *__restrict__ L, int E, in
     T(*T2)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(fsm + (size_t)NB * (NB + 1) * sizeof(T));
     T(*Ps)[33] = reinterpret_cast<T(*)[33]>(fsm);
     T(*Qs)[33] = reinterpret_cast<T(*)[33]>(fsm + (size_t)NB * 33 * sizeof(T));
+    // look-ahead: in the update phase of column kb, CTA 0 first updates the
+    // next diagonal tile (pair 0) and factorises it while the other CTAs
+    // update the rest, so a column costs two grid barriers
+    if (blockIdx.x == 0) potrf_tile<T>(L, E, 0, status, col, piv);
+    if (!grid_barrier(bar, status)) return;
     for (int kb = 0; kb < nb; ++kb) {
-        if (blockIdx.x == 0) potrf_tile<T>(L, E, kb, status, col, piv);
-        if (!grid_barrier(bar, status)) return;
         const int m = nb - kb - 1;
         if (m == 0) break;
         for (int bi = blockIdx.x; bi < m; bi += gridDim.x) trsm_tile<T>(L, E, kb, bi, T1, T2);
         if (!grid_barrier(bar, status)) return;
         const int tiles = m * (m + 1) / 2;
-        for (int t = blockIdx.x; t < tiles; t += gridDim.x) syrk_tile<T>(L, E, kb, t, Ps, Qs);
+        if (blockIdx.x == 0) {
+            syrk_tile<T>(L, E, kb, 0, Ps, Qs);
+            __syncthreads();  // the CTA's own updates of the tile, read back below
+            potrf_tile<T>(L, E, kb + 1, status, col, piv);
+        }
+        const int first = gridDim.x > 1 ? 1 : 0, step = gridDim.x > 1 ? gridDim.x - 1 : 1;
+        if (gridDim.x == 1 || blockIdx.x > 0)
+            for (int t = 1 + (int)blockIdx.x - first; t < tiles; t += step)
+                syrk_tile<T>(L, E, kb, t, Ps, Qs);
         if (!grid_barrier(bar, status)) return;
     }
 }

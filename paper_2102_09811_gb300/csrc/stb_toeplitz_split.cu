@@ -73,7 +73,6 @@ constexpr int SP_PPC = SP_RC / SP_KC;  // pieces per chunk
 constexpr int SP_E1 = SP_PPC == 2 ? 1 : 0;
 constexpr int SP_NS = 5;        // slices per operand
 constexpr int SP_NL = 4;        // accumulators per buffer (levels 0, 1, 2, 3+4)
-constexpr int SP_NA = 7;        // A-slice slots (the shared memory left after the x stages)
 constexpr int SP_SLICERS = 256;   // 8 slicer warps: 32 columns j of one row each
 constexpr int SP_READERS = 256;   // 8 read-back warps: 2 per TMEM lane quarter, 32 columns each
 constexpr int SP_WORKERS = SP_SLICERS + SP_READERS;
@@ -81,17 +80,29 @@ constexpr int SP_THREADS = 64 + SP_WORKERS;
 constexpr uint32_t SP_A_BYTES = SP_M * SP_KC * 2;          // 16 KB
 constexpr uint32_t SP_B_BYTES = SP_N * SP_KC * 2;          // 8 KB per slice
 constexpr uint32_t SP_BSTAGE = SP_NS * SP_B_BYTES;         // 40 KB
-constexpr uint32_t SP_OFF_B = SP_NA * SP_A_BYTES;          // 112 KB
-// low parts of the read-back's running sums, float2 [32 column pairs][128 rows]
-constexpr uint32_t SP_OFF_AL = SP_OFF_B + 2 * SP_BSTAGE;   // 192 KB
-constexpr uint32_t SP_OFF_BAR = SP_OFF_AL + (SP_N / 2) * SP_M * 8;  // 224 KB
-// barriers: bfull[2] bempty[2] afull[SP_NA] aempty[SP_NA] accfull[2] accempty[2] drain
-constexpr int SP_NBAR = 2 + 2 + SP_NA + SP_NA + 2 + 2 + 1;
-constexpr uint32_t SP_OFF_MISC = SP_OFF_BAR + SP_NBAR * 8;
-constexpr size_t SP_SMEM = SP_OFF_MISC + 16 + 1024;  // + alignment slack
 constexpr uint32_t SP_TMEM_COLS = 2 * SP_NL * SP_N;  // 512
 constexpr uint32_t SP_IDESC = idesc_bf16(SP_M, SP_N);
-static_assert(SP_SMEM <= 232448, "shared memory of the split product");
+// Shared memory.  TA (E a multiple of 4, A 16-byte aligned): the FP32 A tile
+// of a piece arrives by TMA (two 32-column halves, 128-byte swizzle) in one
+// stage and the slicers read it from there; otherwise they load their row
+// segments themselves and the A-slice ring has two more slots.
+template <bool TA>
+struct SplitShape {
+    static constexpr int NA = TA ? 5 : 7;  // A-slice slots
+    static constexpr int NF = TA ? 1 : 0;  // FP32 A stages
+    static constexpr uint32_t F_HALF = SP_M * 128, F_BYTES = 2 * F_HALF;
+    static constexpr uint32_t OFF_F = NA * SP_A_BYTES;
+    static constexpr uint32_t OFF_B = OFF_F + NF * F_BYTES;
+    // low parts of the read-back's running sums, float2 [32 column pairs][128 rows]
+    static constexpr uint32_t OFF_AL = OFF_B + 2 * SP_BSTAGE;
+    static constexpr uint32_t OFF_BAR = OFF_AL + (SP_N / 2) * SP_M * 8;
+    // barriers: bfull[2] bempty[2] afull[NA] aempty[NA] accfull[2] accempty[2]
+    // drain ffull[NF] fempty[NF]
+    static constexpr int NBAR = 2 + 2 + NA + NA + 2 + 2 + 1 + 2 * NF;
+    static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
+    static constexpr size_t SMEM = OFF_MISC + 16 + 1024;  // + alignment slack
+    static_assert(SMEM <= 232448, "shared memory of the split product");
+};
 
 __device__ __forceinline__ float pow2f(int k) {  // 2^k; 0 below 2^-149, +inf above 2^127
     if (k >= -126) return __int_as_float(min(k + 127, 255) << 23);
@@ -239,16 +250,19 @@ struct PieceIter {
 
 template <bool VEC>
 __global__ void __launch_bounds__(SP_THREADS, 1)
-k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const SplitArgs a) {
+k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapA,
+                 const SplitArgs a) {
+    using Sh = SplitShape<VEC>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar0 = sbase + SP_OFF_BAR;
-    const uint32_t bfull = bar0, bempty = bar0 + 16, afull = bar0 + 32, aempty = afull + 8 * SP_NA,
-                   accfull = aempty + 8 * SP_NA, accempty = accfull + 16, drain = accempty + 16;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SP_OFF_MISC);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SP_OFF_MISC + 4);
+    const uint32_t bar0 = sbase + Sh::OFF_BAR;
+    const uint32_t bfull = bar0, bempty = bar0 + 16, afull = bar0 + 32, aempty = afull + 8 * Sh::NA,
+                   accfull = aempty + 8 * Sh::NA, accempty = accfull + 16, drain = accempty + 16,
+                   ffull = drain + 8, fempty = ffull + 8 * Sh::NF;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Sh::OFF_MISC);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + Sh::OFF_MISC + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * SP_M;
     const int n0 = blockIdx.y * a.S;  // first step of the box
@@ -264,9 +278,13 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const SplitArgs a) {
             mbar_init(accfull + 8 * s, 1);
             mbar_init(accempty + 8 * s, SP_READERS / 32);
         }
-        for (int s = 0; s < SP_NA; ++s) {
+        for (int s = 0; s < Sh::NA; ++s) {
             mbar_init(afull + 8 * s, SP_SLICERS / 32);
             mbar_init(aempty + 8 * s, 1);
+        }
+        for (int s = 0; s < Sh::NF; ++s) {
+            mbar_init(ffull + 8 * s, 1);
+            mbar_init(fempty + 8 * s, SP_SLICERS / 32);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -279,15 +297,28 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const SplitArgs a) {
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {  // TMA producer: the five x-slice tiles of each piece
+        if (lane == 0) {  // TMA producer: the five x-slice tiles of each piece (and its A tile)
             int issued = 0;
             PieceIter it{d0, 0};
             for (int t = 0; t < T; ++t, it.next(a.n_sub)) {
+                if constexpr (Sh::NF > 0) {
+                    const int f = t % Sh::NF;
+                    if (!mbar_wait_bounded(fempty + 8 * f, ((t / Sh::NF) & 1) ^ 1, a.status, abort_flag,
+                                           TC_WAIT_NS))
+                        break;
+                    const uint32_t fdst = sbase + Sh::OFF_F + f * Sh::F_BYTES;
+                    mbar_expect_tx(ffull + 8 * f, Sh::F_BYTES);
+                    // rows past E of the last row tile read the next block's rows (or
+                    // the tensor's zero fill); the slicers zero them
+                    tma_load_2d(fdst, &mapA, it.c * SP_KC, it.d * a.E + m0, ffull + 8 * f);
+                    tma_load_2d(fdst + Sh::F_HALF, &mapA, it.c * SP_KC + 32, it.d * a.E + m0,
+                                ffull + 8 * f);
+                }
                 const int s = t & 1;
                 if (!mbar_wait_bounded(bempty + 8 * s, ((t >> 1) & 1) ^ 1, a.status, abort_flag,
                                        TC_WAIT_NS))
                     break;
-                const uint32_t dst = sbase + SP_OFF_B + s * SP_BSTAGE;
+                const uint32_t dst = sbase + Sh::OFF_B + s * SP_BSTAGE;
                 const int y0 = (a.S + n0 - it.d) * a.rpad;
                 mbar_expect_tx(bfull + 8 * s, SP_BSTAGE);
 #pragma unroll
@@ -299,6 +330,10 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const SplitArgs a) {
             // the copies of the last two pieces have landed before the CTA may exit
             for (int t = max(0, issued - 2); t < issued; ++t)
                 mbar_wait_bounded(bfull + 8 * (t & 1), (t >> 1) & 1, a.status, nullptr, TC_WAIT_NS);
+            if constexpr (Sh::NF > 0)
+                for (int t = max(0, issued - Sh::NF); t < issued; ++t)
+                    mbar_wait_bounded(ffull + 8 * (t % Sh::NF), (t / Sh::NF) & 1, a.status, nullptr,
+                                      TC_WAIT_NS);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -316,11 +351,11 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const SplitArgs a) {
                                        TC_WAIT_NS))
                     break;
                 tc_fence_after();
-                const uint32_t bst = sbase + SP_OFF_B + (t & 1) * SP_BSTAGE;
+                const uint32_t bst = sbase + Sh::OFF_B + (t & 1) * SP_BSTAGE;
                 bool ok = true;
                 for (int i = 0; i < SP_NS && ok; ++i) {
-                    const int u = SP_NS * t + i, slot = u % SP_NA;
-                    if (!mbar_wait_bounded(afull + 8 * slot, (u / SP_NA) & 1, a.status, abort_flag,
+                    const int u = SP_NS * t + i, slot = u % Sh::NA;
+                    if (!mbar_wait_bounded(afull + 8 * slot, (u / Sh::NA) & 1, a.status, abort_flag,
                                            TC_WAIT_NS)) {
                         ok = false;
                         break;
@@ -371,14 +406,27 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const SplitArgs a) {
             // the current piece in registers; the next two pieces are prefetched
             // into L2 (no registers) and the next one is loaded as soon as the
             // current one is sliced
+            // (with TA: the piece's row segment from the staged A tile instead)
             float4 cur[8];
-            load32<VEC>(a.A, a.E, d0, row, jh, cur);
+            if constexpr (Sh::NF == 0) load32<VEC>(a.A, a.E, d0, row, jh, cur);
             PieceIter it{d0, 0};
             float2 inv = make_float2(0.f, 0.f);
             for (int t = 0; t < T; ++t) {
                 PieceIter nx = it;
                 nx.next(a.n_sub);
-                if (row < a.E) {  // this thread's 128-byte line of pieces t+1 and t+2
+                if constexpr (Sh::NF > 0) {  // this row's 128 bytes of half h, chunk k at k ^ (rl % 8)
+                    const int f = t % Sh::NF;
+                    const bool ok = mbar_wait_bounded(ffull + 8 * f, (t / Sh::NF) & 1, a.status,
+                                                      abort_flag, TC_WAIT_NS);
+                    const unsigned char *seg =
+                        smem + Sh::OFF_F + f * Sh::F_BYTES + h * Sh::F_HALF + rl * 128;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        cur[k] = ok && row < a.E
+                                     ? *reinterpret_cast<const float4 *>(seg + ((k ^ (rl & 7)) << 4))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                if (Sh::NF == 0 && row < a.E) {  // this thread's 128-byte line of pieces t+1 and t+2
                     PieceIter n2 = nx;
 #pragma unroll
                     for (int ahead = 1; ahead <= 2; ++ahead) {
@@ -402,10 +450,17 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const SplitArgs a) {
                     v[2 * i] = __fmul2_rn(make_float2(cur[i].x, cur[i].y), inv);
                     v[2 * i + 1] = __fmul2_rn(make_float2(cur[i].z, cur[i].w), inv);
                 }
+                if constexpr (Sh::NF > 0) {
+                    // the staged tile is released only once its values are in
+                    // registers (v depends on every load), so that the next TMA
+                    // cannot overwrite a load still in flight
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(fempty + 8 * (t % Sh::NF));
+                }
 #pragma unroll
                 for (int i = 0; i < SP_NS; ++i) {
-                    const int u = SP_NS * t + i, slot = u % SP_NA;
-                    const bool ok = mbar_wait_bounded(aempty + 8 * slot, ((u / SP_NA) & 1) ^ 1,
+                    const int u = SP_NS * t + i, slot = u % Sh::NA;
+                    const bool ok = mbar_wait_bounded(aempty + 8 * slot, ((u / Sh::NA) & 1) ^ 1,
                                                       a.status, abort_flag, TC_WAIT_NS);
                     // slice i: round to a multiple of 2^(-8-9i) (|D| <= 256, exact in bf16)
                     const float ci = 1.5f * __int_as_float((127 + 15 - 9 * i) << 23);
@@ -430,7 +485,7 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const SplitArgs a) {
                     __syncwarp();
                     if (lane == 0) mbar_arrive(afull + 8 * slot);
                 }
-                if (t + 1 < T) load32<VEC>(a.A, a.E, nx.d, row, nx.c * SP_KC + jh, cur);
+                if (Sh::NF == 0 && t + 1 < T) load32<VEC>(a.A, a.E, nx.d, row, nx.c * SP_KC + jh, cur);
                 it = nx;
             }
         } else {
@@ -442,7 +497,7 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const SplitArgs a) {
             // running double-float sums of its 32 columns: high parts in registers,
             // low parts in shared memory (consecutive rows: conflict-free)
             float2 ah[16];
-            float2 *al = reinterpret_cast<float2 *>(smem + SP_OFF_AL) + (jc >> 1) * SP_M + rl;
+            float2 *al = reinterpret_cast<float2 *>(smem + Sh::OFF_AL) + (jc >> 1) * SP_M + rl;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 ah[i] = make_float2(0.f, 0.f);
@@ -607,13 +662,21 @@ static stb_status split_run(const float *A, int64_t E, int32_t n_steps, int32_t 
     float *xsc = reinterpret_cast<float *>(sc + p.xs_bytes);
     int8_t *rexp = reinterpret_cast<int8_t *>(sc + p.xs_bytes + p.xsc_bytes);
     double *part = reinterpret_cast<double *>(sc + p.xs_bytes + p.xsc_bytes + p.rexp_bytes);
-    CUtensorMap mapX;
+    CUtensorMap mapX, mapA;
     stb_status st = tc_make_map_2d(&mapX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Xs,
                                    (uint64_t)SP_NS * p.rowsX, (uint64_t)p.E_pad, SP_KC, SP_N);
     if (st) return st;
     const bool vec = E % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
+    if (vec) {  // A as n_steps E rows of E FP32 columns; boxes of 128 rows x 32 columns
+        if ((st = tc_make_map_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, A,
+                                 (uint64_t)n_steps * E, (uint64_t)E, 32, SP_M)))
+            return st;
+    } else {
+        mapA = mapX;  // not read
+    }
     const auto kern = vec ? k_toeplitz_split<true> : k_toeplitz_split<false>;
-    STB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM));
+    const size_t smem = vec ? SplitShape<true>::SMEM : SplitShape<false>::SMEM;
+    STB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {  // row exponents of every 128-column chunk of A (one pass over the blocks)
         const size_t warps = (size_t)n_steps * E;
         count_launch(s);
@@ -633,7 +696,7 @@ static stb_status split_run(const float *A, int64_t E, int32_t n_steps, int32_t 
                        p.rowsX, p.n_sub, p.n_rc, p.dr_len};
         const dim3 grid((unsigned)p.row_tiles, (unsigned)p.n_box, (unsigned)p.n_z);
         count_launch(s);
-        kern<<<grid, SP_THREADS, SP_SMEM, s>>>(mapX, args);
+        kern<<<grid, SP_THREADS, smem, s>>>(mapX, mapA, args);
         if ((st = check_launch("k_toeplitz_split"))) return st;
         const size_t total = (size_t)ng * stride;
         count_launch(s);
@@ -929,8 +992,6 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                     cur[k] = ok ? *reinterpret_cast<const float4 *>(
                                       half + (((4 * (c4 & 1) + k) ^ (rl & 7)) << 4))
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(fempty + 8 * f);
             }
             uint32_t w[PN_NS][8];
 #pragma unroll
@@ -939,6 +1000,10 @@ k_toeplitz_panel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 split3_bf16(make_float2(cur[i].z, cur[i].w), w[0][2 * i + 1], w[1][2 * i + 1],
                             w[2][2 * i + 1]);
             }
+            // the staged tile is released only once its values are consumed (the
+            // slices depend on every load): the next TMA into it cannot race a load
+            __syncwarp();
+            if (lane == 0) mbar_arrive(fempty + 8 * (t % Sh::NF));
 #pragma unroll
             for (int i = 0; i < PN_NS; ++i) {
                 const int u = PN_NS * t + i, slot = u % PN_NA;
