@@ -197,6 +197,9 @@ def parse():
                     help="skip the piecewise-linear data pipeline report (outside the timed region)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-problem batch report (outside the timed region)")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the mixed vs FP64 assembly on the icosphere with 5120 triangles and "
+                         "128 steps (one FP64 assembly of about 40 s)")
     ap.add_argument("--no-c2", action="store_true",
                     help="skip the reports on the 3072-triangle cube (mixed vs FP64 assembly, the "
                          "three-alpha step) outside the timed region")
@@ -446,14 +449,16 @@ def _roofline(name, trace_entry, ms_step, n_reg_pairs, q, n_steps):
 
 
 def mixed_vs_fp64_report(capi, pipeline, torch, stream, a_, b_, alpha=0.5, reps_mixed=5,
-                         reps_fp64=2):
-    """Mixed-precision against FP64 assembly of V and K on the cube with 3072
-    triangles and 64 steps: CUDA events around the whole stb_assemble call
-    (geometry, pair classification, rule tables and kernels) for both, one
-    warm-up call each, the median of the timed calls; relative Frobenius error
-    of every mixed block against the FP64 block; then the other stages of the
-    mixed problem (projection, right-hand side, refined solve, error)."""
-    wl = workloads.workload("cube3072_e64")
+                         reps_fp64=2, workload="cube3072_e64", fp64_warmup=True):
+    """Mixed-precision against FP64 assembly of V and K (by default on the cube
+    with 3072 triangles and 64 steps): CUDA events around the whole
+    stb_assemble call (geometry, pair classification, rule tables and
+    kernels) for both, one warm-up call each (for FP64 optional: a long call
+    needs none once the kernels have run), the median of the timed calls;
+    relative Frobenius error of every mixed block against the FP64 block; then
+    the other stages of the mixed problem (projection, right-hand side,
+    refined solve, error)."""
+    wl = workloads.workload(workload)
     nodes, tris, n, src = wl["nodes"], wl["tris"], wl["n_steps"], wl["sources"]
     mesh = capi.Mesh(nodes, tris)
     E = len(tris)
@@ -461,9 +466,10 @@ def mixed_vs_fp64_report(capi, pipeline, torch, stream, a_, b_, alpha=0.5, reps_
                                    precision=capi.STB_PREC_MIXED, storage=capi.STB_STORE_F32)
     pf = pipeline.DirichletProblem(nodes, tris, alpha, wl["T"], n, src, mesh=mesh)
 
-    def timed(fn, reps):
-        fn(stream)
-        torch.cuda.synchronize()
+    def timed(fn, reps, warm=True):
+        if warm:
+            fn(stream)
+            torch.cuda.synchronize()
         out = []
         for _ in range(reps):
             a_.record(stream)
@@ -474,7 +480,7 @@ def mixed_vs_fp64_report(capi, pipeline, torch, stream, a_, b_, alpha=0.5, reps_
         return out
 
     tm = timed(pm.assemble, reps_mixed)
-    tf = timed(pf.assemble, reps_fp64)
+    tf = timed(pf.assemble, reps_fp64, fp64_warmup)
     errs = {}
     for name, A, B in (("V", pm.V, pf.V), ("K", pm.K, pf.K)):
         errs[name] = max(float(torch.linalg.norm(A[d].double() - B[d]) / torch.linalg.norm(B[d]))
@@ -488,9 +494,10 @@ def mixed_vs_fp64_report(capi, pipeline, torch, stream, a_, b_, alpha=0.5, reps_
                       ("error", pm.error)):
         stages[label] = statistics.median(timed(fn, 2))
     refinements, rel_residual = capi.stb_solve_report(pm.ws_solve)
-    out = {"workload": "cube3072_e64", "alpha": alpha, "entries": entries,
-           "timing": "CUDA events around the whole stb_assemble call, one warm-up call, median "
-                     "of the timed calls",
+    out = {"workload": workload, "alpha": alpha, "entries": entries,
+           "timing": "CUDA events around the whole stb_assemble call, one warm-up call (FP64: %s), "
+                     "median of the timed calls" % ("yes" if fp64_warmup else
+                                                    "none, the kernels ran in the report before"),
            "fp64_assembly_ms": mf, "fp64_runs_ms": tf, "fp64_entries_per_s": entries / (mf / 1e3),
            "mixed_assembly_ms": mm, "mixed_runs_ms": tm, "mixed_entries_per_s": entries / (mm / 1e3),
            "speedup": mf / mm, "max_block_rel_err_mixed_vs_fp64": errs,
@@ -913,9 +920,15 @@ def run_gpu(args):
 
     # the other precision on the 3072-triangle cube with 64 steps (the FP64 GPU
     # baseline workload): both assemblies timed alike, per-block errors
-    cmp = None
+    cmp = cmp3 = None
     if mixed and not args.no_fp64_compare and not args.no_c2:
         cmp = mixed_vs_fp64_report(capi, pipeline, torch, stream, a_, b_)
+    # the same on the precision workload (icosphere 5120, 128 steps, alpha 1):
+    # one FP64 assembly of about 40 s (its kernels are warm from the cube)
+    if mixed and not args.no_fp64_compare and not args.no_c3:
+        cmp3 = mixed_vs_fp64_report(capi, pipeline, torch, stream, a_, b_, alpha=1.0,
+                                    reps_mixed=3, reps_fp64=1, workload="sphere5120_e128",
+                                    fp64_warmup=args.no_c2)
 
     # V and the right-hand side without storing K (matrix-free K g), first
     # problem: time against assembly + stored-K right-hand side
@@ -1123,7 +1136,7 @@ def run_gpu(args):
                        "l2": "no flush: every step writes %.1f GB of V/K blocks (>> 129 MB L2)"
                              % (2 * (4 if mixed else 8) * n * E * E * len(alphas) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "mixed_vs_fp64": cmp, "batch": batch, "matrix_free_rhs": mfree, "p1_data": p1,
+            "mixed_vs_fp64": cmp, "mixed_vs_fp64_sphere5120_e128": cmp3, "batch": batch, "matrix_free_rhs": mfree, "p1_data": p1,
             "neumann": neu,
             "potentials": pots, "nonuniform": nonuni,
             "matvec_tflops": mv_tflops, "matvec_ms": mv_ms, "matvec": matvec,

@@ -105,30 +105,44 @@ __device__ void potrf_tile(T *__restrict__ L, int E, int kb, int32_t *__restrict
     }
 }
 
-// Panel: L_ik = A_ik L_kk^{-T} for tile row i = kb + 1 + bi.
+// Panel: L_ik = A_ik L_kk^{-T} for tile row i = kb + 1 + bi.  Four threads
+// per row (blockDim 256), each holding the columns q, q+4, .. of its row in
+// registers; column c is solved by its owner and broadcast to the other
+// three lanes by a shuffle, and every later column is updated at once
+// (independent FMAs instead of one dependent chain per row).
 template <class T>
-__device__ void trsm_tile(T *__restrict__ L, int E, int kb, int bi, T (*Lk)[NB + 1],
-                          T (*A)[NB + 1]) {
+__device__ void trsm_tile(T *__restrict__ L, int E, int kb, int bi, T (*Lk)[NB + 1]) {
     const int b0 = kb * NB, n = min(NB, E - b0);
     const int i0 = (kb + 1 + bi) * NB, mrows = min(NB, E - i0);
-    __syncthreads();  // the shared tiles of the previous task are consumed
+    const int row = threadIdx.x >> 2, q = threadIdx.x & 3;
+    const unsigned lane = threadIdx.x & 31;
+    __syncthreads();  // the shared tile of the previous task is consumed
     for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
         int i = t / NB, j = t % NB;
         Lk[i][j] = (i < n && j < n) ? __ldcg(L + (size_t)(b0 + i) * E + b0 + j) : (T)0;
-        A[i][j] = (i < mrows && j < n) ? __ldcg(L + (size_t)(i0 + i) * E + b0 + j) : (T)0;
+    }
+    T v[NB / 4];
+#pragma unroll
+    for (int j = 0; j < NB / 4; ++j) {
+        const int c = 4 * j + q;
+        v[j] = (row < mrows && c < n) ? __ldcg(L + (size_t)(i0 + row) * E + b0 + c) : (T)0;
     }
     __syncthreads();
-    for (int row = threadIdx.x; row < mrows; row += blockDim.x) {
-        for (int c = 0; c < n; ++c) {
-            T x = A[row][c];
-            for (int cc = 0; cc < c; ++cc) x = fma(-A[row][cc], Lk[c][cc], x);
-            A[row][c] = x / Lk[c][c];
-        }
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+        if (c >= n) break;
+        const int oj = c >> 2;
+        T x = v[oj] / Lk[c][c];  // meaningful on the owner lane (q == c % 4)
+        x = __shfl_sync(0xffffffffu, x, (int)((lane & ~3u) | (unsigned)(c & 3)));
+        if (q == (c & 3)) v[oj] = x;
+#pragma unroll
+        for (int j = oj; j < NB / 4; ++j)
+            if (4 * j + q > c) v[j] = fma(-x, Lk[4 * j + q][c], v[j]);
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < mrows * n; t += blockDim.x) {
-        int i = t / n, j = t % n;
-        L[(size_t)(i0 + i) * E + b0 + j] = A[i][j];
+#pragma unroll
+    for (int j = 0; j < NB / 4; ++j) {
+        const int c = 4 * j + q;
+        if (row < mrows && c < n) L[(size_t)(i0 + row) * E + b0 + c] = v[j];
     }
 }
 
@@ -202,7 +216,9 @@ __device__ void syrk_tile(T *__restrict__ L, int E, int kb, int t, T (*Ps)[33], 
 
 template <class T>
 constexpr size_t potrf_smem() {
-    return 2 * (size_t)NB * (NB + 1) * sizeof(T);  // the largest phase: two tiles of trsm
+    // the larger of the phases' tiles: L_kk of the panel solve, or the two
+    // operand chunks of the trailing update
+    return (NB * (NB + 1) > 2 * NB * 33 ? (size_t)NB * (NB + 1) : (size_t)2 * NB * 33) * sizeof(T);
 }
 
 template <class T>
@@ -211,7 +227,6 @@ __global__ void __launch_bounds__(256) k_potrf_coop(T *__restrict__ L, int E, in
     extern __shared__ __align__(16) unsigned char fsm[];
     __shared__ T col[2][NB], piv[NB];
     T(*T1)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(fsm);
-    T(*T2)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(fsm + (size_t)NB * (NB + 1) * sizeof(T));
     T(*Ps)[33] = reinterpret_cast<T(*)[33]>(fsm);
     T(*Qs)[33] = reinterpret_cast<T(*)[33]>(fsm + (size_t)NB * 33 * sizeof(T));
     // look-ahead: in the update phase of column kb, CTA 0 first updates the
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(256) k_potrf_coop(T *__restrict__ L, int E, in
     for (int kb = 0; kb < nb; ++kb) {
         const int m = nb - kb - 1;
         if (m == 0) break;
-        for (int bi = blockIdx.x; bi < m; bi += gridDim.x) trsm_tile<T>(L, E, kb, bi, T1, T2);
+        for (int bi = blockIdx.x; bi < m; bi += gridDim.x) trsm_tile<T>(L, E, kb, bi, T1);
         if (!grid_barrier(bar, status)) return;
         const int tiles = m * (m + 1) / 2;
         if (blockIdx.x == 0) {
@@ -985,8 +1000,9 @@ static stb_status solve_mixed(const float *V, int E, int n_steps, int nrhs, cons
         if ((st = check_launch("k_update"))) return st;
         // r_it = r_{it-1} - V_h delta_it (r_{-1} = f), the product on the
         // tensor cores with split operands (about 2^-44 of the chunk scales)
+        // (V's row exponents, formed by the first residual, stay in S.df)
         if ((st = toeplitz_split_f32x(V, E, n_steps, nrhs, S.delta, DF_RESIDUAL,
-                                      it == 0 ? f : S.r, 0.0, S.r, S.df, status, s)))
+                                      it == 0 ? f : S.r, 0.0, S.r, S.df, status, it > 0, s)))
             return st;
         rhs = S.r;
         if (no_sync && it < max_refine) continue;  // fixed count: no norms until the end

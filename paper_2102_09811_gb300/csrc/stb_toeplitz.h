@@ -46,14 +46,17 @@ stb_status toeplitz_df_rect(const float *A, int64_t E, int64_t N, int32_t n_step
 // sums across chunks): error about 2^-44 of the chunk magnitudes.  Any E;
 // scratch of toeplitz_split_bytes; a bounded wait that expires writes
 // STB_ERR_TIMEOUT to *status (device).  Block entries must lie below 2^126 in
-// magnitude.  f may alias y in mode DF_RESIDUAL.
+// magnitude.  f may alias y in mode DF_RESIDUAL.  a_exp_ready: the scratch
+// already holds A's row exponents from an earlier call with the same A and
+// sizes (the refinement residuals of one solve), so the pass over A that
+// forms them is skipped.
 size_t toeplitz_split_bytes(int64_t E, int32_t n_steps, int32_t nrhs);
 stb_status toeplitz_split(const float *A, int64_t E, int32_t n_steps, int32_t nrhs, const double *x,
                           int mode, const double *f, double beta, double *y, void *scratch,
                           int32_t *status, cudaStream_t s);
 stb_status toeplitz_split_f32x(const float *A, int64_t E, int32_t n_steps, int32_t nrhs,
                                const float *x, int mode, const double *f, double beta, double *y,
-                               void *scratch, int32_t *status, cudaStream_t s);
+                               void *scratch, int32_t *status, bool a_exp_ready, cudaStream_t s);
 
 // Far history of a panel of 8 steps of the march on the tensor cores (three
 // floating bf16 slices per operand, six products, FP32 accumulation; FP32

@@ -653,7 +653,7 @@ size_t toeplitz_split_bytes(int64_t E, int32_t n_steps, int32_t nrhs) {
 template <class XT>
 static stb_status split_run(const float *A, int64_t E, int32_t n_steps, int32_t nrhs, const XT *x,
                             int mode, const double *f, double beta, double *y, void *scratch,
-                            int32_t *status, cudaStream_t s) {
+                            int32_t *status, bool a_exp_ready, cudaStream_t s) {
     if (E < 1 || E > 65535 || n_steps < 1 || nrhs < 1)
         return fail(STB_ERR_INVALID_ARG, "split product: need 1 <= E <= 65535, n_steps, nrhs >= 1");
     const SplitPlan p = split_plan(E, n_steps, nrhs);
@@ -677,7 +677,7 @@ static stb_status split_run(const float *A, int64_t E, int32_t n_steps, int32_t 
     const auto kern = vec ? k_toeplitz_split<true> : k_toeplitz_split<false>;
     const size_t smem = vec ? SplitShape<true>::SMEM : SplitShape<false>::SMEM;
     STB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    {  // row exponents of every 128-column chunk of A (one pass over the blocks)
+    if (!a_exp_ready) {  // row exponents of every column chunk of A (one pass over the blocks)
         const size_t warps = (size_t)n_steps * E;
         count_launch(s);
         k_row_exp<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(A, (int)E, n_steps, p.n_rc,
@@ -711,13 +711,14 @@ static stb_status split_run(const float *A, int64_t E, int32_t n_steps, int32_t 
 stb_status toeplitz_split(const float *A, int64_t E, int32_t n_steps, int32_t nrhs, const double *x,
                           int mode, const double *f, double beta, double *y, void *scratch,
                           int32_t *status, cudaStream_t s) {
-    return split_run<double>(A, E, n_steps, nrhs, x, mode, f, beta, y, scratch, status, s);
+    return split_run<double>(A, E, n_steps, nrhs, x, mode, f, beta, y, scratch, status, false, s);
 }
 
 stb_status toeplitz_split_f32x(const float *A, int64_t E, int32_t n_steps, int32_t nrhs,
                                const float *x, int mode, const double *f, double beta, double *y,
-                               void *scratch, int32_t *status, cudaStream_t s) {
-    return split_run<float>(A, E, n_steps, nrhs, x, mode, f, beta, y, scratch, status, s);
+                               void *scratch, int32_t *status, bool a_exp_ready, cudaStream_t s) {
+    return split_run<float>(A, E, n_steps, nrhs, x, mode, f, beta, y, scratch, status, a_exp_ready,
+                            s);
 }
 
 
