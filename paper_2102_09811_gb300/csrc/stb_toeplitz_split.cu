@@ -181,25 +181,38 @@ __global__ void k_split_x(const XT *__restrict__ x, int E, int E_pad, int n_step
     }
 }
 
-// Row exponents of A: rexp[(d E + l) n_rc + c] = e with 2^e just above the
-// largest |A^d[l][j]| of the 128-column chunk c (clamped to [-126, 127]; one
-// warp per row of a block).
-__global__ void k_row_exp(const float *__restrict__ A, int E, int n_steps, int n_rc,
-                          int8_t *__restrict__ rexp) {
-    const size_t wid = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wid >= (size_t)n_steps * E) return;
-    const float *row = A + wid * E;
-    for (int c = 0; c < n_rc; ++c) {
-        float m = 0.f;
+// Row exponents of A: rexp[(d n_rc + c) E + l] = e with 2^e just above the
+// largest |A^d[l][j]| of the column chunk c (clamped to [-126, 127]).  A CTA
+// takes 32 consecutive rows of the stacked blocks (a warp per row) and writes
+// the exponents chunk by chunk, 32 adjacent bytes each, so that the product's
+// slicers and readers read a chunk's exponents of consecutive rows together.
+constexpr int RE_ROWS = 32;
+__global__ void __launch_bounds__(32 * RE_ROWS)
+k_row_exp(const float *__restrict__ A, int E, int n_steps, int n_rc, int8_t *__restrict__ rexp) {
+    extern __shared__ int8_t ex[];  // [n_rc][RE_ROWS]
+    const size_t g0 = (size_t)blockIdx.x * RE_ROWS, rows = (size_t)n_steps * E;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
+        const int r = warp;
+        const size_t g = g0 + r;
+        const float *row = A + min(g, rows - 1) * E;
+        for (int c = 0; c < n_rc && g < rows; ++c) {
+            float m = 0.f;
 #pragma unroll
-        for (int u = 0; u < SP_RC / 32; ++u) {
-            const int j = c * SP_RC + u * 32 + lane;
-            if (j < E) m = fmaxf(m, fabsf(__ldg(row + j)));
+            for (int u = 0; u < SP_RC / 32; ++u) {
+                const int j = c * SP_RC + u * 32 + lane;
+                if (j < E) m = fmaxf(m, fabsf(__ldg(row + j)));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) ex[c * RE_ROWS + r] = (int8_t)min(scale_exp(m), 127);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) rexp[wid * n_rc + c] = (int8_t)min(scale_exp(m), 127);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_rc * RE_ROWS; t += blockDim.x) {
+        const int r = t % RE_ROWS, c = t / RE_ROWS;
+        const size_t g = g0 + r;
+        if (g < rows) rexp[((g / E) * n_rc + c) * E + g % E] = ex[t];
     }
 }
 
@@ -411,6 +424,7 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             if constexpr (Sh::NF == 0) load32<VEC>(a.A, a.E, d0, row, jh, cur);
             PieceIter it{d0, 0};
             float2 inv = make_float2(0.f, 0.f);
+            int e_next = row < a.E ? (int)a.rexp[(size_t)d0 * a.n_rc * a.E + row] : 0;
             for (int t = 0; t < T; ++t) {
                 PieceIter nx = it;
                 nx.next(a.n_sub);
@@ -438,12 +452,13 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                     }
                 }
                 if (it.c % SP_PPC == 0) {  // a new scale chunk: this row's exponent
-                    const int e = row < a.E
-                                      ? (int)a.rexp[((size_t)it.d * a.E + row) * a.n_rc + it.c / SP_PPC]
-                                      : 0;
-                    const float iv = pow2f(-(e + SP_E1));
+                    const float iv = pow2f(-(e_next + SP_E1));
                     inv = make_float2(iv, iv);
                 }
+                if (t + 1 < T && nx.c % SP_PPC == 0)  // the next chunk's, loaded a piece ahead
+                    e_next = row < a.E
+                                 ? (int)a.rexp[((size_t)nx.d * a.n_rc + nx.c / SP_PPC) * a.E + row]
+                                 : 0;
                 float2 v[16];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -508,7 +523,7 @@ k_toeplitz_split(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             int d = d0, pch = 0;
             for (int r = 0; r < n_read; ++r) {
                 const int buf = r & 1;
-                const int e = row < a.E ? (int)a.rexp[((size_t)d * a.E + row) * a.n_rc + pch] : 0;
+                const int e = row < a.E ? (int)a.rexp[((size_t)d * a.n_rc + pch) * a.E + row] : 0;
                 const float rs = pow2f(e + SP_E1);
                 const bool ok = mbar_wait_bounded(accfull + 8 * buf, (r >> 1) & 1, a.status,
                                                   abort_flag, TC_WAIT_NS);
@@ -678,10 +693,10 @@ static stb_status split_run(const float *A, int64_t E, int32_t n_steps, int32_t 
     const size_t smem = vec ? SplitShape<true>::SMEM : SplitShape<false>::SMEM;
     STB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (!a_exp_ready) {  // row exponents of every column chunk of A (one pass over the blocks)
-        const size_t warps = (size_t)n_steps * E;
+        const size_t rows = (size_t)n_steps * E;
         count_launch(s);
-        k_row_exp<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(A, (int)E, n_steps, p.n_rc,
-                                                                       rexp);
+        k_row_exp<<<(unsigned)((rows + RE_ROWS - 1) / RE_ROWS), 32 * RE_ROWS, (size_t)p.n_rc * RE_ROWS, s>>>(
+            A, (int)E, n_steps, p.n_rc, rexp);
         if ((st = check_launch("k_row_exp"))) return st;
     }
     const size_t stride = (size_t)n_steps * E;  // one right-hand side
