@@ -58,6 +58,31 @@ static void host_rules(int q, int nt, std::vector<double> &out) {
 // g_{r,k,j} = (h Delta_j)^{-1} int_{t_k}^{t_{k+1}} int_{gamma_j} g_r  (element mean);
 // NEU: of the Neumann datum w_r = alpha du_r/dn_x = -sum_s weight_s G (x - y_s).n_x
 // / (2 (t - t0_s)) instead of the Dirichlet datum
+// FP32 fast path for one source per right-hand side (uniform steps): the
+// time-node factors of the heat kernel (1/(4 alpha tau), (4 pi alpha tau)^-3/2)
+// depend on the time node only, so the sums run time nodes outside and rule
+// points inside, x - y* in difference form (P0 - y* in FP64 once, rounded,
+// plus the edge vectors in FP32).  Returns, for the triangle's row of nodes,
+// sum_b tw_b c_b sum_a w_a f_a(b) with f = exp(-r^2 / (4 alpha tau)) (MODE 0,
+// the projection) or the error sums of the Neumann datum (MODE 1).
+struct OneSourceGeom {
+    float p[3], e1[3], e2[3];
+};
+__device__ __forceinline__ OneSourceGeom one_source_geom(const double *gj, const float *S) {
+    OneSourceGeom G;
+    for (int c = 0; c < 3; ++c) {
+        G.p[c] = (float)(gj[c] - (double)S[c]);
+        G.e1[c] = (float)(gj[3 + c] - gj[c]);
+        G.e2[c] = (float)(gj[6 + c] - gj[3 + c]);
+    }
+    return G;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x));
+    return e;
+}
+
 template <class R, bool NEU = false>
 __global__ void __launch_bounds__(DIR_THREADS)
 k_project(const double *__restrict__ geo, int E, const double *__restrict__ rule, int nq, int nt,
@@ -76,6 +101,33 @@ k_project(const double *__restrict__ geo, int E, const double *__restrict__ rule
     const double *gj = geo + (size_t)j * GEO_STRIDE;
     const R *tx = rs + 3 * nq, *tw = tx + nt;
     const R nx = (R)gj[GEO_N], ny = (R)gj[GEO_N + 1], nz = (R)gj[GEO_N + 2];
+    if constexpr (sizeof(R) == 4 && !NEU) {
+        if (n_src == 1 && !times) {
+            const R *S = sr;
+            const OneSourceGeom G = one_source_geom(gj, S);
+            float acc1 = 0.f;
+            for (int b = 0; b < nt; ++b) {
+                const float tau = (k + tx[b]) * h - S[3];
+                if (tau <= 0.f) continue;
+                const float q4 = 4.f * alpha * tau, c1 = -1.44269504f / q4;
+                const float sq = 3.14159265f * q4;
+                float sa = 0.f;
+                for (int a = 0; a < nq; ++a) {
+                    const float s1 = rs[3 * a], s2 = rs[3 * a + 1];
+                    float rr = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float d = fmaf(s2, G.e2[c], fmaf(s1, G.e1[c], G.p[c]));
+                        rr = fmaf(d, d, rr);
+                    }
+                    sa = fmaf(rs[3 * a + 2], ex2_approx(rr * c1), sa);
+                }
+                acc1 = fmaf(tw[b] * S[4] * rsqrtf(sq * sq * sq), sa, acc1);
+            }
+            g[(size_t)r * n_steps * E + idx] = 2.0 * (double)acc1;
+            return;
+        }
+    }
     R acc = 0;
     for (int a = 0; a < nq; ++a) {
         R s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
@@ -219,7 +271,42 @@ k_error(const double *__restrict__ geo, int E, const double *__restrict__ rule, 
         const R whv = (R)wh[(size_t)r * n_steps * E + idx];
         const R nx = (R)gj[GEO_N], ny = (R)gj[GEO_N + 1], nz = (R)gj[GEO_N + 2];
         R e2r = 0, r2r = 0;
-        for (int a = 0; a < nq; ++a) {
+        bool done = false;
+        if constexpr (sizeof(R) == 4) {
+            if (n_src == 1 && !times) {
+                const R *S = sr;
+                const OneSourceGeom G = one_source_geom(gj, S);
+                // (x - y*) . n = p.n + s1 e1.n + s2 e2.n
+                const float pn = G.p[0] * nx + G.p[1] * ny + G.p[2] * nz;
+                const float e1n = G.e1[0] * nx + G.e1[1] * ny + G.e1[2] * nz;
+                const float e2n = G.e2[0] * nx + G.e2[1] * ny + G.e2[2] * nz;
+                for (int b = 0; b < nt; ++b) {
+                    const float tau = (k + tx[b]) * h - S[3];
+                    const float q4 = 4.f * alpha * tau, c1 = -1.44269504f / q4;
+                    const float sq = 3.14159265f * q4;
+                    // w = -weight G(r, tau) (r . n) / (2 tau); zero for tau <= 0
+                    const float cb = tau > 0.f ? -S[4] * rsqrtf(sq * sq * sq) / (2.f * tau) : 0.f;
+                    float ie = 0.f, ir = 0.f;
+                    for (int a = 0; a < nq; ++a) {
+                        const float s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
+                        float rr = 0.f;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float d = fmaf(s2, G.e2[c], fmaf(s1, G.e1[c], G.p[c]));
+                            rr = fmaf(d, d, rr);
+                        }
+                        const float dn = fmaf(s2, e2n, fmaf(s1, e1n, pn));
+                        const float wv = tau > 0.f ? cb * ex2_approx(rr * c1) * dn : 0.f;
+                        ie = fmaf(wa, (wv - whv) * (wv - whv), ie);
+                        ir = fmaf(wa, wv * wv, ir);
+                    }
+                    e2r = fmaf(tw[b], ie, e2r);
+                    r2r = fmaf(tw[b], ir, r2r);
+                }
+                done = true;
+            }
+        }
+        for (int a = 0; a < nq && !done; ++a) {
             R s1 = rs[3 * a], s2 = rs[3 * a + 1], wa = rs[3 * a + 2];
             R x[3];
             for (int c = 0; c < 3; ++c)
