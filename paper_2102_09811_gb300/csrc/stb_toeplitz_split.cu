@@ -760,7 +760,7 @@ stb_status toeplitz_split_f32x(const float *A, int64_t E, int32_t n_steps, int32
 // 32-column halves with the 128-byte swizzle, into a ring of FP32 stages;
 // the workers slice them from shared memory into the bf16 slot ring.
 constexpr int PN_NS = 3;
-constexpr int PN_NA = 6;           // A-slice slots
+constexpr int PN_NA = 3;           // A-slice slots (one piece: its slicing is quick from shared memory)
 constexpr int PN_PB = 8;           // steps per panel
 constexpr int PN_MAX_Z = 64;       // slices of the block range
 constexpr int PN_G = 4;            // pieces per tensor-memory accumulation group
@@ -769,7 +769,7 @@ constexpr int PN_THREADS = SP_THREADS;  // warp 0 TMA, warp 1 MMA, 16 workers
 template <int N>
 struct PanelShape {
     static constexpr int NB = N == 64 ? 2 : 4;    // x-slice stages
-    static constexpr int NF = N == 16 ? 3 : 2;    // FP32 A stages
+    static constexpr int NF = 3;                  // FP32 A stages
     static constexpr uint32_t B_BYTES = N * 128;                  // one slice tile
     static constexpr uint32_t BSTAGE = PN_NS * B_BYTES;
     static constexpr uint32_t F_HALF = SP_M * 128;                // 32 FP32 columns
