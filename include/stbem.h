@@ -475,6 +475,18 @@ stb_status stb_toeplitz_matvec_ex(const void *A, int32_t a_storage, int64_t E, i
 stb_status stb_selftest_bounded_wait(const void *probe, int64_t limit_ns, int32_t arrive,
                                      void *workspace, size_t workspace_bytes, stb_stream stream);
 
+/* Self test of the grid barrier of the cooperative kernels (the march of a
+ * panel, the blocked Cholesky): one cooperative launch of n_cta CTAs (at most
+ * one per SM) in which every CTA but `skip` (-1: none) waits on one grid
+ * barrier with a limit of limit_ns nanoseconds (1e3 .. 1e10).  With a CTA
+ * skipping, the other CTAs' waits expire and the workspace status word
+ * receives STB_ERR_TIMEOUT; with skip = -1 it stays STB_OK.  Workspace: at
+ * least 512 + 4 n_cta bytes; bytes [512, 512 + 4 n_cta) receive one int32 per
+ * CTA (1: passed, 0: gave up, 2: skipped).  Asynchronous on `stream`; read
+ * the result with stb_workspace_status. */
+stb_status stb_selftest_grid_barrier(int32_t n_cta, int32_t skip, int64_t limit_ns, void *workspace,
+                                     size_t workspace_bytes, stb_stream stream);
+
 /* ---- the same product without any allocation (no counterpart in the paper) -------
  * For callers that cannot allocate device memory at the point of the call:
  * code running while a CUDA stream is being captured into a graph (where

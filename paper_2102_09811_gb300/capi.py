@@ -117,6 +117,7 @@ _SIGS = {
     "stb_neumann_error": (_I32, [_P, _PAR, _P, _I32, _I32, _P, _I32, _I32, _P, _P, _SZ, _P]),
     "stb_workspace_status": (_I32, [_P, _P]),
     "stb_selftest_bounded_wait": (_I32, [_P, _I64, _I32, _P, _SZ, _P]),
+    "stb_selftest_grid_barrier": (_I32, [_I32, _I32, _I64, _P, _SZ, _P]),
     "stb_measure_peaks": (_I32, [ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "stb_trace_enable": (_I32, [_I32]),
     "stb_trace_reset": (_I32, []),
@@ -598,6 +599,13 @@ def stb_selftest_bounded_wait(probe, limit_ns, arrive, workspace, stream=None):
                                                 _ptr(workspace),
                                                 workspace.numel() * workspace.element_size(),
                                                 _stream(stream)), "stb_selftest_bounded_wait")
+
+
+def stb_selftest_grid_barrier(n_cta, skip, limit_ns, workspace, stream=None):
+    _check(_library().stb_selftest_grid_barrier(int(n_cta), int(skip), int(limit_ns),
+                                                _ptr(workspace),
+                                                workspace.numel() * workspace.element_size(),
+                                                _stream(stream)), "stb_selftest_grid_barrier")
 
 
 def stb_measure_peaks(stream=None):

@@ -29,11 +29,12 @@ __device__ __forceinline__ uint64_t grid_ns() {
 // most the occupancy limit).  Thread 0 of each CTA arrives with a device-scope
 // atomic after a fence that publishes the CTA's writes; the last arrival
 // resets the count and advances the generation, the others poll the
-// generation.  A wait gives up after GRID_WAIT_NS: it sets the abort flag and
-// STB_ERR_TIMEOUT in *status, and every CTA then sees `false` from this or
-// its next barrier and must return.  Data written by other CTAs before the
+// generation.  A wait gives up after limit_ns (default GRID_WAIT_NS): it sets
+// the abort flag and STB_ERR_TIMEOUT in *status, and every CTA then sees
+// `false` from this or its next barrier and must return.  Data written by other CTAs before the
 // barrier must be read with L1-bypassing loads (__ldcg) after it.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *status) {
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *status,
+                                             uint64_t limit_ns = GRID_WAIT_NS) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -53,7 +54,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *status) {
                         ok = false;
                         break;
                     }
-                    if (grid_ns() - t0 > GRID_WAIT_NS) {
+                    if (grid_ns() - t0 > limit_ns) {
                         atomicExch(bar + 2, 1u);
                         atomicCAS(status, 0, STB_ERR_TIMEOUT);
                         ok = false;

@@ -1078,6 +1078,41 @@ static stb_status solve_blocks(int64_t E, const stb_params *p, const void *V, co
                                int32_t nrhs, double *w, void *ws, size_t ws_bytes,
                                stb_stream stream);
 
+// ------------------------------------------------- grid barrier self test ---
+// Every CTA but `skip` (-1: none) enters one grid barrier with the given
+// limit; out[b] = 1 if CTA b passed it, 0 if its wait gave up, 2 if it
+// skipped.  With a CTA skipping, the others' waits expire: STB_ERR_TIMEOUT.
+__global__ void k_selftest_grid(unsigned *bar, int32_t *status, int skip, uint64_t limit_ns,
+                                int32_t *out) {
+    int32_t r = 2;
+    if ((int)blockIdx.x != skip) r = grid_barrier(bar, status, limit_ns) ? 1 : 0;
+    if (threadIdx.x == 0) out[blockIdx.x] = r;
+}
+
+extern "C" stb_status stb_selftest_grid_barrier(int32_t n_cta, int32_t skip, int64_t limit_ns,
+                                                void *ws, size_t ws_bytes, stb_stream stream) {
+    if (n_cta < 1 || skip < -1 || skip >= n_cta)
+        return fail(STB_ERR_INVALID_ARG, "need n_cta >= 1 and -1 <= skip < n_cta");
+    if (limit_ns < 1000 || limit_ns > 10000000000ll)
+        return fail(STB_ERR_INVALID_ARG, "limit_ns must lie in [1000, 1e10]");
+    const int most = coop_grid(k_selftest_grid, 128, 0, 1);
+    if (n_cta > most) return fail(STB_ERR_INVALID_ARG, "n_cta above one CTA per SM (%d)", most);
+    const size_t need = 256 + 256 + (size_t)n_cta * sizeof(int32_t);
+    stb_status st = check_workspace(ws, ws_bytes, need);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    STB_CUDA(cudaMemsetAsync(ws, 0, 512, s));
+    unsigned *bar = reinterpret_cast<unsigned *>(static_cast<char *>(ws) + 256);
+    int32_t *out = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + 512);
+    count_launch(s);
+    if (cudaError_t e = launch_coop(k_selftest_grid, (unsigned)n_cta, 128, 0, s, bar, status_word(ws),
+                                    (int)skip, (uint64_t)limit_ns, out)) {
+        cudaGetLastError();
+        return fail(STB_ERR_CUDA, "k_selftest_grid: %s", cudaGetErrorString(e));
+    }
+    return check_launch("k_selftest_grid");
+}
+
 extern "C" stb_status stb_solve_workspace_size(const stb_mesh *mesh, const stb_params *p,
                                                int32_t nrhs, size_t *bytes) {
     if (!mesh) return fail(STB_ERR_INVALID_ARG, "invalid argument");

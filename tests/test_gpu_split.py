@@ -1,6 +1,7 @@
 """GPU: the split-operand block-Toeplitz product on the tensor cores
 (STB_ARITH_SPLIT, eq. V_mat) against the FP64 oracle product of the same FP32
-blocks, and the expiry path of the bounded device waits.
+blocks, and the expiry paths of the bounded device waits (mbarrier waits of
+the tensor-core kernels, grid barriers of the cooperative kernels).
 
 Bounds.  Per row, block and chunk of 64 columns, and per step vector and
 chunk of x, the split product scales by 2^-e (2^-g), 2^e the power of two
@@ -177,3 +178,28 @@ def test_bounded_wait_expires_without_fault():
     check(A, x, np.zeros_like(x), 0.0)
     with pytest.raises(capi.StbError):
         capi.stb_selftest_bounded_wait(probe, 10, arrive=False, workspace=ws)
+
+
+def test_grid_barrier_expires_without_fault():
+    """The grid barrier of the cooperative kernels: with every CTA arriving it
+    passes (status STB_OK, every CTA reports 1); with one CTA skipping it, the
+    others' waits expire after their limit (STB_ERR_TIMEOUT, those CTAs report
+    0, the skipping one 2) and the context stays usable."""
+    n = 8
+    ws = torch.zeros(512 + 4 * n, dtype=torch.uint8, device="cuda")
+    capi.stb_selftest_grid_barrier(n, -1, 1_000_000, ws)
+    capi.stb_workspace_status(ws)
+    out = ws[512:].view(torch.int32).cpu().tolist()
+    assert out == [1] * n, out
+    capi.stb_selftest_grid_barrier(n, 3, 1_000_000, ws)
+    with pytest.raises(capi.StbError) as e:
+        capi.stb_workspace_status(ws)
+    assert e.value.code == -7
+    out = ws[512:].view(torch.int32).cpu().tolist()
+    assert out[3] == 2 and all(v == 0 for i, v in enumerate(out) if i != 3), out
+    with pytest.raises(capi.StbError):
+        capi.stb_selftest_grid_barrier(n, n, 1_000_000, ws)  # skip out of range
+    rng = np.random.default_rng(2)
+    A = rng.normal(size=(3, 64, 64)).astype(np.float32).astype(np.float64)
+    x = rng.normal(size=(1, 3, 64))
+    check(A, x, np.zeros_like(x), 0.0)
