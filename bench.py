@@ -361,8 +361,9 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             # the oracle times whole rows; the step time is the rate scaled to all
-            # E rows of every problem of the workload
-            "extrapolated": True,
+            # E rows of every problem of the workload (measured, not scaled, when
+            # the sampled rows cover every problem's rows once per timed step)
+            "extrapolated": rows_total < E * len(alphas) * args.steps,
             "measured": {"rows": rows_total, "seconds": secs_total, "threads": threads,
                          "entries": 2.0 * n * E * rows_total},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
