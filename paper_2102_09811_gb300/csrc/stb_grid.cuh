@@ -31,8 +31,9 @@ __device__ __forceinline__ uint64_t grid_ns() {
 // resets the count and advances the generation, the others poll the
 // generation.  A wait gives up after limit_ns (default GRID_WAIT_NS): it sets
 // the abort flag and STB_ERR_TIMEOUT in *status, and every CTA then sees
-// `false` from this or its next barrier and must return.  Data written by other CTAs before the
-// barrier must be read with L1-bypassing loads (__ldcg) after it.
+// `false` from this or its next barrier and must return.  Data written by
+// other CTAs before the barrier must be read with L1-bypassing loads
+// (__ldcg) after it.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *status,
                                              uint64_t limit_ns = GRID_WAIT_NS) {
     __shared__ int ok_s;
