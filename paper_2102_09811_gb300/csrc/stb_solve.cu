@@ -549,13 +549,18 @@ __global__ void k_far_reduce(const T *__restrict__ part, int nz, int E, int n_st
 //   grid barrier
 //   phase 2: x_r^k = (V^0)^{-1} rv_r
 //   grid barrier (not after the last step)
-// A CTA owns blocks of 8 warps x MP_RW rows (grid-stride); the vectors of a
+// A CTA owns blocks of 8 warps x RW rows (grid-stride); the vectors of a
 // phase (x^{k-d}, or rv) are staged in shared memory chunk by chunk by the
 // whole CTA, read from L2 (__ldcg: other CTAs wrote them in this launch), and
 // each warp streams its rows of the matrix against them, four consecutive
 // columns per lane and load, MP_MR right-hand sides per pass.
 constexpr int MP_THREADS = 256;
-constexpr int MP_RW = 2;  // rows per warp
+// rows per warp: 3 for FP32 blocks and vectors (two 256-thread CTAs per SM,
+// about 126 registers), 2 otherwise
+template <class AT, class T>
+constexpr int mp_rw() { return sizeof(AT) == 4 && sizeof(T) == 4 ? 3 : 2; }
+template <class AT, class T>
+constexpr int mp_min_ctas() { return sizeof(AT) == 4 && sizeof(T) == 4 ? 2 : 1; }
 constexpr int MP_MR = 8;  // right-hand sides per pass
 // columns per staged chunk: 16 (FP64: 8) per lane and row, 2 KB of an FP32 row
 template <class AT, class T>
@@ -579,9 +584,9 @@ __device__ __forceinline__ void load4_cg(const T *p, int left, T v[4]) {
 
 // acc[i][r] += sum_j Mat[l0 + i][j] vec_r[j] (this lane's columns; rows past
 // E re-read row E-1 and are never stored), vec_r = vec + r vstride, r < nr.
-template <class MT, class T, int JC, bool VEC>
+template <class MT, class T, int JC, int RW, bool VEC>
 __device__ __forceinline__ void mp_pass(const MT *__restrict__ mat, int E, int l0, const T *vec,
-                                        size_t vstride, int nr, T *stage, T (&acc)[MP_RW][MP_MR]) {
+                                        size_t vstride, int nr, T *stage, T (&acc)[RW][MP_MR]) {
     constexpr int G = JC / 128;  // groups of four columns per lane
     const int lane = threadIdx.x & 31;
     for (int j0 = 0; j0 < E; j0 += JC) {
@@ -595,9 +600,9 @@ __device__ __forceinline__ void mp_pass(const MT *__restrict__ mat, int E, int l
             for (int u = 0; u < 4; ++u) stage[r * JC + jj + u] = v[u];
         }
         __syncthreads();
-        T m[MP_RW][G][4];
+        T m[RW][G][4];
 #pragma unroll
-        for (int i = 0; i < MP_RW; ++i)
+        for (int i = 0; i < RW; ++i)
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 const int jj = 128 * g + 4 * lane;
@@ -623,7 +628,7 @@ __device__ __forceinline__ void mp_pass(const MT *__restrict__ mat, int E, int l
                     xv[0] = a.x, xv[1] = a.y, xv[2] = b.x, xv[3] = b.y;
                 }
 #pragma unroll
-                for (int i = 0; i < MP_RW; ++i)
+                for (int i = 0; i < RW; ++i)
 #pragma unroll
                     for (int u = 0; u < 4; ++u) acc[i][r] = fma(m[i][g][u], xv[u], acc[i][r]);
             }
@@ -632,12 +637,12 @@ __device__ __forceinline__ void mp_pass(const MT *__restrict__ mat, int E, int l
 }
 
 // sums over the warp; lane i MP_MR + r ends up holding (row i, rhs r)
-template <class T>
-__device__ __forceinline__ T mp_reduce(T (&acc)[MP_RW][MP_MR]) {
+template <class T, int RW>
+__device__ __forceinline__ T mp_reduce(T (&acc)[RW][MP_MR]) {
     const int lane = threadIdx.x & 31;
     T mine = (T)0;
 #pragma unroll
-    for (int i = 0; i < MP_RW; ++i)
+    for (int i = 0; i < RW; ++i)
 #pragma unroll
         for (int r = 0; r < MP_MR; ++r) {
             T a = acc[i][r];
@@ -648,52 +653,53 @@ __device__ __forceinline__ T mp_reduce(T (&acc)[MP_RW][MP_MR]) {
 }
 
 template <class AT, class T, bool VEC>
-__global__ void __launch_bounds__(MP_THREADS)
+__global__ void __launch_bounds__(MP_THREADS, mp_min_ctas<AT, T>())
 k_march_panel(const AT *__restrict__ V, const T *__restrict__ Minv, int E, int n_steps, int nrhs,
               int kp, int nb, const double *__restrict__ hv, T *rv, T *x, unsigned *bar,
               int32_t *status) {
     constexpr int JC = mp_chunk<AT, T>();
-    static_assert(MP_RW * MP_MR <= 32, "one lane per (row, right-hand side)");
+    constexpr int RW = mp_rw<AT, T>();
+    static_assert(RW * MP_MR <= 32, "one lane per (row, right-hand side)");
     __shared__ __align__(16) T stage[MP_MR * JC];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rows_cta = 8 * MP_RW, n_rb = (E + rows_cta - 1) / rows_cta;
+    const int rows_cta = 8 * RW, n_rb = (E + rows_cta - 1) / rows_cta;
     const size_t EE = (size_t)E * E, SE = (size_t)n_steps * E;
     const int li = lane / MP_MR, lr = lane % MP_MR;  // this lane's (row, rhs) of a pass
     for (int c = 0; c < nb; ++c) {
         const int k = kp + c;
         for (int rb = blockIdx.x; rb < n_rb; rb += gridDim.x) {
-            const int l0 = rb * rows_cta + warp * MP_RW;
+            const int l0 = rb * rows_cta + warp * RW;
             for (int r0 = 0; r0 < nrhs; r0 += MP_MR) {
                 const int nr = min(MP_MR, nrhs - r0);
-                T acc[MP_RW][MP_MR];
+                T acc[RW][MP_MR];
 #pragma unroll
-                for (int i = 0; i < MP_RW; ++i)
+                for (int i = 0; i < RW; ++i)
 #pragma unroll
                     for (int r = 0; r < MP_MR; ++r) acc[i][r] = (T)0;
                 for (int d = 1; d <= c; ++d)
-                    mp_pass<AT, T, JC, VEC>(V + d * EE, E, l0, x + r0 * SE + (size_t)(k - d) * E, SE,
+                    mp_pass<AT, T, JC, RW, VEC>(V + d * EE, E, l0, x + r0 * SE + (size_t)(k - d) * E, SE,
                                             nr, stage, acc);
                 const T a = mp_reduce(acc);
                 const int l = l0 + li;
-                if (li < MP_RW && lr < nr && l < E)
+                if (li < RW && lr < nr && l < E)
                     rv[(size_t)(r0 + lr) * E + l] =
                         (T)(hv[((size_t)(r0 + lr) * PB + c) * E + l] - (double)a);
             }
         }
         if (!grid_barrier(bar, status)) return;
         for (int rb = blockIdx.x; rb < n_rb; rb += gridDim.x) {
-            const int l0 = rb * rows_cta + warp * MP_RW;
+            const int l0 = rb * rows_cta + warp * RW;
             for (int r0 = 0; r0 < nrhs; r0 += MP_MR) {
                 const int nr = min(MP_MR, nrhs - r0);
-                T acc[MP_RW][MP_MR];
+                T acc[RW][MP_MR];
 #pragma unroll
-                for (int i = 0; i < MP_RW; ++i)
+                for (int i = 0; i < RW; ++i)
 #pragma unroll
                     for (int r = 0; r < MP_MR; ++r) acc[i][r] = (T)0;
-                mp_pass<T, T, JC, VEC>(Minv, E, l0, rv + (size_t)r0 * E, E, nr, stage, acc);
+                mp_pass<T, T, JC, RW, VEC>(Minv, E, l0, rv + (size_t)r0 * E, E, nr, stage, acc);
                 const T a = mp_reduce(acc);
                 const int l = l0 + li;
-                if (li < MP_RW && lr < nr && l < E) x[(size_t)(r0 + lr) * SE + (size_t)k * E + l] = a;
+                if (li < RW && lr < nr && l < E) x[(size_t)(r0 + lr) * SE + (size_t)k * E + l] = a;
             }
         }
         if (c + 1 < nb && !grid_barrier(bar, status)) return;
@@ -935,7 +941,8 @@ static stb_status march(const AT *V, int E, int n_steps, int nrhs, const double 
     const bool mp_vec = vec && reinterpret_cast<uintptr_t>(S.L) % 16 == 0 &&
                         reinterpret_cast<uintptr_t>(S.rv) % 16 == 0;
     const auto mp_kern = mp_vec ? k_march_panel<AT, T, true> : k_march_panel<AT, T, false>;
-    const int mp_rows = (E + 8 * MP_RW - 1) / (8 * MP_RW);
+    constexpr int RW = mp_rw<AT, T>();
+    const int mp_rows = (E + 8 * RW - 1) / (8 * RW);
     const int mp_grid = std::min(mp_rows, coop_grid(mp_kern, MP_THREADS, 0, 4));
     if (mp_grid < 1) return fail(STB_ERR_CUDA, "march: no resident grid for k_march_panel");
     STB_CUDA(grid_barrier_reset(S.bar, s));
