@@ -555,12 +555,11 @@ __global__ void k_far_reduce(const T *__restrict__ part, int nz, int E, int n_st
 // each warp streams its rows of the matrix against them, four consecutive
 // columns per lane and load, MP_MR right-hand sides per pass.
 constexpr int MP_THREADS = 256;
-// rows per warp: 3 for FP32 blocks and vectors (two 256-thread CTAs per SM,
-// about 126 registers), 2 otherwise
-template <class AT, class T>
-constexpr int mp_rw() { return sizeof(AT) == 4 && sizeof(T) == 4 ? 3 : 2; }
-template <class AT, class T>
-constexpr int mp_min_ctas() { return sizeof(AT) == 4 && sizeof(T) == 4 ? 2 : 1; }
+// rows per warp RW: 2, or 3 for FP32 blocks and vectors when the 24-row
+// blocks still give every SM one (fewer, larger blocks then stream the
+// matrices faster: two 256-thread CTAs per SM at about 126 registers)
+template <class AT, class T, int RW>
+constexpr int mp_min_ctas() { return sizeof(AT) == 4 && sizeof(T) == 4 && RW == 3 ? 2 : 1; }
 constexpr int MP_MR = 8;  // right-hand sides per pass
 // columns per staged chunk: 16 (FP64: 8) per lane and row, 2 KB of an FP32 row
 template <class AT, class T>
@@ -652,13 +651,12 @@ __device__ __forceinline__ T mp_reduce(T (&acc)[RW][MP_MR]) {
     return mine;
 }
 
-template <class AT, class T, bool VEC>
-__global__ void __launch_bounds__(MP_THREADS, mp_min_ctas<AT, T>())
+template <class AT, class T, int RW, bool VEC>
+__global__ void __launch_bounds__(MP_THREADS, mp_min_ctas<AT, T, RW>())
 k_march_panel(const AT *__restrict__ V, const T *__restrict__ Minv, int E, int n_steps, int nrhs,
               int kp, int nb, const double *__restrict__ hv, T *rv, T *x, unsigned *bar,
               int32_t *status) {
     constexpr int JC = mp_chunk<AT, T>();
-    constexpr int RW = mp_rw<AT, T>();
     static_assert(RW * MP_MR <= 32, "one lane per (row, right-hand side)");
     __shared__ __align__(16) T stage[MP_MR * JC];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -940,8 +938,15 @@ static stb_status march(const AT *V, int E, int n_steps, int nrhs, const double 
     // can be resident at once (4 per SM)
     const bool mp_vec = vec && reinterpret_cast<uintptr_t>(S.L) % 16 == 0 &&
                         reinterpret_cast<uintptr_t>(S.rv) % 16 == 0;
-    const auto mp_kern = mp_vec ? k_march_panel<AT, T, true> : k_march_panel<AT, T, false>;
-    constexpr int RW = mp_rw<AT, T>();
+    int dev = 0, sms = 0;
+    STB_CUDA(cudaGetDevice(&dev));
+    STB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    constexpr int RW_HI = f32 ? 3 : 2;
+    const bool rw3 = f32 && (E + 23) / 24 >= sms;
+    const auto mp_kern =
+        rw3 ? (mp_vec ? k_march_panel<AT, T, RW_HI, true> : k_march_panel<AT, T, RW_HI, false>)
+            : (mp_vec ? k_march_panel<AT, T, 2, true> : k_march_panel<AT, T, 2, false>);
+    const int RW = rw3 ? RW_HI : 2;
     const int mp_rows = (E + 8 * RW - 1) / (8 * RW);
     const int mp_grid = std::min(mp_rows, coop_grid(mp_kern, MP_THREADS, 0, 4));
     if (mp_grid < 1) return fail(STB_ERR_CUDA, "march: no resident grid for k_march_panel");
